@@ -1,0 +1,613 @@
+"""Pins of the FP64 oracle against facts the mathematics fixes.
+
+None of these compares the oracle with a retyped copy of itself: each checks
+a closed form, a textbook constant, an exact finite difference, an invariant
+or a brute-force enumeration.  A dropped term, a wrong sign, a wrong index or
+a transposed operand in the oracle fails at least one of them.
+"""
+
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.special import erfc
+
+import oracle
+from paper_0902_0827_gb300 import systems as S
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def read_golden(name):
+    out = {}
+    shells = []
+    for line in open(os.path.join(GOLD, name)):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        k, *v = line.split()
+        if k == "shell":
+            shells.append((float(v[0]), int(v[1])))
+        else:
+            out[k] = float(v[0])
+    return out, shells
+
+
+def make_sys(pos, box, q=None, types=None, sigma=(3.0,), eps=(0.2,), excl=(), p14=(),
+             rc=9.0, rs=7.5, alpha=0.0, ke=S.COULOMB_K, s14lj=0.5, s14c=1 / 1.2):
+    pos = np.asarray(pos, np.float32).reshape(-1, 3)
+    n = pos.shape[0]
+    return S.System("t", pos, np.zeros(n, np.float32) if q is None else np.asarray(q, np.float32),
+                    np.zeros(n, np.int32) if types is None else np.asarray(types, np.int32),
+                    np.asarray(sigma, np.float32), np.asarray(eps, np.float32),
+                    np.asarray(box, np.float32),
+                    np.asarray(excl, np.int32).reshape(-1, 2), np.asarray(p14, np.int32).reshape(-1, 2),
+                    cutoff=rc, switch_dist=rs, ewald_alpha=alpha, coulomb_k=ke,
+                    scale14_lj=s14lj, scale14_coul=s14c)
+
+
+def dyadic(sys, bits=10):
+    """Round coordinates to multiples of 2^-bits so FP32 shifts stay exact."""
+    g = 2.0 ** bits
+    pos = np.floor(sys.pos.astype(np.float64) * g) / g
+    box = np.floor(sys.box.astype(np.float64) * g) / g
+    pos = np.mod(pos, box)
+    return S.System(sys.name, pos.astype(np.float32), sys.q, sys.type, sys.sigma, sys.epsilon,
+                    box.astype(np.float32), sys.excl, sys.pairs14, sys.cutoff, sys.switch_dist,
+                    sys.ewald_alpha, sys.coulomb_k, sys.scale14_lj, sys.scale14_coul)
+
+
+# ---------------------------------------------------------------- closed forms
+
+def test_lj_pair_minimum():
+    sig, eps = 3.4, 0.238
+    rmin = 2 ** (1 / 6) * sig
+    s = make_sys([[5, 5, 5], [5 + rmin, 5, 5]], [40, 40, 40], sigma=[sig], eps=[eps], rc=12, rs=11)
+    F, E, W, n = oracle.forces(s)
+    x = s.pos.astype(np.float64)
+    r = x[1, 0] - x[0, 0]
+    assert n == 1
+    # E(r) = -eps at the minimum (eps as stored in FP32); the FP32 position is
+    # within 1 ulp of rmin, a second-order change of the energy.
+    assert abs(E[0] + float(np.float32(eps))) < 1e-12
+    assert np.abs(F).max() < 1e-5
+    # r = sigma: zero energy
+    s2 = make_sys([[5, 5, 5], [5 + sig, 5, 5]], [40, 40, 40], sigma=[sig], eps=[eps], rc=12, rs=11)
+    _, E2, _, _ = oracle.forces(s2)
+    r2 = float(s2.pos[1, 0]) - float(s2.pos[0, 0])
+    sig32, eps32 = float(np.float32(sig)), float(np.float32(eps))
+    assert abs(E2[0] - 4 * eps32 * ((sig32 / r2) ** 12 - (sig32 / r2) ** 6)) < 1e-12
+    assert abs(E2[0]) < 1e-5
+
+
+def test_lorentz_berthelot_mixing():
+    # two types: unlike pair uses sigma=(s1+s2)/2, eps=sqrt(e1 e2); at its own
+    # minimum the pair energy is -eps_12.
+    s1, s2, e1, e2 = 2.0, 4.0, 0.05, 0.2
+    s12, e12 = 3.0, math.sqrt(float(np.float32(e1)) * float(np.float32(e2)))
+    r = 2 ** (1 / 6) * s12
+    s = make_sys([[5, 5, 5], [5, 5 + r, 5]], [40, 40, 40], types=[0, 1], sigma=[s1, s2], eps=[e1, e2],
+                 rc=12, rs=11)
+    _, E, _, _ = oracle.forces(s)
+    assert abs(E[0] + e12) < 1e-9
+
+
+def test_coulomb_plain_and_ewald():
+    q1, q2 = 0.8, -0.45
+    for alpha in (0.0, 0.32):
+        s = make_sys([[3, 3, 3], [3, 3, 7.25]], [30, 30, 30], q=[q1, q2], eps=[0.0], alpha=alpha)
+        F, E, W, n = oracle.forces(s)
+        r = float(s.pos[1, 2]) - float(s.pos[0, 2])
+        qq = float(np.float32(q1)) * float(np.float32(q2)) * float(np.float32(S.COULOMB_K))
+        want = qq / r if alpha == 0 else qq * erfc(float(np.float32(alpha)) * r) / r
+        assert abs(E[1] - want) < 1e-12 * abs(want)
+        assert E[0] == 0.0
+        if alpha == 0:
+            # attractive: force on atom 0 points to +z with magnitude |qq|/r^2
+            assert abs(F[0, 2] + qq / r ** 2) < 1e-12 * abs(qq / r ** 2)
+            assert F[0, 2] > 0
+
+
+def test_switch_endpoints_and_smoothness():
+    sig, eps, rc, rs = 3.0, 0.2, 9.0, 7.5
+
+    def e_at(r):
+        s = make_sys([[2, 2, 2], [2 + r, 2, 2]], [40, 40, 40], sigma=[sig], eps=[eps], rc=rc, rs=rs)
+        F, E, W, n = oracle.forces(s)
+        rr = float(s.pos[1, 0]) - float(s.pos[0, 0])
+        return rr, E[0], F[1, 0], n
+
+    def u(r):
+        e32 = float(np.float32(eps))
+        return 4 * e32 * ((sig / r) ** 12 - (sig / r) ** 6)
+
+    # S(r) = 1 at and below rs: energy equals the bare LJ
+    r, E, _, _ = e_at(rs)
+    assert abs(E - u(r)) < 1e-14
+    r, E, _, _ = e_at(6.0)
+    assert abs(E - u(r)) < 1e-14
+    # energy -> 0 as r -> rc (S(rc) = 0) and the pair leaves the cutoff at rc
+    # the switch has a double zero at rc (energy and force vanish there)
+    r, E, F, n = e_at(rc - 1e-3)
+    r_, E_, F_, _ = e_at(rc - 2e-3)
+    assert n == 1 and abs(E) < 1e-5 * abs(u(r))
+    assert abs(E / E_ - ((rc - r) / (rc - r_)) ** 2) < 0.01
+    assert abs(F / F_ - (rc - r) / (rc - r_)) < 0.01
+    _, E, _, n = e_at(rc)
+    assert n == 0 and E == 0.0
+    # force is continuous across rs (S' continuous): compare just below / above
+    # (linear extrapolation to rs from each side agrees to O(delta^2))
+    dlt = 1e-3
+    Fl = [e_at(rs - k * dlt) for k in (1, 2)]
+    Fr = [e_at(rs + k * dlt) for k in (1, 2)]
+    left = 2 * Fl[0][2] - Fl[1][2]
+    right = 2 * Fr[0][2] - Fr[1][2]
+    assert abs(left - right) < 1e-3 * abs(left)
+    # force equals -dE/dr inside the switching region (central FD in FP64)
+    rm, Em, _, _ = e_at(8.2 - 1e-3)
+    rp, Ep, _, _ = e_at(8.2 + 1e-3)
+    r0, _, F0, _ = e_at(8.2)
+    assert abs(F0 - (-(Ep - Em) / (rp - rm))) < 1e-5 * abs(F0) + 1e-10
+
+
+# --------------------------------------------------------------- FCC lattice
+
+def _fcc_shells(rmax_over_rnn):
+    """Shells of the FCC lattice by integer enumeration: points with integer
+    coordinates and even coordinate sum, in units of a/2 (r_nn = sqrt 2)."""
+    m = int(math.ceil(rmax_over_rnn * math.sqrt(2))) + 1
+    g = np.arange(-m, m + 1)
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    pts = np.stack([X, Y, Z], -1).reshape(-1, 3)
+    pts = pts[(pts.sum(1) % 2 == 0) & np.any(pts != 0, 1)]
+    r2 = (pts ** 2).sum(1)  # in units (a/2)^2; r_nn^2 = 2
+    vals, counts = np.unique(r2, return_counts=True)
+    return np.sqrt(vals / 2.0), counts
+
+
+def test_fcc_shell_structure_matches_golden():
+    _, shells = read_golden("fcc_lattice_sums.txt")
+    r, c = _fcc_shells(2.5)
+    for (rg, cg), rr, cc in zip(shells, r, c):
+        assert abs(rg - rr) < 1e-12 and cg == cc
+
+
+def test_fcc_lattice_sum_constants():
+    gold, _ = read_golden("fcc_lattice_sums.txt")
+    r, c = _fcc_shells(60)
+    keep = r < 60
+    a12 = (c[keep] * r[keep] ** -12.0).sum()
+    a6 = (c[keep] * r[keep] ** -6.0).sum()
+    a6 += 4 * math.pi * (math.sqrt(2) / 1.0) * (1 / 60 ** 3) / 3 * 0 + \
+        (4 * math.pi / 3) * (4 / (2 * math.sqrt(2))) / 60 ** 3  # continuum tail, rho = sqrt2 / r_nn^3
+    assert abs(a12 - gold["A12"]) < 1e-5
+    assert abs(a6 - gold["A6"]) < 1e-4
+
+
+def test_fcc_pair_set_is_the_lattice():
+    s = S.lj_fcc()
+    F, E, W, n = oracle.forces(s)
+    r, c = _fcc_shells(3)
+    rnn = S.fcc_lattice_constant() / math.sqrt(2)
+    per_atom = int(c[r * rnn < 8.5].sum())
+    assert per_atom == 54
+    assert n == s.n_atoms * per_atom // 2 == 6912
+    pairs = oracle.pairs(s)
+    cnt = np.bincount(pairs.ravel(), minlength=s.n_atoms)
+    assert np.all(cnt == 54)
+
+
+def test_fcc_perfect_lattice_energy_and_zero_force():
+    gold, _ = read_golden("fcc_lattice_sums.txt")
+    sig, eps, rc, rs = 3.4, 0.238, 8.5, 7.5
+    a = S.fcc_lattice_constant()
+    ncell = 4
+    basis = np.array([[0, 0, 0], [0.5, 0.5, 0], [0.5, 0, 0.5], [0, 0.5, 0.5]])
+    cells = np.stack(np.meshgrid(*[np.arange(ncell)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    pos = ((cells[:, None, :] + basis[None]) * a).reshape(-1, 3)
+    s = make_sys(pos, [a * ncell] * 3, sigma=[sig], eps=[eps], rc=rc, rs=rs)
+    F, E, W, n = oracle.forces(s)
+    # lattice sum over shells inside the cutoff, with the CHARMM switch on shell 4
+    rnn = a / math.sqrt(2)
+    r, c = _fcc_shells(3)
+    rr = r * rnn
+    keep = rr < rc
+    u = 4 * eps * ((sig / rr) ** 12 - (sig / rr) ** 6)
+    Sw = np.where(rr <= rs, 1.0, (rc ** 2 - rr ** 2) ** 2 * (rc ** 2 + 2 * rr ** 2 - 3 * rs ** 2) / (rc ** 2 - rs ** 2) ** 3)
+    want = 0.5 * (c[keep] * Sw[keep] * u[keep]).sum()
+    # FP32 rounding of the lattice positions moves r by ~1e-6 A
+    assert abs(E[0] / s.n_atoms - want) < 1e-5 * abs(want)
+    assert np.abs(F).max() < 1e-3
+    # the shell count inside the switch differs from the bare lattice sum only
+    # by the switched/truncated tail: no-cutoff limit pinned by A12/A6 below
+    assert n == 6912
+
+
+def test_fcc_cohesive_energy_converges_to_lattice_sums():
+    gold, _ = read_golden("fcc_lattice_sums.txt")
+    sig, eps = 3.4, 0.238
+    a = 5.7266
+    ncell = 8
+    basis = np.array([[0, 0, 0], [0.5, 0.5, 0], [0.5, 0, 0.5], [0, 0.5, 0.5]])
+    cells = np.stack(np.meshgrid(*[np.arange(ncell)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    pos = ((cells[:, None, :] + basis[None]) * a).reshape(-1, 3)
+    L = a * ncell
+    rc = 0.49 * L
+    s = make_sys(pos, [L] * 3, sigma=[sig], eps=[eps], rc=rc, rs=rc)  # no switch
+    F, E, W, n = oracle.forces(s, method="cells")
+    rnn = a / math.sqrt(2)
+    x = sig / rnn
+    lattice = 2 * eps * (gold["A12"] * x ** 12 - gold["A6"] * x ** 6)
+    # truncation tail of the r^-6 term: 2 pi rho (4 eps sig^6) / (3 rc^3)
+    rho = 4 / a ** 3
+    tail = -2 * math.pi * rho * 4 * eps * sig ** 6 / (3 * rc ** 3)
+    assert abs(E[0] / s.n_atoms - (lattice - tail)) < 2e-3 * abs(lattice)
+
+
+# ------------------------------------------------------------ finite differences
+
+def small_water(nw=216, k=11, alpha=0.32):
+    s = S._water_system(S.rng_for(k), nw, "w", alpha=alpha)
+    return s
+
+
+def _pair_margin_ok(s, atoms, h, rc):
+    """True for atoms none of whose pairs lie within h of rc (FD is then smooth)."""
+    x = s.pos.astype(np.float64)
+    d = x[None, :, :] - x[atoms, None, :]
+    d -= s.box * np.round(d / s.box)
+    r = np.sqrt((d ** 2).sum(-1))
+    return np.all(np.abs(r - rc) > 2 * h, axis=1)
+
+
+def test_force_is_minus_gradient():
+    s = dyadic(small_water(), bits=8)
+    F, E, W, n = oracle.forces(s)
+    rng = np.random.default_rng(0)
+    atoms = rng.choice(s.n_atoms, 24, replace=False)
+    h = 2.0 ** -14  # x on a 2^-8 grid below 32 -> x +- h is exact in FP32
+    ok = _pair_margin_ok(s, atoms, 1e-3, s.cutoff)
+    checked = 0
+    for a, good in zip(atoms, ok):
+        if not good:
+            continue
+        for ax in range(3):
+            p = s.pos.copy()
+            p[a, ax] += np.float32(h)
+            _, Ep, _, _ = oracle.forces(s, pos=p)
+            p[a, ax] -= np.float32(2 * h)
+            _, Em, _, _ = oracle.forces(s, pos=p)
+            g = (Ep.sum() - Em.sum()) / (2 * h)
+            assert abs(F[a, ax] + g) < 1e-6 * max(1.0, abs(F[a, ax])), (a, ax, F[a, ax], -g)
+            checked += 1
+    assert checked >= 30
+
+
+def test_newton_third_law_and_translation():
+    s = dyadic(S.solvated_chain(), bits=10) if False else dyadic(small_water(), bits=10)
+    F, E, W, n = oracle.forces(s)
+    assert np.abs(F.sum(0)).max() < 1e-9 * np.abs(F).max() * s.n_atoms ** 0.5
+    # exact translation by a dyadic vector, re-wrapped: identical pair set and values
+    shift = np.array([3.0 + 2 ** -10, -7.5, 11.25])
+    p = np.mod(s.pos.astype(np.float64) + shift, s.box.astype(np.float64)).astype(np.float32)
+    F2, E2, W2, n2 = oracle.forces(s, pos=p)
+    assert n2 == n
+    assert np.allclose(E2, E, rtol=1e-12, atol=1e-9)
+    assert np.abs(F2 - F).max() < 1e-9 * np.abs(F).max()
+    assert np.allclose(W2, W, rtol=1e-10, atol=1e-8)
+
+
+def test_permutation_invariance():
+    s = small_water(64, k=12)
+    F, E, W, n = oracle.forces(s)
+    rng = np.random.default_rng(1)
+    perm = rng.permutation(s.n_atoms)
+    inv = np.argsort(perm)
+    s2 = S.System("p", s.pos[perm], s.q[perm], s.type[perm], s.sigma, s.epsilon, s.box,
+                  inv[s.excl].astype(np.int32), inv[s.pairs14].astype(np.int32).reshape(-1, 2),
+                  s.cutoff, s.switch_dist, s.ewald_alpha)
+    F2, E2, W2, n2 = oracle.forces(s2)
+    assert n2 == n
+    assert np.allclose(E2, E, rtol=1e-12)
+    assert np.abs(F2 - F[perm]).max() < 1e-10 * np.abs(F).max()
+
+
+def test_virial_from_affine_scaling():
+    # LJ-only FCC crystal on a dyadic grid (all pairs far from rc): scaling
+    # x -> lam x, L -> lam L with lam = 1 +- 2^-12 is exact in FP32.
+    base = S.lj_fcc()
+    g = 2.0 ** 6
+    L = math.floor(float(base.box[0]) * g) / g
+    pos = np.mod(np.floor(base.pos.astype(np.float64) * g) / g, L)
+    s = make_sys(pos, [L] * 3, sigma=[3.4], eps=[0.238], rc=8.5, rs=7.5)
+    F, E, W, n = oracle.forces(s)
+    def fd(axes, h):
+        Es = []
+        for lam in (1 + h, 1 - h):
+            sc = np.ones(3)
+            sc[list(axes)] = lam
+            s2 = make_sys(pos * sc, np.array([L] * 3) * sc, sigma=[3.4], eps=[0.238], rc=8.5, rs=7.5)
+            assert np.all(s2.pos.astype(np.float64) == pos * sc)
+            _, E2, _, n2 = oracle.forces(s2)
+            assert n2 == n
+            Es.append(E2[0])
+        return (Es[0] - Es[1]) / (2 * h)
+
+    for axes, want in (((0, 1, 2), -(W[0] + W[1] + W[2])), ((0,), -W[0]), ((2,), -W[2])):
+        # Richardson extrapolation of two exact central differences, O(h^4)
+        g_fd = (4 * fd(axes, 2.0 ** -12) - fd(axes, 2.0 ** -11)) / 3
+        assert abs(g_fd - want) < 1e-7 * abs(want) + 1e-9, (axes, g_fd, want)
+    # symmetric tensor: off-diagonals from the same pair sum are finite and small
+    assert np.all(np.isfinite(W))
+
+
+# ------------------------------------------------------------------- topology
+
+def test_single_water_is_fully_excluded():
+    s = S._water_system(S.rng_for(5), 1, "one")
+    s = S.System("one", s.pos, s.q, s.type, s.sigma, s.epsilon, np.full(3, 30, np.float32),
+                 s.excl, s.pairs14, 9.0, 7.5, 0.32)
+    F, E, W, n = oracle.forces(s)
+    assert n == 0 and np.all(E == 0) and np.all(F == 0)
+
+
+def test_exclusion_removal_adds_closed_form_term():
+    w = S._water_system(S.rng_for(6), 2, "two")
+    pos = np.array(w.pos, np.float64)
+    box = np.full(3, 30.0)
+    pos[3:] += 4.0
+    base = dict(q=w.q, types=w.type, sigma=w.sigma, eps=w.epsilon, alpha=0.0)
+    ex = w.excl
+    s_all = make_sys(pos, box, excl=ex, **base)
+    _, E_all, _, n_all = oracle.forces(s_all)
+    # drop the O-H1 exclusion of water 0 (atoms 0, 1)
+    keep = ~((ex[:, 0] == 0) & (ex[:, 1] == 1))
+    s_less = make_sys(pos, box, excl=ex[keep], **base)
+    _, E_less, _, n_less = oracle.forces(s_less)
+    x = s_less.pos.astype(np.float64)
+    r = np.linalg.norm(x[1] - x[0])
+    qq = float(w.q[0]) * float(w.q[1]) * float(np.float32(S.COULOMB_K))
+    assert n_less == n_all + 1
+    assert abs((E_less[1] - E_all[1]) - qq / r) < 1e-10
+    assert E_less[0] == E_all[0]  # H has eps = 0
+
+
+def test_scaled_14_pair_is_exact_multiple():
+    pos = [[5, 5, 5], [5, 8.2, 5.5]]
+    common = dict(q=[0.3, -0.7], sigma=[3.0], eps=[0.15], alpha=0.32, rc=9, rs=7.5)
+    _, E_n, _, _ = oracle.forces(make_sys(pos, [30] * 3, **common))
+    _, E_s, _, _ = oracle.forces(make_sys(pos, [30] * 3, p14=[[0, 1]], s14lj=0.5, s14c=0.8, **common))
+    assert abs(E_s[0] - 0.5 * E_n[0]) < 1e-15 * abs(E_n[0]) + 1e-300
+    assert abs(E_s[1] - np.float32(0.8) * E_n[1]) < 1e-13 * abs(E_n[1])
+
+
+def test_cell_list_equals_all_pairs():
+    for s in (small_water(), S.lj_fcc()):
+        F, E, W, n = oracle.forces(s)
+        F2, E2, W2, n2 = oracle.forces(s, method="cells")
+        assert n == n2
+        assert np.allclose(E, E2, rtol=1e-12, atol=1e-10)
+        assert np.abs(F - F2).max() < 1e-10 * np.abs(F).max()
+        assert np.allclose(W, W2, rtol=1e-10, atol=1e-8)
+
+
+def test_pairs_brute_force_on_tiny_box():
+    s = small_water(216, k=13)
+    ij = oracle.pairs(s)
+    x = s.pos.astype(np.float32)
+    n = s.n_atoms
+    excl = {(min(a, b), max(a, b)) for a, b in s.excl}
+    want = []
+    rc2 = np.float32(s.cutoff) * np.float32(s.cutoff)
+    half = np.float32(0.5) * s.box
+    for i in range(n):
+        s_ = x[i + 1:] - x[i]          # x_j - x_i in FP32
+        d = s_.copy()
+        up = s_ > half
+        dn = s_ < -half
+        xj = x[i + 1:]
+        d = np.where(up, (xj - s.box) - x[i], d)
+        d = np.where(dn, xj - (x[i] - s.box), d)
+        r2 = (d[:, 0] * d[:, 0]).astype(np.float32)
+        r2 = np.float32(np.fma(d[:, 1].astype(np.float64), d[:, 1], r2)) if False else r2
+        # fma in FP32 via exact FP64 product-sum then one rounding
+        r2 = (d[:, 1].astype(np.float64) * d[:, 1] + r2).astype(np.float32)
+        r2 = (d[:, 2].astype(np.float64) * d[:, 2] + r2).astype(np.float32)
+        for j in np.nonzero(r2 < rc2)[0]:
+            if (i, i + 1 + j) not in excl:
+                want.append((i, i + 1 + j))
+    want = np.array(want, np.int32)
+    assert ij.shape == want.shape and np.all(ij == want)
+
+
+# ------------------------------------------------------------------- adjoint
+
+def _tables_sys(s, A, B):
+    return A, B
+
+
+def test_adjoint_charges_exact_fd():
+    s = small_water(64, k=14)
+    rng = np.random.default_rng(2)
+    G = rng.normal(size=(s.n_atoms, 3))
+    gE = 0.7
+    dx, dq, dA, dB = oracle.backward(s, G, gE)
+
+    def Lq(q):
+        F, E, _, _ = oracle.forces(s, q=q)
+        return (G * F).sum() + gE * E.sum()
+
+    for k in rng.choice(s.n_atoms, 8, replace=False):
+        qp = s.q.copy(); qp[k] = np.float32(qp[k] + 0.25)
+        qm = s.q.copy(); qm[k] = np.float32(qm[k] - 0.25)
+        step = float(qp[k]) - float(qm[k])
+        g = (Lq(qp) - Lq(qm)) / step          # L is linear in each q_k: exact
+        assert abs(g - dq[k]) < 1e-9 * max(1.0, abs(dq[k])), (k, g, dq[k])
+
+
+def _forces_with_tables(s, A, B, pos=None):
+    """Forward with explicit (A, B) tables through the C entry point."""
+    import ctypes
+    args, keep = oracle._args(s, pos)
+    A = np.ascontiguousarray(A, np.float64)
+    B = np.ascontiguousarray(B, np.float64)
+    args[5] = oracle._p(A)
+    args[6] = oracle._p(B)
+    n = args[0]
+    F = np.zeros((n, 3)); E = np.zeros(2); W = np.zeros(6)
+    oracle.lib().orc_forces_allpairs(*args, oracle._p(F), oracle._p(E), oracle._p(W))
+    return F, E
+
+
+def test_adjoint_lj_tables_exact_fd():
+    s = S.solvated_chain()
+    # a small piece: chain atoms only, in a big enough box
+    idx = np.arange(300)
+    sub = S.System("c", s.pos[idx], s.q[idx], s.type[idx], s.sigma, s.epsilon, s.box,
+                   s.excl[(s.excl < 300).all(1)], s.pairs14[(s.pairs14 < 300).all(1)],
+                   9.0, 7.5, 0.32)
+    rng = np.random.default_rng(3)
+    G = rng.normal(size=(sub.n_atoms, 3))
+    gE = -0.3
+    dx, dq, dA, dB = oracle.backward(sub, G, gE)
+    _, _, A, B = oracle.combine_lb(sub.sigma, sub.epsilon)
+    used = np.unique(sub.type)
+    for (a, b) in [(used[0], used[1]), (used[2], used[2]), (used[3], used[5])]:
+        for tab, grad in ((A, dA), (B, dB)):
+            hstep = 0.01 * tab[a, b]
+            Tp = tab.copy(); Tp[a, b] += hstep; Tp[b, a] = Tp[a, b]
+            Tm = tab.copy(); Tm[a, b] -= hstep; Tm[b, a] = Tm[a, b]
+            if tab is A:
+                Fp, Ep = _forces_with_tables(sub, Tp, B); Fm, Em = _forces_with_tables(sub, Tm, B)
+            else:
+                Fp, Ep = _forces_with_tables(sub, A, Tp); Fm, Em = _forces_with_tables(sub, A, Tm)
+            g = ((G * Fp).sum() + gE * Ep.sum() - (G * Fm).sum() - gE * Em.sum()) / (2 * hstep)
+            assert abs(g - grad[a, b]) < 1e-7 * max(abs(grad[a, b]), 1e-12) + 1e-14, (a, b, g, grad[a, b])
+
+
+def test_adjoint_hvp_matches_force_fd():
+    s = dyadic(small_water(125, k=15), bits=10)
+    rng = np.random.default_rng(4)
+    G = rng.integers(-4, 5, size=(s.n_atoms, 3)).astype(np.float64)
+    dx, dq, dA, dB = oracle.backward(s, G, 0.0)
+    h = 2.0 ** -18  # x on a 2^-10 grid below 32, G integer: x +- hG is exact in FP32
+    pp = (s.pos.astype(np.float64) + h * G)
+    pm = (s.pos.astype(np.float64) - h * G)
+    assert np.all(pp.astype(np.float32) == pp) and np.all(pm.astype(np.float32) == pm)
+    Fp, Ep, _, np_ = oracle.forces(s, pos=pp.astype(np.float32))
+    Fm, Em, _, nm = oracle.forces(s, pos=pm.astype(np.float32))
+    # dL/dx = -H G for L = G.F; -H G = (F(x+hG) - F(x-hG)) / (2h) per atom
+    fd = (Fp - Fm) / (2 * h)
+    # compare atoms none of whose pairs lie near rc (the truncated Coulomb
+    # force jumps there, so the stencil is only smooth away from it)
+    ok = _pair_margin_ok(s, np.arange(s.n_atoms), 1e-4, s.cutoff)
+    assert ok.sum() > 0.8 * s.n_atoms
+    assert abs(np_ - nm) <= (~ok).sum()
+    assert np.abs(fd[ok] - dx[ok]).max() < 1e-6 * np.abs(dx).max()
+    # translation invariance of the adjoint: sum_i dL/dx_i = 0
+    assert np.abs(dx.sum(0)).max() < 1e-9 * np.abs(dx).max() * s.n_atoms
+    # gE term alone: dL/dx = -gE F
+    F, E, W, n = oracle.forces(s)
+    dx2, _, _, _ = oracle.backward(s, np.zeros_like(G), 1.0)
+    assert np.abs(dx2 + F).max() < 1e-12 * np.abs(F).max()
+
+
+def test_adjoint_hessian_symmetry_and_homogeneity():
+    s = small_water(64, k=16)
+    rng = np.random.default_rng(5)
+    v = rng.normal(size=(s.n_atoms, 3))
+    w = rng.normal(size=(s.n_atoms, 3))
+    Hv, dqv, dAv, dBv = oracle.backward(s, v, 0.0)
+    Hw, _, _, _ = oracle.backward(s, w, 0.0)
+    assert abs((w * Hv).sum() - (v * Hw).sum()) < 1e-10 * abs((w * Hv).sum())
+    # Euler homogeneity: F_C is degree 2 in q, F_LJ degree 1 in (A, B)
+    F, E, _, _ = oracle.forces(s)
+    zero = np.zeros_like(s.q)
+    F_lj, E_lj, _, _ = oracle.forces(s, q=zero)
+    F_c = F - F_lj
+    assert abs((s.q * dqv).sum() - 2 * (v * F_c).sum()) < 1e-9 * abs((v * F_c).sum())
+    _, _, A, B = oracle.combine_lb(s.sigma, s.epsilon)
+    iu = np.triu_indices(s.n_types)
+    lhs = (A[iu] * dAv[iu]).sum() + (B[iu] * dBv[iu]).sum()
+    assert abs(lhs - (v * F_lj).sum()) < 1e-9 * abs((v * F_lj).sum())
+
+
+def test_lb_chain_matches_fd_in_sigma_eps():
+    s = S.solvated_chain()
+    idx = np.arange(250)
+    sub = S.System("c", s.pos[idx], s.q[idx], s.type[idx], s.sigma, s.epsilon, s.box,
+                   s.excl[(s.excl < 250).all(1)], s.pairs14[(s.pairs14 < 250).all(1)],
+                   9.0, 7.5, 0.32)
+    rng = np.random.default_rng(6)
+    G = rng.normal(size=(sub.n_atoms, 3))
+    dx, dq, dA, dB = oracle.backward(sub, G, 0.5)
+    _, _, ds, de = oracle.lb_chain(sub, dA, dB)
+
+    def L(sig, eps):
+        sys2 = S.System("c", sub.pos, sub.q, sub.type, sig, eps, sub.box, sub.excl, sub.pairs14,
+                        9.0, 7.5, 0.32)
+        F, E, _, _ = oracle.forces(sys2)
+        return (G * F).sum() + 0.5 * E.sum()
+
+    for t in np.unique(sub.type)[:4]:
+        h = 2.0 ** -14
+        sp = sub.sigma.copy(); sp[t] += np.float32(h)
+        sm = sub.sigma.copy(); sm[t] -= np.float32(h)
+        g = (L(sp, sub.epsilon) - L(sm, sub.epsilon)) / (float(sp[t]) - float(sm[t]))
+        assert abs(g - ds[t]) < 1e-5 * abs(ds[t]) + 1e-9, (t, g, ds[t])
+        ep = sub.epsilon.copy(); ep[t] += np.float32(h)
+        em = sub.epsilon.copy(); em[t] -= np.float32(h)
+        g = (L(sub.sigma, ep) - L(sub.sigma, em)) / (float(ep[t]) - float(em[t]))
+        assert abs(g - de[t]) < 1e-5 * abs(de[t]) + 1e-9, (t, g, de[t])
+    # eps = 0 types: sigma gradient 0, eps gradient undefined
+    s_w = small_water(27, k=17)
+    _, _, dA2, dB2 = oracle.backward(s_w, rng.normal(size=(s_w.n_atoms, 3)), 0.0)
+    _, _, ds2, de2 = oracle.lb_chain(s_w, dA2, dB2)
+    assert ds2[1] == 0.0 and np.isnan(de2[1])
+
+
+# ------------------------------------------------------------------- binning
+
+def test_binning_invariants():
+    for s in (S.water_box(), small_water(300, k=18)):
+        perm, cs, (nx, ny) = oracle.binning(s.pos, s.box)
+        n = s.n_atoms
+        real = perm[perm >= 0]
+        assert np.array_equal(np.sort(real), np.arange(n))
+        assert np.all(np.diff(cs) % oracle.CLUSTER == 0)
+        w = s.box.astype(np.float64) / np.array([nx, ny, 1])
+        rho = n / np.prod(s.box.astype(np.float64))
+        # columns sized so that one cluster slab is about cubic
+        assert abs(w[0] - (oracle.CLUSTER / rho) ** (1 / 3)) < w[0] * 0.25
+        for c in range(nx * ny):
+            seg = perm[cs[c]:cs[c + 1]]
+            at = seg[seg >= 0]
+            assert np.all(seg[:len(at)] >= 0)  # padding only at the end
+            cx, cy = c % nx, c // nx
+            x = s.pos[at].astype(np.float64)
+            assert np.all(x[:, 0] >= cx * w[0] - 1e-4) and np.all(x[:, 0] <= (cx + 1) * w[0] + 1e-4)
+            assert np.all(x[:, 1] >= cy * w[1] - 1e-4) and np.all(x[:, 1] <= (cy + 1) * w[1] + 1e-4)
+            z = s.pos[at, 2]
+            key = np.lexsort((at, z))
+            assert np.array_equal(key, np.arange(len(at)))
+            assert len(seg) - len(at) < oracle.CLUSTER
+
+
+def test_wrap_f32():
+    box = np.array([10.0, 20.0, 30.0], np.float32)
+    p = np.array([[-0.5, 41.0, 30.0], [9.999999, -1e-8, 0.0], [-30.0, 20.0, -1e-3]], np.float32)
+    w = oracle.wrap_f32(p, box)
+    assert np.all(w >= 0) and np.all(w < box)
+    assert np.allclose(w[0], [9.5, 1.0, 0.0], atol=1e-5)
+    assert w[1, 0] == np.float32(9.999999)
+
+
+def test_generator_density_matches_paper_benchmark():
+    gold, _ = read_golden("paper_numbers.txt")
+    s = S.solvated_chain()
+    rho_dhfr = gold["dhfr_atoms"] / gold["dhfr_box"] ** 3
+    rho = s.n_atoms / float(np.prod(s.box.astype(np.float64)))
+    assert abs(rho / rho_dhfr - 1) < 0.01
+    # an R/2 = 6 A bin holds about 22 atoms at this density (paper: ~22)
+    assert abs(rho * 6.0 ** 3 - gold["cell_population_R12"]) < 1.5
