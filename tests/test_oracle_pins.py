@@ -342,6 +342,35 @@ def test_virial_from_affine_scaling():
     assert np.all(np.isfinite(W))
 
 
+def test_virial_off_diagonal_from_shear():
+    # An isolated cluster (no periodic image within the cutoff) sheared by
+    # x_a -> x_a + eps x_b: dE/deps = -W_ab.  Coordinates on a 2^-6 grid below
+    # 16 A and eps = 2^-12 keep the sheared coordinates exact in FP32.
+    w = S._water_system(S.rng_for(21), 27, "cl", alpha=0.32)
+    g = 2.0 ** 6
+    pos = np.floor(np.mod(w.pos.astype(np.float64), 9.0) * g) / g + 1.0
+    s = make_sys(pos, [60.0] * 3, q=w.q, types=w.type, sigma=w.sigma, eps=w.epsilon,
+                 excl=w.excl, alpha=0.32, rc=14.0, rs=12.0)
+    F, E, W, n = oracle.forces(s)
+    idx = {(0, 1): 3, (0, 2): 4, (1, 2): 5, (1, 0): 3, (2, 1): 5}
+
+    def fd(a, b, h):
+        Es = []
+        for e in (h, -h):
+            p = pos.copy()
+            p[:, a] += e * pos[:, b]
+            assert np.all(p.astype(np.float32).astype(np.float64) == p)
+            _, E2, _, n2 = oracle.forces(make_sys(p, [60.0] * 3, q=w.q, types=w.type, sigma=w.sigma,
+                                                  eps=w.epsilon, excl=w.excl, alpha=0.32, rc=14.0, rs=12.0))
+            assert n2 == n
+            Es.append(E2.sum())
+        return (Es[0] - Es[1]) / (2 * h)
+
+    for (a, b), k in idx.items():
+        g_fd = (4 * fd(a, b, 2.0 ** -12) - fd(a, b, 2.0 ** -11)) / 3
+        assert abs(g_fd + W[k]) < 1e-6 * np.abs(W).max(), (a, b, g_fd, -W[k])
+
+
 # ------------------------------------------------------------------- topology
 
 def test_single_water_is_fully_excluded():
