@@ -1,0 +1,204 @@
+/*
+ * acenb.h - C ABI of the GB300 short-range non-bonded library.
+ *
+ * The library evaluates the short-range non-bonded forces, energies and
+ * virial of an all-atom system as described in Harvey, Giupponi & De
+ * Fabritiis (2009), section "Molecular dynamics on the GPU": atoms are binned
+ * into a cell list built from their coordinates ("one particle per thread"),
+ * and the non-bonded kernel evaluates Lennard-Jones and electrostatic terms
+ * for every pair within the cutoff R, excluding or scaling bonded pairs
+ * ("exclusion bitmaps", inner/outer kernels).  It adds the adjoint used for
+ * force-field fitting and a batched form for many independent boxes.
+ *
+ * Functional forms (the paper names them but prints no formula):
+ *   U_LJ = w_lj * S(r) * (A_ab / r^12 - B_ab / r^6),
+ *          A_ab = 4 eps_ab sig_ab^12, B_ab = 4 eps_ab sig_ab^6,
+ *          Lorentz-Berthelot: sig_ab = (sig_a + sig_b) / 2, eps_ab = sqrt(eps_a eps_b)
+ *          (CHARMM force field, section "Molecular dynamics on the GPU");
+ *   S(r) = 1 for r <= rs, (rc^2 - r^2)^2 (rc^2 + 2 r^2 - 3 rs^2) / (rc^2 - rs^2)^3
+ *          for rs < r < rc (CHARMM switch; "switched at 7.5 A", section
+ *          "Performance");
+ *   U_C  = w_c * ke * q_i q_j * erfc(alpha r) / r, truncated at rc (real-space
+ *          Ewald part of PME, section "Molecular dynamics on the GPU");
+ *   w    = 0 for excluded (1-2, 1-3) pairs, (s14_lj, s14_coul) for 1-4 pairs,
+ *          1 otherwise.
+ * A pair (i, j) is inside the cutoff iff r2 < rc*rc evaluated in FP32 with the
+ * minimum-image displacement d = x_j - x_i taken per axis as
+ *   s = x_j - x_i;  s > L/2: d = (x_j - L) - x_i;  s < -L/2: d = x_j - (x_i - L);
+ *   else d = s;     r2 = fma(dz, dz, fma(dy, dy, dx * dx)).
+ * Coordinates are first wrapped into [0, L) per axis with FP32 operations.
+ * Pair arithmetic is FP32; per-lane partial sums are combined in 64-bit
+ * fixed point (scale 2^32), so every result is bit-identical from run to run.
+ *
+ * Conventions
+ *   - d_* arguments are device pointers owned by the caller; h_* are host
+ *     pointers.  The context owns all scratch memory (allocated at create).
+ *   - Calls are asynchronous on the context's CUDA stream and launch kernels
+ *     only (no host synchronisation, no allocation), so they can be captured
+ *     into a CUDA graph.  Host-detectable errors are returned immediately;
+ *     device-detected errors are recorded in a device status word and
+ *     reported (and cleared) by nb_get_status.
+ *   - Arrays are row-major.  Positions, forces and gradients are [N, 3] FP32.
+ *   - A batch holds n_sys independent systems; per-atom arrays are the
+ *     systems' arrays concatenated in system order, energies are [n_sys, 2]
+ *     (LJ, Coulomb) and virials [n_sys, 6] (xx, yy, zz, xy, xz, yz).
+ *     W_ab = sum over pairs of d_ab,a * f_ab,b with d = x_i - x_j and f the
+ *     force on i due to j (so dE/dlambda = -tr W under x -> lambda x).
+ */
+#ifndef ACENB_H
+#define ACENB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ACENB_VERSION 1
+
+typedef enum {
+    NB_OK = 0,
+    NB_ERR_INVALID_ARG = 1,   /* a host-checked argument is invalid */
+    NB_ERR_BOX_TOO_SMALL = 2, /* L/2 - rc < 1e-4 L on some axis (minimum image ambiguous) */
+    NB_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+    NB_ERR_OOM = 4,           /* device allocation failed at create */
+    NB_ERR_NOT_BUILT = 5,     /* nb_forces/nb_backward before nb_build_cells */
+    NB_ERR_OVERFLOW = 6,      /* a value left the 64-bit fixed-point range */
+    NB_ERR_LIST_STALE = 7,    /* positions differ from those of the last build */
+    NB_ERR_TIMEOUT = 8,       /* a bounded device-side wait gave up */
+    NB_ERR_NONFINITE = 9,     /* a coordinate is NaN or infinite */
+    NB_ERR_CAPACITY = 10,     /* a per-cluster neighbour list exceeded its capacity */
+    NB_ERR_UNSUPPORTED = 11   /* parameters outside the supported range */
+} nb_status;
+
+typedef struct nb_ctx nb_ctx;
+
+/* Parameters of one system.  Host arrays are copied by nb_create; the caller
+ * may free them afterwards. */
+typedef struct {
+    int32_t n_atoms;        /* N >= 1 */
+    float box[3];           /* orthorhombic edges L_x, L_y, L_z (A); L/2 - rc >= 1e-4 L */
+    float cutoff;           /* rc (A), > 0 */
+    float switch_dist;      /* rs (A); rs >= rc disables the switch */
+    float ewald_alpha;      /* alpha (1/A); 0 gives plain truncated Coulomb */
+    float coulomb_k;        /* ke (kcal A / (mol e^2)); 0 selects 332.0636 */
+    int32_t n_types;        /* T, 1 <= T <= 64 */
+    const float *sigma;     /* host [T] per-type sigma (A), comb_rule 0 */
+    const float *epsilon;   /* host [T] per-type epsilon (kcal/mol), comb_rule 0 */
+    int32_t comb_rule;      /* 0: Lorentz-Berthelot; 1: explicit pair tables */
+    const float *sigma_tab; /* host [T*T] symmetric sig_ab, comb_rule 1 */
+    const float *eps_tab;   /* host [T*T] symmetric eps_ab, comb_rule 1 */
+    int32_t n_excl;         /* number of excluded pairs */
+    const int32_t *excl;    /* host [n_excl*2] atom pairs (i, j), i != j, 0-based */
+    int32_t n_14;           /* number of scaled 1-4 pairs */
+    const int32_t *pairs14; /* host [n_14*2], disjoint from excl */
+    float scale14_lj;       /* LJ scale of 1-4 pairs (e.g. 0.5) */
+    float scale14_coul;     /* Coulomb scale of 1-4 pairs (e.g. 1/1.2) */
+    uint32_t flags;         /* reserved, must be 0 */
+} nb_params;
+
+/* Tuning knobs (chosen by the autotuner; defaults are safe). */
+typedef struct {
+    int32_t i_group;        /* i-atoms per warp task: 1, 2, 4 or 8 */
+    int32_t warps_per_block;/* 2..16 */
+    int32_t blocks_per_sm;  /* resident blocks per SM used to size the persistent grid */
+    int32_t list_capacity;  /* cluster-pair entries per cluster (>= 64) */
+} nb_tuning;
+
+/* nb_create - one system.  Copies params, validates them (box/cutoff ratio,
+ * index ranges, disjoint topology), allocates all device scratch and binds
+ * the context to `cuda_stream` (a cudaStream_t; NULL = legacy default).
+ * Errors: NB_ERR_INVALID_ARG, NB_ERR_BOX_TOO_SMALL, NB_ERR_UNSUPPORTED,
+ * NB_ERR_OOM, NB_ERR_CUDA.  *out is NULL on error. */
+nb_status nb_create(const nb_params *params, void *cuda_stream, nb_ctx **out);
+
+/* nb_create_batch - n_sys independent systems evaluated together in one
+ * persistent launch.  params[s] gives system s; cutoff, switch_dist,
+ * ewald_alpha, coulomb_k, types and 1-4 scales must be equal across systems
+ * (NB_ERR_INVALID_ARG otherwise); n_atoms, box and topology may differ. */
+nb_status nb_create_batch(int32_t n_sys, const nb_params *params, void *cuda_stream, nb_ctx **out);
+
+/* nb_build_cells - wrap d_pos [N, 3] into the box, bin atoms into x-y
+ * columns, z-sort each column, pad columns to whole 8-atom clusters, compute
+ * cluster bounding boxes, map exclusions to the sorted order and build the
+ * cluster-pair list (section "Molecular dynamics on the GPU", cell-list
+ * construction).  Asynchronous.  Device errors: NB_ERR_NONFINITE,
+ * NB_ERR_CAPACITY. */
+nb_status nb_build_cells(nb_ctx *ctx, const float *d_pos);
+
+/* nb_forces - forces, energies and virial for the positions of the last
+ * build (section "Molecular dynamics on the GPU", non-bonded kernel).
+ *   d_pos   [N, 3]  must hold the positions passed to nb_build_cells
+ *                   (NB_ERR_LIST_STALE is recorded otherwise);
+ *   d_q     [N]     charges (e);  d_type [N] LJ types in [0, T);
+ *   d_F     [N, 3]  output forces (kcal/mol/A), overwritten;
+ *   d_energy[n_sys*2] output (E_LJ, E_Coul) in kcal/mol, or NULL;
+ *   d_virial[n_sys*6] output, or NULL.
+ * Returns NB_ERR_NOT_BUILT without a preceding build. */
+nb_status nb_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type,
+                    float *d_F, double *d_energy, double *d_virial);
+
+/* nb_backward - adjoint of L = sum_i G_i . F_i + sum_s gE_s . E_s, the pair
+ * list recomputed from the last build.
+ *   d_dLdF      [N, 3]      G;  d_dLdE [n_sys*2] gE (LJ, Coulomb) or NULL (= 0);
+ *   d_dLdpos    [N, 3]      dL/dx = -H G - (gE weighted) F   (Hessian-vector product);
+ *   d_dLdq      [N]         dL/dq;
+ *   d_dLdsig_tab, d_dLdeps_tab [T*T] FP64 gradients with respect to the
+ *               symmetric type-pair parameters sig_ab, eps_ab (each unordered
+ *               pair's value stored at [a][b] and [b][a]).
+ * Any output pointer may be NULL to skip it. */
+nb_status nb_backward(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type,
+                      const float *d_dLdF, const double *d_dLdE,
+                      float *d_dLdpos, float *d_dLdq, double *d_dLdsig_tab, double *d_dLdeps_tab);
+
+/* nb_set_lj_params - replace the LJ type parameters between calls (e.g. after
+ * a fitting step).  comb_rule 0: h_sigma, h_epsilon [T]; comb_rule 1:
+ * h_sigma_tab, h_eps_tab [T*T] symmetric.  Synchronises the context's stream
+ * and copies the new (A, B) table; not capturable in a CUDA graph.
+ * Errors: NB_ERR_INVALID_ARG for missing or negative values. */
+nb_status nb_set_lj_params(nb_ctx *ctx, const float *h_sigma, const float *h_epsilon,
+                           const float *h_sigma_tab, const float *h_eps_tab);
+
+/* nb_get_status - synchronise the context's stream, return the first
+ * recorded device error (or NB_OK) and clear it. */
+nb_status nb_get_status(nb_ctx *ctx);
+
+/* nb_set_stream - rebind the context to another stream. */
+nb_status nb_set_stream(nb_ctx *ctx, void *cuda_stream);
+
+/* nb_destroy - free every device and host resource of the context. */
+void nb_destroy(nb_ctx *ctx);
+
+/* nb_set_tuning / nb_get_tuning - read or change the launch configuration.
+ * A changed list_capacity reallocates scratch (not allowed during capture). */
+nb_status nb_set_tuning(nb_ctx *ctx, const nb_tuning *t);
+nb_status nb_get_tuning(nb_ctx *ctx, nb_tuning *t);
+
+/* Sizes of the context: total atoms, systems, sorted slots capacity. */
+nb_status nb_get_sizes(nb_ctx *ctx, int64_t *n_atoms, int32_t *n_sys, int64_t *slot_capacity);
+
+/* nb_debug_cells - synchronous copy of the last build's binning:
+ * h_perm [slot_capacity] receives, per sorted slot, the original atom index
+ * (batch-global) or -1 for padding; *n_slots the number of used slots;
+ * h_col_start [n_columns+1] the padded slot offset of each column (columns of
+ * system s follow those of s-1, column id = cy * nx + cx); *n_columns their
+ * count.  Either array may be NULL. */
+nb_status nb_debug_cells(nb_ctx *ctx, int32_t *h_perm, int64_t *n_slots,
+                         int64_t *h_col_start, int64_t *n_columns);
+
+/* nb_debug_pairs - run the pair filter of the force kernel for the last
+ * build and copy out every evaluated pair inside the cutoff and not excluded,
+ * as original atom indices (i < j), into h_ij [cap*2]; *n receives the total
+ * count of such unique pairs (may exceed cap) and *n_ordered the number of
+ * ordered evaluations (2 * n when every pair is seen from both atoms).
+ * Synchronous. */
+nb_status nb_debug_pairs(nb_ctx *ctx, int32_t *h_ij, int64_t cap, int64_t *n, int64_t *n_ordered);
+
+/* nb_status_string - static description of a status code. */
+const char *nb_status_string(nb_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ACENB_H */

@@ -1,0 +1,157 @@
+// nb_internal.cuh - internal types shared by the translation units of the
+// GB300 non-bonded library (never installed; the public ABI is acenb.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "acenb.h"
+
+namespace acenb {
+
+constexpr int kCluster = 8;          // atoms per cluster (column chunk)
+constexpr int kMaxTypes = 64;        // type-pair table lives in shared memory
+constexpr int kMaxPartners = 16;     // exclusion + 1-4 partners per atom
+constexpr int kErfcDeg = 8;          // degree of the erfcx polynomial in t
+constexpr double kFixScale = 4294967296.0;   // 2^32: fixed-point scale
+constexpr int kTaskVals = 8;         // per task: E_lj, E_c, W[6]
+
+// List entry encoding: J (bits 0..24) | shift codes x,y,z (2 bits each,
+// bits 25..30: 0 none, 1 = j-side shift x_j - L, 2 = i-side shift x_i - L)
+// | exclusion flag (bit 31: J holds a topology partner of I).
+constexpr uint32_t kJMask = 0x01FFFFFFu;
+constexpr int kShiftBit = 25;
+constexpr uint32_t kExclFlag = 0x80000000u;
+
+// Queue word: type (bits 0..7) | exclusion bits per i (8..15) | 1-4 bits per i
+// (16..23) | i-side shift per axis (24..26).
+constexpr int kQExcl = 8;
+constexpr int kQ14 = 16;
+constexpr int kQIShift = 24;
+
+// Device status bits (first error wins when reported).
+enum : int {
+    ST_NONFINITE = 1 << 0,
+    ST_CAPACITY = 1 << 1,
+    ST_STALE = 1 << 2,
+    ST_OVERFLOW = 1 << 3,
+    ST_BADTYPE = 1 << 4,
+    ST_TIMEOUT = 1 << 5,
+};
+
+// Per-system descriptor (device resident).  Fields marked [build] are
+// written by the binning kernels at every build.
+struct SysDesc {
+    float L[3];          // box edges
+    float half[3];       // 0.5 * L (FP32, exact)
+    float inv_w[2];      // nx / Lx, ny / Ly rounded to FP32 (column scale)
+    float w[2];          // Lx / nx, Ly / ny (FP32, for list bounds)
+    int nx, ny;          // columns per axis
+    int atom_begin;      // first atom in the concatenated input arrays
+    int n_atoms;
+    int col_begin;       // first global column
+    int slot_begin;      // [build] first sorted slot
+    int clus_begin;      // [build] first cluster
+    int clus_end;        // [build] one past the last cluster
+};
+
+// Pair-model constants passed by value to kernels.
+struct PairParams {
+    float rc2;           // rc * rc (FP32, the membership threshold)
+    float rc, rs2;       // FP32 cutoff and switch distance squared
+    float sw_c0;         // rc2 - 3 rs2
+    float sw_inv;        // 1 / (rc2 - rs2)^3
+    float ke;            // Coulomb constant
+    float alpha_half;    // alpha / 2: t = 1 / (1 + (alpha/2) r)
+    float alpha;         // Ewald alpha
+    float neg_a2_log2e;  // -alpha^2 log2(e): exp(-alpha^2 r^2) = 2^(r2 * this)
+    float two_a_sqpi;    // 2 alpha / sqrt(pi)
+    float s14_lj, s14_c;
+    float list_margin;   // additive margin on bounding-box distances (A)
+    float rcm2;          // (rc + list_margin)^2, bounding-box pruning threshold
+    int n_types;
+    int switched;        // rs < rc
+    int ewald;           // alpha > 0
+    float erfc_c[kErfcDeg + 1]; // erfcx(x) ~ sum c_k t^k on [0, alpha rc]
+};
+
+struct DevBuffers {
+    SysDesc *sys = nullptr;          // [n_sys]
+    int *atom_sys = nullptr;         // [N]
+    int *atom_col = nullptr;         // [N] global column of each atom
+    float4 *wpos = nullptr;          // [N] wrapped coordinates
+    int *part_orig = nullptr;        // [N*K] partner (orig << 1) | is14, -1 pad (static)
+    int *col_sys = nullptr;          // [C] system of each column (static)
+    int *col_count = nullptr;        // [C]
+    int *col_fill = nullptr;         // [C] scatter cursor
+    int *col_slot = nullptr;         // [C+1] padded slot offsets
+    int *stage = nullptr;            // [S] unsorted atoms per column
+    float4 *xyzq = nullptr;          // [S] sorted x, y, z, q (NaN for padding)
+    int *tslot = nullptr;            // [S] sorted types
+    int *perm = nullptr;             // [S] slot -> atom (-1 padding)
+    int *inv = nullptr;              // [N] atom -> slot
+    int *ex_slot = nullptr;          // [S*K] partner slot << 1 | is14, -1 pad
+    float4 *bb_lo = nullptr;         // [NC] cluster bounding boxes
+    float4 *bb_hi = nullptr;         // [NC]
+    int *clus_sys = nullptr;         // [NC] system of each cluster
+    uint32_t *list = nullptr;        // [NC*cap] cluster-pair entries
+    int *list_n = nullptr;           // [NC]
+    long long *task_part = nullptr;  // [NT*kTaskVals] per-task fixed-point partials
+    long long *tab_grad = nullptr;   // [T*T*2] adjoint table gradients (fixed point)
+    int *counts = nullptr;           // [4]: n_slots, n_clusters, pair counters
+    int *status = nullptr;           // [1]
+    float2 *lj_tab = nullptr;        // [T*T] (A, B)
+    long long *dbg_n = nullptr;      // [2] debug pair counters
+    int *dbg_ij = nullptr;           // [cap*2]
+    int64_t dbg_cap = 0;
+    float *scratch_f = nullptr;      // [N*3] debug force sink
+    double *scratch_g = nullptr;     // [T*T*2] adjoint scratch
+};
+
+}  // namespace acenb
+
+struct nb_ctx {
+    int n_sys = 0;
+    int64_t n_atoms = 0;
+    int n_cols = 0;
+    int64_t slot_cap = 0;
+    int64_t clus_cap = 0;
+    int K = 1;                     // partners per atom (>= 1)
+    int comb_rule = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    bool built = false;
+    acenb::PairParams pp{};
+    nb_tuning tune{};
+    std::vector<acenb::SysDesc> sys_h;
+    std::vector<double> sig_tab, eps_tab;  // FP64 type-pair parameters
+    acenb::DevBuffers d;
+};
+
+namespace acenb {
+
+// Wrap one FP32 coordinate into [0, L) with IEEE round-to-nearest operations
+// in a fixed order: k = floor(x / L); x = fma(-k, L, x); then one conditional
+// +L and one conditional -L.
+__device__ __forceinline__ float wrap_coord(float x, float L)
+{
+    if (x >= 0.0f && x < L) return x;
+    float k = floorf(__fdiv_rn(x, L));
+    x = __fmaf_rn(-k, L, x);
+    if (x < 0.0f) x = __fadd_rn(x, L);
+    if (x >= L) x = __fsub_rn(x, L);
+    return x;
+}
+
+// Launchers implemented in the .cu files (all asynchronous on ctx->stream).
+cudaError_t launch_build(nb_ctx *ctx, const float *d_pos);
+cudaError_t launch_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type,
+                          float *d_F, double *d_energy, double *d_virial, bool debug_pairs);
+cudaError_t launch_backward(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type,
+                            const float *d_dLdF, const double *d_dLdE, float *d_dLdpos, float *d_dLdq,
+                            double *d_dsig, double *d_deps);
+
+}  // namespace acenb

@@ -1,0 +1,75 @@
+// nb_pair.cuh - FP32 pair arithmetic shared by the forward and adjoint
+// kernels: LJ 12-6 with the CHARMM switch and real-space Ewald Coulomb
+// (section "Molecular dynamics on the GPU": Lennard-Jones and electrostatic
+// terms of every pair inside the cutoff; section "Performance": switched at
+// 7.5 A; PME real space erfc(alpha r)/r).
+#pragma once
+
+#include "nb_internal.cuh"
+
+namespace acenb {
+
+// Far sentinels: an invalid i lane sits at +kFar, a padding queue entry at
+// -kFar, so their squared distance (about 1.2e37) is finite and never inside
+// the cutoff, and every product with a zero force stays zero.
+constexpr float kFar = 1.0e18f;
+
+// erfcx(x) = exp(x^2) erfc(x) as a polynomial in t = 1 / (1 + x/2), fitted on
+// the host on [0, alpha rc]; erfc(x) = exp(-x^2) * P(t).
+__device__ __forceinline__ float erfcx_poly(const PairParams &P, float t)
+{
+    float p = P.erfc_c[kErfcDeg];
+#pragma unroll
+    for (int k = kErfcDeg - 1; k >= 0; --k) p = fmaf(p, t, P.erfc_c[k]);
+    return p;
+}
+
+// Minimum-image displacement d = x_j - x_i and its FP32 squared length, the
+// membership quantity: r2 = fma(dz, dz, fma(dy, dy, dx * dx)).
+__device__ __forceinline__ float disp_r2(float xj, float yj, float zj, float xi, float yi, float zi,
+                                         float &dx, float &dy, float &dz)
+{
+    dx = __fsub_rn(xj, xi);
+    dy = __fsub_rn(yj, yi);
+    dz = __fsub_rn(zj, zi);
+    return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+}
+
+// Radial part of one pair at squared distance r2 (inside the cutoff):
+//   elj, ec : LJ (switched) and Coulomb energies (unweighted);
+//   frlj, frc : -dU/dr * r of each part.
+template <bool EWALD, bool SWITCH>
+__device__ __forceinline__ void pair_radial(const PairParams &P, float r2, float rinv, float A, float B,
+                                            float qq, float &elj, float &frlj, float &ec, float &frc)
+{
+    const float r2inv = rinv * rinv;
+    const float ir6 = r2inv * r2inv * r2inv;
+    const float t6 = B * ir6;
+    const float t12 = A * ir6 * ir6;
+    elj = t12 - t6;
+    frlj = fmaf(12.0f, t12, -6.0f * t6);
+    if (SWITCH) {
+        // S = (rc2 - r2)^2 (rc2 + 2 r2 - 3 rs2) / (rc2 - rs2)^3 and
+        // r dS/dr = 12 r2 (rc2 - r2)(rs2 - r2) / (rc2 - rs2)^3 for r > rs.
+        const float t = P.rc2 - r2;
+        const float S = t * t * fmaf(2.0f, r2, P.sw_c0) * P.sw_inv;
+        const float rdS = 12.0f * P.sw_inv * r2 * t * (P.rs2 - r2);
+        const bool sw = r2 > P.rs2;
+        frlj = sw ? fmaf(S, frlj, -elj * rdS) : frlj;
+        elj = sw ? S * elj : elj;
+    }
+    if (EWALD) {
+        const float r = r2 * rinv;
+        const float t = __fdividef(1.0f, fmaf(P.alpha_half, r, 1.0f));
+        const float ex = exp2f(r2 * P.neg_a2_log2e);   // exp(-alpha^2 r^2)
+        const float erfcv = ex * erfcx_poly(P, t);
+        ec = qq * erfcv * rinv;
+        // -d/dr [erfc(a r)/r] * r = erfc(a r)/r + (2a/sqrt(pi)) exp(-a^2 r^2)
+        frc = qq * fmaf(erfcv, rinv, P.two_a_sqpi * ex);
+    } else {
+        ec = qq * rinv;
+        frc = ec;
+    }
+}
+
+}  // namespace acenb

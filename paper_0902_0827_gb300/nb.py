@@ -1,0 +1,275 @@
+"""Python binding of the C ABI in ``include/acenb.h`` (argument marshalling only).
+
+Every step of the computation runs in the CUDA library ``_build/libacenb.so``.
+PyTorch supplies device memory and the current CUDA stream.  There is no CPU
+fallback: if the library cannot be loaded, :func:`lib` raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Sequence
+
+import numpy as np
+
+from . import build as _build
+
+NB_OK = 0
+STATUS_NAMES = {
+    0: "NB_OK", 1: "NB_ERR_INVALID_ARG", 2: "NB_ERR_BOX_TOO_SMALL", 3: "NB_ERR_CUDA", 4: "NB_ERR_OOM",
+    5: "NB_ERR_NOT_BUILT", 6: "NB_ERR_OVERFLOW", 7: "NB_ERR_LIST_STALE", 8: "NB_ERR_TIMEOUT",
+    9: "NB_ERR_NONFINITE", 10: "NB_ERR_CAPACITY", 11: "NB_ERR_UNSUPPORTED",
+}
+# every symbol include/acenb.h declares
+EXPORTS = ("nb_create", "nb_create_batch", "nb_build_cells", "nb_forces", "nb_backward", "nb_get_status",
+           "nb_set_stream", "nb_destroy", "nb_set_tuning", "nb_get_tuning", "nb_get_sizes", "nb_debug_cells",
+           "nb_debug_pairs", "nb_status_string", "nb_set_lj_params")
+
+
+class NbError(RuntimeError):
+    def __init__(self, code: int, where: str = ""):
+        self.code = code
+        name = STATUS_NAMES.get(code, str(code))
+        super().__init__(f"{where}: {name}" if where else name)
+
+
+class nb_params(ctypes.Structure):
+    _fields_ = [
+        ("n_atoms", ctypes.c_int32), ("box", ctypes.c_float * 3), ("cutoff", ctypes.c_float),
+        ("switch_dist", ctypes.c_float), ("ewald_alpha", ctypes.c_float), ("coulomb_k", ctypes.c_float),
+        ("n_types", ctypes.c_int32), ("sigma", ctypes.c_void_p), ("epsilon", ctypes.c_void_p),
+        ("comb_rule", ctypes.c_int32), ("sigma_tab", ctypes.c_void_p), ("eps_tab", ctypes.c_void_p),
+        ("n_excl", ctypes.c_int32), ("excl", ctypes.c_void_p), ("n_14", ctypes.c_int32),
+        ("pairs14", ctypes.c_void_p), ("scale14_lj", ctypes.c_float), ("scale14_coul", ctypes.c_float),
+        ("flags", ctypes.c_uint32),
+    ]
+
+
+class nb_tuning(ctypes.Structure):
+    _fields_ = [("i_group", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("list_capacity", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True):
+    """Load the CUDA library (building it in-tree first if it is missing)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise OSError(f"CUDA library not built: {path}")
+            _build.build()
+        L = ctypes.CDLL(path)
+        P, I32, I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        sig = {
+            "nb_create": ([ctypes.POINTER(nb_params), P, ctypes.POINTER(P)], ctypes.c_int),
+            "nb_create_batch": ([I32, ctypes.POINTER(nb_params), P, ctypes.POINTER(P)], ctypes.c_int),
+            "nb_build_cells": ([P, P], ctypes.c_int),
+            "nb_forces": ([P, P, P, P, P, P, P], ctypes.c_int),
+            "nb_backward": ([P, P, P, P, P, P, P, P, P, P], ctypes.c_int),
+            "nb_get_status": ([P], ctypes.c_int),
+            "nb_set_stream": ([P, P], ctypes.c_int),
+            "nb_destroy": ([P], None),
+            "nb_set_tuning": ([P, ctypes.POINTER(nb_tuning)], ctypes.c_int),
+            "nb_get_tuning": ([P, ctypes.POINTER(nb_tuning)], ctypes.c_int),
+            "nb_get_sizes": ([P, ctypes.POINTER(I64), ctypes.POINTER(I32), ctypes.POINTER(I64)], ctypes.c_int),
+            "nb_debug_cells": ([P, P, ctypes.POINTER(I64), P, ctypes.POINTER(I64)], ctypes.c_int),
+            "nb_debug_pairs": ([P, P, I64, ctypes.POINTER(I64), ctypes.POINTER(I64)], ctypes.c_int),
+            "nb_status_string": ([ctypes.c_int], ctypes.c_char_p),
+            "nb_set_lj_params": ([P, P, P, P, P], ctypes.c_int),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(code: int, where: str):
+    if code != NB_OK:
+        raise NbError(code, where)
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p) if a.size else None
+
+
+def _tptr(t):
+    """Device pointer of a contiguous CUDA tensor (None passes NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_handle():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Nonbonded:
+    """One context of the library: a single system or a batch of systems.
+
+    ``systems`` are objects with the attributes of
+    :class:`paper_0902_0827_gb300.systems.System` (box, cutoff, switch_dist,
+    ewald_alpha, coulomb_k, sigma, epsilon, excl, pairs14, scale factors and
+    n_atoms).  For a batch, per-atom tensors are the systems' arrays
+    concatenated in order.
+    """
+
+    def __init__(self, systems, stream=None):
+        L = lib()
+        single = not isinstance(systems, (list, tuple))
+        self.systems = [systems] if single else list(systems)
+        self._keep = []
+        arr = (nb_params * len(self.systems))()
+        for k, s in enumerate(self.systems):
+            sig, eps = _f32(s.sigma), _f32(s.epsilon)
+            ex, p14 = _i32(s.excl).reshape(-1, 2), _i32(s.pairs14).reshape(-1, 2)
+            self._keep += [sig, eps, ex, p14]
+            p = arr[k]
+            p.n_atoms = int(s.n_atoms)
+            for a in range(3):
+                p.box[a] = float(s.box[a])
+            p.cutoff, p.switch_dist = float(s.cutoff), float(s.switch_dist)
+            p.ewald_alpha, p.coulomb_k = float(s.ewald_alpha), float(s.coulomb_k)
+            p.n_types = int(sig.shape[0])
+            p.sigma, p.epsilon = _ptr(sig), _ptr(eps)
+            p.comb_rule = 0
+            p.n_excl, p.excl = int(ex.shape[0]), _ptr(ex)
+            p.n_14, p.pairs14 = int(p14.shape[0]), _ptr(p14)
+            p.scale14_lj, p.scale14_coul = float(s.scale14_lj), float(s.scale14_coul)
+            p.flags = 0
+        h = ctypes.c_void_p()
+        st = stream if stream is not None else _stream_handle()
+        _check(L.nb_create_batch(len(self.systems), arr, st, ctypes.byref(h)), "nb_create_batch")
+        self._keep = []
+        self.h = h
+        self.n_sys = len(self.systems)
+        self.n_atoms = int(sum(s.n_atoms for s in self.systems))
+        self.n_types = int(self.systems[0].sigma.shape[0])
+
+    # -- lifecycle -------------------------------------------------------
+    def close(self):
+        if getattr(self, "h", None):
+            lib().nb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _sync_stream(self):
+        lib().nb_set_stream(self.h, _stream_handle())
+
+    # -- compute ---------------------------------------------------------
+    def build(self, pos):
+        self._sync_stream()
+        _check(lib().nb_build_cells(self.h, _tptr(pos)), "nb_build_cells")
+
+    def forces(self, pos, q, typ, F=None, energy=True, virial=True):
+        """Forces [N,3] (FP32), energies [n_sys,2] and virials [n_sys,6] (FP64)."""
+        import torch
+        self._sync_stream()
+        dev = pos.device
+        if F is None:
+            F = torch.empty((self.n_atoms, 3), dtype=torch.float32, device=dev)
+        E = torch.empty((self.n_sys, 2), dtype=torch.float64, device=dev) if energy is True else energy
+        W = torch.empty((self.n_sys, 6), dtype=torch.float64, device=dev) if virial is True else virial
+        E = E if E is not False else None
+        W = W if W is not False else None
+        _check(lib().nb_forces(self.h, _tptr(pos), _tptr(q), _tptr(typ), _tptr(F), _tptr(E), _tptr(W)),
+               "nb_forces")
+        return F, E, W
+
+    def backward(self, pos, q, typ, dLdF, dLdE=None, want=("pos", "q", "sig", "eps")):
+        import torch
+        self._sync_stream()
+        dev = pos.device
+        T = self.n_types
+        gpos = torch.empty((self.n_atoms, 3), dtype=torch.float32, device=dev) if "pos" in want else None
+        gq = torch.empty((self.n_atoms,), dtype=torch.float32, device=dev) if "q" in want else None
+        gs = torch.empty((T, T), dtype=torch.float64, device=dev) if "sig" in want else None
+        ge = torch.empty((T, T), dtype=torch.float64, device=dev) if "eps" in want else None
+        _check(lib().nb_backward(self.h, _tptr(pos), _tptr(q), _tptr(typ), _tptr(dLdF), _tptr(dLdE),
+                                 _tptr(gpos), _tptr(gq), _tptr(gs), _tptr(ge)), "nb_backward")
+        return gpos, gq, gs, ge
+
+    def set_lj_params(self, sigma, epsilon):
+        """Replace the per-type LJ parameters (Lorentz-Berthelot) of the context."""
+        sig, eps = _f32(sigma), _f32(epsilon)
+        _check(lib().nb_set_lj_params(self.h, _ptr(sig), _ptr(eps), None, None), "nb_set_lj_params")
+
+    def status(self, raise_on_error: bool = True) -> int:
+        code = int(lib().nb_get_status(self.h))
+        if raise_on_error and code != NB_OK:
+            raise NbError(code, "device status")
+        return code
+
+    # -- tuning / debug --------------------------------------------------
+    def tuning(self) -> dict:
+        t = nb_tuning()
+        _check(lib().nb_get_tuning(self.h, ctypes.byref(t)), "nb_get_tuning")
+        return {k: getattr(t, k) for k, _ in nb_tuning._fields_}
+
+    def set_tuning(self, **kw):
+        cur = self.tuning()
+        cur.update(kw)
+        t = nb_tuning(**cur)
+        _check(lib().nb_set_tuning(self.h, ctypes.byref(t)), "nb_set_tuning")
+
+    def sizes(self):
+        n, s, c = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64()
+        _check(lib().nb_get_sizes(self.h, ctypes.byref(n), ctypes.byref(s), ctypes.byref(c)), "nb_get_sizes")
+        return n.value, s.value, c.value
+
+    def debug_cells(self):
+        _, _, cap = self.sizes()
+        perm = np.empty(cap, np.int32)
+        ns, nc = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().nb_debug_cells(self.h, None, ctypes.byref(ns), None, ctypes.byref(nc)), "nb_debug_cells")
+        cs = np.empty(nc.value + 1, np.int64)
+        _check(lib().nb_debug_cells(self.h, _ptr(perm), ctypes.byref(ns), _ptr(cs), ctypes.byref(nc)),
+               "nb_debug_cells")
+        return perm[:ns.value].copy(), cs
+
+    def debug_pairs(self, cap: int | None = None):
+        n, no = ctypes.c_int64(), ctypes.c_int64()
+        if cap is None:
+            _check(lib().nb_debug_pairs(self.h, None, 0, ctypes.byref(n), ctypes.byref(no)), "nb_debug_pairs")
+            cap = n.value
+        ij = np.empty((max(cap, 1), 2), np.int32)
+        _check(lib().nb_debug_pairs(self.h, _ptr(ij), cap, ctypes.byref(n), ctypes.byref(no)), "nb_debug_pairs")
+        m = min(n.value, cap)
+        ij = ij[:m]
+        order = np.lexsort((ij[:, 1], ij[:, 0]))
+        return ij[order], n.value, no.value
+
+
+def concat_inputs(systems: Sequence, device="cuda"):
+    """Concatenated (pos, q, type) tensors of a list of systems on the device."""
+    import torch
+    pos = np.concatenate([s.pos for s in systems]).astype(np.float32)
+    q = np.concatenate([s.q for s in systems]).astype(np.float32)
+    t = np.concatenate([s.type for s in systems]).astype(np.int32)
+    return (torch.from_numpy(pos).to(device), torch.from_numpy(q).to(device), torch.from_numpy(t).to(device))
