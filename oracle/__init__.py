@@ -117,20 +117,24 @@ def _args(sys, pos=None, q=None):
     return args, keep
 
 
-def forces(sys, method: str = "allpairs", pos=None, q=None):
+def forces(sys, method: str = "allpairs", pos=None, q=None, with_scale: bool = False):
     """FP64 forces [N,3], energies (E_LJ, E_Coul), virial [6] and pair count.
 
     method: "allpairs" (plain O(N^2) sum) or "cells" (cell-list traversal).
+    with_scale: also return (sum |e_LJ|, sum |e_Coul|) over pairs, the scale
+    of the rounding error of each summed energy.
     """
     args, keep = _args(sys, pos, q)
     n = args[0]
     F = np.zeros((n, 3))
-    E = np.zeros(2)
+    E = np.zeros(4)
     W = np.zeros(6)
     fn = lib().orc_forces_allpairs if method == "allpairs" else lib().orc_forces_cells
     npairs = fn(*args, _p(F), _p(E), _p(W))
     del keep
-    return F, E, W, int(npairs)
+    if with_scale:
+        return F, E[:2].copy(), W, int(npairs), E[2:].copy()
+    return F, E[:2].copy(), W, int(npairs)
 
 
 def forces_subset(sys, atoms, pos=None, q=None):
@@ -139,11 +143,11 @@ def forces_subset(sys, atoms, pos=None, q=None):
     at = _c(atoms, np.int64)
     m = at.shape[0]
     F = np.zeros((m, 3))
-    E2 = np.zeros((m, 2))
+    E4 = np.zeros((m, 4))
     npair = np.zeros(m, np.int64)
-    lib().orc_forces_subset(*args, m, _p(at), _p(F), _p(E2), _p(npair))
+    lib().orc_forces_subset(*args, m, _p(at), _p(F), _p(E4), _p(npair))
     del keep
-    return F, E2, npair
+    return F, E4[:, :2].copy(), npair
 
 
 def backward(sys, G, gE: float = 0.0, pos=None, q=None):

@@ -233,6 +233,7 @@ static void accum_pair(const prm_t *p, const double *d, double r, double A, doub
 {
     pterm_t t;
     pair_terms(p, r, A, B, qq, wlj, wc, &t);
+    E[2] += fabs(t.e_lj); E[3] += fabs(t.e_c);
     double h = t.du / r; /* F_i = h d, F_j = -h d */
     for (int a = 0; a < 3; ++a) { Fi[a] += h * d[a]; if (Fj) Fj[a] -= h * d[a]; }
     E[0] += t.e_lj; E[1] += t.e_c;
@@ -251,8 +252,10 @@ static void disp64(const float *xi, const float *xj, const float *box, const int
     *r = sqrt(s);
 }
 
-/* Plain O(N^2) sum over unique pairs i < j.  F [n*3], E [2] (LJ, Coulomb),
- * W [6] (xx, yy, zz, xy, xz, yz).  Returns the number of pairs in range. */
+/* Plain O(N^2) sum over unique pairs i < j.  F [n*3], E [4] (LJ, Coulomb,
+ * then the sums of |pair energy| of each part: the scale against which the
+ * rounding error of a summed energy is measured), W [6] (xx, yy, zz, xy, xz,
+ * yz).  Returns the number of pairs in range. */
 int64_t orc_forces_allpairs(int64_t n, const float *pos, const float *q, const int32_t *type,
                             int ntypes, const double *A, const double *B, const float *box,
                             float rc, float rs, float alpha, float ke, float s14_lj, float s14_c,
@@ -264,7 +267,7 @@ int64_t orc_forces_allpairs(int64_t n, const float *pos, const float *q, const i
     topo_t t;
     topo_build(&t, n, nex, ex, n14, p14);
     memset(F, 0, sizeof(double) * 3 * (size_t)n);
-    E[0] = E[1] = 0.0;
+    E[0] = E[1] = E[2] = E[3] = 0.0;
     for (int a = 0; a < 6; ++a) W[a] = 0.0;
     int64_t npairs = 0;
     for (int64_t i = 0; i < n; ++i)
@@ -343,7 +346,7 @@ static int64_t atom_sum(const prm_t *p, const topo_t *t, const grid_t *g, int64_
     int64_t cnt = 0;
     int c[3];
     Fi[0] = Fi[1] = Fi[2] = 0.0;
-    Ei[0] = Ei[1] = 0.0;
+    Ei[0] = Ei[1] = Ei[2] = Ei[3] = 0.0;
     for (int a = 0; a < 6; ++a) Wi[a] = 0.0;
     if (g) grid_cell_of(g, pos + 3 * i, p->box, c);
     int64_t jlist_n = g ? 27 : 1;
@@ -368,9 +371,9 @@ static int64_t atom_sum(const prm_t *p, const topo_t *t, const grid_t *g, int64_
             double d[3], r;
             disp64(pos + 3 * i, pos + 3 * j, p->box, img, d, &r);
             int ab = type[i] * p->ntypes + type[j];
-            double e2[2] = {0.0, 0.0}, w6[6] = {0, 0, 0, 0, 0, 0};
+            double e2[4] = {0.0, 0.0, 0.0, 0.0}, w6[6] = {0, 0, 0, 0, 0, 0};
             accum_pair(p, d, r, p->A[ab], p->B[ab], (double)q[i] * (double)q[j], wlj, wc, Fi, NULL, e2, w6);
-            Ei[0] += 0.5 * e2[0]; Ei[1] += 0.5 * e2[1];
+            for (int a = 0; a < 4; ++a) Ei[a] += 0.5 * e2[a];
             for (int a = 0; a < 6; ++a) Wi[a] += 0.5 * w6[a];
             ++cnt;
         }
@@ -392,17 +395,17 @@ int64_t orc_forces_cells(int64_t n, const float *pos, const float *q, const int3
     topo_build(&t, n, nex, ex, n14, p14);
     grid_t g;
     int have_grid = grid_build(&g, n, pos, box, (double)rc);
-    double *Ep = (double *)malloc(sizeof(double) * 8 * (size_t)(n ? n : 1));
+    double *Ep = (double *)malloc(sizeof(double) * 10 * (size_t)(n ? n : 1));
     int64_t *cnt = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n ? n : 1));
 #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t i = 0; i < n; ++i)
-        cnt[i] = atom_sum(&p, &t, have_grid ? &g : NULL, n, pos, q, type, i, F + 3 * i, Ep + 8 * i, Ep + 8 * i + 2);
-    E[0] = E[1] = 0.0;
+        cnt[i] = atom_sum(&p, &t, have_grid ? &g : NULL, n, pos, q, type, i, F + 3 * i, Ep + 10 * i, Ep + 10 * i + 4);
+    E[0] = E[1] = E[2] = E[3] = 0.0;
     for (int a = 0; a < 6; ++a) W[a] = 0.0;
     int64_t tot = 0;
     for (int64_t i = 0; i < n; ++i) {
-        E[0] += Ep[8 * i]; E[1] += Ep[8 * i + 1];
-        for (int a = 0; a < 6; ++a) W[a] += Ep[8 * i + 2 + a];
+        for (int a = 0; a < 4; ++a) E[a] += Ep[10 * i + a];
+        for (int a = 0; a < 6; ++a) W[a] += Ep[10 * i + 4 + a];
         tot += cnt[i];
     }
     free(Ep); free(cnt);
@@ -412,12 +415,13 @@ int64_t orc_forces_cells(int64_t n, const float *pos, const float *q, const int3
 }
 
 /* Forces on a subset of atoms only (plain loop over all j), for sampled checks
- * of systems too large for the full sum.  F [m*3]; E2 [m*2] half pair energies. */
+ * of systems too large for the full sum.  F [m*3]; E4 [m*4] half pair energies
+ * (LJ, Coulomb, |LJ|, |Coulomb|). */
 void orc_forces_subset(int64_t n, const float *pos, const float *q, const int32_t *type,
                        int ntypes, const double *A, const double *B, const float *box,
                        float rc, float rs, float alpha, float ke, float s14_lj, float s14_c,
                        int64_t nex, const int32_t *ex, int64_t n14, const int32_t *p14,
-                       int64_t m, const int64_t *atoms, double *F, double *E2, int64_t *npair)
+                       int64_t m, const int64_t *atoms, double *F, double *E4, int64_t *npair)
 {
     prm_t p;
     prm_init(&p, box, rc, rs, alpha, ke, s14_lj, s14_c, ntypes, A, B);
@@ -426,7 +430,7 @@ void orc_forces_subset(int64_t n, const float *pos, const float *q, const int32_
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t k = 0; k < m; ++k) {
         double W[6];
-        npair[k] = atom_sum(&p, &t, NULL, n, pos, q, type, atoms[k], F + 3 * k, E2 + 2 * k, W);
+        npair[k] = atom_sum(&p, &t, NULL, n, pos, q, type, atoms[k], F + 3 * k, E4 + 4 * k, W);
     }
     topo_free(&t);
 }

@@ -81,6 +81,18 @@ def test_lj_pair_minimum():
     assert abs(E2[0]) < 1e-5
 
 
+def test_energy_scale_output():
+    # sum of |pair energy| equals |E| for one pair and bounds |E| in general
+    s = make_sys([[5, 5, 5], [5, 8.2, 5.5]], [30] * 3, q=[0.3, -0.7], sigma=[3.0], eps=[0.15], alpha=0.32)
+    _, E, _, _, Es = oracle.forces(s, with_scale=True)
+    assert np.allclose(Es, np.abs(E), rtol=1e-15)
+    w = small_water(64, k=19)
+    _, E, _, _, Es = oracle.forces(w, with_scale=True)
+    assert np.all(Es >= np.abs(E)) and np.all(Es > 0)
+    _, E2, _, _, Es2 = oracle.forces(w, method="cells", with_scale=True)
+    assert np.allclose(Es2, Es, rtol=1e-12)
+
+
 def test_lorentz_berthelot_mixing():
     # two types: unlike pair uses sigma=(s1+s2)/2, eps=sqrt(e1 e2); at its own
     # minimum the pair energy is -eps_12.
@@ -484,9 +496,9 @@ def _forces_with_tables(s, A, B, pos=None):
     args[5] = oracle._p(A)
     args[6] = oracle._p(B)
     n = args[0]
-    F = np.zeros((n, 3)); E = np.zeros(2); W = np.zeros(6)
+    F = np.zeros((n, 3)); E = np.zeros(4); W = np.zeros(6)
     oracle.lib().orc_forces_allpairs(*args, oracle._p(F), oracle._p(E), oracle._p(W))
-    return F, E
+    return F, E[:2]
 
 
 def test_adjoint_lj_tables_exact_fd():
