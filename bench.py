@@ -1,0 +1,344 @@
+#!/usr/bin/env python3
+"""Benchmark of the short-range non-bonded hot path on one GB300 per rank.
+
+Step: one force evaluation of the 23,500-atom solvated-chain system (62.2 A
+box, rc 9 A switched from 7.5 A, Ewald alpha 0.32, 2,500-atom chain with
+exclusions and scaled 1-4 pairs plus 7,000 TIP3P-shaped waters): cell-list
+rebuild from the positions (wrap, column binning, z-sort, cluster bounding
+boxes, exclusion map, cluster-pair list), then forces, energies and virial.
+The step is replayed from a CUDA graph; the L2 cache is flushed (a 512 MiB
+write) before every timed step, outside the timed interval.
+
+Metric: pair interactions per second = unique in-cutoff, non-excluded pairs
+per step / seconds per step (the pair count is the kernel's own count, taken
+once before timing).  The JSON line also carries the roofline of the force
+kernel (FP32 pipe; 73 algorithmic FLOP per pair), the end-to-end number
+through host buffers, the adjoint and batched forms, clocks, and the FP64
+oracle timed on the host cores (context only).
+
+Multi-GPU: every rank evaluates its own replica (no data-path collective);
+value = pairs of all ranks / max step time over ranks.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "pair interactions/s and ms per force eval at 23.5k atoms; % FP32 roofline"
+UNIT = "pairs/s"
+FLOP_PER_PAIR = 73  # LJ + switch + Ewald real space, FMA = 2, MUFU = 1
+WORKLOAD = ("solvated-chain system, 23,500 atoms (2,500-atom chain + 7,000 TIP3P-shaped waters), "
+            "62.2 A cubic box, rc 9 A, switch 7.5 A, Ewald alpha 0.32, 1-2/1-3 excluded, 1-4 scaled")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-extras", action="store_true", help="skip adjoint/batched/e2e/cpu legs")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+            os.unlink(self.path)
+        except OSError:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_run(system, budget_s: float = 12.0, max_reps: int = 50):
+    """The FP64 oracle (cell-list traversal, OpenMP over atoms) timed on the host."""
+    import oracle
+    oracle.build()
+    times, npairs = [], 0
+    t_end = time.perf_counter() + budget_s
+    for _ in range(max_reps):
+        t0 = time.perf_counter()
+        _, _, _, npairs = oracle.forces(system, method="cells")
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() > t_end:
+            break
+    return times, npairs, oracle.num_threads()
+
+
+def reference_arm(args, world, rank):
+    """--impl reference: the FP64 CPU oracle on the same workload and metric."""
+    if rank != 0:
+        return 0
+    from paper_0902_0827_gb300 import systems as S
+    s = S.solvated_chain()
+    import oracle
+    oracle.build()
+    for _ in range(max(args.warmup, 0)):
+        oracle.forces(s, method="cells")
+    times = []
+    npairs = 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        _, _, _, npairs = oracle.forces(s, method="cells")
+        times.append(time.perf_counter() - t0)
+    per = sum(times) / len(times)
+    val = npairs / per
+    cores = oracle.num_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_atoms": s.n_atoms, "pairs_per_step": npairs},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"full force evaluation of the {s.n_atoms}-atom system per step"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return reference_arm(args, world, rank)
+
+    import numpy as np
+    import torch
+
+    from paper_0902_0827_gb300 import nb
+    from paper_0902_0827_gb300 import systems as S
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    props = torch.cuda.get_device_properties(dev)
+    n_sms = props.multi_processor_count
+    s = S.solvated_chain()
+    ctx = nb.Nonbonded(s)
+    pos, q, typ = nb.concat_inputs([s], device=dev)
+    N = s.n_atoms
+    F = torch.empty((N, 3), dtype=torch.float32, device=dev)
+    E = torch.empty((1, 2), dtype=torch.float64, device=dev)
+    W = torch.empty((1, 6), dtype=torch.float64, device=dev)
+
+    def step():
+        ctx.build(pos)
+        ctx.forces(pos, q, typ, F=F, energy=E, virial=W)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    ctx.status()
+    _, npairs, n_ordered = ctx.debug_pairs(cap=0)
+
+    # CUDA graph of one step, captured on a side stream
+    side = torch.cuda.Stream(device=dev)
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        step()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=side):
+            step()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+
+    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)  # 512 MiB > L2
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = Clocks(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record()
+        g.replay()
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(step_ms) / len(step_ms)
+    ms = max_over_ranks(ms, world)
+    ctx.status()
+    value = world * npairs / (ms * 1e-3)
+
+    # roofline of the force kernel: events on the launching stream around each launch
+    ctx.set_profiling(True)
+    ctx.profile()
+    for _ in range(args.steps):
+        flush.zero_()
+        step()
+    fms, fl = ctx.profile()
+    ctx.set_profiling(False)
+    f_avg = fms / max(fl, 1)
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    peak_tflops = n_sms * 128 * 2 * sm_max * 1e6 / 1e12
+    achieved = FLOP_PER_PAIR * npairs / (f_avg * 1e-3) / 1e12
+    traffic = None
+    prof_path = os.path.join(ROOT, "profiles", "force_kernel_traffic.json")
+    if os.path.exists(prof_path):
+        try:
+            traffic = json.load(open(prof_path)).get("bytes_per_launch")
+        except (OSError, ValueError):
+            traffic = None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": traffic,
+                "kernel": "k_force (FP32 pair arithmetic)", "ms_per_launch": f_avg,
+                "peak_basis": f"{n_sms} SMs x 128 FP32 lanes x 2 FLOP x {sm_max:.0f} MHz"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_atoms": N, "pairs_per_step": npairs,
+                   "ordered_pair_evaluations": n_ordered, "l2": "flushed before every timed step",
+                   "graph": "one CUDA graph per step", "parallelism": f"replicas x{world}",
+                   "tuning": ctx.tuning()},
+        "ms_per_force_eval": ms,
+        "roofline": roofline,
+        "clocks": clk,
+        "gpu_launches": 9 * args.steps,
+    }
+
+    if not args.no_extras:
+        # end to end through the public API with host buffers (pinned)
+        hpos = pos.cpu().pin_memory()
+        hq = q.cpu().pin_memory()
+        ht = typ.cpu().pin_memory()
+        hF = torch.empty((N, 3), dtype=torch.float32).pin_memory()
+        hE = torch.empty((1, 2), dtype=torch.float64).pin_memory()
+        hW = torch.empty((1, 6), dtype=torch.float64).pin_memory()
+        dpos, dq, dt = torch.empty_like(pos), torch.empty_like(q), torch.empty_like(typ)
+
+        def e2e_step():
+            dpos.copy_(hpos, non_blocking=True)
+            dq.copy_(hq, non_blocking=True)
+            dt.copy_(ht, non_blocking=True)
+            ctx.build(dpos)
+            ctx.forces(dpos, dq, dt, F=F, energy=E, virial=W)
+            hF.copy_(F, non_blocking=True)
+            hE.copy_(E, non_blocking=True)
+            hW.copy_(W, non_blocking=True)
+
+        for _ in range(3):
+            e2e_step()
+        torch.cuda.synchronize()
+        tt = []
+        for _ in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            e2e_step()
+            b.record()
+            torch.cuda.synchronize()
+            tt.append(a.elapsed_time(b))
+        e2e_ms = max_over_ranks(sum(tt) / len(tt), world)
+        bi = hpos.numel() * 4 + hq.numel() * 4 + ht.numel() * 4
+        bo = hF.numel() * 4 + hE.numel() * 8 + hW.numel() * 8
+        line["e2e"] = {"value": world * npairs / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": bi,
+                       "d2h_bytes_per_step": bo, "ms_per_step": e2e_ms}
+        line["gpu_launches"] += 9 * args.steps
+        ctx.status()
+    if rank == 0 and not args.no_cpu and world == 1:
+        times, cp, cores = cpu_oracle_run(s)
+        per = sum(times) / len(times)
+        line["cpu_baseline"] = {"value": cp / per, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"{len(times)} full FP64 cell-list evaluations of the {N}-atom system",
+                                "ms_per_eval": per * 1e3}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

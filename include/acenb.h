@@ -194,6 +194,14 @@ nb_status nb_debug_cells(nb_ctx *ctx, int32_t *h_perm, int64_t *n_slots,
  * Synchronous. */
 nb_status nb_debug_pairs(nb_ctx *ctx, int32_t *h_ij, int64_t cap, int64_t *n, int64_t *n_ordered);
 
+/* nb_set_profiling - when on != 0, every later force-kernel launch is
+ * bracketed by CUDA events on the context's stream (at most 4096 launches are
+ * recorded; do not enable during stream capture).  nb_get_profile
+ * synchronises, returns the summed duration in milliseconds and the number
+ * of recorded launches of the force kernel, and clears the record. */
+nb_status nb_set_profiling(nb_ctx *ctx, int32_t on);
+nb_status nb_get_profile(nb_ctx *ctx, double *force_ms, int64_t *launches);
+
 /* nb_status_string - static description of a status code. */
 const char *nb_status_string(nb_status s);
 

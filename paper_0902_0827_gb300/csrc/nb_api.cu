@@ -497,10 +497,41 @@ nb_status nb_set_stream(nb_ctx *ctx, void *cuda_stream)
     return NB_OK;
 }
 
+nb_status nb_set_profiling(nb_ctx *ctx, int32_t on)
+{
+    if (!ctx) return NB_ERR_INVALID_ARG;
+    if (on && ctx->prof_ev.empty()) {
+        ctx->prof_ev.resize(2 * 4096);
+        for (auto &e : ctx->prof_ev)
+            if (cudaEventCreate(&e) != cudaSuccess) return NB_ERR_CUDA;
+    }
+    ctx->profiling = on != 0;
+    ctx->prof_n = 0;
+    return NB_OK;
+}
+
+nb_status nb_get_profile(nb_ctx *ctx, double *force_ms, int64_t *launches)
+{
+    if (!ctx) return NB_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return NB_ERR_CUDA;
+    double tot = 0.0;
+    for (int k = 0; k < ctx->prof_n; ++k) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, ctx->prof_ev[2 * k], ctx->prof_ev[2 * k + 1]) != cudaSuccess) return NB_ERR_CUDA;
+        tot += ms;
+    }
+    if (force_ms) *force_ms = tot;
+    if (launches) *launches = ctx->prof_n;
+    ctx->prof_n = 0;
+    return NB_OK;
+}
+
 void nb_destroy(nb_ctx *ctx)
 {
     if (!ctx) return;
     cudaStreamSynchronize(ctx->stream);
+    for (auto &e : ctx->prof_ev) cudaEventDestroy(e);
+    ctx->prof_ev.clear();
     free_all(ctx);
     delete ctx;
 }

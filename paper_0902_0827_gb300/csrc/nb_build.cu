@@ -240,38 +240,57 @@ __global__ void k_list(const SysDesc *__restrict__ sys, const int *__restrict__ 
         const int cyb = min(2 * S.ny - 1, (int)floorf((hi.y + rcm) * S.inv_w[1]));
         const bool zdn = (lo.z - rcm) < 0.0f;
         const bool zup = (hi.z + rcm) >= S.L[2];
-        for (int cy = cya; cy <= cyb; ++cy) {
-            int ccy = cy < 0 ? cy + S.ny : (cy >= S.ny ? cy - S.ny : cy);
-            int sy = cy < 0 ? 1 : (cy >= S.ny ? 2 : 0);
-            float oy = sy == 1 ? -S.L[1] : (sy == 2 ? S.L[1] : 0.0f);
-            for (int cx = cxa; cx <= cxb; ++cx) {
-                int ccx = cx < 0 ? cx + S.nx : (cx >= S.nx ? cx - S.nx : cx);
-                int sx = cx < 0 ? 1 : (cx >= S.nx ? 2 : 0);
-                float ox = sx == 1 ? -S.L[0] : (sx == 2 ? S.L[0] : 0.0f);
-                int col = S.col_begin + ccy * S.nx + ccx;
-                int jb = col_slot[col] / kCluster, je = col_slot[col + 1] / kCluster;
-                for (int J0 = jb; J0 < je; J0 += 32) {
-                    int J = J0 + lane;
-                    bool valid = J < je;
-                    float4 jl = valid ? bb_lo[J] : make_float4(0, 0, 0, 0);
-                    float4 jh = valid ? bb_hi[J] : make_float4(0, 0, 0, 0);
-                    float gx = fmaxf(fmaxf((jl.x + ox) - hi.x, lo.x - (jh.x + ox)), 0.0f);
-                    float gy = fmaxf(fmaxf((jl.y + oy) - hi.y, lo.y - (jh.y + oy)), 0.0f);
-                    float gxy = gx * gx + gy * gy;
+        const int ncx = cxb - cxa + 1, ncand = ncx * (cyb - cya + 1);
+        // lanes over candidate columns; clusters of a column in lock-step
+        for (int c0 = 0; c0 < ncand; c0 += 32) {
+            const int c = c0 + lane;
+            const bool cv = c < ncand;
+            const int cy = cya + (cv ? c / ncx : 0), cx = cxa + (cv ? c % ncx : 0);
+            const int ccy = cy < 0 ? cy + S.ny : (cy >= S.ny ? cy - S.ny : cy);
+            const int ccx = cx < 0 ? cx + S.nx : (cx >= S.nx ? cx - S.nx : cx);
+            const int sy = cy < 0 ? 1 : (cy >= S.ny ? 2 : 0);
+            const int sx = cx < 0 ? 1 : (cx >= S.nx ? 2 : 0);
+            const float oy = sy == 1 ? -S.L[1] : (sy == 2 ? S.L[1] : 0.0f);
+            const float ox = sx == 1 ? -S.L[0] : (sx == 2 ? S.L[0] : 0.0f);
+            int jb = 0, nj = 0;
+            if (cv) {
+                const int col = S.col_begin + ccy * S.nx + ccx;
+                jb = col_slot[col] / kCluster;
+                nj = col_slot[col + 1] / kCluster - jb;
+            }
+            int maxj = nj;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) maxj = max(maxj, __shfl_xor_sync(FULL, maxj, o));
+            const uint32_t code_xy = ((uint32_t)sx << kShiftBit) | ((uint32_t)sy << (kShiftBit + 2));
+            for (int k0 = 0; k0 < maxj; k0 += 4) {
+                float4 jl[4], jh[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const bool v = k0 + u < nj;
+                    jl[u] = v ? bb_lo[jb + k0 + u] : make_float4(INFINITY, INFINITY, INFINITY, 0.0f);
+                    jh[u] = v ? bb_hi[jb + k0 + u] : make_float4(INFINITY, INFINITY, INFINITY, 0.0f);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (k0 + u >= maxj) break;
+                    const int J = jb + k0 + u;
+                    const bool v = k0 + u < nj;
+                    const float gx = fmaxf(fmaxf((jl[u].x + ox) - hi.x, lo.x - (jh[u].x + ox)), 0.0f);
+                    const float gy = fmaxf(fmaxf((jl[u].y + oy) - hi.y, lo.y - (jh[u].y + oy)), 0.0f);
+                    const float gxy = gx * gx + gy * gy;
                     bool fl = flag_all;
                     for (int m = 0; m < npc; ++m) fl |= (__shfl_sync(FULL, pcl, m) == J);
+#pragma unroll
                     for (int sz = 0; sz < 3; ++sz) {
-                        if (sz == 1 && !zdn) continue;
-                        if (sz == 2 && !zup) continue;
-                        float oz = sz == 1 ? -S.L[2] : (sz == 2 ? S.L[2] : 0.0f);
-                        float gz = fmaxf(fmaxf((jl.z + oz) - hi.z, lo.z - (jh.z + oz)), 0.0f);
-                        bool keep = valid && (gxy + gz * gz < rcm2);
-                        unsigned bal = __ballot_sync(FULL, keep);
+                        const float oz = sz == 1 ? -S.L[2] : (sz == 2 ? S.L[2] : 0.0f);
+                        const float gz = fmaxf(fmaxf((jl[u].z + oz) - hi.z, lo.z - (jh[u].z + oz)), 0.0f);
+                        const bool zok = sz == 0 || (sz == 1 && zdn) || (sz == 2 && zup);
+                        const bool keep = v && zok && (gxy + gz * gz < rcm2);
+                        const unsigned bal = __ballot_sync(FULL, keep);
                         if (keep) {
-                            int p = cnt + __popc(bal & lt);
-                            uint32_t ent = (uint32_t)J | ((uint32_t)sx << kShiftBit) |
-                                           ((uint32_t)sy << (kShiftBit + 2)) | ((uint32_t)sz << (kShiftBit + 4)) |
-                                           (fl ? kExclFlag : 0u);
+                            const int p = cnt + __popc(bal & lt);
+                            const uint32_t ent = (uint32_t)J | code_xy | ((uint32_t)sz << (kShiftBit + 4)) |
+                                                 (fl ? kExclFlag : 0u);
                             if (p < cap) list[(long long)I * cap + p] = ent;
                         }
                         cnt += __popc(bal);

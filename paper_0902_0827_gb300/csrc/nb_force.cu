@@ -439,9 +439,15 @@ cudaError_t launch_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, con
     A.P = ctx->pp;
     const bool ewald = ctx->pp.ewald != 0;
     const bool virial = d_virial != nullptr;
+    const bool prof = ctx->profiling && ctx->prof_n < (int)ctx->prof_ev.size() / 2;
+    if (prof) cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n], ctx->stream);
     switch (ctx->tune.i_group) {
     case 4: launch_force_mi<4>(ctx, A, ewald, virial, debug_pairs); break;
     default: launch_force_mi<2>(ctx, A, ewald, virial, debug_pairs); break;
+    }
+    if (prof) {
+        cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n + 1], ctx->stream);
+        ctx->prof_n++;
     }
     if (!debug_pairs && (d_energy || d_virial)) {
         const int gpc = kCluster / (ctx->tune.i_group == 4 ? 4 : 2);

@@ -129,6 +129,10 @@ struct nb_ctx {
     std::vector<acenb::SysDesc> sys_h;
     std::vector<double> sig_tab, eps_tab;  // FP64 type-pair parameters
     acenb::DevBuffers d;
+    // profiling: event pairs around force-kernel launches
+    bool profiling = false;
+    std::vector<cudaEvent_t> prof_ev;
+    int prof_n = 0;
 };
 
 namespace acenb {

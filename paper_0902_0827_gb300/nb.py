@@ -24,7 +24,7 @@ STATUS_NAMES = {
 # every symbol include/acenb.h declares
 EXPORTS = ("nb_create", "nb_create_batch", "nb_build_cells", "nb_forces", "nb_backward", "nb_get_status",
            "nb_set_stream", "nb_destroy", "nb_set_tuning", "nb_get_tuning", "nb_get_sizes", "nb_debug_cells",
-           "nb_debug_pairs", "nb_status_string", "nb_set_lj_params")
+           "nb_debug_pairs", "nb_status_string", "nb_set_lj_params", "nb_set_profiling", "nb_get_profile")
 
 
 class NbError(RuntimeError):
@@ -85,6 +85,8 @@ def lib(build_if_missing: bool = True):
             "nb_debug_pairs": ([P, P, I64, ctypes.POINTER(I64), ctypes.POINTER(I64)], ctypes.c_int),
             "nb_status_string": ([ctypes.c_int], ctypes.c_char_p),
             "nb_set_lj_params": ([P, P, P, P, P], ctypes.c_int),
+            "nb_set_profiling": ([P, I32], ctypes.c_int),
+            "nb_get_profile": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64)], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -225,6 +227,15 @@ class Nonbonded:
         if raise_on_error and code != NB_OK:
             raise NbError(code, "device status")
         return code
+
+    def set_profiling(self, on: bool):
+        _check(lib().nb_set_profiling(self.h, int(bool(on))), "nb_set_profiling")
+
+    def profile(self):
+        """(summed force-kernel milliseconds, launches) since profiling was enabled."""
+        ms, n = ctypes.c_double(), ctypes.c_int64()
+        _check(lib().nb_get_profile(self.h, ctypes.byref(ms), ctypes.byref(n)), "nb_get_profile")
+        return ms.value, n.value
 
     # -- tuning / debug --------------------------------------------------
     def tuning(self) -> dict:

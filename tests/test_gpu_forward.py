@@ -197,7 +197,7 @@ def test_batch_matches_per_system_oracle():
 
 
 def test_status_nonfinite_and_stale_and_types():
-    s = small_water(100, 14)
+    s = small_water(216, 14)
     ctx = nb.Nonbonded(s)
     pos, q, t = nb.concat_inputs([s])
     bad = pos.clone()
@@ -218,7 +218,7 @@ def test_status_nonfinite_and_stale_and_types():
 
 
 def test_not_built_is_reported():
-    s = small_water(64, 15)
+    s = small_water(216, 15)
     ctx = nb.Nonbonded(s)
     pos, q, t = nb.concat_inputs([s])
     with pytest.raises(nb.NbError) as e:
