@@ -99,10 +99,11 @@ typedef struct {
 
 /* Tuning knobs (chosen by the autotuner; defaults are safe). */
 typedef struct {
-    int32_t i_group;        /* i-atoms per warp task: 1, 2, 4 or 8 */
-    int32_t warps_per_block;/* 2..16 */
-    int32_t blocks_per_sm;  /* resident blocks per SM used to size the persistent grid */
-    int32_t list_capacity;  /* cluster-pair entries per cluster (>= 64) */
+    int32_t blocks_per_sm;  /* blocks per SM of the persistent force grid, 1..8 */
+    int32_t stage_capacity; /* cluster-pair entries staged in shared memory per block pass,
+                               16..512, multiple of 4 (longer lists are processed in chunks) */
+    int32_t list_capacity;  /* cluster-pair entries per cluster, 64..65536, multiple of 4 */
+    int32_t reserved;       /* must be 0 */
 } nb_tuning;
 
 /* nb_create - one system.  Copies params, validates them (box/cutoff ratio,
@@ -170,7 +171,10 @@ nb_status nb_set_stream(nb_ctx *ctx, void *cuda_stream);
 void nb_destroy(nb_ctx *ctx);
 
 /* nb_set_tuning / nb_get_tuning - read or change the launch configuration.
- * A changed list_capacity reallocates scratch (not allowed during capture). */
+ * A changed list_capacity reallocates scratch and requires a new build (not
+ * allowed during stream capture).  Errors: NB_ERR_INVALID_ARG for values out
+ * of range, NB_ERR_UNSUPPORTED when the shared-memory footprint of the force
+ * kernel would exceed the device limit. */
 nb_status nb_set_tuning(nb_ctx *ctx, const nb_tuning *t);
 nb_status nb_get_tuning(nb_ctx *ctx, nb_tuning *t);
 

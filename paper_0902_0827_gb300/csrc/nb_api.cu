@@ -102,8 +102,8 @@ void free_all(nb_ctx *c)
 {
     auto &d = c->d;
     void *ptrs[] = {d.sys, d.atom_sys, d.atom_col, d.wpos, d.part_orig, d.col_sys, d.col_count, d.col_fill,
-                    d.col_slot, d.stage, d.xyzq, d.tslot, d.perm, d.inv, d.ex_slot, d.bb_lo, d.bb_hi,
-                    d.clus_sys, d.list, d.list_n, d.task_part, d.tab_grad, d.counts, d.status, d.lj_tab,
+                    d.col_slot, d.stage, d.xyzq, d.tslot, d.perm, d.inv, d.ex_slot, d.bb,
+                    d.clus_sys, d.list, d.list_n, d.sys_acc, d.tab_grad, d.counts, d.status, d.lj_tab,
                     d.dbg_n, d.dbg_ij, d.scratch_f, d.scratch_g};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -194,12 +194,11 @@ nb_status allocate(nb_ctx *c)
     ALLOC(d.perm, S);
     ALLOC(d.inv, N);
     ALLOC(d.ex_slot, S * c->K);
-    ALLOC(d.bb_lo, NC);
-    ALLOC(d.bb_hi, NC);
+    ALLOC(d.bb, NC * 2);
     ALLOC(d.clus_sys, NC);
     ALLOC(d.list, NC * (int64_t)c->tune.list_capacity);
     ALLOC(d.list_n, NC);
-    ALLOC(d.task_part, NC * kCluster * kTaskVals);
+    ALLOC(d.sys_acc, (int64_t)c->n_sys * kTaskVals);
     ALLOC(d.tab_grad, (int64_t)T * T * 2);
     ALLOC(d.counts, 4);
     ALLOC(d.status, 1);
@@ -393,10 +392,14 @@ nb_status nb_create_batch(int32_t n_sys, const nb_params *params, void *cuda_str
     for (int64_t a = 0; a < N; ++a)
         for (size_t k = 0; k < part[a].size(); ++k) part_flat[a * K + k] = part[a][k];
     // tuning defaults
-    c->tune.i_group = (K <= 16) ? 2 : 1;
-    c->tune.warps_per_block = 8;
-    c->tune.blocks_per_sm = 2;
+    c->tune.blocks_per_sm = 3;
+    c->tune.stage_capacity = 160;
     c->tune.list_capacity = 512;
+    c->tune.reserved = 0;
+    c->stage_cap = c->tune.stage_capacity;
+    int smem_optin = 0;
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+    c->smem_optin = smem_optin;
 
     nb_status st = allocate(c);
     if (st == NB_OK) {
@@ -539,11 +542,11 @@ void nb_destroy(nb_ctx *ctx)
 nb_status nb_set_tuning(nb_ctx *ctx, const nb_tuning *t)
 {
     if (!ctx || !t) return NB_ERR_INVALID_ARG;
-    if (!(t->i_group == 2 || t->i_group == 4)) return NB_ERR_UNSUPPORTED;
-    if (t->i_group * ctx->K > 32) return NB_ERR_UNSUPPORTED;
-    if (t->warps_per_block < 2 || t->warps_per_block > 8) return NB_ERR_INVALID_ARG;
-    if (t->blocks_per_sm < 1 || t->blocks_per_sm > 32) return NB_ERR_INVALID_ARG;
-    if (t->list_capacity < 64 || t->list_capacity > (1 << 16)) return NB_ERR_INVALID_ARG;
+    if (t->blocks_per_sm < 1 || t->blocks_per_sm > 8 || t->reserved != 0) return NB_ERR_INVALID_ARG;
+    if (t->stage_capacity < 16 || t->stage_capacity > 512 || t->stage_capacity % 4) return NB_ERR_INVALID_ARG;
+    if (t->list_capacity < 64 || t->list_capacity > (1 << 16) || t->list_capacity % 4) return NB_ERR_INVALID_ARG;
+    if (ctx->smem_optin > 0 && force_smem_for(ctx->pp.n_types, t->stage_capacity) > (size_t)ctx->smem_optin)
+        return NB_ERR_UNSUPPORTED;
     if (t->list_capacity != ctx->tune.list_capacity) {
         if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return NB_ERR_CUDA;
         uint32_t *nl = nullptr;
@@ -553,6 +556,7 @@ nb_status nb_set_tuning(nb_ctx *ctx, const nb_tuning *t)
         ctx->built = false;
     }
     ctx->tune = *t;
+    ctx->stage_cap = t->stage_capacity;
     return NB_OK;
 }
 

@@ -110,8 +110,8 @@ constexpr int kSortSmem = 1024;  // atoms per column sorted from shared memory
 __global__ void k_colsort(const int *__restrict__ col_count, const int *__restrict__ col_slot,
                           const int *__restrict__ col_sys, const int *__restrict__ stage,
                           const float4 *__restrict__ wpos, float4 *__restrict__ xyzq, int *__restrict__ tslot,
-                          int *__restrict__ perm, int *__restrict__ inv, float4 *__restrict__ bb_lo,
-                          float4 *__restrict__ bb_hi, int *__restrict__ clus_sys)
+                          int *__restrict__ perm, int *__restrict__ inv, float4 *__restrict__ bb,
+                          int *__restrict__ clus_sys)
 {
     __shared__ float sz[kSortSmem];
     __shared__ int sid[kSortSmem];
@@ -162,8 +162,8 @@ __global__ void k_colsort(const int *__restrict__ col_count, const int *__restri
             hx = fmaxf(hx, p.x); hy = fmaxf(hy, p.y); hz = fmaxf(hz, p.z);
         }
         int I = base / kCluster + q;
-        bb_lo[I] = make_float4(lx, ly, lz, 0.0f);
-        bb_hi[I] = make_float4(hx, hy, hz, 0.0f);
+        bb[2 * I] = make_float4(lx, ly, lz, 0.0f);
+        bb[2 * I + 1] = make_float4(hx, hy, hz, 0.0f);
         clus_sys[I] = col_sys[c];
     }
 }
@@ -191,7 +191,7 @@ __global__ void k_exmap(int slot_cap, const int *__restrict__ counts, int K, con
 // appends (J, shift codes, exclusion flag) for bounding-box gaps below the
 // cutoff (plus a rounding margin).
 __global__ void k_list(const SysDesc *__restrict__ sys, const int *__restrict__ counts,
-                       const float4 *__restrict__ bb_lo, const float4 *__restrict__ bb_hi,
+                       const float4 *__restrict__ bb,
                        const int *__restrict__ clus_sys, const int *__restrict__ col_slot,
                        const int *__restrict__ ex_slot, int K, float rcm, int cap,
                        uint32_t *__restrict__ list, int *__restrict__ list_n, int *__restrict__ status)
@@ -205,7 +205,7 @@ __global__ void k_list(const SysDesc *__restrict__ sys, const int *__restrict__ 
     const unsigned lt = (1u << lane) - 1u;
     for (int I = gw; I < n_clus; I += nw) {
         const SysDesc &S = sys[clus_sys[I]];
-        const float4 lo = bb_lo[I], hi = bb_hi[I];
+        const float4 lo = bb[2 * I], hi = bb[2 * I + 1];
         // distinct partner clusters of I (lanes 0..npc-1 of pcl)
         int pcl = -1, npc = 0;
         bool flag_all = false;
@@ -267,8 +267,8 @@ __global__ void k_list(const SysDesc *__restrict__ sys, const int *__restrict__ 
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const bool v = k0 + u < nj;
-                    jl[u] = v ? bb_lo[jb + k0 + u] : make_float4(INFINITY, INFINITY, INFINITY, 0.0f);
-                    jh[u] = v ? bb_hi[jb + k0 + u] : make_float4(INFINITY, INFINITY, INFINITY, 0.0f);
+                    jl[u] = v ? bb[2 * (jb + k0 + u)] : make_float4(INFINITY, INFINITY, INFINITY, 0.0f);
+                    jh[u] = v ? bb[2 * (jb + k0 + u) + 1] : make_float4(INFINITY, INFINITY, INFINITY, 0.0f);
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
@@ -317,7 +317,7 @@ cudaError_t launch_build(nb_ctx *ctx, const float *d_pos)
     k_scan<<<1, 1024, 0, st>>>(ctx->n_cols, ctx->n_sys, d.col_count, d.col_slot, d.col_fill, d.sys, d.counts);
     k_scatter<<<(N + tb - 1) / tb, tb, 0, st>>>(N, d.atom_col, d.col_fill, d.stage);
     k_colsort<<<ctx->n_cols, 128, 0, st>>>(d.col_count, d.col_slot, d.col_sys, d.stage, d.wpos, d.xyzq, d.tslot,
-                                           d.perm, d.inv, d.bb_lo, d.bb_hi, d.clus_sys);
+                                           d.perm, d.inv, d.bb, d.clus_sys);
     const int S = (int)ctx->slot_cap;
     k_exmap<<<(S + tb - 1) / tb, tb, 0, st>>>(S, d.counts, ctx->K, d.perm, d.part_orig, d.inv, d.ex_slot);
     const int lw = 8;  // warps per block in the list kernel
@@ -325,7 +325,7 @@ cudaError_t launch_build(nb_ctx *ctx, const float *d_pos)
     int lmax = ctx->num_sms * 16;
     if (lblocks > lmax) lblocks = lmax;
     if (lblocks < 1) lblocks = 1;
-    k_list<<<lblocks, lw * 32, 0, st>>>(d.sys, d.counts, d.bb_lo, d.bb_hi, d.clus_sys, d.col_slot, d.ex_slot,
+    k_list<<<lblocks, lw * 32, 0, st>>>(d.sys, d.counts, d.bb, d.clus_sys, d.col_slot, d.ex_slot,
                                         ctx->K, ctx->pp.rc + ctx->pp.list_margin, ctx->tune.list_capacity,
                                         d.list, d.list_n, d.status);
     return cudaGetLastError();

@@ -2,32 +2,36 @@
 // the GPU": the non-bonded kernel computes the full Lennard-Jones and
 // electrostatic force on each particle; as in the paper, the reciprocal force
 // F_ji is not reused, so every atom accumulates its own force and no
-// scattered writes or atomics are needed).
+// scattered force writes or atomics are needed).
 //
-// Work decomposition (GB300 design, not the paper's one-cell-per-block):
-//   task  = (cluster I of 8 sorted atoms, i-group of MI consecutive atoms);
-//   warp  = one task at a time, persistent grid of warps;
-//   lanes = MI i-atoms x JS = 32/MI j-slots.
-// For each task the warp streams I's cluster-pair list, tests every candidate
-// j atom against the i-group's bounding box and compacts the survivors into a
-// per-warp shared-memory queue (x, y, z, q and a type/exclusion word).  Full
-// JS-wide steps of the queue are then evaluated pair by pair in FP32.  Queue
-// entries needing an i-side periodic shift, an exclusion test or the i == j
-// test (the paper's "inner" kernel) go to the top of the queue and use the
-// general path; everything else (the "outer" kernel) uses the fast path.
+// GB300 work decomposition (the paper's one-cell-per-block staging of the
+// neighbour cells in shared memory, re-cut for this machine):
+//   block = one 8-atom cluster I at a time (persistent grid of blocks);
+//   warp  = one i atom of I;
+//   lanes = 32 j candidates (filter) or 32 in-range pairs (compute).
+// For each cluster the first warp stages I's cluster-pair list and, for
+// every listed cluster J, its 8 coordinates+charges, 8 types and bounding
+// box into shared memory with bulk asynchronous copies (TMA) completing on
+// an mbarrier.  Each warp then (1) prunes the staged clusters whose bounding
+// box lies beyond the cutoff of its own atom, (2) tests every remaining j
+// atom with the exact FP32 membership predicate (exclusions and the i == j
+// case removed, the paper's "inner" test, only for flagged clusters) and
+// compacts the in-range pairs (d, r^2, q_j, type/1-4 word) into a per-warp
+// queue, and (3) evaluates full 32-pair steps of the queue in FP32.
 #include <cuda_runtime.h>
 #include <math.h>
 
-#include <type_traits>
+#include <algorithm>
 
 #include "nb_pair.cuh"
+#include "nb_tma.cuh"
 
 namespace acenb {
 
-constexpr int kQCap = 256;   // queue entries per warp
-using FastT = std::integral_constant<bool, false>;  // outer (no exclusion test) path
-using GenT = std::integral_constant<bool, true>;    // inner path
+constexpr int kQ = 64;             // queue entries per warp (drained at >= 32)
 constexpr unsigned kFull = 0xffffffffu;
+constexpr uint32_t kW14 = 1u << 8;  // queue word: pair is a scaled 1-4 pair
+constexpr uint32_t kWaitPolls = 1u << 20;
 
 struct ForceArgs {
     const SysDesc *sys;
@@ -36,14 +40,16 @@ struct ForceArgs {
     const int *tslot;
     const int *perm;
     const int *clus_sys;
+    const float4 *bb;
     const uint32_t *list;
     const int *list_n;
     int cap;
+    int scap;
     const int *ex_slot;
     int K;
     const float2 *lj_tab;
     float *F;
-    long long *task_part;
+    long long *sys_acc;
     int *status;
     long long *dbg_n;
     int *dbg_ij;
@@ -51,68 +57,9 @@ struct ForceArgs {
     PairParams P;
 };
 
-struct Acc {
-    float fx, fy, fz, elj, ec;
-    float w[6];
-};
-
-template <bool EWALD, bool VIRIAL, bool DEBUG, bool GENERAL>
-__device__ __forceinline__ void eval_entry(const ForceArgs &A, const float2 *__restrict__ lj, int ti_row,
-                                           float xi, float yi, float zi, float xim, float yim, float zim,
-                                           float qi, int il, int iorig, float4 pj, uint32_t w, int jorig,
-                                           Acc &acc)
-{
-    float ax = xi, ay = yi, az = zi;
-    if (GENERAL) {
-        if (w & (1u << kQIShift)) ax = xim;
-        if (w & (2u << kQIShift)) ay = yim;
-        if (w & (4u << kQIShift)) az = zim;
-    }
-    float dx, dy, dz;
-    const float r2 = disp_r2(pj.x, pj.y, pj.z, ax, ay, az, dx, dy, dz);
-    bool in = r2 < A.P.rc2;
-    float wlj = 1.0f, wc = 1.0f;
-    if (GENERAL) {
-        if ((w >> (kQExcl + il)) & 1u) in = false;
-        if ((w >> (kQ14 + il)) & 1u) { wlj = A.P.s14_lj; wc = A.P.s14_c; }
-    }
-    const float rinv = rsqrtf(r2);
-    const float2 ab = lj[ti_row + (int)(w & 0xFFu)];
-    float elj, frlj, ec, frc;
-    pair_radial<EWALD, true>(A.P, r2, rinv, ab.x, ab.y, qi * pj.w, elj, frlj, ec, frc);
-    float fs = fmaf(wlj, frlj, wc * frc) * (rinv * rinv);
-    fs = in ? fs : 0.0f;
-    // F_i = U'(r) d / r = -fs d  with fs = -U'(r) / r
-    acc.fx = fmaf(-fs, dx, acc.fx);
-    acc.fy = fmaf(-fs, dy, acc.fy);
-    acc.fz = fmaf(-fs, dz, acc.fz);
-    acc.elj += in ? wlj * elj : 0.0f;
-    acc.ec += in ? wc * ec : 0.0f;
-    if (VIRIAL) {
-        // W_ab += d_ij,a f_ij,b with d_ij = -d and f_ij = -fs d
-        const float fdx = fs * dx, fdy = fs * dy, fdz = fs * dz;
-        acc.w[0] = fmaf(fdx, dx, acc.w[0]);
-        acc.w[1] = fmaf(fdy, dy, acc.w[1]);
-        acc.w[2] = fmaf(fdz, dz, acc.w[2]);
-        acc.w[3] = fmaf(fdx, dy, acc.w[3]);
-        acc.w[4] = fmaf(fdx, dz, acc.w[4]);
-        acc.w[5] = fmaf(fdy, dz, acc.w[5]);
-    }
-    if (DEBUG && in) {
-        atomicAdd((unsigned long long *)&A.dbg_n[0], 1ull);
-        if (iorig < jorig) {
-            long long k = (long long)atomicAdd((unsigned long long *)&A.dbg_n[1], 1ull);
-            if (k < A.dbg_cap) {
-                A.dbg_ij[2 * k] = iorig;
-                A.dbg_ij[2 * k + 1] = jorig;
-            }
-        }
-    }
-}
-
 __device__ __forceinline__ long long to_fixed(float v, int *status)
 {
-    // |v| < 2^26 keeps the sum of 32 lanes inside int64 at scale 2^32
+    // |v| < 2^26 keeps a sum of 32 lanes inside int64 at scale 2^32
     if (!(fabsf(v) < 67108864.0f)) {
         atomicOr(status, ST_OVERFLOW);
         return 0;
@@ -120,200 +67,316 @@ __device__ __forceinline__ long long to_fixed(float v, int *status)
     return __float2ll_rn(v * 4294967296.0f);
 }
 
-template <int MI, bool EWALD, bool VIRIAL, bool DEBUG>
-__global__ void __launch_bounds__(256) k_force(ForceArgs A)
+struct ForceSmem {
+    float2 *lj;
+    uint32_t *ent;
+    float4 *pos;
+    int *typ;
+    float4 *bb;
+    uint16_t *surv;
+    float4 *qd;
+    float2 *qa;
+    uint64_t *bar;
+    int *abort;
+    unsigned long long *cacc;
+};
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+__host__ __device__ inline size_t force_smem_bytes(int T, int scap, int nwarps)
+{
+    size_t b = align16((size_t)T * T * 8);
+    b += align16((size_t)scap * 4);
+    b += (size_t)scap * kCluster * 16;
+    b += (size_t)scap * kCluster * 4;
+    b += (size_t)scap * 2 * 16;
+    b += align16((size_t)nwarps * scap * 2);
+    b += (size_t)nwarps * kQ * 16;
+    b += (size_t)nwarps * kQ * 8;
+    b += 16 + 16 + kTaskVals * 8;
+    return b;
+}
+
+__device__ __forceinline__ ForceSmem carve(unsigned char *smem, int T, int scap, int nwarps, int w)
+{
+    ForceSmem S;
+    size_t off = 0;
+    S.lj = reinterpret_cast<float2 *>(smem + off);
+    off += align16((size_t)T * T * 8);
+    S.ent = reinterpret_cast<uint32_t *>(smem + off);
+    off += align16((size_t)scap * 4);
+    S.pos = reinterpret_cast<float4 *>(smem + off);
+    off += (size_t)scap * kCluster * 16;
+    S.typ = reinterpret_cast<int *>(smem + off);
+    off += (size_t)scap * kCluster * 4;
+    S.bb = reinterpret_cast<float4 *>(smem + off);
+    off += (size_t)scap * 2 * 16;
+    S.surv = reinterpret_cast<uint16_t *>(smem + off) + (size_t)w * scap;
+    off += align16((size_t)nwarps * scap * 2);
+    S.qd = reinterpret_cast<float4 *>(smem + off) + w * kQ;
+    off += (size_t)nwarps * kQ * 16;
+    S.qa = reinterpret_cast<float2 *>(smem + off) + w * kQ;
+    off += (size_t)nwarps * kQ * 8;
+    S.bar = reinterpret_cast<uint64_t *>(smem + off);
+    off += 16;
+    S.abort = reinterpret_cast<int *>(smem + off);
+    off += 16;
+    S.cacc = reinterpret_cast<unsigned long long *>(smem + off);
+    return S;
+}
+
+// Stage the chunk [c0, c0 + n) of cluster I's list (warp 0 only).
+__device__ __forceinline__ void stage_chunk(const ForceArgs &A, const ForceSmem &S, int I, int c0, int n, int lane)
+{
+    const uint32_t *src = A.list + (long long)I * A.cap + c0;
+    const uint32_t ent_bytes = (uint32_t)align16((size_t)n * 4);
+    if (lane == 0) {
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(S.bar, ent_bytes + (uint32_t)n * (kCluster * 16 + kCluster * 4 + 32));
+    }
+    __syncwarp();
+    if (lane == 0) bulk_g2s(S.ent, src, ent_bytes, S.bar);
+    for (int e = lane; e < n; e += 32) {
+        const long long J = (long long)(src[e] & kJMask);
+        bulk_g2s(S.pos + e * kCluster, A.xyzq + J * kCluster, kCluster * 16, S.bar);
+        bulk_g2s(S.typ + e * kCluster, A.tslot + J * kCluster, kCluster * 4, S.bar);
+        bulk_g2s(S.bb + e * 2, A.bb + J * 2, 32, S.bar);
+    }
+}
+
+struct Acc {
+    float fx, fy, fz, elj, ec;
+    float w[6];
+};
+
+// One in-range pair from the queue: d = x_j - x_i (exact-shift image), r2 its
+// FP32 squared length, q_j and the type / 1-4 word.
+template <bool EWALD, bool VIRIAL>
+__device__ __forceinline__ void eval_pair(const PairParams &P, const float2 *__restrict__ lj, int ti_row, float qi,
+                                          float4 d, float2 a, Acc &acc)
+{
+    const uint32_t wd = __float_as_uint(a.y);
+    const float rinv = rsqrtf(d.w);
+    const float2 ab = lj[ti_row + (int)(wd & 0xFFu)];
+    float elj, frlj, ec, frc;
+    pair_radial<EWALD, true>(P, d.w, rinv, ab.x, ab.y, qi * a.x, elj, frlj, ec, frc);
+    const bool is14 = (wd & kW14) != 0u;
+    const float wlj = is14 ? P.s14_lj : 1.0f;
+    const float wc = is14 ? P.s14_c : 1.0f;
+    // F_i = U'(r) d / r = -fs d with fs = -U'(r) / r
+    const float fs = fmaf(wlj, frlj, wc * frc) * (rinv * rinv);
+    acc.elj = fmaf(wlj, elj, acc.elj);
+    acc.ec = fmaf(wc, ec, acc.ec);
+    const float fdx = fs * d.x, fdy = fs * d.y, fdz = fs * d.z;
+    acc.fx -= fdx;
+    acc.fy -= fdy;
+    acc.fz -= fdz;
+    if (VIRIAL) {
+        // W_ab += d_ij,a f_ij,b with d_ij = -d and f_ij = -fs d
+        acc.w[0] = fmaf(fdx, d.x, acc.w[0]);
+        acc.w[1] = fmaf(fdy, d.y, acc.w[1]);
+        acc.w[2] = fmaf(fdz, d.z, acc.w[2]);
+        acc.w[3] = fmaf(fdx, d.y, acc.w[3]);
+        acc.w[4] = fmaf(fdx, d.z, acc.w[4]);
+        acc.w[5] = fmaf(fdy, d.z, acc.w[5]);
+    }
+}
+
+template <bool EWALD, bool VIRIAL, bool DEBUG>
+__global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    constexpr int GPC = kCluster / MI;
-    constexpr int JS = 32 / MI;
     const int T = A.P.n_types;
     const int nwarps = blockDim.x >> 5;
-    const int wib = threadIdx.x >> 5;
+    const int w = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-
-    float2 *lj = reinterpret_cast<float2 *>(smem);
-    const int tab_bytes = (T * T * 8 + 15) & ~15;
-    float4 *qpos = reinterpret_cast<float4 *>(smem + tab_bytes) + wib * kQCap;
-    uint32_t *qword = reinterpret_cast<uint32_t *>(smem + tab_bytes + nwarps * kQCap * 16) + wib * kQCap;
-    int *qorig = DEBUG ? reinterpret_cast<int *>(smem + tab_bytes + nwarps * kQCap * 20) + wib * kQCap : nullptr;
-    for (int k = threadIdx.x; k < T * T; k += blockDim.x) lj[k] = A.lj_tab[k];
+    const ForceSmem S = carve(smem, T, A.scap, nwarps, w);
+    for (int k = threadIdx.x; k < T * T; k += blockDim.x) S.lj[k] = A.lj_tab[k];
+    if (threadIdx.x == 0) {
+        mbar_init(S.bar, 1);
+        *S.abort = 0;
+    }
+    if (threadIdx.x < kTaskVals) S.cacc[threadIdx.x] = 0ull;
     __syncthreads();
 
-    const int il = lane % MI;
-    const int js = lane / MI;
-    const int n_tasks = A.counts[1] * GPC;
-    const int npk = MI * A.K;
-    const float4 padj = make_float4(-kFar, -kFar, -kFar, 0.0f);
-
-    for (int t = blockIdx.x * nwarps + wib; t < n_tasks; t += gridDim.x * nwarps) {
-        const int I = t / GPC;
-        const int i0 = I * kCluster + (t - I * GPC) * MI;
-        const float4 pi = A.xyzq[i0 + il];
-        const int ti = A.tslot[i0 + il];
-        const bool iv = pi.x == pi.x;
-        const SysDesc &S = A.sys[A.clus_sys[I]];
-        const float Lx = S.L[0], Ly = S.L[1], Lz = S.L[2];
-        const float xi = iv ? pi.x : kFar, yi = iv ? pi.y : kFar, zi = iv ? pi.z : kFar;
-        const float xim = __fsub_rn(xi, Lx), yim = __fsub_rn(yi, Ly), zim = __fsub_rn(zi, Lz);
-        const float qi = iv ? pi.w * A.P.ke : 0.0f;
-        const int ti_row = ti * T;
-        const int iorig = DEBUG ? A.perm[i0 + il] : -1;
-        // bounding box of the i-group (valid atoms only)
-        float lox = iv ? pi.x : INFINITY, loy = iv ? pi.y : INFINITY, loz = iv ? pi.z : INFINITY;
-        float hix = iv ? pi.x : -INFINITY, hiy = iv ? pi.y : -INFINITY, hiz = iv ? pi.z : -INFINITY;
+    uint32_t phase = 0;
+    int cur_sys = -1;
+    long long wacc[kTaskVals];
 #pragma unroll
-        for (int o = 1; o < MI; o <<= 1) {
-            lox = fminf(lox, __shfl_xor_sync(kFull, lox, o));
-            loy = fminf(loy, __shfl_xor_sync(kFull, loy, o));
-            loz = fminf(loz, __shfl_xor_sync(kFull, loz, o));
-            hix = fmaxf(hix, __shfl_xor_sync(kFull, hix, o));
-            hiy = fmaxf(hiy, __shfl_xor_sync(kFull, hiy, o));
-            hiz = fmaxf(hiz, __shfl_xor_sync(kFull, hiz, o));
-        }
-        if (!__any_sync(kFull, iv)) {
-            if (lane < kTaskVals) A.task_part[(long long)t * kTaskVals + lane] = 0;
-            continue;
-        }
-        const int pe = lane < npk ? A.ex_slot[(long long)i0 * A.K + lane] : -1;
+    for (int k = 0; k < kTaskVals; ++k) wacc[k] = 0;
+    const int n_clus = A.counts[1];
+    const float rcm2 = A.P.rcm2;
 
+    for (int I = blockIdx.x; I < n_clus; I += gridDim.x) {
+        const int sys_id = A.clus_sys[I];
+        if (sys_id != cur_sys) {
+            // flush the per-warp energy/virial of the previous system through
+            // the block accumulator (integer sums: order independent)
+            if (cur_sys >= 0) {
+                if (lane == 0)
+#pragma unroll
+                    for (int k = 0; k < kTaskVals; ++k) atomicAdd(&S.cacc[k], (unsigned long long)wacc[k]);
+                __syncthreads();
+                if (threadIdx.x < kTaskVals) {
+                    atomicAdd((unsigned long long *)&A.sys_acc[cur_sys * kTaskVals + threadIdx.x], S.cacc[threadIdx.x]);
+                    S.cacc[threadIdx.x] = 0ull;
+                }
+                __syncthreads();
+            }
+#pragma unroll
+            for (int k = 0; k < kTaskVals; ++k) wacc[k] = 0;
+            cur_sys = sys_id;
+        }
+        const SysDesc &SD = A.sys[sys_id];
+        const float Lx = SD.L[0], Ly = SD.L[1], Lz = SD.L[2];
+        const int islot = I * kCluster + w;
+        const float4 pi = A.xyzq[islot];
+        const bool iv = pi.x == pi.x;
+        const int ti_row = A.tslot[islot] * T;
+        const float xi = pi.x, yi = pi.y, zi = pi.z;
+        const float xim = __fsub_rn(xi, Lx), yim = __fsub_rn(yi, Ly), zim = __fsub_rn(zi, Lz);
+        const float qi = pi.w * A.P.ke;
+        const int pe = lane < A.K ? A.ex_slot[(long long)islot * A.K + lane] : -1;
+        const int iorig = DEBUG ? A.perm[islot] : -1;
         Acc acc;
         acc.fx = acc.fy = acc.fz = acc.elj = acc.ec = 0.0f;
 #pragma unroll
         for (int k = 0; k < 6; ++k) acc.w[k] = 0.0f;
-
-        auto drain = [&](int beg, int end, auto general) {
-            constexpr bool GEN = decltype(general)::value;
-            for (int k = beg; k < end; k += JS) {
-                const int e = k + js;
-                const float4 pj = qpos[e];
-                const uint32_t w = qword[e];
-                const int jo = DEBUG ? qorig[e] : 0;
-                eval_entry<EWALD, VIRIAL, DEBUG, GEN>(A, lj, ti_row, xi, yi, zi, xim, yim, zim, qi, il, iorig,
-                                                      pj, w, jo, acc);
-            }
-        };
-
-        int nA = 0, nB = 0;
+        int nq = 0;
         const int nE = A.list_n[I];
-        const uint32_t *L0 = A.list + (long long)I * A.cap;
-        for (int e0 = 0; e0 < nE; e0 += 4) {
-            const int e = e0 + (lane >> 3);
-            const bool ok = e < nE;
-            const uint32_t ent = ok ? L0[e] : 0u;
-            const int J = (int)(ent & kJMask);
-            const int cx = (ent >> kShiftBit) & 3, cy = (ent >> (kShiftBit + 2)) & 3, cz = (ent >> (kShiftBit + 4)) & 3;
-            const bool fl = (ent & kExclFlag) != 0u;
-            const int j = J * kCluster + (lane & 7);
-            float4 pj = ok ? A.xyzq[j] : padj;
-            const int tj = ok ? A.tslot[j] : 0;
-            const bool jv = ok && (pj.x == pj.x);
-            if (cx == 1) pj.x = __fsub_rn(pj.x, Lx);
-            if (cy == 1) pj.y = __fsub_rn(pj.y, Ly);
-            if (cz == 1) pj.z = __fsub_rn(pj.z, Lz);
-            const float bxl = cx == 2 ? lox - Lx : lox, bxh = cx == 2 ? hix - Lx : hix;
-            const float byl = cy == 2 ? loy - Ly : loy, byh = cy == 2 ? hiy - Ly : hiy;
-            const float bzl = cz == 2 ? loz - Lz : loz, bzh = cz == 2 ? hiz - Lz : hiz;
-            const float gx = fmaxf(fmaxf(bxl - pj.x, pj.x - bxh), 0.0f);
-            const float gy = fmaxf(fmaxf(byl - pj.y, pj.y - byh), 0.0f);
-            const float gz = fmaxf(fmaxf(bzl - pj.z, pj.z - bzh), 0.0f);
-            const bool keep = jv && (gx * gx + gy * gy + gz * gz < A.P.rcm2);
-            const uint32_t ish = (uint32_t)(cx == 2) | ((uint32_t)(cy == 2) << 1) | ((uint32_t)(cz == 2) << 2);
-            const bool self = (J == I) && (((ent >> kShiftBit) & 0x3Fu) == 0u);
-            const bool clsB = keep && (ish != 0u || self || fl);
-            uint32_t word = (uint32_t)tj | (ish << kQIShift);
-            if (__any_sync(kFull, clsB && (self || fl))) {
-                uint32_t bits = 0u;
-                if (self) {
-                    const int m = j - i0;
-                    if (m >= 0 && m < MI) bits |= 1u << (kQExcl + m);
+
+        for (int c0 = 0; c0 < nE; c0 += A.scap) {
+            const int nC = min(A.scap, nE - c0);
+            __syncthreads();  // the staging buffers are free
+            if (w == 0) stage_chunk(A, S, I, c0, nC, lane);
+            bool ok = mbar_wait_bounded(S.bar, phase, kWaitPolls);
+            if (!ok) {
+                atomicOr(A.status, ST_TIMEOUT);
+                *S.abort = 1;
+                mbar_wait_bounded(S.bar, phase, kWaitPolls);  // let copies in flight land
+            }
+            phase ^= 1u;
+            __syncthreads();
+            if (*S.abort) return;
+            if (!iv) continue;
+            // (1) prune staged clusters against this atom
+            int ns = 0;
+            for (int e0 = 0; e0 < nC; e0 += 32) {
+                const int e = e0 + lane;
+                bool keep = false;
+                if (e < nC) {
+                    const uint32_t ent = S.ent[e];
+                    const int cx = (ent >> kShiftBit) & 3, cy = (ent >> (kShiftBit + 2)) & 3,
+                              cz = (ent >> (kShiftBit + 4)) & 3;
+                    const float ox = cx == 1 ? -Lx : (cx == 2 ? Lx : 0.0f);
+                    const float oy = cy == 1 ? -Ly : (cy == 2 ? Ly : 0.0f);
+                    const float oz = cz == 1 ? -Lz : (cz == 2 ? Lz : 0.0f);
+                    const float4 lo = S.bb[2 * e], hi = S.bb[2 * e + 1];
+                    const float gx = fmaxf(fmaxf((lo.x + ox) - xi, xi - (hi.x + ox)), 0.0f);
+                    const float gy = fmaxf(fmaxf((lo.y + oy) - yi, yi - (hi.y + oy)), 0.0f);
+                    const float gz = fmaxf(fmaxf((lo.z + oz) - zi, zi - (hi.z + oz)), 0.0f);
+                    keep = gx * gx + gy * gy + gz * gz < rcm2;
                 }
-                for (int m = 0; m < npk; ++m) {
-                    const int pv = __shfl_sync(kFull, pe, m);
-                    if (fl && pv >= 0 && (pv >> 1) == j)
-                        bits |= 1u << (((pv & 1) ? kQ14 : kQExcl) + m / A.K);
-                }
-                word |= bits;
+                const unsigned b = __ballot_sync(kFull, keep);
+                if (keep) S.surv[ns + __popc(b & lt)] = (uint16_t)e;
+                ns += __popc(b);
             }
-            const bool toA = keep && !clsB;
-            const unsigned bA = __ballot_sync(kFull, toA);
-            const unsigned bB = __ballot_sync(kFull, clsB);
-            if (toA) {
-                const int p = nA + __popc(bA & lt);
-                qpos[p] = pj;
-                qword[p] = word;
-                if (DEBUG) qorig[p] = A.perm[j];
-            }
-            if (clsB) {
-                const int p = kQCap - 1 - (nB + __popc(bB & lt));
-                qpos[p] = pj;
-                qword[p] = word;
-                if (DEBUG) qorig[p] = A.perm[j];
-            }
-            nA += __popc(bA);
-            nB += __popc(bB);
             __syncwarp();
-            if (nA + nB + 32 > kQCap) {
-                // drain whole JS-wide steps from the inner end of each region;
-                // the remainders stay where they are (bottom of A, top of B)
-                const int remA = nA % JS;
-                drain(remA, nA, FastT{});
-                nA = remA;
-                if (nA + nB + 32 > kQCap) {
-                    const int remB = nB % JS;
-                    drain(kQCap - nB, kQCap - remB, GenT{});
-                    nB = remB;
+            // (2) exact membership test of the survivors' atoms, 4 clusters x 8 atoms per step
+            for (int s0 = 0; s0 < ns; s0 += 4) {
+                const int si = s0 + (lane >> 3);
+                const bool sv = si < ns;
+                const int e = sv ? (int)S.surv[si] : 0;
+                const int k = lane & 7;
+                const uint32_t ent = S.ent[e];
+                const float4 pj = S.pos[e * kCluster + k];
+                const int tj = S.typ[e * kCluster + k];
+                const int cx = (ent >> kShiftBit) & 3, cy = (ent >> (kShiftBit + 2)) & 3,
+                          cz = (ent >> (kShiftBit + 4)) & 3;
+                const float xj = cx == 1 ? __fsub_rn(pj.x, Lx) : pj.x;
+                const float yj = cy == 1 ? __fsub_rn(pj.y, Ly) : pj.y;
+                const float zj = cz == 1 ? __fsub_rn(pj.z, Lz) : pj.z;
+                float dx, dy, dz;
+                const float r2 = disp_r2(xj, yj, zj, cx == 2 ? xim : xi, cy == 2 ? yim : yi, cz == 2 ? zim : zi,
+                                         dx, dy, dz);
+                bool in = sv && (r2 < A.P.rc2);  // NaN padding fails
+                const int jslot = (int)(ent & kJMask) * kCluster + k;
+                if (jslot == islot && ((ent >> kShiftBit) & 0x3Fu) == 0u) in = false;
+                uint32_t word = (uint32_t)tj;
+                const bool fl = sv && (ent & kExclFlag) != 0u;
+                if (__any_sync(kFull, fl && in)) {
+                    for (int m = 0; m < A.K; ++m) {
+                        const int pv = __shfl_sync(kFull, pe, m);
+                        if (fl && pv >= 0 && (pv >> 1) == jslot) {
+                            if (pv & 1) word |= kW14;
+                            else in = false;
+                        }
+                    }
                 }
+                if (DEBUG && in) {
+                    atomicAdd((unsigned long long *)&A.dbg_n[0], 1ull);
+                    const int jorig = A.perm[jslot];
+                    if (iorig < jorig) {
+                        const long long q = (long long)atomicAdd((unsigned long long *)&A.dbg_n[1], 1ull);
+                        if (q < A.dbg_cap) {
+                            A.dbg_ij[2 * q] = iorig;
+                            A.dbg_ij[2 * q + 1] = jorig;
+                        }
+                    }
+                }
+                const unsigned b = __ballot_sync(kFull, in);
+                if (in) {
+                    const int p = nq + __popc(b & lt);
+                    S.qd[p] = make_float4(dx, dy, dz, r2);
+                    S.qa[p] = make_float2(pj.w, __uint_as_float(word));
+                }
+                nq += __popc(b);
                 __syncwarp();
+                if (nq >= 32) {
+                    // (3) one full step: the top 32 queue entries, one per lane
+                    const int e2 = nq - 32 + lane;
+                    eval_pair<EWALD, VIRIAL>(A.P, S.lj, ti_row, qi, S.qd[e2], S.qa[e2], acc);
+                    nq -= 32;
+                    __syncwarp();
+                }
             }
         }
-        // final drains: whole steps first, then one padded step per region
-        {
-            const int remB = nB % JS;
-            drain(kQCap - nB, kQCap - remB, GenT{});
-            const int remA = nA % JS;
-            drain(remA, nA, FastT{});
-            __syncwarp();
-            if (remA) {
-                if (lane >= remA && lane < JS) { qpos[lane] = padj; qword[lane] = 0u; if (DEBUG) qorig[lane] = 0; }
-                __syncwarp();
-                drain(0, JS, FastT{});
-            }
-            if (remB) {
-                const int p = kQCap - JS + lane;
-                if (lane < JS - remB) { qpos[p] = padj; qword[p] = 0u; if (DEBUG) qorig[p] = 0; }
-                __syncwarp();
-                drain(kQCap - JS, kQCap, GenT{});
-            }
-            __syncwarp();
-        }
-        // forces: sum the JS lanes of each i atom in 64-bit fixed point
+        if (!iv) continue;
+        if (lane < nq) eval_pair<EWALD, VIRIAL>(A.P, S.lj, ti_row, qi, S.qd[lane], S.qa[lane], acc);
+        __syncwarp();
+        // force of atom i: sum of the 32 lanes in 64-bit fixed point
         long long vx = to_fixed(acc.fx, A.status), vy = to_fixed(acc.fy, A.status), vz = to_fixed(acc.fz, A.status);
 #pragma unroll
-        for (int o = MI; o < 32; o <<= 1) {
+        for (int o = 16; o > 0; o >>= 1) {
             vx += __shfl_xor_sync(kFull, vx, o);
             vy += __shfl_xor_sync(kFull, vy, o);
             vz += __shfl_xor_sync(kFull, vz, o);
         }
-        if (js == 0 && iv) {
-            const int a = A.perm[i0 + il];
+        if (lane == 0) {
+            const long long a = A.perm[islot];
             const float sc = 2.3283064365386963e-10f;  // 2^-32
-            A.F[3 * (long long)a] = __ll2float_rn(vx) * sc;
-            A.F[3 * (long long)a + 1] = __ll2float_rn(vy) * sc;
-            A.F[3 * (long long)a + 2] = __ll2float_rn(vz) * sc;
+            A.F[3 * a] = __ll2float_rn(vx) * sc;
+            A.F[3 * a + 1] = __ll2float_rn(vy) * sc;
+            A.F[3 * a + 2] = __ll2float_rn(vz) * sc;
         }
-        // energies and virial of the task: FP32 butterfly (fixed order), then fixed point
+        // energies and virial of atom i: FP32 butterfly (fixed order), then fixed point
         float v[kTaskVals] = {acc.elj, acc.ec, acc.w[0], acc.w[1], acc.w[2], acc.w[3], acc.w[4], acc.w[5]};
 #pragma unroll
         for (int k = 0; k < (VIRIAL ? kTaskVals : 2); ++k) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(kFull, v[k], o);
+            wacc[k] += to_fixed(v[k], A.status);
         }
-        if (lane == 0) {
+    }
+    // final flush of the last system
+    if (cur_sys >= 0) {
+        if (lane == 0)
 #pragma unroll
-            for (int k = 0; k < kTaskVals; ++k)
-                A.task_part[(long long)t * kTaskVals + k] = (VIRIAL || k < 2) ? to_fixed(v[k], A.status) : 0ll;
-        }
+            for (int k = 0; k < kTaskVals; ++k) atomicAdd(&S.cacc[k], (unsigned long long)wacc[k]);
+        __syncthreads();
+        if (threadIdx.x < kTaskVals)
+            atomicAdd((unsigned long long *)&A.sys_acc[cur_sys * kTaskVals + threadIdx.x], S.cacc[threadIdx.x]);
     }
 }
 
@@ -343,69 +406,39 @@ __global__ void k_pack(int slot_cap, const int *__restrict__ counts, const int *
     tslot[s] = t;
 }
 
-// Per-system energy/virial: exact int64 sum of the task partials (order
-// independent, hence deterministic), halved because every pair is visited
-// from both of its atoms.
-__global__ void k_reduce(const SysDesc *__restrict__ sys, int gpc, const long long *__restrict__ task_part,
-                         double *__restrict__ energy, double *__restrict__ virial)
+// Per-system energy/virial: the exact int64 sums (order independent, hence
+// deterministic) to FP64, halved because every pair is visited from both of
+// its atoms.
+__global__ void k_finalize(int n_sys, const long long *__restrict__ sys_acc, double *__restrict__ energy,
+                           double *__restrict__ virial)
 {
-    __shared__ long long red[kTaskVals][256];
-    const int s = blockIdx.x;
-    const int t0 = sys[s].clus_begin * gpc, t1 = sys[s].clus_end * gpc;
-    long long acc[kTaskVals] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x)
-#pragma unroll
-        for (int k = 0; k < kTaskVals; ++k) acc[k] += task_part[(long long)t * kTaskVals + k];
-#pragma unroll
-    for (int k = 0; k < kTaskVals; ++k) red[k][threadIdx.x] = acc[k];
-    __syncthreads();
-    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-        if (threadIdx.x < h)
-#pragma unroll
-            for (int k = 0; k < kTaskVals; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + h];
-        __syncthreads();
-    }
-    if (threadIdx.x < kTaskVals) {
-        const double v = (double)red[threadIdx.x][0] * (0.5 / kFixScale);
-        if (threadIdx.x < 2) {
-            if (energy) energy[2 * s + threadIdx.x] = v;
-        } else if (virial) {
-            virial[6 * s + threadIdx.x - 2] = v;
-        }
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_sys * kTaskVals) return;
+    const int s = i / kTaskVals, k = i % kTaskVals;
+    const double v = (double)sys_acc[i] * (0.5 / kFixScale);
+    if (k < 2) {
+        if (energy) energy[2 * s + k] = v;
+    } else if (virial) {
+        virial[6 * s + k - 2] = v;
     }
 }
 
-template <int MI, bool EWALD, bool VIRIAL, bool DEBUG>
+template <bool EWALD, bool VIRIAL, bool DEBUG>
 static void launch_force_t(nb_ctx *ctx, const ForceArgs &A)
 {
-    const int nw = ctx->tune.warps_per_block;
-    const int tab_bytes = (A.P.n_types * A.P.n_types * 8 + 15) & ~15;
-    const size_t smem = (size_t)tab_bytes + (size_t)nw * kQCap * (DEBUG ? 24 : 20);
+    const int nw = kCluster;
+    const size_t smem = force_smem_bytes(A.P.n_types, A.scap, nw);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_force<MI, EWALD, VIRIAL, DEBUG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             200 * 1024);
+        cudaFuncSetAttribute(k_force<EWALD, VIRIAL, DEBUG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
         attr_set = true;
     }
-    const int grid = ctx->num_sms * ctx->tune.blocks_per_sm;
-    k_force<MI, EWALD, VIRIAL, DEBUG><<<grid, nw * 32, smem, ctx->stream>>>(A);
-}
-
-template <int MI>
-static void launch_force_mi(nb_ctx *ctx, const ForceArgs &A, bool ewald, bool virial, bool debug)
-{
-    if (debug) {
-        if (ewald) launch_force_t<MI, true, false, true>(ctx, A);
-        else launch_force_t<MI, false, false, true>(ctx, A);
-        return;
-    }
-    if (ewald) {
-        if (virial) launch_force_t<MI, true, true, false>(ctx, A);
-        else launch_force_t<MI, true, false, false>(ctx, A);
-    } else {
-        if (virial) launch_force_t<MI, false, true, false>(ctx, A);
-        else launch_force_t<MI, false, false, false>(ctx, A);
-    }
+    // persistent grid: never more blocks than can be resident at once
+    int resident = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_force<EWALD, VIRIAL, DEBUG>, nw * 32, smem);
+    const int per_sm = std::max(1, std::min(ctx->tune.blocks_per_sm, resident));
+    const int grid = ctx->num_sms * per_sm;
+    k_force<EWALD, VIRIAL, DEBUG><<<grid, nw * 32, smem, ctx->stream>>>(A);
 }
 
 cudaError_t launch_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type, float *d_F,
@@ -417,6 +450,7 @@ cudaError_t launch_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, con
     if (d_pos)  // the debug pair export reuses the last packed values
         k_pack<<<(S + tb - 1) / tb, tb, 0, ctx->stream>>>(S, d.counts, d.perm, d.xyzq, d.tslot, d_pos, d_q, d_type,
                                                            d.sys, d.atom_sys, ctx->pp.n_types, d.status);
+    cudaMemsetAsync(d.sys_acc, 0, sizeof(long long) * kTaskVals * ctx->n_sys, ctx->stream);
     ForceArgs A;
     A.sys = d.sys;
     A.counts = d.counts;
@@ -424,14 +458,16 @@ cudaError_t launch_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, con
     A.tslot = d.tslot;
     A.perm = d.perm;
     A.clus_sys = d.clus_sys;
+    A.bb = d.bb;
     A.list = d.list;
     A.list_n = d.list_n;
     A.cap = ctx->tune.list_capacity;
+    A.scap = ctx->stage_cap;
     A.ex_slot = d.ex_slot;
     A.K = ctx->K;
     A.lj_tab = d.lj_tab;
     A.F = d_F;
-    A.task_part = d.task_part;
+    A.sys_acc = d.sys_acc;
     A.status = d.status;
     A.dbg_n = d.dbg_n;
     A.dbg_ij = d.dbg_ij;
@@ -441,19 +477,27 @@ cudaError_t launch_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, con
     const bool virial = d_virial != nullptr;
     const bool prof = ctx->profiling && ctx->prof_n < (int)ctx->prof_ev.size() / 2;
     if (prof) cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n], ctx->stream);
-    switch (ctx->tune.i_group) {
-    case 4: launch_force_mi<4>(ctx, A, ewald, virial, debug_pairs); break;
-    default: launch_force_mi<2>(ctx, A, ewald, virial, debug_pairs); break;
+    if (debug_pairs) {
+        if (ewald) launch_force_t<true, false, true>(ctx, A);
+        else launch_force_t<false, false, true>(ctx, A);
+    } else if (ewald) {
+        if (virial) launch_force_t<true, true, false>(ctx, A);
+        else launch_force_t<true, false, false>(ctx, A);
+    } else {
+        if (virial) launch_force_t<false, true, false>(ctx, A);
+        else launch_force_t<false, false, false>(ctx, A);
     }
     if (prof) {
         cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n + 1], ctx->stream);
         ctx->prof_n++;
     }
     if (!debug_pairs && (d_energy || d_virial)) {
-        const int gpc = kCluster / (ctx->tune.i_group == 4 ? 4 : 2);
-        k_reduce<<<ctx->n_sys, 256, 0, ctx->stream>>>(d.sys, gpc, d.task_part, d_energy, d_virial);
+        const int n = ctx->n_sys * kTaskVals;
+        k_finalize<<<(n + 255) / 256, 256, 0, ctx->stream>>>(ctx->n_sys, d.sys_acc, d_energy, d_virial);
     }
     return cudaGetLastError();
 }
+
+size_t force_smem_for(int T, int scap) { return force_smem_bytes(T, scap, kCluster); }
 
 }  // namespace acenb

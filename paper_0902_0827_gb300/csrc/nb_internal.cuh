@@ -93,12 +93,11 @@ struct DevBuffers {
     int *perm = nullptr;             // [S] slot -> atom (-1 padding)
     int *inv = nullptr;              // [N] atom -> slot
     int *ex_slot = nullptr;          // [S*K] partner slot << 1 | is14, -1 pad
-    float4 *bb_lo = nullptr;         // [NC] cluster bounding boxes
-    float4 *bb_hi = nullptr;         // [NC]
+    float4 *bb = nullptr;            // [NC*2] cluster bounding boxes (lo, hi interleaved)
     int *clus_sys = nullptr;         // [NC] system of each cluster
     uint32_t *list = nullptr;        // [NC*cap] cluster-pair entries
     int *list_n = nullptr;           // [NC]
-    long long *task_part = nullptr;  // [NT*kTaskVals] per-task fixed-point partials
+    long long *sys_acc = nullptr;    // [n_sys*kTaskVals] per-system fixed-point energy/virial
     long long *tab_grad = nullptr;   // [T*T*2] adjoint table gradients (fixed point)
     int *counts = nullptr;           // [4]: n_slots, n_clusters, pair counters
     int *status = nullptr;           // [1]
@@ -120,6 +119,8 @@ struct nb_ctx {
     int64_t clus_cap = 0;
     int K = 1;                     // partners per atom (>= 1)
     int comb_rule = 0;
+    int stage_cap = 160;           // list entries staged per block pass
+    int smem_optin = 0;            // device opt-in shared memory per block
     cudaStream_t stream = nullptr;
     int device = 0;
     int num_sms = 0;
@@ -154,6 +155,7 @@ __device__ __forceinline__ float wrap_coord(float x, float L)
 cudaError_t launch_build(nb_ctx *ctx, const float *d_pos);
 cudaError_t launch_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type,
                           float *d_F, double *d_energy, double *d_virial, bool debug_pairs);
+size_t force_smem_for(int T, int scap);
 cudaError_t launch_backward(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type,
                             const float *d_dLdF, const double *d_dLdE, float *d_dLdpos, float *d_dLdq,
                             double *d_dsig, double *d_deps);

@@ -47,8 +47,8 @@ class nb_params(ctypes.Structure):
 
 
 class nb_tuning(ctypes.Structure):
-    _fields_ = [("i_group", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32), ("list_capacity", ctypes.c_int32)]
+    _fields_ = [("blocks_per_sm", ctypes.c_int32), ("stage_capacity", ctypes.c_int32),
+                ("list_capacity", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _lib = None

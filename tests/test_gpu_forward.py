@@ -112,14 +112,16 @@ def test_forces_energy_virial_parity(case):
     check_virial(W[0], Wo)
 
 
-def test_i_group_variants_agree(case):
+def test_tuning_variants_agree(case):
+    # small staging capacity forces the list of every cluster through several
+    # chunks; other grid sizes change the block-to-cluster assignment
     name, s, Fo, Eo, Wo, npairs, Es = case
-    for ig in (2, 4):
-        if ig * 6 > 32 and s.pairs14.size:
-            continue
-        ctx, inp, F, E, W = gpu_eval(s, tuning=dict(i_group=ig, warps_per_block=4, blocks_per_sm=3))
+    for tune in (dict(stage_capacity=16, blocks_per_sm=1), dict(stage_capacity=64, blocks_per_sm=3),
+                 dict(stage_capacity=256, blocks_per_sm=2)):
+        ctx, inp, F, E, W = gpu_eval(s, tuning=tune)
         check_forces(F, Fo)
         check_energy(E[0], Eo, Es)
+        check_virial(W[0], Wo)
 
 
 def test_reruns_bitwise_identical():
