@@ -9,10 +9,10 @@
 //   block = one 8-atom cluster I at a time (persistent grid of blocks);
 //   warp  = one i atom of I;
 //   lanes = 32 j candidates (filter) or 32 in-range pairs (compute).
-// For each cluster the first warp stages I's cluster-pair list and, for
-// every listed cluster J, its 8 coordinates+charges, 8 types and bounding
-// box into shared memory with bulk asynchronous copies (TMA) completing on
-// an mbarrier.  Each warp then (1) prunes the staged clusters whose bounding
+// For each cluster the block stages I's cluster-pair list and, for every
+// listed cluster J, its 8 coordinates+charges, 8 types and bounding box into
+// shared memory with 16-byte asynchronous copies (cp.async) issued by all
+// threads.  Each warp then (1) prunes the staged clusters whose bounding
 // box lies beyond the cutoff of its own atom, (2) tests every remaining j
 // atom with the exact FP32 membership predicate (exclusions and the i == j
 // case removed, the paper's "inner" test, only for flagged clusters) and
@@ -24,14 +24,12 @@
 #include <algorithm>
 
 #include "nb_pair.cuh"
-#include "nb_tma.cuh"
 
 namespace acenb {
 
 constexpr int kQ = 64;             // queue entries per warp (drained at >= 32)
 constexpr unsigned kFull = 0xffffffffu;
 constexpr uint32_t kW14 = 1u << 8;  // queue word: pair is a scaled 1-4 pair
-constexpr uint32_t kWaitPolls = 1u << 20;
 
 struct ForceArgs {
     const SysDesc *sys;
@@ -76,10 +74,13 @@ struct ForceSmem {
     uint16_t *surv;
     float4 *qd;
     float2 *qa;
-    uint64_t *bar;
-    int *abort;
     unsigned long long *cacc;
 };
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
@@ -93,7 +94,7 @@ __host__ __device__ inline size_t force_smem_bytes(int T, int scap, int nwarps)
     b += align16((size_t)nwarps * scap * 2);
     b += (size_t)nwarps * kQ * 16;
     b += (size_t)nwarps * kQ * 8;
-    b += 16 + 16 + kTaskVals * 8;
+    b += kTaskVals * 8;
     return b;
 }
 
@@ -117,31 +118,47 @@ __device__ __forceinline__ ForceSmem carve(unsigned char *smem, int T, int scap,
     off += (size_t)nwarps * kQ * 16;
     S.qa = reinterpret_cast<float2 *>(smem + off) + w * kQ;
     off += (size_t)nwarps * kQ * 8;
-    S.bar = reinterpret_cast<uint64_t *>(smem + off);
-    off += 16;
-    S.abort = reinterpret_cast<int *>(smem + off);
-    off += 16;
     S.cacc = reinterpret_cast<unsigned long long *>(smem + off);
     return S;
 }
 
-// Stage the chunk [c0, c0 + n) of cluster I's list (warp 0 only).
-__device__ __forceinline__ void stage_chunk(const ForceArgs &A, const ForceSmem &S, int I, int c0, int n, int lane)
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
 {
-    const uint32_t *src = A.list + (long long)I * A.cap + c0;
-    const uint32_t ent_bytes = (uint32_t)align16((size_t)n * 4);
-    if (lane == 0) {
-        fence_proxy_async_smem();
-        mbar_arrive_expect_tx(S.bar, ent_bytes + (uint32_t)n * (kCluster * 16 + kCluster * 4 + 32));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+// Stage the chunk [c0, c0 + n) of cluster I's list, then for every listed
+// cluster J its 8 coordinates+charges, 8 types and bounding box, with 16-byte
+// asynchronous copies issued by every thread of the block.
+__device__ __forceinline__ void stage_chunk(const ForceArgs &A, const ForceSmem &S, int I, int c0, int n)
+{
+    const uint4 *src = reinterpret_cast<const uint4 *>(A.list + (long long)I * A.cap + c0);
+    const int nent16 = (n + 3) >> 2;
+    for (int p = threadIdx.x; p < nent16; p += blockDim.x) cp_async16(reinterpret_cast<uint4 *>(S.ent) + p, src + p);
+    cp_async_wait_all();
+    __syncthreads();
+    constexpr int kPieces = kCluster + 2 + 2;  // 16-byte pieces per entry: 8 pos, 2 type, 2 bbox
+    for (int p = threadIdx.x; p < kPieces * n; p += blockDim.x) {
+        const int e = p / kPieces, sub = p - e * kPieces;
+        const long long J = (long long)(S.ent[e] & kJMask);
+        if (sub < kCluster) {
+            cp_async16(S.pos + e * kCluster + sub, A.xyzq + J * kCluster + sub);
+        } else if (sub < kCluster + 2) {
+            const int h = sub - kCluster;
+            cp_async16(reinterpret_cast<uint4 *>(S.typ + e * kCluster) + h,
+                       reinterpret_cast<const uint4 *>(A.tslot + J * kCluster) + h);
+        } else {
+            const int h = sub - kCluster - 2;
+            cp_async16(S.bb + e * 2 + h, A.bb + J * 2 + h);
+        }
     }
-    __syncwarp();
-    if (lane == 0) bulk_g2s(S.ent, src, ent_bytes, S.bar);
-    for (int e = lane; e < n; e += 32) {
-        const long long J = (long long)(src[e] & kJMask);
-        bulk_g2s(S.pos + e * kCluster, A.xyzq + J * kCluster, kCluster * 16, S.bar);
-        bulk_g2s(S.typ + e * kCluster, A.tslot + J * kCluster, kCluster * 4, S.bar);
-        bulk_g2s(S.bb + e * 2, A.bb + J * 2, 32, S.bar);
-    }
+    cp_async_wait_all();
+    __syncthreads();
 }
 
 struct Acc {
@@ -193,14 +210,9 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
     const unsigned lt = (1u << lane) - 1u;
     const ForceSmem S = carve(smem, T, A.scap, nwarps, w);
     for (int k = threadIdx.x; k < T * T; k += blockDim.x) S.lj[k] = A.lj_tab[k];
-    if (threadIdx.x == 0) {
-        mbar_init(S.bar, 1);
-        *S.abort = 0;
-    }
     if (threadIdx.x < kTaskVals) S.cacc[threadIdx.x] = 0ull;
     __syncthreads();
 
-    uint32_t phase = 0;
     int cur_sys = -1;
     long long wacc[kTaskVals];
 #pragma unroll
@@ -249,16 +261,7 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
         for (int c0 = 0; c0 < nE; c0 += A.scap) {
             const int nC = min(A.scap, nE - c0);
             __syncthreads();  // the staging buffers are free
-            if (w == 0) stage_chunk(A, S, I, c0, nC, lane);
-            bool ok = mbar_wait_bounded(S.bar, phase, kWaitPolls);
-            if (!ok) {
-                atomicOr(A.status, ST_TIMEOUT);
-                *S.abort = 1;
-                mbar_wait_bounded(S.bar, phase, kWaitPolls);  // let copies in flight land
-            }
-            phase ^= 1u;
-            __syncthreads();
-            if (*S.abort) return;
+            stage_chunk(A, S, I, c0, nC);
             if (!iv) continue;
             // (1) prune staged clusters against this atom
             int ns = 0;
