@@ -145,11 +145,10 @@ __global__ void k_colsort(const int *__restrict__ col_count, const int *__restri
         xyzq[slot] = make_float4(p.x, p.y, p.z, 0.0f);
         if (small) sp[rank] = p;
     }
-    const float qnan = __int_as_float(0x7fc00000);
     for (int k = n + threadIdx.x; k < npad; k += blockDim.x) {
         perm[base + k] = -1;
         tslot[base + k] = 0;
-        xyzq[base + k] = make_float4(qnan, qnan, qnan, 0.0f);
+        xyzq[base + k] = make_float4(kPadCoord, kPadCoord, kPadCoord, 0.0f);
     }
     __syncthreads();
     // cluster bounding boxes over the real atoms of each 8-slot cluster

@@ -8,16 +8,16 @@
 // neighbour cells in shared memory, re-cut for this machine):
 //   block = one 8-atom cluster I at a time (persistent grid of blocks);
 //   warp  = one i atom of I;
-//   lanes = 32 j candidates (filter) or 32 in-range pairs (compute).
+//   lane  = one candidate cluster J (its 8 atoms evaluated in turn).
 // For each cluster the block stages I's cluster-pair list and, for every
 // listed cluster J, its 8 coordinates+charges, 8 types and bounding box into
-// shared memory with 16-byte asynchronous copies (cp.async) issued by all
-// threads.  Each warp then (1) prunes the staged clusters whose bounding
-// box lies beyond the cutoff of its own atom, (2) tests every remaining j
-// atom with the exact FP32 membership predicate (exclusions and the i == j
-// case removed, the paper's "inner" test, only for flagged clusters) and
-// compacts the in-range pairs (d, r^2, q_j, type/1-4 word) into a per-warp
-// queue, and (3) evaluates full 32-pair steps of the queue in FP32.
+// shared memory with asynchronous copies (cp.async) issued by all threads;
+// coordinates and types are swizzled by J so that lanes reading the same atom
+// slot of different clusters hit different banks.  Each warp prunes the
+// staged clusters whose bounding box lies beyond the cutoff of its own atom,
+// then evaluates the surviving clusters one per lane with the exact FP32
+// membership predicate as the mask of the pair arithmetic (exclusions and the
+// i == j case masked too, the paper's "inner" test, only for flagged clusters).
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -27,9 +27,7 @@
 
 namespace acenb {
 
-constexpr int kQ = 64;             // queue entries per warp (drained at >= 32)
 constexpr unsigned kFull = 0xffffffffu;
-constexpr uint32_t kW14 = 1u << 8;  // queue word: pair is a scaled 1-4 pair
 
 struct ForceArgs {
     const SysDesc *sys;
@@ -72,8 +70,6 @@ struct ForceSmem {
     int *typ;
     float4 *bb;
     uint16_t *surv;
-    float4 *qd;
-    float2 *qa;
     unsigned long long *cacc;
 };
 
@@ -92,8 +88,6 @@ __host__ __device__ inline size_t force_smem_bytes(int T, int scap, int nwarps)
     b += (size_t)scap * kCluster * 4;
     b += (size_t)scap * 2 * 16;
     b += align16((size_t)nwarps * scap * 2);
-    b += (size_t)nwarps * kQ * 16;
-    b += (size_t)nwarps * kQ * 8;
     b += kTaskVals * 8;
     return b;
 }
@@ -114,10 +108,6 @@ __device__ __forceinline__ ForceSmem carve(unsigned char *smem, int T, int scap,
     off += (size_t)scap * 2 * 16;
     S.surv = reinterpret_cast<uint16_t *>(smem + off) + (size_t)w * scap;
     off += align16((size_t)nwarps * scap * 2);
-    S.qd = reinterpret_cast<float4 *>(smem + off) + w * kQ;
-    off += (size_t)nwarps * kQ * 16;
-    S.qa = reinterpret_cast<float2 *>(smem + off) + w * kQ;
-    off += (size_t)nwarps * kQ * 8;
     S.cacc = reinterpret_cast<unsigned long long *>(smem + off);
     return S;
 }
@@ -127,13 +117,21 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 
+__device__ __forceinline__ void cp_async4(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
 __device__ __forceinline__ void cp_async_wait_all()
 {
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
+// Slot of atom k of staged entry e (swizzle by e, conflict-free lane access).
+__device__ __forceinline__ int swz(int e, int k) { return e * kCluster + (k ^ (e & (kCluster - 1))); }
+
 // Stage the chunk [c0, c0 + n) of cluster I's list, then for every listed
-// cluster J its 8 coordinates+charges, 8 types and bounding box, with 16-byte
+// cluster J its 8 coordinates+charges, 8 types and bounding box, with
 // asynchronous copies issued by every thread of the block.
 __device__ __forceinline__ void stage_chunk(const ForceArgs &A, const ForceSmem &S, int I, int c0, int n)
 {
@@ -142,18 +140,17 @@ __device__ __forceinline__ void stage_chunk(const ForceArgs &A, const ForceSmem 
     for (int p = threadIdx.x; p < nent16; p += blockDim.x) cp_async16(reinterpret_cast<uint4 *>(S.ent) + p, src + p);
     cp_async_wait_all();
     __syncthreads();
-    constexpr int kPieces = kCluster + 2 + 2;  // 16-byte pieces per entry: 8 pos, 2 type, 2 bbox
+    constexpr int kPieces = 2 * kCluster + 2;  // per entry: 8 coordinates (16 B), 8 types (4 B), 2 box corners
     for (int p = threadIdx.x; p < kPieces * n; p += blockDim.x) {
         const int e = p / kPieces, sub = p - e * kPieces;
         const long long J = (long long)(S.ent[e] & kJMask);
         if (sub < kCluster) {
-            cp_async16(S.pos + e * kCluster + sub, A.xyzq + J * kCluster + sub);
-        } else if (sub < kCluster + 2) {
-            const int h = sub - kCluster;
-            cp_async16(reinterpret_cast<uint4 *>(S.typ + e * kCluster) + h,
-                       reinterpret_cast<const uint4 *>(A.tslot + J * kCluster) + h);
+            cp_async16(S.pos + swz(e, sub), A.xyzq + J * kCluster + sub);
+        } else if (sub < 2 * kCluster) {
+            const int k = sub - kCluster;
+            cp_async4(S.typ + swz(e, k), A.tslot + J * kCluster + k);
         } else {
-            const int h = sub - kCluster - 2;
+            const int h = sub - 2 * kCluster;
             cp_async16(S.bb + e * 2 + h, A.bb + J * 2 + h);
         }
     }
@@ -166,36 +163,36 @@ struct Acc {
     float w[6];
 };
 
-// One in-range pair from the queue: d = x_j - x_i (exact-shift image), r2 its
-// FP32 squared length, q_j and the type / 1-4 word.
+// One candidate pair: d = x_j - x_i (exact-shift image), r2 its FP32 squared
+// length; the arithmetic is done for every candidate and masked by `in`.
 template <bool EWALD, bool VIRIAL>
 __device__ __forceinline__ void eval_pair(const PairParams &P, const float2 *__restrict__ lj, int ti_row, float qi,
-                                          float4 d, float2 a, Acc &acc)
+                                          bool in, float dx, float dy, float dz, float r2, float qj, int tj,
+                                          bool is14, Acc &acc)
 {
-    const uint32_t wd = __float_as_uint(a.y);
-    const float rinv = rsqrtf(d.w);
-    const float2 ab = lj[ti_row + (int)(wd & 0xFFu)];
+    const float rinv = rsqrtf(r2);
+    const float2 ab = lj[ti_row + tj];
     float elj, frlj, ec, frc;
-    pair_radial<EWALD, true>(P, d.w, rinv, ab.x, ab.y, qi * a.x, elj, frlj, ec, frc);
-    const bool is14 = (wd & kW14) != 0u;
+    pair_radial<EWALD, true>(P, r2, rinv, ab.x, ab.y, qi * qj, elj, frlj, ec, frc);
     const float wlj = is14 ? P.s14_lj : 1.0f;
     const float wc = is14 ? P.s14_c : 1.0f;
     // F_i = U'(r) d / r = -fs d with fs = -U'(r) / r
-    const float fs = fmaf(wlj, frlj, wc * frc) * (rinv * rinv);
-    acc.elj = fmaf(wlj, elj, acc.elj);
-    acc.ec = fmaf(wc, ec, acc.ec);
-    const float fdx = fs * d.x, fdy = fs * d.y, fdz = fs * d.z;
+    float fs = fmaf(wlj, frlj, wc * frc) * (rinv * rinv);
+    fs = in ? fs : 0.0f;
+    acc.elj += in ? wlj * elj : 0.0f;
+    acc.ec += in ? wc * ec : 0.0f;
+    const float fdx = fs * dx, fdy = fs * dy, fdz = fs * dz;
     acc.fx -= fdx;
     acc.fy -= fdy;
     acc.fz -= fdz;
     if (VIRIAL) {
         // W_ab += d_ij,a f_ij,b with d_ij = -d and f_ij = -fs d
-        acc.w[0] = fmaf(fdx, d.x, acc.w[0]);
-        acc.w[1] = fmaf(fdy, d.y, acc.w[1]);
-        acc.w[2] = fmaf(fdz, d.z, acc.w[2]);
-        acc.w[3] = fmaf(fdx, d.y, acc.w[3]);
-        acc.w[4] = fmaf(fdx, d.z, acc.w[4]);
-        acc.w[5] = fmaf(fdy, d.z, acc.w[5]);
+        acc.w[0] = fmaf(fdx, dx, acc.w[0]);
+        acc.w[1] = fmaf(fdy, dy, acc.w[1]);
+        acc.w[2] = fmaf(fdz, dz, acc.w[2]);
+        acc.w[3] = fmaf(fdx, dy, acc.w[3]);
+        acc.w[4] = fmaf(fdx, dz, acc.w[4]);
+        acc.w[5] = fmaf(fdy, dz, acc.w[5]);
     }
 }
 
@@ -244,7 +241,7 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
         const float Lx = SD.L[0], Ly = SD.L[1], Lz = SD.L[2];
         const int islot = I * kCluster + w;
         const float4 pi = A.xyzq[islot];
-        const bool iv = pi.x == pi.x;
+        const bool iv = is_real_coord(pi.x);
         const int ti_row = A.tslot[islot] * T;
         const float xi = pi.x, yi = pi.y, zi = pi.z;
         const float xim = __fsub_rn(xi, Lx), yim = __fsub_rn(yi, Ly), zim = __fsub_rn(zi, Lz);
@@ -255,7 +252,6 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
         acc.fx = acc.fy = acc.fz = acc.elj = acc.ec = 0.0f;
 #pragma unroll
         for (int k = 0; k < 6; ++k) acc.w[k] = 0.0f;
-        int nq = 0;
         const int nE = A.list_n[I];
 
         for (int c0 = 0; c0 < nE; c0 += A.scap) {
@@ -286,68 +282,57 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
                 ns += __popc(b);
             }
             __syncwarp();
-            // (2) exact membership test of the survivors' atoms, 4 clusters x 8 atoms per step
-            for (int s0 = 0; s0 < ns; s0 += 4) {
-                const int si = s0 + (lane >> 3);
+            // (2) one surviving cluster per lane, its 8 atoms in turn
+            for (int s0 = 0; s0 < ns; s0 += 32) {
+                const int si = s0 + lane;
                 const bool sv = si < ns;
                 const int e = sv ? (int)S.surv[si] : 0;
-                const int k = lane & 7;
                 const uint32_t ent = S.ent[e];
-                const float4 pj = S.pos[e * kCluster + k];
-                const int tj = S.typ[e * kCluster + k];
+                const int J = (int)(ent & kJMask);
                 const int cx = (ent >> kShiftBit) & 3, cy = (ent >> (kShiftBit + 2)) & 3,
                           cz = (ent >> (kShiftBit + 4)) & 3;
-                const float xj = cx == 1 ? __fsub_rn(pj.x, Lx) : pj.x;
-                const float yj = cy == 1 ? __fsub_rn(pj.y, Ly) : pj.y;
-                const float zj = cz == 1 ? __fsub_rn(pj.z, Lz) : pj.z;
-                float dx, dy, dz;
-                const float r2 = disp_r2(xj, yj, zj, cx == 2 ? xim : xi, cy == 2 ? yim : yi, cz == 2 ? zim : zi,
-                                         dx, dy, dz);
-                bool in = sv && (r2 < A.P.rc2);  // NaN padding fails
-                const int jslot = (int)(ent & kJMask) * kCluster + k;
-                if (jslot == islot && ((ent >> kShiftBit) & 0x3Fu) == 0u) in = false;
-                uint32_t word = (uint32_t)tj;
+                // j-side image: x_j - L (exact for j in the upper half); i-side: x_i - L
+                const float sx = cx == 1 ? Lx : 0.0f, sy = cy == 1 ? Ly : 0.0f, sz = cz == 1 ? Lz : 0.0f;
+                const float ax = cx == 2 ? xim : xi, ay = cy == 2 ? yim : yi, az = cz == 2 ? zim : zi;
+                uint32_t exm = sv ? 0u : 0xFFu, m14 = 0u;
+                if (J == I && ((ent >> kShiftBit) & 0x3Fu) == 0u) exm |= 1u << w;  // i == j
                 const bool fl = sv && (ent & kExclFlag) != 0u;
-                if (__any_sync(kFull, fl && in)) {
+                if (__any_sync(kFull, fl)) {
                     for (int m = 0; m < A.K; ++m) {
                         const int pv = __shfl_sync(kFull, pe, m);
-                        if (fl && pv >= 0 && (pv >> 1) == jslot) {
-                            if (pv & 1) word |= kW14;
-                            else in = false;
+                        if (fl && pv >= 0 && ((pv >> 1) >> 3) == J) {
+                            const uint32_t b = 1u << ((pv >> 1) & (kCluster - 1));
+                            if (pv & 1) m14 |= b;
+                            else exm |= b;
                         }
                     }
                 }
-                if (DEBUG && in) {
-                    atomicAdd((unsigned long long *)&A.dbg_n[0], 1ull);
-                    const int jorig = A.perm[jslot];
-                    if (iorig < jorig) {
-                        const long long q = (long long)atomicAdd((unsigned long long *)&A.dbg_n[1], 1ull);
-                        if (q < A.dbg_cap) {
-                            A.dbg_ij[2 * q] = iorig;
-                            A.dbg_ij[2 * q + 1] = jorig;
+#pragma unroll 2
+                for (int k = 0; k < kCluster; ++k) {
+                    const int idx = swz(e, k);
+                    const float4 pj = S.pos[idx];
+                    const int tj = S.typ[idx];
+                    float dx, dy, dz;
+                    const float r2 = disp_r2(__fsub_rn(pj.x, sx), __fsub_rn(pj.y, sy), __fsub_rn(pj.z, sz), ax, ay,
+                                             az, dx, dy, dz);
+                    const bool in = (r2 < A.P.rc2) && !((exm >> k) & 1u);
+                    if (DEBUG && in) {
+                        atomicAdd((unsigned long long *)&A.dbg_n[0], 1ull);
+                        const int jorig = A.perm[J * kCluster + k];
+                        if (iorig < jorig) {
+                            const long long q = (long long)atomicAdd((unsigned long long *)&A.dbg_n[1], 1ull);
+                            if (q < A.dbg_cap) {
+                                A.dbg_ij[2 * q] = iorig;
+                                A.dbg_ij[2 * q + 1] = jorig;
+                            }
                         }
                     }
-                }
-                const unsigned b = __ballot_sync(kFull, in);
-                if (in) {
-                    const int p = nq + __popc(b & lt);
-                    S.qd[p] = make_float4(dx, dy, dz, r2);
-                    S.qa[p] = make_float2(pj.w, __uint_as_float(word));
-                }
-                nq += __popc(b);
-                __syncwarp();
-                if (nq >= 32) {
-                    // (3) one full step: the top 32 queue entries, one per lane
-                    const int e2 = nq - 32 + lane;
-                    eval_pair<EWALD, VIRIAL>(A.P, S.lj, ti_row, qi, S.qd[e2], S.qa[e2], acc);
-                    nq -= 32;
-                    __syncwarp();
+                    eval_pair<EWALD, VIRIAL>(A.P, S.lj, ti_row, qi, in, dx, dy, dz, r2, pj.w, tj,
+                                             ((m14 >> k) & 1u) != 0u, acc);
                 }
             }
         }
         if (!iv) continue;
-        if (lane < nq) eval_pair<EWALD, VIRIAL>(A.P, S.lj, ti_row, qi, S.qd[lane], S.qa[lane], acc);
-        __syncwarp();
         // force of atom i: sum of the 32 lanes in 64-bit fixed point
         long long vx = to_fixed(acc.fx, A.status), vy = to_fixed(acc.fy, A.status), vz = to_fixed(acc.fz, A.status);
 #pragma unroll

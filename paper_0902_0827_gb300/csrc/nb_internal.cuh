@@ -17,6 +17,11 @@ constexpr int kMaxPartners = 16;     // exclusion + 1-4 partners per atom
 constexpr int kErfcDeg = 8;          // degree of the erfcx polynomial in t
 constexpr double kFixScale = 4294967296.0;   // 2^32: fixed-point scale
 constexpr int kTaskVals = 8;         // per task: E_lj, E_c, W[6]
+// Padding slots of the sorted arrays sit at this finite, far-away coordinate:
+// their squared distance to any atom (about 3e36) stays finite and is never
+// inside a cutoff, so masked pair arithmetic needs no further guards.
+constexpr float kPadCoord = -1.0e18f;
+__host__ __device__ inline bool is_real_coord(float x) { return x > -1.0e17f; }
 
 // List entry encoding: J (bits 0..24) | shift codes x,y,z (2 bits each,
 // bits 25..30: 0 none, 1 = j-side shift x_j - L, 2 = i-side shift x_i - L)
@@ -88,7 +93,7 @@ struct DevBuffers {
     int *col_fill = nullptr;         // [C] scatter cursor
     int *col_slot = nullptr;         // [C+1] padded slot offsets
     int *stage = nullptr;            // [S] unsorted atoms per column
-    float4 *xyzq = nullptr;          // [S] sorted x, y, z, q (NaN for padding)
+    float4 *xyzq = nullptr;          // [S] sorted x, y, z, q (kPadCoord for padding)
     int *tslot = nullptr;            // [S] sorted types
     int *perm = nullptr;             // [S] slot -> atom (-1 padding)
     int *inv = nullptr;              // [N] atom -> slot
