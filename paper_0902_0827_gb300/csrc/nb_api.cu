@@ -13,83 +13,15 @@
 #include <vector>
 
 #include "acenb.h"
+#include "nb_host.cuh"
 #include "nb_internal.cuh"
 
 using namespace acenb;
+using namespace acenb::host;
 
 namespace {
 
-constexpr double kDefaultKe = 332.0636;
-
 nb_status cuda_status(cudaError_t e) { return e == cudaSuccess ? NB_OK : (e == cudaErrorMemoryAllocation ? NB_ERR_OOM : NB_ERR_CUDA); }
-
-// Number of x-y columns along one axis: the largest n with n^3 * 8 <= L^3 rho,
-// so a one-cluster slab of a column is about cubic.  Evaluated in FP64 with a
-// fixed operation order (the binning is part of the bit-exact cell contract).
-int column_count(double L, double rho)
-{
-    int n = 1;
-    while (n < 4096 && (double)(n + 1) * (n + 1) * (n + 1) * kCluster <= L * L * L * rho) ++n;
-    return n;
-}
-
-// Least-squares fit of erfcx(x) = exp(x^2) erfc(x) as a degree-kErfcDeg
-// polynomial in t = 1 / (1 + x/2) on x in [0, xmax] (Householder QR on
-// Chebyshev-distributed nodes).  Returns the max absolute error of
-// exp(-x^2) P(t) against erfc(x) on a dense grid.
-double fit_erfcx(double xmax, float *coef)
-{
-    const int m = 96, n = kErfcDeg + 1;
-    const double tmin = 1.0 / (1.0 + 0.5 * xmax);
-    std::vector<double> A(m * n), b(m);
-    for (int i = 0; i < m; ++i) {
-        double c = cos(M_PI * (i + 0.5) / m);
-        double t = 0.5 * (1.0 + tmin) + 0.5 * (1.0 - tmin) * c;
-        double x = 2.0 * (1.0 / t - 1.0);
-        double p = 1.0;
-        for (int k = 0; k < n; ++k) { A[i * n + k] = p; p *= t; }
-        b[i] = erfc(x) * exp(x * x);
-    }
-    // Householder QR: A = Q R, solve R c = Q^T b
-    for (int k = 0; k < n; ++k) {
-        double nrm = 0.0;
-        for (int i = k; i < m; ++i) nrm += A[i * n + k] * A[i * n + k];
-        nrm = sqrt(nrm);
-        double alpha = A[k * n + k] > 0 ? -nrm : nrm;
-        std::vector<double> v(m, 0.0);
-        for (int i = k; i < m; ++i) v[i] = A[i * n + k];
-        v[k] -= alpha;
-        double vn = 0.0;
-        for (int i = k; i < m; ++i) vn += v[i] * v[i];
-        if (vn == 0.0) continue;
-        for (int j = k; j < n; ++j) {
-            double s = 0.0;
-            for (int i = k; i < m; ++i) s += v[i] * A[i * n + j];
-            s = 2.0 * s / vn;
-            for (int i = k; i < m; ++i) A[i * n + j] -= s * v[i];
-        }
-        double s = 0.0;
-        for (int i = k; i < m; ++i) s += v[i] * b[i];
-        s = 2.0 * s / vn;
-        for (int i = k; i < m; ++i) b[i] -= s * v[i];
-    }
-    double c[kErfcDeg + 1];
-    for (int k = n - 1; k >= 0; --k) {
-        double s = b[k];
-        for (int j = k + 1; j < n; ++j) s -= A[k * n + j] * c[j];
-        c[k] = s / A[k * n + k];
-    }
-    for (int k = 0; k < n; ++k) coef[k] = (float)c[k];
-    double err = 0.0;
-    for (int i = 0; i <= 4000; ++i) {
-        double x = xmax * i / 4000.0;
-        double t = 1.0 / (1.0 + 0.5 * x);
-        double p = 0.0;
-        for (int k = n - 1; k >= 0; --k) p = p * t + (double)coef[k];
-        err = std::max(err, fabs(exp(-x * x) * p - erfc(x)));
-    }
-    return err;
-}
 
 template <class T>
 cudaError_t dalloc(T **p, size_t count)
@@ -108,50 +40,6 @@ void free_all(nb_ctx *c)
     for (void *p : ptrs)
         if (p) cudaFree(p);
     d = DevBuffers();
-}
-
-nb_status validate_one(const nb_params *p)
-{
-    if (!p) return NB_ERR_INVALID_ARG;
-    if (p->n_atoms < 1 || p->flags != 0u) return NB_ERR_INVALID_ARG;
-    for (int a = 0; a < 3; ++a)
-        if (!(p->box[a] > 0.0f) || !isfinite(p->box[a])) return NB_ERR_INVALID_ARG;
-    if (!(p->cutoff > 0.0f) || !isfinite(p->cutoff)) return NB_ERR_INVALID_ARG;
-    if (!(p->switch_dist > 0.0f) || !isfinite(p->switch_dist)) return NB_ERR_INVALID_ARG;
-    if (!(p->ewald_alpha >= 0.0f) || !isfinite(p->ewald_alpha)) return NB_ERR_INVALID_ARG;
-    if (!(p->coulomb_k >= 0.0f) || !isfinite(p->coulomb_k)) return NB_ERR_INVALID_ARG;
-    for (int a = 0; a < 3; ++a)
-        if ((double)p->box[a] * 0.5 - (double)p->cutoff < 1e-4 * (double)p->box[a]) return NB_ERR_BOX_TOO_SMALL;
-    if (p->n_types < 1) return NB_ERR_INVALID_ARG;
-    if (p->n_types > kMaxTypes) return NB_ERR_UNSUPPORTED;
-    if (p->comb_rule == 0) {
-        if (!p->sigma || !p->epsilon) return NB_ERR_INVALID_ARG;
-        for (int t = 0; t < p->n_types; ++t)
-            if (!(p->sigma[t] >= 0.0f) || !(p->epsilon[t] >= 0.0f) || !isfinite(p->sigma[t]) || !isfinite(p->epsilon[t]))
-                return NB_ERR_INVALID_ARG;
-    } else if (p->comb_rule == 1) {
-        if (!p->sigma_tab || !p->eps_tab) return NB_ERR_INVALID_ARG;
-        const int T = p->n_types;
-        for (int a = 0; a < T; ++a)
-            for (int b = 0; b < T; ++b) {
-                float s = p->sigma_tab[a * T + b], e = p->eps_tab[a * T + b];
-                if (!(s >= 0.0f) || !(e >= 0.0f) || !isfinite(s) || !isfinite(e)) return NB_ERR_INVALID_ARG;
-                if (s != p->sigma_tab[b * T + a] || e != p->eps_tab[b * T + a]) return NB_ERR_INVALID_ARG;
-            }
-    } else {
-        return NB_ERR_INVALID_ARG;
-    }
-    if (p->n_excl < 0 || p->n_14 < 0) return NB_ERR_INVALID_ARG;
-    if ((p->n_excl > 0 && !p->excl) || (p->n_14 > 0 && !p->pairs14)) return NB_ERR_INVALID_ARG;
-    for (int k = 0; k < p->n_excl; ++k) {
-        int i = p->excl[2 * k], j = p->excl[2 * k + 1];
-        if (i < 0 || j < 0 || i >= p->n_atoms || j >= p->n_atoms || i == j) return NB_ERR_INVALID_ARG;
-    }
-    for (int k = 0; k < p->n_14; ++k) {
-        int i = p->pairs14[2 * k], j = p->pairs14[2 * k + 1];
-        if (i < 0 || j < 0 || i >= p->n_atoms || j >= p->n_atoms || i == j) return NB_ERR_INVALID_ARG;
-    }
-    return NB_OK;
 }
 
 bool same_shared(const nb_params &a, const nb_params &b)
@@ -213,32 +101,6 @@ nb_status allocate(nb_ctx *c)
     return cuda_status(e);
 }
 
-// (A, B) = (4 eps sig^12, 4 eps sig^6) per type pair, from per-type
-// Lorentz-Berthelot parameters (comb_rule 0) or explicit pair tables.
-void make_tables(int T, int comb_rule, const float *sigma, const float *eps, const float *sig_tab,
-                 const float *eps_tab, std::vector<double> &sg_out, std::vector<double> &ep_out,
-                 std::vector<float2> &lj)
-{
-    sg_out.assign((size_t)T * T, 0.0);
-    ep_out.assign((size_t)T * T, 0.0);
-    lj.resize((size_t)T * T);
-    for (int a = 0; a < T; ++a)
-        for (int b = 0; b < T; ++b) {
-            double sg, ep;
-            if (comb_rule == 0) {
-                sg = 0.5 * ((double)sigma[a] + (double)sigma[b]);
-                ep = sqrt((double)eps[a] * (double)eps[b]);
-            } else {
-                sg = sig_tab[a * T + b];
-                ep = eps_tab[a * T + b];
-            }
-            sg_out[a * T + b] = sg;
-            ep_out[a * T + b] = ep;
-            double s6 = sg * sg * sg * sg * sg * sg;
-            lj[a * T + b] = make_float2((float)(4.0 * ep * s6 * s6), (float)(4.0 * ep * s6));
-        }
-}
-
 }  // namespace
 
 extern "C" {
@@ -288,42 +150,15 @@ nb_status nb_create_batch(int32_t n_sys, const nb_params *params, void *cuda_str
     const nb_params &P0 = params[0];
     const int T = P0.n_types;
     // type-pair tables in FP64, then (A, B) in FP32
-    std::vector<float2> lj;
-    make_tables(T, P0.comb_rule, P0.sigma, P0.epsilon, P0.sigma_tab, P0.eps_tab, c->sig_tab, c->eps_tab, lj);
+    std::vector<float2> lj((size_t)T * T);
+    c->sig_tab.assign((size_t)T * T, 0.0);
+    c->eps_tab.assign((size_t)T * T, 0.0);
+    make_tables(T, P0.comb_rule, P0.sigma, P0.epsilon, P0.sigma_tab, P0.eps_tab, c->sig_tab.data(),
+                c->eps_tab.data(), lj.data());
     c->comb_rule = P0.comb_rule;
-    // pair constants
-    PairParams &pp = c->pp;
-    const float rc = P0.cutoff, rs = P0.switch_dist;
-    pp.rc = rc;
-    pp.rc2 = rc * rc;
-    pp.switched = rs < rc;
-    if (pp.switched) {
-        pp.rs2 = rs * rs;
-        double rc2 = (double)pp.rc2, rs2 = (double)pp.rs2;
-        pp.sw_c0 = (float)(rc2 - 3.0 * rs2);
-        pp.sw_inv = (float)(1.0 / ((rc2 - rs2) * (rc2 - rs2) * (rc2 - rs2)));
-    } else {
-        pp.rs2 = pp.rc2;  // r2 > rs2 never holds inside the cutoff
-        pp.sw_c0 = 0.0f;
-        pp.sw_inv = 0.0f;
-    }
-    pp.ke = P0.coulomb_k > 0.0f ? P0.coulomb_k : (float)kDefaultKe;
-    pp.alpha = P0.ewald_alpha;
-    pp.ewald = P0.ewald_alpha > 0.0f;
-    pp.alpha_half = 0.5f * P0.ewald_alpha;
-    pp.neg_a2_log2e = (float)(-(double)P0.ewald_alpha * (double)P0.ewald_alpha * 1.4426950408889634);
-    pp.two_a_sqpi = (float)(2.0 * (double)P0.ewald_alpha / sqrt(M_PI));
-    pp.s14_lj = P0.scale14_lj;
-    pp.s14_c = P0.scale14_coul;
-    pp.n_types = T;
-    pp.list_margin = 2e-3f;
-    pp.rcm2 = (rc + pp.list_margin) * (rc + pp.list_margin);
-    if (pp.ewald) {
-        double err = fit_erfcx((double)P0.ewald_alpha * (double)rc, pp.erfc_c);
-        if (!(err < 2e-7)) {
-            delete c;
-            return NB_ERR_UNSUPPORTED;
-        }
+    if (init_pair_params(P0, c->pp) != NB_OK) {
+        delete c;
+        return NB_ERR_UNSUPPORTED;
     }
     // systems, columns
     c->sys_h.resize(n_sys);
@@ -332,21 +167,7 @@ nb_status nb_create_batch(int32_t n_sys, const nb_params *params, void *cuda_str
     for (int s = 0; s < n_sys; ++s) {
         const nb_params &p = params[s];
         SysDesc &S = c->sys_h[s];
-        memset(&S, 0, sizeof(S));
-        double rho = (double)p.n_atoms / ((double)p.box[0] * (double)p.box[1] * (double)p.box[2]);
-        S.nx = column_count((double)p.box[0], rho);
-        S.ny = column_count((double)p.box[1], rho);
-        for (int a = 0; a < 3; ++a) {
-            S.L[a] = p.box[a];
-            S.half[a] = 0.5f * p.box[a];
-        }
-        S.inv_w[0] = (float)((double)S.nx / (double)p.box[0]);
-        S.inv_w[1] = (float)((double)S.ny / (double)p.box[1]);
-        S.w[0] = (float)((double)p.box[0] / S.nx);
-        S.w[1] = (float)((double)p.box[1] / S.ny);
-        S.atom_begin = atom;
-        S.n_atoms = p.n_atoms;
-        S.col_begin = col;
+        init_sysdesc(p, S, atom, col);
         for (int a = 0; a < p.n_atoms; ++a) atom_sys[atom + a] = s;
         for (int k = 0; k < S.nx * S.ny; ++k) col_sys.push_back(s);
         atom += p.n_atoms;
@@ -469,8 +290,9 @@ nb_status nb_set_lj_params(nb_ctx *ctx, const float *h_sigma, const float *h_eps
         for (int k = 0; k < T * T; ++k)
             if (!(h_sigma_tab[k] >= 0.0f) || !(h_eps_tab[k] >= 0.0f)) return NB_ERR_INVALID_ARG;
     }
-    std::vector<float2> lj;
-    make_tables(T, ctx->comb_rule, h_sigma, h_epsilon, h_sigma_tab, h_eps_tab, ctx->sig_tab, ctx->eps_tab, lj);
+    std::vector<float2> lj((size_t)T * T);
+    make_tables(T, ctx->comb_rule, h_sigma, h_epsilon, h_sigma_tab, h_eps_tab, ctx->sig_tab.data(),
+                ctx->eps_tab.data(), lj.data());
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return NB_ERR_CUDA;
     if (cudaMemcpy(ctx->d.lj_tab, lj.data(), sizeof(float2) * lj.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         return NB_ERR_CUDA;
