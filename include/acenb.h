@@ -68,7 +68,8 @@ typedef enum {
     NB_ERR_TIMEOUT = 8,       /* a bounded device-side wait gave up */
     NB_ERR_NONFINITE = 9,     /* a coordinate is NaN or infinite */
     NB_ERR_CAPACITY = 10,     /* a per-cluster neighbour list exceeded its capacity */
-    NB_ERR_UNSUPPORTED = 11   /* parameters outside the supported range */
+    NB_ERR_UNSUPPORTED = 11,  /* parameters outside the supported range */
+    NB_ERR_TOO_LARGE = 12     /* system larger than nb_forces_noalloc's fixed scratch */
 } nb_status;
 
 typedef struct nb_ctx nb_ctx;
@@ -205,6 +206,32 @@ nb_status nb_debug_pairs(nb_ctx *ctx, int32_t *h_ij, int64_t cap, int64_t *n, in
  * of recorded launches of the force kernel, and clears the record. */
 nb_status nb_set_profiling(nb_ctx *ctx, int32_t on);
 nb_status nb_get_profile(nb_ctx *ctx, double *force_ms, int64_t *launches);
+
+/* nb_forces_noalloc - forces, energies and virial of ONE system for callers
+ * that cannot allocate device memory (for example a host application whose
+ * device memory all comes from its own pool, or a plug-in that may not call
+ * cudaMalloc after start-up).  The paper has no counterpart: this is an
+ * interface convenience around the same binning and force kernels as
+ * nb_build_cells + nb_forces.
+ *   params   as for nb_create (one system);
+ *   d_pos, d_q, d_type, d_F, d_energy [2], d_virial [6]: as for nb_forces
+ *            (d_energy / d_virial may be NULL);
+ *   cuda_stream: the stream the work runs on.
+ * All scratch lives in one static device array of about 4.4 MiB that every
+ * GPU loading this library holds until the library is unloaded; it bounds
+ * the system to NB_NOALLOC_MAX_ATOMS atoms and NB_NOALLOC_MAX_COLUMNS x-y
+ * columns (NB_ERR_TOO_LARGE otherwise).  The call allocates nothing (no
+ * cudaMalloc, no cudaFree, no host heap).  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  The call
+ * synchronises its stream and returns device-detected errors itself.  Every
+ * call reuses the same array: calls that overlap on the GPU, or run from
+ * several host threads at once, race and must be serialised by the caller. */
+#define NB_NOALLOC_MAX_ATOMS 4096
+#define NB_NOALLOC_MAX_COLUMNS 1024
+nb_status nb_forces_noalloc(const nb_params *params, const float *d_pos, const float *d_q,
+                            const int32_t *d_type, float *d_F, double *d_energy, double *d_virial,
+                            void *cuda_stream);
 
 /* nb_status_string - static description of a status code. */
 const char *nb_status_string(nb_status s);

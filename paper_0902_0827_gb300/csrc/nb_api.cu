@@ -120,6 +120,7 @@ const char *nb_status_string(nb_status s)
     case NB_ERR_NONFINITE: return "non-finite coordinate";
     case NB_ERR_CAPACITY: return "cluster-pair list capacity exceeded";
     case NB_ERR_UNSUPPORTED: return "unsupported parameters";
+    case NB_ERR_TOO_LARGE: return "system exceeds the fixed scratch of nb_forces_noalloc";
     }
     return "unknown status";
 }

@@ -19,12 +19,13 @@ NB_OK = 0
 STATUS_NAMES = {
     0: "NB_OK", 1: "NB_ERR_INVALID_ARG", 2: "NB_ERR_BOX_TOO_SMALL", 3: "NB_ERR_CUDA", 4: "NB_ERR_OOM",
     5: "NB_ERR_NOT_BUILT", 6: "NB_ERR_OVERFLOW", 7: "NB_ERR_LIST_STALE", 8: "NB_ERR_TIMEOUT",
-    9: "NB_ERR_NONFINITE", 10: "NB_ERR_CAPACITY", 11: "NB_ERR_UNSUPPORTED",
+    9: "NB_ERR_NONFINITE", 10: "NB_ERR_CAPACITY", 11: "NB_ERR_UNSUPPORTED", 12: "NB_ERR_TOO_LARGE",
 }
 # every symbol include/acenb.h declares
 EXPORTS = ("nb_create", "nb_create_batch", "nb_build_cells", "nb_forces", "nb_backward", "nb_get_status",
            "nb_set_stream", "nb_destroy", "nb_set_tuning", "nb_get_tuning", "nb_get_sizes", "nb_debug_cells",
-           "nb_debug_pairs", "nb_status_string", "nb_set_lj_params", "nb_set_profiling", "nb_get_profile")
+           "nb_debug_pairs", "nb_status_string", "nb_set_lj_params", "nb_set_profiling", "nb_get_profile",
+           "nb_forces_noalloc")
 
 
 class NbError(RuntimeError):
@@ -87,6 +88,7 @@ def lib(build_if_missing: bool = True):
             "nb_set_lj_params": ([P, P, P, P, P], ctypes.c_int),
             "nb_set_profiling": ([P, I32], ctypes.c_int),
             "nb_get_profile": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64)], ctypes.c_int),
+            "nb_forces_noalloc": ([ctypes.POINTER(nb_params), P, P, P, P, P, P, P], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -127,6 +129,41 @@ def _stream_handle():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
+def make_params(systems):
+    """nb_params array for a list of systems plus the host arrays it points to
+    (keep them alive until the library has copied them)."""
+    keep = []
+    arr = (nb_params * len(systems))()
+    for k, s in enumerate(systems):
+        sig, eps = _f32(s.sigma), _f32(s.epsilon)
+        ex, p14 = _i32(s.excl).reshape(-1, 2), _i32(s.pairs14).reshape(-1, 2)
+        keep += [sig, eps, ex, p14]
+        p = arr[k]
+        p.n_atoms = int(s.n_atoms)
+        for a in range(3):
+            p.box[a] = float(s.box[a])
+        p.cutoff, p.switch_dist = float(s.cutoff), float(s.switch_dist)
+        p.ewald_alpha, p.coulomb_k = float(s.ewald_alpha), float(s.coulomb_k)
+        p.n_types = int(sig.shape[0])
+        p.sigma, p.epsilon = _ptr(sig), _ptr(eps)
+        p.comb_rule = 0
+        p.n_excl, p.excl = int(ex.shape[0]), _ptr(ex)
+        p.n_14, p.pairs14 = int(p14.shape[0]), _ptr(p14)
+        p.scale14_lj, p.scale14_coul = float(s.scale14_lj), float(s.scale14_coul)
+        p.flags = 0
+    return arr, keep
+
+
+def forces_noalloc(system, pos, q, typ, F, energy=None, virial=None):
+    """nb_forces_noalloc: one small system, no device allocation by the library
+    (scratch in its static device array).  Outputs are caller-owned tensors."""
+    arr, keep = make_params([system])
+    code = lib().nb_forces_noalloc(arr, _tptr(pos), _tptr(q), _tptr(typ), _tptr(F), _tptr(energy),
+                                   _tptr(virial), _stream_handle())
+    del keep
+    _check(code, "nb_forces_noalloc")
+
+
 class Nonbonded:
     """One context of the library: a single system or a batch of systems.
 
@@ -141,25 +178,7 @@ class Nonbonded:
         L = lib()
         single = not isinstance(systems, (list, tuple))
         self.systems = [systems] if single else list(systems)
-        self._keep = []
-        arr = (nb_params * len(self.systems))()
-        for k, s in enumerate(self.systems):
-            sig, eps = _f32(s.sigma), _f32(s.epsilon)
-            ex, p14 = _i32(s.excl).reshape(-1, 2), _i32(s.pairs14).reshape(-1, 2)
-            self._keep += [sig, eps, ex, p14]
-            p = arr[k]
-            p.n_atoms = int(s.n_atoms)
-            for a in range(3):
-                p.box[a] = float(s.box[a])
-            p.cutoff, p.switch_dist = float(s.cutoff), float(s.switch_dist)
-            p.ewald_alpha, p.coulomb_k = float(s.ewald_alpha), float(s.coulomb_k)
-            p.n_types = int(sig.shape[0])
-            p.sigma, p.epsilon = _ptr(sig), _ptr(eps)
-            p.comb_rule = 0
-            p.n_excl, p.excl = int(ex.shape[0]), _ptr(ex)
-            p.n_14, p.pairs14 = int(p14.shape[0]), _ptr(p14)
-            p.scale14_lj, p.scale14_coul = float(s.scale14_lj), float(s.scale14_coul)
-            p.flags = 0
+        arr, self._keep = make_params(self.systems)
         h = ctypes.c_void_p()
         st = stream if stream is not None else _stream_handle()
         _check(L.nb_create_batch(len(self.systems), arr, st, ctypes.byref(h)), "nb_create_batch")

@@ -33,7 +33,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_status_strings():
     L = nb.lib()
-    for code in range(12):
+    for code in range(13):
         s = L.nb_status_string(code)
         assert isinstance(s, bytes) and len(s) > 0
 
