@@ -170,7 +170,7 @@ __device__ __forceinline__ void eval_pair(const PairParams &P, const float2 *__r
                                           bool in, float dx, float dy, float dz, float r2, float qj, int tj,
                                           bool is14, Acc &acc)
 {
-    const float rinv = rsqrtf(r2);
+    const float rinv = fast_rsqrt(r2);
     const float2 ab = lj[ti_row + tj];
     float elj, frlj, ec, frc;
     pair_radial<EWALD, true>(P, r2, rinv, ab.x, ab.y, qi * qj, elj, frlj, ec, frc);
