@@ -7,17 +7,20 @@
 // GB300 work decomposition (the paper's one-cell-per-block staging of the
 // neighbour cells in shared memory, re-cut for this machine):
 //   block = one 8-atom cluster I at a time (persistent grid of blocks);
-//   warp  = one i atom of I;
-//   lane  = one candidate cluster J (its 8 atoms evaluated in turn).
+//   warp  = one i atom of I.
 // For each cluster the block stages I's cluster-pair list and, for every
 // listed cluster J, its 8 coordinates+charges, 8 types and bounding box into
 // shared memory with asynchronous copies (cp.async) issued by all threads;
 // coordinates and types are swizzled by J so that lanes reading the same atom
-// slot of different clusters hit different banks.  Each warp prunes the
-// staged clusters whose bounding box lies beyond the cutoff of its own atom,
-// then evaluates the surviving clusters one per lane with the exact FP32
-// membership predicate as the mask of the pair arithmetic (exclusions and the
-// i == j case masked too, the paper's "inner" test, only for flagged clusters).
+// slot of different clusters hit different banks.  Each warp then
+//   (1) prunes the staged clusters whose bounding box lies beyond the cutoff
+//       of its own atom;
+//   (2) membership: one surviving cluster per lane, its 8 atoms tested with
+//       the exact FP32 predicate (exclusions and the i == j case removed, the
+//       paper's "inner" test, only for flagged clusters) into an 8-bit mask;
+//   (3) compaction: a warp scan of the mask counts places every in-range
+//       (cluster, atom) item into a per-warp ring in shared memory;
+//   (4) compute: full 32-pair steps of the ring, one pair per lane, FP32.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -28,6 +31,7 @@
 namespace acenb {
 
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kRing = 512;  // per-warp ring of in-range (cluster, atom) items
 
 struct ForceArgs {
     const SysDesc *sys;
@@ -70,6 +74,7 @@ struct ForceSmem {
     int *typ;
     float4 *bb;
     uint16_t *surv;
+    uint32_t *ring;
     unsigned long long *cacc;
 };
 
@@ -88,6 +93,7 @@ __host__ __device__ inline size_t force_smem_bytes(int T, int scap, int nwarps)
     b += (size_t)scap * kCluster * 4;
     b += (size_t)scap * 2 * 16;
     b += align16((size_t)nwarps * scap * 2);
+    b += (size_t)nwarps * kRing * 4;
     b += kTaskVals * 8;
     return b;
 }
@@ -108,6 +114,8 @@ __device__ __forceinline__ ForceSmem carve(unsigned char *smem, int T, int scap,
     off += (size_t)scap * 2 * 16;
     S.surv = reinterpret_cast<uint16_t *>(smem + off) + (size_t)w * scap;
     off += align16((size_t)nwarps * scap * 2);
+    S.ring = reinterpret_cast<uint32_t *>(smem + off) + (size_t)w * kRing;
+    off += (size_t)nwarps * kRing * 4;
     S.cacc = reinterpret_cast<unsigned long long *>(smem + off);
     return S;
 }
@@ -196,6 +204,39 @@ __device__ __forceinline__ void eval_pair(const PairParams &P, const float2 *__r
     }
 }
 
+// One ring item: staged cluster e, atom k, 1-4 flag.  The displacement is
+// recomputed with the same operations as the membership test (same value).
+template <bool EWALD, bool VIRIAL, bool DEBUG>
+__device__ __forceinline__ void eval_item(const ForceArgs &A, const ForceSmem &S, int I, float Lx, float Ly, float Lz,
+                                          float xi, float yi, float zi, float xim, float yim, float zim, float qi,
+                                          int ti_row, int iorig, uint32_t item, bool active, Acc &acc)
+{
+    const int e = (int)(item >> 4), k = (int)((item >> 1) & 7u);
+    const uint32_t ent = S.ent[e];
+    const int cx = (ent >> kShiftBit) & 3, cy = (ent >> (kShiftBit + 2)) & 3, cz = (ent >> (kShiftBit + 4)) & 3;
+    const float sx = cx == 1 ? Lx : 0.0f, sy = cy == 1 ? Ly : 0.0f, sz = cz == 1 ? Lz : 0.0f;
+    const float ax = cx == 2 ? xim : xi, ay = cy == 2 ? yim : yi, az = cz == 2 ? zim : zi;
+    const int idx = swz(e, k);
+    const float4 pj = S.pos[idx];
+    const int tj = S.typ[idx];
+    float dx, dy, dz;
+    const float r2 =
+        disp_r2(__fsub_rn(pj.x, sx), __fsub_rn(pj.y, sy), __fsub_rn(pj.z, sz), ax, ay, az, dx, dy, dz);
+    if (DEBUG && active) {
+        atomicAdd((unsigned long long *)&A.dbg_n[0], 1ull);
+        const int jorig = A.perm[(int)(ent & kJMask) * kCluster + k];
+        if (iorig < jorig) {
+            const long long q = (long long)atomicAdd((unsigned long long *)&A.dbg_n[1], 1ull);
+            if (q < A.dbg_cap) {
+                A.dbg_ij[2 * q] = iorig;
+                A.dbg_ij[2 * q + 1] = jorig;
+            }
+        }
+    }
+    eval_pair<EWALD, VIRIAL>(A.P, S.lj, ti_row, qi, active, dx, dy, dz, active ? r2 : 1.0f, pj.w, tj,
+                             (item & 1u) != 0u, acc);
+}
+
 template <bool EWALD, bool VIRIAL, bool DEBUG>
 __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
 {
@@ -282,7 +323,9 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
                 ns += __popc(b);
             }
             __syncwarp();
-            // (2) one surviving cluster per lane, its 8 atoms in turn
+            // (2) membership: one surviving cluster per lane -> 8-bit mask
+            // (3) compaction into the ring, (4) full 32-pair compute steps
+            int head = 0, tail = 0;
             for (int s0 = 0; s0 < ns; s0 += 32) {
                 const int si = s0 + lane;
                 const bool sv = si < ns;
@@ -291,7 +334,6 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
                 const int J = (int)(ent & kJMask);
                 const int cx = (ent >> kShiftBit) & 3, cy = (ent >> (kShiftBit + 2)) & 3,
                           cz = (ent >> (kShiftBit + 4)) & 3;
-                // j-side image: x_j - L (exact for j in the upper half); i-side: x_i - L
                 const float sx = cx == 1 ? Lx : 0.0f, sy = cy == 1 ? Ly : 0.0f, sz = cz == 1 ? Lz : 0.0f;
                 const float ax = cx == 2 ? xim : xi, ay = cy == 2 ? yim : yi, az = cz == 2 ? zim : zi;
                 uint32_t exm = sv ? 0u : 0xFFu, m14 = 0u;
@@ -307,30 +349,52 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
                         }
                     }
                 }
-#pragma unroll 2
+                uint32_t mask = 0u;
+                const int sw = e & (kCluster - 1);
+#pragma unroll
                 for (int k = 0; k < kCluster; ++k) {
-                    const int idx = swz(e, k);
-                    const float4 pj = S.pos[idx];
-                    const int tj = S.typ[idx];
+                    const float4 pj = S.pos[e * kCluster + (k ^ sw)];
                     float dx, dy, dz;
                     const float r2 = disp_r2(__fsub_rn(pj.x, sx), __fsub_rn(pj.y, sy), __fsub_rn(pj.z, sz), ax, ay,
                                              az, dx, dy, dz);
-                    const bool in = (r2 < A.P.rc2) && !((exm >> k) & 1u);
-                    if (DEBUG && in) {
-                        atomicAdd((unsigned long long *)&A.dbg_n[0], 1ull);
-                        const int jorig = A.perm[J * kCluster + k];
-                        if (iorig < jorig) {
-                            const long long q = (long long)atomicAdd((unsigned long long *)&A.dbg_n[1], 1ull);
-                            if (q < A.dbg_cap) {
-                                A.dbg_ij[2 * q] = iorig;
-                                A.dbg_ij[2 * q + 1] = jorig;
-                            }
-                        }
-                    }
-                    eval_pair<EWALD, VIRIAL>(A.P, S.lj, ti_row, qi, in, dx, dy, dz, r2, pj.w, tj,
-                                             ((m14 >> k) & 1u) != 0u, acc);
+                    mask |= (r2 < A.P.rc2) ? (1u << k) : 0u;
                 }
+                mask &= ~exm;
+                // exclusive scan of the per-lane counts
+                const int cnt = __popc(mask);
+                int incl = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(kFull, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const int total = __shfl_sync(kFull, incl, 31);
+                int pos = tail + incl - cnt;
+                uint32_t mm = mask;
+#pragma unroll
+                for (int m = 0; m < kCluster; ++m) {
+                    if (mm) {
+                        const int k = __ffs(mm) - 1;
+                        mm &= mm - 1u;
+                        S.ring[(pos++) & (kRing - 1)] = ((uint32_t)e << 4) | ((uint32_t)k << 1) | ((m14 >> k) & 1u);
+                    }
+                }
+                tail += total;
+                __syncwarp();
+                while (tail - head >= 32) {
+                    eval_item<EWALD, VIRIAL, DEBUG>(A, S, I, Lx, Ly, Lz, xi, yi, zi, xim, yim, zim, qi, ti_row, iorig,
+                                                    S.ring[(head + lane) & (kRing - 1)], true, acc);
+                    head += 32;
+                }
+                __syncwarp();
             }
+            if (tail > head) {  // partial step before the staged data is replaced
+                const int n = tail - head;
+                const uint32_t item = lane < n ? S.ring[(head + lane) & (kRing - 1)] : 0u;
+                eval_item<EWALD, VIRIAL, DEBUG>(A, S, I, Lx, Ly, Lz, xi, yi, zi, xim, yim, zim, qi, ti_row, iorig,
+                                                item, lane < n, acc);
+            }
+            __syncwarp();
         }
         if (!iv) continue;
         // force of atom i: sum of the 32 lanes in 64-bit fixed point
