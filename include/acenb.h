@@ -161,6 +161,16 @@ nb_status nb_backward(nb_ctx *ctx, const float *d_pos, const float *d_q, const i
 nb_status nb_set_lj_params(nb_ctx *ctx, const float *h_sigma, const float *h_epsilon,
                            const float *h_sigma_tab, const float *h_eps_tab);
 
+/* nb_type_gradients - per-type gradients from the type-pair gradients of
+ * nb_backward under the Lorentz-Berthelot rule (comb_rule 0):
+ *   dL/dsig_t = sum_{b != t} dL/dsig_tb / 2 + dL/dsig_tt,
+ *   dL/deps_t = sum_{b != t} dL/deps_tb * eps_b / (2 sqrt(eps_t eps_b)) + dL/deps_tt
+ * (NaN for a type with eps_t = 0, where sqrt(eps_t eps_b) has no derivative).
+ *   d_dLdsig_tab, d_dLdeps_tab [T*T] FP64 device inputs; d_dLdsigma, d_dLdeps
+ *   [T] FP64 device outputs.  Asynchronous.  NB_ERR_UNSUPPORTED for comb_rule 1. */
+nb_status nb_type_gradients(nb_ctx *ctx, const double *d_dLdsig_tab, const double *d_dLdeps_tab,
+                            double *d_dLdsigma, double *d_dLdeps);
+
 /* nb_get_status - synchronise the context's stream, return the first
  * recorded device error (or NB_OK) and clear it. */
 nb_status nb_get_status(nb_ctx *ctx);

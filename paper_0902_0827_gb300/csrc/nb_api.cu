@@ -36,7 +36,7 @@ void free_all(nb_ctx *c)
     void *ptrs[] = {d.sys, d.atom_sys, d.atom_col, d.wpos, d.part_orig, d.col_sys, d.col_count, d.col_fill,
                     d.col_slot, d.stage, d.xyzq, d.tslot, d.perm, d.inv, d.ex_slot, d.bb,
                     d.clus_sys, d.list, d.list_n, d.sys_acc, d.tab_grad, d.counts, d.status, d.lj_tab,
-                    d.dbg_n, d.dbg_ij, d.scratch_f, d.scratch_g};
+                    d.dbg_n, d.dbg_ij, d.scratch_f, d.scratch_g, d.lj_d, d.gslot, d.eps_type};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     d = DevBuffers();
@@ -91,6 +91,9 @@ nb_status allocate(nb_ctx *c)
     ALLOC(d.counts, 4);
     ALLOC(d.status, 1);
     ALLOC(d.lj_tab, (int64_t)T * T);
+    ALLOC(d.lj_d, (int64_t)T * T);
+    ALLOC(d.gslot, S);
+    ALLOC(d.eps_type, T);
     ALLOC(d.dbg_n, 2);
 #undef ALLOC
     if (e != cudaSuccess) return cuda_status(e);
@@ -152,10 +155,11 @@ nb_status nb_create_batch(int32_t n_sys, const nb_params *params, void *cuda_str
     const int T = P0.n_types;
     // type-pair tables in FP64, then (A, B) in FP32
     std::vector<float2> lj((size_t)T * T);
+    std::vector<float4> ljd((size_t)T * T);
     c->sig_tab.assign((size_t)T * T, 0.0);
     c->eps_tab.assign((size_t)T * T, 0.0);
     make_tables(T, P0.comb_rule, P0.sigma, P0.epsilon, P0.sigma_tab, P0.eps_tab, c->sig_tab.data(),
-                c->eps_tab.data(), lj.data());
+                c->eps_tab.data(), lj.data(), ljd.data());
     c->comb_rule = P0.comb_rule;
     if (init_pair_params(P0, c->pp) != NB_OK) {
         delete c;
@@ -231,6 +235,9 @@ nb_status nb_create_batch(int32_t n_sys, const nb_params *params, void *cuda_str
         if (e == cudaSuccess)
             e = cudaMemcpy(c->d.part_orig, part_flat.data(), sizeof(int) * part_flat.size(), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(c->d.lj_tab, lj.data(), sizeof(float2) * lj.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(c->d.lj_d, ljd.data(), sizeof(float4) * ljd.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && P0.comb_rule == 0)
+            e = cudaMemcpy(c->d.eps_type, P0.epsilon, sizeof(float) * T, cudaMemcpyHostToDevice);
         st = cuda_status(e);
     }
     if (st != NB_OK) {
@@ -292,12 +299,27 @@ nb_status nb_set_lj_params(nb_ctx *ctx, const float *h_sigma, const float *h_eps
             if (!(h_sigma_tab[k] >= 0.0f) || !(h_eps_tab[k] >= 0.0f)) return NB_ERR_INVALID_ARG;
     }
     std::vector<float2> lj((size_t)T * T);
+    std::vector<float4> ljd((size_t)T * T);
     make_tables(T, ctx->comb_rule, h_sigma, h_epsilon, h_sigma_tab, h_eps_tab, ctx->sig_tab.data(),
-                ctx->eps_tab.data(), lj.data());
+                ctx->eps_tab.data(), lj.data(), ljd.data());
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return NB_ERR_CUDA;
     if (cudaMemcpy(ctx->d.lj_tab, lj.data(), sizeof(float2) * lj.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         return NB_ERR_CUDA;
+    if (cudaMemcpy(ctx->d.lj_d, ljd.data(), sizeof(float4) * ljd.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return NB_ERR_CUDA;
+    if (ctx->comb_rule == 0 &&
+        cudaMemcpy(ctx->d.eps_type, h_epsilon, sizeof(float) * T, cudaMemcpyHostToDevice) != cudaSuccess)
+        return NB_ERR_CUDA;
     return NB_OK;
+}
+
+nb_status nb_type_gradients(nb_ctx *ctx, const double *d_dLdsig_tab, const double *d_dLdeps_tab, double *d_dLdsigma,
+                            double *d_dLdeps)
+{
+    if (!ctx || !d_dLdsig_tab || !d_dLdeps_tab || !d_dLdsigma || !d_dLdeps) return NB_ERR_INVALID_ARG;
+    if (ctx->comb_rule != 0) return NB_ERR_UNSUPPORTED;
+    return launch_type_grad(ctx, d_dLdsig_tab, d_dLdeps_tab, d_dLdsigma, d_dLdeps) == cudaSuccess ? NB_OK
+                                                                                                  : NB_ERR_CUDA;
 }
 
 nb_status nb_get_status(nb_ctx *ctx)

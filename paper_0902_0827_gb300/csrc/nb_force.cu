@@ -25,6 +25,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "nb_pair.cuh"
 
@@ -55,6 +56,13 @@ struct ForceArgs {
     int *dbg_ij;
     long long dbg_cap;
     PairParams P;
+    // adjoint only
+    const float4 *gslot;     // [S] dL/dF in sorted order (x, y, z, 0)
+    const double *dLdE;      // [n_sys*2] dL/dE_LJ, dL/dE_C, or null
+    const float4 *lj_d;      // [T*T] 48 eps sig^11, 24 eps sig^5, 4 sig^12, 4 sig^6
+    float *dpos;             // [N*3] dL/dx (caller order), or null
+    float *dq;               // [N] dL/dq (caller order), or null
+    long long *tab_acc;      // [T*T*2] fixed-point dL/dsig_ab, dL/deps_ab (one ordered half)
 };
 
 __device__ __forceinline__ long long to_fixed(float v, int *status)
@@ -76,6 +84,9 @@ struct ForceSmem {
     uint16_t *surv;
     uint32_t *ring;
     unsigned long long *cacc;
+    float4 *gj;                // adjoint: staged dL/dF of the j atoms
+    float4 *ljd;               // adjoint: derivative factors of the type pairs
+    unsigned long long *tacc;  // adjoint: block table of fixed-point parameter gradients
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -85,9 +96,10 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p)
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-__host__ __device__ inline size_t force_smem_bytes(int T, int scap, int nwarps)
+__host__ __device__ inline size_t force_smem_bytes(int T, int scap, int nwarps, bool adj = false)
 {
-    size_t b = align16((size_t)T * T * 8);
+    size_t b = adj ? (size_t)scap * kCluster * 16 + (size_t)T * T * 16 + (size_t)T * T * 16 : 0;
+    b += align16((size_t)T * T * 8);
     b += align16((size_t)scap * 4);
     b += (size_t)scap * kCluster * 16;
     b += (size_t)scap * kCluster * 4;
@@ -98,10 +110,20 @@ __host__ __device__ inline size_t force_smem_bytes(int T, int scap, int nwarps)
     return b;
 }
 
-__device__ __forceinline__ ForceSmem carve(unsigned char *smem, int T, int scap, int nwarps, int w)
+__device__ __forceinline__ ForceSmem carve(unsigned char *smem, int T, int scap, int nwarps, int w, bool adj = false)
 {
     ForceSmem S;
     size_t off = 0;
+    S.gj = S.ljd = nullptr;
+    S.tacc = nullptr;
+    if (adj) {
+        S.gj = reinterpret_cast<float4 *>(smem + off);
+        off += (size_t)scap * kCluster * 16;
+        S.ljd = reinterpret_cast<float4 *>(smem + off);
+        off += (size_t)T * T * 16;
+        S.tacc = reinterpret_cast<unsigned long long *>(smem + off);
+        off += (size_t)T * T * 16;
+    }
     S.lj = reinterpret_cast<float2 *>(smem + off);
     off += align16((size_t)T * T * 8);
     S.ent = reinterpret_cast<uint32_t *>(smem + off);
@@ -141,6 +163,7 @@ __device__ __forceinline__ int swz(int e, int k) { return e * kCluster + (k ^ (e
 // Stage the chunk [c0, c0 + n) of cluster I's list, then for every listed
 // cluster J its 8 coordinates+charges, 8 types and bounding box, with
 // asynchronous copies issued by every thread of the block.
+template <bool ADJ>
 __device__ __forceinline__ void stage_chunk(const ForceArgs &A, const ForceSmem &S, int I, int c0, int n)
 {
     const uint4 *src = reinterpret_cast<const uint4 *>(A.list + (long long)I * A.cap + c0);
@@ -148,19 +171,18 @@ __device__ __forceinline__ void stage_chunk(const ForceArgs &A, const ForceSmem 
     for (int p = threadIdx.x; p < nent16; p += blockDim.x) cp_async16(reinterpret_cast<uint4 *>(S.ent) + p, src + p);
     cp_async_wait_all();
     __syncthreads();
-    constexpr int kPieces = 2 * kCluster + 2;  // per entry: 8 coordinates (16 B), 8 types (4 B), 2 box corners
-    for (int p = threadIdx.x; p < kPieces * n; p += blockDim.x) {
-        const int e = p / kPieces, sub = p - e * kPieces;
-        const long long J = (long long)(S.ent[e] & kJMask);
-        if (sub < kCluster) {
-            cp_async16(S.pos + swz(e, sub), A.xyzq + J * kCluster + sub);
-        } else if (sub < 2 * kCluster) {
-            const int k = sub - kCluster;
-            cp_async4(S.typ + swz(e, k), A.tslot + J * kCluster + k);
-        } else {
-            const int h = sub - 2 * kCluster;
-            cp_async16(S.bb + e * 2 + h, A.bb + J * 2 + h);
-        }
+    // per entry: 8 coordinates (16 B each), 8 types (4 B each), 2 box corners
+    // (16 B each) and, for the adjoint, 8 dL/dF vectors (16 B each)
+    for (int p = threadIdx.x; p < n * kCluster; p += blockDim.x) {
+        const int e = p >> 3, k = p & 7;
+        const long long j = (long long)(S.ent[e] & kJMask) * kCluster + k;
+        cp_async16(S.pos + swz(e, k), A.xyzq + j);
+        cp_async4(S.typ + swz(e, k), A.tslot + j);
+        if (ADJ) cp_async16(S.gj + swz(e, k), A.gslot + j);
+    }
+    for (int p = threadIdx.x; p < n * 2; p += blockDim.x) {
+        const int e = p >> 1;
+        cp_async16(S.bb + p, A.bb + (long long)(S.ent[e] & kJMask) * 2 + (p & 1));
     }
     cp_async_wait_all();
     __syncthreads();
@@ -170,6 +192,98 @@ struct Acc {
     float fx, fy, fz, elj, ec;
     float w[6];
 };
+
+struct AccAdj {
+    float dx, dy, dz, dq;
+};
+
+constexpr double kTabScale = 65536.0;  // fixed-point scale of the parameter gradients
+
+__device__ __forceinline__ long long to_fixed_tab(float v, int *status)
+{
+    if (!(fabsf(v) < 1.0e13f)) {
+        atomicOr(status, ST_OVERFLOW);
+        return 0;
+    }
+    return __float2ll_rn(v * (float)kTabScale);
+}
+
+// Adjoint of one ordered pair (i, j) for L = sum G.F + gE_lj E_lj + gE_c E_C.
+// With d = x_j - x_i, F_i = h d where h = U'(r)/r, and g = G_i - G_j:
+//   dL/dx_i -= h g + (h'/r)(g.d) d + (gE-weighted h) d     (h' = dh/dr)
+//   dL/dq_i += w_c ke q_j (phi'(r)/r (g.d) + gE_c phi(r))
+//   dL/dsig_ab, dL/deps_ab (+= half: each unordered pair is visited twice)
+// through dU/dA = w S r^-12, dU/dB = -w S r^-6 and the chain factors
+// dA/dsig = 48 eps sig^11, dB/dsig = 24 eps sig^5, dA/deps = 4 sig^12,
+// dB/deps = 4 sig^6 of the type pair.
+template <bool EWALD>
+__device__ __forceinline__ void eval_pair_adj(const PairParams &P, const ForceSmem &S, int ti_row, float qi_ke, float gix,
+                                              float giy, float giz, float gE_lj, float gE_c, bool in, float dx,
+                                              float dy, float dz, float r2, float qj, int tj, float4 gj, bool is14,
+                                              int *status, AccAdj &acc)
+{
+    const float rinv = fast_rsqrt(r2);
+    const float r = r2 * rinv, ir2 = rinv * rinv;
+    const float2 ab = S.lj[ti_row + tj];
+    const float ir6 = ir2 * ir2 * ir2, ir12 = ir6 * ir6;
+    // LJ V = A r^-12 - B r^-6 and its r-derivatives
+    const float t12 = ab.x * ir12, t6 = ab.y * ir6;
+    const float V = t12 - t6;
+    const float V1 = (6.0f * t6 - 12.0f * t12) * rinv;
+    const float V2 = (156.0f * t12 - 42.0f * t6) * ir2;
+    // switch S(r), S', S'' (r > rs)
+    float Sw = 1.0f, S1 = 0.0f, S2 = 0.0f;
+    if (r2 > P.rs2) {
+        const float t = P.rc2 - r2, u = P.rs2 - r2;
+        Sw = t * t * fmaf(2.0f, r2, P.sw_c0) * P.sw_inv;
+        S1 = 12.0f * r * t * u * P.sw_inv;
+        S2 = 12.0f * (t * u - 2.0f * r2 * u - 2.0f * r2 * t) * P.sw_inv;
+    }
+    const float wlj = is14 ? P.s14_lj : 1.0f;
+    const float wc = is14 ? P.s14_c : 1.0f;
+    const float Ulj1 = wlj * fmaf(S1, V, Sw * V1);
+    const float Ulj2 = wlj * (S2 * V + 2.0f * S1 * V1 + Sw * V2);
+    // Coulomb phi = erfc(a r)/r and its r-derivatives (without q_i q_j)
+    float phi, phi1, phi2;
+    if (EWALD) {
+        const float tt = fast_rcp(fmaf(P.alpha_half, r, 1.0f));
+        const float ex = fast_exp2(r2 * P.neg_a2_log2e);
+        const float erfcv = ex * erfcx_poly(P, tt);
+        const float cg = P.two_a_sqpi * ex;
+        phi = erfcv * rinv;
+        phi1 = -(cg + phi) * rinv;
+        phi2 = 2.0f * P.alpha * P.alpha * cg + 2.0f * (cg + phi) * ir2;
+    } else {
+        phi = rinv;
+        phi1 = -ir2;
+        phi2 = 2.0f * ir2 * rinv;
+    }
+    const float qq = qi_ke * qj;
+    const float U1 = fmaf(wc * qq, phi1, Ulj1);
+    const float U2 = fmaf(wc * qq, phi2, Ulj2);
+    const float h = U1 * rinv;
+    const float h1r = (U2 - U1 * rinv) * ir2;  // (dh/dr) / r
+    const float gx = gix - gj.x, gy = giy - gj.y, gz = giz - gj.z;
+    const float gd = fmaf(gx, dx, fmaf(gy, dy, gz * dz));
+    const float hE = (gE_lj * Ulj1 + gE_c * wc * qq * phi1) * rinv;
+    const float cd = fmaf(h1r, gd, hE);
+    const float m = in ? 1.0f : 0.0f;
+    acc.dx -= m * fmaf(h, gx, cd * dx);
+    acc.dy -= m * fmaf(h, gy, cd * dy);
+    acc.dz -= m * fmaf(h, gz, cd * dz);
+    acc.dq += m * wc * P.ke * qj * fmaf(phi1 * rinv, gd, gE_c * phi);
+    // type-pair parameters
+    const float uA = wlj * Sw * ir12, uB = -wlj * Sw * ir6;
+    const float uA1 = wlj * fmaf(S1, ir12, -12.0f * Sw * ir12 * rinv);
+    const float uB1 = -wlj * fmaf(S1, ir6, -6.0f * Sw * ir6 * rinv);
+    const float gA = fmaf(uA1 * rinv, gd, gE_lj * uA), gB = fmaf(uB1 * rinv, gd, gE_lj * uB);
+    if (in) {
+        const float4 c = S.ljd[ti_row + tj];
+        const float dsig = 0.5f * fmaf(gA, c.x, gB * c.y), deps = 0.5f * fmaf(gA, c.z, gB * c.w);
+        atomicAdd(&S.tacc[2 * (ti_row + tj)], (unsigned long long)to_fixed_tab(dsig, status));
+        atomicAdd(&S.tacc[2 * (ti_row + tj) + 1], (unsigned long long)to_fixed_tab(deps, status));
+    }
+}
 
 // One candidate pair: d = x_j - x_i (exact-shift image), r2 its FP32 squared
 // length; the arithmetic is done for every candidate and masked by `in`.
@@ -204,18 +318,26 @@ __device__ __forceinline__ void eval_pair(const PairParams &P, const float2 *__r
     }
 }
 
+// Per-warp data of the i atom.
+struct IAtom {
+    float xi, yi, zi, xim, yim, zim;
+    float qi;     // ke * q_i
+    int ti_row;   // t_i * T
+    int iorig;    // caller index (debug)
+    float gix, giy, giz, gE_lj, gE_c;  // adjoint
+};
+
 // One ring item: staged cluster e, atom k, 1-4 flag.  The displacement is
 // recomputed with the same operations as the membership test (same value).
-template <bool EWALD, bool VIRIAL, bool DEBUG>
-__device__ __forceinline__ void eval_item(const ForceArgs &A, const ForceSmem &S, int I, float Lx, float Ly, float Lz,
-                                          float xi, float yi, float zi, float xim, float yim, float zim, float qi,
-                                          int ti_row, int iorig, uint32_t item, bool active, Acc &acc)
+template <bool ADJ, bool EWALD, bool VIRIAL, bool DEBUG, class AccT>
+__device__ __forceinline__ void eval_item(const ForceArgs &A, const ForceSmem &S, float Lx, float Ly, float Lz,
+                                          const IAtom &ia, uint32_t item, bool active, AccT &acc)
 {
     const int e = (int)(item >> 4), k = (int)((item >> 1) & 7u);
     const uint32_t ent = S.ent[e];
     const int cx = (ent >> kShiftBit) & 3, cy = (ent >> (kShiftBit + 2)) & 3, cz = (ent >> (kShiftBit + 4)) & 3;
     const float sx = cx == 1 ? Lx : 0.0f, sy = cy == 1 ? Ly : 0.0f, sz = cz == 1 ? Lz : 0.0f;
-    const float ax = cx == 2 ? xim : xi, ay = cy == 2 ? yim : yi, az = cz == 2 ? zim : zi;
+    const float ax = cx == 2 ? ia.xim : ia.xi, ay = cy == 2 ? ia.yim : ia.yi, az = cz == 2 ? ia.zim : ia.zi;
     const int idx = swz(e, k);
     const float4 pj = S.pos[idx];
     const int tj = S.typ[idx];
@@ -225,19 +347,24 @@ __device__ __forceinline__ void eval_item(const ForceArgs &A, const ForceSmem &S
     if (DEBUG && active) {
         atomicAdd((unsigned long long *)&A.dbg_n[0], 1ull);
         const int jorig = A.perm[(int)(ent & kJMask) * kCluster + k];
-        if (iorig < jorig) {
+        if (ia.iorig < jorig) {
             const long long q = (long long)atomicAdd((unsigned long long *)&A.dbg_n[1], 1ull);
             if (q < A.dbg_cap) {
-                A.dbg_ij[2 * q] = iorig;
+                A.dbg_ij[2 * q] = ia.iorig;
                 A.dbg_ij[2 * q + 1] = jorig;
             }
         }
     }
-    eval_pair<EWALD, VIRIAL>(A.P, S.lj, ti_row, qi, active, dx, dy, dz, active ? r2 : 1.0f, pj.w, tj,
-                             (item & 1u) != 0u, acc);
+    if constexpr (ADJ) {
+        eval_pair_adj<EWALD>(A.P, S, ia.ti_row, ia.qi, ia.gix, ia.giy, ia.giz, ia.gE_lj, ia.gE_c, active, dx, dy, dz,
+                             active ? r2 : 1.0f, pj.w, tj, S.gj[idx], (item & 1u) != 0u, A.status, acc);
+    } else {
+        eval_pair<EWALD, VIRIAL>(A.P, S.lj, ia.ti_row, ia.qi, active, dx, dy, dz, active ? r2 : 1.0f, pj.w, tj,
+                                 (item & 1u) != 0u, acc);
+    }
 }
 
-template <bool EWALD, bool VIRIAL, bool DEBUG>
+template <bool ADJ, bool EWALD, bool VIRIAL, bool DEBUG>
 __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -246,10 +373,18 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
     const int w = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    const ForceSmem S = carve(smem, T, A.scap, nwarps, w);
+    const ForceSmem S = carve(smem, T, A.scap, nwarps, w, ADJ);
     for (int k = threadIdx.x; k < T * T; k += blockDim.x) S.lj[k] = A.lj_tab[k];
+    if (ADJ) {
+        for (int k = threadIdx.x; k < T * T; k += blockDim.x) {
+            S.ljd[k] = A.lj_d[k];
+            S.tacc[2 * k] = 0ull;
+            S.tacc[2 * k + 1] = 0ull;
+        }
+    }
     if (threadIdx.x < kTaskVals) S.cacc[threadIdx.x] = 0ull;
     __syncthreads();
+    using AccT = typename std::conditional<ADJ, AccAdj, Acc>::type;
 
     int cur_sys = -1;
     long long wacc[kTaskVals];
@@ -260,7 +395,7 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
 
     for (int I = blockIdx.x; I < n_clus; I += gridDim.x) {
         const int sys_id = A.clus_sys[I];
-        if (sys_id != cur_sys) {
+        if (!ADJ && sys_id != cur_sys) {
             // flush the per-warp energy/virial of the previous system through
             // the block accumulator (integer sums: order independent)
             if (cur_sys >= 0) {
@@ -283,22 +418,36 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
         const int islot = I * kCluster + w;
         const float4 pi = A.xyzq[islot];
         const bool iv = is_real_coord(pi.x);
-        const int ti_row = A.tslot[islot] * T;
-        const float xi = pi.x, yi = pi.y, zi = pi.z;
-        const float xim = __fsub_rn(xi, Lx), yim = __fsub_rn(yi, Ly), zim = __fsub_rn(zi, Lz);
-        const float qi = pi.w * A.P.ke;
+        IAtom ia;
+        ia.ti_row = A.tslot[islot] * T;
+        ia.xi = pi.x;
+        ia.yi = pi.y;
+        ia.zi = pi.z;
+        ia.xim = __fsub_rn(pi.x, Lx);
+        ia.yim = __fsub_rn(pi.y, Ly);
+        ia.zim = __fsub_rn(pi.z, Lz);
+        ia.qi = pi.w * A.P.ke;
+        ia.iorig = DEBUG ? A.perm[islot] : -1;
+        const float xi = ia.xi, yi = ia.yi, zi = ia.zi, xim = ia.xim, yim = ia.yim, zim = ia.zim;
+        if (ADJ) {
+            const float4 gi = A.gslot[islot];
+            ia.gix = gi.x;
+            ia.giy = gi.y;
+            ia.giz = gi.z;
+            ia.gE_lj = A.dLdE ? (float)A.dLdE[2 * sys_id] : 0.0f;
+            ia.gE_c = A.dLdE ? (float)A.dLdE[2 * sys_id + 1] : 0.0f;
+        } else {
+            ia.gix = ia.giy = ia.giz = ia.gE_lj = ia.gE_c = 0.0f;
+        }
         const int pe = lane < A.K ? A.ex_slot[(long long)islot * A.K + lane] : -1;
-        const int iorig = DEBUG ? A.perm[islot] : -1;
-        Acc acc;
-        acc.fx = acc.fy = acc.fz = acc.elj = acc.ec = 0.0f;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) acc.w[k] = 0.0f;
+        AccT acc;
+        memset(&acc, 0, sizeof(acc));
         const int nE = A.list_n[I];
 
         for (int c0 = 0; c0 < nE; c0 += A.scap) {
             const int nC = min(A.scap, nE - c0);
             __syncthreads();  // the staging buffers are free
-            stage_chunk(A, S, I, c0, nC);
+            stage_chunk<ADJ>(A, S, I, c0, nC);
             if (!iv) continue;
             // (1) prune staged clusters against this atom
             int ns = 0;
@@ -382,8 +531,8 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
                 tail += total;
                 __syncwarp();
                 while (tail - head >= 32) {
-                    eval_item<EWALD, VIRIAL, DEBUG>(A, S, I, Lx, Ly, Lz, xi, yi, zi, xim, yim, zim, qi, ti_row, iorig,
-                                                    S.ring[(head + lane) & (kRing - 1)], true, acc);
+                    eval_item<ADJ, EWALD, VIRIAL, DEBUG>(A, S, Lx, Ly, Lz, ia, S.ring[(head + lane) & (kRing - 1)],
+                                                         true, acc);
                     head += 32;
                 }
                 __syncwarp();
@@ -391,35 +540,64 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
             if (tail > head) {  // partial step before the staged data is replaced
                 const int n = tail - head;
                 const uint32_t item = lane < n ? S.ring[(head + lane) & (kRing - 1)] : 0u;
-                eval_item<EWALD, VIRIAL, DEBUG>(A, S, I, Lx, Ly, Lz, xi, yi, zi, xim, yim, zim, qi, ti_row, iorig,
-                                                item, lane < n, acc);
+                eval_item<ADJ, EWALD, VIRIAL, DEBUG>(A, S, Lx, Ly, Lz, ia, item, lane < n, acc);
             }
             __syncwarp();
         }
         if (!iv) continue;
-        // force of atom i: sum of the 32 lanes in 64-bit fixed point
-        long long vx = to_fixed(acc.fx, A.status), vy = to_fixed(acc.fy, A.status), vz = to_fixed(acc.fz, A.status);
+        if constexpr (ADJ) {
+            long long v0 = to_fixed(acc.dx, A.status), v1 = to_fixed(acc.dy, A.status),
+                      v2 = to_fixed(acc.dz, A.status), v3 = to_fixed(acc.dq, A.status);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            vx += __shfl_xor_sync(kFull, vx, o);
-            vy += __shfl_xor_sync(kFull, vy, o);
-            vz += __shfl_xor_sync(kFull, vz, o);
-        }
-        if (lane == 0) {
-            const long long a = A.perm[islot];
-            const float sc = 2.3283064365386963e-10f;  // 2^-32
-            A.F[3 * a] = __ll2float_rn(vx) * sc;
-            A.F[3 * a + 1] = __ll2float_rn(vy) * sc;
-            A.F[3 * a + 2] = __ll2float_rn(vz) * sc;
-        }
-        // energies and virial of atom i: FP32 butterfly (fixed order), then fixed point
-        float v[kTaskVals] = {acc.elj, acc.ec, acc.w[0], acc.w[1], acc.w[2], acc.w[3], acc.w[4], acc.w[5]};
+            for (int o = 16; o > 0; o >>= 1) {
+                v0 += __shfl_xor_sync(kFull, v0, o);
+                v1 += __shfl_xor_sync(kFull, v1, o);
+                v2 += __shfl_xor_sync(kFull, v2, o);
+                v3 += __shfl_xor_sync(kFull, v3, o);
+            }
+            if (lane == 0) {
+                const long long a = A.perm[islot];
+                const float sc = 2.3283064365386963e-10f;  // 2^-32
+                if (A.dpos) {
+                    A.dpos[3 * a] = __ll2float_rn(v0) * sc;
+                    A.dpos[3 * a + 1] = __ll2float_rn(v1) * sc;
+                    A.dpos[3 * a + 2] = __ll2float_rn(v2) * sc;
+                }
+                if (A.dq) A.dq[a] = __ll2float_rn(v3) * sc;
+            }
+        } else {
+            // force of atom i: sum of the 32 lanes in 64-bit fixed point
+            long long vx = to_fixed(acc.fx, A.status), vy = to_fixed(acc.fy, A.status),
+                      vz = to_fixed(acc.fz, A.status);
 #pragma unroll
-        for (int k = 0; k < (VIRIAL ? kTaskVals : 2); ++k) {
+            for (int o = 16; o > 0; o >>= 1) {
+                vx += __shfl_xor_sync(kFull, vx, o);
+                vy += __shfl_xor_sync(kFull, vy, o);
+                vz += __shfl_xor_sync(kFull, vz, o);
+            }
+            if (lane == 0) {
+                const long long a = A.perm[islot];
+                const float sc = 2.3283064365386963e-10f;  // 2^-32
+                A.F[3 * a] = __ll2float_rn(vx) * sc;
+                A.F[3 * a + 1] = __ll2float_rn(vy) * sc;
+                A.F[3 * a + 2] = __ll2float_rn(vz) * sc;
+            }
+            // energies and virial of atom i: FP32 butterfly (fixed order), then fixed point
+            float v[kTaskVals] = {acc.elj, acc.ec, acc.w[0], acc.w[1], acc.w[2], acc.w[3], acc.w[4], acc.w[5]};
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(kFull, v[k], o);
-            wacc[k] += to_fixed(v[k], A.status);
+            for (int k = 0; k < (VIRIAL ? kTaskVals : 2); ++k) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(kFull, v[k], o);
+                wacc[k] += to_fixed(v[k], A.status);
+            }
         }
+    }
+    if constexpr (ADJ) {
+        // block table of parameter gradients -> global (integer sums)
+        __syncthreads();
+        for (int k = threadIdx.x; k < 2 * T * T; k += blockDim.x)
+            if (S.tacc[k]) atomicAdd((unsigned long long *)&A.tab_acc[k], S.tacc[k]);
+        return;
     }
     // final flush of the last system
     if (cur_sys >= 0) {
@@ -475,35 +653,30 @@ __global__ void k_finalize(int n_sys, const long long *__restrict__ sys_acc, dou
     }
 }
 
-template <bool EWALD, bool VIRIAL, bool DEBUG>
+template <bool ADJ, bool EWALD, bool VIRIAL, bool DEBUG>
 static void launch_force_t(nb_ctx *ctx, const ForceArgs &A)
 {
     const int nw = kCluster;
-    const size_t smem = force_smem_bytes(A.P.n_types, A.scap, nw);
+    const size_t smem = force_smem_bytes(A.P.n_types, A.scap, nw, ADJ);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_force<EWALD, VIRIAL, DEBUG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        cudaFuncSetAttribute(k_force<ADJ, EWALD, VIRIAL, DEBUG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             220 * 1024);
         attr_set = true;
     }
     // persistent grid: never more blocks than can be resident at once
     int resident = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_force<EWALD, VIRIAL, DEBUG>, nw * 32, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_force<ADJ, EWALD, VIRIAL, DEBUG>, nw * 32, smem);
     const int per_sm = std::max(1, std::min(ctx->tune.blocks_per_sm, resident));
     const int grid = ctx->num_sms * per_sm;
-    k_force<EWALD, VIRIAL, DEBUG><<<grid, nw * 32, smem, ctx->stream>>>(A);
+    k_force<ADJ, EWALD, VIRIAL, DEBUG><<<grid, nw * 32, smem, ctx->stream>>>(A);
 }
 
-cudaError_t launch_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type, float *d_F,
-                          double *d_energy, double *d_virial, bool debug_pairs)
+static ForceArgs make_args(nb_ctx *ctx)
 {
     auto &d = ctx->d;
-    const int tb = 256;
-    const int S = (int)ctx->slot_cap;
-    if (d_pos)  // the debug pair export reuses the last packed values
-        k_pack<<<(S + tb - 1) / tb, tb, 0, ctx->stream>>>(S, d.counts, d.perm, d.xyzq, d.tslot, d_pos, d_q, d_type,
-                                                           d.sys, d.atom_sys, ctx->pp.n_types, d.status);
-    cudaMemsetAsync(d.sys_acc, 0, sizeof(long long) * kTaskVals * ctx->n_sys, ctx->stream);
     ForceArgs A;
+    memset(&A, 0, sizeof(A));
     A.sys = d.sys;
     A.counts = d.counts;
     A.xyzq = d.xyzq;
@@ -518,26 +691,49 @@ cudaError_t launch_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, con
     A.ex_slot = d.ex_slot;
     A.K = ctx->K;
     A.lj_tab = d.lj_tab;
-    A.F = d_F;
     A.sys_acc = d.sys_acc;
     A.status = d.status;
     A.dbg_n = d.dbg_n;
     A.dbg_ij = d.dbg_ij;
     A.dbg_cap = d.dbg_cap;
     A.P = ctx->pp;
+    return A;
+}
+
+cudaError_t launch_pack(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type)
+{
+    auto &d = ctx->d;
+    const int tb = 256;
+    const int S = (int)ctx->slot_cap;
+    k_pack<<<(S + tb - 1) / tb, tb, 0, ctx->stream>>>(S, d.counts, d.perm, d.xyzq, d.tslot, d_pos, d_q, d_type, d.sys,
+                                                       d.atom_sys, ctx->pp.n_types, d.status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type, float *d_F,
+                          double *d_energy, double *d_virial, bool debug_pairs)
+{
+    auto &d = ctx->d;
+    if (d_pos) {  // the debug pair export reuses the last packed values
+        cudaError_t e = launch_pack(ctx, d_pos, d_q, d_type);
+        if (e != cudaSuccess) return e;
+    }
+    cudaMemsetAsync(d.sys_acc, 0, sizeof(long long) * kTaskVals * ctx->n_sys, ctx->stream);
+    ForceArgs A = make_args(ctx);
+    A.F = d_F;
     const bool ewald = ctx->pp.ewald != 0;
     const bool virial = d_virial != nullptr;
     const bool prof = ctx->profiling && ctx->prof_n < (int)ctx->prof_ev.size() / 2;
     if (prof) cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n], ctx->stream);
     if (debug_pairs) {
-        if (ewald) launch_force_t<true, false, true>(ctx, A);
-        else launch_force_t<false, false, true>(ctx, A);
+        if (ewald) launch_force_t<false, true, false, true>(ctx, A);
+        else launch_force_t<false, false, false, true>(ctx, A);
     } else if (ewald) {
-        if (virial) launch_force_t<true, true, false>(ctx, A);
-        else launch_force_t<true, false, false>(ctx, A);
+        if (virial) launch_force_t<false, true, true, false>(ctx, A);
+        else launch_force_t<false, true, false, false>(ctx, A);
     } else {
-        if (virial) launch_force_t<false, true, false>(ctx, A);
-        else launch_force_t<false, false, false>(ctx, A);
+        if (virial) launch_force_t<false, false, true, false>(ctx, A);
+        else launch_force_t<false, false, false, false>(ctx, A);
     }
     if (prof) {
         cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n + 1], ctx->stream);
@@ -550,6 +746,21 @@ cudaError_t launch_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, con
     return cudaGetLastError();
 }
 
-size_t force_smem_for(int T, int scap) { return force_smem_bytes(T, scap, kCluster); }
+size_t force_smem_for(int T, int scap) { return force_smem_bytes(T, scap, kCluster, true); }
+
+cudaError_t launch_adjoint_tile(nb_ctx *ctx, const double *d_dLdE, float *d_dpos, float *d_dq)
+{
+    auto &d = ctx->d;
+    ForceArgs A = make_args(ctx);
+    A.gslot = d.gslot;
+    A.dLdE = d_dLdE;
+    A.lj_d = d.lj_d;
+    A.dpos = d_dpos;
+    A.dq = d_dq;
+    A.tab_acc = d.tab_grad;
+    if (ctx->pp.ewald) launch_force_t<true, true, false, false>(ctx, A);
+    else launch_force_t<true, false, false, false>(ctx, A);
+    return cudaGetLastError();
+}
 
 }  // namespace acenb

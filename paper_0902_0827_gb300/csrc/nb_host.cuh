@@ -132,7 +132,7 @@ inline nb_status validate_one(const nb_params *p)
 // (A, B) = (4 eps sig^12, 4 eps sig^6) per type pair, from per-type
 // Lorentz-Berthelot parameters (comb_rule 0) or explicit pair tables.
 inline void make_tables(int T, int comb_rule, const float *sigma, const float *eps, const float *sig_tab,
-                        const float *eps_tab, double *sg_out, double *ep_out, float2 *lj)
+                        const float *eps_tab, double *sg_out, double *ep_out, float2 *lj, float4 *lj_d = nullptr)
 {
     for (int a = 0; a < T; ++a)
         for (int b = 0; b < T; ++b) {
@@ -148,6 +148,11 @@ inline void make_tables(int T, int comb_rule, const float *sigma, const float *e
             ep_out[a * T + b] = ep;
             double s6 = sg * sg * sg * sg * sg * sg;
             lj[a * T + b] = make_float2((float)(4.0 * ep * s6 * s6), (float)(4.0 * ep * s6));
+            if (lj_d) {  // dA/dsig, dB/dsig, dA/deps, dB/deps
+                const double s5 = sg * sg * sg * sg * sg, s11 = s6 * s5;
+                lj_d[a * T + b] = make_float4((float)(48.0 * ep * s11), (float)(24.0 * ep * s5),
+                                              (float)(4.0 * s6 * s6), (float)(4.0 * s6));
+            }
         }
 }
 

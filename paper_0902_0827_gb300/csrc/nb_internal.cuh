@@ -103,10 +103,13 @@ struct DevBuffers {
     uint32_t *list = nullptr;        // [NC*cap] cluster-pair entries
     int *list_n = nullptr;           // [NC]
     long long *sys_acc = nullptr;    // [n_sys*kTaskVals] per-system fixed-point energy/virial
-    long long *tab_grad = nullptr;   // [T*T*2] adjoint table gradients (fixed point)
+    long long *tab_grad = nullptr;   // [T*T*2] adjoint dL/dsig_ab, dL/deps_ab (fixed point, one ordered half)
     int *counts = nullptr;           // [4]: n_slots, n_clusters, pair counters
     int *status = nullptr;           // [1]
     float2 *lj_tab = nullptr;        // [T*T] (A, B)
+    float4 *lj_d = nullptr;          // [T*T] 48 eps sig^11, 24 eps sig^5, 4 sig^12, 4 sig^6
+    float4 *gslot = nullptr;         // [S] adjoint input dL/dF in sorted order
+    float *eps_type = nullptr;       // [T] per-type epsilon (Lorentz-Berthelot chain)
     long long *dbg_n = nullptr;      // [2] debug pair counters
     int *dbg_ij = nullptr;           // [cap*2]
     int64_t dbg_cap = 0;
@@ -161,6 +164,9 @@ cudaError_t launch_build(nb_ctx *ctx, const float *d_pos);
 cudaError_t launch_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type,
                           float *d_F, double *d_energy, double *d_virial, bool debug_pairs);
 size_t force_smem_for(int T, int scap);
+cudaError_t launch_pack(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type);
+cudaError_t launch_type_grad(nb_ctx *ctx, const double *gsig_tab, const double *geps_tab, double *gsig, double *geps);
+cudaError_t launch_adjoint_tile(nb_ctx *ctx, const double *d_dLdE, float *d_dpos, float *d_dq);
 cudaError_t launch_backward(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type,
                             const float *d_dLdF, const double *d_dLdE, float *d_dLdpos, float *d_dLdq,
                             double *d_dsig, double *d_deps);

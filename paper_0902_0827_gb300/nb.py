@@ -25,7 +25,7 @@ STATUS_NAMES = {
 EXPORTS = ("nb_create", "nb_create_batch", "nb_build_cells", "nb_forces", "nb_backward", "nb_get_status",
            "nb_set_stream", "nb_destroy", "nb_set_tuning", "nb_get_tuning", "nb_get_sizes", "nb_debug_cells",
            "nb_debug_pairs", "nb_status_string", "nb_set_lj_params", "nb_set_profiling", "nb_get_profile",
-           "nb_forces_noalloc")
+           "nb_forces_noalloc", "nb_type_gradients")
 
 
 class NbError(RuntimeError):
@@ -89,6 +89,7 @@ def lib(build_if_missing: bool = True):
             "nb_set_profiling": ([P, I32], ctypes.c_int),
             "nb_get_profile": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64)], ctypes.c_int),
             "nb_forces_noalloc": ([ctypes.POINTER(nb_params), P, P, P, P, P, P, P], ctypes.c_int),
+            "nb_type_gradients": ([P, P, P, P, P], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -236,6 +237,16 @@ class Nonbonded:
                                  _tptr(gpos), _tptr(gq), _tptr(gs), _tptr(ge)), "nb_backward")
         return gpos, gq, gs, ge
 
+    def type_gradients(self, gsig_tab, geps_tab):
+        """Per-type (sigma, epsilon) gradients from type-pair gradients (Lorentz-Berthelot)."""
+        import torch
+        gs = torch.empty((self.n_types,), dtype=torch.float64, device=gsig_tab.device)
+        ge = torch.empty((self.n_types,), dtype=torch.float64, device=gsig_tab.device)
+        self._sync_stream()
+        _check(lib().nb_type_gradients(self.h, _tptr(gsig_tab.contiguous()), _tptr(geps_tab.contiguous()),
+                                       _tptr(gs), _tptr(ge)), "nb_type_gradients")
+        return gs, ge
+
     def set_lj_params(self, sigma, epsilon):
         """Replace the per-type LJ parameters (Lorentz-Berthelot) of the context."""
         sig, eps = _f32(sigma), _f32(epsilon)
@@ -303,3 +314,59 @@ def concat_inputs(systems: Sequence, device="cuda"):
     q = np.concatenate([s.q for s in systems]).astype(np.float32)
     t = np.concatenate([s.type for s in systems]).astype(np.int32)
     return (torch.from_numpy(pos).to(device), torch.from_numpy(q).to(device), torch.from_numpy(t).to(device))
+
+
+def _autograd():
+    import torch
+
+    class NonbondedFn(torch.autograd.Function):
+        """(F, E) = NonbondedFn.apply(pos, q, sigma, epsilon, ctx, types).
+
+        forward: cell-list rebuild + forces and energies (E is [n_sys, 2]:
+        LJ, Coulomb).  backward: the library's adjoint kernel with the pair
+        list recomputed from a fresh build, giving dL/dpos (Hessian-vector
+        product plus the energy term), dL/dq and per-type dL/dsigma, dL/deps.
+        sigma/epsilon are per-type tensors; the context's LJ table is updated
+        from them when their values change.
+        """
+
+        @staticmethod
+        def forward(fctx, pos, q, sigma, epsilon, nbctx, typ):
+            sig = sigma.detach().double().cpu().numpy().astype(np.float32)
+            eps = epsilon.detach().double().cpu().numpy().astype(np.float32)
+            key = (sig.tobytes(), eps.tobytes())
+            if getattr(nbctx, "_lj_key", None) != key:
+                nbctx.set_lj_params(sig, eps)
+                nbctx._lj_key = key
+            nbctx.build(pos)
+            F, E, _ = nbctx.forces(pos, q, typ, virial=False)
+            fctx.save_for_backward(pos, q)
+            fctx.nb = nbctx
+            fctx.typ = typ
+            fctx.sig_meta = (sigma.dtype, sigma.device, epsilon.dtype, epsilon.device)
+            return F, E
+
+        @staticmethod
+        def backward(fctx, gF, gE):
+            pos, q = fctx.saved_tensors
+            nbctx = fctx.nb
+            gF = torch.zeros_like(pos) if gF is None else gF.contiguous().float()
+            gE = None if gE is None else gE.contiguous().double()
+            nbctx.build(pos)  # the pair list is recomputed, not stored
+            gpos, gq, gs_tab, ge_tab = nbctx.backward(pos, q, fctx.typ, gF, gE)
+            gs, ge = nbctx.type_gradients(gs_tab, ge_tab)
+            sd, sdev, ed, edev = fctx.sig_meta
+            return gpos, gq, gs.to(sdev, sd), ge.to(edev, ed), None, None
+
+    return NonbondedFn
+
+
+_fn_cache = None
+
+
+def nonbonded(pos, q, sigma, epsilon, nbctx, typ):
+    """Differentiable (F, E) through the library's forward and adjoint kernels."""
+    global _fn_cache
+    if _fn_cache is None:
+        _fn_cache = _autograd()
+    return _fn_cache.apply(pos, q, sigma, epsilon, nbctx, typ)
