@@ -60,7 +60,7 @@ def lib():
             L.orc_forces_cells.restype = I64
             L.orc_forces_subset.argtypes = common + [I64, P, P, P, P]
             L.orc_forces_subset.restype = None
-            L.orc_backward_allpairs.argtypes = common + [P, D, P, P, P, P]
+            L.orc_backward_allpairs.argtypes = common + [P, D, P, P, P, P, P, P]
             L.orc_backward_allpairs.restype = I64
             L.orc_pairs.argtypes = [I64, P, P, F, I64, P, I64, P, I64, P]
             L.orc_pairs.restype = I64
@@ -150,8 +150,9 @@ def forces_subset(sys, atoms, pos=None, q=None):
     return F, E4[:, :2].copy(), npair
 
 
-def backward(sys, G, gE: float = 0.0, pos=None, q=None):
-    """Adjoint of L = sum G.F + gE*E: dL/dx [N,3], dL/dq [N], dL/dA, dL/dB [T,T]."""
+def backward(sys, G, gE: float = 0.0, pos=None, q=None, with_scale: bool = False):
+    """Adjoint of L = sum G.F + gE*E: dL/dx [N,3], dL/dq [N], dL/dA, dL/dB [T,T]
+    (and, with with_scale, the sums of |pair contribution| of dL/dA, dL/dB)."""
     args, keep = _args(sys, pos, q)
     n = args[0]
     T = sys.n_types
@@ -160,8 +161,12 @@ def backward(sys, G, gE: float = 0.0, pos=None, q=None):
     dq = np.zeros(n)
     dA = np.zeros((T, T))
     dB = np.zeros((T, T))
-    lib().orc_backward_allpairs(*args, _p(Gd), float(gE), _p(dx), _p(dq), _p(dA), _p(dB))
+    aA = np.zeros((T, T))
+    aB = np.zeros((T, T))
+    lib().orc_backward_allpairs(*args, _p(Gd), float(gE), _p(dx), _p(dq), _p(dA), _p(dB), _p(aA), _p(aB))
     del keep
+    if with_scale:
+        return dx, dq, dA, dB, aA, aB
     return dx, dq, dA, dB
 
 

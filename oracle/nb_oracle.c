@@ -481,14 +481,15 @@ int64_t orc_pairs(int64_t n, const float *pos, const float *box, float rc,
 /* Adjoint.  L = sum_i G_i . F_i + gE * (E_LJ + E_C).                  */
 /* Outputs dL/dx [n*3] (the Hessian-vector product -H G plus -gE F),   */
 /* dL/dq [n], dL/dA_ab and dL/dB_ab [T*T] (symmetric: each unordered    */
-/* type pair's value is stored in both [a][b] and [b][a]).             */
+/* type pair's value is stored in both [a][b] and [b][a]) and, when     */
+/* non-null, the sums of |pair contribution| of each table entry.      */
 /* ------------------------------------------------------------------ */
 int64_t orc_backward_allpairs(int64_t n, const float *pos, const float *q, const int32_t *type,
                               int ntypes, const double *A, const double *B, const float *box,
                               float rc, float rs, float alpha, float ke, float s14_lj, float s14_c,
                               int64_t nex, const int32_t *ex, int64_t n14, const int32_t *p14,
                               const double *G, double gE,
-                              double *dx, double *dq, double *dA, double *dB)
+                              double *dx, double *dq, double *dA, double *dB, double *dAabs, double *dBabs)
 {
     prm_t p;
     prm_init(&p, box, rc, rs, alpha, ke, s14_lj, s14_c, ntypes, A, B);
@@ -498,6 +499,8 @@ int64_t orc_backward_allpairs(int64_t n, const float *pos, const float *q, const
     memset(dq, 0, sizeof(double) * (size_t)n);
     memset(dA, 0, sizeof(double) * (size_t)ntypes * ntypes);
     memset(dB, 0, sizeof(double) * (size_t)ntypes * ntypes);
+    if (dAabs) memset(dAabs, 0, sizeof(double) * (size_t)ntypes * ntypes);
+    if (dBabs) memset(dBabs, 0, sizeof(double) * (size_t)ntypes * ntypes);
     int64_t npairs = 0;
     for (int64_t i = 0; i < n; ++i)
         for (int64_t j = i + 1; j < n; ++j) {
@@ -531,6 +534,9 @@ int64_t orc_backward_allpairs(int64_t n, const float *pos, const float *q, const
             int ba = type[j] * ntypes + type[i];
             dA[ab] += gA; dB[ab] += gB;
             if (ba != ab) { dA[ba] += gA; dB[ba] += gB; }
+            /* summation scale of each table entry (sum of |contribution|) */
+            if (dAabs) { dAabs[ab] += fabs(gA); if (ba != ab) dAabs[ba] += fabs(gA); }
+            if (dBabs) { dBabs[ab] += fabs(gB); if (ba != ab) dBabs[ba] += fabs(gB); }
             ++npairs;
         }
     topo_free(&t);

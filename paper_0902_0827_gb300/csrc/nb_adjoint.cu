@@ -31,7 +31,7 @@ __global__ void k_tab_finalize(int T, const long long *__restrict__ acc, double 
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= T * T) return;
     const int a = k / T, b = k % T;
-    const double sc = 1.0 / 65536.0;
+    const double sc = 1.0 / 4294967296.0;  // 2^-32
     long long s = acc[2 * k], e = acc[2 * k + 1];
     if (a != b) {
         s += acc[2 * (b * T + a)];

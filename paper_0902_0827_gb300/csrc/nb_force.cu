@@ -197,11 +197,11 @@ struct AccAdj {
     float dx, dy, dz, dq;
 };
 
-constexpr double kTabScale = 65536.0;  // fixed-point scale of the parameter gradients
+constexpr double kTabScale = 4294967296.0;  // fixed-point scale of the parameter gradients (2^32)
 
 __device__ __forceinline__ long long to_fixed_tab(float v, int *status)
 {
-    if (!(fabsf(v) < 1.0e13f)) {
+    if (!(fabsf(v) < 1073741824.0f)) {  // 2^30 per contribution
         atomicOr(status, ST_OVERFLOW);
         return 0;
     }
