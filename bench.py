@@ -134,6 +134,116 @@ def max_over_ranks(x: float, world: int) -> float:
     return float(t.item())
 
 
+def graph_of(fn, dev):
+    """Capture fn() (already warmed up) into a CUDA graph on a side stream."""
+    import torch
+    side = torch.cuda.Stream(device=dev)
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        fn()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=side):
+            fn()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    return g
+
+
+def time_steps(fn, steps, flush):
+    """Mean ms of fn() over `steps` calls, L2 flushed before each (outside the events)."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record()
+        fn()
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev) / steps
+
+
+def adjoint_leg(ctx, pos, q, typ, steps, flush, fwd_ms, npairs):
+    """Rebuild + adjoint (dL/dx, dL/dq, type-pair gradients) of the fitting
+    loss sum |F - F_target|^2 on the same system, replayed from a CUDA graph."""
+    import torch
+    from paper_0902_0827_gb300 import systems as S
+    N = pos.shape[0]
+    Ft = torch.from_numpy(S.target_forces(S.solvated_chain())).to(pos.device)
+    F, _, _ = ctx.forces(pos, q, typ, virial=False)
+    G = (2.0 * (F - Ft)).contiguous()
+    T = ctx.n_types
+    gpos = torch.empty((N, 3), dtype=torch.float32, device=pos.device)
+    gq = torch.empty((N,), dtype=torch.float32, device=pos.device)
+    gs = torch.empty((T, T), dtype=torch.float64, device=pos.device)
+    ge = torch.empty((T, T), dtype=torch.float64, device=pos.device)
+    from paper_0902_0827_gb300 import nb
+
+    def step():
+        ctx.build(pos)
+        ctx._sync_stream()
+        nb._check(nb.lib().nb_backward(ctx.h, nb._tptr(pos), nb._tptr(q), nb._tptr(typ), nb._tptr(G), None,
+                                       nb._tptr(gpos), nb._tptr(gq), nb._tptr(gs), nb._tptr(ge)), "nb_backward")
+
+    for _ in range(3):
+        step()
+    g = graph_of(step, pos.device)
+    ms = time_steps(g.replay, steps, flush)
+    ctx.status()
+    return {"ms_per_step": ms, "pairs_per_s": npairs / (ms * 1e-3), "ratio_to_forward": ms / fwd_ms,
+            "step": "cell-list rebuild + adjoint of sum|F - F_target|^2 (HVP, dL/dq, dL/dsig_ab, dL/deps_ab)",
+            "gpu_launches_per_step": 10}
+
+
+def batched_leg(steps, flush, dev):
+    """64 water boxes (log-uniform 500..20,000 atoms): one autotuned,
+    graph-captured rebuild + force step of the whole batch vs 64 sequential
+    per-system contexts with plain launches."""
+    import torch
+    from paper_0902_0827_gb300 import autotune, nb
+    from paper_0902_0827_gb300 import systems as S
+    systems = S.water_ensemble()
+    ctx = nb.Nonbonded(systems)
+    pos, q, typ = nb.concat_inputs(systems, device=dev)
+    cands = [dict(blocks_per_sm=b, stage_capacity=c) for b in (2, 3, 4) for c in (96, 160, 224)]
+    rec = autotune.autotune(ctx, pos, q, typ, candidates=cands, reps=3)
+    N = pos.shape[0]
+    F = torch.empty((N, 3), device=dev)
+    E = torch.empty((len(systems), 2), dtype=torch.float64, device=dev)
+    W = torch.empty((len(systems), 6), dtype=torch.float64, device=dev)
+
+    def step():
+        ctx.build(pos)
+        ctx.forces(pos, q, typ, F=F, energy=E, virial=W)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    _, npairs, _ = ctx.debug_pairs(cap=0)
+    g = graph_of(step, dev)
+    ms = time_steps(g.replay, steps, flush)
+    ctx.status()
+    # sequential: one context per system, plain launches one after another
+    seq = []
+    for s in systems:
+        c = nb.Nonbonded(s)
+        p1, q1, t1 = nb.concat_inputs([s], device=dev)
+        seq.append((c, p1, q1, t1))
+
+    def seq_step():
+        for c, p1, q1, t1 in seq:
+            c.build(p1)
+            c.forces(p1, q1, t1)
+
+    for _ in range(2):
+        seq_step()
+    torch.cuda.synchronize()
+    seq_ms = time_steps(seq_step, max(3, steps // 5), flush)
+    return {"n_systems": len(systems), "n_atoms": N, "pairs_per_step": npairs, "ms_per_step": ms,
+            "pairs_per_s": npairs / (ms * 1e-3), "sequential_ms_per_step": seq_ms,
+            "speedup_vs_sequential": seq_ms / ms, "tuning": rec["best"],
+            "gpu_launches_per_step": 9}
+
+
 def cpu_oracle_run(system, budget_s: float = 12.0, max_reps: int = 50):
     """The FP64 oracle (cell-list traversal, OpenMP over atoms) timed on the host."""
     import oracle
@@ -288,6 +398,8 @@ def main():
     }
 
     if not args.no_extras:
+        line["adjoint"] = adjoint_leg(ctx, pos, q, typ, args.steps, flush, ms, npairs)
+        line["batched"] = batched_leg(args.steps, flush, dev)
         # end to end through the public API with host buffers (pinned)
         hpos = pos.cpu().pin_memory()
         hq = q.cpu().pin_memory()
