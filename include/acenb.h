@@ -103,7 +103,8 @@ typedef struct {
     int32_t blocks_per_sm;  /* blocks per SM of the persistent force grid, 1..8 */
     int32_t stage_capacity; /* cluster-pair entries staged in shared memory per block pass,
                                16..512, multiple of 4 (longer lists are processed in chunks) */
-    int32_t list_capacity;  /* cluster-pair entries per cluster, 64..65536, multiple of 4 */
+    int32_t list_capacity;  /* cluster-pair entries of one cluster's list, built in shared
+                               memory by the force kernel, 64..4096, multiple of 4 */
     int32_t reserved;       /* must be 0 */
 } nb_tuning;
 
@@ -181,11 +182,11 @@ nb_status nb_set_stream(nb_ctx *ctx, void *cuda_stream);
 /* nb_destroy - free every device and host resource of the context. */
 void nb_destroy(nb_ctx *ctx);
 
-/* nb_set_tuning / nb_get_tuning - read or change the launch configuration.
- * A changed list_capacity reallocates scratch and requires a new build (not
- * allowed during stream capture).  Errors: NB_ERR_INVALID_ARG for values out
- * of range, NB_ERR_UNSUPPORTED when the shared-memory footprint of the force
- * kernel would exceed the device limit. */
+/* nb_set_tuning / nb_get_tuning - read or change the launch configuration;
+ * takes effect at the next force or adjoint launch (allowed between captures,
+ * no reallocation).  Errors: NB_ERR_INVALID_ARG for values out of range,
+ * NB_ERR_UNSUPPORTED when the shared-memory footprint of the force kernel
+ * would exceed the device limit. */
 nb_status nb_set_tuning(nb_ctx *ctx, const nb_tuning *t);
 nb_status nb_get_tuning(nb_ctx *ctx, nb_tuning *t);
 
@@ -227,7 +228,7 @@ nb_status nb_get_profile(nb_ctx *ctx, double *force_ms, int64_t *launches);
  *   d_pos, d_q, d_type, d_F, d_energy [2], d_virial [6]: as for nb_forces
  *            (d_energy / d_virial may be NULL);
  *   cuda_stream: the stream the work runs on.
- * All scratch lives in one static device array of about 4.4 MiB that every
+ * All scratch lives in one static device array of about 0.8 MiB that every
  * GPU loading this library holds until the library is unloaded; it bounds
  * the system to NB_NOALLOC_MAX_ATOMS atoms and NB_NOALLOC_MAX_COLUMNS x-y
  * columns (NB_ERR_TOO_LARGE otherwise).  The call allocates nothing (no

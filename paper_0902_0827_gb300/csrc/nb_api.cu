@@ -34,8 +34,8 @@ void free_all(nb_ctx *c)
 {
     auto &d = c->d;
     void *ptrs[] = {d.sys, d.atom_sys, d.atom_col, d.wpos, d.part_orig, d.col_sys, d.col_count, d.col_fill,
-                    d.col_slot, d.stage, d.xyzq, d.tslot, d.perm, d.inv, d.ex_slot, d.bb,
-                    d.clus_sys, d.list, d.list_n, d.sys_acc, d.tab_grad, d.counts, d.status, d.lj_tab,
+                    d.col_slot, d.stage, d.xyzq, d.tslot, d.perm, d.inv, d.bb,
+                    d.clus_sys, d.sys_acc, d.tab_grad, d.counts, d.status, d.lj_tab,
                     d.dbg_n, d.dbg_ij, d.scratch_f, d.scratch_g, d.lj_d, d.gslot, d.eps_type};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -81,11 +81,8 @@ nb_status allocate(nb_ctx *c)
     ALLOC(d.tslot, S);
     ALLOC(d.perm, S);
     ALLOC(d.inv, N);
-    ALLOC(d.ex_slot, S * c->K);
     ALLOC(d.bb, NC * 2);
     ALLOC(d.clus_sys, NC);
-    ALLOC(d.list, NC * (int64_t)c->tune.list_capacity);
-    ALLOC(d.list_n, NC);
     ALLOC(d.sys_acc, (int64_t)c->n_sys * kTaskVals);
     ALLOC(d.tab_grad, (int64_t)T * T * 2);
     ALLOC(d.counts, 4);
@@ -100,7 +97,6 @@ nb_status allocate(nb_ctx *c)
     e = cudaMemset(d.tslot, 0, sizeof(int) * S);
     if (e == cudaSuccess) e = cudaMemset(d.status, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(d.counts, 0, sizeof(int) * 4);
-    if (e == cudaSuccess) e = cudaMemset(d.list_n, 0, sizeof(int) * NC);
     return cuda_status(e);
 }
 
@@ -389,17 +385,10 @@ nb_status nb_set_tuning(nb_ctx *ctx, const nb_tuning *t)
     if (!ctx || !t) return NB_ERR_INVALID_ARG;
     if (t->blocks_per_sm < 1 || t->blocks_per_sm > 8 || t->reserved != 0) return NB_ERR_INVALID_ARG;
     if (t->stage_capacity < 16 || t->stage_capacity > 512 || t->stage_capacity % 4) return NB_ERR_INVALID_ARG;
-    if (t->list_capacity < 64 || t->list_capacity > (1 << 16) || t->list_capacity % 4) return NB_ERR_INVALID_ARG;
-    if (ctx->smem_optin > 0 && force_smem_for(ctx->pp.n_types, t->stage_capacity) > (size_t)ctx->smem_optin)
+    if (t->list_capacity < 64 || t->list_capacity > 4096 || t->list_capacity % 4) return NB_ERR_INVALID_ARG;
+    if (ctx->smem_optin > 0 &&
+        force_smem_for(ctx->pp.n_types, t->stage_capacity, t->list_capacity, ctx->K) > (size_t)ctx->smem_optin)
         return NB_ERR_UNSUPPORTED;
-    if (t->list_capacity != ctx->tune.list_capacity) {
-        if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return NB_ERR_CUDA;
-        uint32_t *nl = nullptr;
-        if (dalloc(&nl, (size_t)ctx->clus_cap * t->list_capacity) != cudaSuccess) return NB_ERR_OOM;
-        cudaFree(ctx->d.list);
-        ctx->d.list = nl;
-        ctx->built = false;
-    }
     ctx->tune = *t;
     ctx->stage_cap = t->stage_capacity;
     return NB_OK;

@@ -1,6 +1,6 @@
 // nb_build.cu - cell-list construction: wrap, column binning, per-column
-// z-sort, cluster bounding boxes, sorted exclusion map and the cluster-pair
-// list.  Section "Molecular dynamics on the GPU": particles are binned
+// z-sort and cluster bounding boxes.  (Each cluster's pair list is built in
+// shared memory by the force kernel itself.)  Section "Molecular dynamics on the GPU": particles are binned
 // according to their coordinates, one particle per thread, with atomic
 // operations for concurrent updates of the cell arrays.  Here the bins are
 // x-y columns whose atoms are z-sorted and cut into 8-atom clusters, so the
@@ -167,143 +167,6 @@ __global__ void k_colsort(const int *__restrict__ col_count, const int *__restri
     }
 }
 
-// A4a: exclusion/1-4 partners in sorted-slot space.
-__global__ void k_exmap(int slot_cap, const int *__restrict__ counts, int K, const int *__restrict__ perm,
-                        const int *__restrict__ part_orig, const int *__restrict__ inv, int *__restrict__ ex_slot)
-{
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= slot_cap || s >= counts[0]) return;
-    int a = perm[s];
-    for (int k = 0; k < K; ++k) {
-        int v = -1;
-        if (a >= 0) {
-            int p = part_orig[(long long)a * K + k];
-            if (p >= 0) v = (inv[p >> 1] << 1) | (p & 1);
-        }
-        ex_slot[(long long)s * K + k] = v;
-    }
-}
-
-// A4b: cluster-pair list, one warp per cluster I.  Enumerates the columns
-// within reach of I's bounding box (with periodic images), tests every
-// cluster of those columns against I under each admissible z image, and
-// appends (J, shift codes, exclusion flag) for bounding-box gaps below the
-// cutoff (plus a rounding margin).
-__global__ void k_list(const SysDesc *__restrict__ sys, const int *__restrict__ counts,
-                       const float4 *__restrict__ bb,
-                       const int *__restrict__ clus_sys, const int *__restrict__ col_slot,
-                       const int *__restrict__ ex_slot, int K, float rcm, int cap,
-                       uint32_t *__restrict__ list, int *__restrict__ list_n, int *__restrict__ status)
-{
-    const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    const int n_clus = counts[1];
-    const float rcm2 = rcm * rcm;
-    const unsigned lt = (1u << lane) - 1u;
-    for (int I = gw; I < n_clus; I += nw) {
-        const SysDesc &S = sys[clus_sys[I]];
-        const float4 lo = bb[2 * I], hi = bb[2 * I + 1];
-        // distinct partner clusters of I (lanes 0..npc-1 of pcl)
-        int pcl = -1, npc = 0;
-        bool flag_all = false;
-        const int np = kCluster * K;
-        for (int b = 0; b < np; b += 32) {
-            int v = -1;
-            if (b + lane < np) {
-                int e = ex_slot[(long long)I * kCluster * K + b + lane];
-                if (e >= 0) v = (e >> 1) / kCluster;
-            }
-            unsigned peers = __match_any_sync(FULL, v);
-            bool leader = (v >= 0) && ((__ffs(peers) - 1) == lane);
-            // drop values already present
-            for (int m = 0; m < npc; ++m) {
-                int u = __shfl_sync(FULL, pcl, m);
-                if (u == v) leader = false;
-            }
-            unsigned bal = __ballot_sync(FULL, leader);
-            if (npc + __popc(bal) > 32) flag_all = true;
-            // append the new leaders to the lane-distributed list pcl
-            int p = npc;
-            for (unsigned b2 = bal; b2; b2 &= b2 - 1u, ++p) {
-                int vv = __shfl_sync(FULL, v, __ffs(b2) - 1);
-                if (lane == p) pcl = vv;
-            }
-            npc = min(32, npc + __popc(bal));
-        }
-        int cnt = 0;
-        const int cxa = max(-S.nx, (int)floorf((lo.x - rcm) * S.inv_w[0]));
-        const int cxb = min(2 * S.nx - 1, (int)floorf((hi.x + rcm) * S.inv_w[0]));
-        const int cya = max(-S.ny, (int)floorf((lo.y - rcm) * S.inv_w[1]));
-        const int cyb = min(2 * S.ny - 1, (int)floorf((hi.y + rcm) * S.inv_w[1]));
-        const bool zdn = (lo.z - rcm) < 0.0f;
-        const bool zup = (hi.z + rcm) >= S.L[2];
-        const int ncx = cxb - cxa + 1, ncand = ncx * (cyb - cya + 1);
-        // lanes over candidate columns; clusters of a column in lock-step
-        for (int c0 = 0; c0 < ncand; c0 += 32) {
-            const int c = c0 + lane;
-            const bool cv = c < ncand;
-            const int cy = cya + (cv ? c / ncx : 0), cx = cxa + (cv ? c % ncx : 0);
-            const int ccy = cy < 0 ? cy + S.ny : (cy >= S.ny ? cy - S.ny : cy);
-            const int ccx = cx < 0 ? cx + S.nx : (cx >= S.nx ? cx - S.nx : cx);
-            const int sy = cy < 0 ? 1 : (cy >= S.ny ? 2 : 0);
-            const int sx = cx < 0 ? 1 : (cx >= S.nx ? 2 : 0);
-            const float oy = sy == 1 ? -S.L[1] : (sy == 2 ? S.L[1] : 0.0f);
-            const float ox = sx == 1 ? -S.L[0] : (sx == 2 ? S.L[0] : 0.0f);
-            int jb = 0, nj = 0;
-            if (cv) {
-                const int col = S.col_begin + ccy * S.nx + ccx;
-                jb = col_slot[col] / kCluster;
-                nj = col_slot[col + 1] / kCluster - jb;
-            }
-            int maxj = nj;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) maxj = max(maxj, __shfl_xor_sync(FULL, maxj, o));
-            const uint32_t code_xy = ((uint32_t)sx << kShiftBit) | ((uint32_t)sy << (kShiftBit + 2));
-            for (int k0 = 0; k0 < maxj; k0 += 4) {
-                float4 jl[4], jh[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const bool v = k0 + u < nj;
-                    jl[u] = v ? bb[2 * (jb + k0 + u)] : make_float4(INFINITY, INFINITY, INFINITY, 0.0f);
-                    jh[u] = v ? bb[2 * (jb + k0 + u) + 1] : make_float4(INFINITY, INFINITY, INFINITY, 0.0f);
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    if (k0 + u >= maxj) break;
-                    const int J = jb + k0 + u;
-                    const bool v = k0 + u < nj;
-                    const float gx = fmaxf(fmaxf((jl[u].x + ox) - hi.x, lo.x - (jh[u].x + ox)), 0.0f);
-                    const float gy = fmaxf(fmaxf((jl[u].y + oy) - hi.y, lo.y - (jh[u].y + oy)), 0.0f);
-                    const float gxy = gx * gx + gy * gy;
-                    bool fl = flag_all;
-                    for (int m = 0; m < npc; ++m) fl |= (__shfl_sync(FULL, pcl, m) == J);
-#pragma unroll
-                    for (int sz = 0; sz < 3; ++sz) {
-                        const float oz = sz == 1 ? -S.L[2] : (sz == 2 ? S.L[2] : 0.0f);
-                        const float gz = fmaxf(fmaxf((jl[u].z + oz) - hi.z, lo.z - (jh[u].z + oz)), 0.0f);
-                        const bool zok = sz == 0 || (sz == 1 && zdn) || (sz == 2 && zup);
-                        const bool keep = v && zok && (gxy + gz * gz < rcm2);
-                        const unsigned bal = __ballot_sync(FULL, keep);
-                        if (keep) {
-                            const int p = cnt + __popc(bal & lt);
-                            const uint32_t ent = (uint32_t)J | code_xy | ((uint32_t)sz << (kShiftBit + 4)) |
-                                                 (fl ? kExclFlag : 0u);
-                            if (p < cap) list[(long long)I * cap + p] = ent;
-                        }
-                        cnt += __popc(bal);
-                    }
-                }
-            }
-        }
-        if (lane == 0) {
-            list_n[I] = min(cnt, cap);
-            if (cnt > cap) atomicOr(status, ST_CAPACITY);
-        }
-    }
-}
-
 cudaError_t launch_build(nb_ctx *ctx, const float *d_pos)
 {
     auto &d = ctx->d;
@@ -317,16 +180,6 @@ cudaError_t launch_build(nb_ctx *ctx, const float *d_pos)
     k_scatter<<<(N + tb - 1) / tb, tb, 0, st>>>(N, d.atom_col, d.col_fill, d.stage);
     k_colsort<<<ctx->n_cols, 128, 0, st>>>(d.col_count, d.col_slot, d.col_sys, d.stage, d.wpos, d.xyzq, d.tslot,
                                            d.perm, d.inv, d.bb, d.clus_sys);
-    const int S = (int)ctx->slot_cap;
-    k_exmap<<<(S + tb - 1) / tb, tb, 0, st>>>(S, d.counts, ctx->K, d.perm, d.part_orig, d.inv, d.ex_slot);
-    const int lw = 8;  // warps per block in the list kernel
-    int lblocks = (int)((ctx->clus_cap + lw - 1) / lw);
-    int lmax = ctx->num_sms * 16;
-    if (lblocks > lmax) lblocks = lmax;
-    if (lblocks < 1) lblocks = 1;
-    k_list<<<lblocks, lw * 32, 0, st>>>(d.sys, d.counts, d.bb, d.clus_sys, d.col_slot, d.ex_slot,
-                                        ctx->K, ctx->pp.rc + ctx->pp.list_margin, ctx->tune.list_capacity,
-                                        d.list, d.list_n, d.status);
     return cudaGetLastError();
 }
 

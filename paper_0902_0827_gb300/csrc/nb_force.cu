@@ -42,11 +42,11 @@ struct ForceArgs {
     const int *perm;
     const int *clus_sys;
     const float4 *bb;
-    const uint32_t *list;
-    const int *list_n;
-    int cap;
+    const int *col_slot;      // [C+1] padded slot offsets of the columns
+    const int *part_orig;     // [N*K] topology partners (orig << 1) | is14
+    const int *inv;           // [N] atom -> sorted slot
+    int cap;                  // list entries per cluster (shared memory)
     int scap;
-    const int *ex_slot;
     int K;
     const float2 *lj_tab;
     float *F;
@@ -75,8 +75,18 @@ __device__ __forceinline__ long long to_fixed(float v, int *status)
     return __float2ll_rn(v * 4294967296.0f);
 }
 
+constexpr int kMaxCand = 256;  // candidate columns of one cluster (with images)
+static_assert(kMaxCand == kCluster * 32, "the candidate scan gives one column to each thread of the block");
+
 struct ForceSmem {
     float2 *lj;
+    uint32_t *lst;             // this cluster's pair list [cap]
+    int *cjb, *cnj, *ccode;    // candidate columns: first cluster, clusters, image code [kMaxCand]
+    int *cpre;                 // exclusive prefix of cnj [kMaxCand + 1]
+    int *pslot;                // partner slots of the 8 atoms [8 * K] (slot << 1 | is14, -1)
+    int *pcl;                  // distinct partner clusters [8 * K]
+    int *misc;                 // [32]: npc, wcnt[24] ... (see build_list)
+    int *woff;                 // [32]
     uint32_t *ent;
     float4 *pos;
     int *typ;
@@ -96,11 +106,17 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p)
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-__host__ __device__ inline size_t force_smem_bytes(int T, int scap, int nwarps, bool adj = false)
+__host__ __device__ inline size_t list_smem_bytes(int cap, int K)
+{
+    return align16((size_t)cap * 4) + (size_t)kMaxCand * 4 * 3 + align16((size_t)(kMaxCand + 1) * 4) +
+           2 * align16((size_t)kCluster * K * 4) + 32 * 4 + 32 * 4;
+}
+
+__host__ __device__ inline size_t force_smem_bytes(int T, int scap, int nwarps, bool adj, int cap, int K)
 {
     size_t b = adj ? (size_t)scap * kCluster * 16 + (size_t)T * T * 16 + (size_t)T * T * 16 : 0;
+    b += list_smem_bytes(cap, K);
     b += align16((size_t)T * T * 8);
-    b += align16((size_t)scap * 4);
     b += (size_t)scap * kCluster * 16;
     b += (size_t)scap * kCluster * 4;
     b += (size_t)scap * 2 * 16;
@@ -110,10 +126,29 @@ __host__ __device__ inline size_t force_smem_bytes(int T, int scap, int nwarps, 
     return b;
 }
 
-__device__ __forceinline__ ForceSmem carve(unsigned char *smem, int T, int scap, int nwarps, int w, bool adj = false)
+__device__ __forceinline__ ForceSmem carve(unsigned char *smem, int T, int scap, int nwarps, int w, bool adj, int cap,
+                                           int K)
 {
     ForceSmem S;
     size_t off = 0;
+    S.lst = reinterpret_cast<uint32_t *>(smem + off);
+    off += align16((size_t)cap * 4);
+    S.cjb = reinterpret_cast<int *>(smem + off);
+    off += (size_t)kMaxCand * 4;
+    S.cnj = reinterpret_cast<int *>(smem + off);
+    off += (size_t)kMaxCand * 4;
+    S.ccode = reinterpret_cast<int *>(smem + off);
+    off += (size_t)kMaxCand * 4;
+    S.cpre = reinterpret_cast<int *>(smem + off);
+    off += align16((size_t)(kMaxCand + 1) * 4);
+    S.pslot = reinterpret_cast<int *>(smem + off);
+    off += align16((size_t)kCluster * K * 4);
+    S.pcl = reinterpret_cast<int *>(smem + off);
+    off += align16((size_t)kCluster * K * 4);
+    S.misc = reinterpret_cast<int *>(smem + off);
+    off += 32 * 4;
+    S.woff = reinterpret_cast<int *>(smem + off);
+    off += 32 * 4;
     S.gj = S.ljd = nullptr;
     S.tacc = nullptr;
     if (adj) {
@@ -126,8 +161,7 @@ __device__ __forceinline__ ForceSmem carve(unsigned char *smem, int T, int scap,
     }
     S.lj = reinterpret_cast<float2 *>(smem + off);
     off += align16((size_t)T * T * 8);
-    S.ent = reinterpret_cast<uint32_t *>(smem + off);
-    off += align16((size_t)scap * 4);
+    S.ent = nullptr;  // points into lst, per staged chunk
     S.pos = reinterpret_cast<float4 *>(smem + off);
     off += (size_t)scap * kCluster * 16;
     S.typ = reinterpret_cast<int *>(smem + off);
@@ -160,19 +194,12 @@ __device__ __forceinline__ void cp_async_wait_all()
 // Slot of atom k of staged entry e (swizzle by e, conflict-free lane access).
 __device__ __forceinline__ int swz(int e, int k) { return e * kCluster + (k ^ (e & (kCluster - 1))); }
 
-// Stage the chunk [c0, c0 + n) of cluster I's list, then for every listed
-// cluster J its 8 coordinates+charges, 8 types and bounding box, with
-// asynchronous copies issued by every thread of the block.
+// Stage, for the n list entries at S.ent, every listed cluster J's 8
+// coordinates+charges, 8 types, bounding box and (adjoint) 8 dL/dF vectors
+// with asynchronous copies issued by every thread of the block.
 template <bool ADJ>
-__device__ __forceinline__ void stage_chunk(const ForceArgs &A, const ForceSmem &S, int I, int c0, int n)
+__device__ __forceinline__ void stage_chunk(const ForceArgs &A, const ForceSmem &S, int n)
 {
-    const uint4 *src = reinterpret_cast<const uint4 *>(A.list + (long long)I * A.cap + c0);
-    const int nent16 = (n + 3) >> 2;
-    for (int p = threadIdx.x; p < nent16; p += blockDim.x) cp_async16(reinterpret_cast<uint4 *>(S.ent) + p, src + p);
-    cp_async_wait_all();
-    __syncthreads();
-    // per entry: 8 coordinates (16 B each), 8 types (4 B each), 2 box corners
-    // (16 B each) and, for the adjoint, 8 dL/dF vectors (16 B each)
     for (int p = threadIdx.x; p < n * kCluster; p += blockDim.x) {
         const int e = p >> 3, k = p & 7;
         const long long j = (long long)(S.ent[e] & kJMask) * kCluster + k;
@@ -186,6 +213,170 @@ __device__ __forceinline__ void stage_chunk(const ForceArgs &A, const ForceSmem 
     }
     cp_async_wait_all();
     __syncthreads();
+}
+
+// Build cluster I's pair list in shared memory (the paper's neighbour cells
+// within R of the current cell, at cluster granularity): every candidate
+// column within reach of I's bounding box (with periodic images), every
+// cluster J of those columns, under up to three z images; an entry is kept
+// when the bounding-box gap is below rc (plus a rounding margin).  Entries:
+// J | image code per axis (1: x_j - L, 2: x_i - L) | flag when J holds a
+// topology partner of I.  Threads spread over the (column, cluster) pairs;
+// hits are compacted in (round, z image, warp, lane) order, so the list and
+// every sum built from it are deterministic.  Also fills the partner slots of
+// I's atoms.  Returns the list length (all threads).
+__device__ int build_list(const ForceArgs &A, const ForceSmem &S, int I, const SysDesc &SD)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nthr = blockDim.x;
+    const unsigned lt = (1u << lane) - 1u;
+    const float4 lo = A.bb[2 * I], hi = A.bb[2 * I + 1];
+    const float rcm = A.P.rc + A.P.list_margin, rcm2 = A.P.rcm2;
+    const int cxa = max(-SD.nx, (int)floorf((lo.x - rcm) * SD.inv_w[0]));
+    const int cxb = min(2 * SD.nx - 1, (int)floorf((hi.x + rcm) * SD.inv_w[0]));
+    const int cya = max(-SD.ny, (int)floorf((lo.y - rcm) * SD.inv_w[1]));
+    const int cyb = min(2 * SD.ny - 1, (int)floorf((hi.y + rcm) * SD.inv_w[1]));
+    const bool zdn = (lo.z - rcm) < 0.0f, zup = (hi.z + rcm) >= SD.L[2];
+    const int ncx = cxb - cxa + 1;
+    int ncand = ncx * (cyb - cya + 1);
+    if (ncand > kMaxCand) {
+        if (tid == 0) atomicOr(A.status, ST_CAPACITY);
+        ncand = kMaxCand;
+    }
+    // partner slots of the 8 atoms of I
+    const int npk = kCluster * A.K;
+    for (int t = tid; t < npk; t += nthr) {
+        const int a = A.perm[I * kCluster + t / A.K];
+        int v = -1;
+        if (a >= 0) {
+            const int p = A.part_orig[(long long)a * A.K + t % A.K];
+            if (p >= 0) v = (A.inv[p >> 1] << 1) | (p & 1);
+        }
+        S.pslot[t] = v;
+    }
+    // candidate columns
+    for (int c = tid; c < kMaxCand; c += nthr) {
+        int jb = 0, nj = 0, code = 0;
+        if (c < ncand) {
+            const int cy = cya + c / ncx, cx = cxa + c % ncx;
+            const int ccy = cy < 0 ? cy + SD.ny : (cy >= SD.ny ? cy - SD.ny : cy);
+            const int ccx = cx < 0 ? cx + SD.nx : (cx >= SD.nx ? cx - SD.nx : cx);
+            const int sy = cy < 0 ? 1 : (cy >= SD.ny ? 2 : 0);
+            const int sx = cx < 0 ? 1 : (cx >= SD.nx ? 2 : 0);
+            const int col = SD.col_begin + ccy * SD.nx + ccx;
+            jb = A.col_slot[col] / kCluster;
+            nj = A.col_slot[col + 1] / kCluster - jb;
+            code = sx | (sy << 2);
+        }
+        S.cjb[c] = jb;
+        S.cnj[c] = nj;
+        S.ccode[c] = code;
+    }
+    __syncthreads();
+    // exclusive scan of the column sizes (kMaxCand == blockDim.x) and the
+    // distinct partner clusters (warp 0)
+    {
+        const int v = S.cnj[tid];
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) S.woff[w] = x;
+        __syncthreads();
+        int base = 0;
+        for (int k = 0; k < w; ++k) base += S.woff[k];
+        S.cpre[tid] = base + x - v;
+        if (tid == nthr - 1) S.cpre[kMaxCand] = base + x;
+        if (w == 0) {
+            int npc = 0;
+            for (int b = 0; b < npk; b += 32) {
+                int v2 = -1;
+                if (b + lane < npk && S.pslot[b + lane] >= 0) v2 = (S.pslot[b + lane] >> 1) / kCluster;
+                const unsigned peers = __match_any_sync(FULL, v2);
+                bool leader = v2 >= 0 && (__ffs(peers) - 1) == lane;
+                for (int m = 0; m < npc; ++m)
+                    if (S.pcl[m] == v2) leader = false;
+                const unsigned bal = __ballot_sync(FULL, leader);
+                if (leader) S.pcl[npc + __popc(bal & lt)] = v2;
+                npc += __popc(bal);
+                __syncwarp();
+            }
+            if (lane == 0) S.misc[0] = npc;
+        }
+        __syncthreads();
+    }
+    const int P = S.cpre[kMaxCand];
+    const int npc = S.misc[0];
+    int nE = 0;
+    for (int p0 = 0; p0 < P; p0 += nthr) {
+        const int p = p0 + tid;
+        const bool valid = p < P;
+        bool h0 = false, h1 = false, h2 = false;
+        uint32_t base_ent = 0u;
+        if (valid) {
+            int c = 0;
+            for (int step = kMaxCand / 2; step >= 1; step >>= 1)
+                if (c + step < ncand && S.cpre[c + step] <= p) c += step;
+            const int J = S.cjb[c] + (p - S.cpre[c]);
+            const int code = S.ccode[c];
+            const int sx = code & 3, sy = code >> 2;
+            const float ox = sx == 1 ? -SD.L[0] : (sx == 2 ? SD.L[0] : 0.0f);
+            const float oy = sy == 1 ? -SD.L[1] : (sy == 2 ? SD.L[1] : 0.0f);
+            const float4 jl = A.bb[2 * J], jh = A.bb[2 * J + 1];
+            const float gx = fmaxf(fmaxf((jl.x + ox) - hi.x, lo.x - (jh.x + ox)), 0.0f);
+            const float gy = fmaxf(fmaxf((jl.y + oy) - hi.y, lo.y - (jh.y + oy)), 0.0f);
+            const float gxy = gx * gx + gy * gy;
+            bool fl = false;
+            for (int m = 0; m < npc; ++m) fl |= (S.pcl[m] == J);
+            base_ent = (uint32_t)J | ((uint32_t)code << kShiftBit) | (fl ? kExclFlag : 0u);
+            const float gz0 = fmaxf(fmaxf(jl.z - hi.z, lo.z - jh.z), 0.0f);
+            const float gz1 = fmaxf(fmaxf((jl.z - SD.L[2]) - hi.z, lo.z - (jh.z - SD.L[2])), 0.0f);
+            const float gz2 = fmaxf(fmaxf((jl.z + SD.L[2]) - hi.z, lo.z - (jh.z + SD.L[2])), 0.0f);
+            h0 = gxy + gz0 * gz0 < rcm2;
+            h1 = zdn && (gxy + gz1 * gz1 < rcm2);
+            h2 = zup && (gxy + gz2 * gz2 < rcm2);
+        }
+        const unsigned b0 = __ballot_sync(FULL, h0), b1 = __ballot_sync(FULL, h1), b2 = __ballot_sync(FULL, h2);
+        if (lane == 0) {
+            S.misc[1 + w] = __popc(b0);
+            S.misc[9 + w] = __popc(b1);
+            S.misc[17 + w] = __popc(b2);
+        }
+        __syncthreads();
+        if (w == 0) {  // exclusive scan of the 24 (z image, warp) counts
+            const int v = lane < 24 ? S.misc[1 + lane] : 0;
+            int x = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(FULL, x, o);
+                if (lane >= o) x += y;
+            }
+            S.woff[lane] = x - v;  // lanes >= 24 add nothing: woff[24] is the total
+        }
+        __syncthreads();
+        const int wb0 = nE + S.woff[w], wb1 = nE + S.woff[8 + w], wb2 = nE + S.woff[16 + w];
+        if (h0) {
+            const int q = wb0 + __popc(b0 & lt);
+            if (q < A.cap) S.lst[q] = base_ent;
+        }
+        if (h1) {
+            const int q = wb1 + __popc(b1 & lt);
+            if (q < A.cap) S.lst[q] = base_ent | (1u << (kShiftBit + 4));
+        }
+        if (h2) {
+            const int q = wb2 + __popc(b2 & lt);
+            if (q < A.cap) S.lst[q] = base_ent | (2u << (kShiftBit + 4));
+        }
+        nE += S.woff[24];
+        __syncthreads();
+    }
+    if (nE > A.cap) {
+        if (tid == 0) atomicOr(A.status, ST_CAPACITY);
+        nE = A.cap;
+    }
+    return nE;
 }
 
 struct Acc {
@@ -373,7 +564,7 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
     const int w = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    const ForceSmem S = carve(smem, T, A.scap, nwarps, w, ADJ);
+    const ForceSmem S = carve(smem, T, A.scap, nwarps, w, ADJ, A.cap, A.K);
     for (int k = threadIdx.x; k < T * T; k += blockDim.x) S.lj[k] = A.lj_tab[k];
     if (ADJ) {
         for (int k = threadIdx.x; k < T * T; k += blockDim.x) {
@@ -439,15 +630,18 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
         } else {
             ia.gix = ia.giy = ia.giz = ia.gE_lj = ia.gE_c = 0.0f;
         }
-        const int pe = lane < A.K ? A.ex_slot[(long long)islot * A.K + lane] : -1;
         AccT acc;
         memset(&acc, 0, sizeof(acc));
-        const int nE = A.list_n[I];
+        __syncthreads();  // the list and staging buffers are free
+        const int nE = build_list(A, S, I, SD);
+        const int pe = lane < A.K ? S.pslot[w * A.K + lane] : -1;
 
         for (int c0 = 0; c0 < nE; c0 += A.scap) {
             const int nC = min(A.scap, nE - c0);
-            __syncthreads();  // the staging buffers are free
-            stage_chunk<ADJ>(A, S, I, c0, nC);
+            if (c0 > 0) __syncthreads();  // the staging buffers are free
+            ForceSmem Sc = S;
+            Sc.ent = S.lst + c0;
+            stage_chunk<ADJ>(A, Sc, nC);
             if (!iv) continue;
             // (1) prune staged clusters against this atom
             int ns = 0;
@@ -455,7 +649,7 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
                 const int e = e0 + lane;
                 bool keep = false;
                 if (e < nC) {
-                    const uint32_t ent = S.ent[e];
+                    const uint32_t ent = Sc.ent[e];
                     const int cx = (ent >> kShiftBit) & 3, cy = (ent >> (kShiftBit + 2)) & 3,
                               cz = (ent >> (kShiftBit + 4)) & 3;
                     const float ox = cx == 1 ? -Lx : (cx == 2 ? Lx : 0.0f);
@@ -479,7 +673,7 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
                 const int si = s0 + lane;
                 const bool sv = si < ns;
                 const int e = sv ? (int)S.surv[si] : 0;
-                const uint32_t ent = S.ent[e];
+                const uint32_t ent = Sc.ent[e];
                 const int J = (int)(ent & kJMask);
                 const int cx = (ent >> kShiftBit) & 3, cy = (ent >> (kShiftBit + 2)) & 3,
                           cz = (ent >> (kShiftBit + 4)) & 3;
@@ -531,7 +725,7 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
                 tail += total;
                 __syncwarp();
                 while (tail - head >= 32) {
-                    eval_item<ADJ, EWALD, VIRIAL, DEBUG>(A, S, Lx, Ly, Lz, ia, S.ring[(head + lane) & (kRing - 1)],
+                    eval_item<ADJ, EWALD, VIRIAL, DEBUG>(A, Sc, Lx, Ly, Lz, ia, S.ring[(head + lane) & (kRing - 1)],
                                                          true, acc);
                     head += 32;
                 }
@@ -540,7 +734,7 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
             if (tail > head) {  // partial step before the staged data is replaced
                 const int n = tail - head;
                 const uint32_t item = lane < n ? S.ring[(head + lane) & (kRing - 1)] : 0u;
-                eval_item<ADJ, EWALD, VIRIAL, DEBUG>(A, S, Lx, Ly, Lz, ia, item, lane < n, acc);
+                eval_item<ADJ, EWALD, VIRIAL, DEBUG>(A, Sc, Lx, Ly, Lz, ia, item, lane < n, acc);
             }
             __syncwarp();
         }
@@ -657,7 +851,7 @@ template <bool ADJ, bool EWALD, bool VIRIAL, bool DEBUG>
 static void launch_force_t(nb_ctx *ctx, const ForceArgs &A)
 {
     const int nw = kCluster;
-    const size_t smem = force_smem_bytes(A.P.n_types, A.scap, nw, ADJ);
+    const size_t smem = force_smem_bytes(A.P.n_types, A.scap, nw, ADJ, A.cap, A.K);
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(k_force<ADJ, EWALD, VIRIAL, DEBUG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -684,11 +878,11 @@ static ForceArgs make_args(nb_ctx *ctx)
     A.perm = d.perm;
     A.clus_sys = d.clus_sys;
     A.bb = d.bb;
-    A.list = d.list;
-    A.list_n = d.list_n;
+    A.col_slot = d.col_slot;
+    A.part_orig = d.part_orig;
+    A.inv = d.inv;
     A.cap = ctx->tune.list_capacity;
     A.scap = ctx->stage_cap;
-    A.ex_slot = d.ex_slot;
     A.K = ctx->K;
     A.lj_tab = d.lj_tab;
     A.sys_acc = d.sys_acc;
@@ -746,7 +940,7 @@ cudaError_t launch_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, con
     return cudaGetLastError();
 }
 
-size_t force_smem_for(int T, int scap) { return force_smem_bytes(T, scap, kCluster, true); }
+size_t force_smem_for(int T, int scap, int cap, int K) { return force_smem_bytes(T, scap, kCluster, true, cap, K); }
 
 cudaError_t launch_adjoint_tile(nb_ctx *ctx, const double *d_dLdE, float *d_dpos, float *d_dq)
 {

@@ -97,11 +97,8 @@ struct DevBuffers {
     int *tslot = nullptr;            // [S] sorted types
     int *perm = nullptr;             // [S] slot -> atom (-1 padding)
     int *inv = nullptr;              // [N] atom -> slot
-    int *ex_slot = nullptr;          // [S*K] partner slot << 1 | is14, -1 pad
     float4 *bb = nullptr;            // [NC*2] cluster bounding boxes (lo, hi interleaved)
     int *clus_sys = nullptr;         // [NC] system of each cluster
-    uint32_t *list = nullptr;        // [NC*cap] cluster-pair entries
-    int *list_n = nullptr;           // [NC]
     long long *sys_acc = nullptr;    // [n_sys*kTaskVals] per-system fixed-point energy/virial
     long long *tab_grad = nullptr;   // [T*T*2] adjoint dL/dsig_ab, dL/deps_ab (fixed point, one ordered half)
     int *counts = nullptr;           // [4]: n_slots, n_clusters, pair counters
@@ -163,7 +160,7 @@ __device__ __forceinline__ float wrap_coord(float x, float L)
 cudaError_t launch_build(nb_ctx *ctx, const float *d_pos);
 cudaError_t launch_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type,
                           float *d_F, double *d_energy, double *d_virial, bool debug_pairs);
-size_t force_smem_for(int T, int scap);
+size_t force_smem_for(int T, int scap, int cap, int K);
 cudaError_t launch_pack(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type);
 cudaError_t launch_type_grad(nb_ctx *ctx, const double *gsig_tab, const double *geps_tab, double *gsig, double *geps);
 cudaError_t launch_adjoint_tile(nb_ctx *ctx, const double *d_dLdE, float *d_dpos, float *d_dq);

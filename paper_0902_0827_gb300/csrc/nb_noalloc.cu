@@ -9,7 +9,7 @@
 // runs the same binning and force kernels as nb_build_cells + nb_forces for
 // one system of at most NB_NOALLOC_MAX_ATOMS atoms, with every scratch buffer
 // carved from one file-scope device array (g_noalloc_scratch below, about
-// 4.4 MiB).  That array exists on every GPU that loads this library, for as
+// 0.8 MiB).  That array exists on every GPU that loads this library, for as
 // long as the library stays loaded.
 //
 // In host code the name g_noalloc_scratch only stands for the device symbol;
@@ -61,12 +61,9 @@ constexpr size_t oXyzq = oStage + a256(4ull * kSlots);
 constexpr size_t oTslot = oXyzq + a256(16ull * kSlots);
 constexpr size_t oPerm = oTslot + a256(4ull * kSlots);
 constexpr size_t oInv = oPerm + a256(4ull * kSlots);
-constexpr size_t oExSlot = oInv + a256(4ull * kMaxAtoms);
-constexpr size_t oBb = oExSlot + a256(4ull * kSlots * kMaxPartners);
+constexpr size_t oBb = oInv + a256(4ull * kMaxAtoms);
 constexpr size_t oClusSys = oBb + a256(32ull * kClus);
-constexpr size_t oList = oClusSys + a256(4ull * kClus);
-constexpr size_t oListN = oList + a256(4ull * kClus * kListCap);
-constexpr size_t oSysAcc = oListN + a256(4ull * kClus);
+constexpr size_t oSysAcc = oClusSys + a256(4ull * kClus);
 constexpr size_t oCounts = oSysAcc + a256(8ull * kTaskVals);
 constexpr size_t oStatus = oCounts + a256(16);
 constexpr size_t oLj = oStatus + a256(16);
@@ -184,11 +181,8 @@ extern "C" nb_status nb_forces_noalloc(const nb_params *params, const float *d_p
     d.tslot = at<int>(base, oTslot);
     d.perm = at<int>(base, oPerm);
     d.inv = at<int>(base, oInv);
-    d.ex_slot = at<int>(base, oExSlot);
     d.bb = at<float4>(base, oBb);
     d.clus_sys = at<int>(base, oClusSys);
-    d.list = at<uint32_t>(base, oList);
-    d.list_n = at<int>(base, oListN);
     d.sys_acc = at<long long>(base, oSysAcc);
     d.counts = at<int>(base, oCounts);
     d.status = at<int>(base, oStatus);
