@@ -103,8 +103,9 @@ typedef struct {
     int32_t blocks_per_sm;  /* blocks per SM of the persistent force grid, 1..8 */
     int32_t stage_capacity; /* cluster-pair entries staged in shared memory per block pass,
                                16..512, multiple of 4 (longer lists are processed in chunks) */
-    int32_t list_capacity;  /* cluster-pair entries of one cluster's list, built in shared
-                               memory by the force kernel, 64..4096, multiple of 4 */
+    int32_t list_capacity;  /* entries of each half of a cluster's pair list (the half the
+                               forward kernel visits, and the other half), 64..65536,
+                               multiple of 4 */
     int32_t reserved;       /* must be 0 */
 } nb_tuning;
 
@@ -183,10 +184,11 @@ nb_status nb_set_stream(nb_ctx *ctx, void *cuda_stream);
 void nb_destroy(nb_ctx *ctx);
 
 /* nb_set_tuning / nb_get_tuning - read or change the launch configuration;
- * takes effect at the next force or adjoint launch (allowed between captures,
- * no reallocation).  Errors: NB_ERR_INVALID_ARG for values out of range,
- * NB_ERR_UNSUPPORTED when the shared-memory footprint of the force kernel
- * would exceed the device limit. */
+ * takes effect at the next launch.  A changed list_capacity reallocates the
+ * pair lists (synchronises the stream; not allowed during stream capture) and
+ * requires a new nb_build_cells.  Errors: NB_ERR_INVALID_ARG for values out of
+ * range, NB_ERR_UNSUPPORTED when the shared-memory footprint of the force
+ * kernel would exceed the device limit, NB_ERR_OOM. */
 nb_status nb_set_tuning(nb_ctx *ctx, const nb_tuning *t);
 nb_status nb_get_tuning(nb_ctx *ctx, nb_tuning *t);
 
@@ -206,8 +208,8 @@ nb_status nb_debug_cells(nb_ctx *ctx, int32_t *h_perm, int64_t *n_slots,
  * build and copy out every evaluated pair inside the cutoff and not excluded,
  * as original atom indices (i < j), into h_ij [cap*2]; *n receives the total
  * count of such unique pairs (may exceed cap) and *n_ordered the number of
- * ordered evaluations (2 * n when every pair is seen from both atoms).
- * Synchronous. */
+ * pair evaluations of the forward kernel (equal to n: it evaluates every
+ * unique pair once and applies the force to both atoms).  Synchronous. */
 nb_status nb_debug_pairs(nb_ctx *ctx, int32_t *h_ij, int64_t cap, int64_t *n, int64_t *n_ordered);
 
 /* nb_set_profiling - when on != 0, every later force-kernel launch is
@@ -228,7 +230,7 @@ nb_status nb_get_profile(nb_ctx *ctx, double *force_ms, int64_t *launches);
  *   d_pos, d_q, d_type, d_F, d_energy [2], d_virial [6]: as for nb_forces
  *            (d_energy / d_virial may be NULL);
  *   cuda_stream: the stream the work runs on.
- * All scratch lives in one static device array of about 0.8 MiB that every
+ * All scratch lives in one static device array of about 4.5 MiB that every
  * GPU loading this library holds until the library is unloaded; it bounds
  * the system to NB_NOALLOC_MAX_ATOMS atoms and NB_NOALLOC_MAX_COLUMNS x-y
  * columns (NB_ERR_TOO_LARGE otherwise).  The call allocates nothing (no

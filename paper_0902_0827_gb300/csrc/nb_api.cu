@@ -35,7 +35,7 @@ void free_all(nb_ctx *c)
     auto &d = c->d;
     void *ptrs[] = {d.sys, d.atom_sys, d.atom_col, d.wpos, d.part_orig, d.col_sys, d.col_count, d.col_fill,
                     d.col_slot, d.stage, d.xyzq, d.tslot, d.perm, d.inv, d.bb,
-                    d.clus_sys, d.sys_acc, d.tab_grad, d.counts, d.status, d.lj_tab,
+                    d.clus_sys, d.sys_acc, d.facc, d.list, d.list_n, d.pslot, d.zbin, d.tab_grad, d.counts, d.status, d.lj_tab,
                     d.dbg_n, d.dbg_ij, d.scratch_f, d.scratch_g, d.lj_d, d.gslot, d.eps_type};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -84,6 +84,11 @@ nb_status allocate(nb_ctx *c)
     ALLOC(d.bb, NC * 2);
     ALLOC(d.clus_sys, NC);
     ALLOC(d.sys_acc, (int64_t)c->n_sys * kTaskVals);
+    ALLOC(d.facc, S * 3);
+    ALLOC(d.list, NC * 2 * c->list_cap);
+    ALLOC(d.list_n, NC * 2);
+    ALLOC(d.pslot, S * c->K);
+    ALLOC(d.zbin, c->zb_total);
     ALLOC(d.tab_grad, (int64_t)T * T * 2);
     ALLOC(d.counts, 4);
     ALLOC(d.status, 1);
@@ -164,17 +169,24 @@ nb_status nb_create_batch(int32_t n_sys, const nb_params *params, void *cuda_str
     // systems, columns
     c->sys_h.resize(n_sys);
     int col = 0, atom = 0;
+    int64_t zb = 0;
     std::vector<int> atom_sys(N), col_sys;
     for (int s = 0; s < n_sys; ++s) {
         const nb_params &p = params[s];
         SysDesc &S = c->sys_h[s];
-        init_sysdesc(p, S, atom, col);
+        if (zb > 0x7fffffff) {
+            delete c;
+            return NB_ERR_TOO_LARGE;
+        }
+        init_sysdesc(p, S, atom, col, (int)zb);
+        zb += zbin_entries(S);
         for (int a = 0; a < p.n_atoms; ++a) atom_sys[atom + a] = s;
         for (int k = 0; k < S.nx * S.ny; ++k) col_sys.push_back(s);
         atom += p.n_atoms;
         col += S.nx * S.ny;
     }
     c->n_cols = col;
+    c->zb_total = zb;
     c->slot_cap = N + (int64_t)(kCluster - 1) * col;
     c->slot_cap = (c->slot_cap + kCluster - 1) / kCluster * kCluster;
     c->clus_cap = c->slot_cap / kCluster;
@@ -215,10 +227,11 @@ nb_status nb_create_batch(int32_t n_sys, const nb_params *params, void *cuda_str
         for (size_t k = 0; k < part[a].size(); ++k) part_flat[a * K + k] = part[a][k];
     // tuning defaults
     c->tune.blocks_per_sm = 3;
-    c->tune.stage_capacity = 160;
+    c->tune.stage_capacity = 96;
     c->tune.list_capacity = 512;
     c->tune.reserved = 0;
     c->stage_cap = c->tune.stage_capacity;
+    c->list_cap = c->tune.list_capacity;
     int smem_optin = 0;
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
     c->smem_optin = smem_optin;
@@ -385,10 +398,19 @@ nb_status nb_set_tuning(nb_ctx *ctx, const nb_tuning *t)
     if (!ctx || !t) return NB_ERR_INVALID_ARG;
     if (t->blocks_per_sm < 1 || t->blocks_per_sm > 8 || t->reserved != 0) return NB_ERR_INVALID_ARG;
     if (t->stage_capacity < 16 || t->stage_capacity > 512 || t->stage_capacity % 4) return NB_ERR_INVALID_ARG;
-    if (t->list_capacity < 64 || t->list_capacity > 4096 || t->list_capacity % 4) return NB_ERR_INVALID_ARG;
-    if (ctx->smem_optin > 0 &&
-        force_smem_for(ctx->pp.n_types, t->stage_capacity, t->list_capacity, ctx->K) > (size_t)ctx->smem_optin)
+    if (t->list_capacity < 64 || t->list_capacity > 65536 || t->list_capacity % 4) return NB_ERR_INVALID_ARG;
+    if (ctx->smem_optin > 0 && force_smem_for(ctx->pp.n_types, t->stage_capacity, ctx->K) > (size_t)ctx->smem_optin)
         return NB_ERR_UNSUPPORTED;
+    if (t->list_capacity != ctx->list_cap) {
+        // new list storage: the lists of the last build are gone
+        uint32_t *nl = nullptr;
+        if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return NB_ERR_CUDA;
+        if (dalloc(&nl, (size_t)ctx->clus_cap * 2 * t->list_capacity) != cudaSuccess) return NB_ERR_OOM;
+        cudaFree(ctx->d.list);
+        ctx->d.list = nl;
+        ctx->list_cap = t->list_capacity;
+        ctx->built = false;
+    }
     ctx->tune = *t;
     ctx->stage_cap = t->stage_capacity;
     return NB_OK;

@@ -1,12 +1,16 @@
 // nb_build.cu - cell-list construction: wrap, column binning, per-column
-// z-sort and cluster bounding boxes.  (Each cluster's pair list is built in
-// shared memory by the force kernel itself.)  Section "Molecular dynamics on the GPU": particles are binned
-// according to their coordinates, one particle per thread, with atomic
-// operations for concurrent updates of the cell arrays.  Here the bins are
-// x-y columns whose atoms are z-sorted and cut into 8-atom clusters, so the
-// force kernel can prune whole clusters by bounding box.
+// z-sort, cluster bounding boxes and the cluster-pair lists.  Section
+// "Molecular dynamics on the GPU": particles are binned according to their
+// coordinates, one particle per thread, with atomic operations for concurrent
+// updates of the cell arrays; the force kernel then visits the neighbour
+// cells within the cutoff.  Here the bins are x-y columns whose atoms are
+// z-sorted and cut into 8-atom clusters, and each cluster gets the list of
+// clusters whose bounding boxes come within the cutoff, so the force kernel
+// can stage exactly those.
 #include <cuda_runtime.h>
 #include <math.h>
+
+#include <algorithm>
 
 #include "nb_internal.cuh"
 
@@ -106,12 +110,13 @@ __global__ void k_scatter(int n, const int *__restrict__ atom_col, int *__restri
 constexpr int kSortSmem = 1024;  // atoms per column sorted from shared memory
 
 // A3b: one block per column: rank sort by (z, atom index), write the sorted
-// slot arrays and padding, then the cluster bounding boxes.
+// slot arrays and padding, the cluster bounding boxes and the column's z-bin
+// index (the clusters are z-sorted, so their z_lo and z_hi never decrease).
 __global__ void k_colsort(const int *__restrict__ col_count, const int *__restrict__ col_slot,
-                          const int *__restrict__ col_sys, const int *__restrict__ stage,
-                          const float4 *__restrict__ wpos, float4 *__restrict__ xyzq, int *__restrict__ tslot,
-                          int *__restrict__ perm, int *__restrict__ inv, float4 *__restrict__ bb,
-                          int *__restrict__ clus_sys)
+                          const int *__restrict__ col_sys, const SysDesc *__restrict__ sys,
+                          const int *__restrict__ stage, const float4 *__restrict__ wpos, float4 *__restrict__ xyzq,
+                          int *__restrict__ tslot, int *__restrict__ perm, int *__restrict__ inv,
+                          float4 *__restrict__ bb, int *__restrict__ clus_sys, int2 *__restrict__ zbin)
 {
     __shared__ float sz[kSortSmem];
     __shared__ int sid[kSortSmem];
@@ -165,6 +170,210 @@ __global__ void k_colsort(const int *__restrict__ col_count, const int *__restri
         bb[2 * I + 1] = make_float4(hx, hy, hz, 0.0f);
         clus_sys[I] = col_sys[c];
     }
+    __syncthreads();
+    // z-bin index: for b = 0..nzb, (first cluster with z_hi >= b dz, first
+    // cluster with z_lo > (b + 1) dz), by binary search over the column
+    const SysDesc &S = sys[col_sys[c]];
+    const float4 *cb = bb + 2ll * (base / kCluster);
+    int2 *zt = zbin + S.zb_begin + (long long)(c - S.col_begin) * (S.nzb + 1);
+    for (int b = threadIdx.x; b <= S.nzb; b += blockDim.x) {
+        const float z0 = (float)b * S.dz, z1 = (float)(b + 1) * S.dz;
+        int lo = 0, hi = nclus;  // first q with cb[q].hi.z >= z0
+        while (lo < hi) {
+            const int m = (lo + hi) >> 1;
+            if (cb[2 * m + 1].z >= z0) hi = m;
+            else lo = m + 1;
+        }
+        int lo2 = 0, hi2 = nclus;  // first q with cb[q].lo.z > z1
+        while (lo2 < hi2) {
+            const int m = (lo2 + hi2) >> 1;
+            if (cb[2 * m].z > z1) hi2 = m;
+            else lo2 = m + 1;
+        }
+        zt[b] = make_int2(lo, lo2);
+    }
+}
+
+// Opposite periodic image of a list entry's shift code: 1 <-> 2 on every axis.
+__device__ __forceinline__ uint32_t opposite_code(uint32_t c) { return ((c & 0x15u) << 1) | ((c & 0x2Au) >> 1); }
+
+// Half list for Newton's third law: of the two entries (I, J, c) and
+// (J, I, opposite c) of one cluster pair exactly one is kept, chosen by a
+// checkerboard on the indices so that every cluster keeps about half of its
+// neighbours; of a cluster's own periodic images the smaller code of each
+// opposite pair, and the direct self entry (whose pairs j > i the force kernel
+// takes).
+__device__ __forceinline__ bool keep_half(int I, int J, uint32_t code)
+{
+    if (J == I) return code == 0u || code < opposite_code(code);
+    return ((I ^ J) & 1) ? (I < J) : (I > J);
+}
+
+// A4: cluster-pair lists, one warp per cluster I.  The columns within reach
+// of I's bounding box (with periodic images) go to the lanes.  Clusters of a
+// column are z-sorted, so the ones whose z-range (under the z images -L, 0,
+// +L, concatenated as virtual indices -nj..2nj-1) comes within the cutoff of
+// I form one window per column; the windows of all lanes are flattened and
+// every candidate (J, image) is tested by bounding-box gap < rc + margin.
+// Kept entries go to the half list (Newton's third law, used by the forward
+// kernel) or to the other half (the adjoint visits both), each compacted in
+// (column round, candidate round, lane) order, so the lists are
+// deterministic.  Also writes the partner slots of I's atoms and flags the
+// entries whose cluster holds a topology partner of I.
+__global__ void __launch_bounds__(256) k_list(const SysDesc *__restrict__ sys, const int *__restrict__ counts,
+                                              const float4 *__restrict__ bb, const int *__restrict__ clus_sys,
+                                              const int *__restrict__ col_slot, const int2 *__restrict__ zbin,
+                                              const int *__restrict__ perm,
+                                              const int *__restrict__ part_orig, const int *__restrict__ inv, int K,
+                                              float rcm, int cap, uint32_t *__restrict__ list,
+                                              int *__restrict__ list_n, int *__restrict__ pslot,
+                                              int *__restrict__ status)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const int n_clus = counts[1];
+    const float rcm2 = rcm * rcm;
+    for (int I = gw; I < n_clus; I += nw) {
+        const SysDesc &S = sys[clus_sys[I]];
+        const float4 lo = bb[2 * I], hi = bb[2 * I + 1];
+        // partner slots of I's atoms; distinct partner clusters in lanes 0..npc-1
+        int pcl = -1, npc = 0;
+        bool flag_all = false;
+        const int np = kCluster * K;
+        for (int b = 0; b < np; b += 32) {
+            int v = -1, c = -1;
+            if (b + lane < np) {
+                const int a = perm[I * kCluster + (b + lane) / K];
+                if (a >= 0) {
+                    const int p = part_orig[(long long)a * K + (b + lane) % K];
+                    if (p >= 0) v = (inv[p >> 1] << 1) | (p & 1);
+                }
+                pslot[(long long)I * np + b + lane] = v;
+                if (v >= 0) c = (v >> 1) / kCluster;
+            }
+            const unsigned peers = __match_any_sync(FULL, c);
+            bool leader = c >= 0 && (__ffs(peers) - 1) == lane;
+            for (int m = 0; m < npc; ++m)
+                if (__shfl_sync(FULL, pcl, m) == c) leader = false;
+            const unsigned bal = __ballot_sync(FULL, leader);
+            if (npc + __popc(bal) > 32) flag_all = true;
+            int q = npc;
+            for (unsigned b2 = bal; b2; b2 &= b2 - 1u, ++q) {
+                const int cc = __shfl_sync(FULL, c, __ffs(b2) - 1);
+                if (lane == q) pcl = cc;
+            }
+            npc = min(32, npc + __popc(bal));
+        }
+        const int cxa = max(-S.nx, (int)floorf((lo.x - rcm) * S.inv_w[0]));
+        const int cxb = min(2 * S.nx - 1, (int)floorf((hi.x + rcm) * S.inv_w[0]));
+        const int cya = max(-S.ny, (int)floorf((lo.y - rcm) * S.inv_w[1]));
+        const int cyb = min(2 * S.ny - 1, (int)floorf((hi.y + rcm) * S.inv_w[1]));
+        const bool zdn = (lo.z - rcm) < 0.0f, zup = (hi.z + rcm) >= S.L[2];
+        const float Lz = S.L[2];
+        // conservative margin of the column-geometry test (binning rounds in FP32)
+        const float cmarg = 1e-3f + 1e-6f * fmaxf(S.L[0], S.L[1]);
+        const int ncx = cxb - cxa + 1, ncand = ncx * (cyb - cya + 1);
+        int nA = 0, nB = 0;
+        uint32_t *LA = list + (long long)(2 * I) * cap;
+        uint32_t *LB = LA + cap;
+        for (int c0 = 0; c0 < ncand; c0 += 32) {
+            const int c = c0 + lane;
+            int jb = 0, nj = 0, va = 0, cnt = 0;
+            uint32_t code_xy = 0u;
+            float ox = 0.0f, oy = 0.0f;
+            if (c < ncand) {
+                const int cy = cya + c / ncx, cx = cxa + c % ncx;
+                // lower bound of the xy gap from the column's geometry
+                const float gcx = fmaxf(fmaxf(cx * S.w[0] - hi.x, lo.x - (cx + 1) * S.w[0]) - cmarg, 0.0f);
+                const float gcy = fmaxf(fmaxf(cy * S.w[1] - hi.y, lo.y - (cy + 1) * S.w[1]) - cmarg, 0.0f);
+                if (gcx * gcx + gcy * gcy < rcm2) {
+                    const int ccy = cy < 0 ? cy + S.ny : (cy >= S.ny ? cy - S.ny : cy);
+                    const int ccx = cx < 0 ? cx + S.nx : (cx >= S.nx ? cx - S.nx : cx);
+                    const uint32_t sy = cy < 0 ? 1u : (cy >= S.ny ? 2u : 0u);
+                    const uint32_t sx = cx < 0 ? 1u : (cx >= S.nx ? 2u : 0u);
+                    ox = sx == 1u ? -S.L[0] : (sx == 2u ? S.L[0] : 0.0f);
+                    oy = sy == 1u ? -S.L[1] : (sy == 2u ? S.L[1] : 0.0f);
+                    code_xy = sx | (sy << 2);
+                    const int col = S.col_begin + ccy * S.nx + ccx;
+                    jb = col_slot[col] / kCluster;
+                    nj = col_slot[col + 1] / kCluster - jb;
+                    // z window over the virtual indices v (image -L: v - nj, 0: v, +L: v + nj)
+                    // from the column's z-bin index, one bin wider on each side
+                    // than the FP32 bin arithmetic needs
+                    const int2 *zt = zbin + S.zb_begin + (long long)(col - S.col_begin) * (S.nzb + 1);
+                    const float za = lo.z - rcm, zb = hi.z + rcm;
+                    const int ba = (int)floorf((za < 0.0f ? za + Lz : za) * S.inv_dz) - 1;
+                    const int bz = (int)floorf((zb >= Lz ? zb - Lz : zb) * S.inv_dz) + 1;
+                    const int vlo = zt[min(max(ba, 0), S.nzb)].x - (za < 0.0f ? nj : 0);
+                    const int vhi = zt[min(max(bz, 0), S.nzb)].y + (zb >= Lz ? nj : 0);  // one past
+                    if (vhi > vlo) {
+                        va = vlo;
+                        cnt = vhi - vlo;
+                    }
+                }
+            }
+            // flatten the windows of the 32 lanes
+            int incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int off = incl - cnt, total = __shfl_sync(FULL, incl, 31);
+            for (int p0 = 0; p0 < total; p0 += 32) {
+                const int p = p0 + lane;
+                // owner lane: the last lane whose window starts at or before p
+                int src = 0;
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1) {
+                    const int o2 = __shfl_sync(FULL, off, src + step);
+                    if (o2 <= p) src += step;
+                }
+                const int s_off = __shfl_sync(FULL, off, src), s_va = __shfl_sync(FULL, va, src);
+                const int s_jb = __shfl_sync(FULL, jb, src), s_nj = __shfl_sync(FULL, nj, src);
+                const uint32_t s_code = __shfl_sync(FULL, code_xy, src);
+                const float s_ox = __shfl_sync(FULL, ox, src), s_oy = __shfl_sync(FULL, oy, src);
+                bool hit = false;
+                int J = -1;
+                uint32_t code = 0u;
+                if (p < total) {
+                    const int v = s_va + (p - s_off);
+                    const uint32_t zimg = v < 0 ? 1u : (v >= s_nj ? 2u : 0u);
+                    J = s_jb + v + (zimg == 1u ? s_nj : (zimg == 2u ? -s_nj : 0));
+                    const float oz = zimg == 1u ? -Lz : (zimg == 2u ? Lz : 0.0f);
+                    const float4 jl = bb[2 * J], jh = bb[2 * J + 1];
+                    const float gx = fmaxf(fmaxf((jl.x + s_ox) - hi.x, lo.x - (jh.x + s_ox)), 0.0f);
+                    const float gy = fmaxf(fmaxf((jl.y + s_oy) - hi.y, lo.y - (jh.y + s_oy)), 0.0f);
+                    const float gz = fmaxf(fmaxf((jl.z + oz) - hi.z, lo.z - (jh.z + oz)), 0.0f);
+                    hit = gx * gx + gy * gy + gz * gz < rcm2;
+                    code = s_code | (zimg << 4);
+                }
+                bool fl = flag_all;
+                for (int m = 0; m < npc; ++m) fl |= (__shfl_sync(FULL, pcl, m) == J);
+                const uint32_t ent = (uint32_t)J | (code << kShiftBit) | (fl ? kExclFlag : 0u);
+                const bool hitA = hit && keep_half(I, J, code), hitB = hit && !hitA;
+                const unsigned bA = __ballot_sync(FULL, hitA), bB = __ballot_sync(FULL, hitB);
+                if (hitA) {
+                    const int q = nA + __popc(bA & lt);
+                    if (q < cap) LA[q] = ent;
+                }
+                if (hitB) {
+                    const int q = nB + __popc(bB & lt);
+                    if (q < cap) LB[q] = ent;
+                }
+                nA += __popc(bA);
+                nB += __popc(bB);
+            }
+        }
+        if (lane == 0) {
+            list_n[2 * I] = min(nA, cap);
+            list_n[2 * I + 1] = min(nB, cap);
+            if (nA > cap || nB > cap) atomicOr(status, ST_CAPACITY);
+        }
+    }
 }
 
 cudaError_t launch_build(nb_ctx *ctx, const float *d_pos)
@@ -178,8 +387,14 @@ cudaError_t launch_build(nb_ctx *ctx, const float *d_pos)
     k_bin<<<(N + tb - 1) / tb, tb, 0, st>>>(N, d_pos, d.sys, d.atom_sys, d.wpos, d.atom_col, d.col_count, d.status);
     k_scan<<<1, 1024, 0, st>>>(ctx->n_cols, ctx->n_sys, d.col_count, d.col_slot, d.col_fill, d.sys, d.counts);
     k_scatter<<<(N + tb - 1) / tb, tb, 0, st>>>(N, d.atom_col, d.col_fill, d.stage);
-    k_colsort<<<ctx->n_cols, 128, 0, st>>>(d.col_count, d.col_slot, d.col_sys, d.stage, d.wpos, d.xyzq, d.tslot,
-                                           d.perm, d.inv, d.bb, d.clus_sys);
+    k_colsort<<<ctx->n_cols, 128, 0, st>>>(d.col_count, d.col_slot, d.col_sys, d.sys, d.stage, d.wpos, d.xyzq,
+                                           d.tslot, d.perm, d.inv, d.bb, d.clus_sys, d.zbin);
+    const int lw = 8;  // warps (clusters) per block of the list kernel
+    const int lblocks = (int)std::max<int64_t>(1, (ctx->clus_cap + lw - 1) / lw);
+    k_list<<<lblocks, lw * 32, 0, st>>>(d.sys, d.counts, d.bb, d.clus_sys, d.col_slot, d.zbin, d.perm, d.part_orig,
+                                        d.inv,
+                                        ctx->K, ctx->pp.rc + ctx->pp.list_margin, ctx->list_cap, d.list, d.list_n,
+                                        d.pslot, d.status);
     return cudaGetLastError();
 }
 

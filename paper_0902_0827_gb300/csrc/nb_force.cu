@@ -1,8 +1,11 @@
 // nb_force.cu - the non-bonded force kernel (section "Molecular dynamics on
 // the GPU": the non-bonded kernel computes the full Lennard-Jones and
-// electrostatic force on each particle; as in the paper, the reciprocal force
-// F_ji is not reused, so every atom accumulates its own force and no
-// scattered force writes or atomics are needed).
+// electrostatic force on each particle).  The paper's kernel does not reuse
+// the reciprocal force F_ji; here the forward kernel does (Newton's third
+// law): every unique pair is evaluated once, from the atom of the lower
+// cluster, and its force goes to both atoms as 64-bit fixed point (2^32), so
+// the sums stay exact and order independent.  The adjoint kernel visits
+// every ordered pair, as in the paper.
 //
 // GB300 work decomposition (the paper's one-cell-per-block staging of the
 // neighbour cells in shared memory, re-cut for this machine):
@@ -21,6 +24,10 @@
 //   (3) compaction: a warp scan of the mask counts places every in-range
 //       (cluster, atom) item into a per-warp ring in shared memory;
 //   (4) compute: full 32-pair steps of the ring, one pair per lane, FP32.
+// Forward only: the force on j goes to a block-shared fixed-point slot of the
+// staged atom (integer atomics), flushed to the global fixed-point force array
+// when the chunk is done; the force on i is summed over the warp and added
+// once per cluster.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -42,14 +49,15 @@ struct ForceArgs {
     const int *perm;
     const int *clus_sys;
     const float4 *bb;
-    const int *col_slot;      // [C+1] padded slot offsets of the columns
-    const int *part_orig;     // [N*K] topology partners (orig << 1) | is14
-    const int *inv;           // [N] atom -> sorted slot
-    int cap;                  // list entries per cluster (shared memory)
+    const uint32_t *list;     // [NC*2*cap] per cluster: half list, other half
+    const int *list_n;        // [NC*2]
+    const int *pslot;         // [S*K] partner slots (slot << 1) | is14, -1 pad
+    int cap;                  // entries per half list
     int scap;
     int K;
     const float2 *lj_tab;
     float *F;
+    long long *facc;          // [S*3] fixed-point forces in sorted order (forward)
     long long *sys_acc;
     int *status;
     long long *dbg_n;
@@ -75,25 +83,17 @@ __device__ __forceinline__ long long to_fixed(float v, int *status)
     return __float2ll_rn(v * 4294967296.0f);
 }
 
-constexpr int kMaxCand = 256;  // candidate columns of one cluster (with images)
-static_assert(kMaxCand == kCluster * 32, "the candidate scan gives one column to each thread of the block");
-
 struct ForceSmem {
     float2 *lj;
-    uint32_t *lst;             // this cluster's pair list [cap]
-    int *cjb, *cnj, *ccode;    // candidate columns: first cluster, clusters, image code [kMaxCand]
-    int *cpre;                 // exclusive prefix of cnj [kMaxCand + 1]
-    int *pslot;                // partner slots of the 8 atoms [8 * K] (slot << 1 | is14, -1)
-    int *pcl;                  // distinct partner clusters [8 * K]
-    int *misc;                 // [32]: npc, wcnt[24] ... (see build_list)
-    int *woff;                 // [32]
-    uint32_t *ent;
+    uint32_t *lst;             // list entries of the staged chunks [2][scap] (double buffer)
+    uint32_t *ent;             // entries of the current chunk
     float4 *pos;
     int *typ;
     float4 *bb;
     uint16_t *surv;
     uint32_t *ring;
     unsigned long long *cacc;
+    unsigned long long *jf;    // forward: fixed-point forces of the staged j atoms [3][scap * 8]
     float4 *gj;                // adjoint: staged dL/dF of the j atoms
     float4 *ljd;               // adjoint: derivative factors of the type pairs
     unsigned long long *tacc;  // adjoint: block table of fixed-point parameter gradients
@@ -106,16 +106,11 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p)
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-__host__ __device__ inline size_t list_smem_bytes(int cap, int K)
+__host__ __device__ inline size_t force_smem_bytes(int T, int scap, int nwarps, bool adj)
 {
-    return align16((size_t)cap * 4) + (size_t)kMaxCand * 4 * 3 + align16((size_t)(kMaxCand + 1) * 4) +
-           2 * align16((size_t)kCluster * K * 4) + 32 * 4 + 32 * 4;
-}
-
-__host__ __device__ inline size_t force_smem_bytes(int T, int scap, int nwarps, bool adj, int cap, int K)
-{
-    size_t b = adj ? (size_t)scap * kCluster * 16 + (size_t)T * T * 16 + (size_t)T * T * 16 : 0;
-    b += list_smem_bytes(cap, K);
+    size_t b = adj ? (size_t)scap * kCluster * 16 + (size_t)T * T * 16 + (size_t)T * T * 16
+                   : (size_t)scap * kCluster * 3 * 8;
+    b += (size_t)2 * scap * 4;
     b += align16((size_t)T * T * 8);
     b += (size_t)scap * kCluster * 16;
     b += (size_t)scap * kCluster * 4;
@@ -126,31 +121,19 @@ __host__ __device__ inline size_t force_smem_bytes(int T, int scap, int nwarps, 
     return b;
 }
 
-__device__ __forceinline__ ForceSmem carve(unsigned char *smem, int T, int scap, int nwarps, int w, bool adj, int cap,
-                                           int K)
+__device__ __forceinline__ ForceSmem carve(unsigned char *smem, int T, int scap, int nwarps, int w, bool adj)
 {
     ForceSmem S;
     size_t off = 0;
     S.lst = reinterpret_cast<uint32_t *>(smem + off);
-    off += align16((size_t)cap * 4);
-    S.cjb = reinterpret_cast<int *>(smem + off);
-    off += (size_t)kMaxCand * 4;
-    S.cnj = reinterpret_cast<int *>(smem + off);
-    off += (size_t)kMaxCand * 4;
-    S.ccode = reinterpret_cast<int *>(smem + off);
-    off += (size_t)kMaxCand * 4;
-    S.cpre = reinterpret_cast<int *>(smem + off);
-    off += align16((size_t)(kMaxCand + 1) * 4);
-    S.pslot = reinterpret_cast<int *>(smem + off);
-    off += align16((size_t)kCluster * K * 4);
-    S.pcl = reinterpret_cast<int *>(smem + off);
-    off += align16((size_t)kCluster * K * 4);
-    S.misc = reinterpret_cast<int *>(smem + off);
-    off += 32 * 4;
-    S.woff = reinterpret_cast<int *>(smem + off);
-    off += 32 * 4;
+    off += (size_t)2 * scap * 4;
     S.gj = S.ljd = nullptr;
     S.tacc = nullptr;
+    S.jf = nullptr;
+    if (!adj) {
+        S.jf = reinterpret_cast<unsigned long long *>(smem + off);
+        off += (size_t)scap * kCluster * 3 * 8;
+    }
     if (adj) {
         S.gj = reinterpret_cast<float4 *>(smem + off);
         off += (size_t)scap * kCluster * 16;
@@ -194,189 +177,33 @@ __device__ __forceinline__ void cp_async_wait_all()
 // Slot of atom k of staged entry e (swizzle by e, conflict-free lane access).
 __device__ __forceinline__ int swz(int e, int k) { return e * kCluster + (k ^ (e & (kCluster - 1))); }
 
-// Stage, for the n list entries at S.ent, every listed cluster J's 8
-// coordinates+charges, 8 types, bounding box and (adjoint) 8 dL/dF vectors
-// with asynchronous copies issued by every thread of the block.
+// List entry e of cluster I: the half list first, then (adjoint) the other
+// half.
+__device__ __forceinline__ uint32_t list_entry(const ForceArgs &A, int I, int nA, int e)
+{
+    const long long row = 2ll * I * A.cap;
+    return __ldg(A.list + (e < nA ? row + e : row + A.cap + (e - nA)));
+}
+
+// Stage the n list entries from c0 of cluster I into S.ent, and for every
+// listed cluster J its 8 coordinates+charges, 8 types, bounding box and
+// (adjoint) 8 dL/dF vectors, with asynchronous copies issued by every thread
+// of the block.
 template <bool ADJ>
-__device__ __forceinline__ void stage_chunk(const ForceArgs &A, const ForceSmem &S, int n)
+__device__ __forceinline__ void stage_chunk(const ForceArgs &A, const ForceSmem &S, int I, int nA, int c0, int n)
 {
     for (int p = threadIdx.x; p < n * kCluster; p += blockDim.x) {
         const int e = p >> 3, k = p & 7;
-        const long long j = (long long)(S.ent[e] & kJMask) * kCluster + k;
+        const uint32_t ent = list_entry(A, I, nA, c0 + e);
+        if (k == 0) S.ent[e] = ent;
+        const long long j = (long long)(ent & kJMask) * kCluster + k;
         cp_async16(S.pos + swz(e, k), A.xyzq + j);
         cp_async4(S.typ + swz(e, k), A.tslot + j);
         if (ADJ) cp_async16(S.gj + swz(e, k), A.gslot + j);
-    }
-    for (int p = threadIdx.x; p < n * 2; p += blockDim.x) {
-        const int e = p >> 1;
-        cp_async16(S.bb + p, A.bb + (long long)(S.ent[e] & kJMask) * 2 + (p & 1));
+        if (k < 2) cp_async16(S.bb + 2 * e + k, A.bb + (long long)(ent & kJMask) * 2 + k);
     }
     cp_async_wait_all();
     __syncthreads();
-}
-
-// Build cluster I's pair list in shared memory (the paper's neighbour cells
-// within R of the current cell, at cluster granularity): every candidate
-// column within reach of I's bounding box (with periodic images), every
-// cluster J of those columns, under up to three z images; an entry is kept
-// when the bounding-box gap is below rc (plus a rounding margin).  Entries:
-// J | image code per axis (1: x_j - L, 2: x_i - L) | flag when J holds a
-// topology partner of I.  Threads spread over the (column, cluster) pairs;
-// hits are compacted in (round, z image, warp, lane) order, so the list and
-// every sum built from it are deterministic.  Also fills the partner slots of
-// I's atoms.  Returns the list length (all threads).
-__device__ int build_list(const ForceArgs &A, const ForceSmem &S, int I, const SysDesc &SD)
-{
-    const unsigned FULL = 0xffffffffu;
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nthr = blockDim.x;
-    const unsigned lt = (1u << lane) - 1u;
-    const float4 lo = A.bb[2 * I], hi = A.bb[2 * I + 1];
-    const float rcm = A.P.rc + A.P.list_margin, rcm2 = A.P.rcm2;
-    const int cxa = max(-SD.nx, (int)floorf((lo.x - rcm) * SD.inv_w[0]));
-    const int cxb = min(2 * SD.nx - 1, (int)floorf((hi.x + rcm) * SD.inv_w[0]));
-    const int cya = max(-SD.ny, (int)floorf((lo.y - rcm) * SD.inv_w[1]));
-    const int cyb = min(2 * SD.ny - 1, (int)floorf((hi.y + rcm) * SD.inv_w[1]));
-    const bool zdn = (lo.z - rcm) < 0.0f, zup = (hi.z + rcm) >= SD.L[2];
-    const int ncx = cxb - cxa + 1;
-    int ncand = ncx * (cyb - cya + 1);
-    if (ncand > kMaxCand) {
-        if (tid == 0) atomicOr(A.status, ST_CAPACITY);
-        ncand = kMaxCand;
-    }
-    // partner slots of the 8 atoms of I
-    const int npk = kCluster * A.K;
-    for (int t = tid; t < npk; t += nthr) {
-        const int a = A.perm[I * kCluster + t / A.K];
-        int v = -1;
-        if (a >= 0) {
-            const int p = A.part_orig[(long long)a * A.K + t % A.K];
-            if (p >= 0) v = (A.inv[p >> 1] << 1) | (p & 1);
-        }
-        S.pslot[t] = v;
-    }
-    // candidate columns
-    for (int c = tid; c < kMaxCand; c += nthr) {
-        int jb = 0, nj = 0, code = 0;
-        if (c < ncand) {
-            const int cy = cya + c / ncx, cx = cxa + c % ncx;
-            const int ccy = cy < 0 ? cy + SD.ny : (cy >= SD.ny ? cy - SD.ny : cy);
-            const int ccx = cx < 0 ? cx + SD.nx : (cx >= SD.nx ? cx - SD.nx : cx);
-            const int sy = cy < 0 ? 1 : (cy >= SD.ny ? 2 : 0);
-            const int sx = cx < 0 ? 1 : (cx >= SD.nx ? 2 : 0);
-            const int col = SD.col_begin + ccy * SD.nx + ccx;
-            jb = A.col_slot[col] / kCluster;
-            nj = A.col_slot[col + 1] / kCluster - jb;
-            code = sx | (sy << 2);
-        }
-        S.cjb[c] = jb;
-        S.cnj[c] = nj;
-        S.ccode[c] = code;
-    }
-    __syncthreads();
-    // exclusive scan of the column sizes (kMaxCand == blockDim.x) and the
-    // distinct partner clusters (warp 0)
-    {
-        const int v = S.cnj[tid];
-        int x = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(FULL, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) S.woff[w] = x;
-        __syncthreads();
-        int base = 0;
-        for (int k = 0; k < w; ++k) base += S.woff[k];
-        S.cpre[tid] = base + x - v;
-        if (tid == nthr - 1) S.cpre[kMaxCand] = base + x;
-        if (w == 0) {
-            int npc = 0;
-            for (int b = 0; b < npk; b += 32) {
-                int v2 = -1;
-                if (b + lane < npk && S.pslot[b + lane] >= 0) v2 = (S.pslot[b + lane] >> 1) / kCluster;
-                const unsigned peers = __match_any_sync(FULL, v2);
-                bool leader = v2 >= 0 && (__ffs(peers) - 1) == lane;
-                for (int m = 0; m < npc; ++m)
-                    if (S.pcl[m] == v2) leader = false;
-                const unsigned bal = __ballot_sync(FULL, leader);
-                if (leader) S.pcl[npc + __popc(bal & lt)] = v2;
-                npc += __popc(bal);
-                __syncwarp();
-            }
-            if (lane == 0) S.misc[0] = npc;
-        }
-        __syncthreads();
-    }
-    const int P = S.cpre[kMaxCand];
-    const int npc = S.misc[0];
-    int nE = 0;
-    for (int p0 = 0; p0 < P; p0 += nthr) {
-        const int p = p0 + tid;
-        const bool valid = p < P;
-        bool h0 = false, h1 = false, h2 = false;
-        uint32_t base_ent = 0u;
-        if (valid) {
-            int c = 0;
-            for (int step = kMaxCand / 2; step >= 1; step >>= 1)
-                if (c + step < ncand && S.cpre[c + step] <= p) c += step;
-            const int J = S.cjb[c] + (p - S.cpre[c]);
-            const int code = S.ccode[c];
-            const int sx = code & 3, sy = code >> 2;
-            const float ox = sx == 1 ? -SD.L[0] : (sx == 2 ? SD.L[0] : 0.0f);
-            const float oy = sy == 1 ? -SD.L[1] : (sy == 2 ? SD.L[1] : 0.0f);
-            const float4 jl = A.bb[2 * J], jh = A.bb[2 * J + 1];
-            const float gx = fmaxf(fmaxf((jl.x + ox) - hi.x, lo.x - (jh.x + ox)), 0.0f);
-            const float gy = fmaxf(fmaxf((jl.y + oy) - hi.y, lo.y - (jh.y + oy)), 0.0f);
-            const float gxy = gx * gx + gy * gy;
-            bool fl = false;
-            for (int m = 0; m < npc; ++m) fl |= (S.pcl[m] == J);
-            base_ent = (uint32_t)J | ((uint32_t)code << kShiftBit) | (fl ? kExclFlag : 0u);
-            const float gz0 = fmaxf(fmaxf(jl.z - hi.z, lo.z - jh.z), 0.0f);
-            const float gz1 = fmaxf(fmaxf((jl.z - SD.L[2]) - hi.z, lo.z - (jh.z - SD.L[2])), 0.0f);
-            const float gz2 = fmaxf(fmaxf((jl.z + SD.L[2]) - hi.z, lo.z - (jh.z + SD.L[2])), 0.0f);
-            h0 = gxy + gz0 * gz0 < rcm2;
-            h1 = zdn && (gxy + gz1 * gz1 < rcm2);
-            h2 = zup && (gxy + gz2 * gz2 < rcm2);
-        }
-        const unsigned b0 = __ballot_sync(FULL, h0), b1 = __ballot_sync(FULL, h1), b2 = __ballot_sync(FULL, h2);
-        if (lane == 0) {
-            S.misc[1 + w] = __popc(b0);
-            S.misc[9 + w] = __popc(b1);
-            S.misc[17 + w] = __popc(b2);
-        }
-        __syncthreads();
-        if (w == 0) {  // exclusive scan of the 24 (z image, warp) counts
-            const int v = lane < 24 ? S.misc[1 + lane] : 0;
-            int x = v;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(FULL, x, o);
-                if (lane >= o) x += y;
-            }
-            S.woff[lane] = x - v;  // lanes >= 24 add nothing: woff[24] is the total
-        }
-        __syncthreads();
-        const int wb0 = nE + S.woff[w], wb1 = nE + S.woff[8 + w], wb2 = nE + S.woff[16 + w];
-        if (h0) {
-            const int q = wb0 + __popc(b0 & lt);
-            if (q < A.cap) S.lst[q] = base_ent;
-        }
-        if (h1) {
-            const int q = wb1 + __popc(b1 & lt);
-            if (q < A.cap) S.lst[q] = base_ent | (1u << (kShiftBit + 4));
-        }
-        if (h2) {
-            const int q = wb2 + __popc(b2 & lt);
-            if (q < A.cap) S.lst[q] = base_ent | (2u << (kShiftBit + 4));
-        }
-        nE += S.woff[24];
-        __syncthreads();
-    }
-    if (nE > A.cap) {
-        if (tid == 0) atomicOr(A.status, ST_CAPACITY);
-        nE = A.cap;
-    }
-    return nE;
 }
 
 struct Acc {
@@ -413,6 +240,11 @@ __device__ __forceinline__ void eval_pair_adj(const PairParams &P, const ForceSm
                                               float dy, float dz, float r2, float qj, int tj, float4 gj, bool is14,
                                               int *status, AccAdj &acc)
 {
+    if (!in) {  // masked lanes: keep every product finite (padding sits far away)
+        dx = 0.0f;
+        dy = 0.0f;
+        dz = 0.0f;
+    }
     const float rinv = fast_rsqrt(r2);
     const float r = r2 * rinv, ir2 = rinv * rinv;
     const float2 ab = S.lj[ti_row + tj];
@@ -481,7 +313,7 @@ __device__ __forceinline__ void eval_pair_adj(const PairParams &P, const ForceSm
 template <bool EWALD, bool VIRIAL>
 __device__ __forceinline__ void eval_pair(const PairParams &P, const float2 *__restrict__ lj, int ti_row, float qi,
                                           bool in, float dx, float dy, float dz, float r2, float qj, int tj,
-                                          bool is14, Acc &acc)
+                                          bool is14, Acc &acc, float &fjx, float &fjy, float &fjz)
 {
     const float rinv = fast_rsqrt(r2);
     const float2 ab = lj[ti_row + tj];
@@ -498,8 +330,11 @@ __device__ __forceinline__ void eval_pair(const PairParams &P, const float2 *__r
     acc.fx -= fdx;
     acc.fy -= fdy;
     acc.fz -= fdz;
+    fjx = fdx;  // F_j = -F_i
+    fjy = fdy;
+    fjz = fdz;
     if (VIRIAL) {
-        // W_ab += d_ij,a f_ij,b with d_ij = -d and f_ij = -fs d
+        // W_ab += d_ij,a f_ij,b with d_ij = -d and f_ij = -fs d (once per pair)
         acc.w[0] = fmaf(fdx, dx, acc.w[0]);
         acc.w[1] = fmaf(fdy, dy, acc.w[1]);
         acc.w[2] = fmaf(fdz, dz, acc.w[2]);
@@ -536,22 +371,47 @@ __device__ __forceinline__ void eval_item(const ForceArgs &A, const ForceSmem &S
     const float r2 =
         disp_r2(__fsub_rn(pj.x, sx), __fsub_rn(pj.y, sy), __fsub_rn(pj.z, sz), ax, ay, az, dx, dy, dz);
     if (DEBUG && active) {
+        // forward visits: every unique pair exactly once
         atomicAdd((unsigned long long *)&A.dbg_n[0], 1ull);
         const int jorig = A.perm[(int)(ent & kJMask) * kCluster + k];
-        if (ia.iorig < jorig) {
-            const long long q = (long long)atomicAdd((unsigned long long *)&A.dbg_n[1], 1ull);
-            if (q < A.dbg_cap) {
-                A.dbg_ij[2 * q] = ia.iorig;
-                A.dbg_ij[2 * q + 1] = jorig;
-            }
+        const long long q = (long long)atomicAdd((unsigned long long *)&A.dbg_n[1], 1ull);
+        if (q < A.dbg_cap) {
+            A.dbg_ij[2 * q] = min(ia.iorig, jorig);
+            A.dbg_ij[2 * q + 1] = max(ia.iorig, jorig);
         }
     }
     if constexpr (ADJ) {
         eval_pair_adj<EWALD>(A.P, S, ia.ti_row, ia.qi, ia.gix, ia.giy, ia.giz, ia.gE_lj, ia.gE_c, active, dx, dy, dz,
                              active ? r2 : 1.0f, pj.w, tj, S.gj[idx], (item & 1u) != 0u, A.status, acc);
     } else {
+        float fjx, fjy, fjz;
         eval_pair<EWALD, VIRIAL>(A.P, S.lj, ia.ti_row, ia.qi, active, dx, dy, dz, active ? r2 : 1.0f, pj.w, tj,
-                                 (item & 1u) != 0u, acc);
+                                 (item & 1u) != 0u, acc, fjx, fjy, fjz);
+        if (active) {
+            const int js = A.scap * kCluster;
+            atomicAdd(&S.jf[idx], (unsigned long long)to_fixed(fjx, A.status));
+            atomicAdd(&S.jf[js + idx], (unsigned long long)to_fixed(fjy, A.status));
+            atomicAdd(&S.jf[2 * js + idx], (unsigned long long)to_fixed(fjz, A.status));
+        }
+    }
+}
+
+// Forward: add the block's fixed-point forces of the n staged j clusters
+// listed at ent to the global fixed-point force array and clear them.
+__device__ __forceinline__ void flush_jf(const ForceArgs &A, const ForceSmem &S, const uint32_t *ent, int n)
+{
+    const int js = A.scap * kCluster;
+    for (int p = threadIdx.x; p < n * kCluster; p += blockDim.x) {
+        const int e = p >> 3, k = (p & 7) ^ (e & 7);  // p = swz(e, k)
+        const long long g = 3ll * ((long long)(ent[e] & kJMask) * kCluster + k);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const unsigned long long v = S.jf[c * js + p];
+            if (v) {
+                atomicAdd((unsigned long long *)&A.facc[g + c], v);
+                S.jf[c * js + p] = 0ull;
+            }
+        }
     }
 }
 
@@ -564,7 +424,7 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
     const int w = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    const ForceSmem S = carve(smem, T, A.scap, nwarps, w, ADJ, A.cap, A.K);
+    const ForceSmem S = carve(smem, T, A.scap, nwarps, w, ADJ);
     for (int k = threadIdx.x; k < T * T; k += blockDim.x) S.lj[k] = A.lj_tab[k];
     if (ADJ) {
         for (int k = threadIdx.x; k < T * T; k += blockDim.x) {
@@ -574,6 +434,8 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
         }
     }
     if (threadIdx.x < kTaskVals) S.cacc[threadIdx.x] = 0ull;
+    if (!ADJ)
+        for (int k = threadIdx.x; k < 3 * A.scap * kCluster; k += blockDim.x) S.jf[k] = 0ull;
     __syncthreads();
     using AccT = typename std::conditional<ADJ, AccAdj, Acc>::type;
 
@@ -632,16 +494,21 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
         }
         AccT acc;
         memset(&acc, 0, sizeof(acc));
-        __syncthreads();  // the list and staging buffers are free
-        const int nE = build_list(A, S, I, SD);
-        const int pe = lane < A.K ? S.pslot[w * A.K + lane] : -1;
+        // forward: the half list (Newton's third law); adjoint: both halves
+        const int nA = A.list_n[2 * I];
+        const int nE = ADJ ? nA + A.list_n[2 * I + 1] : nA;
+        const int pe = lane < A.K ? A.pslot[(long long)islot * A.K + lane] : -1;
+        __syncthreads();  // the staging buffers are free
 
-        for (int c0 = 0; c0 < nE; c0 += A.scap) {
+        for (int c0 = 0, ci = 0; c0 < nE; c0 += A.scap, ++ci) {
             const int nC = min(A.scap, nE - c0);
-            if (c0 > 0) __syncthreads();  // the staging buffers are free
+            if (c0 > 0) {
+                __syncthreads();  // the staging buffers are free
+                if (!ADJ) flush_jf(A, S, S.lst + ((ci - 1) & 1) * A.scap, A.scap);
+            }
             ForceSmem Sc = S;
-            Sc.ent = S.lst + c0;
-            stage_chunk<ADJ>(A, Sc, nC);
+            Sc.ent = S.lst + (ci & 1) * A.scap;
+            stage_chunk<ADJ>(A, Sc, I, nA, c0, nC);
             if (!iv) continue;
             // (1) prune staged clusters against this atom
             int ns = 0;
@@ -680,7 +547,8 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
                 const float sx = cx == 1 ? Lx : 0.0f, sy = cy == 1 ? Ly : 0.0f, sz = cz == 1 ? Lz : 0.0f;
                 const float ax = cx == 2 ? xim : xi, ay = cy == 2 ? yim : yi, az = cz == 2 ? zim : zi;
                 uint32_t exm = sv ? 0u : 0xFFu, m14 = 0u;
-                if (J == I && ((ent >> kShiftBit) & 0x3Fu) == 0u) exm |= 1u << w;  // i == j
+                if (J == I && ((ent >> kShiftBit) & 0x3Fu) == 0u)
+                    exm |= ADJ ? 1u << w : (2u << w) - 1u;  // i == j; forward: j > i only
                 const bool fl = sv && (ent & kExclFlag) != 0u;
                 if (__any_sync(kFull, fl)) {
                     for (int m = 0; m < A.K; ++m) {
@@ -738,6 +606,11 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
             }
             __syncwarp();
         }
+        if (!ADJ && nE > 0) {
+            const int last = (nE - 1) / A.scap;
+            __syncthreads();
+            flush_jf(A, S, S.lst + (last & 1) * A.scap, nE - last * A.scap);
+        }
         if (!iv) continue;
         if constexpr (ADJ) {
             long long v0 = to_fixed(acc.dx, A.status), v1 = to_fixed(acc.dy, A.status),
@@ -770,11 +643,9 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
                 vz += __shfl_xor_sync(kFull, vz, o);
             }
             if (lane == 0) {
-                const long long a = A.perm[islot];
-                const float sc = 2.3283064365386963e-10f;  // 2^-32
-                A.F[3 * a] = __ll2float_rn(vx) * sc;
-                A.F[3 * a + 1] = __ll2float_rn(vy) * sc;
-                A.F[3 * a + 2] = __ll2float_rn(vz) * sc;
+                atomicAdd((unsigned long long *)&A.facc[3ll * islot], (unsigned long long)vx);
+                atomicAdd((unsigned long long *)&A.facc[3ll * islot + 1], (unsigned long long)vy);
+                atomicAdd((unsigned long long *)&A.facc[3ll * islot + 2], (unsigned long long)vz);
             }
             // energies and virial of atom i: FP32 butterfly (fixed order), then fixed point
             float v[kTaskVals] = {acc.elj, acc.ec, acc.w[0], acc.w[1], acc.w[2], acc.w[3], acc.w[4], acc.w[5]};
@@ -830,16 +701,28 @@ __global__ void k_pack(int slot_cap, const int *__restrict__ counts, const int *
     tslot[s] = t;
 }
 
+// Fixed-point forces (sorted order) to FP32 in the caller's order.
+__global__ void k_unpack_forces(int slot_cap, const int *__restrict__ counts, const int *__restrict__ perm,
+                                const long long *__restrict__ facc, float *__restrict__ F)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= slot_cap || s >= counts[0]) return;
+    const int a = perm[s];
+    if (a < 0) return;
+    const float sc = 2.3283064365386963e-10f;  // 2^-32
+#pragma unroll
+    for (int c = 0; c < 3; ++c) F[3ll * a + c] = __ll2float_rn(facc[3ll * s + c]) * sc;
+}
+
 // Per-system energy/virial: the exact int64 sums (order independent, hence
-// deterministic) to FP64, halved because every pair is visited from both of
-// its atoms.
+// deterministic) to FP64; every pair was evaluated once.
 __global__ void k_finalize(int n_sys, const long long *__restrict__ sys_acc, double *__restrict__ energy,
                            double *__restrict__ virial)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_sys * kTaskVals) return;
     const int s = i / kTaskVals, k = i % kTaskVals;
-    const double v = (double)sys_acc[i] * (0.5 / kFixScale);
+    const double v = (double)sys_acc[i] * (1.0 / kFixScale);
     if (k < 2) {
         if (energy) energy[2 * s + k] = v;
     } else if (virial) {
@@ -851,7 +734,7 @@ template <bool ADJ, bool EWALD, bool VIRIAL, bool DEBUG>
 static void launch_force_t(nb_ctx *ctx, const ForceArgs &A)
 {
     const int nw = kCluster;
-    const size_t smem = force_smem_bytes(A.P.n_types, A.scap, nw, ADJ, A.cap, A.K);
+    const size_t smem = force_smem_bytes(A.P.n_types, A.scap, nw, ADJ);
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(k_force<ADJ, EWALD, VIRIAL, DEBUG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -878,10 +761,10 @@ static ForceArgs make_args(nb_ctx *ctx)
     A.perm = d.perm;
     A.clus_sys = d.clus_sys;
     A.bb = d.bb;
-    A.col_slot = d.col_slot;
-    A.part_orig = d.part_orig;
-    A.inv = d.inv;
-    A.cap = ctx->tune.list_capacity;
+    A.list = d.list;
+    A.list_n = d.list_n;
+    A.pslot = d.pslot;
+    A.cap = ctx->list_cap;
     A.scap = ctx->stage_cap;
     A.K = ctx->K;
     A.lj_tab = d.lj_tab;
@@ -913,8 +796,10 @@ cudaError_t launch_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, con
         if (e != cudaSuccess) return e;
     }
     cudaMemsetAsync(d.sys_acc, 0, sizeof(long long) * kTaskVals * ctx->n_sys, ctx->stream);
+    cudaMemsetAsync(d.facc, 0, sizeof(long long) * 3 * ctx->slot_cap, ctx->stream);
     ForceArgs A = make_args(ctx);
     A.F = d_F;
+    A.facc = d.facc;
     const bool ewald = ctx->pp.ewald != 0;
     const bool virial = d_virial != nullptr;
     const bool prof = ctx->profiling && ctx->prof_n < (int)ctx->prof_ev.size() / 2;
@@ -933,6 +818,11 @@ cudaError_t launch_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, con
         cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n + 1], ctx->stream);
         ctx->prof_n++;
     }
+    {
+        const int tb = 256;
+        const int S = (int)ctx->slot_cap;
+        k_unpack_forces<<<(S + tb - 1) / tb, tb, 0, ctx->stream>>>(S, d.counts, d.perm, d.facc, d_F);
+    }
     if (!debug_pairs && (d_energy || d_virial)) {
         const int n = ctx->n_sys * kTaskVals;
         k_finalize<<<(n + 255) / 256, 256, 0, ctx->stream>>>(ctx->n_sys, d.sys_acc, d_energy, d_virial);
@@ -940,7 +830,11 @@ cudaError_t launch_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, con
     return cudaGetLastError();
 }
 
-size_t force_smem_for(int T, int scap, int cap, int K) { return force_smem_bytes(T, scap, kCluster, true, cap, K); }
+size_t force_smem_for(int T, int scap, int K)
+{
+    (void)K;
+    return std::max(force_smem_bytes(T, scap, kCluster, true), force_smem_bytes(T, scap, kCluster, false));
+}
 
 cudaError_t launch_adjoint_tile(nb_ctx *ctx, const double *d_dLdE, float *d_dpos, float *d_dq)
 {

@@ -193,7 +193,11 @@ inline nb_status init_pair_params(const nb_params &P0, PairParams &pp)
 }
 
 // Box, column grid and offsets of one system.
-inline void init_sysdesc(const nb_params &p, SysDesc &S, int atom_begin, int col_begin)
+// Bins of the per-column z index: about 1 A high, at most max_nzb per column.
+constexpr int kMaxZBins = 4096;
+
+inline void init_sysdesc(const nb_params &p, SysDesc &S, int atom_begin, int col_begin, int zb_begin,
+                         int max_nzb = kMaxZBins)
 {
     memset(&S, 0, sizeof(S));
     const double rho = (double)p.n_atoms / ((double)p.box[0] * (double)p.box[1] * (double)p.box[2]);
@@ -210,7 +214,15 @@ inline void init_sysdesc(const nb_params &p, SysDesc &S, int atom_begin, int col
     S.atom_begin = atom_begin;
     S.n_atoms = p.n_atoms;
     S.col_begin = col_begin;
+    int nzb = (int)ceil((double)p.box[2] / 1.0);
+    S.nzb = nzb < 1 ? 1 : (nzb > max_nzb ? max_nzb : nzb);
+    S.zb_begin = zb_begin;
+    S.inv_dz = (float)((double)S.nzb / (double)p.box[2]);
+    S.dz = (float)((double)p.box[2] / S.nzb);
 }
+
+// Entries of a system's z-bin index.
+inline int64_t zbin_entries(const SysDesc &S) { return (int64_t)S.nx * S.ny * (S.nzb + 1); }
 
 }  // namespace host
 }  // namespace acenb

@@ -30,12 +30,6 @@ constexpr uint32_t kJMask = 0x01FFFFFFu;
 constexpr int kShiftBit = 25;
 constexpr uint32_t kExclFlag = 0x80000000u;
 
-// Queue word: type (bits 0..7) | exclusion bits per i (8..15) | 1-4 bits per i
-// (16..23) | i-side shift per axis (24..26).
-constexpr int kQExcl = 8;
-constexpr int kQ14 = 16;
-constexpr int kQIShift = 24;
-
 // Device status bits (first error wins when reported).
 enum : int {
     ST_NONFINITE = 1 << 0,
@@ -60,6 +54,13 @@ struct SysDesc {
     int slot_begin;      // [build] first sorted slot
     int clus_begin;      // [build] first cluster
     int clus_end;        // [build] one past the last cluster
+    // z-bin index of every column: bins of height dz = Lz / nzb; per column
+    // nzb + 1 pairs (first cluster with z_hi >= b dz, first cluster with
+    // z_lo > (b + 1) dz), at zb_begin + local column * (nzb + 1)
+    int nzb;
+    int zb_begin;
+    float inv_dz;        // nzb / Lz (FP32)
+    float dz;            // Lz / nzb (FP32)
 };
 
 // Pair-model constants passed by value to kernels.
@@ -100,6 +101,11 @@ struct DevBuffers {
     float4 *bb = nullptr;            // [NC*2] cluster bounding boxes (lo, hi interleaved)
     int *clus_sys = nullptr;         // [NC] system of each cluster
     long long *sys_acc = nullptr;    // [n_sys*kTaskVals] per-system fixed-point energy/virial
+    long long *facc = nullptr;       // [S*3] fixed-point forces in sorted order (both atoms of each pair)
+    uint32_t *list = nullptr;        // [NC*2*list_cap] per cluster: half list, then the other half
+    int *list_n = nullptr;           // [NC*2] lengths of the two halves
+    int *pslot = nullptr;            // [S*K] partner slots (slot << 1) | is14, -1 pad
+    int2 *zbin = nullptr;            // [zb_total] z-bin index of the columns (see SysDesc)
     long long *tab_grad = nullptr;   // [T*T*2] adjoint dL/dsig_ab, dL/deps_ab (fixed point, one ordered half)
     int *counts = nullptr;           // [4]: n_slots, n_clusters, pair counters
     int *status = nullptr;           // [1]
@@ -124,7 +130,9 @@ struct nb_ctx {
     int64_t clus_cap = 0;
     int K = 1;                     // partners per atom (>= 1)
     int comb_rule = 0;
-    int stage_cap = 160;           // list entries staged per block pass
+    int stage_cap = 96;            // list entries staged per block pass
+    int list_cap = 512;            // entries per half list of a cluster
+    int64_t zb_total = 0;          // entries of the z-bin index
     int smem_optin = 0;            // device opt-in shared memory per block
     cudaStream_t stream = nullptr;
     int device = 0;
@@ -160,7 +168,7 @@ __device__ __forceinline__ float wrap_coord(float x, float L)
 cudaError_t launch_build(nb_ctx *ctx, const float *d_pos);
 cudaError_t launch_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type,
                           float *d_F, double *d_energy, double *d_virial, bool debug_pairs);
-size_t force_smem_for(int T, int scap, int cap, int K);
+size_t force_smem_for(int T, int scap, int K);
 cudaError_t launch_pack(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type);
 cudaError_t launch_type_grad(nb_ctx *ctx, const double *gsig_tab, const double *geps_tab, double *gsig, double *geps);
 cudaError_t launch_adjoint_tile(nb_ctx *ctx, const double *d_dLdE, float *d_dpos, float *d_dq);

@@ -9,7 +9,7 @@
 // runs the same binning and force kernels as nb_build_cells + nb_forces for
 // one system of at most NB_NOALLOC_MAX_ATOMS atoms, with every scratch buffer
 // carved from one file-scope device array (g_noalloc_scratch below, about
-// 0.8 MiB).  That array exists on every GPU that loads this library, for as
+// 4.5 MiB).  That array exists on every GPU that loads this library, for as
 // long as the library stays loaded.
 //
 // In host code the name g_noalloc_scratch only stands for the device symbol;
@@ -38,7 +38,8 @@ namespace {
 
 constexpr int kMaxAtoms = NB_NOALLOC_MAX_ATOMS;
 constexpr int kMaxCols = NB_NOALLOC_MAX_COLUMNS;
-constexpr int kListCap = 512;
+constexpr int kListCap = 256;  // entries per half list
+constexpr int kZbEntries = 65536;  // z-bin index entries (bins per column shrink to fit)
 constexpr int kMaxDevices = 64;
 constexpr long long kSlots = ((long long)kMaxAtoms + (kCluster - 1) * (long long)kMaxCols + kCluster - 1) /
                              kCluster * kCluster;
@@ -64,7 +65,12 @@ constexpr size_t oInv = oPerm + a256(4ull * kSlots);
 constexpr size_t oBb = oInv + a256(4ull * kMaxAtoms);
 constexpr size_t oClusSys = oBb + a256(32ull * kClus);
 constexpr size_t oSysAcc = oClusSys + a256(4ull * kClus);
-constexpr size_t oCounts = oSysAcc + a256(8ull * kTaskVals);
+constexpr size_t oFacc = oSysAcc + a256(8ull * kTaskVals);
+constexpr size_t oList = oFacc + a256(24ull * kSlots);
+constexpr size_t oListN = oList + a256(8ull * kClus * kListCap);
+constexpr size_t oPslot = oListN + a256(8ull * kClus);
+constexpr size_t oZbin = oPslot + a256(4ull * kSlots * kMaxPartners);
+constexpr size_t oCounts = oZbin + a256(8ull * kZbEntries);
 constexpr size_t oStatus = oCounts + a256(16);
 constexpr size_t oLj = oStatus + a256(16);
 constexpr size_t oDbg = oLj + a256(8ull * kMaxTypes * kMaxTypes);
@@ -109,9 +115,10 @@ extern "C" nb_status nb_forces_noalloc(const nb_params *params, const float *d_p
     const nb_params &p = *params;
     if (p.n_atoms > kMaxAtoms) return NB_ERR_TOO_LARGE;
     SysDesc S;
-    host::init_sysdesc(p, S, 0, 0);
+    host::init_sysdesc(p, S, 0, 0, 0);
     const int C = S.nx * S.ny;
     if (C > kMaxCols) return NB_ERR_TOO_LARGE;
+    host::init_sysdesc(p, S, 0, 0, 0, kZbEntries / C - 1);
     PairParams pp;
     if (host::init_pair_params(p, pp) != NB_OK) return NB_ERR_UNSUPPORTED;
     // topology: per-atom partners (orig << 1) | is14, padded with -1
@@ -161,10 +168,12 @@ extern "C" nb_status nb_forces_noalloc(const nb_params *params, const float *d_p
     c.built = true;
     c.pp = pp;
     c.tune.blocks_per_sm = 3;
-    c.tune.stage_capacity = 160;
+    c.tune.stage_capacity = 96;
     c.tune.list_capacity = kListCap;
     c.tune.reserved = 0;
-    c.stage_cap = 160;
+    c.stage_cap = 96;
+    c.list_cap = kListCap;
+    c.zb_total = host::zbin_entries(S);
     c.comb_rule = p.comb_rule;
     DevBuffers &d = c.d;
     d.sys = at<SysDesc>(base, oSys);
@@ -184,6 +193,11 @@ extern "C" nb_status nb_forces_noalloc(const nb_params *params, const float *d_p
     d.bb = at<float4>(base, oBb);
     d.clus_sys = at<int>(base, oClusSys);
     d.sys_acc = at<long long>(base, oSysAcc);
+    d.facc = at<long long>(base, oFacc);
+    d.list = at<uint32_t>(base, oList);
+    d.list_n = at<int>(base, oListN);
+    d.pslot = at<int>(base, oPslot);
+    d.zbin = at<int2>(base, oZbin);
     d.counts = at<int>(base, oCounts);
     d.status = at<int>(base, oStatus);
     d.lj_tab = at<float2>(base, oLj);

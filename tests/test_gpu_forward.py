@@ -99,7 +99,7 @@ def test_pairs_bit_exact(case):
     ij, n, n_ordered = ctx.debug_pairs()
     ctx.status()
     assert n == npairs
-    assert n_ordered == 2 * n  # every pair is evaluated from both atoms
+    assert n_ordered == n  # every unique pair is evaluated once (Newton's third law)
     want = oracle.pairs(s)
     assert np.array_equal(ij, want)
 
