@@ -73,7 +73,7 @@ nb_status allocate(nb_ctx *c)
     ALLOC(d.wpos, N);
     ALLOC(d.part_orig, N * c->K);
     ALLOC(d.col_sys, C);
-    ALLOC(d.col_count, C);
+    ALLOC(d.col_count, C + 1);
     ALLOC(d.col_fill, C);
     ALLOC(d.col_slot, C + 1);
     ALLOC(d.stage, S);

@@ -24,32 +24,25 @@ __device__ __forceinline__ int column_of(float x, float inv_w, int n)
     return c;
 }
 
-// A1: one atom per thread: wrap, column index, column histogram.
-__global__ void k_bin(int n, const float *__restrict__ pos, const SysDesc *__restrict__ sys,
-                      const int *__restrict__ atom_sys, float4 *__restrict__ wpos, int *__restrict__ atom_col,
-                      int *__restrict__ col_count, int *__restrict__ status)
+// Warp-aggregated counter update: lanes with the same key (-1 = none) take
+// consecutive positions from one atomic per distinct key; returns the old
+// counter value plus the lane's rank among its peers.
+__device__ __forceinline__ int warp_aggregated_add(int *counter_base, int key)
 {
-    int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= n) return;
-    const SysDesc &S = sys[atom_sys[a]];
-    float x = pos[3 * a], y = pos[3 * a + 1], z = pos[3 * a + 2];
-    if (!(isfinite(x) && isfinite(y) && isfinite(z))) {
-        atomicOr(status, ST_NONFINITE);
-        x = 0.0f; y = 0.0f; z = 0.0f;
-    }
-    x = wrap_coord(x, S.L[0]);
-    y = wrap_coord(y, S.L[1]);
-    z = wrap_coord(z, S.L[2]);
-    int col = S.col_begin + column_of(y, S.inv_w[1], S.ny) * S.nx + column_of(x, S.inv_w[0], S.nx);
-    atom_col[a] = col;
-    wpos[a] = make_float4(x, y, z, 0.0f);
-    atomicAdd(&col_count[col], 1);
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    int base = 0;
+    if (key >= 0 && lane == leader) base = atomicAdd(&counter_base[key], __popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    return base + __popc(peers & ((1u << lane) - 1u));
 }
 
-// A2: exclusive scan of the padded column sizes (single block).  Also fills
-// the scatter cursors, the totals and the per-system slot/cluster ranges.
-__global__ void k_scan(int n_cols, int n_sys, const int *__restrict__ col_count, int *__restrict__ col_slot,
-                       int *__restrict__ col_fill, SysDesc *__restrict__ sys, int *__restrict__ counts)
+// Block-wide exclusive scan of the padded column sizes (one block).  Fills
+// the column slot offsets, the scatter cursors, the totals and the
+// per-system slot/cluster ranges.
+__device__ void scan_columns(int n_cols, int n_sys, const int *__restrict__ col_count, int *__restrict__ col_slot,
+                             int *__restrict__ col_fill, SysDesc *__restrict__ sys, int *__restrict__ counts)
 {
     __shared__ int warp_sum[32];
     __shared__ int carry;
@@ -58,7 +51,7 @@ __global__ void k_scan(int n_cols, int n_sys, const int *__restrict__ col_count,
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int base = 0; base < n_cols; base += blockDim.x) {
         int c = base + threadIdx.x;
-        int v = c < n_cols ? (col_count[c] + kCluster - 1) / kCluster * kCluster : 0;
+        int v = c < n_cols ? (__ldcg(&col_count[c]) + kCluster - 1) / kCluster * kCluster : 0;
         int x = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -97,60 +90,152 @@ __global__ void k_scan(int n_cols, int n_sys, const int *__restrict__ col_count,
     }
 }
 
+// A1 + A2: one atom per thread: wrap, column index, column histogram
+// (warp-aggregated atomics); the last block to finish scans the histogram.
+// col_count[n_cols] is the completion ticket (zero on entry, reset on exit).
+__global__ void k_bin(int n, const float *__restrict__ pos, SysDesc *__restrict__ sys,
+                      const int *__restrict__ atom_sys, float4 *__restrict__ wpos, int *__restrict__ atom_col,
+                      int *__restrict__ col_count, int n_cols, int n_sys, int *__restrict__ col_slot,
+                      int *__restrict__ col_fill, int *__restrict__ counts, int *__restrict__ status)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    int col = -1;
+    if (a < n) {
+        const SysDesc &S = sys[atom_sys[a]];
+        float x = pos[3ll * a], y = pos[3ll * a + 1], z = pos[3ll * a + 2];
+        if (!(isfinite(x) && isfinite(y) && isfinite(z))) {
+            atomicOr(status, ST_NONFINITE);
+            x = 0.0f; y = 0.0f; z = 0.0f;
+        }
+        x = wrap_coord(x, S.L[0]);
+        y = wrap_coord(y, S.L[1]);
+        z = wrap_coord(z, S.L[2]);
+        col = S.col_begin + column_of(y, S.inv_w[1], S.ny) * S.nx + column_of(x, S.inv_w[0], S.nx);
+        atom_col[a] = col;
+        wpos[a] = make_float4(x, y, z, 0.0f);
+    }
+    warp_aggregated_add(col_count, col);
+    // last block: the histogram is complete.  The barrier orders the block's
+    // counter updates before thread 0's fence, which (cumulatively) orders
+    // them before the ticket.
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&col_count[n_cols], 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    scan_columns(n_cols, n_sys, col_count, col_slot, col_fill, sys, counts);
+    if (threadIdx.x == 0) col_count[n_cols] = 0;
+}
+
 // A3a: place atoms into their column segment (order fixed by the sort below).
 __global__ void k_scatter(int n, const int *__restrict__ atom_col, int *__restrict__ col_fill,
                           int *__restrict__ stage)
 {
-    int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= n) return;
-    int p = atomicAdd(&col_fill[atom_col[a]], 1);
-    stage[p] = a;
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    const int col = a < n ? atom_col[a] : -1;
+    const int p = warp_aggregated_add(col_fill, col);
+    if (a < n) stage[p] = a;
 }
 
 constexpr int kSortSmem = 1024;  // atoms per column sorted from shared memory
+constexpr int kSortThreads = 128;
+constexpr int kSortPer = kSortSmem / kSortThreads;  // atoms per thread (shared-memory path)
+
+// Sort key of (z, atom index): z >= 0 after wrapping (+0.0f turns -0 into
+// +0), so its IEEE bits order like the value; the index breaks ties.
+__device__ __forceinline__ unsigned long long zkey(float z, int a)
+{
+    return ((unsigned long long)__float_as_uint(z + 0.0f) << 32) | (unsigned)a;
+}
+
+// rank[u] += number of the n shared keys smaller than key[u], u < U.
+template <int U>
+__device__ __forceinline__ void rank_keys(const unsigned long long *skey, int n, const unsigned long long *key,
+                                          int *rank)
+{
+#pragma unroll 4
+    for (int m = 0; m < n; ++m) {
+        const unsigned long long km = skey[m];
+#pragma unroll
+        for (int u = 0; u < U; ++u) rank[u] += km < key[u];
+    }
+}
 
 // A3b: one block per column: rank sort by (z, atom index), write the sorted
 // slot arrays and padding, the cluster bounding boxes and the column's z-bin
 // index (the clusters are z-sorted, so their z_lo and z_hi never decrease).
-__global__ void k_colsort(const int *__restrict__ col_count, const int *__restrict__ col_slot,
-                          const int *__restrict__ col_sys, const SysDesc *__restrict__ sys,
-                          const int *__restrict__ stage, const float4 *__restrict__ wpos, float4 *__restrict__ xyzq,
-                          int *__restrict__ tslot, int *__restrict__ perm, int *__restrict__ inv,
-                          float4 *__restrict__ bb, int *__restrict__ clus_sys, int2 *__restrict__ zbin)
+// Columns of up to kSortSmem atoms sort from shared memory: every thread
+// holds up to kSortPer keys and counts, per broadcast key, how many are
+// smaller.
+__global__ void __launch_bounds__(kSortThreads) k_colsort(
+    const int *__restrict__ col_count, const int *__restrict__ col_slot, const int *__restrict__ col_sys,
+    const SysDesc *__restrict__ sys, const int *__restrict__ stage, const float4 *__restrict__ wpos,
+    float4 *__restrict__ xyzq, int *__restrict__ tslot, int *__restrict__ perm, int *__restrict__ inv,
+    float4 *__restrict__ bb, int *__restrict__ clus_sys, int2 *__restrict__ zbin)
 {
-    __shared__ float sz[kSortSmem];
-    __shared__ int sid[kSortSmem];
+    __shared__ unsigned long long skey[kSortSmem];
     __shared__ float4 sp[kSortSmem];
     const int c = blockIdx.x;
+    const int tid = threadIdx.x;
     const int n = col_count[c];
     const int base = col_slot[c];
     const int npad = (n + kCluster - 1) / kCluster * kCluster;
     const bool small = n <= kSortSmem;
     if (small) {
-        for (int k = threadIdx.x; k < n; k += blockDim.x) {
-            int a = stage[base + k];
-            sid[k] = a;
-            sz[k] = wpos[a].z;
+        const int nper = (n + kSortThreads - 1) / kSortThreads;
+        unsigned long long key[kSortPer];
+        float4 p[kSortPer];
+        int rank[kSortPer];
+#pragma unroll
+        for (int u = 0; u < kSortPer; ++u) {
+            const int k = tid + u * kSortThreads;
+            key[u] = ~0ull;
+            rank[u] = 0;
+            if (k < n) {
+                const int a = stage[base + k];
+                p[u] = wpos[a];
+                key[u] = zkey(p[u].z, a);
+                skey[k] = key[u];
+            }
         }
         __syncthreads();
-    }
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-        int a = small ? sid[k] : stage[base + k];
-        float z = small ? sz[k] : wpos[a].z;
-        int rank = 0;
-        for (int m = 0; m < n; ++m) {
-            int b = small ? sid[m] : stage[base + m];
-            float zb = small ? sz[m] : wpos[b].z;
-            rank += (zb < z) || (zb == z && b < a);
+        if (nper <= 1) rank_keys<1>(skey, n, key, rank);
+        else if (nper <= 2) rank_keys<2>(skey, n, key, rank);
+        else if (nper <= 4) rank_keys<4>(skey, n, key, rank);
+        else rank_keys<kSortPer>(skey, n, key, rank);
+#pragma unroll
+        for (int u = 0; u < kSortPer; ++u) {
+            const int k = tid + u * kSortThreads;
+            if (k < n) {
+                const int a = (int)(unsigned)(key[u] & 0xffffffffull);
+                const int slot = base + rank[u];
+                perm[slot] = a;
+                inv[a] = slot;
+                xyzq[slot] = make_float4(p[u].x, p[u].y, p[u].z, 0.0f);
+                sp[rank[u]] = p[u];
+            }
         }
-        int slot = base + rank;
-        float4 p = wpos[a];
-        perm[slot] = a;
-        inv[a] = slot;
-        xyzq[slot] = make_float4(p.x, p.y, p.z, 0.0f);
-        if (small) sp[rank] = p;
+    } else {
+        for (int k = tid; k < n; k += blockDim.x) {
+            const int a = stage[base + k];
+            const float4 pa = wpos[a];
+            const unsigned long long ka = zkey(pa.z, a);
+            int rank = 0;
+            for (int m = 0; m < n; ++m) {
+                const int b = stage[base + m];
+                rank += zkey(wpos[b].z, b) < ka;
+            }
+            const int slot = base + rank;
+            perm[slot] = a;
+            inv[a] = slot;
+            xyzq[slot] = make_float4(pa.x, pa.y, pa.z, 0.0f);
+        }
     }
-    for (int k = n + threadIdx.x; k < npad; k += blockDim.x) {
+    for (int k = n + tid; k < npad; k += blockDim.x) {
         perm[base + k] = -1;
         tslot[base + k] = 0;
         xyzq[base + k] = make_float4(kPadCoord, kPadCoord, kPadCoord, 0.0f);
@@ -158,36 +243,40 @@ __global__ void k_colsort(const int *__restrict__ col_count, const int *__restri
     __syncthreads();
     // cluster bounding boxes over the real atoms of each 8-slot cluster
     const int nclus = npad / kCluster;
-    for (int q = threadIdx.x; q < nclus; q += blockDim.x) {
+    for (int q = tid; q < nclus; q += blockDim.x) {
         float lx = INFINITY, ly = INFINITY, lz = INFINITY, hx = -INFINITY, hy = -INFINITY, hz = -INFINITY;
         for (int k = q * kCluster; k < min(n, (q + 1) * kCluster); ++k) {
-            float4 p = small ? sp[k] : xyzq[base + k];
+            const float4 p = small ? sp[k] : xyzq[base + k];
             lx = fminf(lx, p.x); ly = fminf(ly, p.y); lz = fminf(lz, p.z);
             hx = fmaxf(hx, p.x); hy = fmaxf(hy, p.y); hz = fmaxf(hz, p.z);
         }
-        int I = base / kCluster + q;
+        const int I = base / kCluster + q;
         bb[2 * I] = make_float4(lx, ly, lz, 0.0f);
         bb[2 * I + 1] = make_float4(hx, hy, hz, 0.0f);
         clus_sys[I] = col_sys[c];
     }
     __syncthreads();
     // z-bin index: for b = 0..nzb, (first cluster with z_hi >= b dz, first
-    // cluster with z_lo > (b + 1) dz), by binary search over the column
+    // cluster with z_lo > (b + 1) dz), by binary search over the column.  The
+    // atoms are z-sorted: a cluster's z_lo is its first atom's z and its z_hi
+    // its last real atom's z.
     const SysDesc &S = sys[col_sys[c]];
     const float4 *cb = bb + 2ll * (base / kCluster);
     int2 *zt = zbin + S.zb_begin + (long long)(c - S.col_begin) * (S.nzb + 1);
-    for (int b = threadIdx.x; b <= S.nzb; b += blockDim.x) {
+    for (int b = tid; b <= S.nzb; b += blockDim.x) {
         const float z0 = (float)b * S.dz, z1 = (float)(b + 1) * S.dz;
-        int lo = 0, hi = nclus;  // first q with cb[q].hi.z >= z0
+        int lo = 0, hi = nclus;  // first q with z_hi(q) >= z0
         while (lo < hi) {
             const int m = (lo + hi) >> 1;
-            if (cb[2 * m + 1].z >= z0) hi = m;
+            const float zh = small ? sp[min(n, (m + 1) * kCluster) - 1].z : cb[2 * m + 1].z;
+            if (zh >= z0) hi = m;
             else lo = m + 1;
         }
-        int lo2 = 0, hi2 = nclus;  // first q with cb[q].lo.z > z1
+        int lo2 = 0, hi2 = nclus;  // first q with z_lo(q) > z1
         while (lo2 < hi2) {
             const int m = (lo2 + hi2) >> 1;
-            if (cb[2 * m].z > z1) hi2 = m;
+            const float zl = small ? sp[m * kCluster].z : cb[2 * m].z;
+            if (zl > z1) hi2 = m;
             else lo2 = m + 1;
         }
         zt[b] = make_int2(lo, lo2);
@@ -220,7 +309,29 @@ __device__ __forceinline__ bool keep_half(int I, int J, uint32_t code)
 // (column round, candidate round, lane) order, so the lists are
 // deterministic.  Also writes the partner slots of I's atoms and flags the
 // entries whose cluster holds a topology partner of I.
-__global__ void __launch_bounds__(256) k_list(const SysDesc *__restrict__ sys, const int *__restrict__ counts,
+// Candidate v of a column window (virtual index: image -L below 0, +L from
+// nj): J when its bounding box comes within rc + margin of I's, else -1;
+// code receives the entry's shift code.
+__device__ __forceinline__ int window_candidate(const float4 *__restrict__ bb, float4 lo, float4 hi, int v, int jb,
+                                                int nj, uint32_t code_xy, float ox, float oy, float Lz, float rcm2,
+                                                uint32_t &code)
+{
+    const uint32_t zimg = v < 0 ? 1u : (v >= nj ? 2u : 0u);
+    const int J = jb + v + (zimg == 1u ? nj : (zimg == 2u ? -nj : 0));
+    const float oz = zimg == 1u ? -Lz : (zimg == 2u ? Lz : 0.0f);
+    const float4 jl = bb[2 * J], jh = bb[2 * J + 1];
+    const float gx = fmaxf(fmaxf((jl.x + ox) - hi.x, lo.x - (jh.x + ox)), 0.0f);
+    const float gy = fmaxf(fmaxf((jl.y + oy) - hi.y, lo.y - (jh.y + oy)), 0.0f);
+    const float gz = fmaxf(fmaxf((jl.z + oz) - hi.z, lo.z - (jh.z + oz)), 0.0f);
+    code = code_xy | (zimg << 4);
+    return gx * gx + gy * gy + gz * gz < rcm2 ? J : -1;
+}
+
+constexpr int kListWarps = 8;   // warps (clusters in flight) per block of the list kernel
+constexpr int kListGroup = 64;  // candidate columns compacted per pass
+constexpr int kPartnerRounds = (kCluster * kMaxPartners + 31) / 32;
+
+__global__ void __launch_bounds__(kListWarps * 32) k_list(const SysDesc *__restrict__ sys, const int *__restrict__ counts,
                                               const float4 *__restrict__ bb, const int *__restrict__ clus_sys,
                                               const int *__restrict__ col_slot, const int2 *__restrict__ zbin,
                                               const int *__restrict__ perm,
@@ -236,6 +347,9 @@ __global__ void __launch_bounds__(256) k_list(const SysDesc *__restrict__ sys, c
     const int nw = (gridDim.x * blockDim.x) >> 5;
     const int n_clus = counts[1];
     const float rcm2 = rcm * rcm;
+    __shared__ int s_col[kListWarps][kListGroup];  // compacted candidate columns per warp
+    __shared__ int s_pcl[kListWarps][32];          // distinct partner clusters per warp
+    const int wib = threadIdx.x >> 5;
     for (int I = gw; I < n_clus; I += nw) {
         const SysDesc &S = sys[clus_sys[I]];
         const float4 lo = bb[2 * I], hi = bb[2 * I + 1];
@@ -243,17 +357,29 @@ __global__ void __launch_bounds__(256) k_list(const SysDesc *__restrict__ sys, c
         int pcl = -1, npc = 0;
         bool flag_all = false;
         const int np = kCluster * K;
-        for (int b = 0; b < np; b += 32) {
-            int v = -1, c = -1;
-            if (b + lane < np) {
-                const int a = perm[I * kCluster + (b + lane) / K];
-                if (a >= 0) {
-                    const int p = part_orig[(long long)a * K + (b + lane) % K];
-                    if (p >= 0) v = (inv[p >> 1] << 1) | (p & 1);
-                }
-                pslot[(long long)I * np + b + lane] = v;
-                if (v >= 0) c = (v >> 1) / kCluster;
-            }
+        // the loads of all rounds first (three dependent levels, not three per round)
+        int pv[kPartnerRounds];
+#pragma unroll
+        for (int r = 0; r < kPartnerRounds; ++r) {
+            const int t = r * 32 + lane;
+            pv[r] = t < np ? perm[I * kCluster + t / K] : -1;
+        }
+#pragma unroll
+        for (int r = 0; r < kPartnerRounds; ++r) {
+            const int t = r * 32 + lane;
+            pv[r] = pv[r] >= 0 ? part_orig[(long long)pv[r] * K + t % K] : -1;
+        }
+#pragma unroll
+        for (int r = 0; r < kPartnerRounds; ++r) {
+            const int t = r * 32 + lane;
+            pv[r] = pv[r] >= 0 ? (inv[pv[r] >> 1] << 1) | (pv[r] & 1) : -1;
+            if (t < np) pslot[(long long)I * np + t] = pv[r];
+        }
+#pragma unroll
+        for (int r = 0; r < kPartnerRounds; ++r) {
+            if (r * 32 >= np) break;
+            const int v = pv[r];
+            const int c = v >= 0 ? (v >> 1) / kCluster : -1;
             const unsigned peers = __match_any_sync(FULL, c);
             bool leader = c >= 0 && (__ffs(peers) - 1) == lane;
             for (int m = 0; m < npc; ++m)
@@ -267,11 +393,13 @@ __global__ void __launch_bounds__(256) k_list(const SysDesc *__restrict__ sys, c
             }
             npc = min(32, npc + __popc(bal));
         }
+        __syncwarp();
+        if (lane < npc) s_pcl[wib][lane] = pcl;
+        __syncwarp();
         const int cxa = max(-S.nx, (int)floorf((lo.x - rcm) * S.inv_w[0]));
         const int cxb = min(2 * S.nx - 1, (int)floorf((hi.x + rcm) * S.inv_w[0]));
         const int cya = max(-S.ny, (int)floorf((lo.y - rcm) * S.inv_w[1]));
         const int cyb = min(2 * S.ny - 1, (int)floorf((hi.y + rcm) * S.inv_w[1]));
-        const bool zdn = (lo.z - rcm) < 0.0f, zup = (hi.z + rcm) >= S.L[2];
         const float Lz = S.L[2];
         // conservative margin of the column-geometry test (binning rounds in FP32)
         const float cmarg = 1e-3f + 1e-6f * fmaxf(S.L[0], S.L[1]);
@@ -279,17 +407,31 @@ __global__ void __launch_bounds__(256) k_list(const SysDesc *__restrict__ sys, c
         int nA = 0, nB = 0;
         uint32_t *LA = list + (long long)(2 * I) * cap;
         uint32_t *LB = LA + cap;
-        for (int c0 = 0; c0 < ncand; c0 += 32) {
-            const int c = c0 + lane;
-            int jb = 0, nj = 0, va = 0, cnt = 0;
-            uint32_t code_xy = 0u;
-            float ox = 0.0f, oy = 0.0f;
-            if (c < ncand) {
-                const int cy = cya + c / ncx, cx = cxa + c % ncx;
-                // lower bound of the xy gap from the column's geometry
-                const float gcx = fmaxf(fmaxf(cx * S.w[0] - hi.x, lo.x - (cx + 1) * S.w[0]) - cmarg, 0.0f);
-                const float gcy = fmaxf(fmaxf(cy * S.w[1] - hi.y, lo.y - (cy + 1) * S.w[1]) - cmarg, 0.0f);
-                if (gcx * gcx + gcy * gcy < rcm2) {
+        for (int g0 = 0; g0 < ncand; g0 += kListGroup) {
+            // the candidate columns of this group whose geometry (a lower bound of
+            // the xy gap) passes, compacted in order
+            int npass = 0;
+            for (int h = 0; h < kListGroup; h += 32) {
+                const int c = g0 + h + lane;
+                bool pass = false;
+                if (c < ncand) {
+                    const int cy = cya + c / ncx, cx = cxa + c % ncx;
+                    const float gcx = fmaxf(fmaxf(cx * S.w[0] - hi.x, lo.x - (cx + 1) * S.w[0]) - cmarg, 0.0f);
+                    const float gcy = fmaxf(fmaxf(cy * S.w[1] - hi.y, lo.y - (cy + 1) * S.w[1]) - cmarg, 0.0f);
+                    pass = gcx * gcx + gcy * gcy < rcm2;
+                }
+                const unsigned b = __ballot_sync(FULL, pass);
+                if (pass) s_col[wib][npass + __popc(b & lt)] = c;
+                npass += __popc(b);
+            }
+            __syncwarp();
+            for (int r0 = 0; r0 < npass; r0 += 32) {
+                const int c = r0 + lane < npass ? s_col[wib][r0 + lane] : -1;
+                int jb = 0, nj = 0, va = 0, cnt = 0;
+                uint32_t code_xy = 0u;
+                float ox = 0.0f, oy = 0.0f;
+                if (c >= 0) {
+                    const int cy = cya + c / ncx, cx = cxa + c % ncx;
                     const int ccy = cy < 0 ? cy + S.ny : (cy >= S.ny ? cy - S.ny : cy);
                     const int ccx = cx < 0 ? cx + S.nx : (cx >= S.nx ? cx - S.nx : cx);
                     const uint32_t sy = cy < 0 ? 1u : (cy >= S.ny ? 2u : 0u);
@@ -314,59 +456,60 @@ __global__ void __launch_bounds__(256) k_list(const SysDesc *__restrict__ sys, c
                         cnt = vhi - vlo;
                     }
                 }
-            }
-            // flatten the windows of the 32 lanes
-            int incl = cnt;
+                // flatten the windows of the 32 lanes
+                int incl = cnt;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(FULL, incl, o);
-                if (lane >= o) incl += y;
-            }
-            const int off = incl - cnt, total = __shfl_sync(FULL, incl, 31);
-            for (int p0 = 0; p0 < total; p0 += 32) {
-                const int p = p0 + lane;
-                // owner lane: the last lane whose window starts at or before p
-                int src = 0;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(FULL, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const int off = incl - cnt, total = __shfl_sync(FULL, incl, 31);
+                // two candidate rounds at a time: both rounds' box loads are in
+                // flight together; entries are appended in round order
+                for (int p0 = 0; p0 < total; p0 += 64) {
+                    int J[2];
+                    uint32_t code[2];
 #pragma unroll
-                for (int step = 16; step >= 1; step >>= 1) {
-                    const int o2 = __shfl_sync(FULL, off, src + step);
-                    if (o2 <= p) src += step;
+                    for (int h = 0; h < 2; ++h) {
+                        const int p = p0 + 32 * h + lane;
+                        // owner lane: the last lane whose window starts at or before p
+                        int src = 0;
+#pragma unroll
+                        for (int step = 16; step >= 1; step >>= 1) {
+                            const int o2 = __shfl_sync(FULL, off, src + step);
+                            if (o2 <= p) src += step;
+                        }
+                        const int s_off = __shfl_sync(FULL, off, src), s_va = __shfl_sync(FULL, va, src);
+                        const int s_jb = __shfl_sync(FULL, jb, src), s_nj = __shfl_sync(FULL, nj, src);
+                        const uint32_t s_code = __shfl_sync(FULL, code_xy, src);
+                        const float s_ox = __shfl_sync(FULL, ox, src), s_oy = __shfl_sync(FULL, oy, src);
+                        J[h] = -1;
+                        code[h] = 0u;
+                        if (p < total)
+                            J[h] = window_candidate(bb, lo, hi, s_va + (p - s_off), s_jb, s_nj, s_code, s_ox, s_oy, Lz,
+                                                    rcm2, code[h]);
+                    }
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        bool fl = flag_all;
+                        for (int m = 0; m < npc; ++m) fl |= s_pcl[wib][m] == J[h];
+                        const uint32_t ent = (uint32_t)J[h] | (code[h] << kShiftBit) | (fl ? kExclFlag : 0u);
+                        const bool hitA = J[h] >= 0 && keep_half(I, J[h], code[h]), hitB = J[h] >= 0 && !hitA;
+                        const unsigned bA = __ballot_sync(FULL, hitA), bB = __ballot_sync(FULL, hitB);
+                        if (hitA) {
+                            const int q = nA + __popc(bA & lt);
+                            if (q < cap) LA[q] = ent;
+                        }
+                        if (hitB) {
+                            const int q = nB + __popc(bB & lt);
+                            if (q < cap) LB[q] = ent;
+                        }
+                        nA += __popc(bA);
+                        nB += __popc(bB);
+                    }
                 }
-                const int s_off = __shfl_sync(FULL, off, src), s_va = __shfl_sync(FULL, va, src);
-                const int s_jb = __shfl_sync(FULL, jb, src), s_nj = __shfl_sync(FULL, nj, src);
-                const uint32_t s_code = __shfl_sync(FULL, code_xy, src);
-                const float s_ox = __shfl_sync(FULL, ox, src), s_oy = __shfl_sync(FULL, oy, src);
-                bool hit = false;
-                int J = -1;
-                uint32_t code = 0u;
-                if (p < total) {
-                    const int v = s_va + (p - s_off);
-                    const uint32_t zimg = v < 0 ? 1u : (v >= s_nj ? 2u : 0u);
-                    J = s_jb + v + (zimg == 1u ? s_nj : (zimg == 2u ? -s_nj : 0));
-                    const float oz = zimg == 1u ? -Lz : (zimg == 2u ? Lz : 0.0f);
-                    const float4 jl = bb[2 * J], jh = bb[2 * J + 1];
-                    const float gx = fmaxf(fmaxf((jl.x + s_ox) - hi.x, lo.x - (jh.x + s_ox)), 0.0f);
-                    const float gy = fmaxf(fmaxf((jl.y + s_oy) - hi.y, lo.y - (jh.y + s_oy)), 0.0f);
-                    const float gz = fmaxf(fmaxf((jl.z + oz) - hi.z, lo.z - (jh.z + oz)), 0.0f);
-                    hit = gx * gx + gy * gy + gz * gz < rcm2;
-                    code = s_code | (zimg << 4);
-                }
-                bool fl = flag_all;
-                for (int m = 0; m < npc; ++m) fl |= (__shfl_sync(FULL, pcl, m) == J);
-                const uint32_t ent = (uint32_t)J | (code << kShiftBit) | (fl ? kExclFlag : 0u);
-                const bool hitA = hit && keep_half(I, J, code), hitB = hit && !hitA;
-                const unsigned bA = __ballot_sync(FULL, hitA), bB = __ballot_sync(FULL, hitB);
-                if (hitA) {
-                    const int q = nA + __popc(bA & lt);
-                    if (q < cap) LA[q] = ent;
-                }
-                if (hitB) {
-                    const int q = nB + __popc(bB & lt);
-                    if (q < cap) LB[q] = ent;
-                }
-                nA += __popc(bA);
-                nB += __popc(bB);
             }
+            __syncwarp();
         }
         if (lane == 0) {
             list_n[2 * I] = min(nA, cap);
@@ -381,15 +524,15 @@ cudaError_t launch_build(nb_ctx *ctx, const float *d_pos)
     auto &d = ctx->d;
     cudaStream_t st = ctx->stream;
     const int N = (int)ctx->n_atoms;
-    cudaError_t e = cudaMemsetAsync(d.col_count, 0, sizeof(int) * ctx->n_cols, st);
+    cudaError_t e = cudaMemsetAsync(d.col_count, 0, sizeof(int) * (ctx->n_cols + 1), st);
     if (e != cudaSuccess) return e;
     const int tb = 256;
-    k_bin<<<(N + tb - 1) / tb, tb, 0, st>>>(N, d_pos, d.sys, d.atom_sys, d.wpos, d.atom_col, d.col_count, d.status);
-    k_scan<<<1, 1024, 0, st>>>(ctx->n_cols, ctx->n_sys, d.col_count, d.col_slot, d.col_fill, d.sys, d.counts);
+    k_bin<<<(N + tb - 1) / tb, tb, 0, st>>>(N, d_pos, d.sys, d.atom_sys, d.wpos, d.atom_col, d.col_count,
+                                            ctx->n_cols, ctx->n_sys, d.col_slot, d.col_fill, d.counts, d.status);
     k_scatter<<<(N + tb - 1) / tb, tb, 0, st>>>(N, d.atom_col, d.col_fill, d.stage);
-    k_colsort<<<ctx->n_cols, 128, 0, st>>>(d.col_count, d.col_slot, d.col_sys, d.sys, d.stage, d.wpos, d.xyzq,
+    k_colsort<<<ctx->n_cols, kSortThreads, 0, st>>>(d.col_count, d.col_slot, d.col_sys, d.sys, d.stage, d.wpos, d.xyzq,
                                            d.tslot, d.perm, d.inv, d.bb, d.clus_sys, d.zbin);
-    const int lw = 8;  // warps (clusters) per block of the list kernel
+    const int lw = kListWarps;
     const int lblocks = (int)std::max<int64_t>(1, (ctx->clus_cap + lw - 1) / lw);
     k_list<<<lblocks, lw * 32, 0, st>>>(d.sys, d.counts, d.bb, d.clus_sys, d.col_slot, d.zbin, d.perm, d.part_orig,
                                         d.inv,

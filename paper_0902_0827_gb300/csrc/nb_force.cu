@@ -388,12 +388,64 @@ __device__ __forceinline__ void eval_item(const ForceArgs &A, const ForceSmem &S
         eval_pair<EWALD, VIRIAL>(A.P, S.lj, ia.ti_row, ia.qi, active, dx, dy, dz, active ? r2 : 1.0f, pj.w, tj,
                                  (item & 1u) != 0u, acc, fjx, fjy, fjz);
         if (active) {
+            // one range check per pair: each component below 2^26 keeps the
+            // fixed-point sums inside int64
+            if (!(fmaxf(fabsf(fjx), fmaxf(fabsf(fjy), fabsf(fjz))) < 67108864.0f)) atomicOr(A.status, ST_OVERFLOW);
             const int js = A.scap * kCluster;
-            atomicAdd(&S.jf[idx], (unsigned long long)to_fixed(fjx, A.status));
-            atomicAdd(&S.jf[js + idx], (unsigned long long)to_fixed(fjy, A.status));
-            atomicAdd(&S.jf[2 * js + idx], (unsigned long long)to_fixed(fjz, A.status));
+            unsigned long long *slot = S.jf + idx;
+            atomicAdd(slot, (unsigned long long)__float2ll_rn(fjx * 4294967296.0f));
+            atomicAdd(slot + js, (unsigned long long)__float2ll_rn(fjy * 4294967296.0f));
+            atomicAdd(slot + 2 * js, (unsigned long long)__float2ll_rn(fjz * 4294967296.0f));
         }
     }
+}
+
+// Per-cluster inputs of a warp (one i atom): system, sorted coordinates and
+// charge, type, list lengths, topology partner slot of this lane and (adjoint)
+// dL/dF of the atom.
+struct ClusterHead {
+    int sys_id;
+    float4 pi;
+    int ti;
+    int nA, nE;
+    int pe;
+    float4 gi;
+};
+
+template <bool ADJ>
+__device__ __forceinline__ ClusterHead load_head(const ForceArgs &A, int I, int w, int lane)
+{
+    ClusterHead h;
+    const long long islot = (long long)I * kCluster + w;
+    h.sys_id = __ldg(A.clus_sys + I);
+    h.pi = __ldg(A.xyzq + islot);
+    h.ti = __ldg(A.tslot + islot);
+    h.nA = __ldg(A.list_n + 2 * I);
+    h.nE = ADJ ? h.nA + __ldg(A.list_n + 2 * I + 1) : h.nA;
+    h.pe = lane < A.K ? __ldg(A.pslot + islot * A.K + lane) : -1;
+    if (ADJ) h.gi = __ldg(A.gslot + islot);
+    return h;
+}
+
+// Add the per-lane fixed-point energy/virial of a system to its global sums
+// (warp reduction, block accumulator, one atomic per value and block).
+template <bool VIRIAL>
+__device__ __forceinline__ void flush_energy(const ForceArgs &A, const ForceSmem &S, const long long *wacc, int sys,
+                                             int lane)
+{
+#pragma unroll
+    for (int k = 0; k < (VIRIAL ? kTaskVals : 2); ++k) {
+        long long x = wacc[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+        if (lane == 0) atomicAdd(&S.cacc[k], (unsigned long long)x);
+    }
+    __syncthreads();
+    if (threadIdx.x < kTaskVals) {
+        atomicAdd((unsigned long long *)&A.sys_acc[sys * kTaskVals + threadIdx.x], S.cacc[threadIdx.x]);
+        S.cacc[threadIdx.x] = 0ull;
+    }
+    __syncthreads();
 }
 
 // Forward: add the block's fixed-point forces of the n staged j clusters
@@ -440,39 +492,32 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
     using AccT = typename std::conditional<ADJ, AccAdj, Acc>::type;
 
     int cur_sys = -1;
-    long long wacc[kTaskVals];
+    float Lx = 0.0f, Ly = 0.0f, Lz = 0.0f;
+    long long wacc[kTaskVals];  // per lane: fixed-point energy/virial of the current system
 #pragma unroll
     for (int k = 0; k < kTaskVals; ++k) wacc[k] = 0;
     const int n_clus = A.counts[1];
     const float rcm2 = A.P.rcm2;
 
     for (int I = blockIdx.x; I < n_clus; I += gridDim.x) {
-        const int sys_id = A.clus_sys[I];
-        if (!ADJ && sys_id != cur_sys) {
-            // flush the per-warp energy/virial of the previous system through
-            // the block accumulator (integer sums: order independent)
-            if (cur_sys >= 0) {
-                if (lane == 0)
-#pragma unroll
-                    for (int k = 0; k < kTaskVals; ++k) atomicAdd(&S.cacc[k], (unsigned long long)wacc[k]);
-                __syncthreads();
-                if (threadIdx.x < kTaskVals) {
-                    atomicAdd((unsigned long long *)&A.sys_acc[cur_sys * kTaskVals + threadIdx.x], S.cacc[threadIdx.x]);
-                    S.cacc[threadIdx.x] = 0ull;
-                }
-                __syncthreads();
-            }
+        const ClusterHead cur = load_head<ADJ>(A, I, w, lane);
+        const int sys_id = cur.sys_id;
+        if (sys_id != cur_sys) {
+            // flush the energy/virial of the previous system through the
+            // block accumulator (integer sums: order independent)
+            if (!ADJ && cur_sys >= 0) flush_energy<VIRIAL>(A, S, wacc, cur_sys, lane);
 #pragma unroll
             for (int k = 0; k < kTaskVals; ++k) wacc[k] = 0;
             cur_sys = sys_id;
+            Lx = A.sys[sys_id].L[0];
+            Ly = A.sys[sys_id].L[1];
+            Lz = A.sys[sys_id].L[2];
         }
-        const SysDesc &SD = A.sys[sys_id];
-        const float Lx = SD.L[0], Ly = SD.L[1], Lz = SD.L[2];
         const int islot = I * kCluster + w;
-        const float4 pi = A.xyzq[islot];
+        const float4 pi = cur.pi;
         const bool iv = is_real_coord(pi.x);
         IAtom ia;
-        ia.ti_row = A.tslot[islot] * T;
+        ia.ti_row = cur.ti * T;
         ia.xi = pi.x;
         ia.yi = pi.y;
         ia.zi = pi.z;
@@ -483,7 +528,7 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
         ia.iorig = DEBUG ? A.perm[islot] : -1;
         const float xi = ia.xi, yi = ia.yi, zi = ia.zi, xim = ia.xim, yim = ia.yim, zim = ia.zim;
         if (ADJ) {
-            const float4 gi = A.gslot[islot];
+            const float4 gi = cur.gi;
             ia.gix = gi.x;
             ia.giy = gi.y;
             ia.giz = gi.z;
@@ -495,9 +540,9 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
         AccT acc;
         memset(&acc, 0, sizeof(acc));
         // forward: the half list (Newton's third law); adjoint: both halves
-        const int nA = A.list_n[2 * I];
-        const int nE = ADJ ? nA + A.list_n[2 * I + 1] : nA;
-        const int pe = lane < A.K ? A.pslot[(long long)islot * A.K + lane] : -1;
+        const int nA = cur.nA;
+        const int nE = cur.nE;
+        const int pe = cur.pe;
         __syncthreads();  // the staging buffers are free
 
         for (int c0 = 0, ci = 0; c0 < nE; c0 += A.scap, ++ci) {
@@ -647,14 +692,11 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
                 atomicAdd((unsigned long long *)&A.facc[3ll * islot + 1], (unsigned long long)vy);
                 atomicAdd((unsigned long long *)&A.facc[3ll * islot + 2], (unsigned long long)vz);
             }
-            // energies and virial of atom i: FP32 butterfly (fixed order), then fixed point
-            float v[kTaskVals] = {acc.elj, acc.ec, acc.w[0], acc.w[1], acc.w[2], acc.w[3], acc.w[4], acc.w[5]};
+            // energies and virial: per lane in fixed point (reduced when the
+            // system's sums are flushed)
+            const float v[kTaskVals] = {acc.elj, acc.ec, acc.w[0], acc.w[1], acc.w[2], acc.w[3], acc.w[4], acc.w[5]};
 #pragma unroll
-            for (int k = 0; k < (VIRIAL ? kTaskVals : 2); ++k) {
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(kFull, v[k], o);
-                wacc[k] += to_fixed(v[k], A.status);
-            }
+            for (int k = 0; k < (VIRIAL ? kTaskVals : 2); ++k) wacc[k] += to_fixed(v[k], A.status);
         }
     }
     if constexpr (ADJ) {
@@ -664,15 +706,9 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
             if (S.tacc[k]) atomicAdd((unsigned long long *)&A.tab_acc[k], S.tacc[k]);
         return;
     }
-    // final flush of the last system
-    if (cur_sys >= 0) {
-        if (lane == 0)
-#pragma unroll
-            for (int k = 0; k < kTaskVals; ++k) atomicAdd(&S.cacc[k], (unsigned long long)wacc[k]);
-        __syncthreads();
-        if (threadIdx.x < kTaskVals)
-            atomicAdd((unsigned long long *)&A.sys_acc[cur_sys * kTaskVals + threadIdx.x], S.cacc[threadIdx.x]);
-    }
+    // final flush of the last system (every block reaches it: cur_sys is
+    // block-uniform)
+    if (cur_sys >= 0) flush_energy<VIRIAL>(A, S, wacc, cur_sys, lane);
 }
 
 // Gather charges and types into sorted order and check that the positions

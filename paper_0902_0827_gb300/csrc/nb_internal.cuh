@@ -90,7 +90,7 @@ struct DevBuffers {
     float4 *wpos = nullptr;          // [N] wrapped coordinates
     int *part_orig = nullptr;        // [N*K] partner (orig << 1) | is14, -1 pad (static)
     int *col_sys = nullptr;          // [C] system of each column (static)
-    int *col_count = nullptr;        // [C]
+    int *col_count = nullptr;        // [C+1] column histogram; [C] = completion ticket of the binning kernel
     int *col_fill = nullptr;         // [C] scatter cursor
     int *col_slot = nullptr;         // [C+1] padded slot offsets
     int *stage = nullptr;            // [S] unsorted atoms per column

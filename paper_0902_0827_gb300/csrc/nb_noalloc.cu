@@ -55,7 +55,7 @@ constexpr size_t oWpos = oAtomCol + a256(4ull * kMaxAtoms);
 constexpr size_t oPart = oWpos + a256(16ull * kMaxAtoms);
 constexpr size_t oColSys = oPart + a256(4ull * kMaxAtoms * kMaxPartners);
 constexpr size_t oColCount = oColSys + a256(4ull * kMaxCols);
-constexpr size_t oColFill = oColCount + a256(4ull * kMaxCols);
+constexpr size_t oColFill = oColCount + a256(4ull * (kMaxCols + 1));
 constexpr size_t oColSlot = oColFill + a256(4ull * kMaxCols);
 constexpr size_t oStage = oColSlot + a256(4ull * (kMaxCols + 1));
 constexpr size_t oXyzq = oStage + a256(4ull * kSlots);
