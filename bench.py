@@ -250,6 +250,23 @@ def batched_leg(steps, flush, dev):
             "gpu_launches_per_step": BUILD_LAUNCHES + FORCE_LAUNCHES}
 
 
+def force_kernel_traffic():
+    """DRAM bytes per force-kernel launch from the committed ncu record, or
+    None when the kernel sources changed since the counters were taken."""
+    import hashlib
+    prof_path = os.path.join(ROOT, "profiles", "force_kernel_traffic.json")
+    try:
+        rec = json.load(open(prof_path))
+        h = hashlib.sha256()
+        for src in rec["sources"]:
+            h.update(open(os.path.join(ROOT, src), "rb").read())
+        if h.hexdigest() != rec["source_sha256"]:
+            return None
+        return rec["bytes_per_launch"]
+    except (OSError, ValueError, KeyError):
+        return None
+
+
 def cpu_oracle_run(system, budget_s: float = 12.0, max_reps: int = 50):
     """The FP64 oracle (cell-list traversal, OpenMP over atoms) timed on the host."""
     import oracle
@@ -377,13 +394,7 @@ def main():
     sm_max = clk.get("sm_max_mhz") or 2070.0
     peak_tflops = n_sms * 128 * 2 * sm_max * 1e6 / 1e12
     achieved = FLOP_PER_PAIR * npairs / (f_avg * 1e-3) / 1e12
-    traffic = None
-    prof_path = os.path.join(ROOT, "profiles", "force_kernel_traffic.json")
-    if os.path.exists(prof_path):
-        try:
-            traffic = json.load(open(prof_path)).get("bytes_per_launch")
-        except (OSError, ValueError):
-            traffic = None
+    traffic = force_kernel_traffic()
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": traffic,
                 "kernel": "k_force (FP32 pair arithmetic)", "ms_per_launch": f_avg,
