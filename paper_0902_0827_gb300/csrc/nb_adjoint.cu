@@ -15,6 +15,7 @@ namespace acenb {
 __global__ void k_gather_g(int slot_cap, const int *__restrict__ counts, const int *__restrict__ perm,
                            const float *__restrict__ G, float4 *__restrict__ gslot)
 {
+    pdl_entry();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= slot_cap || s >= counts[0]) return;
     const int a = perm[s];
@@ -28,6 +29,7 @@ __global__ void k_gather_g(int slot_cap, const int *__restrict__ counts, const i
 __global__ void k_tab_finalize(int T, const long long *__restrict__ acc, double *__restrict__ dsig,
                                double *__restrict__ deps)
 {
+    pdl_entry();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= T * T) return;
     const int a = k / T, b = k % T;
@@ -46,6 +48,7 @@ __global__ void k_tab_finalize(int T, const long long *__restrict__ acc, double 
 __global__ void k_type_grad(int T, const float *__restrict__ eps, const double *__restrict__ gsig_tab,
                             const double *__restrict__ geps_tab, double *__restrict__ gsig, double *__restrict__ geps)
 {
+    pdl_entry();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T) return;
     double gs = 0.0, ge = 0.0;
@@ -66,7 +69,7 @@ __global__ void k_type_grad(int T, const float *__restrict__ eps, const double *
 cudaError_t launch_type_grad(nb_ctx *ctx, const double *gsig_tab, const double *geps_tab, double *gsig, double *geps)
 {
     const int T = ctx->pp.n_types;
-    k_type_grad<<<1, 64, 0, ctx->stream>>>(T, ctx->d.eps_type, gsig_tab, geps_tab, gsig, geps);
+    launch_pdl(k_type_grad, dim3(1), dim3(64), 0, ctx->stream, T, ctx->d.eps_type, gsig_tab, geps_tab, gsig, geps);
     return cudaGetLastError();
 }
 
@@ -78,14 +81,14 @@ cudaError_t launch_backward(nb_ctx *ctx, const float *d_pos, const float *d_q, c
     const int tb = 256;
     const int S = (int)ctx->slot_cap;
     const int T = ctx->pp.n_types;
-    cudaError_t e = launch_pack(ctx, d_pos, d_q, d_type);
+    cudaError_t e = launch_pack(ctx, d_pos, d_q, d_type, false);
     if (e != cudaSuccess) return e;
-    k_gather_g<<<(S + tb - 1) / tb, tb, 0, ctx->stream>>>(S, d.counts, d.perm, d_dLdF, d.gslot);
+    launch_pdl(k_gather_g, dim3((S + tb - 1) / tb), dim3(tb), 0, ctx->stream, S, d.counts, d.perm, d_dLdF, d.gslot);
     e = cudaMemsetAsync(d.tab_grad, 0, sizeof(long long) * 2 * T * T, ctx->stream);
     if (e != cudaSuccess) return e;
     e = launch_adjoint_tile(ctx, d_dLdE, d_dLdpos, d_dLdq);
     if (e != cudaSuccess) return e;
-    if (d_dsig || d_deps) k_tab_finalize<<<(T * T + tb - 1) / tb, tb, 0, ctx->stream>>>(T, d.tab_grad, d_dsig, d_deps);
+    if (d_dsig || d_deps) launch_pdl(k_tab_finalize, dim3((T * T + tb - 1) / tb), dim3(tb), 0, ctx->stream, T, d.tab_grad, d_dsig, d_deps);
     return cudaGetLastError();
 }
 

@@ -98,6 +98,7 @@ __global__ void k_bin(int n, const float *__restrict__ pos, SysDesc *__restrict_
                       int *__restrict__ col_count, int n_cols, int n_sys, int *__restrict__ col_slot,
                       int *__restrict__ col_fill, int *__restrict__ counts, int *__restrict__ status)
 {
+    pdl_entry();
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     int col = -1;
     if (a < n) {
@@ -135,6 +136,7 @@ __global__ void k_bin(int n, const float *__restrict__ pos, SysDesc *__restrict_
 __global__ void k_scatter(int n, const int *__restrict__ atom_col, int *__restrict__ col_fill,
                           int *__restrict__ stage)
 {
+    pdl_entry();
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     const int col = a < n ? atom_col[a] : -1;
     const int p = warp_aggregated_add(col_fill, col);
@@ -177,6 +179,7 @@ __global__ void __launch_bounds__(kSortThreads) k_colsort(
     float4 *__restrict__ xyzq, int *__restrict__ tslot, int *__restrict__ perm, int *__restrict__ inv,
     float4 *__restrict__ bb, int *__restrict__ clus_sys, int2 *__restrict__ zbin)
 {
+    pdl_entry();
     __shared__ unsigned long long skey[kSortSmem];
     __shared__ float4 sp[kSortSmem];
     const int c = blockIdx.x;
@@ -340,6 +343,7 @@ __global__ void __launch_bounds__(kListWarps * 32) k_list(const SysDesc *__restr
                                               int *__restrict__ list_n, int *__restrict__ pslot,
                                               int *__restrict__ status)
 {
+    pdl_entry();
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
@@ -527,14 +531,14 @@ cudaError_t launch_build(nb_ctx *ctx, const float *d_pos)
     cudaError_t e = cudaMemsetAsync(d.col_count, 0, sizeof(int) * (ctx->n_cols + 1), st);
     if (e != cudaSuccess) return e;
     const int tb = 256;
-    k_bin<<<(N + tb - 1) / tb, tb, 0, st>>>(N, d_pos, d.sys, d.atom_sys, d.wpos, d.atom_col, d.col_count,
+    launch_pdl(k_bin, dim3((N + tb - 1) / tb), dim3(tb), 0, st, N, d_pos, d.sys, d.atom_sys, d.wpos, d.atom_col, d.col_count,
                                             ctx->n_cols, ctx->n_sys, d.col_slot, d.col_fill, d.counts, d.status);
-    k_scatter<<<(N + tb - 1) / tb, tb, 0, st>>>(N, d.atom_col, d.col_fill, d.stage);
-    k_colsort<<<ctx->n_cols, kSortThreads, 0, st>>>(d.col_count, d.col_slot, d.col_sys, d.sys, d.stage, d.wpos, d.xyzq,
+    launch_pdl(k_scatter, dim3((N + tb - 1) / tb), dim3(tb), 0, st, N, d.atom_col, d.col_fill, d.stage);
+    launch_pdl(k_colsort, dim3(ctx->n_cols), dim3(kSortThreads), 0, st, d.col_count, d.col_slot, d.col_sys, d.sys, d.stage, d.wpos, d.xyzq,
                                            d.tslot, d.perm, d.inv, d.bb, d.clus_sys, d.zbin);
     const int lw = kListWarps;
     const int lblocks = (int)std::max<int64_t>(1, (ctx->clus_cap + lw - 1) / lw);
-    k_list<<<lblocks, lw * 32, 0, st>>>(d.sys, d.counts, d.bb, d.clus_sys, d.col_slot, d.zbin, d.perm, d.part_orig,
+    launch_pdl(k_list, dim3(lblocks), dim3(lw * 32), 0, st, d.sys, d.counts, d.bb, d.clus_sys, d.col_slot, d.zbin, d.perm, d.part_orig,
                                         d.inv,
                                         ctx->K, ctx->pp.rc + ctx->pp.list_margin, ctx->list_cap, d.list, d.list_n,
                                         d.pslot, d.status);

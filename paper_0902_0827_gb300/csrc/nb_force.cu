@@ -190,14 +190,27 @@ __device__ __forceinline__ uint32_t list_entry(const ForceArgs &A, int I, int nA
 // (adjoint) 8 dL/dF vectors, with asynchronous copies issued by every thread
 // of the block.
 template <bool ADJ>
-__device__ __forceinline__ void stage_chunk(const ForceArgs &A, const ForceSmem &S, int I, int nA, int c0, int n)
+__device__ __forceinline__ void stage_chunk(const ForceArgs &A, const ForceSmem &S, int I, int nA, int c0, int n,
+                                            float3 L)
 {
     for (int p = threadIdx.x; p < n * kCluster; p += blockDim.x) {
         const int e = p >> 3, k = p & 7;
         const uint32_t ent = list_entry(A, I, nA, c0 + e);
         if (k == 0) S.ent[e] = ent;
         const long long j = (long long)(ent & kJMask) * kCluster + k;
-        cp_async16(S.pos + swz(e, k), A.xyzq + j);
+        // axes with a j-side image (code 1) are staged as fl(x_j - L): the
+        // first operation of the exact displacement (x_j - L) - x_i
+        const uint32_t code = (ent >> kShiftBit) & 0x3Fu;
+        const uint32_t jside = code & ~(code >> 1) & 0x15u;  // bit 2a set: axis a has code 1
+        if (jside) {
+            float4 v = __ldg(A.xyzq + j);
+            if (jside & 0x01u) v.x = __fsub_rn(v.x, L.x);
+            if (jside & 0x04u) v.y = __fsub_rn(v.y, L.y);
+            if (jside & 0x10u) v.z = __fsub_rn(v.z, L.z);
+            S.pos[swz(e, k)] = v;
+        } else {
+            cp_async16(S.pos + swz(e, k), A.xyzq + j);
+        }
         cp_async4(S.typ + swz(e, k), A.tslot + j);
         if (ADJ) cp_async16(S.gj + swz(e, k), A.gslot + j);
         if (k < 2) cp_async16(S.bb + 2 * e + k, A.bb + (long long)(ent & kJMask) * 2 + k);
@@ -208,7 +221,6 @@ __device__ __forceinline__ void stage_chunk(const ForceArgs &A, const ForceSmem 
 
 struct Acc {
     float fx, fy, fz, elj, ec;
-    float w[6];
 };
 
 struct AccAdj {
@@ -310,7 +322,7 @@ __device__ __forceinline__ void eval_pair_adj(const PairParams &P, const ForceSm
 
 // One candidate pair: d = x_j - x_i (exact-shift image), r2 its FP32 squared
 // length; the arithmetic is done for every candidate and masked by `in`.
-template <bool EWALD, bool VIRIAL>
+template <bool EWALD>
 __device__ __forceinline__ void eval_pair(const PairParams &P, const float2 *__restrict__ lj, int ti_row, float qi,
                                           bool in, float dx, float dy, float dz, float r2, float qj, int tj,
                                           bool is14, Acc &acc, float &fjx, float &fjy, float &fjz)
@@ -333,15 +345,6 @@ __device__ __forceinline__ void eval_pair(const PairParams &P, const float2 *__r
     fjx = fdx;  // F_j = -F_i
     fjy = fdy;
     fjz = fdz;
-    if (VIRIAL) {
-        // W_ab += d_ij,a f_ij,b with d_ij = -d and f_ij = -fs d (once per pair)
-        acc.w[0] = fmaf(fdx, dx, acc.w[0]);
-        acc.w[1] = fmaf(fdy, dy, acc.w[1]);
-        acc.w[2] = fmaf(fdz, dz, acc.w[2]);
-        acc.w[3] = fmaf(fdx, dy, acc.w[3]);
-        acc.w[4] = fmaf(fdx, dz, acc.w[4]);
-        acc.w[5] = fmaf(fdy, dz, acc.w[5]);
-    }
 }
 
 // Per-warp data of the i atom.
@@ -353,27 +356,25 @@ struct IAtom {
     float gix, giy, giz, gE_lj, gE_c;  // adjoint
 };
 
-// One ring item: staged cluster e, atom k, 1-4 flag.  The displacement is
+// One ring item: staged entry e (bits 7..15), i-side image per axis (bits
+// 4..6), atom k (bits 1..3), 1-4 flag (bit 0).  The displacement is
 // recomputed with the same operations as the membership test (same value).
 template <bool ADJ, bool EWALD, bool VIRIAL, bool DEBUG, class AccT>
 __device__ __forceinline__ void eval_item(const ForceArgs &A, const ForceSmem &S, float Lx, float Ly, float Lz,
                                           const IAtom &ia, uint32_t item, bool active, AccT &acc)
 {
-    const int e = (int)(item >> 4), k = (int)((item >> 1) & 7u);
-    const uint32_t ent = S.ent[e];
-    const int cx = (ent >> kShiftBit) & 3, cy = (ent >> (kShiftBit + 2)) & 3, cz = (ent >> (kShiftBit + 4)) & 3;
-    const float sx = cx == 1 ? Lx : 0.0f, sy = cy == 1 ? Ly : 0.0f, sz = cz == 1 ? Lz : 0.0f;
-    const float ax = cx == 2 ? ia.xim : ia.xi, ay = cy == 2 ? ia.yim : ia.yi, az = cz == 2 ? ia.zim : ia.zi;
+    const int e = (int)(item >> 7), k = (int)((item >> 1) & 7u);
+    const float ax = (item & 0x10u) ? ia.xim : ia.xi, ay = (item & 0x20u) ? ia.yim : ia.yi,
+                az = (item & 0x40u) ? ia.zim : ia.zi;
     const int idx = swz(e, k);
-    const float4 pj = S.pos[idx];
+    const float4 pj = S.pos[idx];  // j-side images already applied at staging
     const int tj = S.typ[idx];
     float dx, dy, dz;
-    const float r2 =
-        disp_r2(__fsub_rn(pj.x, sx), __fsub_rn(pj.y, sy), __fsub_rn(pj.z, sz), ax, ay, az, dx, dy, dz);
+    const float r2 = disp_r2(pj.x, pj.y, pj.z, ax, ay, az, dx, dy, dz);
     if (DEBUG && active) {
         // forward visits: every unique pair exactly once
         atomicAdd((unsigned long long *)&A.dbg_n[0], 1ull);
-        const int jorig = A.perm[(int)(ent & kJMask) * kCluster + k];
+        const int jorig = A.perm[(int)(S.ent[e] & kJMask) * kCluster + k];
         const long long q = (long long)atomicAdd((unsigned long long *)&A.dbg_n[1], 1ull);
         if (q < A.dbg_cap) {
             A.dbg_ij[2 * q] = min(ia.iorig, jorig);
@@ -385,8 +386,8 @@ __device__ __forceinline__ void eval_item(const ForceArgs &A, const ForceSmem &S
                              active ? r2 : 1.0f, pj.w, tj, S.gj[idx], (item & 1u) != 0u, A.status, acc);
     } else {
         float fjx, fjy, fjz;
-        eval_pair<EWALD, VIRIAL>(A.P, S.lj, ia.ti_row, ia.qi, active, dx, dy, dz, active ? r2 : 1.0f, pj.w, tj,
-                                 (item & 1u) != 0u, acc, fjx, fjy, fjz);
+        eval_pair<EWALD>(A.P, S.lj, ia.ti_row, ia.qi, active, dx, dy, dz, active ? r2 : 1.0f, pj.w, tj,
+                                (item & 1u) != 0u, acc, fjx, fjy, fjz);
         if (active) {
             // one range check per pair: each component below 2^26 keeps the
             // fixed-point sums inside int64
@@ -427,15 +428,16 @@ __device__ __forceinline__ ClusterHead load_head(const ForceArgs &A, int I, int 
     return h;
 }
 
-// Add the per-lane fixed-point energy/virial of a system to its global sums
-// (warp reduction, block accumulator, one atomic per value and block).
+// Add the per-lane fixed-point energies and the per-thread periodic-image
+// virial terms (scale 2^20) of a system to its global sums (warp reduction,
+// block accumulator, one atomic per value and block).
 template <bool VIRIAL>
-__device__ __forceinline__ void flush_energy(const ForceArgs &A, const ForceSmem &S, const long long *wacc, int sys,
-                                             int lane)
+__device__ __forceinline__ void flush_energy(const ForceArgs &A, const ForceSmem &S, const long long *wacc,
+                                             const float *wimg, int sys, int lane)
 {
 #pragma unroll
     for (int k = 0; k < (VIRIAL ? kTaskVals : 2); ++k) {
-        long long x = wacc[k];
+        long long x = k < 2 ? wacc[k] : __float2ll_rn(wimg[k - 2] * (float)kVirScale);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
         if (lane == 0) atomicAdd(&S.cacc[k], (unsigned long long)x);
@@ -450,19 +452,42 @@ __device__ __forceinline__ void flush_energy(const ForceArgs &A, const ForceSmem
 
 // Forward: add the block's fixed-point forces of the n staged j clusters
 // listed at ent to the global fixed-point force array and clear them.
-__device__ __forceinline__ void flush_jf(const ForceArgs &A, const ForceSmem &S, const uint32_t *ent, int n)
+// With VIRIAL, also add the periodic-image part of the virial: a pair whose
+// j atom was taken at its image x_j + s contributes s (x) f_j beyond the
+// x (x) F sum over atoms (see k_unpack_forces); s is the entry's shift
+// (code 1: -L, code 2: +L per axis) and sum f_j over the block's i atoms is
+// the slot's value.  wimg: xx, yy, zz, xy, xz, yz.
+template <bool VIRIAL>
+__device__ __forceinline__ void flush_jf(const ForceArgs &A, const ForceSmem &S, const uint32_t *ent, int n,
+                                         float Lx, float Ly, float Lz, float *wimg)
 {
     const int js = A.scap * kCluster;
     for (int p = threadIdx.x; p < n * kCluster; p += blockDim.x) {
         const int e = p >> 3, k = (p & 7) ^ (e & 7);  // p = swz(e, k)
-        const long long g = 3ll * ((long long)(ent[e] & kJMask) * kCluster + k);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const unsigned long long v = S.jf[c * js + p];
-            if (v) {
-                atomicAdd((unsigned long long *)&A.facc[g + c], v);
-                S.jf[c * js + p] = 0ull;
-            }
+        const uint32_t en = ent[e];
+        const long long g = 3ll * ((long long)(en & kJMask) * kCluster + k);
+        const unsigned long long v0 = S.jf[p], v1 = S.jf[js + p], v2 = S.jf[2 * js + p];
+        if (v0) atomicAdd((unsigned long long *)&A.facc[g], v0);
+        if (v1) atomicAdd((unsigned long long *)&A.facc[g + 1], v1);
+        if (v2) atomicAdd((unsigned long long *)&A.facc[g + 2], v2);
+        S.jf[p] = 0ull;
+        S.jf[js + p] = 0ull;
+        S.jf[2 * js + p] = 0ull;
+        const uint32_t code = (en >> kShiftBit) & 0x3Fu;
+        if (VIRIAL && code) {
+            const uint32_t cx = code & 3u, cy = (code >> 2) & 3u, cz = code >> 4;
+            const float sx = cx == 1u ? -Lx : (cx == 2u ? Lx : 0.0f);
+            const float sy = cy == 1u ? -Ly : (cy == 2u ? Ly : 0.0f);
+            const float sz = cz == 1u ? -Lz : (cz == 2u ? Lz : 0.0f);
+            const float sc = 2.3283064365386963e-10f;  // 2^-32
+            const float fx = __ll2float_rn((long long)v0) * sc, fy = __ll2float_rn((long long)v1) * sc,
+                        fz = __ll2float_rn((long long)v2) * sc;
+            wimg[0] = fmaf(sx, fx, wimg[0]);
+            wimg[1] = fmaf(sy, fy, wimg[1]);
+            wimg[2] = fmaf(sz, fz, wimg[2]);
+            wimg[3] = fmaf(sx, fy, wimg[3]);
+            wimg[4] = fmaf(sx, fz, wimg[4]);
+            wimg[5] = fmaf(sy, fz, wimg[5]);
         }
     }
 }
@@ -470,6 +495,7 @@ __device__ __forceinline__ void flush_jf(const ForceArgs &A, const ForceSmem &S,
 template <bool ADJ, bool EWALD, bool VIRIAL, bool DEBUG>
 __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
 {
+    pdl_entry();
     extern __shared__ __align__(16) unsigned char smem[];
     const int T = A.P.n_types;
     const int nwarps = blockDim.x >> 5;
@@ -493,9 +519,8 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
 
     int cur_sys = -1;
     float Lx = 0.0f, Ly = 0.0f, Lz = 0.0f;
-    long long wacc[kTaskVals];  // per lane: fixed-point energy/virial of the current system
-#pragma unroll
-    for (int k = 0; k < kTaskVals; ++k) wacc[k] = 0;
+    long long wacc[2] = {0, 0};  // per lane: fixed-point energies of the current system
+    float wimg[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};  // per thread: periodic-image virial terms
     const int n_clus = A.counts[1];
     const float rcm2 = A.P.rcm2;
 
@@ -505,9 +530,10 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
         if (sys_id != cur_sys) {
             // flush the energy/virial of the previous system through the
             // block accumulator (integer sums: order independent)
-            if (!ADJ && cur_sys >= 0) flush_energy<VIRIAL>(A, S, wacc, cur_sys, lane);
+            if (!ADJ && cur_sys >= 0) flush_energy<VIRIAL>(A, S, wacc, wimg, cur_sys, lane);
+            wacc[0] = wacc[1] = 0;
 #pragma unroll
-            for (int k = 0; k < kTaskVals; ++k) wacc[k] = 0;
+            for (int k = 0; k < 6; ++k) wimg[k] = 0.0f;
             cur_sys = sys_id;
             Lx = A.sys[sys_id].L[0];
             Ly = A.sys[sys_id].L[1];
@@ -549,11 +575,11 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
             const int nC = min(A.scap, nE - c0);
             if (c0 > 0) {
                 __syncthreads();  // the staging buffers are free
-                if (!ADJ) flush_jf(A, S, S.lst + ((ci - 1) & 1) * A.scap, A.scap);
+                if (!ADJ) flush_jf<VIRIAL>(A, S, S.lst + ((ci - 1) & 1) * A.scap, A.scap, Lx, Ly, Lz, wimg);
             }
             ForceSmem Sc = S;
             Sc.ent = S.lst + (ci & 1) * A.scap;
-            stage_chunk<ADJ>(A, Sc, I, nA, c0, nC);
+            stage_chunk<ADJ>(A, Sc, I, nA, c0, nC, make_float3(Lx, Ly, Lz));
             if (!iv) continue;
             // (1) prune staged clusters against this atom
             int ns = 0;
@@ -589,8 +615,11 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
                 const int J = (int)(ent & kJMask);
                 const int cx = (ent >> kShiftBit) & 3, cy = (ent >> (kShiftBit + 2)) & 3,
                           cz = (ent >> (kShiftBit + 4)) & 3;
-                const float sx = cx == 1 ? Lx : 0.0f, sy = cy == 1 ? Ly : 0.0f, sz = cz == 1 ? Lz : 0.0f;
+                // j-side images are already in the staged coordinates; the
+                // i side uses x_i - L on axes with code 2
                 const float ax = cx == 2 ? xim : xi, ay = cy == 2 ? yim : yi, az = cz == 2 ? zim : zi;
+                const uint32_t ishift = (cx == 2 ? 1u : 0u) | (cy == 2 ? 2u : 0u) | (cz == 2 ? 4u : 0u);
+                const uint32_t ibase = ((uint32_t)e << 7) | (ishift << 4);
                 uint32_t exm = sv ? 0u : 0xFFu, m14 = 0u;
                 if (J == I && ((ent >> kShiftBit) & 0x3Fu) == 0u)
                     exm |= ADJ ? 1u << w : (2u << w) - 1u;  // i == j; forward: j > i only
@@ -611,8 +640,7 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
                 for (int k = 0; k < kCluster; ++k) {
                     const float4 pj = S.pos[e * kCluster + (k ^ sw)];
                     float dx, dy, dz;
-                    const float r2 = disp_r2(__fsub_rn(pj.x, sx), __fsub_rn(pj.y, sy), __fsub_rn(pj.z, sz), ax, ay,
-                                             az, dx, dy, dz);
+                    const float r2 = disp_r2(pj.x, pj.y, pj.z, ax, ay, az, dx, dy, dz);
                     mask |= (r2 < A.P.rc2) ? (1u << k) : 0u;
                 }
                 mask &= ~exm;
@@ -632,7 +660,7 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
                     if (mm) {
                         const int k = __ffs(mm) - 1;
                         mm &= mm - 1u;
-                        S.ring[(pos++) & (kRing - 1)] = ((uint32_t)e << 4) | ((uint32_t)k << 1) | ((m14 >> k) & 1u);
+                        S.ring[(pos++) & (kRing - 1)] = ibase | ((uint32_t)k << 1) | ((m14 >> k) & 1u);
                     }
                 }
                 tail += total;
@@ -654,7 +682,7 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
         if (!ADJ && nE > 0) {
             const int last = (nE - 1) / A.scap;
             __syncthreads();
-            flush_jf(A, S, S.lst + (last & 1) * A.scap, nE - last * A.scap);
+            flush_jf<VIRIAL>(A, S, S.lst + (last & 1) * A.scap, nE - last * A.scap, Lx, Ly, Lz, wimg);
         }
         if (!iv) continue;
         if constexpr (ADJ) {
@@ -692,11 +720,10 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
                 atomicAdd((unsigned long long *)&A.facc[3ll * islot + 1], (unsigned long long)vy);
                 atomicAdd((unsigned long long *)&A.facc[3ll * islot + 2], (unsigned long long)vz);
             }
-            // energies and virial: per lane in fixed point (reduced when the
-            // system's sums are flushed)
-            const float v[kTaskVals] = {acc.elj, acc.ec, acc.w[0], acc.w[1], acc.w[2], acc.w[3], acc.w[4], acc.w[5]};
-#pragma unroll
-            for (int k = 0; k < (VIRIAL ? kTaskVals : 2); ++k) wacc[k] += to_fixed(v[k], A.status);
+            // energies: per lane in fixed point (reduced when the system's
+            // sums are flushed)
+            wacc[0] += to_fixed(acc.elj, A.status);
+            wacc[1] += to_fixed(acc.ec, A.status);
         }
     }
     if constexpr (ADJ) {
@@ -708,7 +735,7 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
     }
     // final flush of the last system (every block reaches it: cur_sys is
     // block-uniform)
-    if (cur_sys >= 0) flush_energy<VIRIAL>(A, S, wacc, cur_sys, lane);
+    if (cur_sys >= 0) flush_energy<VIRIAL>(A, S, wacc, wimg, cur_sys, lane);
 }
 
 // Gather charges and types into sorted order and check that the positions
@@ -716,9 +743,18 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
 __global__ void k_pack(int slot_cap, const int *__restrict__ counts, const int *__restrict__ perm,
                        float4 *__restrict__ xyzq, int *__restrict__ tslot, const float *__restrict__ pos,
                        const float *__restrict__ q, const int *__restrict__ type, const SysDesc *__restrict__ sys,
-                       const int *__restrict__ atom_sys, int T, int *__restrict__ status)
+                       const int *__restrict__ atom_sys, int T, int *__restrict__ status,
+                       long long *__restrict__ facc, long long *__restrict__ sys_acc, int n_acc)
 {
+    pdl_entry();
     int s = blockIdx.x * blockDim.x + threadIdx.x;
+    // zero the force kernel's fixed-point sums (forward calls pass them)
+    if (facc && s < slot_cap) {
+        facc[3ll * s] = 0;
+        facc[3ll * s + 1] = 0;
+        facc[3ll * s + 2] = 0;
+    }
+    if (sys_acc && s < n_acc) sys_acc[s] = 0;
     if (s >= slot_cap || s >= counts[0]) return;
     int a = perm[s];
     if (a < 0) return;
@@ -737,28 +773,113 @@ __global__ void k_pack(int slot_cap, const int *__restrict__ counts, const int *
     tslot[s] = t;
 }
 
-// Fixed-point forces (sorted order) to FP32 in the caller's order.
-__global__ void k_unpack_forces(int slot_cap, const int *__restrict__ counts, const int *__restrict__ perm,
-                                const long long *__restrict__ facc, float *__restrict__ F)
+// Add a warp's per-lane fixed-point virial terms (lanes with sys < 0 hold
+// none) to the per-system sums: one reduction and 6 atomics per distinct
+// system among the lanes, into the block's shared sums when the system is
+// the block's (blk_sys), else straight to global memory.
+__device__ __forceinline__ void flush_virial_warp(long long *w, int sys, long long *sys_acc, int blk_sys,
+                                                  unsigned long long *blk_w)
 {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= slot_cap || s >= counts[0]) return;
-    const int a = perm[s];
-    if (a < 0) return;
-    const float sc = 2.3283064365386963e-10f;  // 2^-32
+    unsigned rem = __ballot_sync(kFull, sys >= 0);
+    while (rem) {
+        const int leader = __ffs(rem) - 1;
+        const int cs = __shfl_sync(kFull, sys, leader);
+        const bool mine = sys == cs;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) F[3ll * a + c] = __ll2float_rn(facc[3ll * s + c]) * sc;
+        for (int k = 0; k < 6; ++k) {
+            long long x = mine ? w[k] : 0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+            if ((int)(threadIdx.x & 31) == leader) {
+                if (cs == blk_sys) atomicAdd(&blk_w[k], (unsigned long long)x);
+                else atomicAdd((unsigned long long *)&sys_acc[cs * kTaskVals + 2 + k], (unsigned long long)x);
+            }
+        }
+        rem &= ~__ballot_sync(kFull, mine);
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) w[k] = 0;
+}
+
+// Fixed-point forces (sorted order) to FP32 in the caller's order.  With
+// VIRIAL, also the atom part of the virial: for central pair forces
+// W_ab = sum_pairs d_a f_b (d = x_j' - x_i, f the force on j) equals
+// sum_atoms x_a F_b over the wrapped coordinates x and total forces F, plus
+// the periodic-image terms added by the force kernel.  Each atom's terms are
+// rounded to the 2^20 fixed-point grid in FP64 and summed as integers per
+// thread (grid-stride loop, slots in system order) and per warp.
+template <bool VIRIAL>
+__global__ void __launch_bounds__(256) k_unpack_forces(int slot_cap, const int *__restrict__ counts,
+                                                       const int *__restrict__ perm, const long long *__restrict__ facc,
+                                                       float *__restrict__ F, const float4 *__restrict__ xyzq,
+                                                       const int *__restrict__ clus_sys, long long *__restrict__ sys_acc)
+{
+    pdl_entry();
+    const int nslots = min(slot_cap, counts[0]);
+    long long w[6] = {0, 0, 0, 0, 0, 0};
+    int wsys = -1;
+    __shared__ unsigned long long blk_w[6];
+    __shared__ int blk_sys;
+    if (VIRIAL) {
+        if (threadIdx.x < 6) blk_w[threadIdx.x] = 0ull;
+        if (threadIdx.x == 0) blk_sys = blockIdx.x * blockDim.x < nslots ? clus_sys[blockIdx.x * blockDim.x / kCluster] : -1;
+        __syncthreads();
+    }
+    for (int s0 = blockIdx.x * blockDim.x; s0 < nslots; s0 += gridDim.x * blockDim.x) {
+        const int s = s0 + threadIdx.x;
+        const int a = s < nslots ? perm[s] : -1;
+        int sys = -1;
+        long long c[6];
+        if (a >= 0) {
+            const long long v0 = facc[3ll * s], v1 = facc[3ll * s + 1], v2 = facc[3ll * s + 2];
+            const float sc = 2.3283064365386963e-10f;  // 2^-32
+            F[3ll * a] = __ll2float_rn(v0) * sc;
+            F[3ll * a + 1] = __ll2float_rn(v1) * sc;
+            F[3ll * a + 2] = __ll2float_rn(v2) * sc;
+            if (VIRIAL) {
+                const double r = kVirScale / kFixScale;
+                const double fx = (double)v0 * r, fy = (double)v1 * r, fz = (double)v2 * r;
+                const float4 x = xyzq[s];
+                c[0] = __double2ll_rn(x.x * fx);
+                c[1] = __double2ll_rn(x.y * fy);
+                c[2] = __double2ll_rn(x.z * fz);
+                c[3] = __double2ll_rn(x.x * fy);
+                c[4] = __double2ll_rn(x.x * fz);
+                c[5] = __double2ll_rn(x.y * fz);
+                sys = clus_sys[s / kCluster];
+            }
+        }
+        if (VIRIAL) {
+            // slots come in system order: flush a lane's sums before it moves on
+            if (__any_sync(kFull, sys >= 0 && wsys >= 0 && sys != wsys)) {
+                flush_virial_warp(w, wsys, sys_acc, blk_sys, blk_w);
+                wsys = -1;
+            }
+            if (sys >= 0) {
+                wsys = sys;
+#pragma unroll
+                for (int k = 0; k < 6; ++k) w[k] += c[k];
+            }
+        }
+    }
+    if (VIRIAL) {
+        flush_virial_warp(w, wsys, sys_acc, blk_sys, blk_w);
+        __syncthreads();
+        if (threadIdx.x < 6 && blk_sys >= 0 && blk_w[threadIdx.x])
+            atomicAdd((unsigned long long *)&sys_acc[blk_sys * kTaskVals + 2 + threadIdx.x], blk_w[threadIdx.x]);
+    }
 }
 
 // Per-system energy/virial: the exact int64 sums (order independent, hence
-// deterministic) to FP64; every pair was evaluated once.
+// deterministic) to FP64: energies at scale 2^32, virial at 2^20.
 __global__ void k_finalize(int n_sys, const long long *__restrict__ sys_acc, double *__restrict__ energy,
                            double *__restrict__ virial)
 {
+    pdl_entry();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_sys * kTaskVals) return;
     const int s = i / kTaskVals, k = i % kTaskVals;
-    const double v = (double)sys_acc[i] * (1.0 / kFixScale);
+    const double v = (double)sys_acc[i] * (k < 2 ? 1.0 / kFixScale : 1.0 / kVirScale);
     if (k < 2) {
         if (energy) energy[2 * s + k] = v;
     } else if (virial) {
@@ -782,7 +903,7 @@ static void launch_force_t(nb_ctx *ctx, const ForceArgs &A)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_force<ADJ, EWALD, VIRIAL, DEBUG>, nw * 32, smem);
     const int per_sm = std::max(1, std::min(ctx->tune.blocks_per_sm, resident));
     const int grid = ctx->num_sms * per_sm;
-    k_force<ADJ, EWALD, VIRIAL, DEBUG><<<grid, nw * 32, smem, ctx->stream>>>(A);
+    launch_pdl(k_force<ADJ, EWALD, VIRIAL, DEBUG>, dim3(grid), dim3(nw * 32), smem, ctx->stream, A);
 }
 
 static ForceArgs make_args(nb_ctx *ctx)
@@ -813,26 +934,27 @@ static ForceArgs make_args(nb_ctx *ctx)
     return A;
 }
 
-cudaError_t launch_pack(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type)
+cudaError_t launch_pack(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type, bool zero_sums)
 {
     auto &d = ctx->d;
     const int tb = 256;
     const int S = (int)ctx->slot_cap;
-    k_pack<<<(S + tb - 1) / tb, tb, 0, ctx->stream>>>(S, d.counts, d.perm, d.xyzq, d.tslot, d_pos, d_q, d_type, d.sys,
-                                                       d.atom_sys, ctx->pp.n_types, d.status);
-    return cudaGetLastError();
+    return launch_pdl(k_pack, dim3((S + tb - 1) / tb), dim3(tb), 0, ctx->stream, S, d.counts, d.perm, d.xyzq,
+                      d.tslot, d_pos, d_q, d_type, d.sys, d.atom_sys, ctx->pp.n_types, d.status,
+                      zero_sums ? d.facc : nullptr, zero_sums ? d.sys_acc : nullptr, kTaskVals * ctx->n_sys);
 }
 
 cudaError_t launch_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type, float *d_F,
                           double *d_energy, double *d_virial, bool debug_pairs)
 {
     auto &d = ctx->d;
-    if (d_pos) {  // the debug pair export reuses the last packed values
-        cudaError_t e = launch_pack(ctx, d_pos, d_q, d_type);
+    if (d_pos) {  // packs and zeroes the fixed-point sums
+        cudaError_t e = launch_pack(ctx, d_pos, d_q, d_type, true);
         if (e != cudaSuccess) return e;
+    } else {  // the debug pair export reuses the last packed values
+        cudaMemsetAsync(d.sys_acc, 0, sizeof(long long) * kTaskVals * ctx->n_sys, ctx->stream);
+        cudaMemsetAsync(d.facc, 0, sizeof(long long) * 3 * ctx->slot_cap, ctx->stream);
     }
-    cudaMemsetAsync(d.sys_acc, 0, sizeof(long long) * kTaskVals * ctx->n_sys, ctx->stream);
-    cudaMemsetAsync(d.facc, 0, sizeof(long long) * 3 * ctx->slot_cap, ctx->stream);
     ForceArgs A = make_args(ctx);
     A.F = d_F;
     A.facc = d.facc;
@@ -857,11 +979,17 @@ cudaError_t launch_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, con
     {
         const int tb = 256;
         const int S = (int)ctx->slot_cap;
-        k_unpack_forces<<<(S + tb - 1) / tb, tb, 0, ctx->stream>>>(S, d.counts, d.perm, d.facc, d_F);
+        const int blocks = std::max(1, std::min((S + tb - 1) / tb, 4 * ctx->num_sms));
+        if (virial)
+            launch_pdl(k_unpack_forces<true>, dim3(blocks), dim3(tb), 0, ctx->stream, S, d.counts, d.perm, d.facc, d_F, d.xyzq, d.clus_sys,
+                                                                  d.sys_acc);
+        else
+            launch_pdl(k_unpack_forces<false>, dim3(blocks), dim3(tb), 0, ctx->stream, S, d.counts, d.perm, d.facc, d_F, d.xyzq,
+                                                                   d.clus_sys, d.sys_acc);
     }
     if (!debug_pairs && (d_energy || d_virial)) {
         const int n = ctx->n_sys * kTaskVals;
-        k_finalize<<<(n + 255) / 256, 256, 0, ctx->stream>>>(ctx->n_sys, d.sys_acc, d_energy, d_virial);
+        launch_pdl(k_finalize, dim3((n + 255) / 256), dim3(256), 0, ctx->stream, ctx->n_sys, d.sys_acc, d_energy, d_virial);
     }
     return cudaGetLastError();
 }

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
 #include <vector>
 
 #include "acenb.h"
@@ -16,7 +17,8 @@ constexpr int kMaxTypes = 64;        // type-pair table lives in shared memory
 constexpr int kMaxPartners = 16;     // exclusion + 1-4 partners per atom
 constexpr int kErfcDeg = 8;          // degree of the erfcx polynomial in t
 constexpr double kFixScale = 4294967296.0;   // 2^32: fixed-point scale
-constexpr int kTaskVals = 8;         // per task: E_lj, E_c, W[6]
+constexpr int kTaskVals = 8;         // per system: E_lj, E_c (scale 2^32), W[6] (scale 2^20)
+constexpr double kVirScale = 1048576.0;      // 2^20: fixed-point scale of the virial sums
 // Padding slots of the sorted arrays sit at this finite, far-away coordinate:
 // their squared distance to any atom (about 3e36) stays finite and is never
 // inside a cutoff, so masked pair arithmetic needs no further guards.
@@ -100,7 +102,7 @@ struct DevBuffers {
     int *inv = nullptr;              // [N] atom -> slot
     float4 *bb = nullptr;            // [NC*2] cluster bounding boxes (lo, hi interleaved)
     int *clus_sys = nullptr;         // [NC] system of each cluster
-    long long *sys_acc = nullptr;    // [n_sys*kTaskVals] per-system fixed-point energy/virial
+    long long *sys_acc = nullptr;    // [n_sys*kTaskVals] per-system fixed-point energies (2^32) and virial (2^20)
     long long *facc = nullptr;       // [S*3] fixed-point forces in sorted order (both atoms of each pair)
     uint32_t *list = nullptr;        // [NC*2*list_cap] per cluster: half list, then the other half
     int *list_n = nullptr;           // [NC*2] lengths of the two halves
@@ -164,12 +166,41 @@ __device__ __forceinline__ float wrap_coord(float x, float L)
     return x;
 }
 
+// Programmatic dependent launch.  Every kernel of the library starts with
+// pdl_entry(): griddepcontrol.wait blocks until the preceding kernel in the
+// stream has completed and its memory is visible (a no-op for a plain
+// launch), then launch_dependents lets the next kernel's blocks be scheduled
+// while this one runs, so consecutive launches do not leave the GPU idle.
+__device__ __forceinline__ void pdl_entry()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Launch with programmatic stream serialization (see pdl_entry).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // Launchers implemented in the .cu files (all asynchronous on ctx->stream).
 cudaError_t launch_build(nb_ctx *ctx, const float *d_pos);
 cudaError_t launch_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type,
                           float *d_F, double *d_energy, double *d_virial, bool debug_pairs);
 size_t force_smem_for(int T, int scap, int K);
-cudaError_t launch_pack(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type);
+cudaError_t launch_pack(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type, bool zero_sums);
 cudaError_t launch_type_grad(nb_ctx *ctx, const double *gsig_tab, const double *geps_tab, double *gsig, double *geps);
 cudaError_t launch_adjoint_tile(nb_ctx *ctx, const double *d_dLdE, float *d_dpos, float *d_dq);
 cudaError_t launch_backward(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type,
