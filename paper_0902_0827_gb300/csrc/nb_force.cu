@@ -93,7 +93,7 @@ struct ForceSmem {
     uint16_t *surv;
     uint32_t *ring;
     unsigned long long *cacc;
-    unsigned long long *jf;    // forward: fixed-point forces of the staged j atoms [3][scap * 8]
+    int *jf;                   // forward: forces of the staged j atoms, [hi, lo][3][scap * 8] (see add_jf)
     float4 *gj;                // adjoint: staged dL/dF of the j atoms
     float4 *ljd;               // adjoint: derivative factors of the type pairs
     unsigned long long *tacc;  // adjoint: block table of fixed-point parameter gradients
@@ -131,7 +131,7 @@ __device__ __forceinline__ ForceSmem carve(unsigned char *smem, int T, int scap,
     S.tacc = nullptr;
     S.jf = nullptr;
     if (!adj) {
-        S.jf = reinterpret_cast<unsigned long long *>(smem + off);
+        S.jf = reinterpret_cast<int *>(smem + off);
         off += (size_t)scap * kCluster * 3 * 8;
     }
     if (adj) {
@@ -347,6 +347,28 @@ __device__ __forceinline__ void eval_pair(const PairParams &P, const float2 *__r
     fjz = fdz;
 }
 
+// Force on a staged j atom, exactly at the 2^32 fixed-point grid of the
+// global sums, with two 32-bit shared-memory integer atomics: f 2^32 =
+// hi 2^16 + lo with hi = rint(f 2^16) and lo = rint((f 2^16 - hi) 2^16)
+// (both products and the difference are exact in FP32).  A chunk adds at
+// most 8 contributions (one per i atom of the block's cluster) to a slot, so
+// for |f| < 2048 neither 32-bit sum can overflow; larger (or non-finite)
+// forces go straight to the global 64-bit sums.  The hi array is at slot,
+// the lo array 3 * js further.
+__device__ __forceinline__ void add_jf(const ForceArgs &A, const ForceSmem &S, int e, int k, int slot, int comp,
+                                       float f)
+{
+    if (fabsf(f) < 2048.0f) {
+        const float t = f * 65536.0f;
+        const float hf = rintf(t);
+        atomicAdd(S.jf + slot, (int)hf);
+        atomicAdd(S.jf + slot + 3 * A.scap * kCluster, __float2int_rn((t - hf) * 65536.0f));
+    } else {
+        long long *g = A.facc + 3ll * ((long long)(S.ent[e] & kJMask) * kCluster + k) + comp;
+        atomicAdd((unsigned long long *)g, (unsigned long long)to_fixed(f, A.status));
+    }
+}
+
 // Per-warp data of the i atom.
 struct IAtom {
     float xi, yi, zi, xim, yim, zim;
@@ -389,14 +411,10 @@ __device__ __forceinline__ void eval_item(const ForceArgs &A, const ForceSmem &S
         eval_pair<EWALD>(A.P, S.lj, ia.ti_row, ia.qi, active, dx, dy, dz, active ? r2 : 1.0f, pj.w, tj,
                                 (item & 1u) != 0u, acc, fjx, fjy, fjz);
         if (active) {
-            // one range check per pair: each component below 2^26 keeps the
-            // fixed-point sums inside int64
-            if (!(fmaxf(fabsf(fjx), fmaxf(fabsf(fjy), fabsf(fjz))) < 67108864.0f)) atomicOr(A.status, ST_OVERFLOW);
             const int js = A.scap * kCluster;
-            unsigned long long *slot = S.jf + idx;
-            atomicAdd(slot, (unsigned long long)__float2ll_rn(fjx * 4294967296.0f));
-            atomicAdd(slot + js, (unsigned long long)__float2ll_rn(fjy * 4294967296.0f));
-            atomicAdd(slot + 2 * js, (unsigned long long)__float2ll_rn(fjz * 4294967296.0f));
+            add_jf(A, S, e, k, idx, 0, fjx);
+            add_jf(A, S, e, k, idx + js, 1, fjy);
+            add_jf(A, S, e, k, idx + 2 * js, 2, fjz);
         }
     }
 }
@@ -466,13 +484,21 @@ __device__ __forceinline__ void flush_jf(const ForceArgs &A, const ForceSmem &S,
         const int e = p >> 3, k = (p & 7) ^ (e & 7);  // p = swz(e, k)
         const uint32_t en = ent[e];
         const long long g = 3ll * ((long long)(en & kJMask) * kCluster + k);
-        const unsigned long long v0 = S.jf[p], v1 = S.jf[js + p], v2 = S.jf[2 * js + p];
+        const int *lo = S.jf + 3 * js;
+        const unsigned long long v0 = ((unsigned long long)(long long)S.jf[p] << 16) + (unsigned long long)(long long)lo[p];
+        const unsigned long long v1 =
+            ((unsigned long long)(long long)S.jf[js + p] << 16) + (unsigned long long)(long long)lo[js + p];
+        const unsigned long long v2 =
+            ((unsigned long long)(long long)S.jf[2 * js + p] << 16) + (unsigned long long)(long long)lo[2 * js + p];
         if (v0) atomicAdd((unsigned long long *)&A.facc[g], v0);
         if (v1) atomicAdd((unsigned long long *)&A.facc[g + 1], v1);
         if (v2) atomicAdd((unsigned long long *)&A.facc[g + 2], v2);
-        S.jf[p] = 0ull;
-        S.jf[js + p] = 0ull;
-        S.jf[2 * js + p] = 0ull;
+        S.jf[p] = 0;
+        S.jf[js + p] = 0;
+        S.jf[2 * js + p] = 0;
+        S.jf[3 * js + p] = 0;
+        S.jf[4 * js + p] = 0;
+        S.jf[5 * js + p] = 0;
         const uint32_t code = (en >> kShiftBit) & 0x3Fu;
         if (VIRIAL && code) {
             const uint32_t cx = code & 3u, cy = (code >> 2) & 3u, cz = code >> 4;
@@ -513,7 +539,7 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
     }
     if (threadIdx.x < kTaskVals) S.cacc[threadIdx.x] = 0ull;
     if (!ADJ)
-        for (int k = threadIdx.x; k < 3 * A.scap * kCluster; k += blockDim.x) S.jf[k] = 0ull;
+        for (int k = threadIdx.x; k < 6 * A.scap * kCluster; k += blockDim.x) S.jf[k] = 0;
     __syncthreads();
     using AccT = typename std::conditional<ADJ, AccAdj, Acc>::type;
 
