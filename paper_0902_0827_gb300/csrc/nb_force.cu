@@ -94,6 +94,7 @@ struct ForceSmem {
     uint32_t *ring;
     unsigned long long *cacc;
     int *jf;                   // forward: forces of the staged j atoms, [hi, lo][3][scap * 8] (see add_jf)
+    float *wimg;               // forward: per-thread periodic-image virial terms [6][blockDim]
     float4 *gj;                // adjoint: staged dL/dF of the j atoms
     float4 *ljd;               // adjoint: derivative factors of the type pairs
     unsigned long long *tacc;  // adjoint: block table of fixed-point parameter gradients
@@ -109,7 +110,7 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t
 __host__ __device__ inline size_t force_smem_bytes(int T, int scap, int nwarps, bool adj)
 {
     size_t b = adj ? (size_t)scap * kCluster * 16 + (size_t)T * T * 16 + (size_t)T * T * 16
-                   : (size_t)scap * kCluster * 3 * 8;
+                   : (size_t)scap * kCluster * 3 * 8 + (size_t)6 * nwarps * 32 * 4;
     b += (size_t)2 * scap * 4;
     b += align16((size_t)T * T * 8);
     b += (size_t)scap * kCluster * 16;
@@ -130,9 +131,12 @@ __device__ __forceinline__ ForceSmem carve(unsigned char *smem, int T, int scap,
     S.gj = S.ljd = nullptr;
     S.tacc = nullptr;
     S.jf = nullptr;
+    S.wimg = nullptr;
     if (!adj) {
         S.jf = reinterpret_cast<int *>(smem + off);
         off += (size_t)scap * kCluster * 3 * 8;
+        S.wimg = reinterpret_cast<float *>(smem + off);
+        off += (size_t)6 * nwarps * 32 * 4;
     }
     if (adj) {
         S.gj = reinterpret_cast<float4 *>(smem + off);
@@ -213,7 +217,21 @@ __device__ __forceinline__ void stage_chunk(const ForceArgs &A, const ForceSmem 
         }
         cp_async4(S.typ + swz(e, k), A.tslot + j);
         if (ADJ) cp_async16(S.gj + swz(e, k), A.gslot + j);
-        if (k < 2) cp_async16(S.bb + 2 * e + k, A.bb + (long long)(ent & kJMask) * 2 + k);
+        if (k < 2) {
+            // the box is staged at J's image (shifted by -L for code 1, +L
+            // for code 2 on each axis): only a filter, rounding is harmless
+            const float4 *src = A.bb + (long long)(ent & kJMask) * 2 + k;
+            if (code) {
+                float4 v = __ldg(src);
+                const uint32_t cx = code & 3u, cy = (code >> 2) & 3u, cz = code >> 4;
+                v.x += cx == 1u ? -L.x : (cx == 2u ? L.x : 0.0f);
+                v.y += cy == 1u ? -L.y : (cy == 2u ? L.y : 0.0f);
+                v.z += cz == 1u ? -L.z : (cz == 2u ? L.z : 0.0f);
+                S.bb[2 * e + k] = v;
+            } else {
+                cp_async16(S.bb + 2 * e + k, src);
+            }
+        }
     }
     cp_async_wait_all();
     __syncthreads();
@@ -450,12 +468,17 @@ __device__ __forceinline__ ClusterHead load_head(const ForceArgs &A, int I, int 
 // virial terms (scale 2^20) of a system to its global sums (warp reduction,
 // block accumulator, one atomic per value and block).
 template <bool VIRIAL>
-__device__ __forceinline__ void flush_energy(const ForceArgs &A, const ForceSmem &S, const long long *wacc,
-                                             const float *wimg, int sys, int lane)
+__device__ __forceinline__ void flush_energy(const ForceArgs &A, const ForceSmem &S, const long long *wacc, int sys,
+                                             int lane)
 {
 #pragma unroll
     for (int k = 0; k < (VIRIAL ? kTaskVals : 2); ++k) {
-        long long x = k < 2 ? wacc[k] : __float2ll_rn(wimg[k - 2] * (float)kVirScale);
+        long long x = wacc[k & 1];
+        if (k >= 2) {
+            float &wk = S.wimg[(k - 2) * blockDim.x + threadIdx.x];
+            x = __float2ll_rn(wk * (float)kVirScale);
+            wk = 0.0f;
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
         if (lane == 0) atomicAdd(&S.cacc[k], (unsigned long long)x);
@@ -477,8 +500,10 @@ __device__ __forceinline__ void flush_energy(const ForceArgs &A, const ForceSmem
 // the slot's value.  wimg: xx, yy, zz, xy, xz, yz.
 template <bool VIRIAL>
 __device__ __forceinline__ void flush_jf(const ForceArgs &A, const ForceSmem &S, const uint32_t *ent, int n,
-                                         float Lx, float Ly, float Lz, float *wimg)
+                                         float Lx, float Ly, float Lz)
 {
+    float *wimg = S.wimg + threadIdx.x;  // component c at wimg[c * blockDim.x]
+    const int wst = blockDim.x;
     const int js = A.scap * kCluster;
     for (int p = threadIdx.x; p < n * kCluster; p += blockDim.x) {
         const int e = p >> 3, k = (p & 7) ^ (e & 7);  // p = swz(e, k)
@@ -509,11 +534,11 @@ __device__ __forceinline__ void flush_jf(const ForceArgs &A, const ForceSmem &S,
             const float fx = __ll2float_rn((long long)v0) * sc, fy = __ll2float_rn((long long)v1) * sc,
                         fz = __ll2float_rn((long long)v2) * sc;
             wimg[0] = fmaf(sx, fx, wimg[0]);
-            wimg[1] = fmaf(sy, fy, wimg[1]);
-            wimg[2] = fmaf(sz, fz, wimg[2]);
-            wimg[3] = fmaf(sx, fy, wimg[3]);
-            wimg[4] = fmaf(sx, fz, wimg[4]);
-            wimg[5] = fmaf(sy, fz, wimg[5]);
+            wimg[wst] = fmaf(sy, fy, wimg[wst]);
+            wimg[2 * wst] = fmaf(sz, fz, wimg[2 * wst]);
+            wimg[3 * wst] = fmaf(sx, fy, wimg[3 * wst]);
+            wimg[4 * wst] = fmaf(sx, fz, wimg[4 * wst]);
+            wimg[5 * wst] = fmaf(sy, fz, wimg[5 * wst]);
         }
     }
 }
@@ -538,15 +563,16 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
         }
     }
     if (threadIdx.x < kTaskVals) S.cacc[threadIdx.x] = 0ull;
-    if (!ADJ)
+    if (!ADJ) {
         for (int k = threadIdx.x; k < 6 * A.scap * kCluster; k += blockDim.x) S.jf[k] = 0;
+        for (int k = threadIdx.x; k < 6 * (int)blockDim.x; k += blockDim.x) S.wimg[k] = 0.0f;
+    }
     __syncthreads();
     using AccT = typename std::conditional<ADJ, AccAdj, Acc>::type;
 
     int cur_sys = -1;
     float Lx = 0.0f, Ly = 0.0f, Lz = 0.0f;
     long long wacc[2] = {0, 0};  // per lane: fixed-point energies of the current system
-    float wimg[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};  // per thread: periodic-image virial terms
     const int n_clus = A.counts[1];
     const float rcm2 = A.P.rcm2;
 
@@ -556,10 +582,8 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
         if (sys_id != cur_sys) {
             // flush the energy/virial of the previous system through the
             // block accumulator (integer sums: order independent)
-            if (!ADJ && cur_sys >= 0) flush_energy<VIRIAL>(A, S, wacc, wimg, cur_sys, lane);
+            if (!ADJ && cur_sys >= 0) flush_energy<VIRIAL>(A, S, wacc, cur_sys, lane);
             wacc[0] = wacc[1] = 0;
-#pragma unroll
-            for (int k = 0; k < 6; ++k) wimg[k] = 0.0f;
             cur_sys = sys_id;
             Lx = A.sys[sys_id].L[0];
             Ly = A.sys[sys_id].L[1];
@@ -601,7 +625,7 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
             const int nC = min(A.scap, nE - c0);
             if (c0 > 0) {
                 __syncthreads();  // the staging buffers are free
-                if (!ADJ) flush_jf<VIRIAL>(A, S, S.lst + ((ci - 1) & 1) * A.scap, A.scap, Lx, Ly, Lz, wimg);
+                if (!ADJ) flush_jf<VIRIAL>(A, S, S.lst + ((ci - 1) & 1) * A.scap, A.scap, Lx, Ly, Lz);
             }
             ForceSmem Sc = S;
             Sc.ent = S.lst + (ci & 1) * A.scap;
@@ -613,16 +637,10 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
                 const int e = e0 + lane;
                 bool keep = false;
                 if (e < nC) {
-                    const uint32_t ent = Sc.ent[e];
-                    const int cx = (ent >> kShiftBit) & 3, cy = (ent >> (kShiftBit + 2)) & 3,
-                              cz = (ent >> (kShiftBit + 4)) & 3;
-                    const float ox = cx == 1 ? -Lx : (cx == 2 ? Lx : 0.0f);
-                    const float oy = cy == 1 ? -Ly : (cy == 2 ? Ly : 0.0f);
-                    const float oz = cz == 1 ? -Lz : (cz == 2 ? Lz : 0.0f);
-                    const float4 lo = S.bb[2 * e], hi = S.bb[2 * e + 1];
-                    const float gx = fmaxf(fmaxf((lo.x + ox) - xi, xi - (hi.x + ox)), 0.0f);
-                    const float gy = fmaxf(fmaxf((lo.y + oy) - yi, yi - (hi.y + oy)), 0.0f);
-                    const float gz = fmaxf(fmaxf((lo.z + oz) - zi, zi - (hi.z + oz)), 0.0f);
+                    const float4 lo = S.bb[2 * e], hi = S.bb[2 * e + 1];  // at J's image
+                    const float gx = fmaxf(fmaxf(lo.x - xi, xi - hi.x), 0.0f);
+                    const float gy = fmaxf(fmaxf(lo.y - yi, yi - hi.y), 0.0f);
+                    const float gz = fmaxf(fmaxf(lo.z - zi, zi - hi.z), 0.0f);
                     keep = gx * gx + gy * gy + gz * gz < rcm2;
                 }
                 const unsigned b = __ballot_sync(kFull, keep);
@@ -708,7 +726,7 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
         if (!ADJ && nE > 0) {
             const int last = (nE - 1) / A.scap;
             __syncthreads();
-            flush_jf<VIRIAL>(A, S, S.lst + (last & 1) * A.scap, nE - last * A.scap, Lx, Ly, Lz, wimg);
+            flush_jf<VIRIAL>(A, S, S.lst + (last & 1) * A.scap, nE - last * A.scap, Lx, Ly, Lz);
         }
         if (!iv) continue;
         if constexpr (ADJ) {
@@ -761,7 +779,7 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
     }
     // final flush of the last system (every block reaches it: cur_sys is
     // block-uniform)
-    if (cur_sys >= 0) flush_energy<VIRIAL>(A, S, wacc, wimg, cur_sys, lane);
+    if (cur_sys >= 0) flush_energy<VIRIAL>(A, S, wacc, cur_sys, lane);
 }
 
 // Gather charges and types into sorted order and check that the positions
