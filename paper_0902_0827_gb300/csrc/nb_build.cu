@@ -301,17 +301,6 @@ __device__ __forceinline__ bool keep_half(int I, int J, uint32_t code)
     return ((I ^ J) & 1) ? (I < J) : (I > J);
 }
 
-// A4: cluster-pair lists, one warp per cluster I.  The columns within reach
-// of I's bounding box (with periodic images) go to the lanes.  Clusters of a
-// column are z-sorted, so the ones whose z-range (under the z images -L, 0,
-// +L, concatenated as virtual indices -nj..2nj-1) comes within the cutoff of
-// I form one window per column; the windows of all lanes are flattened and
-// every candidate (J, image) is tested by bounding-box gap < rc + margin.
-// Kept entries go to the half list (Newton's third law, used by the forward
-// kernel) or to the other half (the adjoint visits both), each compacted in
-// (column round, candidate round, lane) order, so the lists are
-// deterministic.  Also writes the partner slots of I's atoms and flags the
-// entries whose cluster holds a topology partner of I.
 // Candidate v of a column window (virtual index: image -L below 0, +L from
 // nj): J when its bounding box comes within rc + margin of I's, else -1;
 // code receives the entry's shift code.
@@ -330,10 +319,27 @@ __device__ __forceinline__ int window_candidate(const float4 *__restrict__ bb, f
     return gx * gx + gy * gy + gz * gz < rcm2 ? J : -1;
 }
 
+// Bit of a cluster index in the 64-bit partner-cluster filter (multiplicative
+// hash).
+__device__ __forceinline__ unsigned bloom_bit(int c) { return ((unsigned)c * 0x9E3779B1u) >> 26; }
+
 constexpr int kListWarps = 8;   // warps (clusters in flight) per block of the list kernel
 constexpr int kListGroup = 64;  // candidate columns compacted per pass
+constexpr int kOwnCap = 512;    // flattened candidates whose owner lane is tabulated
 constexpr int kPartnerRounds = (kCluster * kMaxPartners + 31) / 32;
 
+// A4: cluster-pair lists, one warp per cluster I.  The columns within reach
+// of I's bounding box (with periodic images) go to the lanes.  Clusters of a
+// column are z-sorted, so the ones whose z-range (under the z images -L, 0,
+// +L, concatenated as virtual indices -nj..2nj-1) comes within the cutoff of
+// I form one window per column; the windows of all lanes are flattened and
+// every candidate (J, image) is tested by bounding-box gap < rc + margin.
+// Kept entries go to the half list (Newton's third law, used by the forward
+// kernel) or to the other half (the adjoint visits both), each compacted in
+// (column round, candidate round, lane) order, so the lists are
+// deterministic.  Also writes the partner slots of I's atoms and flags the
+// entries whose cluster may hold a topology partner of I (a Bloom filter of
+// the partners' clusters: never a missed partner, rarely a spurious flag).
 __global__ void __launch_bounds__(kListWarps * 32) k_list(const SysDesc *__restrict__ sys, const int *__restrict__ counts,
                                               const float4 *__restrict__ bb, const int *__restrict__ clus_sys,
                                               const int *__restrict__ col_slot, const int2 *__restrict__ zbin,
@@ -352,14 +358,16 @@ __global__ void __launch_bounds__(kListWarps * 32) k_list(const SysDesc *__restr
     const int n_clus = counts[1];
     const float rcm2 = rcm * rcm;
     __shared__ int s_col[kListWarps][kListGroup];  // compacted candidate columns per warp
-    __shared__ int s_pcl[kListWarps][32];          // distinct partner clusters per warp
+    __shared__ unsigned char s_own[kListWarps][kOwnCap];  // owner lane of each flattened candidate
     const int wib = threadIdx.x >> 5;
     for (int I = gw; I < n_clus; I += nw) {
         const SysDesc &S = sys[clus_sys[I]];
         const float4 lo = bb[2 * I], hi = bb[2 * I + 1];
-        // partner slots of I's atoms; distinct partner clusters in lanes 0..npc-1
-        int pcl = -1, npc = 0;
-        bool flag_all = false;
+        // partner slots of I's atoms, and a 64-bit Bloom filter of the
+        // clusters that hold them: an entry is flagged when its cluster's
+        // bit is set (false positives only cost the force kernel a partner
+        // check, a real partner is never missed)
+        unsigned long long bloom = 0ull;
         const int np = kCluster * K;
         // the loads of all rounds first (three dependent levels, not three per round)
         int pv[kPartnerRounds];
@@ -380,26 +388,10 @@ __global__ void __launch_bounds__(kListWarps * 32) k_list(const SysDesc *__restr
             if (t < np) pslot[(long long)I * np + t] = pv[r];
         }
 #pragma unroll
-        for (int r = 0; r < kPartnerRounds; ++r) {
-            if (r * 32 >= np) break;
-            const int v = pv[r];
-            const int c = v >= 0 ? (v >> 1) / kCluster : -1;
-            const unsigned peers = __match_any_sync(FULL, c);
-            bool leader = c >= 0 && (__ffs(peers) - 1) == lane;
-            for (int m = 0; m < npc; ++m)
-                if (__shfl_sync(FULL, pcl, m) == c) leader = false;
-            const unsigned bal = __ballot_sync(FULL, leader);
-            if (npc + __popc(bal) > 32) flag_all = true;
-            int q = npc;
-            for (unsigned b2 = bal; b2; b2 &= b2 - 1u, ++q) {
-                const int cc = __shfl_sync(FULL, c, __ffs(b2) - 1);
-                if (lane == q) pcl = cc;
-            }
-            npc = min(32, npc + __popc(bal));
-        }
-        __syncwarp();
-        if (lane < npc) s_pcl[wib][lane] = pcl;
-        __syncwarp();
+        for (int r = 0; r < kPartnerRounds; ++r)
+            if (pv[r] >= 0) bloom |= 1ull << bloom_bit((pv[r] >> 1) / kCluster);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) bloom |= __shfl_xor_sync(FULL, bloom, o);
         const int cxa = max(-S.nx, (int)floorf((lo.x - rcm) * S.inv_w[0]));
         const int cxb = min(2 * S.nx - 1, (int)floorf((hi.x + rcm) * S.inv_w[0]));
         const int cya = max(-S.ny, (int)floorf((lo.y - rcm) * S.inv_w[1]));
@@ -468,6 +460,9 @@ __global__ void __launch_bounds__(kListWarps * 32) k_list(const SysDesc *__restr
                     if (lane >= o) incl += y;
                 }
                 const int off = incl - cnt, total = __shfl_sync(FULL, incl, 31);
+                // owner lane of each flattened candidate, for the first kOwnCap
+                for (int t = off; t < min(off + cnt, kOwnCap); ++t) s_own[wib][t] = (unsigned char)lane;
+                __syncwarp();
                 // two candidate rounds at a time: both rounds' box loads are in
                 // flight together; entries are appended in round order
                 for (int p0 = 0; p0 < total; p0 += 64) {
@@ -478,10 +473,14 @@ __global__ void __launch_bounds__(kListWarps * 32) k_list(const SysDesc *__restr
                         const int p = p0 + 32 * h + lane;
                         // owner lane: the last lane whose window starts at or before p
                         int src = 0;
+                        if (p0 + 32 * h + 31 < kOwnCap) {
+                            src = p < total ? s_own[wib][p] : 0;
+                        } else {
 #pragma unroll
-                        for (int step = 16; step >= 1; step >>= 1) {
-                            const int o2 = __shfl_sync(FULL, off, src + step);
-                            if (o2 <= p) src += step;
+                            for (int step = 16; step >= 1; step >>= 1) {
+                                const int o2 = __shfl_sync(FULL, off, src + step);
+                                if (o2 <= p) src += step;
+                            }
                         }
                         const int s_off = __shfl_sync(FULL, off, src), s_va = __shfl_sync(FULL, va, src);
                         const int s_jb = __shfl_sync(FULL, jb, src), s_nj = __shfl_sync(FULL, nj, src);
@@ -495,8 +494,7 @@ __global__ void __launch_bounds__(kListWarps * 32) k_list(const SysDesc *__restr
                     }
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
-                        bool fl = flag_all;
-                        for (int m = 0; m < npc; ++m) fl |= s_pcl[wib][m] == J[h];
+                        const bool fl = J[h] >= 0 && ((bloom >> bloom_bit(J[h])) & 1ull);
                         const uint32_t ent = (uint32_t)J[h] | (code[h] << kShiftBit) | (fl ? kExclFlag : 0u);
                         const bool hitA = J[h] >= 0 && keep_half(I, J[h], code[h]), hitB = J[h] >= 0 && !hitA;
                         const unsigned bA = __ballot_sync(FULL, hitA), bB = __ballot_sync(FULL, hitB);
@@ -512,6 +510,7 @@ __global__ void __launch_bounds__(kListWarps * 32) k_list(const SysDesc *__restr
                         nB += __popc(bB);
                     }
                 }
+                __syncwarp();  // the owner table is rewritten by the next round
             }
             __syncwarp();
         }
