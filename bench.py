@@ -37,11 +37,11 @@ if ROOT not in sys.path:
 
 METRIC = "pair interactions/s and ms per force eval at 23.5k atoms; % FP32 roofline"
 UNIT = "pairs/s"
-# kernels of this library per step: binning (bin, scan, scatter, column sort);
-# forward (pack, force, force unpack, energy/virial finalize); adjoint (pack,
-# dL/dF gather, adjoint tile kernel, type-pair gradient finalize)
+# kernels of this library per step: binning and lists (bin + scan, scatter,
+# column sort, pair lists); forward (pack, force, unpack + energy/virial);
+# adjoint (pack, dL/dF gather, adjoint tile kernel, type-pair gradients)
 BUILD_LAUNCHES = 4
-FORCE_LAUNCHES = 4
+FORCE_LAUNCHES = 3
 ADJOINT_LAUNCHES = 4
 FLOP_PER_PAIR = 73  # LJ + switch + Ewald real space, FMA = 2, MUFU = 1
 WORKLOAD = ("solvated-chain system, 23,500 atoms (2,500-atom chain + 7,000 TIP3P-shaped waters), "
@@ -395,6 +395,20 @@ def main():
     peak_tflops = n_sms * 128 * 2 * sm_max * 1e6 / 1e12
     achieved = FLOP_PER_PAIR * npairs / (f_avg * 1e-3) / 1e12
     traffic = force_kernel_traffic()
+    # force evaluation alone, the pair lists of the last rebuild reused
+    # (positions unchanged), same graph and L2 protocol
+    def fstep():
+        ctx.forces(pos, q, typ, F=F, energy=E, virial=W)
+
+    ctx.build(pos)
+    for _ in range(3):
+        fstep()
+    gf = graph_of(fstep, dev)
+    fo_ms = max_over_ranks(time_steps(gf.replay, args.steps, flush), world)
+    ctx.status()
+    force_only = {"ms_per_eval": fo_ms, "pairs_per_s": world * npairs / (fo_ms * 1e-3),
+                  "step": "pack + force kernel + unpack, lists of the last rebuild"}
+
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": traffic,
                 "kernel": "k_force (FP32 pair arithmetic)", "ms_per_launch": f_avg,
@@ -409,6 +423,7 @@ def main():
                    "graph": "one CUDA graph per step", "parallelism": f"replicas x{world}",
                    "tuning": ctx.tuning()},
         "ms_per_force_eval": ms,
+        "force_only": force_only,
         "roofline": roofline,
         "clocks": clk,
         "gpu_launches": (BUILD_LAUNCHES + FORCE_LAUNCHES) * args.steps,

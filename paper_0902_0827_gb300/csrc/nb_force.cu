@@ -853,10 +853,11 @@ __device__ __forceinline__ void flush_virial_warp(long long *w, int sys, long lo
 // rounded to the 2^20 fixed-point grid in FP64 and summed as integers per
 // thread (grid-stride loop, slots in system order) and per warp.
 template <bool VIRIAL>
-__global__ void __launch_bounds__(256) k_unpack_forces(int slot_cap, const int *__restrict__ counts,
+__global__ void __launch_bounds__(256) k_unpack_forces(int slot_cap, int *__restrict__ counts,
                                                        const int *__restrict__ perm, const long long *__restrict__ facc,
                                                        float *__restrict__ F, const float4 *__restrict__ xyzq,
-                                                       const int *__restrict__ clus_sys, long long *__restrict__ sys_acc)
+                                                       const int *__restrict__ clus_sys, long long *__restrict__ sys_acc,
+                                                       int n_sys, double *__restrict__ energy, double *__restrict__ virial)
 {
     pdl_entry();
     const int nslots = min(slot_cap, counts[0]);
@@ -912,23 +913,28 @@ __global__ void __launch_bounds__(256) k_unpack_forces(int slot_cap, const int *
         if (threadIdx.x < 6 && blk_sys >= 0 && blk_w[threadIdx.x])
             atomicAdd((unsigned long long *)&sys_acc[blk_sys * kTaskVals + 2 + threadIdx.x], blk_w[threadIdx.x]);
     }
-}
-
-// Per-system energy/virial: the exact int64 sums (order independent, hence
-// deterministic) to FP64: energies at scale 2^32, virial at 2^20.
-__global__ void k_finalize(int n_sys, const long long *__restrict__ sys_acc, double *__restrict__ energy,
-                           double *__restrict__ virial)
-{
-    pdl_entry();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_sys * kTaskVals) return;
-    const int s = i / kTaskVals, k = i % kTaskVals;
-    const double v = (double)sys_acc[i] * (k < 2 ? 1.0 / kFixScale : 1.0 / kVirScale);
-    if (k < 2) {
-        if (energy) energy[2 * s + k] = v;
-    } else if (virial) {
-        virial[6 * s + k - 2] = v;
+    if (!energy && !virial) return;
+    // the last block to finish converts the per-system sums (counts[2] is the
+    // completion ticket: zero on entry, reset here)
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&counts[2], 1) == (int)gridDim.x - 1;
     }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int i = threadIdx.x; i < n_sys * kTaskVals; i += blockDim.x) {
+        const int sy = i / kTaskVals, k = i % kTaskVals;
+        const double v = (double)__ldcg(&sys_acc[i]) * (k < 2 ? 1.0 / kFixScale : 1.0 / kVirScale);
+        if (k < 2) {
+            if (energy) energy[2 * sy + k] = v;
+        } else if (virial) {
+            virial[6 * sy + k - 2] = v;
+        }
+    }
+    if (threadIdx.x == 0) counts[2] = 0;
 }
 
 template <bool ADJ, bool EWALD, bool VIRIAL, bool DEBUG>
@@ -1024,16 +1030,14 @@ cudaError_t launch_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, con
         const int tb = 256;
         const int S = (int)ctx->slot_cap;
         const int blocks = std::max(1, std::min((S + tb - 1) / tb, 4 * ctx->num_sms));
+        double *en = debug_pairs ? nullptr : d_energy;
+        double *vi = debug_pairs ? nullptr : d_virial;
         if (virial)
-            launch_pdl(k_unpack_forces<true>, dim3(blocks), dim3(tb), 0, ctx->stream, S, d.counts, d.perm, d.facc, d_F, d.xyzq, d.clus_sys,
-                                                                  d.sys_acc);
+            launch_pdl(k_unpack_forces<true>, dim3(blocks), dim3(tb), 0, ctx->stream, S, d.counts, d.perm, d.facc, d_F,
+                       d.xyzq, d.clus_sys, d.sys_acc, ctx->n_sys, en, vi);
         else
-            launch_pdl(k_unpack_forces<false>, dim3(blocks), dim3(tb), 0, ctx->stream, S, d.counts, d.perm, d.facc, d_F, d.xyzq,
-                                                                   d.clus_sys, d.sys_acc);
-    }
-    if (!debug_pairs && (d_energy || d_virial)) {
-        const int n = ctx->n_sys * kTaskVals;
-        launch_pdl(k_finalize, dim3((n + 255) / 256), dim3(256), 0, ctx->stream, ctx->n_sys, d.sys_acc, d_energy, d_virial);
+            launch_pdl(k_unpack_forces<false>, dim3(blocks), dim3(tb), 0, ctx->stream, S, d.counts, d.perm, d.facc,
+                       d_F, d.xyzq, d.clus_sys, d.sys_acc, ctx->n_sys, en, vi);
     }
     return cudaGetLastError();
 }
