@@ -39,10 +39,10 @@ METRIC = "pair interactions/s and ms per force eval at 23.5k atoms; % FP32 roofl
 UNIT = "pairs/s"
 # kernels of this library per step: binning and lists (bin + scan, scatter,
 # column sort, pair lists); forward (pack, force, unpack + energy/virial);
-# adjoint (pack, dL/dF gather, adjoint tile kernel, type-pair gradients)
+# adjoint (pack, dL/dF gather, adjoint kernel, unpack, type-pair gradients)
 BUILD_LAUNCHES = 4
 FORCE_LAUNCHES = 3
-ADJOINT_LAUNCHES = 4
+ADJOINT_LAUNCHES = 5
 FLOP_PER_PAIR = 73  # LJ + switch + Ewald real space, FMA = 2, MUFU = 1
 WORKLOAD = ("solvated-chain system, 23,500 atoms (2,500-atom chain + 7,000 TIP3P-shaped waters), "
             "62.2 A cubic box, rc 9 A, switch 7.5 A, Ewald alpha 0.32, 1-2/1-3 excluded, 1-4 scaled")

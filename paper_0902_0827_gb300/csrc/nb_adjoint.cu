@@ -13,19 +13,25 @@ namespace acenb {
 
 // dL/dF of every sorted slot (zero for padding).
 __global__ void k_gather_g(int slot_cap, const int *__restrict__ counts, const int *__restrict__ perm,
-                           const float *__restrict__ G, float4 *__restrict__ gslot)
+                           const float *__restrict__ G, float4 *__restrict__ gslot, long long *__restrict__ gacc)
 {
     pdl_entry();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < slot_cap) {  // zero the adjoint's fixed-point sums
+        gacc[4ll * s] = 0;
+        gacc[4ll * s + 1] = 0;
+        gacc[4ll * s + 2] = 0;
+        gacc[4ll * s + 3] = 0;
+    }
     if (s >= slot_cap || s >= counts[0]) return;
     const int a = perm[s];
     gslot[s] = a >= 0 ? make_float4(G[3 * (long long)a], G[3 * (long long)a + 1], G[3 * (long long)a + 2], 0.0f)
                       : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 }
 
-// Symmetric type-pair gradients: each ordered pair added half of its
-// unordered pair's derivative to [t_i][t_j], so the value of the symmetric
-// parameter is [a][b] + [b][a] (a != b) or [a][a].
+// Symmetric type-pair gradients: each unique pair added its derivative to
+// [t_i][t_j] for the order in which it was visited, so the value of the
+// symmetric parameter is [a][b] + [b][a] (a != b) or [a][a].
 __global__ void k_tab_finalize(int T, const long long *__restrict__ acc, double *__restrict__ dsig,
                                double *__restrict__ deps)
 {
@@ -83,7 +89,8 @@ cudaError_t launch_backward(nb_ctx *ctx, const float *d_pos, const float *d_q, c
     const int T = ctx->pp.n_types;
     cudaError_t e = launch_pack(ctx, d_pos, d_q, d_type, false);
     if (e != cudaSuccess) return e;
-    launch_pdl(k_gather_g, dim3((S + tb - 1) / tb), dim3(tb), 0, ctx->stream, S, d.counts, d.perm, d_dLdF, d.gslot);
+    launch_pdl(k_gather_g, dim3((S + tb - 1) / tb), dim3(tb), 0, ctx->stream, S, d.counts, d.perm, d_dLdF, d.gslot,
+               d.gacc);
     e = cudaMemsetAsync(d.tab_grad, 0, sizeof(long long) * 2 * T * T, ctx->stream);
     if (e != cudaSuccess) return e;
     e = launch_adjoint_tile(ctx, d_dLdE, d_dLdpos, d_dLdq);

@@ -35,7 +35,7 @@ void free_all(nb_ctx *c)
     auto &d = c->d;
     void *ptrs[] = {d.sys, d.atom_sys, d.atom_col, d.wpos, d.part_orig, d.col_sys, d.col_count, d.col_fill,
                     d.col_slot, d.stage, d.xyzq, d.tslot, d.perm, d.inv, d.bb,
-                    d.clus_sys, d.sys_acc, d.facc, d.list, d.list_n, d.pslot, d.zbin, d.tab_grad, d.counts, d.status, d.lj_tab,
+                    d.clus_sys, d.sys_acc, d.facc, d.gacc, d.list, d.list_n, d.pslot, d.zbin, d.tab_grad, d.counts, d.status, d.lj_tab,
                     d.dbg_n, d.dbg_ij, d.scratch_f, d.scratch_g, d.lj_d, d.gslot, d.eps_type};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -85,6 +85,7 @@ nb_status allocate(nb_ctx *c)
     ALLOC(d.clus_sys, NC);
     ALLOC(d.sys_acc, (int64_t)c->n_sys * kTaskVals);
     ALLOC(d.facc, S * 3);
+    ALLOC(d.gacc, S * 4);
     ALLOC(d.list, NC * 2 * c->list_cap);
     ALLOC(d.list_n, NC * 2);
     ALLOC(d.pslot, S * c->K);

@@ -40,6 +40,7 @@ namespace acenb {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kRing = 512;  // per-warp ring of in-range (cluster, atom) items
+constexpr int kAdjStage = 64;  // staging capacity cap of the adjoint (its larger shared footprint)
 
 struct ForceArgs {
     const SysDesc *sys;
@@ -70,7 +71,8 @@ struct ForceArgs {
     const float4 *lj_d;      // [T*T] 48 eps sig^11, 24 eps sig^5, 4 sig^12, 4 sig^6
     float *dpos;             // [N*3] dL/dx (caller order), or null
     float *dq;               // [N] dL/dq (caller order), or null
-    long long *tab_acc;      // [T*T*2] fixed-point dL/dsig_ab, dL/deps_ab (one ordered half)
+    long long *tab_acc;      // [T*T*2] fixed-point dL/dsig_ab, dL/deps_ab (each unique pair in one order)
+    long long *gacc;         // [S*4] fixed-point dL/dx, dL/dq in sorted order (both atoms of each pair)
 };
 
 __device__ __forceinline__ long long to_fixed(float v, int *status)
@@ -93,7 +95,8 @@ struct ForceSmem {
     uint16_t *surv;
     uint32_t *ring;
     unsigned long long *cacc;
-    int *jf;                   // forward: forces of the staged j atoms, [hi, lo][3][scap * 8] (see add_jf)
+    int *jf;                   // j-atom sums of the staged chunk, [hi, lo][nc][scap * 8] (see add_jf); nc = 3
+                               // forward (force), 4 adjoint (dL/dx, dL/dq)
     float *wimg;               // forward: per-thread periodic-image virial terms [6][blockDim]
     float4 *gj;                // adjoint: staged dL/dF of the j atoms
     float4 *ljd;               // adjoint: derivative factors of the type pairs
@@ -109,7 +112,8 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t
 
 __host__ __device__ inline size_t force_smem_bytes(int T, int scap, int nwarps, bool adj)
 {
-    size_t b = adj ? (size_t)scap * kCluster * 16 + (size_t)T * T * 16 + (size_t)T * T * 16
+    size_t b = adj ? (size_t)scap * kCluster * 16 + (size_t)T * T * 16 + (size_t)T * T * 16 +
+                         (size_t)scap * kCluster * 4 * 8
                    : (size_t)scap * kCluster * 3 * 8 + (size_t)6 * nwarps * 32 * 4;
     b += (size_t)2 * scap * 4;
     b += align16((size_t)T * T * 8);
@@ -139,6 +143,8 @@ __device__ __forceinline__ ForceSmem carve(unsigned char *smem, int T, int scap,
         off += (size_t)6 * nwarps * 32 * 4;
     }
     if (adj) {
+        S.jf = reinterpret_cast<int *>(smem + off);
+        off += (size_t)scap * kCluster * 4 * 8;
         S.gj = reinterpret_cast<float4 *>(smem + off);
         off += (size_t)scap * kCluster * 16;
         S.ljd = reinterpret_cast<float4 *>(smem + off);
@@ -260,7 +266,7 @@ __device__ __forceinline__ long long to_fixed_tab(float v, int *status)
 // With d = x_j - x_i, F_i = h d where h = U'(r)/r, and g = G_i - G_j:
 //   dL/dx_i -= h g + (h'/r)(g.d) d + (gE-weighted h) d     (h' = dh/dr)
 //   dL/dq_i += w_c ke q_j (phi'(r)/r (g.d) + gE_c phi(r))
-//   dL/dsig_ab, dL/deps_ab (+= half: each unordered pair is visited twice)
+//   dL/dsig_ab, dL/deps_ab (each unique pair is visited once)
 // through dU/dA = w S r^-12, dU/dB = -w S r^-6 and the chain factors
 // dA/dsig = 48 eps sig^11, dB/dsig = 24 eps sig^5, dA/deps = 4 sig^12,
 // dB/deps = 4 sig^6 of the type pair.
@@ -268,7 +274,7 @@ template <bool EWALD>
 __device__ __forceinline__ void eval_pair_adj(const PairParams &P, const ForceSmem &S, int ti_row, float qi_ke, float gix,
                                               float giy, float giz, float gE_lj, float gE_c, bool in, float dx,
                                               float dy, float dz, float r2, float qj, int tj, float4 gj, bool is14,
-                                              int *status, AccAdj &acc)
+                                              int *status, AccAdj &acc, float &jx, float &jy, float &jz, float &jq)
 {
     if (!in) {  // masked lanes: keep every product finite (padding sits far away)
         dx = 0.0f;
@@ -321,10 +327,17 @@ __device__ __forceinline__ void eval_pair_adj(const PairParams &P, const ForceSm
     const float hE = (gE_lj * Ulj1 + gE_c * wc * qq * phi1) * rinv;
     const float cd = fmaf(h1r, gd, hE);
     const float m = in ? 1.0f : 0.0f;
-    acc.dx -= m * fmaf(h, gx, cd * dx);
-    acc.dy -= m * fmaf(h, gy, cd * dy);
-    acc.dz -= m * fmaf(h, gz, cd * dz);
-    acc.dq += m * wc * P.ke * qj * fmaf(phi1 * rinv, gd, gE_c * phi);
+    // the pair seen from j: d -> -d and g -> -g, so dL/dx_j gets the opposite
+    // of dL/dx_i's term and dL/dq_j the same bracket times q_j's partner q_i
+    jx = m * fmaf(h, gx, cd * dx);
+    jy = m * fmaf(h, gy, cd * dy);
+    jz = m * fmaf(h, gz, cd * dz);
+    acc.dx -= jx;
+    acc.dy -= jy;
+    acc.dz -= jz;
+    const float xq = m * wc * fmaf(phi1 * rinv, gd, gE_c * phi);
+    acc.dq += xq * P.ke * qj;
+    jq = xq * qi_ke;
     // type-pair parameters
     const float uA = wlj * Sw * ir12, uB = -wlj * Sw * ir6;
     const float uA1 = wlj * fmaf(S1, ir12, -12.0f * Sw * ir12 * rinv);
@@ -332,7 +345,7 @@ __device__ __forceinline__ void eval_pair_adj(const PairParams &P, const ForceSm
     const float gA = fmaf(uA1 * rinv, gd, gE_lj * uA), gB = fmaf(uB1 * rinv, gd, gE_lj * uB);
     if (in) {
         const float4 c = S.ljd[ti_row + tj];
-        const float dsig = 0.5f * fmaf(gA, c.x, gB * c.y), deps = 0.5f * fmaf(gA, c.z, gB * c.w);
+        const float dsig = fmaf(gA, c.x, gB * c.y), deps = fmaf(gA, c.z, gB * c.w);
         atomicAdd(&S.tacc[2 * (ti_row + tj)], (unsigned long long)to_fixed_tab(dsig, status));
         atomicAdd(&S.tacc[2 * (ti_row + tj) + 1], (unsigned long long)to_fixed_tab(deps, status));
     }
@@ -365,24 +378,26 @@ __device__ __forceinline__ void eval_pair(const PairParams &P, const float2 *__r
     fjz = fdz;
 }
 
-// Force on a staged j atom, exactly at the 2^32 fixed-point grid of the
-// global sums, with two 32-bit shared-memory integer atomics: f 2^32 =
-// hi 2^16 + lo with hi = rint(f 2^16) and lo = rint((f 2^16 - hi) 2^16)
-// (both products and the difference are exact in FP32).  A chunk adds at
-// most 8 contributions (one per i atom of the block's cluster) to a slot, so
-// for |f| < 2048 neither 32-bit sum can overflow; larger (or non-finite)
-// forces go straight to the global 64-bit sums.  The hi array is at slot,
-// the lo array 3 * js further.
-__device__ __forceinline__ void add_jf(const ForceArgs &A, const ForceSmem &S, int e, int k, int slot, int comp,
-                                       float f)
+// Contribution to a staged j atom, exactly at the 2^32 fixed-point grid of
+// the global sums, with two 32-bit shared-memory integer atomics:
+// f 2^32 = hi 2^24 + lo with hi = rint(f 2^8) and lo = rint((f 2^8 - hi) 2^24)
+// (the products and the difference are exact in FP32, and lo is an integer
+// whenever |f 2^8| >= 1).  A chunk adds at most 8 contributions (one per i
+// atom of the block's cluster) to a slot, so for |f| < 2^19 neither 32-bit
+// sum can overflow; larger (or non-finite) values go straight to the global
+// 64-bit sums (nc components per slot there).  The hi array is at slot, the
+// lo array nc * js further.
+template <int NC>
+__device__ __forceinline__ void add_jf(const ForceArgs &A, const ForceSmem &S, long long *gsum, int e, int k, int slot,
+                                       int comp, float f)
 {
-    if (fabsf(f) < 2048.0f) {
-        const float t = f * 65536.0f;
+    if (fabsf(f) < 524288.0f) {
+        const float t = f * 256.0f;
         const float hf = rintf(t);
         atomicAdd(S.jf + slot, (int)hf);
-        atomicAdd(S.jf + slot + 3 * A.scap * kCluster, __float2int_rn((t - hf) * 65536.0f));
+        atomicAdd(S.jf + slot + NC * A.scap * kCluster, __float2int_rn((t - hf) * 16777216.0f));
     } else {
-        long long *g = A.facc + 3ll * ((long long)(S.ent[e] & kJMask) * kCluster + k) + comp;
+        long long *g = gsum + (long long)NC * ((long long)(S.ent[e] & kJMask) * kCluster + k) + comp;
         atomicAdd((unsigned long long *)g, (unsigned long long)to_fixed(f, A.status));
     }
 }
@@ -422,17 +437,26 @@ __device__ __forceinline__ void eval_item(const ForceArgs &A, const ForceSmem &S
         }
     }
     if constexpr (ADJ) {
+        float jx, jy, jz, jq;
         eval_pair_adj<EWALD>(A.P, S, ia.ti_row, ia.qi, ia.gix, ia.giy, ia.giz, ia.gE_lj, ia.gE_c, active, dx, dy, dz,
-                             active ? r2 : 1.0f, pj.w, tj, S.gj[idx], (item & 1u) != 0u, A.status, acc);
+                             active ? r2 : 1.0f, pj.w, tj, S.gj[idx], (item & 1u) != 0u, A.status, acc, jx, jy, jz,
+                             jq);
+        if (active) {
+            const int js = A.scap * kCluster;
+            add_jf<4>(A, S, A.gacc, e, k, idx, 0, jx);
+            add_jf<4>(A, S, A.gacc, e, k, idx + js, 1, jy);
+            add_jf<4>(A, S, A.gacc, e, k, idx + 2 * js, 2, jz);
+            add_jf<4>(A, S, A.gacc, e, k, idx + 3 * js, 3, jq);
+        }
     } else {
         float fjx, fjy, fjz;
         eval_pair<EWALD>(A.P, S.lj, ia.ti_row, ia.qi, active, dx, dy, dz, active ? r2 : 1.0f, pj.w, tj,
                                 (item & 1u) != 0u, acc, fjx, fjy, fjz);
         if (active) {
             const int js = A.scap * kCluster;
-            add_jf(A, S, e, k, idx, 0, fjx);
-            add_jf(A, S, e, k, idx + js, 1, fjy);
-            add_jf(A, S, e, k, idx + 2 * js, 2, fjz);
+            add_jf<3>(A, S, A.facc, e, k, idx, 0, fjx);
+            add_jf<3>(A, S, A.facc, e, k, idx + js, 1, fjy);
+            add_jf<3>(A, S, A.facc, e, k, idx + 2 * js, 2, fjz);
         }
     }
 }
@@ -458,7 +482,7 @@ __device__ __forceinline__ ClusterHead load_head(const ForceArgs &A, int I, int 
     h.pi = __ldg(A.xyzq + islot);
     h.ti = __ldg(A.tslot + islot);
     h.nA = __ldg(A.list_n + 2 * I);
-    h.nE = ADJ ? h.nA + __ldg(A.list_n + 2 * I + 1) : h.nA;
+    h.nE = h.nA;  // the half list: every pair once (Newton's third law, both modes)
     h.pe = lane < A.K ? __ldg(A.pslot + islot * A.K + lane) : -1;
     if (ADJ) h.gi = __ldg(A.gslot + islot);
     return h;
@@ -493,6 +517,30 @@ __device__ __forceinline__ void flush_energy(const ForceArgs &A, const ForceSmem
 
 // Forward: add the block's fixed-point forces of the n staged j clusters
 // listed at ent to the global fixed-point force array and clear them.
+// The 2^32 fixed-point value of a hi/lo slot pair (see add_jf).
+__device__ __forceinline__ unsigned long long split_sum(const int *jf, int lo_off, int i)
+{
+    return (unsigned long long)(((long long)jf[i] << 24) + (long long)jf[lo_off + i]);
+}
+
+// Adjoint: add the block's j-atom sums (dL/dx, dL/dq) of the n staged
+// clusters listed at ent to the global fixed-point sums and clear them.
+__device__ __forceinline__ void flush_jadj(const ForceArgs &A, const ForceSmem &S, const uint32_t *ent, int n)
+{
+    const int js = A.scap * kCluster;
+    for (int p = threadIdx.x; p < n * kCluster; p += blockDim.x) {
+        const int e = p >> 3, k = (p & 7) ^ (e & 7);  // p = swz(e, k)
+        long long *g = A.gacc + 4ll * ((long long)(ent[e] & kJMask) * kCluster + k);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const unsigned long long v = split_sum(S.jf, 4 * js, c * js + p);
+            if (v) atomicAdd((unsigned long long *)&g[c], v);
+            S.jf[c * js + p] = 0;
+            S.jf[4 * js + c * js + p] = 0;
+        }
+    }
+}
+
 // With VIRIAL, also add the periodic-image part of the virial: a pair whose
 // j atom was taken at its image x_j + s contributes s (x) f_j beyond the
 // x (x) F sum over atoms (see k_unpack_forces); s is the entry's shift
@@ -509,12 +557,8 @@ __device__ __forceinline__ void flush_jf(const ForceArgs &A, const ForceSmem &S,
         const int e = p >> 3, k = (p & 7) ^ (e & 7);  // p = swz(e, k)
         const uint32_t en = ent[e];
         const long long g = 3ll * ((long long)(en & kJMask) * kCluster + k);
-        const int *lo = S.jf + 3 * js;
-        const unsigned long long v0 = ((unsigned long long)(long long)S.jf[p] << 16) + (unsigned long long)(long long)lo[p];
-        const unsigned long long v1 =
-            ((unsigned long long)(long long)S.jf[js + p] << 16) + (unsigned long long)(long long)lo[js + p];
-        const unsigned long long v2 =
-            ((unsigned long long)(long long)S.jf[2 * js + p] << 16) + (unsigned long long)(long long)lo[2 * js + p];
+        const unsigned long long v0 = split_sum(S.jf, 3 * js, p), v1 = split_sum(S.jf, 3 * js, js + p),
+                                 v2 = split_sum(S.jf, 3 * js, 2 * js + p);
         if (v0) atomicAdd((unsigned long long *)&A.facc[g], v0);
         if (v1) atomicAdd((unsigned long long *)&A.facc[g + 1], v1);
         if (v2) atomicAdd((unsigned long long *)&A.facc[g + 2], v2);
@@ -563,10 +607,9 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
         }
     }
     if (threadIdx.x < kTaskVals) S.cacc[threadIdx.x] = 0ull;
-    if (!ADJ) {
-        for (int k = threadIdx.x; k < 6 * A.scap * kCluster; k += blockDim.x) S.jf[k] = 0;
+    for (int k = threadIdx.x; k < (ADJ ? 8 : 6) * A.scap * kCluster; k += blockDim.x) S.jf[k] = 0;
+    if (!ADJ)
         for (int k = threadIdx.x; k < 6 * (int)blockDim.x; k += blockDim.x) S.wimg[k] = 0.0f;
-    }
     __syncthreads();
     using AccT = typename std::conditional<ADJ, AccAdj, Acc>::type;
 
@@ -625,7 +668,8 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
             const int nC = min(A.scap, nE - c0);
             if (c0 > 0) {
                 __syncthreads();  // the staging buffers are free
-                if (!ADJ) flush_jf<VIRIAL>(A, S, S.lst + ((ci - 1) & 1) * A.scap, A.scap, Lx, Ly, Lz);
+                if (ADJ) flush_jadj(A, S, S.lst + ((ci - 1) & 1) * A.scap, A.scap);
+                else flush_jf<VIRIAL>(A, S, S.lst + ((ci - 1) & 1) * A.scap, A.scap, Lx, Ly, Lz);
             }
             ForceSmem Sc = S;
             Sc.ent = S.lst + (ci & 1) * A.scap;
@@ -666,7 +710,7 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
                 const uint32_t ibase = ((uint32_t)e << 7) | (ishift << 4);
                 uint32_t exm = sv ? 0u : 0xFFu, m14 = 0u;
                 if (J == I && ((ent >> kShiftBit) & 0x3Fu) == 0u)
-                    exm |= ADJ ? 1u << w : (2u << w) - 1u;  // i == j; forward: j > i only
+                    exm |= (2u << w) - 1u;  // pairs of I itself: j > i only
                 const bool fl = sv && (ent & kExclFlag) != 0u;
                 if (__any_sync(kFull, fl)) {
                     for (int m = 0; m < A.K; ++m) {
@@ -723,10 +767,11 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
             }
             __syncwarp();
         }
-        if (!ADJ && nE > 0) {
+        if (nE > 0) {
             const int last = (nE - 1) / A.scap;
             __syncthreads();
-            flush_jf<VIRIAL>(A, S, S.lst + (last & 1) * A.scap, nE - last * A.scap, Lx, Ly, Lz);
+            if (ADJ) flush_jadj(A, S, S.lst + (last & 1) * A.scap, nE - last * A.scap);
+            else flush_jf<VIRIAL>(A, S, S.lst + (last & 1) * A.scap, nE - last * A.scap, Lx, Ly, Lz);
         }
         if (!iv) continue;
         if constexpr (ADJ) {
@@ -740,14 +785,11 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
                 v3 += __shfl_xor_sync(kFull, v3, o);
             }
             if (lane == 0) {
-                const long long a = A.perm[islot];
-                const float sc = 2.3283064365386963e-10f;  // 2^-32
-                if (A.dpos) {
-                    A.dpos[3 * a] = __ll2float_rn(v0) * sc;
-                    A.dpos[3 * a + 1] = __ll2float_rn(v1) * sc;
-                    A.dpos[3 * a + 2] = __ll2float_rn(v2) * sc;
-                }
-                if (A.dq) A.dq[a] = __ll2float_rn(v3) * sc;
+                unsigned long long *g = (unsigned long long *)A.gacc + 4ll * islot;
+                atomicAdd(g, (unsigned long long)v0);
+                atomicAdd(g + 1, (unsigned long long)v1);
+                atomicAdd(g + 2, (unsigned long long)v2);
+                atomicAdd(g + 3, (unsigned long long)v3);
             }
         } else {
             // force of atom i: sum of the 32 lanes in 64-bit fixed point
@@ -937,6 +979,25 @@ __global__ void __launch_bounds__(256) k_unpack_forces(int slot_cap, int *__rest
     if (threadIdx.x == 0) counts[2] = 0;
 }
 
+// Adjoint sums (sorted order, fixed point) to FP32 dL/dx, dL/dq in the
+// caller's order.
+__global__ void k_unpack_adjoint(int slot_cap, const int *__restrict__ counts, const int *__restrict__ perm,
+                                 const long long *__restrict__ gacc, float *__restrict__ dpos, float *__restrict__ dq)
+{
+    pdl_entry();
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= slot_cap || s >= counts[0]) return;
+    const int a = perm[s];
+    if (a < 0) return;
+    const float sc = 2.3283064365386963e-10f;  // 2^-32
+    if (dpos) {
+        dpos[3ll * a] = __ll2float_rn(gacc[4ll * s]) * sc;
+        dpos[3ll * a + 1] = __ll2float_rn(gacc[4ll * s + 1]) * sc;
+        dpos[3ll * a + 2] = __ll2float_rn(gacc[4ll * s + 2]) * sc;
+    }
+    if (dq) dq[a] = __ll2float_rn(gacc[4ll * s + 3]) * sc;
+}
+
 template <bool ADJ, bool EWALD, bool VIRIAL, bool DEBUG>
 static void launch_force_t(nb_ctx *ctx, const ForceArgs &A)
 {
@@ -1045,7 +1106,8 @@ cudaError_t launch_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, con
 size_t force_smem_for(int T, int scap, int K)
 {
     (void)K;
-    return std::max(force_smem_bytes(T, scap, kCluster, true), force_smem_bytes(T, scap, kCluster, false));
+    return std::max(force_smem_bytes(T, std::min(scap, kAdjStage), kCluster, true),
+                    force_smem_bytes(T, scap, kCluster, false));
 }
 
 cudaError_t launch_adjoint_tile(nb_ctx *ctx, const double *d_dLdE, float *d_dpos, float *d_dq)
@@ -1058,9 +1120,14 @@ cudaError_t launch_adjoint_tile(nb_ctx *ctx, const double *d_dLdE, float *d_dpos
     A.dpos = d_dpos;
     A.dq = d_dq;
     A.tab_acc = d.tab_grad;
+    A.gacc = d.gacc;
+    A.scap = std::min(ctx->stage_cap, kAdjStage);
     if (ctx->pp.ewald) launch_force_t<true, true, false, false>(ctx, A);
     else launch_force_t<true, false, false, false>(ctx, A);
-    return cudaGetLastError();
+    const int tb = 256;
+    const int S = (int)ctx->slot_cap;
+    return launch_pdl(k_unpack_adjoint, dim3((S + tb - 1) / tb), dim3(tb), 0, ctx->stream, S, d.counts, d.perm,
+                      d.gacc, d_dpos, d_dq);
 }
 
 }  // namespace acenb

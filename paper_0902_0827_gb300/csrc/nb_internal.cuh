@@ -104,6 +104,7 @@ struct DevBuffers {
     int *clus_sys = nullptr;         // [NC] system of each cluster
     long long *sys_acc = nullptr;    // [n_sys*kTaskVals] per-system fixed-point energies (2^32) and virial (2^20)
     long long *facc = nullptr;       // [S*3] fixed-point forces in sorted order (both atoms of each pair)
+    long long *gacc = nullptr;       // [S*4] adjoint: fixed-point dL/dx, dL/dq in sorted order
     uint32_t *list = nullptr;        // [NC*2*list_cap] per cluster: half list, then the other half
     int *list_n = nullptr;           // [NC*2] lengths of the two halves
     int *pslot = nullptr;            // [S*K] partner slots (slot << 1) | is14, -1 pad
