@@ -114,30 +114,18 @@ class Clocks:
 
 
 def dist_setup():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        import torch.distributed as dist
-        backend = "nccl"
-        dist.init_process_group(backend=backend)
-    return world, rank, local
+    from paper_0902_0827_gb300 import replicas
+    return replicas.setup("nccl")
 
 
 def barrier(world):
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
+    from paper_0902_0827_gb300 import replicas
+    replicas.barrier(world)
 
 
 def max_over_ranks(x: float, world: int) -> float:
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_0902_0827_gb300 import replicas
+    return replicas.max_over_ranks(x, world, "cuda")
 
 
 def graph_of(fn, dev):
