@@ -95,7 +95,10 @@ cudaError_t launch_backward(nb_ctx *ctx, const float *d_pos, const float *d_q, c
     if (e != cudaSuccess) return e;
     e = launch_adjoint_tile(ctx, d_dLdE, d_dLdpos, d_dLdq);
     if (e != cudaSuccess) return e;
-    if (d_dsig || d_deps) launch_pdl(k_tab_finalize, dim3((T * T + tb - 1) / tb), dim3(tb), 0, ctx->stream, T, d.tab_grad, d_dsig, d_deps);
+    if (d_dsig || d_deps)
+        e = launch_pdl(k_tab_finalize, dim3((T * T + tb - 1) / tb), dim3(tb), 0, ctx->stream, T, d.tab_grad, d_dsig,
+                       d_deps);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

@@ -340,14 +340,12 @@ constexpr int kPartnerRounds = (kCluster * kMaxPartners + 31) / 32;
 // deterministic.  Also writes the partner slots of I's atoms and flags the
 // entries whose cluster may hold a topology partner of I (a Bloom filter of
 // the partners' clusters: never a missed partner, rarely a spurious flag).
-__global__ void __launch_bounds__(kListWarps * 32) k_list(const SysDesc *__restrict__ sys, const int *__restrict__ counts,
-                                              const float4 *__restrict__ bb, const int *__restrict__ clus_sys,
-                                              const int *__restrict__ col_slot, const int2 *__restrict__ zbin,
-                                              const int *__restrict__ perm,
-                                              const int *__restrict__ part_orig, const int *__restrict__ inv, int K,
-                                              float rcm, int cap, uint32_t *__restrict__ list,
-                                              int *__restrict__ list_n, int *__restrict__ pslot,
-                                              int *__restrict__ status)
+__global__ void __launch_bounds__(kListWarps * 32)
+    k_list(const SysDesc *__restrict__ sys, const int *__restrict__ counts, const float4 *__restrict__ bb,
+           const int *__restrict__ clus_sys, const int *__restrict__ col_slot, const int2 *__restrict__ zbin,
+           const int *__restrict__ perm, const int *__restrict__ part_orig, const int *__restrict__ inv, int K,
+           float rcm, int cap, uint32_t *__restrict__ list, int *__restrict__ list_n, int *__restrict__ pslot,
+           int *__restrict__ status)
 {
     pdl_entry();
     const unsigned FULL = 0xffffffffu;
@@ -530,17 +528,20 @@ cudaError_t launch_build(nb_ctx *ctx, const float *d_pos)
     cudaError_t e = cudaMemsetAsync(d.col_count, 0, sizeof(int) * (ctx->n_cols + 1), st);
     if (e != cudaSuccess) return e;
     const int tb = 256;
-    launch_pdl(k_bin, dim3((N + tb - 1) / tb), dim3(tb), 0, st, N, d_pos, d.sys, d.atom_sys, d.wpos, d.atom_col, d.col_count,
-                                            ctx->n_cols, ctx->n_sys, d.col_slot, d.col_fill, d.counts, d.status);
-    launch_pdl(k_scatter, dim3((N + tb - 1) / tb), dim3(tb), 0, st, N, d.atom_col, d.col_fill, d.stage);
-    launch_pdl(k_colsort, dim3(ctx->n_cols), dim3(kSortThreads), 0, st, d.col_count, d.col_slot, d.col_sys, d.sys, d.stage, d.wpos, d.xyzq,
-                                           d.tslot, d.perm, d.inv, d.bb, d.clus_sys, d.zbin);
+    e = launch_pdl(k_bin, dim3((N + tb - 1) / tb), dim3(tb), 0, st, N, d_pos, d.sys, d.atom_sys, d.wpos, d.atom_col,
+                   d.col_count, ctx->n_cols, ctx->n_sys, d.col_slot, d.col_fill, d.counts, d.status);
+    if (e == cudaSuccess)
+        e = launch_pdl(k_scatter, dim3((N + tb - 1) / tb), dim3(tb), 0, st, N, d.atom_col, d.col_fill, d.stage);
+    if (e == cudaSuccess)
+        e = launch_pdl(k_colsort, dim3(ctx->n_cols), dim3(kSortThreads), 0, st, d.col_count, d.col_slot, d.col_sys,
+                       d.sys, d.stage, d.wpos, d.xyzq, d.tslot, d.perm, d.inv, d.bb, d.clus_sys, d.zbin);
     const int lw = kListWarps;
     const int lblocks = (int)std::max<int64_t>(1, (ctx->clus_cap + lw - 1) / lw);
-    launch_pdl(k_list, dim3(lblocks), dim3(lw * 32), 0, st, d.sys, d.counts, d.bb, d.clus_sys, d.col_slot, d.zbin, d.perm, d.part_orig,
-                                        d.inv,
-                                        ctx->K, ctx->pp.rc + ctx->pp.list_margin, ctx->list_cap, d.list, d.list_n,
-                                        d.pslot, d.status);
+    if (e == cudaSuccess)
+        e = launch_pdl(k_list, dim3(lblocks), dim3(lw * 32), 0, st, d.sys, d.counts, d.bb, d.clus_sys, d.col_slot,
+                       d.zbin, d.perm, d.part_orig, d.inv, ctx->K, ctx->pp.rc + ctx->pp.list_margin, ctx->list_cap,
+                       d.list, d.list_n, d.pslot, d.status);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

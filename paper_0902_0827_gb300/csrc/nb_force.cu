@@ -909,7 +909,10 @@ __global__ void __launch_bounds__(256) k_unpack_forces(int slot_cap, int *__rest
     __shared__ int blk_sys;
     if (VIRIAL) {
         if (threadIdx.x < 6) blk_w[threadIdx.x] = 0ull;
-        if (threadIdx.x == 0) blk_sys = blockIdx.x * blockDim.x < nslots ? clus_sys[blockIdx.x * blockDim.x / kCluster] : -1;
+        if (threadIdx.x == 0) {
+            const int s0 = blockIdx.x * blockDim.x;
+            blk_sys = s0 < nslots ? clus_sys[s0 / kCluster] : -1;
+        }
         __syncthreads();
     }
     for (int s0 = blockIdx.x * blockDim.x; s0 < nslots; s0 += gridDim.x * blockDim.x) {
