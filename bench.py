@@ -420,40 +420,41 @@ def main():
     if not args.no_extras:
         line["adjoint"] = adjoint_leg(ctx, pos, q, typ, args.steps, flush, ms, npairs)
         line["batched"] = batched_leg(args.steps, flush, dev)
-        # end to end through the public API with host buffers (pinned)
-        hpos = pos.cpu().pin_memory()
-        hq = q.cpu().pin_memory()
-        ht = typ.cpu().pin_memory()
-        hF = torch.empty((N, 3), dtype=torch.float32).pin_memory()
-        hE = torch.empty((1, 2), dtype=torch.float64).pin_memory()
-        hW = torch.empty((1, 6), dtype=torch.float64).pin_memory()
-        dpos, dq, dt = torch.empty_like(pos), torch.empty_like(q), torch.empty_like(typ)
+        # end to end through the public API with host buffers (pinned): the
+        # step's inputs (positions, charges, types) travel in one host->device
+        # copy and its results (forces, energies, virial) in one
+        # device->host copy, as a caller packing its buffers would do
+        nb_in = N * 12 + N * 4 + N * 4
+        out_f, out_e = N * 12, (N * 12 + 7) // 8 * 8
+        nb_out = out_e + 2 * 8 + 6 * 8
+        h_in = torch.empty(nb_in, dtype=torch.uint8).pin_memory()
+        h_out = torch.empty(nb_out, dtype=torch.uint8).pin_memory()
+        h_in[:N * 12].view(torch.float32).copy_(pos.cpu().reshape(-1))
+        h_in[N * 12:N * 16].view(torch.float32).copy_(q.cpu())
+        h_in[N * 16:].view(torch.int32).copy_(typ.cpu())
+        d_in = torch.empty(nb_in, dtype=torch.uint8, device=dev)
+        d_out = torch.empty(nb_out, dtype=torch.uint8, device=dev)
+        dpos = d_in[:N * 12].view(torch.float32).view(N, 3)
+        dq = d_in[N * 12:N * 16].view(torch.float32)
+        dt = d_in[N * 16:].view(torch.int32)
+        oF = d_out[:out_f].view(torch.float32).view(N, 3)
+        oE = d_out[out_e:out_e + 16].view(torch.float64).view(1, 2)
+        oW = d_out[out_e + 16:].view(torch.float64).view(1, 6)
 
         def e2e_step():
-            dpos.copy_(hpos, non_blocking=True)
-            dq.copy_(hq, non_blocking=True)
-            dt.copy_(ht, non_blocking=True)
+            d_in.copy_(h_in, non_blocking=True)
             ctx.build(dpos)
-            ctx.forces(dpos, dq, dt, F=F, energy=E, virial=W)
-            hF.copy_(F, non_blocking=True)
-            hE.copy_(E, non_blocking=True)
-            hW.copy_(W, non_blocking=True)
+            ctx.forces(dpos, dq, dt, F=oF, energy=oE, virial=oW)
+            h_out.copy_(d_out, non_blocking=True)
 
         for _ in range(3):
             e2e_step()
         torch.cuda.synchronize()
-        tt = []
-        for _ in range(args.steps):
-            flush.zero_()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
-            e2e_step()
-            b.record()
-            torch.cuda.synchronize()
-            tt.append(a.elapsed_time(b))
+        # the same CUDA-graph replay as the device-side step (copies included)
+        ge = graph_of(e2e_step, dev)
+        tt = [time_steps(ge.replay, 1, flush) for _ in range(args.steps)]
         e2e_ms = max_over_ranks(sum(tt) / len(tt), world)
-        bi = hpos.numel() * 4 + hq.numel() * 4 + ht.numel() * 4
-        bo = hF.numel() * 4 + hE.numel() * 8 + hW.numel() * 8
+        bi, bo = nb_in, nb_out
         line["e2e"] = {"value": world * npairs / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": bi,
                        "d2h_bytes_per_step": bo, "ms_per_step": e2e_ms}
         line["gpu_launches"] += (BUILD_LAUNCHES + FORCE_LAUNCHES) * args.steps
