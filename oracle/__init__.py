@@ -21,6 +21,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "nb_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "ewald_oracle.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
@@ -33,10 +34,10 @@ def build(force: bool = False) -> str:
     """Compile liboracle.so (gcc, FP contraction off so FP32 predicates round
     exactly as written)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(os.path.getmtime(s) for s in _SRCS):
         tmp = _LIB + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared", "-fopenmp",
-               "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+               "-ffp-contract=off", "-fno-fast-math", "-o", tmp, *_SRCS, "-lm"]
         subprocess.check_call(cmd)
         os.replace(tmp, _LIB)
     return _LIB
@@ -76,6 +77,10 @@ def lib():
             L.orc_grid_dims.restype = None
             L.orc_num_threads.argtypes = []
             L.orc_num_threads.restype = I
+            L.orc_ewald_recip.argtypes = [I64, P, P, P, D, D, I, I, I, P, P, P]
+            L.orc_ewald_recip.restype = I
+            L.orc_ewald_corrections.argtypes = [I64, P, P, P, D, D, I64, P, I64, P, D, P, P, P]
+            L.orc_ewald_corrections.restype = None
             _lib = L
     return _lib
 
