@@ -23,6 +23,11 @@ import numpy as np
 from . import _c, _p, lib
 
 
+def _f32(x) -> float:
+    """A parameter as the FP32 value the library's parameter block carries."""
+    return float(np.float32(x))
+
+
 def ewald_recip(sys, kmax, pos=None, q=None):
     """Direct reciprocal-space Ewald sum: (F [N,3], E, W [6]) in FP64."""
     pos = _c(sys.pos if pos is None else pos, np.float32)
@@ -33,7 +38,7 @@ def ewald_recip(sys, kmax, pos=None, q=None):
     E = np.zeros(1)
     W = np.zeros(6)
     kx, ky, kz = (kmax, kmax, kmax) if np.isscalar(kmax) else kmax
-    rc = lib().orc_ewald_recip(n, _p(pos), _p(q), _p(box), float(sys.ewald_alpha), float(sys.coulomb_k),
+    rc = lib().orc_ewald_recip(n, _p(pos), _p(q), _p(box), _f32(sys.ewald_alpha), _f32(sys.coulomb_k),
                                int(kx), int(ky), int(kz), _p(F), _p(E), _p(W))
     if rc != 0:
         raise MemoryError("orc_ewald_recip")
@@ -51,8 +56,8 @@ def ewald_corrections(sys, pos=None, q=None):
     F = np.zeros((n, 3))
     E = np.zeros(2)
     W = np.zeros(6)
-    lib().orc_ewald_corrections(n, _p(pos), _p(q), _p(box), float(sys.ewald_alpha), float(sys.coulomb_k),
-                                ex.shape[0], _p(ex), p14.shape[0], _p(p14), float(sys.scale14_coul),
+    lib().orc_ewald_corrections(n, _p(pos), _p(q), _p(box), _f32(sys.ewald_alpha), _f32(sys.coulomb_k),
+                                ex.shape[0], _p(ex), p14.shape[0], _p(p14), _f32(sys.scale14_coul),
                                 _p(F), _p(E), _p(W))
     return F, float(E[0]), float(E[1]), W
 
@@ -80,13 +85,16 @@ def spme_moduli(K: int, n: int) -> np.ndarray:
 
 def spme(sys, grid, order: int = 4, pos=None, q=None):
     """Smooth PME reciprocal energy, forces and virial in FP64 (no
-    corrections): (F [N,3], E, W [6])."""
+    corrections): (F [N,3], E, W [6]).  Even orders only: for odd n the
+    B-spline modulus sum vanishes at the Nyquist index of an even grid."""
+    if order % 2 or order < 4:
+        raise ValueError("smooth PME is defined here for even orders >= 4")
     x = np.asarray(sys.pos if pos is None else pos, dtype=np.float64)
     qv = np.asarray(sys.q if q is None else q, dtype=np.float64)
     L = np.asarray(sys.box, dtype=np.float64)
     K = np.asarray(grid, dtype=np.int64)
     n = order
-    alpha, ke = float(sys.ewald_alpha), float(sys.coulomb_k)
+    alpha, ke = _f32(sys.ewald_alpha), _f32(sys.coulomb_k)
     V = float(np.prod(L))
     x = x - L * np.floor(x / L)
     u = x * K / L

@@ -103,7 +103,7 @@ def test_direct_sum_forces_are_minus_gradient():
 
 def test_pme_forces_are_minus_gradient():
     s = water216(0.32)
-    grid, order = (24, 20, 28), 5
+    grid, order = (24, 20, 28), 6
     F, _, _ = ew.spme(s, grid, order)
     x = s.pos.astype(np.float64)
     h = 1e-5
@@ -171,14 +171,15 @@ def test_shear_virial_by_triclinic_finite_difference():
     r32 = s.pos.astype(np.float64)
     q32 = s.q.astype(np.float64)
     h0 = np.diag(s.box.astype(np.float64))
-    assert abs(triclinic_recip_energy(r32, q32, h0, 0.3, s.coulomb_k, kmax) - E) <= 1e-9 * abs(E)
+    a32, ke32 = float(np.float32(0.3)), float(np.float32(s.coulomb_k))  # parameters are FP32 values
+    assert abs(triclinic_recip_energy(r32, q32, h0, a32, ke32, kmax) - E) <= 1e-9 * abs(E)
     h = 1e-6
     for k, (a, b) in zip((3, 4, 5), ((0, 1), (0, 2), (1, 2))):
         Es = []
         for e in (h, -h):
             D = np.eye(3)
             D[a, b] += e  # x_a -> x_a + e x_b
-            Es.append(triclinic_recip_energy(r32 @ D.T, q32, D @ h0, 0.3, s.coulomb_k, kmax))
+            Es.append(triclinic_recip_energy(r32 @ D.T, q32, D @ h0, a32, ke32, kmax))
         fd = -(Es[0] - Es[1]) / (2 * h)
         assert abs(fd - W[k]) <= 1e-6 * max(1.0, np.abs(W).max())
 
