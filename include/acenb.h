@@ -143,7 +143,8 @@ nb_status nb_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, const int
                     float *d_F, double *d_energy, double *d_virial);
 
 /* nb_backward - adjoint of L = sum_i G_i . F_i + sum_s gE_s . E_s, the pair
- * list recomputed from the last build.
+ * list recomputed from the last build (short-range terms; a context with
+ * smooth PME enabled returns NB_ERR_UNSUPPORTED).
  *   d_dLdF      [N, 3]      G;  d_dLdE [n_sys*2] gE (LJ, Coulomb) or NULL (= 0);
  *   d_dLdpos    [N, 3]      dL/dx = -H G - (gE weighted) F   (Hessian-vector product);
  *   d_dLdq      [N]         dL/dq;
@@ -245,6 +246,50 @@ nb_status nb_get_profile(nb_ctx *ctx, double *force_ms, int64_t *launches);
 nb_status nb_forces_noalloc(const nb_params *params, const float *d_pos, const float *d_q,
                             const int32_t *d_type, float *d_F, double *d_energy, double *d_virial,
                             void *cuda_stream);
+
+/* Smooth particle-mesh Ewald (section "Molecular dynamics on the GPU": the
+ * long-range electrostatics by PME with the FFT library; section
+ * "Performance": 64^3 grid, fourth-order interpolation), after Essmann et
+ * al.: charges spread on a K1 x K2 x K3 grid with cardinal B-splines of
+ * order n, E_recip = 1/2 sum_{m != 0} ke B(m) C(m) |FQ(m)|^2 with
+ * C(m) = exp(-pi^2 m^2 / alpha^2) / (pi V m^2) and the B-spline moduli B(m),
+ * forces by differentiating the B-splines, virial
+ * W_ab = sum_m E(m) (delta_ab - 2 (1 + pi^2 m^2 / alpha^2) m_a m_b / m^2).
+ * With it come the Ewald corrections that make real + reciprocal space the
+ * Coulomb sum the topology asks for: the self energy
+ * E_self = -ke alpha / sqrt(pi) sum_i q_i^2 and, per excluded pair,
+ * -ke q_i q_j erf(alpha r) / r, per scaled 1-4 pair (1 - scale14_coul) times
+ * that (r from the FP64 minimum image of the caller's coordinates).  Each
+ * pair then contributes w_c ke q_i q_j / r in total: 0 when excluded,
+ * scale14_coul when 1-4, 1 otherwise.
+ * The charge grid is summed in 64-bit fixed point (scale 2^40) and forces,
+ * energies and virial in the library's fixed-point sums, so reruns are
+ * bit-identical; the FFTs are cuFFT's. */
+typedef struct {
+    int32_t grid[3]; /* K1, K2, K3: grid points per box edge, order..1024 */
+    int32_t order;   /* B-spline order n: 4, 6 or 8 */
+    int32_t flags;   /* reserved, must be 0 */
+} nb_pme_params;
+
+/* nb_set_pme - enable smooth PME on a single-system context with Ewald
+ * (ewald_alpha > 0), or disable it (p == NULL).  Allocates the grids and the
+ * FFT plans and tabulates B(m) C(m) for the context's box; synchronises the
+ * stream; not capturable.  Once enabled, nb_forces adds the reciprocal-space
+ * forces and the corrections to d_F, E_recip + E_self + the pair corrections
+ * to the Coulomb energy and their virial to d_virial.
+ * Errors: NB_ERR_INVALID_ARG (grid out of range, flags != 0),
+ * NB_ERR_UNSUPPORTED (batch context, alpha = 0, order not 4/6/8),
+ * NB_ERR_OOM, NB_ERR_CUDA (also for an FFT plan failure). */
+nb_status nb_set_pme(nb_ctx *ctx, const nb_pme_params *p);
+
+/* nb_pme_forces - the long-range part alone (no cell list needed):
+ *   d_pos [N, 3] coordinates (wrapped into the box in FP64), d_q [N] charges;
+ *   d_F [N, 3] output: reciprocal-space forces plus the corrections' forces;
+ *   d_energy [3] output (E_recip, E_self, E_excl) or NULL;
+ *   d_virial [6] output (reciprocal + corrections) or NULL.
+ * Asynchronous.  NB_ERR_NOT_BUILT when PME is not enabled. */
+nb_status nb_pme_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, float *d_F, double *d_energy,
+                        double *d_virial);
 
 /* nb_status_string - static description of a status code. */
 const char *nb_status_string(nb_status s);

@@ -288,6 +288,7 @@ nb_status nb_backward(nb_ctx *ctx, const float *d_pos, const float *d_q, const i
 {
     if (!ctx || !d_pos || !d_q || !d_type || !d_dLdF) return NB_ERR_INVALID_ARG;
     if (!ctx->built) return NB_ERR_NOT_BUILT;
+    if (ctx->pme) return NB_ERR_UNSUPPORTED;
     cudaError_t e = launch_backward(ctx, d_pos, d_q, d_type, d_dLdF, d_dLdE, d_dLdpos, d_dLdq, d_dLdsig_tab,
                                     d_dLdeps_tab);
     return e == cudaSuccess ? NB_OK : NB_ERR_CUDA;
@@ -390,6 +391,7 @@ void nb_destroy(nb_ctx *ctx)
     cudaStreamSynchronize(ctx->stream);
     for (auto &e : ctx->prof_ev) cudaEventDestroy(e);
     ctx->prof_ev.clear();
+    pme_free(ctx);
     free_all(ctx);
     delete ctx;
 }

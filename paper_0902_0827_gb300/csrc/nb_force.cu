@@ -899,7 +899,9 @@ __global__ void __launch_bounds__(256) k_unpack_forces(int slot_cap, int *__rest
                                                        const int *__restrict__ perm, const long long *__restrict__ facc,
                                                        float *__restrict__ F, const float4 *__restrict__ xyzq,
                                                        const int *__restrict__ clus_sys, long long *__restrict__ sys_acc,
-                                                       int n_sys, double *__restrict__ energy, double *__restrict__ virial)
+                                                       int n_sys, double *__restrict__ energy, double *__restrict__ virial,
+                                                       const long long *__restrict__ pme_f,
+                                                       const long long *__restrict__ pme_s)
 {
     pdl_entry();
     const int nslots = min(slot_cap, counts[0]);
@@ -923,9 +925,13 @@ __global__ void __launch_bounds__(256) k_unpack_forces(int slot_cap, int *__rest
         if (a >= 0) {
             const long long v0 = facc[3ll * s], v1 = facc[3ll * s + 1], v2 = facc[3ll * s + 2];
             const float sc = 2.3283064365386963e-10f;  // 2^-32
-            F[3ll * a] = __ll2float_rn(v0) * sc;
-            F[3ll * a + 1] = __ll2float_rn(v1) * sc;
-            F[3ll * a + 2] = __ll2float_rn(v2) * sc;
+            // PME forces (caller order) join the sum before the one rounding;
+            // the atom part of the virial is the short-range forces' alone
+            const long long p0 = pme_f ? pme_f[3ll * a] : 0, p1 = pme_f ? pme_f[3ll * a + 1] : 0,
+                            p2 = pme_f ? pme_f[3ll * a + 2] : 0;
+            F[3ll * a] = __ll2float_rn(v0 + p0) * sc;
+            F[3ll * a + 1] = __ll2float_rn(v1 + p1) * sc;
+            F[3ll * a + 2] = __ll2float_rn(v2 + p2) * sc;
             if (VIRIAL) {
                 const double r = kVirScale / kFixScale;
                 const double fx = (double)v0 * r, fy = (double)v1 * r, fz = (double)v2 * r;
@@ -972,7 +978,12 @@ __global__ void __launch_bounds__(256) k_unpack_forces(int slot_cap, int *__rest
     __threadfence();
     for (int i = threadIdx.x; i < n_sys * kTaskVals; i += blockDim.x) {
         const int sy = i / kTaskVals, k = i % kTaskVals;
-        const double v = (double)__ldcg(&sys_acc[i]) * (k < 2 ? 1.0 / kFixScale : 1.0 / kVirScale);
+        long long raw = __ldcg(&sys_acc[i]);
+        if (pme_s) {  // single system: reciprocal + self + pair corrections join E_Coul and W
+            if (k == 1) raw += __ldcg(&pme_s[0]) + __ldcg(&pme_s[1]) + __ldcg(&pme_s[2]);
+            if (k >= 2) raw += __ldcg(&pme_s[1 + k]);
+        }
+        const double v = (double)raw * (k < 2 ? 1.0 / kFixScale : 1.0 / kVirScale);
         if (k < 2) {
             if (energy) energy[2 * sy + k] = v;
         } else if (virial) {
@@ -1090,18 +1101,24 @@ cudaError_t launch_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, con
         cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n + 1], ctx->stream);
         ctx->prof_n++;
     }
+    const bool pme = ctx->pme && d_pos && !debug_pairs;
+    if (pme) {
+        cudaError_t e = launch_pme(ctx, d_pos, d_q);
+        if (e != cudaSuccess) return e;
+    }
     {
         const int tb = 256;
         const int S = (int)ctx->slot_cap;
         const int blocks = std::max(1, std::min((S + tb - 1) / tb, 4 * ctx->num_sms));
         double *en = debug_pairs ? nullptr : d_energy;
         double *vi = debug_pairs ? nullptr : d_virial;
+        const long long *pf = pme ? pme_forces_acc(ctx) : nullptr, *ps = pme ? pme_sums_acc(ctx) : nullptr;
         if (virial)
             launch_pdl(k_unpack_forces<true>, dim3(blocks), dim3(tb), 0, ctx->stream, S, d.counts, d.perm, d.facc, d_F,
-                       d.xyzq, d.clus_sys, d.sys_acc, ctx->n_sys, en, vi);
+                       d.xyzq, d.clus_sys, d.sys_acc, ctx->n_sys, en, vi, pf, ps);
         else
             launch_pdl(k_unpack_forces<false>, dim3(blocks), dim3(tb), 0, ctx->stream, S, d.counts, d.perm, d.facc,
-                       d_F, d.xyzq, d.clus_sys, d.sys_acc, ctx->n_sys, en, vi);
+                       d_F, d.xyzq, d.clus_sys, d.sys_acc, ctx->n_sys, en, vi, pf, ps);
     }
     return cudaGetLastError();
 }

@@ -19,6 +19,9 @@ constexpr int kErfcDeg = 8;          // degree of the erfcx polynomial in t
 constexpr double kFixScale = 4294967296.0;   // 2^32: fixed-point scale
 constexpr int kTaskVals = 8;         // per system: E_lj, E_c (scale 2^32), W[6] (scale 2^20)
 constexpr double kVirScale = 1048576.0;      // 2^20: fixed-point scale of the virial sums
+constexpr int kPmeAcc = 9;           // PME sums: E_recip, E_self, E_excl (2^32), W[6] (2^20)
+constexpr int kPmeMaxGrid = 1024;    // largest PME grid edge
+struct PmeState;                     // smooth PME state of a single-system context (nb_pme.cu)
 // Padding slots of the sorted arrays sit at this finite, far-away coordinate:
 // their squared distance to any atom (about 3e36) stays finite and is never
 // inside a cutoff, so masked pair arithmetic needs no further guards.
@@ -146,6 +149,7 @@ struct nb_ctx {
     std::vector<acenb::SysDesc> sys_h;
     std::vector<double> sig_tab, eps_tab;  // FP64 type-pair parameters
     acenb::DevBuffers d;
+    acenb::PmeState *pme = nullptr;  // smooth PME, when enabled by nb_set_pme
     // profiling: event pairs around force-kernel launches
     bool profiling = false;
     std::vector<cudaEvent_t> prof_ev;
@@ -204,6 +208,12 @@ size_t force_smem_for(int T, int scap, int K);
 cudaError_t launch_pack(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type, bool zero_sums);
 cudaError_t launch_type_grad(nb_ctx *ctx, const double *gsig_tab, const double *geps_tab, double *gsig, double *geps);
 cudaError_t launch_adjoint_tile(nb_ctx *ctx, const double *d_dLdE, float *d_dpos, float *d_dq);
+// Smooth PME (nb_pme.cu): the reciprocal-space chain into the context's PME
+// force and energy sums; the sums' device arrays (NULL when PME is off).
+cudaError_t launch_pme(nb_ctx *ctx, const float *d_pos, const float *d_q);
+void pme_free(nb_ctx *ctx);
+const long long *pme_forces_acc(const nb_ctx *ctx);
+const long long *pme_sums_acc(const nb_ctx *ctx);
 cudaError_t launch_backward(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type,
                             const float *d_dLdF, const double *d_dLdE, float *d_dLdpos, float *d_dLdq,
                             double *d_dsig, double *d_deps);

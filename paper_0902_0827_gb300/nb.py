@@ -25,7 +25,7 @@ STATUS_NAMES = {
 EXPORTS = ("nb_create", "nb_create_batch", "nb_build_cells", "nb_forces", "nb_backward", "nb_get_status",
            "nb_set_stream", "nb_destroy", "nb_set_tuning", "nb_get_tuning", "nb_get_sizes", "nb_debug_cells",
            "nb_debug_pairs", "nb_status_string", "nb_set_lj_params", "nb_set_profiling", "nb_get_profile",
-           "nb_forces_noalloc", "nb_type_gradients")
+           "nb_forces_noalloc", "nb_type_gradients", "nb_set_pme", "nb_pme_forces")
 
 
 class NbError(RuntimeError):
@@ -50,6 +50,10 @@ class nb_params(ctypes.Structure):
 class nb_tuning(ctypes.Structure):
     _fields_ = [("blocks_per_sm", ctypes.c_int32), ("stage_capacity", ctypes.c_int32),
                 ("list_capacity", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class nb_pme_params(ctypes.Structure):
+    _fields_ = [("grid", ctypes.c_int32 * 3), ("order", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
 
 _lib = None
@@ -90,6 +94,8 @@ def lib(build_if_missing: bool = True):
             "nb_get_profile": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64)], ctypes.c_int),
             "nb_forces_noalloc": ([ctypes.POINTER(nb_params), P, P, P, P, P, P, P], ctypes.c_int),
             "nb_type_gradients": ([P, P, P, P, P], ctypes.c_int),
+            "nb_set_pme": ([P, ctypes.POINTER(nb_pme_params)], ctypes.c_int),
+            "nb_pme_forces": ([P, P, P, P, P, P], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -222,6 +228,32 @@ class Nonbonded:
         W = W if W is not False else None
         _check(lib().nb_forces(self.h, _tptr(pos), _tptr(q), _tptr(typ), _tptr(F), _tptr(E), _tptr(W)),
                "nb_forces")
+        return F, E, W
+
+    def set_pme(self, grid=None, order: int = 4):
+        """Enable smooth PME on the grid (K1, K2, K3) with B-splines of the
+        given order (nb_forces then returns the full Ewald electrostatics), or
+        disable it with grid=None."""
+        if grid is None:
+            _check(lib().nb_set_pme(self.h, None), "nb_set_pme")
+            return
+        p = nb_pme_params()
+        for a in range(3):
+            p.grid[a] = int(grid[a])
+        p.order, p.flags = int(order), 0
+        _check(lib().nb_set_pme(self.h, ctypes.byref(p)), "nb_set_pme")
+
+    def pme_forces(self, pos, q, F=None):
+        """Long-range part alone: forces [N,3] (FP32), energies (E_recip,
+        E_self, E_excl) and virial [6] (FP64)."""
+        import torch
+        self._sync_stream()
+        dev = pos.device
+        if F is None:
+            F = torch.empty((self.n_atoms, 3), dtype=torch.float32, device=dev)
+        E = torch.empty((3,), dtype=torch.float64, device=dev)
+        W = torch.empty((6,), dtype=torch.float64, device=dev)
+        _check(lib().nb_pme_forces(self.h, _tptr(pos), _tptr(q), _tptr(F), _tptr(E), _tptr(W)), "nb_pme_forces")
         return F, E, W
 
     def backward(self, pos, q, typ, dLdF, dLdE=None, want=("pos", "q", "sig", "eps")):
