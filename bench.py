@@ -13,8 +13,9 @@ Metric: pair interactions per second = unique in-cutoff, non-excluded pairs
 per step / seconds per step (the pair count is the kernel's own count, taken
 once before timing).  The JSON line also carries the roofline of the force
 kernel (FP32 pipe; 73 algorithmic FLOP per pair), the end-to-end number
-through host buffers, the adjoint and batched forms, clocks, and the FP64
-oracle timed on the host cores (context only).
+through host buffers, the adjoint and batched forms, the step with smooth
+PME added, clocks, and the FP64 oracle timed on the host cores (context
+only).
 
 Multi-GPU: every rank evaluates its own replica (no data-path collective);
 value = pairs of all ranks / max step time over ranks.
@@ -43,6 +44,10 @@ UNIT = "pairs/s"
 BUILD_LAUNCHES = 4
 FORCE_LAUNCHES = 3
 ADJOINT_LAUNCHES = 5
+# smooth PME adds spread, grid conversion, solve, gather (+ the FFT library's
+# forward and inverse transforms, not counted as this library's kernels)
+PME_LAUNCHES = 4
+PME_GRID, PME_ORDER = (64, 64, 64), 4  # the paper's DHFR setting
 FLOP_PER_PAIR = 73  # LJ + switch + Ewald real space, FMA = 2, MUFU = 1
 WORKLOAD = ("solvated-chain system, 23,500 atoms (2,500-atom chain + 7,000 TIP3P-shaped waters), "
             "62.2 A cubic box, rc 9 A, switch 7.5 A, Ewald alpha 0.32, 1-2/1-3 excluded, 1-4 scaled")
@@ -56,6 +61,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-extras", action="store_true", help="skip adjoint/batched/e2e/cpu legs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--pme-only", action="store_true",
+                    help="time only the step with smooth PME (for profiling its kernels)")
     return ap.parse_args()
 
 
@@ -186,6 +193,46 @@ def adjoint_leg(ctx, pos, q, typ, steps, flush, fwd_ms, npairs):
     return {"ms_per_step": ms, "pairs_per_s": npairs / (ms * 1e-3), "ratio_to_forward": ms / fwd_ms,
             "step": "cell-list rebuild + adjoint of sum|F - F_target|^2 (HVP, dL/dq, dL/dsig_ab, dL/deps_ab)",
             "gpu_launches_per_step": BUILD_LAUNCHES + ADJOINT_LAUNCHES}
+
+
+def pme_leg(s, steps, flush, dev, npairs, base_ms):
+    """The same step with smooth PME on (64^3 grid, fourth-order B-splines):
+    rebuild + short-range forces + reciprocal space + Ewald corrections,
+    replayed from a CUDA graph; and the long-range part alone."""
+    import torch
+    from paper_0902_0827_gb300 import nb
+    ctx = nb.Nonbonded(s)
+    ctx.set_pme(PME_GRID, PME_ORDER)
+    pos, q, typ = nb.concat_inputs([s], device=dev)
+    N = s.n_atoms
+    F = torch.empty((N, 3), dtype=torch.float32, device=dev)
+    E = torch.empty((1, 2), dtype=torch.float64, device=dev)
+    W = torch.empty((1, 6), dtype=torch.float64, device=dev)
+    E3 = torch.empty((3,), dtype=torch.float64, device=dev)
+    W6 = torch.empty((6,), dtype=torch.float64, device=dev)
+
+    def step():
+        ctx.build(pos)
+        ctx.forces(pos, q, typ, F=F, energy=E, virial=W)
+
+    def lr_step():
+        ctx._sync_stream()
+        nb._check(nb.lib().nb_pme_forces(ctx.h, nb._tptr(pos), nb._tptr(q), nb._tptr(F), nb._tptr(E3),
+                                         nb._tptr(W6)), "nb_pme_forces")
+
+    for _ in range(3):
+        step()
+        lr_step()
+    g = graph_of(step, dev)
+    ms = time_steps(g.replay, steps, flush)
+    gl = graph_of(lr_step, dev)
+    lr_ms = time_steps(gl.replay, steps, flush)
+    ctx.status()
+    return {"grid": list(PME_GRID), "order": PME_ORDER, "ms_per_step": ms,
+            "pairs_per_s": npairs / (ms * 1e-3), "added_ms_vs_short_range": ms - base_ms,
+            "long_range_only_ms": lr_ms,
+            "step": "cell-list rebuild + short-range forces + smooth PME + Ewald self/exclusion corrections",
+            "gpu_launches_per_step": BUILD_LAUNCHES + FORCE_LAUNCHES + PME_LAUNCHES}
 
 
 def batched_leg(steps, flush, dev):
@@ -319,6 +366,10 @@ def main():
     props = torch.cuda.get_device_properties(dev)
     n_sms = props.multi_processor_count
     s = S.solvated_chain()
+    if args.pme_only:
+        flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)
+        print(json.dumps({"pme": pme_leg(s, args.steps, flush, dev, 0, 0.0)}))
+        return 0
     ctx = nb.Nonbonded(s)
     pos, q, typ = nb.concat_inputs([s], device=dev)
     N = s.n_atoms
@@ -419,6 +470,7 @@ def main():
 
     if not args.no_extras:
         line["adjoint"] = adjoint_leg(ctx, pos, q, typ, args.steps, flush, ms, npairs)
+        line["pme"] = pme_leg(s, args.steps, flush, dev, npairs, ms)
         line["batched"] = batched_leg(args.steps, flush, dev)
         # end to end through the public API with host buffers (pinned): the
         # step's inputs (positions, charges, types) travel in one host->device

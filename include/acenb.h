@@ -259,12 +259,15 @@ nb_status nb_forces_noalloc(const nb_params *params, const float *d_pos, const f
  * Coulomb sum the topology asks for: the self energy
  * E_self = -ke alpha / sqrt(pi) sum_i q_i^2 and, per excluded pair,
  * -ke q_i q_j erf(alpha r) / r, per scaled 1-4 pair (1 - scale14_coul) times
- * that (r from the FP64 minimum image of the caller's coordinates).  Each
+ * that (FP32 pair arithmetic on the wrapped coordinates, minimum image).  Each
  * pair then contributes w_c ke q_i q_j / r in total: 0 when excluded,
  * scale14_coul when 1-4, 1 otherwise.
- * The charge grid is summed in 64-bit fixed point (scale 2^40) and forces,
- * energies and virial in the library's fixed-point sums, so reruns are
- * bit-identical; the FFTs are cuFFT's. */
+ * The charges are spread from the cell list of the last nb_build_cells (each
+ * x plane of the grid by one block, from the columns its atoms can come
+ * from), summed in fixed point (scale 2^32) in shared memory; forces,
+ * energies and virial go to the library's fixed-point sums, so reruns are
+ * bit-identical.  B-spline weights and pair terms are FP32; the FFTs are
+ * cuFFT's (FP32). */
 typedef struct {
     int32_t grid[3]; /* K1, K2, K3: grid points per box edge, order..1024 */
     int32_t order;   /* B-spline order n: 4, 6 or 8 */
@@ -282,12 +285,14 @@ typedef struct {
  * NB_ERR_OOM, NB_ERR_CUDA (also for an FFT plan failure). */
 nb_status nb_set_pme(nb_ctx *ctx, const nb_pme_params *p);
 
-/* nb_pme_forces - the long-range part alone (no cell list needed):
- *   d_pos [N, 3] coordinates (wrapped into the box in FP64), d_q [N] charges;
+/* nb_pme_forces - the long-range part alone, for the positions of the last
+ * nb_build_cells (NB_ERR_LIST_STALE is recorded otherwise):
+ *   d_pos [N, 3] coordinates, d_q [N] charges;
  *   d_F [N, 3] output: reciprocal-space forces plus the corrections' forces;
  *   d_energy [3] output (E_recip, E_self, E_excl) or NULL;
  *   d_virial [6] output (reciprocal + corrections) or NULL.
- * Asynchronous.  NB_ERR_NOT_BUILT when PME is not enabled. */
+ * Asynchronous.  NB_ERR_NOT_BUILT when PME is not enabled or no build
+ * preceded the call. */
 nb_status nb_pme_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, float *d_F, double *d_energy,
                         double *d_virial);
 

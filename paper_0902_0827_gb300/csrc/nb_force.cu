@@ -901,7 +901,7 @@ __global__ void __launch_bounds__(256) k_unpack_forces(int slot_cap, int *__rest
                                                        const int *__restrict__ clus_sys, long long *__restrict__ sys_acc,
                                                        int n_sys, double *__restrict__ energy, double *__restrict__ virial,
                                                        const long long *__restrict__ pme_f,
-                                                       const long long *__restrict__ pme_s)
+                                                       const long long *__restrict__ pme_s, double pme_self)
 {
     pdl_entry();
     const int nslots = min(slot_cap, counts[0]);
@@ -925,10 +925,10 @@ __global__ void __launch_bounds__(256) k_unpack_forces(int slot_cap, int *__rest
         if (a >= 0) {
             const long long v0 = facc[3ll * s], v1 = facc[3ll * s + 1], v2 = facc[3ll * s + 2];
             const float sc = 2.3283064365386963e-10f;  // 2^-32
-            // PME forces (caller order) join the sum before the one rounding;
-            // the atom part of the virial is the short-range forces' alone
-            const long long p0 = pme_f ? pme_f[3ll * a] : 0, p1 = pme_f ? pme_f[3ll * a + 1] : 0,
-                            p2 = pme_f ? pme_f[3ll * a + 2] : 0;
+            // PME forces (same slot order) join the sum before the one
+            // rounding; the atom part of the virial is the short-range forces' alone
+            const long long p0 = pme_f ? pme_f[3ll * s] : 0, p1 = pme_f ? pme_f[3ll * s + 1] : 0,
+                            p2 = pme_f ? pme_f[3ll * s + 2] : 0;
             F[3ll * a] = __ll2float_rn(v0 + p0) * sc;
             F[3ll * a + 1] = __ll2float_rn(v1 + p1) * sc;
             F[3ll * a + 2] = __ll2float_rn(v2 + p2) * sc;
@@ -980,7 +980,9 @@ __global__ void __launch_bounds__(256) k_unpack_forces(int slot_cap, int *__rest
         const int sy = i / kTaskVals, k = i % kTaskVals;
         long long raw = __ldcg(&sys_acc[i]);
         if (pme_s) {  // single system: reciprocal + self + pair corrections join E_Coul and W
-            if (k == 1) raw += __ldcg(&pme_s[0]) + __ldcg(&pme_s[1]) + __ldcg(&pme_s[2]);
+            if (k == 1)  // the self term from sum q^2 (scale 2^36) to the energy scale 2^32
+                raw += __ldcg(&pme_s[0]) + __ldcg(&pme_s[2]) +
+                       __double2ll_rn(pme_self * (double)__ldcg(&pme_s[1]) * (1.0 / 16.0));
             if (k >= 2) raw += __ldcg(&pme_s[1 + k]);
         }
         const double v = (double)raw * (k < 2 ? 1.0 / kFixScale : 1.0 / kVirScale);
@@ -1113,12 +1115,13 @@ cudaError_t launch_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, con
         double *en = debug_pairs ? nullptr : d_energy;
         double *vi = debug_pairs ? nullptr : d_virial;
         const long long *pf = pme ? pme_forces_acc(ctx) : nullptr, *ps = pme ? pme_sums_acc(ctx) : nullptr;
+        const double pself = pme ? pme_self_coef(ctx) : 0.0;
         if (virial)
             launch_pdl(k_unpack_forces<true>, dim3(blocks), dim3(tb), 0, ctx->stream, S, d.counts, d.perm, d.facc, d_F,
-                       d.xyzq, d.clus_sys, d.sys_acc, ctx->n_sys, en, vi, pf, ps);
+                       d.xyzq, d.clus_sys, d.sys_acc, ctx->n_sys, en, vi, pf, ps, pself);
         else
             launch_pdl(k_unpack_forces<false>, dim3(blocks), dim3(tb), 0, ctx->stream, S, d.counts, d.perm, d.facc,
-                       d_F, d.xyzq, d.clus_sys, d.sys_acc, ctx->n_sys, en, vi, pf, ps);
+                       d_F, d.xyzq, d.clus_sys, d.sys_acc, ctx->n_sys, en, vi, pf, ps, pself);
     }
     return cudaGetLastError();
 }

@@ -214,6 +214,7 @@ cudaError_t launch_pme(nb_ctx *ctx, const float *d_pos, const float *d_q);
 void pme_free(nb_ctx *ctx);
 const long long *pme_forces_acc(const nb_ctx *ctx);
 const long long *pme_sums_acc(const nb_ctx *ctx);
+double pme_self_coef(const nb_ctx *ctx);  // -ke alpha / sqrt(pi), multiplies sum q^2
 cudaError_t launch_backward(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type,
                             const float *d_dLdF, const double *d_dLdE, float *d_dLdpos, float *d_dLdq,
                             double *d_dsig, double *d_deps);
