@@ -12,6 +12,7 @@ cites the passage it follows.
 
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -77,6 +78,8 @@ def lib():
             L.orc_grid_dims.restype = None
             L.orc_num_threads.argtypes = []
             L.orc_num_threads.restype = I
+            L.orc_set_table.argtypes = [I]
+            L.orc_set_table.restype = None
             L.orc_ewald_recip.argtypes = [I64, P, P, P, D, D, I, I, I, P, P, P]
             L.orc_ewald_recip.restype = I
             L.orc_ewald_corrections.argtypes = [I64, P, P, P, D, D, I64, P, I64, P, D, P, P, P]
@@ -95,6 +98,18 @@ def _c(a, dtype):
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+@contextlib.contextmanager
+def tabulated(n: int):
+    """Within the block, the forward functions (forces, forces_subset)
+    evaluate the radial functions by linear interpolation of n-interval
+    tables on [0, rc] instead of directly (see nb_oracle.c, tab_t)."""
+    lib().orc_set_table(int(n))
+    try:
+        yield
+    finally:
+        lib().orc_set_table(0)
 
 
 def combine_lb(sigma, epsilon):

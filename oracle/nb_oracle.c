@@ -119,6 +119,24 @@ static void topo_free(topo_t *t) { free(t->start); free(t->partner); free(t->kin
 /* ------------------------------------------------------------------ */
 /* Parameters.                                                         */
 /* ------------------------------------------------------------------ */
+/* Tabulated radial functions (section "Molecular dynamics on the GPU": the
+ * radial parts of the van der Waals and electrostatic terms linearly
+ * interpolated from lookup tables; n = 4096 in the paper's error figure).
+ * Six functions of r: E12 = S r^-12, E6 = S r^-6, Ec = erfc(alpha r)/r (1/r
+ * for alpha = 0) and their -r d/dr: F12, F6, Fc.  Table point k sits at
+ * r_k = k rc / n (k = 0..n), evaluated at max(r_k, TAB_RFLOOR); the table
+ * holds, per interval k < n, the FP32 rounding of f(r_k) and of
+ * f(r_{k+1}) - f(r_k).  A distance r uses interval k = min(floor(r n / rc),
+ * n - 1), t = r n / rc - k and f = T_k + t D_k. */
+#define TAB_RFLOOR 0.5
+static int g_tab_n = 0; /* 0: direct evaluation (set by orc_set_table) */
+
+typedef struct {
+    int n;
+    double inv_h;
+    float *T, *D; /* [n][6] values and differences: E12, E6, Ec, F12, F6, Fc */
+} tab_t;
+
 typedef struct {
     float box[3];
     float rc_f, rc2_f;           /* FP32 cutoff and its FP32 square (membership) */
@@ -127,7 +145,10 @@ typedef struct {
     int switched;
     int ntypes;
     const double *A, *B;         /* [T*T] A_ab = 4 eps sig^12, B_ab = 4 eps sig^6 */
+    tab_t *tab;                  /* tabulated radial functions, or NULL */
 } prm_t;
+
+void orc_set_table(int n) { g_tab_n = n; }
 
 static void prm_init(prm_t *p, const float *box, float rc, float rs, float alpha, float ke,
                      float s14_lj, float s14_c, int ntypes, const double *A, const double *B)
@@ -139,6 +160,57 @@ static void prm_init(prm_t *p, const float *box, float rc, float rs, float alpha
     p->s14_lj = s14_lj; p->s14_c = s14_c;
     p->switched = rs < rc;
     p->ntypes = ntypes; p->A = A; p->B = B;
+    p->tab = NULL;
+}
+
+static void switch_fn(const prm_t *p, double r, double *S, double *S1, double *S2);
+
+/* The six radial functions at r (see tab_t). */
+static void radial_fns(const prm_t *p, double r, double f[6])
+{
+    double S, S1, S2;
+    switch_fn(p, r, &S, &S1, &S2);
+    double ir = 1.0 / r, ir6 = ir * ir * ir * ir * ir * ir, ir12 = ir6 * ir6;
+    f[0] = S * ir12;
+    f[1] = S * ir6;
+    f[3] = 12.0 * S * ir12 - r * S1 * ir12;
+    f[4] = 6.0 * S * ir6 - r * S1 * ir6;
+    if (p->alpha > 0.0) {
+        f[2] = erfc(p->alpha * r) * ir;
+        f[5] = f[2] + 2.0 * p->alpha / sqrt(M_PI) * exp(-p->alpha * p->alpha * r * r);
+    } else {
+        f[2] = ir;
+        f[5] = ir;
+    }
+}
+
+static void tab_build(prm_t *p, int n)
+{
+    tab_t *t = (tab_t *)malloc(sizeof(tab_t));
+    t->n = n;
+    t->inv_h = (double)n / p->rc;
+    t->T = (float *)malloc(sizeof(float) * 6 * (size_t)n);
+    t->D = (float *)malloc(sizeof(float) * 6 * (size_t)n);
+    double f0[6], f1[6];
+    for (int k = 0; k < n; ++k) {
+        double r0 = (double)k * p->rc / n, r1 = (double)(k + 1) * p->rc / n;
+        radial_fns(p, r0 > TAB_RFLOOR ? r0 : TAB_RFLOOR, f0);
+        radial_fns(p, r1 > TAB_RFLOOR ? r1 : TAB_RFLOOR, f1);
+        for (int c = 0; c < 6; ++c) {
+            t->T[6 * k + c] = (float)f0[c];
+            t->D[6 * k + c] = (float)(f1[c] - f0[c]);
+        }
+    }
+    p->tab = t;
+}
+
+static void prm_free(prm_t *p)
+{
+    if (!p->tab) return;
+    free(p->tab->T);
+    free(p->tab->D);
+    free(p->tab);
+    p->tab = NULL;
 }
 
 /* Lorentz-Berthelot combination on the type-pair table (CHARMM rule). */
@@ -232,7 +304,20 @@ static void accum_pair(const prm_t *p, const double *d, double r, double A, doub
                        double wlj, double wc, double *Fi, double *Fj, double *E, double *W)
 {
     pterm_t t;
-    pair_terms(p, r, A, B, qq, wlj, wc, &t);
+    if (p->tab) {
+        /* interpolated radial functions; du = dU/dr = -(-r dU/dr) / r */
+        const tab_t *tb = p->tab;
+        double x = r * tb->inv_h;
+        int k = (int)floor(x);
+        if (k > tb->n - 1) k = tb->n - 1;
+        double u = x - (double)k, f[6];
+        for (int c = 0; c < 6; ++c) f[c] = (double)tb->T[6 * k + c] + u * (double)tb->D[6 * k + c];
+        t.e_lj = wlj * (A * f[0] - B * f[1]);
+        t.e_c = qq * wc * p->ke * f[2];
+        t.du = -(wlj * (A * f[3] - B * f[4]) + qq * wc * p->ke * f[5]) / r;
+    } else {
+        pair_terms(p, r, A, B, qq, wlj, wc, &t);
+    }
     E[2] += fabs(t.e_lj); E[3] += fabs(t.e_c);
     double h = t.du / r; /* F_i = h d, F_j = -h d */
     for (int a = 0; a < 3; ++a) { Fi[a] += h * d[a]; if (Fj) Fj[a] -= h * d[a]; }
@@ -264,6 +349,7 @@ int64_t orc_forces_allpairs(int64_t n, const float *pos, const float *q, const i
 {
     prm_t p;
     prm_init(&p, box, rc, rs, alpha, ke, s14_lj, s14_c, ntypes, A, B);
+    if (g_tab_n > 0) tab_build(&p, g_tab_n);
     topo_t t;
     topo_build(&t, n, nex, ex, n14, p14);
     memset(F, 0, sizeof(double) * 3 * (size_t)n);
@@ -285,6 +371,7 @@ int64_t orc_forces_allpairs(int64_t n, const float *pos, const float *q, const i
                        F + 3 * i, F + 3 * j, E, W);
             ++npairs;
         }
+    prm_free(&p);
     topo_free(&t);
     return npairs;
 }
@@ -391,6 +478,7 @@ int64_t orc_forces_cells(int64_t n, const float *pos, const float *q, const int3
 {
     prm_t p;
     prm_init(&p, box, rc, rs, alpha, ke, s14_lj, s14_c, ntypes, A, B);
+    if (g_tab_n > 0) tab_build(&p, g_tab_n);
     topo_t t;
     topo_build(&t, n, nex, ex, n14, p14);
     grid_t g;
@@ -410,6 +498,7 @@ int64_t orc_forces_cells(int64_t n, const float *pos, const float *q, const int3
     }
     free(Ep); free(cnt);
     if (have_grid) grid_free(&g);
+    prm_free(&p);
     topo_free(&t);
     return tot / 2;
 }
@@ -425,6 +514,7 @@ void orc_forces_subset(int64_t n, const float *pos, const float *q, const int32_
 {
     prm_t p;
     prm_init(&p, box, rc, rs, alpha, ke, s14_lj, s14_c, ntypes, A, B);
+    if (g_tab_n > 0) tab_build(&p, g_tab_n);
     topo_t t;
     topo_build(&t, n, nex, ex, n14, p14);
 #pragma omp parallel for schedule(dynamic, 1)
@@ -432,6 +522,7 @@ void orc_forces_subset(int64_t n, const float *pos, const float *q, const int32_
         double W[6];
         npair[k] = atom_sum(&p, &t, NULL, n, pos, q, type, atoms[k], F + 3 * k, E4 + 4 * k, W);
     }
+    prm_free(&p);
     topo_free(&t);
 }
 
