@@ -14,7 +14,7 @@ per step / seconds per step (the pair count is the kernel's own count, taken
 once before timing).  The JSON line also carries the roofline of the force
 kernel (FP32 pipe; 73 algorithmic FLOP per pair), the end-to-end number
 through host buffers, the adjoint and batched forms, the step with smooth
-PME added, clocks, and the FP64 oracle timed on the host cores (context
+PME added, the step with tabulated radial functions, clocks, and the FP64 oracle timed on the host cores (context
 only).
 
 Multi-GPU: every rank evaluates its own replica (no data-path collective);
@@ -48,6 +48,7 @@ ADJOINT_LAUNCHES = 5
 # forward and inverse transforms, not counted as this library's kernels)
 PME_LAUNCHES = 4
 PME_GRID, PME_ORDER = (64, 64, 64), 4  # the paper's DHFR setting
+TABLE_INTERVALS = 4096  # the paper's lookup-table size
 FLOP_PER_PAIR = 73  # LJ + switch + Ewald real space, FMA = 2, MUFU = 1
 WORKLOAD = ("solvated-chain system, 23,500 atoms (2,500-atom chain + 7,000 TIP3P-shaped waters), "
             "62.2 A cubic box, rc 9 A, switch 7.5 A, Ewald alpha 0.32, 1-2/1-3 excluded, 1-4 scaled")
@@ -63,6 +64,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--pme-only", action="store_true",
                     help="time only the step with smooth PME (for profiling its kernels)")
+    ap.add_argument("--tables-only", action="store_true",
+                    help="time only the step with tabulated radial functions (for profiling)")
     return ap.parse_args()
 
 
@@ -235,6 +238,41 @@ def pme_leg(s, steps, flush, dev, npairs, base_ms):
             "gpu_launches_per_step": BUILD_LAUNCHES + FORCE_LAUNCHES + PME_LAUNCHES}
 
 
+def tables_leg(s, steps, flush, dev, npairs, base_ms, base_fo_ms):
+    """The same step with the radial functions interpolated from 4096-interval
+    tables (the paper's lookup-table variant) instead of evaluated directly:
+    rebuild + forces, and the force evaluation alone."""
+    import torch
+    from paper_0902_0827_gb300 import nb
+    ctx = nb.Nonbonded(s)
+    ctx.set_tables(TABLE_INTERVALS)
+    pos, q, typ = nb.concat_inputs([s], device=dev)
+    N = s.n_atoms
+    F = torch.empty((N, 3), dtype=torch.float32, device=dev)
+    E = torch.empty((1, 2), dtype=torch.float64, device=dev)
+    W = torch.empty((1, 6), dtype=torch.float64, device=dev)
+
+    def step():
+        ctx.build(pos)
+        ctx.forces(pos, q, typ, F=F, energy=E, virial=W)
+
+    def fstep():
+        ctx.forces(pos, q, typ, F=F, energy=E, virial=W)
+
+    for _ in range(3):
+        step()
+    g = graph_of(step, dev)
+    ms = time_steps(g.replay, steps, flush)
+    ctx.build(pos)
+    gf = graph_of(fstep, dev)
+    fo_ms = time_steps(gf.replay, steps, flush)
+    ctx.status()
+    return {"intervals": TABLE_INTERVALS, "ms_per_step": ms, "pairs_per_s": npairs / (ms * 1e-3),
+            "force_only_ms": fo_ms, "speedup_vs_direct": base_ms / ms, "force_only_speedup_vs_direct": base_fo_ms / fo_ms,
+            "step": "cell-list rebuild + forces with tabulated radial functions (linear interpolation)",
+            "gpu_launches_per_step": BUILD_LAUNCHES + FORCE_LAUNCHES}
+
+
 def batched_leg(steps, flush, dev):
     """64 water boxes (log-uniform 500..20,000 atoms): one autotuned,
     graph-captured rebuild + force step of the whole batch vs 64 sequential
@@ -366,9 +404,12 @@ def main():
     props = torch.cuda.get_device_properties(dev)
     n_sms = props.multi_processor_count
     s = S.solvated_chain()
-    if args.pme_only:
+    if args.pme_only or args.tables_only:
         flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)
-        print(json.dumps({"pme": pme_leg(s, args.steps, flush, dev, 0, 0.0)}))
+        if args.pme_only:
+            print(json.dumps({"pme": pme_leg(s, args.steps, flush, dev, 0, 0.0)}))
+        else:
+            print(json.dumps({"tables": tables_leg(s, args.steps, flush, dev, 0, float("nan"), float("nan"))}))
         return 0
     ctx = nb.Nonbonded(s)
     pos, q, typ = nb.concat_inputs([s], device=dev)
@@ -471,6 +512,7 @@ def main():
     if not args.no_extras:
         line["adjoint"] = adjoint_leg(ctx, pos, q, typ, args.steps, flush, ms, npairs)
         line["pme"] = pme_leg(s, args.steps, flush, dev, npairs, ms)
+        line["tables"] = tables_leg(s, args.steps, flush, dev, npairs, ms, fo_ms)
         line["batched"] = batched_leg(args.steps, flush, dev)
         # end to end through the public API with host buffers (pinned): the
         # step's inputs (positions, charges, types) travel in one host->device

@@ -143,8 +143,9 @@ nb_status nb_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, const int
                     float *d_F, double *d_energy, double *d_virial);
 
 /* nb_backward - adjoint of L = sum_i G_i . F_i + sum_s gE_s . E_s, the pair
- * list recomputed from the last build (short-range terms; a context with
- * smooth PME enabled returns NB_ERR_UNSUPPORTED).
+ * list recomputed from the last build (short-range terms, direct radial
+ * functions; a context with smooth PME or tables enabled returns
+ * NB_ERR_UNSUPPORTED).
  *   d_dLdF      [N, 3]      G;  d_dLdE [n_sys*2] gE (LJ, Coulomb) or NULL (= 0);
  *   d_dLdpos    [N, 3]      dL/dx = -H G - (gE weighted) F   (Hessian-vector product);
  *   d_dLdq      [N]         dL/dq;
@@ -246,6 +247,24 @@ nb_status nb_get_profile(nb_ctx *ctx, double *force_ms, int64_t *launches);
 nb_status nb_forces_noalloc(const nb_params *params, const float *d_pos, const float *d_q,
                             const int32_t *d_type, float *d_F, double *d_energy, double *d_virial,
                             void *cuda_stream);
+
+/* nb_set_tables - evaluate the radial functions of the forward kernel by
+ * linear interpolation of lookup tables instead of directly (section
+ * "Molecular dynamics on the GPU": the texture units interpolate the radial
+ * parts of the van der Waals and electrostatic terms from tables; its error
+ * figure uses n = 4096 points).  n_intervals > 0 tabulates, on [0, rc] with
+ * r_k = k rc / n, the six functions E12 = S r^-12, E6 = S r^-6,
+ * Ec = erfc(alpha r)/r (1/r without Ewald) and F = -r dE/dr of each, as the
+ * FP32 values at r_k (at max(r_k, 0.5 A)) and the FP32 differences to
+ * r_{k+1}; a pair at distance r uses interval k = floor(r n / rc) (at most
+ * n - 1) and f = T_k + t D_k with t = r n / rc - k, in FP32.  Then
+ * U_LJ = w_lj (A E12 - B E6) and U_C = w_c ke q_i q_j Ec.  n_intervals = 0
+ * restores direct evaluation.  The pair set is unchanged.  Allocates
+ * 48 n bytes, synchronises the stream, not capturable; applies to nb_forces
+ * (nb_backward returns NB_ERR_UNSUPPORTED while tables are on).
+ * Errors: NB_ERR_INVALID_ARG (n_intervals not 0 and outside 16..65536),
+ * NB_ERR_OOM, NB_ERR_CUDA. */
+nb_status nb_set_tables(nb_ctx *ctx, int32_t n_intervals);
 
 /* Smooth particle-mesh Ewald (section "Molecular dynamics on the GPU": the
  * long-range electrostatics by PME with the FFT library; section

@@ -36,7 +36,7 @@ void free_all(nb_ctx *c)
     void *ptrs[] = {d.sys, d.atom_sys, d.atom_col, d.wpos, d.part_orig, d.col_sys, d.col_count, d.col_fill,
                     d.col_slot, d.stage, d.xyzq, d.tslot, d.perm, d.inv, d.bb,
                     d.clus_sys, d.sys_acc, d.facc, d.gacc, d.list, d.list_n, d.pslot, d.zbin, d.tab_grad, d.counts, d.status, d.lj_tab,
-                    d.dbg_n, d.dbg_ij, d.scratch_f, d.scratch_g, d.lj_d, d.gslot, d.eps_type};
+                    d.dbg_n, d.dbg_ij, d.scratch_f, d.scratch_g, d.lj_d, d.gslot, d.eps_type, d.rtab};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     d = DevBuffers();
@@ -288,10 +288,75 @@ nb_status nb_backward(nb_ctx *ctx, const float *d_pos, const float *d_q, const i
 {
     if (!ctx || !d_pos || !d_q || !d_type || !d_dLdF) return NB_ERR_INVALID_ARG;
     if (!ctx->built) return NB_ERR_NOT_BUILT;
-    if (ctx->pme) return NB_ERR_UNSUPPORTED;
+    if (ctx->pme || ctx->tab_n > 0) return NB_ERR_UNSUPPORTED;
     cudaError_t e = launch_backward(ctx, d_pos, d_q, d_type, d_dLdF, d_dLdE, d_dLdpos, d_dLdq, d_dLdsig_tab,
                                     d_dLdeps_tab);
     return e == cudaSuccess ? NB_OK : NB_ERR_CUDA;
+}
+
+// The six radial functions at r: E12 = S r^-12, E6 = S r^-6, Ec = erfc(alpha r)/r
+// (1/r without Ewald) and F = -r dE/dr of each (FP64, host).
+static void radial_functions(const PairParams &pp, double rc, double rs, double alpha, double r, double f[6])
+{
+    double S = 1.0, rS1 = 0.0;  // switch and r dS/dr
+    if (pp.switched && r > rs) {
+        const double rc2 = rc * rc, rs2 = rs * rs, r2 = r * r, D = (rc2 - rs2) * (rc2 - rs2) * (rc2 - rs2);
+        S = (rc2 - r2) * (rc2 - r2) * (rc2 + 2.0 * r2 - 3.0 * rs2) / D;
+        rS1 = 12.0 * r2 * (rc2 - r2) * (rs2 - r2) / D;
+    }
+    const double ir = 1.0 / r, ir6 = ir * ir * ir * ir * ir * ir, ir12 = ir6 * ir6;
+    f[0] = S * ir12;
+    f[1] = S * ir6;
+    f[3] = 12.0 * S * ir12 - rS1 * ir12;
+    f[4] = 6.0 * S * ir6 - rS1 * ir6;
+    if (alpha > 0.0) {
+        f[2] = std::erfc(alpha * r) * ir;
+        f[5] = f[2] + 2.0 * alpha / std::sqrt(M_PI) * std::exp(-alpha * alpha * r * r);
+    } else {
+        f[2] = ir;
+        f[5] = ir;
+    }
+}
+
+nb_status nb_set_tables(nb_ctx *ctx, int32_t n_intervals)
+{
+    if (!ctx) return NB_ERR_INVALID_ARG;
+    if (n_intervals != 0 && (n_intervals < 16 || n_intervals > 65536)) return NB_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return NB_ERR_CUDA;
+    cudaFree(ctx->d.rtab);
+    ctx->d.rtab = nullptr;
+    ctx->tab_n = 0;
+    ctx->pp.tab_n = 0;
+    if (n_intervals == 0) return NB_OK;
+    const int n = n_intervals;
+    const double rc = (double)ctx->pp.rc, rs = (double)ctx->pp.rs, alpha = (double)ctx->pp.alpha;
+    const double rfloor = 0.5;  // below it every point repeats the value at 0.5 A (never reached)
+    std::vector<float4> h((size_t)3 * n);
+    double f0[6], f1[6];
+    for (int k = 0; k < n; ++k) {
+        const double r0 = (double)k * rc / n, r1 = (double)(k + 1) * rc / n;
+        radial_functions(ctx->pp, rc, rs, alpha, std::max(r0, rfloor), f0);
+        radial_functions(ctx->pp, rc, rs, alpha, std::max(r1, rfloor), f1);
+        float v[6], dv[6];
+        for (int c = 0; c < 6; ++c) {
+            v[c] = (float)f0[c];
+            dv[c] = (float)(f1[c] - f0[c]);
+        }
+        h[3 * k] = make_float4(v[0], dv[0], v[1], dv[1]);
+        h[3 * k + 1] = make_float4(v[2], dv[2], v[3], dv[3]);
+        h[3 * k + 2] = make_float4(v[4], dv[4], v[5], dv[5]);
+    }
+    float4 *dt = nullptr;
+    if (cudaMalloc(&dt, sizeof(float4) * h.size()) != cudaSuccess) return NB_ERR_OOM;
+    if (cudaMemcpy(dt, h.data(), sizeof(float4) * h.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(dt);
+        return NB_ERR_CUDA;
+    }
+    ctx->d.rtab = dt;
+    ctx->tab_n = n;
+    ctx->pp.tab_n = n;
+    ctx->pp.tab_inv_h = (float)((double)n / rc);
+    return NB_OK;
 }
 
 nb_status nb_set_lj_params(nb_ctx *ctx, const float *h_sigma, const float *h_epsilon, const float *h_sigma_tab,

@@ -57,6 +57,7 @@ struct ForceArgs {
     int scap;
     int K;
     const float2 *lj_tab;
+    const float4 *rtab;       // [n*3] tabulated radial functions, or null
     float *F;
     long long *facc;          // [S*3] fixed-point forces in sorted order (forward)
     long long *sys_acc;
@@ -353,15 +354,21 @@ __device__ __forceinline__ void eval_pair_adj(const PairParams &P, const ForceSm
 
 // One candidate pair: d = x_j - x_i (exact-shift image), r2 its FP32 squared
 // length; the arithmetic is done for every candidate and masked by `in`.
-template <bool EWALD>
-__device__ __forceinline__ void eval_pair(const PairParams &P, const float2 *__restrict__ lj, int ti_row, float qi,
-                                          bool in, float dx, float dy, float dz, float r2, float qj, int tj,
-                                          bool is14, Acc &acc, float &fjx, float &fjy, float &fjz)
+// RAD: radial functions evaluated directly with plain Coulomb (0) or Ewald
+// (1), or interpolated from the tables (2).
+template <int RAD>
+__device__ __forceinline__ void eval_pair(const PairParams &P, const float2 *__restrict__ lj,
+                                          const float4 *__restrict__ rtab, int ti_row, float qi, bool in, float dx,
+                                          float dy, float dz, float r2, float qj, int tj, bool is14, Acc &acc,
+                                          float &fjx, float &fjy, float &fjz)
 {
     const float rinv = fast_rsqrt(r2);
     const float2 ab = lj[ti_row + tj];
     float elj, frlj, ec, frc;
-    pair_radial<EWALD, true>(P, r2, rinv, ab.x, ab.y, qi * qj, elj, frlj, ec, frc);
+    if constexpr (RAD == 2)
+        pair_radial_tab(P, rtab, r2, rinv, ab.x, ab.y, qi * qj, elj, frlj, ec, frc);
+    else
+        pair_radial<RAD == 1, true>(P, r2, rinv, ab.x, ab.y, qi * qj, elj, frlj, ec, frc);
     const float wlj = is14 ? P.s14_lj : 1.0f;
     const float wc = is14 ? P.s14_c : 1.0f;
     // F_i = U'(r) d / r = -fs d with fs = -U'(r) / r
@@ -414,7 +421,7 @@ struct IAtom {
 // One ring item: staged entry e (bits 7..15), i-side image per axis (bits
 // 4..6), atom k (bits 1..3), 1-4 flag (bit 0).  The displacement is
 // recomputed with the same operations as the membership test (same value).
-template <bool ADJ, bool EWALD, bool VIRIAL, bool DEBUG, class AccT>
+template <bool ADJ, int RAD, bool VIRIAL, bool DEBUG, class AccT>
 __device__ __forceinline__ void eval_item(const ForceArgs &A, const ForceSmem &S, float Lx, float Ly, float Lz,
                                           const IAtom &ia, uint32_t item, bool active, AccT &acc)
 {
@@ -438,7 +445,7 @@ __device__ __forceinline__ void eval_item(const ForceArgs &A, const ForceSmem &S
     }
     if constexpr (ADJ) {
         float jx, jy, jz, jq;
-        eval_pair_adj<EWALD>(A.P, S, ia.ti_row, ia.qi, ia.gix, ia.giy, ia.giz, ia.gE_lj, ia.gE_c, active, dx, dy, dz,
+        eval_pair_adj<RAD == 1>(A.P, S, ia.ti_row, ia.qi, ia.gix, ia.giy, ia.giz, ia.gE_lj, ia.gE_c, active, dx, dy, dz,
                              active ? r2 : 1.0f, pj.w, tj, S.gj[idx], (item & 1u) != 0u, A.status, acc, jx, jy, jz,
                              jq);
         if (active) {
@@ -450,8 +457,8 @@ __device__ __forceinline__ void eval_item(const ForceArgs &A, const ForceSmem &S
         }
     } else {
         float fjx, fjy, fjz;
-        eval_pair<EWALD>(A.P, S.lj, ia.ti_row, ia.qi, active, dx, dy, dz, active ? r2 : 1.0f, pj.w, tj,
-                                (item & 1u) != 0u, acc, fjx, fjy, fjz);
+        eval_pair<RAD>(A.P, S.lj, A.rtab, ia.ti_row, ia.qi, active, dx, dy, dz, active ? r2 : 1.0f, pj.w, tj,
+                       (item & 1u) != 0u, acc, fjx, fjy, fjz);
         if (active) {
             const int js = A.scap * kCluster;
             add_jf<3>(A, S, A.facc, e, k, idx, 0, fjx);
@@ -587,7 +594,7 @@ __device__ __forceinline__ void flush_jf(const ForceArgs &A, const ForceSmem &S,
     }
 }
 
-template <bool ADJ, bool EWALD, bool VIRIAL, bool DEBUG>
+template <bool ADJ, int RAD, bool VIRIAL, bool DEBUG>
 __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
 {
     pdl_entry();
@@ -754,7 +761,7 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
                 tail += total;
                 __syncwarp();
                 while (tail - head >= 32) {
-                    eval_item<ADJ, EWALD, VIRIAL, DEBUG>(A, Sc, Lx, Ly, Lz, ia, S.ring[(head + lane) & (kRing - 1)],
+                    eval_item<ADJ, RAD, VIRIAL, DEBUG>(A, Sc, Lx, Ly, Lz, ia, S.ring[(head + lane) & (kRing - 1)],
                                                          true, acc);
                     head += 32;
                 }
@@ -763,7 +770,7 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
             if (tail > head) {  // partial step before the staged data is replaced
                 const int n = tail - head;
                 const uint32_t item = lane < n ? S.ring[(head + lane) & (kRing - 1)] : 0u;
-                eval_item<ADJ, EWALD, VIRIAL, DEBUG>(A, Sc, Lx, Ly, Lz, ia, item, lane < n, acc);
+                eval_item<ADJ, RAD, VIRIAL, DEBUG>(A, Sc, Lx, Ly, Lz, ia, item, lane < n, acc);
             }
             __syncwarp();
         }
@@ -1014,23 +1021,23 @@ __global__ void k_unpack_adjoint(int slot_cap, const int *__restrict__ counts, c
     if (dq) dq[a] = __ll2float_rn(gacc[4ll * s + 3]) * sc;
 }
 
-template <bool ADJ, bool EWALD, bool VIRIAL, bool DEBUG>
+template <bool ADJ, int RAD, bool VIRIAL, bool DEBUG>
 static void launch_force_t(nb_ctx *ctx, const ForceArgs &A)
 {
     const int nw = kCluster;
     const size_t smem = force_smem_bytes(A.P.n_types, A.scap, nw, ADJ);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_force<ADJ, EWALD, VIRIAL, DEBUG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_force<ADJ, RAD, VIRIAL, DEBUG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              220 * 1024);
         attr_set = true;
     }
     // persistent grid: never more blocks than can be resident at once
     int resident = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_force<ADJ, EWALD, VIRIAL, DEBUG>, nw * 32, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_force<ADJ, RAD, VIRIAL, DEBUG>, nw * 32, smem);
     const int per_sm = std::max(1, std::min(ctx->tune.blocks_per_sm, resident));
     const int grid = ctx->num_sms * per_sm;
-    launch_pdl(k_force<ADJ, EWALD, VIRIAL, DEBUG>, dim3(grid), dim3(nw * 32), smem, ctx->stream, A);
+    launch_pdl(k_force<ADJ, RAD, VIRIAL, DEBUG>, dim3(grid), dim3(nw * 32), smem, ctx->stream, A);
 }
 
 static ForceArgs make_args(nb_ctx *ctx)
@@ -1052,6 +1059,7 @@ static ForceArgs make_args(nb_ctx *ctx)
     A.scap = ctx->stage_cap;
     A.K = ctx->K;
     A.lj_tab = d.lj_tab;
+    A.rtab = d.rtab;
     A.sys_acc = d.sys_acc;
     A.status = d.status;
     A.dbg_n = d.dbg_n;
@@ -1089,15 +1097,18 @@ cudaError_t launch_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, con
     const bool virial = d_virial != nullptr;
     const bool prof = ctx->profiling && ctx->prof_n < (int)ctx->prof_ev.size() / 2;
     if (prof) cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n], ctx->stream);
-    if (debug_pairs) {
-        if (ewald) launch_force_t<false, true, false, true>(ctx, A);
-        else launch_force_t<false, false, false, true>(ctx, A);
+    if (debug_pairs) {  // the pair set does not depend on the radial functions
+        if (ewald) launch_force_t<false, 1, false, true>(ctx, A);
+        else launch_force_t<false, 0, false, true>(ctx, A);
+    } else if (ctx->tab_n > 0) {
+        if (virial) launch_force_t<false, 2, true, false>(ctx, A);
+        else launch_force_t<false, 2, false, false>(ctx, A);
     } else if (ewald) {
-        if (virial) launch_force_t<false, true, true, false>(ctx, A);
-        else launch_force_t<false, true, false, false>(ctx, A);
+        if (virial) launch_force_t<false, 1, true, false>(ctx, A);
+        else launch_force_t<false, 1, false, false>(ctx, A);
     } else {
-        if (virial) launch_force_t<false, false, true, false>(ctx, A);
-        else launch_force_t<false, false, false, false>(ctx, A);
+        if (virial) launch_force_t<false, 0, true, false>(ctx, A);
+        else launch_force_t<false, 0, false, false>(ctx, A);
     }
     if (prof) {
         cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n + 1], ctx->stream);
@@ -1145,8 +1156,8 @@ cudaError_t launch_adjoint_tile(nb_ctx *ctx, const double *d_dLdE, float *d_dpos
     A.tab_acc = d.tab_grad;
     A.gacc = d.gacc;
     A.scap = std::min(ctx->stage_cap, kAdjStage);
-    if (ctx->pp.ewald) launch_force_t<true, true, false, false>(ctx, A);
-    else launch_force_t<true, false, false, false>(ctx, A);
+    if (ctx->pp.ewald) launch_force_t<true, 1, false, false>(ctx, A);
+    else launch_force_t<true, 0, false, false>(ctx, A);
     const int tb = 256;
     const int S = (int)ctx->slot_cap;
     return launch_pdl(k_unpack_adjoint, dim3((S + tb - 1) / tb), dim3(tb), 0, ctx->stream, S, d.counts, d.perm,

@@ -162,6 +162,7 @@ inline nb_status init_pair_params(const nb_params &P0, PairParams &pp)
     memset(&pp, 0, sizeof(pp));
     const float rc = P0.cutoff, rs = P0.switch_dist;
     pp.rc = rc;
+    pp.rs = rs;
     pp.rc2 = rc * rc;
     pp.switched = rs < rc;
     if (pp.switched) {

@@ -86,6 +86,9 @@ struct PairParams {
     int switched;        // rs < rc
     int ewald;           // alpha > 0
     float erfc_c[kErfcDeg + 1]; // erfcx(x) ~ sum c_k t^k on [0, alpha rc]
+    float rs;            // FP32 switch distance
+    float tab_inv_h;     // n / rc (FP32) of the radial-function tables
+    int tab_n;           // intervals of the tables (0: direct evaluation)
 };
 
 struct DevBuffers {
@@ -117,6 +120,7 @@ struct DevBuffers {
     int *status = nullptr;           // [1]
     float2 *lj_tab = nullptr;        // [T*T] (A, B)
     float4 *lj_d = nullptr;          // [T*T] 48 eps sig^11, 24 eps sig^5, 4 sig^12, 4 sig^6
+    float4 *rtab = nullptr;          // [tab_n*3] tabulated radial functions (nb_set_tables)
     float4 *gslot = nullptr;         // [S] adjoint input dL/dF in sorted order
     float *eps_type = nullptr;       // [T] per-type epsilon (Lorentz-Berthelot chain)
     long long *dbg_n = nullptr;      // [2] debug pair counters
@@ -138,6 +142,7 @@ struct nb_ctx {
     int comb_rule = 0;
     int stage_cap = 96;            // list entries staged per block pass
     int list_cap = 512;            // entries per half list of a cluster
+    int tab_n = 0;                 // radial-function table intervals (0: direct evaluation)
     int64_t zb_total = 0;          // entries of the z-bin index
     int smem_optin = 0;            // device opt-in shared memory per block
     cudaStream_t stream = nullptr;

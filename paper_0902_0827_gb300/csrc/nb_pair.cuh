@@ -92,4 +92,30 @@ __device__ __forceinline__ void pair_radial(const PairParams &P, float r2, float
     }
 }
 
+// Radial part by linear interpolation of the tables (section "Molecular
+// dynamics on the GPU": radial components of the van der Waals and
+// electrostatic terms interpolated from lookup tables).  Interval k of
+// [0, rc] (n intervals, r_k = k rc / n) holds three float4:
+// (E12, dE12, E6, dE6), (Ec, dEc, F12, dF12), (F6, dF6, Fc, dFc) -- the
+// values at r_k of E12 = S r^-12, E6 = S r^-6, Ec = erfc(alpha r)/r and of
+// F = -r dE/dr for each, with the differences to r_{k+1}.  Same outputs as
+// pair_radial.  The interpolation is FP32 (one FMA per function) on the
+// caller's r = r2 rsqrt(r2).
+__device__ __forceinline__ void pair_radial_tab(const PairParams &P, const float4 *__restrict__ tab, float r2,
+                                                float rinv, float A, float B, float qq, float &elj, float &frlj,
+                                                float &ec, float &frc)
+{
+    const float x = r2 * rinv * P.tab_inv_h;
+    const int k = max(0, min((int)x, P.tab_n - 1));
+    const float t = x - (float)k;
+    const float4 a = __ldg(&tab[3 * k]), b = __ldg(&tab[3 * k + 1]), c = __ldg(&tab[3 * k + 2]);
+    const float e12 = fmaf(t, a.y, a.x), e6 = fmaf(t, a.w, a.z);
+    const float ecv = fmaf(t, b.y, b.x), f12 = fmaf(t, b.w, b.z);
+    const float f6 = fmaf(t, c.y, c.x), fcv = fmaf(t, c.w, c.z);
+    elj = fmaf(A, e12, -B * e6);
+    frlj = fmaf(A, f12, -B * f6);
+    ec = qq * ecv;
+    frc = qq * fcv;
+}
+
 }  // namespace acenb

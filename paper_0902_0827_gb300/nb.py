@@ -25,7 +25,7 @@ STATUS_NAMES = {
 EXPORTS = ("nb_create", "nb_create_batch", "nb_build_cells", "nb_forces", "nb_backward", "nb_get_status",
            "nb_set_stream", "nb_destroy", "nb_set_tuning", "nb_get_tuning", "nb_get_sizes", "nb_debug_cells",
            "nb_debug_pairs", "nb_status_string", "nb_set_lj_params", "nb_set_profiling", "nb_get_profile",
-           "nb_forces_noalloc", "nb_type_gradients", "nb_set_pme", "nb_pme_forces")
+           "nb_forces_noalloc", "nb_type_gradients", "nb_set_pme", "nb_pme_forces", "nb_set_tables")
 
 
 class NbError(RuntimeError):
@@ -96,6 +96,7 @@ def lib(build_if_missing: bool = True):
             "nb_type_gradients": ([P, P, P, P, P], ctypes.c_int),
             "nb_set_pme": ([P, ctypes.POINTER(nb_pme_params)], ctypes.c_int),
             "nb_pme_forces": ([P, P, P, P, P, P], ctypes.c_int),
+            "nb_set_tables": ([P, I32], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -229,6 +230,11 @@ class Nonbonded:
         _check(lib().nb_forces(self.h, _tptr(pos), _tptr(q), _tptr(typ), _tptr(F), _tptr(E), _tptr(W)),
                "nb_forces")
         return F, E, W
+
+    def set_tables(self, n_intervals: int = 4096):
+        """Radial functions by linear interpolation of n-interval tables on
+        [0, rc] (0 restores direct evaluation)."""
+        _check(lib().nb_set_tables(self.h, int(n_intervals)), "nb_set_tables")
 
     def set_pme(self, grid=None, order: int = 4):
         """Enable smooth PME on the grid (K1, K2, K3) with B-splines of the

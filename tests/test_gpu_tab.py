@@ -1,0 +1,118 @@
+"""Tabulated radial functions on the GPU (nb_set_tables) against the oracle
+evaluating the same tables in FP64, and against direct evaluation (the
+paper's bound for its lookup tables: relative force error below 1e-4).
+
+Tolerances against the tabulated oracle are the direct path's: the tables
+hold the same FP32 values on both sides and the interpolation differs only
+by FP32 rounding of r, t and one FMA per function.
+"""
+
+import dataclasses
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_0902_0827_gb300 import nb
+from paper_0902_0827_gb300 import systems as S
+
+pytestmark = pytest.mark.gpu
+
+F_RMS, F_MAX, E_REL, W_REL = 5e-6, 1e-3, 1e-6, 1e-5
+PAPER_BOUND = 1e-4
+
+
+def run(s, n):
+    ctx = nb.Nonbonded(s)
+    if n:
+        ctx.set_tables(n)
+    pos, q, t = nb.concat_inputs([s])
+    ctx.build(pos)
+    F, E, W = ctx.forces(pos, q, t)
+    _, npairs, _ = ctx.debug_pairs(cap=0)
+    torch.cuda.synchronize()
+    ctx.status()
+    return ctx, F.double().cpu().numpy(), E[0].cpu().numpy(), W[0].cpu().numpy(), npairs
+
+
+@pytest.mark.parametrize("which", ["lj_fcc", "water_box", "solvated_chain"])
+def test_tables_match_the_tabulated_oracle(which):
+    s = getattr(S, which)()
+    n = 4096
+    _, F, E, W, npairs = run(s, n)
+    with oracle.tabulated(n):
+        Fo, Eo, Wo, no, Es = oracle.forces(s, method="cells", with_scale=True)
+    assert npairs == no
+    rel = np.linalg.norm(F - Fo) / np.linalg.norm(Fo)
+    print(which, "tab f_rms", rel)
+    assert rel <= F_RMS
+    assert np.abs(F - Fo).max() <= F_MAX
+    for k in range(2):
+        assert abs(E[k] - Eo[k]) <= E_REL * Es[k] + 1e-12
+    assert np.abs(W - Wo).max() <= W_REL * np.abs(Wo).max()
+    if which == "lj_fcc":
+        return  # nearly force-free crystal: net forces cancel, no relative bound
+    # and against direct evaluation: the paper's bound for its tables
+    Fd, Ed, _, _, Esd = oracle.forces(s, method="cells", with_scale=True)
+    reld = np.linalg.norm(F - Fd) / np.linalg.norm(Fd)
+    print(which, "vs direct f_rms", reld)
+    assert reld <= PAPER_BOUND
+    for k in range(2):
+        assert abs(E[k] - Ed[k]) <= PAPER_BOUND * Esd[k] + 1e-12
+
+
+def test_table_size_sets_the_error():
+    s = S.water_box()
+    Fd, _, _, _ = oracle.forces(s, method="cells")
+    errs = []
+    for n in (1024, 4096):
+        _, F, _, _, _ = run(s, n)
+        errs.append(np.linalg.norm(F - Fd) / np.linalg.norm(Fd))
+    assert 8.0 <= errs[0] / errs[1] <= 24.0, errs  # h^2: 16x for 4x more points
+
+
+def test_tables_off_restores_direct_and_adjoint_is_refused():
+    s = S.water_box()
+    ctx = nb.Nonbonded(s)
+    pos, q, t = nb.concat_inputs([s])
+    ctx.build(pos)
+    F0, E0, W0 = ctx.forces(pos, q, t)
+    F0, E0, W0 = F0.clone(), E0.clone(), W0.clone()
+    ctx.set_tables(4096)
+    F1, _, _ = ctx.forces(pos, q, t)
+    F1 = F1.clone()
+    F2, _, _ = ctx.forces(pos, q, t)
+    assert torch.equal(F1, F2)  # bit-identical reruns
+    assert not torch.equal(F0, F1)
+    with pytest.raises(nb.NbError) as ei:
+        ctx.backward(pos, q, t, torch.zeros_like(F1))
+    assert ei.value.code == 11
+    ctx.set_tables(0)
+    F3, E3, W3 = ctx.forces(pos, q, t)
+    torch.cuda.synchronize()
+    assert torch.equal(F0, F3) and torch.equal(E0, E3) and torch.equal(W0, W3)
+    with pytest.raises(nb.NbError):
+        ctx.set_tables(8)
+
+
+def test_tables_in_a_batch():
+    systems = S.water_ensemble()[:6]
+    ctx = nb.Nonbonded(systems)
+    ctx.set_tables(4096)
+    pos, q, t = nb.concat_inputs(systems)
+    ctx.build(pos)
+    F, E, W = ctx.forces(pos, q, t)
+    torch.cuda.synchronize()
+    ctx.status()
+    F = F.double().cpu().numpy()
+    off = 0
+    for k, s in enumerate(systems):
+        with oracle.tabulated(4096):
+            Fo, Eo, Wo, _, Es = oracle.forces(s, method="cells", with_scale=True)
+        Fk = F[off:off + s.n_atoms]
+        off += s.n_atoms
+        assert np.linalg.norm(Fk - Fo) / np.linalg.norm(Fo) <= F_RMS
+        for c in range(2):
+            assert abs(E[k, c].item() - Eo[c]) <= E_REL * Es[c]
