@@ -345,6 +345,79 @@ def big_water(k: int = 4, n_waters: int = 333_333) -> System:
     return _water_system(rng_for(k), n_waters, "big_water")
 
 
+# ---------------------------------------------------------------------------
+# Molecular-dynamics inputs: masses, bonded terms and rigid-water constraints
+# (section "Molecular dynamics on the GPU": bonded terms, velocity-Verlet
+# integration, Langevin thermostat, M-SHAKE/RATTLE constraints).  The chain
+# gets CHARMM-like parameters of an sp3 carbon backbone (the random-walk
+# geometry does not sit at their minimum, so it relaxes at the start of a
+# run).
+
+MASS_CHAIN = 12.011   # amu (carbon-like beads)
+MASS_O = 15.9994
+MASS_H = 1.008
+TIP3P_RHH = 2.0 * TIP3P_ROH * math.sin(0.5 * TIP3P_THETA)
+BOND_K, BOND_R0 = 300.0, 1.5               # U = k (r - r0)^2, kcal/mol/A^2, A
+ANGLE_K, ANGLE_THETA0 = 50.0, math.radians(111.0)  # U = k (theta - theta0)^2
+DIHEDRAL_K, DIHEDRAL_N, DIHEDRAL_PHASE = 0.2, 3, 0.0  # U = k (1 + cos(n phi - delta))
+
+
+@dataclasses.dataclass
+class MDTopology:
+    """Bonded terms (int32 indices, FP32 parameters), rigid 3-site waters
+    (O, H1, H2) and per-atom masses of one system."""
+
+    mass: np.ndarray          # float32 [N] (amu)
+    bonds: np.ndarray         # int32 [nb, 2]
+    bond_k: np.ndarray        # float32 [nb]
+    bond_r0: np.ndarray       # float32 [nb]
+    angles: np.ndarray        # int32 [na, 3], the middle atom is the vertex
+    angle_k: np.ndarray
+    angle_theta0: np.ndarray  # radians
+    dihedrals: np.ndarray     # int32 [nd, 4]
+    dihedral_k: np.ndarray
+    dihedral_n: np.ndarray    # int32
+    dihedral_phase: np.ndarray  # radians
+    waters: np.ndarray        # int32 [nw, 3]
+    water_roh: float = TIP3P_ROH
+    water_rhh: float = TIP3P_RHH
+
+
+def md_topology(sys: System, n_chain: int = 0) -> MDTopology:
+    """MD inputs of a water box (n_chain = 0) or of the solvated chain (its
+    first n_chain atoms form the chain, the rest are waters)."""
+    n = sys.n_atoms
+    nw = (n - n_chain) // 3
+    mass = np.concatenate([np.full(n_chain, MASS_CHAIN), np.tile([MASS_O, MASS_H, MASS_H], nw)])
+    waters = (n_chain + 3 * np.arange(nw))[:, None] + np.arange(3)[None, :]
+    i = np.arange(max(n_chain, 0))
+    bonds = np.stack([i[:-1], i[:-1] + 1], 1) if n_chain > 1 else np.zeros((0, 2), np.int64)
+    angles = np.stack([i[:-2], i[:-2] + 1, i[:-2] + 2], 1) if n_chain > 2 else np.zeros((0, 3), np.int64)
+    dih = np.stack([i[:-3], i[:-3] + 1, i[:-3] + 2, i[:-3] + 3], 1) if n_chain > 3 else np.zeros((0, 4), np.int64)
+    return MDTopology(
+        mass=mass.astype(np.float32),
+        bonds=bonds.astype(np.int32), bond_k=np.full(len(bonds), BOND_K, np.float32),
+        bond_r0=np.full(len(bonds), BOND_R0, np.float32),
+        angles=angles.astype(np.int32), angle_k=np.full(len(angles), ANGLE_K, np.float32),
+        angle_theta0=np.full(len(angles), ANGLE_THETA0, np.float32),
+        dihedrals=dih.astype(np.int32), dihedral_k=np.full(len(dih), DIHEDRAL_K, np.float32),
+        dihedral_n=np.full(len(dih), DIHEDRAL_N, np.int32),
+        dihedral_phase=np.full(len(dih), DIHEDRAL_PHASE, np.float32),
+        waters=waters.astype(np.int32))
+
+
+def initial_velocities(top: MDTopology, temperature: float = 300.0, seed: int = 11) -> np.ndarray:
+    """Seeded Maxwell-Boltzmann velocities (A/ps) at the temperature (K):
+    each component N(0, kT/m) with kT in kcal/mol and 1 kcal/mol/amu =
+    418.4 A^2/ps^2; the centre-of-mass velocity removed."""
+    rng = np.random.Generator(np.random.PCG64(SEED_BASE + 200 + seed))
+    kT = 0.0019872041 * temperature
+    m = top.mass.astype(np.float64)
+    v = rng.normal(size=(m.size, 3)) * np.sqrt(kT * 418.4 / m)[:, None]
+    v -= (m[:, None] * v).sum(0) / m.sum()
+    return v.astype(np.float32)
+
+
 def make(name: str, **kw):
     table = {"lj_fcc": lj_fcc, "water_box": water_box, "solvated_chain": solvated_chain,
              "water_ensemble": water_ensemble, "big_water": big_water}

@@ -1,0 +1,237 @@
+"""Pins of the MD oracle (bonded terms, Philox noise, M-SHAKE, RATTLE,
+Langevin velocity Verlet) against what the mathematics fixes:
+
+* bonded forces = -grad E by central differences; net force zero; virial
+  diagonal = -dE/d(strain) by affine finite differences;
+* closed forms: a bond stretched by delta has k delta^2; a right angle
+  k (pi/2 - theta0)^2; the dihedral of a geometry with IUPAC torsion +60
+  degrees (and its mirror image, -60) under U = k (1 + sin phi);
+* Philox: uniform and normal moments, avalanche of a one-bit counter change;
+* M-SHAKE: constraints met to 1e-12, centre of mass of every water kept,
+  each displacement a combination of the reference bond vectors;
+* RATTLE: r . (v_a - v_b) = 0, momentum kept, idempotent;
+* integrator: NVE energy conservation of a rigid-water box, time
+  reversibility of plain velocity Verlet, and the Langevin thermostat's
+  equipartition for an ideal gas.
+"""
+
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle
+import oracle.md as md
+from paper_0902_0827_gb300 import systems as S
+
+
+def small_chain(n=10, seed=5):
+    rng = np.random.default_rng(seed)
+    steps = rng.normal(size=(n - 1, 3))
+    steps = 1.5 * steps / np.linalg.norm(steps, axis=1, keepdims=True)
+    pos = np.concatenate([[[10.0, 10.0, 10.0]], 10.0 + np.cumsum(steps, 0)])
+    pos = pos + rng.normal(0, 0.05, size=pos.shape)
+    s = S.System("chain", pos.astype(np.float32), np.zeros(n, np.float32), np.zeros(n, np.int32),
+                 np.array([1.0], np.float32), np.array([0.0], np.float32), np.full(3, 40.0, np.float32),
+                 np.zeros((0, 2), np.int32), np.zeros((0, 2), np.int32), 9.0, 7.5, 0.0)
+    top = S.md_topology(s, n_chain=n)
+    top = dataclasses.replace(top, dihedral_phase=np.full(len(top.dihedrals), 0.4, np.float32),
+                              dihedral_n=np.array([1, 2, 3, 1, 2, 3, 1][:len(top.dihedrals)], np.int32))
+    return s, top
+
+
+def energy(top, x, box):
+    return sum(md.bonded(top, x, box)[1])
+
+
+def test_bonded_forces_are_minus_gradient_and_balance():
+    s, top = small_chain()
+    x = s.pos.astype(np.float64)
+    F, E, W = md.bonded(top, x, s.box)
+    assert np.abs(F.sum(0)).max() < 1e-10
+    h = 1e-6
+    for i in range(len(x)):
+        for a in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[i, a] += h
+            xm[i, a] -= h
+            fd = -(energy(top, xp, s.box) - energy(top, xm, s.box)) / (2 * h)
+            assert abs(fd - F[i, a]) <= 1e-6 * max(1.0, abs(F[i, a]))
+    for a in range(3):
+        Es = []
+        for e in (h, -h):
+            y = x.copy()
+            y[:, a] *= 1 + e
+            Es.append(energy(top, y, s.box))
+        assert abs(-(Es[0] - Es[1]) / (2 * h) - W[a]) <= 1e-6 * max(1.0, np.abs(W).max())
+
+
+def three_body(top_kw, pos):
+    n = len(pos)
+    s = S.System("t", np.asarray(pos, np.float32), np.zeros(n, np.float32), np.zeros(n, np.int32),
+                 np.array([1.0], np.float32), np.array([0.0], np.float32), np.full(3, 40.0, np.float32),
+                 np.zeros((0, 2), np.int32), np.zeros((0, 2), np.int32), 9.0, 7.5, 0.0)
+    empty2, empty3, empty4 = (np.zeros((0, k), np.int32) for k in (2, 3, 4))
+    z = np.zeros(0, np.float32)
+    base = dict(mass=np.ones(n, np.float32), bonds=empty2, bond_k=z, bond_r0=z, angles=empty3, angle_k=z,
+                angle_theta0=z, dihedrals=empty4, dihedral_k=z, dihedral_n=np.zeros(0, np.int32),
+                dihedral_phase=z, waters=np.zeros((0, 3), np.int32))
+    base.update(top_kw)
+    return s, S.MDTopology(**base)
+
+
+def test_closed_forms():
+    # bond stretched by 0.1 A
+    s, top = three_body(dict(bonds=np.array([[0, 1]], np.int32), bond_k=np.array([300.0], np.float32),
+                             bond_r0=np.array([1.5], np.float32)), [[5, 5, 5], [6.6, 5, 5]])
+    F, E, _ = md.bonded(top, s.pos.astype(np.float64), s.box)
+    dlt = float(np.float32(6.6)) - 5.0 - 1.5  # the FP32 coordinate
+    assert abs(E[0] - 300.0 * dlt ** 2) < 1e-9
+    assert abs(F[0, 0] - 2 * 300.0 * dlt) < 1e-9  # pulled towards atom 1
+    # right angle
+    t0 = np.float32(np.radians(111.0))
+    s, top = three_body(dict(angles=np.array([[0, 1, 2]], np.int32), angle_k=np.array([50.0], np.float32),
+                             angle_theta0=np.array([t0], np.float32)), [[6, 5, 5], [5, 5, 5], [5, 6, 5]])
+    _, E, _ = md.bonded(top, s.pos.astype(np.float64), s.box)
+    assert abs(E[1] - 50.0 * (np.pi / 2 - float(t0)) ** 2) < 1e-9
+    # IUPAC torsion: i on +x, j at the origin, k on +z, l at 60 degrees
+    # counterclockwise seen from +z: viewed along j->k the front bond turns
+    # clockwise by 60 degrees onto the rear one, so phi = +60
+    c, sn = 0.5, np.sqrt(3) / 2
+    pts = np.array([[1, 0, 0], [0, 0, 0], [0, 0, 1], [c, sn, 1]], float) + 10.0
+    kw = dict(dihedrals=np.array([[0, 1, 2, 3]], np.int32), dihedral_k=np.array([2.0], np.float32),
+              dihedral_n=np.array([1], np.int32), dihedral_phase=np.array([np.pi / 2], np.float32))
+    s, top = three_body(kw, pts)
+    _, E, _ = md.bonded(top, pts, s.box)
+    dl = float(np.float32(np.pi / 2))
+    assert abs(E[2] - 2.0 * (1 + np.cos(np.pi / 3 - dl))) < 1e-6
+    assert E[2] > 3.7  # 2 (1 + sin 60)
+    mirror = pts * np.array([1, -1, 1]) + np.array([0, 20.0, 0])
+    _, E, _ = md.bonded(top, mirror, s.box)
+    assert E[2] < 0.3  # 2 (1 - sin 60)
+
+
+def test_philox_statistics_and_avalanche():
+    n = 200000
+    a = np.arange(n)
+    o = md.philox4x32_10(a, np.zeros(n), np.zeros(n), np.zeros(n), 12345, 678)
+    u = np.concatenate([md.uniforms24(t) for t in o])
+    assert abs(u.mean() - 0.5) < 3e-3 and abs(u.var() - 1 / 12) < 2e-3
+    z = md.normals(a, 7, 0, 99).ravel()
+    assert abs(z.mean()) < 5e-3 and abs(z.var() - 1) < 1e-2
+    assert abs(((z - z.mean()) ** 4).mean() / z.var() ** 2 - 3.0) < 0.05
+    # one counter bit flipped: about half of the 128 output bits change
+    o2 = md.philox4x32_10(a ^ 1, np.zeros(n), np.zeros(n), np.zeros(n), 12345, 678)
+    flips = sum(np.unpackbits(np.asarray(x ^ y, dtype=np.uint32).view(np.uint8)).sum() for x, y in zip(o, o2))
+    assert abs(flips / (128 * n) - 0.5) < 0.01
+
+
+def water_md(nw=216, seed=40):
+    s = S._water_system(S.rng_for(seed), nw, f"w{nw}")
+    return s, S.md_topology(s)
+
+
+def test_shake_meets_constraints_and_keeps_centres_of_mass():
+    s, top = water_md()
+    x = s.pos.astype(np.float64)
+    m = top.mass.astype(np.float64)
+    rng = np.random.default_rng(1)
+    xn = x + rng.normal(0, 0.02, size=x.shape)
+    xc, disp, it = md.shake(top, x, xn, s.box, m)
+    w = top.waters
+    for (a, b), d in (((0, 1), top.water_roh), ((0, 2), top.water_roh), ((1, 2), top.water_rhh)):
+        r = md.min_image(xc[w[:, a]] - xc[w[:, b]], s.box.astype(np.float64))
+        assert np.abs(np.einsum("ij,ij->i", r, r) / d ** 2 - 1).max() < 1e-12
+    assert it < 10  # Newton: a few iterations
+    com = (m[w][..., None] * disp[w]).sum(1)
+    assert np.abs(com).max() < 1e-12
+    # m_i disp_i lies in the span of the reference bond vectors of the water
+    r = np.stack([md.min_image(x[w[:, a]] - x[w[:, b]], s.box.astype(np.float64))
+                  for a, b in ((0, 1), (0, 2), (1, 2))], 1)
+    for atom in range(3):
+        md_i = m[w[:, atom]][:, None] * disp[w[:, atom]]
+        coef, res, *_ = np.linalg.lstsq(r[0].T, md_i[0], rcond=None)
+        assert np.linalg.norm(r[0].T @ coef - md_i[0]) < 1e-12
+
+
+def test_rattle_projects_velocities():
+    s, top = water_md()
+    x = s.pos.astype(np.float64)
+    m = top.mass.astype(np.float64)
+    v = np.random.default_rng(2).normal(0, 5, size=x.shape)
+    vr = md.rattle(top, x, v, s.box, m)
+    w = top.waters
+    for a, b in ((0, 1), (0, 2), (1, 2)):
+        r = md.min_image(x[w[:, a]] - x[w[:, b]], s.box.astype(np.float64))
+        assert np.abs(np.einsum("ij,ij->i", r, vr[w[:, a]] - vr[w[:, b]])).max() < 1e-10
+    assert np.abs((m[:, None] * (vr - v)).sum(0)).max() < 1e-9
+    assert np.abs(md.rattle(top, x, vr, s.box, m) - vr).max() < 1e-12
+
+
+def test_nve_energy_is_conserved_for_rigid_water():
+    s, top = water_md(nw=216)
+    s = dataclasses.replace(s, ewald_alpha=0.32)
+    prm = md.MDParams(dt=0.001, gamma=0.0)
+    m = top.mass.astype(np.float64)
+    x = s.pos.astype(np.float64)
+    v = md.rattle(top, x, S.initial_velocities(top, 300.0).astype(np.float64), s.box, m)
+    F, Ep = md.forces_at(s, top, x, prm)
+    E0 = Ep.sum() + md.kinetic(v, m)
+    Es = []
+    for k in range(60):
+        x, v, F, E = md.step(s, top, x, v, F, k, prm)
+        Es.append(E.sum())
+    Es = np.array(Es)
+    ke = md.kinetic(v, m)
+    # a plainly truncated erfc Coulomb makes small jumps; the drift must stay
+    # a small fraction of the kinetic energy
+    assert abs(Es[-1] - E0) < 0.01 * ke
+    assert Es.std() < 0.01 * ke
+
+
+def test_velocity_verlet_is_time_reversible():
+    s = S.lj_fcc()
+    n = s.n_atoms
+    empty = np.zeros(0, np.float32)
+    top = S.MDTopology(mass=np.full(n, 39.9, np.float32), bonds=np.zeros((0, 2), np.int32), bond_k=empty,
+                       bond_r0=empty, angles=np.zeros((0, 3), np.int32), angle_k=empty, angle_theta0=empty,
+                       dihedrals=np.zeros((0, 4), np.int32), dihedral_k=empty, dihedral_n=np.zeros(0, np.int32),
+                       dihedral_phase=empty, waters=np.zeros((0, 3), np.int32))
+    prm = md.MDParams(dt=0.002, gamma=0.0)
+    x0 = s.pos.astype(np.float64)
+    v0 = S.initial_velocities(top, 100.0).astype(np.float64)
+    F, _ = md.forces_at(s, top, x0, prm)
+    x, v = x0, v0
+    for k in range(20):
+        x, v, F, _ = md.step(s, top, x, v, F, k, prm)
+    v = -v
+    for k in range(20):
+        x, v, F, _ = md.step(s, top, x, v, F, k, prm)
+    L = s.box.astype(np.float64)
+    assert np.abs(md.min_image(x - x0, L)).max() < 1e-5
+    assert np.abs(-v - v0).max() < 1e-3 * np.abs(v0).max()
+
+
+def test_langevin_equipartition_of_an_ideal_gas():
+    n = 600
+    rng = np.random.default_rng(3)
+    s = S.System("gas", rng.uniform(0, 30, size=(n, 3)).astype(np.float32), np.zeros(n, np.float32),
+                 np.zeros(n, np.int32), np.array([1.0], np.float32), np.array([0.0], np.float32),
+                 np.full(3, 30.0, np.float32), np.zeros((0, 2), np.int32), np.zeros((0, 2), np.int32),
+                 9.0, 7.5, 0.0)
+    empty = np.zeros(0, np.float32)
+    top = S.MDTopology(mass=rng.uniform(1, 40, n).astype(np.float32), bonds=np.zeros((0, 2), np.int32),
+                       bond_k=empty, bond_r0=empty, angles=np.zeros((0, 3), np.int32), angle_k=empty,
+                       angle_theta0=empty, dihedrals=np.zeros((0, 4), np.int32), dihedral_k=empty,
+                       dihedral_n=np.zeros(0, np.int32), dihedral_phase=empty, waters=np.zeros((0, 3), np.int32))
+    prm = md.MDParams(dt=0.002, gamma=20.0, temperature=300.0)
+    m = top.mass.astype(np.float64)
+    x, v = s.pos.astype(np.float64), np.zeros((n, 3))
+    F = np.zeros((n, 3))
+    kes = []
+    for k in range(150):
+        x, v, F, E = md.step(s, top, x, v, F, k, prm)
+        if k >= 50:
+            kes.append(E[5])
+    kt = md.KB * 300.0
+    assert abs(np.mean(kes) / (1.5 * n * kt) - 1.0) < 0.03
