@@ -315,6 +315,84 @@ nb_status nb_set_pme(nb_ctx *ctx, const nb_pme_params *p);
 nb_status nb_pme_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, float *d_F, double *d_energy,
                         double *d_virial);
 
+/* Molecular dynamics around the non-bonded path (section "Molecular dynamics
+ * on the GPU": bonded terms, velocity-Verlet integration, Langevin
+ * thermostat, M-SHAKE and RATTLE constraints; section "Performance": the
+ * DHFR step).  Functional forms (the paper names the terms but prints no
+ * formula):
+ *   bond     U = k (r - r0)^2;
+ *   angle    U = k (theta - theta0)^2, theta at the middle atom;
+ *   dihedral U = k (1 + cos(n phi - delta)), IUPAC phi =
+ *            atan2(|b2| b1 . (b2 x b3), (b1 x b2) . (b2 x b3)),
+ *            b1 = x_j - x_i, b2 = x_k - x_j, b3 = x_l - x_k (minimum images);
+ *   rigid 3-site waters (O, H1, H2): |O-H| = water_roh, |H-H| = water_rhh.
+ * One step of length dt (ps), Langevin velocity Verlet with constraints:
+ *   v <- c v + sqrt((1 - c^2) kT / m) xi, c = exp(-gamma dt / 2);
+ *   v <- v + dt/2 F/m;  x' = x + dt v;  M-SHAKE on every water (Newton
+ *   iterations on the three distance equations along the bond vectors of
+ *   x, at most shake_max_iter, until every |r^2 - d^2| / d^2 <
+ *   shake_tolerance; NB_ERR_TIMEOUT is recorded otherwise) with the velocity
+ *   changed by the constraint displacement / dt;  F = forces(x'') (cell
+ *   list + short-range + PME when enabled + bonded);  v <- v + dt/2 F/m;
+ *   v <- c v + sqrt((1 - c^2) kT / m) xi';  RATTLE on every water.
+ * xi: Philox4x32-10 on the counter (atom, step, stream 0 or 1, 0) with the
+ * key (seed low, seed high), 24-bit uniforms, Box-Muller.  Units kcal/mol,
+ * A, amu, ps (F/m times 418.4 is A/ps^2), K. */
+typedef struct {
+    const float *mass;           /* host [N] atomic masses (amu), > 0 */
+    int32_t n_bonds;
+    const int32_t *bonds;        /* host [n_bonds*2] */
+    const float *bond_k;         /* [n_bonds] kcal/mol/A^2 */
+    const float *bond_r0;        /* [n_bonds] A */
+    int32_t n_angles;
+    const int32_t *angles;       /* host [n_angles*3], middle atom at the vertex */
+    const float *angle_k;        /* kcal/mol/rad^2 */
+    const float *angle_theta0;   /* rad */
+    int32_t n_dihedrals;
+    const int32_t *dihedrals;    /* host [n_dihedrals*4] */
+    const float *dihedral_k;     /* kcal/mol */
+    const int32_t *dihedral_n;   /* multiplicity */
+    const float *dihedral_phase; /* rad */
+    int32_t n_waters;
+    const int32_t *waters;       /* host [n_waters*3] (O, H1, H2), each atom in one water at most */
+    float water_roh, water_rhh;  /* constraint lengths (A) */
+    float dt;                    /* time step (ps), > 0 */
+    float gamma;                 /* friction (1/ps); 0 = NVE velocity Verlet */
+    float temperature;           /* K */
+    uint64_t seed;               /* Philox key */
+    int32_t shake_max_iter;      /* >= 1 */
+    float shake_tolerance;       /* > 0, relative */
+    uint32_t flags;              /* reserved, must be 0 */
+} nb_md_params;
+
+/* nb_md_init - attach an MD state to a single-system context (copies the
+ * topology; synchronises the stream; not capturable).  The step counter of
+ * the noise starts at 0.  Errors: NB_ERR_INVALID_ARG (indices out of range,
+ * non-positive masses, an atom in two waters, ...), NB_ERR_UNSUPPORTED
+ * (batch context), NB_ERR_OOM, NB_ERR_CUDA. */
+nb_status nb_md_init(nb_ctx *ctx, const nb_md_params *p);
+
+/* nb_md_step - advance d_pos [N,3] and d_vel [N,3] (FP32, A and A/ps,
+ * updated in place; positions are kept wrapped into the box) by n_steps
+ * steps with charges d_q and types d_type.  The first call after
+ * nb_md_init evaluates the forces at the starting positions; later calls
+ * reuse those of the previous step, so between calls the positions must
+ * change only through nb_md_step.  d_energy [6] (E_LJ, E_Coul (with PME
+ * when enabled), E_bond, E_angle, E_dihedral, E_kin; kcal/mol) receives
+ * the energies after the last step, or NULL.  Asynchronous, capturable
+ * (a device counter numbers the steps, so graph replays draw new noise).
+ * NB_ERR_NOT_BUILT without nb_md_init. */
+nb_status nb_md_step(nb_ctx *ctx, float *d_pos, float *d_vel, const float *d_q, const int32_t *d_type,
+                     int32_t n_steps, double *d_energy);
+
+/* nb_bonded_forces - the bonded terms alone at d_pos: d_F [N,3] forces,
+ * d_energy [3] (bond, angle, dihedral) or NULL.  FP32 terms, forces summed
+ * in 64-bit fixed point (2^32).  NB_ERR_NOT_BUILT without nb_md_init. */
+nb_status nb_bonded_forces(nb_ctx *ctx, const float *d_pos, float *d_F, double *d_energy);
+
+/* nb_md_set_step - set the device step counter (synchronises the stream). */
+nb_status nb_md_set_step(nb_ctx *ctx, uint64_t step);
+
 /* nb_status_string - static description of a status code. */
 const char *nb_status_string(nb_status s);
 

@@ -457,6 +457,7 @@ void nb_destroy(nb_ctx *ctx)
     for (auto &e : ctx->prof_ev) cudaEventDestroy(e);
     ctx->prof_ev.clear();
     pme_free(ctx);
+    md_free(ctx);
     free_all(ctx);
     delete ctx;
 }

@@ -22,6 +22,7 @@ constexpr double kVirScale = 1048576.0;      // 2^20: fixed-point scale of the v
 constexpr int kPmeAcc = 9;           // PME sums: E_recip, E_self, E_excl (2^32), W[6] (2^20)
 constexpr int kPmeMaxGrid = 1024;    // largest PME grid edge
 struct PmeState;                     // smooth PME state of a single-system context (nb_pme.cu)
+struct MdState;                      // molecular-dynamics state of a single-system context (nb_md.cu)
 // Padding slots of the sorted arrays sit at this finite, far-away coordinate:
 // their squared distance to any atom (about 3e36) stays finite and is never
 // inside a cutoff, so masked pair arithmetic needs no further guards.
@@ -155,6 +156,7 @@ struct nb_ctx {
     std::vector<double> sig_tab, eps_tab;  // FP64 type-pair parameters
     acenb::DevBuffers d;
     acenb::PmeState *pme = nullptr;  // smooth PME, when enabled by nb_set_pme
+    acenb::MdState *md = nullptr;    // molecular dynamics, after nb_md_init
     // profiling: event pairs around force-kernel launches
     bool profiling = false;
     std::vector<cudaEvent_t> prof_ev;
@@ -220,6 +222,7 @@ void pme_free(nb_ctx *ctx);
 const long long *pme_forces_acc(const nb_ctx *ctx);
 const long long *pme_sums_acc(const nb_ctx *ctx);
 double pme_self_coef(const nb_ctx *ctx);  // -ke alpha / sqrt(pi), multiplies sum q^2
+void md_free(nb_ctx *ctx);
 cudaError_t launch_backward(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type,
                             const float *d_dLdF, const double *d_dLdE, float *d_dLdpos, float *d_dLdq,
                             double *d_dsig, double *d_deps);

@@ -25,7 +25,8 @@ STATUS_NAMES = {
 EXPORTS = ("nb_create", "nb_create_batch", "nb_build_cells", "nb_forces", "nb_backward", "nb_get_status",
            "nb_set_stream", "nb_destroy", "nb_set_tuning", "nb_get_tuning", "nb_get_sizes", "nb_debug_cells",
            "nb_debug_pairs", "nb_status_string", "nb_set_lj_params", "nb_set_profiling", "nb_get_profile",
-           "nb_forces_noalloc", "nb_type_gradients", "nb_set_pme", "nb_pme_forces", "nb_set_tables")
+           "nb_forces_noalloc", "nb_type_gradients", "nb_set_pme", "nb_pme_forces", "nb_set_tables", "nb_md_init", "nb_md_step", "nb_bonded_forces",
+           "nb_md_set_step")
 
 
 class NbError(RuntimeError):
@@ -54,6 +55,23 @@ class nb_tuning(ctypes.Structure):
 
 class nb_pme_params(ctypes.Structure):
     _fields_ = [("grid", ctypes.c_int32 * 3), ("order", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+
+class nb_md_params(ctypes.Structure):
+    _fields_ = [
+        ("mass", ctypes.c_void_p),
+        ("n_bonds", ctypes.c_int32), ("bonds", ctypes.c_void_p), ("bond_k", ctypes.c_void_p),
+        ("bond_r0", ctypes.c_void_p),
+        ("n_angles", ctypes.c_int32), ("angles", ctypes.c_void_p), ("angle_k", ctypes.c_void_p),
+        ("angle_theta0", ctypes.c_void_p),
+        ("n_dihedrals", ctypes.c_int32), ("dihedrals", ctypes.c_void_p), ("dihedral_k", ctypes.c_void_p),
+        ("dihedral_n", ctypes.c_void_p), ("dihedral_phase", ctypes.c_void_p),
+        ("n_waters", ctypes.c_int32), ("waters", ctypes.c_void_p), ("water_roh", ctypes.c_float),
+        ("water_rhh", ctypes.c_float),
+        ("dt", ctypes.c_float), ("gamma", ctypes.c_float), ("temperature", ctypes.c_float),
+        ("seed", ctypes.c_uint64), ("shake_max_iter", ctypes.c_int32), ("shake_tolerance", ctypes.c_float),
+        ("flags", ctypes.c_uint32),
+    ]
 
 
 _lib = None
@@ -97,6 +115,10 @@ def lib(build_if_missing: bool = True):
             "nb_set_pme": ([P, ctypes.POINTER(nb_pme_params)], ctypes.c_int),
             "nb_pme_forces": ([P, P, P, P, P, P], ctypes.c_int),
             "nb_set_tables": ([P, I32], ctypes.c_int),
+            "nb_md_init": ([P, ctypes.POINTER(nb_md_params)], ctypes.c_int),
+            "nb_md_step": ([P, P, P, P, P, I32, P], ctypes.c_int),
+            "nb_bonded_forces": ([P, P, P, P], ctypes.c_int),
+            "nb_md_set_step": ([P, ctypes.c_uint64], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -235,6 +257,54 @@ class Nonbonded:
         """Radial functions by linear interpolation of n-interval tables on
         [0, rc] (0 restores direct evaluation)."""
         _check(lib().nb_set_tables(self.h, int(n_intervals)), "nb_set_tables")
+
+    def md_init(self, top, dt=0.002, gamma=1.0, temperature=300.0, seed=2009, shake_max_iter=10,
+                shake_tolerance=1e-6):
+        """Attach the MD state: ``top`` has the attributes of
+        :class:`paper_0902_0827_gb300.systems.MDTopology`."""
+        keep = []
+
+        def arr(a, dt_):
+            a = np.ascontiguousarray(a, dtype=dt_)
+            keep.append(a)
+            return _ptr(a)
+
+        p = nb_md_params()
+        p.mass = arr(top.mass, np.float32)
+        p.n_bonds = len(top.bonds)
+        p.bonds, p.bond_k, p.bond_r0 = arr(top.bonds, np.int32), arr(top.bond_k, np.float32), arr(top.bond_r0, np.float32)
+        p.n_angles = len(top.angles)
+        p.angles, p.angle_k = arr(top.angles, np.int32), arr(top.angle_k, np.float32)
+        p.angle_theta0 = arr(top.angle_theta0, np.float32)
+        p.n_dihedrals = len(top.dihedrals)
+        p.dihedrals, p.dihedral_k = arr(top.dihedrals, np.int32), arr(top.dihedral_k, np.float32)
+        p.dihedral_n, p.dihedral_phase = arr(top.dihedral_n, np.int32), arr(top.dihedral_phase, np.float32)
+        p.n_waters = len(top.waters)
+        p.waters = arr(top.waters, np.int32)
+        p.water_roh, p.water_rhh = float(top.water_roh), float(top.water_rhh)
+        p.dt, p.gamma, p.temperature = float(dt), float(gamma), float(temperature)
+        p.seed, p.shake_max_iter, p.shake_tolerance, p.flags = int(seed), int(shake_max_iter), float(shake_tolerance), 0
+        _check(lib().nb_md_init(self.h, ctypes.byref(p)), "nb_md_init")
+        del keep
+
+    def md_step(self, pos, vel, q, typ, n_steps=1, energy=None):
+        """Advance pos and vel (CUDA FP32 [N,3], in place) by n_steps; energy
+        (FP64 [6] tensor or None) receives E_LJ, E_Coul, E_bond, E_angle,
+        E_dihedral, E_kin after the last step."""
+        self._sync_stream()
+        _check(lib().nb_md_step(self.h, _tptr(pos), _tptr(vel), _tptr(q), _tptr(typ), int(n_steps), _tptr(energy)),
+               "nb_md_step")
+
+    def bonded_forces(self, pos):
+        import torch
+        self._sync_stream()
+        F = torch.empty((self.n_atoms, 3), dtype=torch.float32, device=pos.device)
+        E = torch.empty((3,), dtype=torch.float64, device=pos.device)
+        _check(lib().nb_bonded_forces(self.h, _tptr(pos), _tptr(F), _tptr(E)), "nb_bonded_forces")
+        return F, E
+
+    def md_set_step(self, step: int):
+        _check(lib().nb_md_set_step(self.h, int(step)), "nb_md_set_step")
 
     def set_pme(self, grid=None, order: int = 4):
         """Enable smooth PME on the grid (K1, K2, K3) with B-splines of the

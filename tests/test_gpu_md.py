@@ -1,0 +1,171 @@
+"""The MD step on the GPU (nb_md_init / nb_md_step / nb_bonded_forces)
+against the FP64 oracle of oracle/md.py.
+
+Tolerances.  Bonded terms are FP32 (atan2f, cross products of A-sized
+vectors): forces to 1e-5 relative RMS.  One step moves positions by dt v
+(~0.01 A) in FP32 coordinates of up to 62 A, whose rounding is ~4e-6 A, so
+positions are compared to 2e-5 A (minimum image) and velocities to 1e-5
+relative RMS; after a few steps both grow with the FP32 differences of the
+forces.  Constraints hold to the FP32 resolution of the coordinates.
+"""
+
+import dataclasses
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle.md as omd
+from paper_0902_0827_gb300 import nb
+from paper_0902_0827_gb300 import systems as S
+
+pytestmark = pytest.mark.gpu
+
+
+def setup(s, top, gamma=0.0, dt=0.001, pme=None, seed=2009):
+    ctx = nb.Nonbonded(s)
+    if pme:
+        ctx.set_pme(*pme)
+    ctx.md_init(top, dt=dt, gamma=gamma, temperature=300.0, seed=seed)
+    pos, q, t = nb.concat_inputs([s])
+    return ctx, pos, q, t
+
+
+def min_image(d, L):
+    return d - L * np.rint(d / L)
+
+
+def test_bonded_forces_match_oracle():
+    s = S.solvated_chain()
+    top = S.md_topology(s, n_chain=2500)
+    ctx, pos, q, t = setup(s, top)
+    F, E = ctx.bonded_forces(pos)
+    torch.cuda.synchronize()
+    ctx.status()
+    Fo, Eo, _ = omd.bonded(top, s.pos.astype(np.float64), s.box)
+    F = F.double().cpu().numpy()
+    rel = np.linalg.norm(F - Fo) / np.linalg.norm(Fo)
+    print("bonded f_rms", rel)
+    assert rel <= 1e-5
+    for k in range(3):
+        assert abs(E[k].item() - Eo[k]) <= 1e-6 * max(abs(Eo[k]), 1.0)
+
+
+def water(nw=512, seed=41):
+    s = S._water_system(S.rng_for(seed), nw, f"w{nw}")
+    return s, S.md_topology(s)
+
+
+@pytest.mark.parametrize("gamma", [0.0, 5.0])
+def test_one_step_matches_oracle(gamma):
+    s, top = water()
+    ctx, pos, q, t = setup(s, top, gamma=gamma)
+    v0 = S.initial_velocities(top, 300.0)
+    vel = torch.from_numpy(v0).cuda()
+    E = torch.empty(6, dtype=torch.float64, device="cuda")
+    ctx.md_step(pos, vel, q, t, 1, E)
+    torch.cuda.synchronize()
+    ctx.status()
+    prm = omd.MDParams(dt=0.001, gamma=gamma, temperature=300.0, seed=2009)
+    x = s.pos.astype(np.float64)
+    F, _ = omd.forces_at(s, top, x, prm)
+    xo, vo, _, Eo = omd.step(s, top, x, v0.astype(np.float64), F, 0, prm)
+    L = s.box.astype(np.float64)
+    dx = np.abs(min_image(pos.double().cpu().numpy() - xo, L)).max()
+    vg = vel.double().cpu().numpy()
+    rv = np.linalg.norm(vg - vo) / np.linalg.norm(vo)
+    print("step gamma", gamma, "max dx", dx, "v rel", rv)
+    assert dx <= 2e-5
+    assert rv <= 1e-5
+    Eg = E.cpu().numpy()
+    assert abs(Eg[5] - Eo[5]) <= 1e-5 * Eo[5]  # kinetic energy
+
+
+def test_solvated_chain_with_pme_three_steps():
+    s = S.solvated_chain()
+    top = S.md_topology(s, n_chain=2500)
+    pme = ((64, 64, 64), 4)
+    ctx, pos, q, t = setup(s, top, gamma=1.0, dt=0.002, pme=pme)
+    v0 = S.initial_velocities(top, 300.0)
+    vel = torch.from_numpy(v0).cuda()
+    E = torch.empty(6, dtype=torch.float64, device="cuda")
+    ctx.md_step(pos, vel, q, t, 3, E)
+    torch.cuda.synchronize()
+    ctx.status()
+    prm = omd.MDParams(dt=0.002, gamma=1.0, temperature=300.0, seed=2009, pme=pme)
+    x = s.pos.astype(np.float64)
+    v = v0.astype(np.float64)
+    F, _ = omd.forces_at(s, top, x, prm)
+    for k in range(3):
+        x, v, F, Eo = omd.step(s, top, x, v, F, k, prm)
+    L = s.box.astype(np.float64)
+    dx = np.abs(min_image(pos.double().cpu().numpy() - x, L)).max()
+    rv = np.linalg.norm(vel.double().cpu().numpy() - v) / np.linalg.norm(v)
+    Eg = E.cpu().numpy()
+    print("chain 3 steps max dx", dx, "v rel", rv, "E", Eg, Eo)
+    assert dx <= 1e-4
+    assert rv <= 1e-4
+    assert abs(Eg[5] - Eo[5]) <= 1e-4 * Eo[5]
+    for k in range(2, 5):
+        assert abs(Eg[k] - Eo[k]) <= 1e-4 * max(abs(Eo[k]), 1.0)
+
+
+def test_constraints_hold_and_nve_energy_is_conserved():
+    s, top = water(nw=512)
+    ctx, pos, q, t = setup(s, top, gamma=0.0, dt=0.001)
+    vel = torch.from_numpy(S.initial_velocities(top, 300.0)).cuda()
+    E = torch.empty(6, dtype=torch.float64, device="cuda")
+    ctx.md_step(pos, vel, q, t, 50, E)  # relax the synthetic start
+    torch.cuda.synchronize()
+    E0 = E.sum().item()
+    ke = []
+    tot = []
+    for _ in range(20):
+        ctx.md_step(pos, vel, q, t, 10, E)
+        e = E.cpu().numpy()
+        tot.append(e.sum())
+        ke.append(e[5])
+    ctx.status()
+    x = pos.double().cpu().numpy()
+    L = s.box.astype(np.float64)
+    w = top.waters
+    for (a, b), d in (((0, 1), top.water_roh), ((0, 2), top.water_roh), ((1, 2), top.water_rhh)):
+        r = np.linalg.norm(min_image(x[w[:, a]] - x[w[:, b]], L), axis=1)
+        assert np.abs(r - d).max() < 5e-5
+    print("NVE drift", tot[-1] - E0, "KE", np.mean(ke))
+    assert abs(tot[-1] - E0) < 0.01 * np.mean(ke)
+
+
+def test_md_is_deterministic_and_graph_capturable():
+    s, top = water(nw=216, seed=43)
+    v0 = torch.from_numpy(S.initial_velocities(top, 300.0)).cuda()
+    outs = []
+    for _ in range(2):
+        ctx, pos, q, t = setup(s, top, gamma=2.0, dt=0.002)
+        vel = v0.clone()
+        ctx.md_step(pos, vel, q, t, 20)
+        torch.cuda.synchronize()
+        outs.append((pos.clone(), vel.clone()))
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+    # graph: 10 steps captured once, replayed twice = 20 steps from the
+    # same state (the device step counter numbers the noise)
+    ctx, pos, q, t = setup(s, top, gamma=2.0, dt=0.002)
+    vel = v0.clone()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        ctx.md_step(pos, vel, q, t, 0)  # forces at the start (not captured)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=side):
+            ctx.md_step(pos, vel, q, t, 10)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    # capture executed nothing: state, forces and step counter are those of
+    # the start
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    ctx.status()
+    assert torch.equal(pos, outs[0][0]) and torch.equal(vel, outs[0][1])
