@@ -14,7 +14,8 @@ per step / seconds per step (the pair count is the kernel's own count, taken
 once before timing).  The JSON line also carries the roofline of the force
 kernel (FP32 pipe; 73 algorithmic FLOP per pair), the end-to-end number
 through host buffers, the adjoint and batched forms, the step with smooth
-PME added, the step with tabulated radial functions, clocks, and the FP64 oracle timed on the host cores (context
+PME added, the step with tabulated radial functions, the molecular-dynamics
+step (ns/day), clocks, and the FP64 oracle timed on the host cores (context
 only).
 
 Multi-GPU: every rank evaluates its own replica (no data-path collective);
@@ -44,11 +45,15 @@ UNIT = "pairs/s"
 BUILD_LAUNCHES = 4
 FORCE_LAUNCHES = 3
 ADJOINT_LAUNCHES = 5
-# smooth PME adds spread, grid conversion, solve, gather (+ the FFT library's
-# forward and inverse transforms, not counted as this library's kernels)
-PME_LAUNCHES = 4
+# smooth PME adds spread, solve, gather (+ the FFT library's forward and
+# inverse transforms, not counted as this library's kernels)
+PME_LAUNCHES = 3
 PME_GRID, PME_ORDER = (64, 64, 64), 4  # the paper's DHFR setting
 TABLE_INTERVALS = 4096  # the paper's lookup-table size
+MD_DT_PS, MD_GRAPH_STEPS = 0.004, 10  # the paper's 4 fs step with mass repartitioning
+MD_WATERS = 7833  # 23,499 atoms in 61.7 A, the size of the paper's DHFR system
+# MD step: kick/drift, M-SHAKE, rebuild, forces, PME, (bonded), kick, RATTLE, finish
+MD_LAUNCHES = 1 + 1 + BUILD_LAUNCHES + FORCE_LAUNCHES + PME_LAUNCHES + 1 + 1 + 1
 FLOP_PER_PAIR = 73  # LJ + switch + Ewald real space, FMA = 2, MUFU = 1
 WORKLOAD = ("solvated-chain system, 23,500 atoms (2,500-atom chain + 7,000 TIP3P-shaped waters), "
             "62.2 A cubic box, rc 9 A, switch 7.5 A, Ewald alpha 0.32, 1-2/1-3 excluded, 1-4 scaled")
@@ -66,6 +71,7 @@ def parse():
                     help="time only the step with smooth PME (for profiling its kernels)")
     ap.add_argument("--tables-only", action="store_true",
                     help="time only the step with tabulated radial functions (for profiling)")
+    ap.add_argument("--md-only", action="store_true", help="time only the MD leg (for profiling)")
     return ap.parse_args()
 
 
@@ -273,6 +279,52 @@ def tables_leg(s, steps, flush, dev, npairs, base_ms, base_fo_ms):
             "gpu_launches_per_step": BUILD_LAUNCHES + FORCE_LAUNCHES}
 
 
+def md_leg(steps, flush, dev):
+    """Molecular dynamics with the paper's DHFR settings: PME 64^3 / order 4
+    every step, rc 9 A switched at 7.5 A, rigid waters by M-SHAKE/RATTLE,
+    hydrogen mass repartitioning, dt 4 fs, Langevin thermostat (1/ps,
+    300 K), on a 23,499-atom water box (7,833 TIP3P-shaped waters, 61.7 A):
+    the synthetic chain's random LJ contacts are not stable at 4 fs (its
+    energy diverges within 20 steps even after damped relaxation), so a
+    DHFR-sized water box stands in.  MD_GRAPH_STEPS steps are captured in
+    one CUDA graph; the L2 is flushed before each replay, the steps inside
+    a replay run back to back as in a production loop."""
+    import torch
+    from paper_0902_0827_gb300 import nb
+    from paper_0902_0827_gb300 import systems as S
+    s = S.water_box(n_waters=MD_WATERS)
+    top = S.hmr_masses(S.md_topology(s))
+    ctx = nb.Nonbonded(s)
+    ctx.set_pme(PME_GRID, PME_ORDER)
+    pos, q, typ = nb.concat_inputs([s], device=dev)
+    vel = torch.from_numpy(S.initial_velocities(top, 300.0)).to(dev)
+    E = torch.empty(6, dtype=torch.float64, device=dev)
+    # equilibrate the synthetic start (random orientations release potential
+    # energy): 1 ps at 2 fs under strong friction, then 0.2 ps at 4 fs
+    ctx.md_init(top, dt=0.002, gamma=20.0, temperature=300.0, seed=2008)
+    ctx.md_step(pos, vel, q, typ, 500, E)
+    ctx.md_init(top, dt=MD_DT_PS, gamma=1.0, temperature=300.0, seed=2009)
+    ctx.md_step(pos, vel, q, typ, 50, E)
+    torch.cuda.synchronize()
+
+    def run():
+        ctx.md_step(pos, vel, q, typ, MD_GRAPH_STEPS, E)
+
+    g = graph_of(run, dev)
+    reps = max(3, steps // MD_GRAPH_STEPS)
+    ms = time_steps(g.replay, reps, flush) / MD_GRAPH_STEPS
+    ctx.status()
+    e = E.cpu().numpy()
+    n_dof = 3 * s.n_atoms - 3 * len(top.waters)
+    return {"system": f"water box, {s.n_atoms} atoms, {float(s.box[0]):.1f} A", "ms_per_step": ms,
+            "ns_per_day": MD_DT_PS * 1e-3 * 86400.0 / (ms * 1e-3), "dt_fs": MD_DT_PS * 1e3,
+            "temperature_K": 2.0 * e[5] / (n_dof * 0.0019872041), "steps_timed": reps * MD_GRAPH_STEPS,
+            "step": "Langevin velocity Verlet: integrate, M-SHAKE, cell-list rebuild, short-range forces, PME, "
+                    "bonded terms, integrate, RATTLE",
+            "paper_context": "DHFR 17.55 ms/step, 19.7 ns/day on one GTX 280 (section Performance)",
+            "gpu_launches_per_step": MD_LAUNCHES + (1 if len(top.bonds) + len(top.angles) + len(top.dihedrals) else 0)}
+
+
 def batched_leg(steps, flush, dev):
     """64 water boxes (log-uniform 500..20,000 atoms): one autotuned,
     graph-captured rebuild + force step of the whole batch vs 64 sequential
@@ -404,10 +456,12 @@ def main():
     props = torch.cuda.get_device_properties(dev)
     n_sms = props.multi_processor_count
     s = S.solvated_chain()
-    if args.pme_only or args.tables_only:
+    if args.pme_only or args.tables_only or args.md_only:
         flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)
         if args.pme_only:
             print(json.dumps({"pme": pme_leg(s, args.steps, flush, dev, 0, 0.0)}))
+        elif args.md_only:
+            print(json.dumps({"md": md_leg(args.steps, flush, dev)}))
         else:
             print(json.dumps({"tables": tables_leg(s, args.steps, flush, dev, 0, float("nan"), float("nan"))}))
         return 0
@@ -513,6 +567,7 @@ def main():
         line["adjoint"] = adjoint_leg(ctx, pos, q, typ, args.steps, flush, ms, npairs)
         line["pme"] = pme_leg(s, args.steps, flush, dev, npairs, ms)
         line["tables"] = tables_leg(s, args.steps, flush, dev, npairs, ms, fo_ms)
+        line["md"] = md_leg(args.steps, flush, dev)
         line["batched"] = batched_leg(args.steps, flush, dev)
         # end to end through the public API with host buffers (pinned): the
         # step's inputs (positions, charges, types) travel in one host->device

@@ -111,6 +111,12 @@ __global__ void k_bin(int n, const float *__restrict__ pos, SysDesc *__restrict_
         x = wrap_coord(x, S.L[0]);
         y = wrap_coord(y, S.L[1]);
         z = wrap_coord(z, S.L[2]);
+        // a finite coordinate too large for the FP32 wrap (|x| beyond ~2^24 L)
+        // is reported like a non-finite one: every later index stays in range
+        if (!(x >= 0.0f && x < S.L[0] && y >= 0.0f && y < S.L[1] && z >= 0.0f && z < S.L[2])) {
+            atomicOr(status, ST_NONFINITE);
+            x = 0.0f; y = 0.0f; z = 0.0f;
+        }
         col = S.col_begin + column_of(y, S.inv_w[1], S.ny) * S.nx + column_of(x, S.inv_w[0], S.nx);
         atom_col[a] = col;
         wpos[a] = make_float4(x, y, z, 0.0f);

@@ -105,7 +105,8 @@ __device__ __forceinline__ void bspline_weights(float f, float (&w)[N], float (&
 }
 
 // Grid base index floor(u) in [0, K) and offset f = u - floor(u) of a
-// coordinate x in [0, L), u = x K / L.  K / L is carried as an FP32 pair
+// coordinate x in [0, L), u = x K / L (any other input gives index 0 and
+// f = 0, so no index leaves the grid).  K / L is carried as an FP32 pair
 // (s_hi + s_lo) and the product's rounding error is recovered with an FMA,
 // so f is accurate to FP32 rounding of f itself (about 6e-8 grid spacings)
 // although u reaches K.
@@ -125,6 +126,10 @@ __device__ __forceinline__ int grid_coord(float x, float s_hi, float s_lo, int K
     int i0 = (int)fl;
     if (i0 >= K) i0 -= K;
     if (i0 < 0) i0 += K;
+    if ((unsigned)i0 >= (unsigned)K || !(fr >= 0.0f && fr <= 1.0f)) {  // not a wrapped coordinate
+        i0 = 0;
+        fr = 0.0f;
+    }
     f = fr;
     return i0;
 }

@@ -406,6 +406,18 @@ def md_topology(sys: System, n_chain: int = 0) -> MDTopology:
         waters=waters.astype(np.int32))
 
 
+def hmr_masses(top: MDTopology, h_mass: float = 4.032) -> MDTopology:
+    """Hydrogen mass repartitioning (section "Molecular dynamics on the GPU",
+    after Feenstra et al.): each water H gets h_mass and its O gives up the
+    difference, so every molecule keeps its mass (allows 4 fs steps)."""
+    m = top.mass.astype(np.float64).copy()
+    w = top.waters
+    for h in (1, 2):
+        m[w[:, 0]] -= h_mass - m[w[:, h]]
+        m[w[:, h]] = h_mass
+    return dataclasses.replace(top, mass=m.astype(np.float32))
+
+
 def initial_velocities(top: MDTopology, temperature: float = 300.0, seed: int = 11) -> np.ndarray:
     """Seeded Maxwell-Boltzmann velocities (A/ps) at the temperature (K):
     each component N(0, kT/m) with kT in kcal/mol and 1 kcal/mol/amu =
