@@ -1090,6 +1090,13 @@ cudaError_t launch_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, con
         cudaMemsetAsync(d.sys_acc, 0, sizeof(long long) * kTaskVals * ctx->n_sys, ctx->stream);
         cudaMemsetAsync(d.facc, 0, sizeof(long long) * 3 * ctx->slot_cap, ctx->stream);
     }
+    // smooth PME: forked onto its own stream so that it overlaps the
+    // short-range kernel; joined back before the unpack reads its sums
+    const bool pme = ctx->pme && d_pos && !debug_pairs;
+    if (pme) {
+        cudaError_t e = launch_pme_fork(ctx, d_pos, d_q);
+        if (e != cudaSuccess) return e;
+    }
     ForceArgs A = make_args(ctx);
     A.F = d_F;
     A.facc = d.facc;
@@ -1114,9 +1121,8 @@ cudaError_t launch_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, con
         cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n + 1], ctx->stream);
         ctx->prof_n++;
     }
-    const bool pme = ctx->pme && d_pos && !debug_pairs;
     if (pme) {
-        cudaError_t e = launch_pme(ctx, d_pos, d_q);
+        cudaError_t e = launch_pme_join(ctx);
         if (e != cudaSuccess) return e;
     }
     {

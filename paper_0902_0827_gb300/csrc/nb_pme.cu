@@ -73,6 +73,10 @@ struct PmeState {
     double self_coef = 0.0;     // -ke alpha / sqrt(pi)
     cufftHandle fwd = 0, inv = 0;
     bool have_fwd = false, have_inv = false;
+    // nb_forces runs the chain on `side`, forked from and joined back to the
+    // context's stream, so it overlaps the short-range kernel
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
     PmeGeom g{};
     PmeCorr c{};
 };
@@ -571,6 +575,12 @@ void pme_free(nb_ctx *ctx)
     if (!p) return;
     if (p->have_fwd) cufftDestroy(p->fwd);
     if (p->have_inv) cufftDestroy(p->inv);
+    if (p->side) {
+        cudaStreamSynchronize(p->side);
+        cudaStreamDestroy(p->side);
+    }
+    if (p->fork) cudaEventDestroy(p->fork);
+    if (p->join) cudaEventDestroy(p->join);
     void *ptrs[] = {p->grid, p->fq, p->gfac, p->pacc, p->acc};
     for (void *q : ptrs)
         if (q) cudaFree(q);
@@ -583,11 +593,10 @@ const long long *pme_sums_acc(const nb_ctx *ctx) { return ctx->pme ? ctx->pme->a
 double pme_self_coef(const nb_ctx *ctx) { return ctx->pme ? ctx->pme->self_coef : 0.0; }
 
 template <int N>
-static cudaError_t launch_pme_t(nb_ctx *ctx, const float *d_pos, const float *d_q)
+static cudaError_t launch_pme_t(nb_ctx *ctx, cudaStream_t st, const float *d_pos, const float *d_q)
 {
     PmeState &P = *ctx->pme;
     const PmeGeom &g = P.g;
-    const cudaStream_t st = ctx->stream;
     auto &d = ctx->d;
     const dim3 sgrid(g.K1, (g.K2 + g.Ty - 1) / g.Ty);
     const size_t smem = 2 * sizeof(int) * g.Ty * g.K3;
@@ -613,14 +622,34 @@ static cudaError_t launch_pme_t(nb_ctx *ctx, const float *d_pos, const float *d_
                       (const float *)P.grid, (const int *)d.part_orig, ctx->K, P.pacc, P.acc, d.status);
 }
 
-cudaError_t launch_pme(nb_ctx *ctx, const float *d_pos, const float *d_q)
+static cudaError_t launch_pme_on(nb_ctx *ctx, cudaStream_t st, const float *d_pos, const float *d_q)
 {
     switch (ctx->pme->order) {
-    case 4: return launch_pme_t<4>(ctx, d_pos, d_q);
-    case 6: return launch_pme_t<6>(ctx, d_pos, d_q);
-    case 8: return launch_pme_t<8>(ctx, d_pos, d_q);
+    case 4: return launch_pme_t<4>(ctx, st, d_pos, d_q);
+    case 6: return launch_pme_t<6>(ctx, st, d_pos, d_q);
+    case 8: return launch_pme_t<8>(ctx, st, d_pos, d_q);
     default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_pme(nb_ctx *ctx, const float *d_pos, const float *d_q)
+{
+    return launch_pme_on(ctx, ctx->stream, d_pos, d_q);
+}
+
+cudaError_t launch_pme_fork(nb_ctx *ctx, const float *d_pos, const float *d_q)
+{
+    PmeState &P = *ctx->pme;
+    cudaError_t e = cudaEventRecord(P.fork, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(P.side, P.fork, 0);
+    if (e == cudaSuccess) e = launch_pme_on(ctx, P.side, d_pos, d_q);
+    if (e == cudaSuccess) e = cudaEventRecord(P.join, P.side);
+    return e;
+}
+
+cudaError_t launch_pme_join(nb_ctx *ctx)
+{
+    return cudaStreamWaitEvent(ctx->stream, ctx->pme->join, 0);
 }
 
 }  // namespace acenb
@@ -690,6 +719,9 @@ extern "C" nb_status nb_set_pme(nb_ctx *ctx, const nb_pme_params *p)
     if (e == cudaSuccess) e = cudaMalloc(&P->pacc, sizeof(long long) * 3 * std::max<int64_t>(ctx->slot_cap, 1));
     if (e == cudaSuccess) e = cudaMalloc(&P->acc, sizeof(long long) * kPmeAcc);
     if (e == cudaSuccess) e = cudaMemset(P->acc, 0, sizeof(long long) * kPmeAcc);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->join, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         pme_free(ctx);
         return e == cudaErrorMemoryAllocation ? NB_ERR_OOM : NB_ERR_CUDA;
