@@ -15,7 +15,7 @@ once before timing).  The JSON line also carries the roofline of the force
 kernel (FP32 pipe; 73 algorithmic FLOP per pair), the end-to-end number
 through host buffers, the adjoint and batched forms, the step with smooth
 PME added, the step with tabulated radial functions, the molecular-dynamics
-step (ns/day), clocks, and the FP64 oracle timed on the host cores (context
+step (ns/day), the 1 M-atom water box, clocks, and the FP64 oracle timed on the host cores (context
 only).
 
 Multi-GPU: every rank evaluates its own replica (no data-path collective);
@@ -55,6 +55,12 @@ MD_WATERS = 7833  # 23,499 atoms in 61.7 A, the size of the paper's DHFR system
 # MD step: kick/drift, M-SHAKE, rebuild, forces, PME, (bonded), kick, RATTLE, finish
 MD_LAUNCHES = 1 + 1 + BUILD_LAUNCHES + FORCE_LAUNCHES + PME_LAUNCHES + 1 + 1 + 1
 FLOP_PER_PAIR = 73  # LJ + switch + Ewald real space, FMA = 2, MUFU = 1
+# algorithmic DRAM bytes of one rebuild per atom: positions in (12), wrapped
+# coordinates and column out and back (20 + 20), scatter slot (8), sorted
+# x,y,z,q + permutation + inverse (24), cluster boxes (4 per atom), z-bin
+# index (~4), pair lists (two halves of ~66 4-byte entries per 8-atom
+# cluster: 66)
+BUILD_BYTES_PER_ATOM = 158
 WORKLOAD = ("solvated-chain system, 23,500 atoms (2,500-atom chain + 7,000 TIP3P-shaped waters), "
             "62.2 A cubic box, rc 9 A, switch 7.5 A, Ewald alpha 0.32, 1-2/1-3 excluded, 1-4 scaled")
 
@@ -72,6 +78,7 @@ def parse():
     ap.add_argument("--tables-only", action="store_true",
                     help="time only the step with tabulated radial functions (for profiling)")
     ap.add_argument("--md-only", action="store_true", help="time only the MD leg (for profiling)")
+    ap.add_argument("--large-only", action="store_true", help="time only the 1 M-atom leg (for profiling)")
     return ap.parse_args()
 
 
@@ -325,6 +332,59 @@ def md_leg(steps, flush, dev):
             "gpu_launches_per_step": MD_LAUNCHES + (1 if len(top.bonds) + len(top.angles) + len(top.dihedrals) else 0)}
 
 
+def large_leg(steps, flush, dev):
+    """The 999,999-atom water box (333,333 waters, L ~ 215 A): rebuild +
+    forces every step, the rebuild alone and the force evaluation alone,
+    each replayed from a CUDA graph with the L2 flushed before every step;
+    the force kernel's FP32 roofline and the rebuild's algorithmic DRAM
+    bandwidth (BUILD_BYTES_PER_ATOM per atom)."""
+    import torch
+    from paper_0902_0827_gb300 import nb
+    from paper_0902_0827_gb300 import systems as S
+    s = S.big_water()
+    ctx = nb.Nonbonded(s)
+    pos, q, typ = nb.concat_inputs([s], device=dev)
+    N = s.n_atoms
+    F = torch.empty((N, 3), dtype=torch.float32, device=dev)
+    E = torch.empty((1, 2), dtype=torch.float64, device=dev)
+    W = torch.empty((1, 6), dtype=torch.float64, device=dev)
+
+    def step():
+        ctx.build(pos)
+        ctx.forces(pos, q, typ, F=F, energy=E, virial=W)
+
+    def bstep():
+        ctx.build(pos)
+
+    def fstep():
+        ctx.forces(pos, q, typ, F=F, energy=E, virial=W)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    _, npairs, _ = ctx.debug_pairs(cap=0)
+    reps = max(3, steps // 5)
+    ms = time_steps(graph_of(step, dev).replay, reps, flush)
+    b_ms = time_steps(graph_of(bstep, dev).replay, reps, flush)
+    ctx.build(pos)
+    f_ms = time_steps(graph_of(fstep, dev).replay, reps, flush)
+    ctx.set_profiling(True)
+    ctx.profile()
+    for _ in range(reps):
+        flush.zero_()
+        fstep()
+    kms, kl = ctx.profile()
+    ctx.set_profiling(False)
+    ctx.status()
+    k_avg = kms / max(kl, 1)
+    return {"n_atoms": N, "pairs_per_step": npairs, "ms_per_step": ms, "pairs_per_s": npairs / (ms * 1e-3),
+            "rebuild_ms": b_ms, "force_eval_ms": f_ms, "force_kernel_ms": k_avg,
+            "force_kernel_tflops": FLOP_PER_PAIR * npairs / (k_avg * 1e-3) / 1e12,
+            "rebuild_algorithmic_gbs": BUILD_BYTES_PER_ATOM * N / (b_ms * 1e-3) / 1e9,
+            "step": "cell-list rebuild + forces, energies and virial (rc 9 A, Ewald real space)",
+            "gpu_launches_per_step": BUILD_LAUNCHES + FORCE_LAUNCHES}
+
+
 def batched_leg(steps, flush, dev):
     """64 water boxes (log-uniform 500..20,000 atoms): one autotuned,
     graph-captured rebuild + force step of the whole batch vs 64 sequential
@@ -456,9 +516,11 @@ def main():
     props = torch.cuda.get_device_properties(dev)
     n_sms = props.multi_processor_count
     s = S.solvated_chain()
-    if args.pme_only or args.tables_only or args.md_only:
+    if args.pme_only or args.tables_only or args.md_only or args.large_only:
         flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)
-        if args.pme_only:
+        if args.large_only:
+            print(json.dumps({"large": large_leg(args.steps, flush, dev)}))
+        elif args.pme_only:
             print(json.dumps({"pme": pme_leg(s, args.steps, flush, dev, 0, 0.0)}))
         elif args.md_only:
             print(json.dumps({"md": md_leg(args.steps, flush, dev)}))
@@ -569,6 +631,7 @@ def main():
         line["tables"] = tables_leg(s, args.steps, flush, dev, npairs, ms, fo_ms)
         line["md"] = md_leg(args.steps, flush, dev)
         line["batched"] = batched_leg(args.steps, flush, dev)
+        line["large"] = large_leg(args.steps, flush, dev)
         # end to end through the public API with host buffers (pinned): the
         # step's inputs (positions, charges, types) travel in one host->device
         # copy and its results (forces, energies, virial) in one
