@@ -100,13 +100,15 @@ typedef struct {
 
 /* Tuning knobs (chosen by the autotuner; defaults are safe). */
 typedef struct {
-    int32_t blocks_per_sm;  /* blocks per SM of the persistent force grid, 1..8 */
-    int32_t stage_capacity; /* cluster-pair entries staged in shared memory per block pass,
-                               16..512, multiple of 4 (longer lists are processed in chunks) */
+    int32_t blocks_per_sm;  /* blocks per SM of the persistent force grids, 1..8 */
+    int32_t stage_capacity; /* adjoint kernel: cluster-pair entries staged in shared memory per
+                               block pass, 16..512, multiple of 4 (longer lists are processed
+                               in chunks) */
     int32_t list_capacity;  /* entries of each half of a cluster's pair list (the half the
                                forward kernel visits, and the other half), 64..65536,
                                multiple of 4 */
-    int32_t reserved;       /* must be 0 */
+    int32_t list_split;     /* forward kernel: work units (warps) per cluster's half list,
+                               1..8; 0 = default (4) */
 } nb_tuning;
 
 /* nb_create - one system.  Copies params, validates them (box/cutoff ratio,

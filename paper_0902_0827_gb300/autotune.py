@@ -1,12 +1,15 @@
-"""Autotuner of the launch configuration (persistent-grid size, staging
-capacity) of a context.
+"""Autotuner of the launch configuration (persistent-grid size, work units
+per cluster list) of a context.
 
 Each candidate is timed with CUDA events over a few rebuild + force
 evaluations on the caller's stream; the fastest is applied and cached per
 (device, size bucket, number of systems).  The candidates only change how
-work is split (block count, shared-memory chunking of each cluster's list),
-never the arithmetic, so every candidate gives results within the parity
-tolerances; the choice is deterministic for a given cache.
+work is split (block count, number of warps sharing each cluster's list).
+The block count changes no result bit; the list split changes where a
+cluster's FP32 force sums are cut before they join the fixed-point totals,
+so results differ between splits by FP32 rounding only (every candidate is
+within the parity tolerances, and each is run-to-run bit-identical).  The
+choice is deterministic for a given cache.
 """
 
 from __future__ import annotations
@@ -17,8 +20,8 @@ import os
 
 _CACHE: dict = {}
 
-DEFAULT_CANDIDATES = [dict(blocks_per_sm=b, stage_capacity=s)
-                      for b in (1, 2, 3, 4) for s in (64, 96, 128, 160, 192, 256)]
+DEFAULT_CANDIDATES = [dict(blocks_per_sm=b, list_split=s)
+                      for b in (2, 3, 4) for s in (1, 2, 3, 4, 6, 8)]
 
 
 def _key(ctx) -> str:

@@ -230,7 +230,7 @@ nb_status nb_create_batch(int32_t n_sys, const nb_params *params, void *cuda_str
     c->tune.blocks_per_sm = 3;
     c->tune.stage_capacity = 96;
     c->tune.list_capacity = 512;
-    c->tune.reserved = 0;
+    c->tune.list_split = kDefaultListSplit;
     c->stage_cap = c->tune.stage_capacity;
     c->list_cap = c->tune.list_capacity;
     int smem_optin = 0;
@@ -465,7 +465,7 @@ void nb_destroy(nb_ctx *ctx)
 nb_status nb_set_tuning(nb_ctx *ctx, const nb_tuning *t)
 {
     if (!ctx || !t) return NB_ERR_INVALID_ARG;
-    if (t->blocks_per_sm < 1 || t->blocks_per_sm > 8 || t->reserved != 0) return NB_ERR_INVALID_ARG;
+    if (t->blocks_per_sm < 1 || t->blocks_per_sm > 8 || t->list_split < 0 || t->list_split > 8) return NB_ERR_INVALID_ARG;
     if (t->stage_capacity < 16 || t->stage_capacity > 512 || t->stage_capacity % 4) return NB_ERR_INVALID_ARG;
     if (t->list_capacity < 64 || t->list_capacity > 65536 || t->list_capacity % 4) return NB_ERR_INVALID_ARG;
     if (ctx->smem_optin > 0 && force_smem_for(ctx->pp.n_types, t->stage_capacity, ctx->K) > (size_t)ctx->smem_optin)

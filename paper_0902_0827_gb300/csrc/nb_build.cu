@@ -326,7 +326,8 @@ __device__ __forceinline__ int window_candidate(const float4 *__restrict__ bb, f
 }
 
 // Bit of a cluster index in the 64-bit partner-cluster filter (multiplicative
-// hash).
+// hash of the index within the cluster's system, so that a system's lists
+// and flags do not depend on the other systems of a batch).
 __device__ __forceinline__ unsigned bloom_bit(int c) { return ((unsigned)c * 0x9E3779B1u) >> 26; }
 
 constexpr int kListWarps = 8;   // warps (clusters in flight) per block of the list kernel
@@ -393,7 +394,7 @@ __global__ void __launch_bounds__(kListWarps * 32)
         }
 #pragma unroll
         for (int r = 0; r < kPartnerRounds; ++r)
-            if (pv[r] >= 0) bloom |= 1ull << bloom_bit((pv[r] >> 1) / kCluster);
+            if (pv[r] >= 0) bloom |= 1ull << bloom_bit((pv[r] >> 1) / kCluster - S.clus_begin);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) bloom |= __shfl_xor_sync(FULL, bloom, o);
         const int cxa = max(-S.nx, (int)floorf((lo.x - rcm) * S.inv_w[0]));
@@ -498,7 +499,7 @@ __global__ void __launch_bounds__(kListWarps * 32)
                     }
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
-                        const bool fl = J[h] >= 0 && ((bloom >> bloom_bit(J[h])) & 1ull);
+                        const bool fl = J[h] >= 0 && ((bloom >> bloom_bit(J[h] - S.clus_begin)) & 1ull);
                         const uint32_t ent = (uint32_t)J[h] | (code[h] << kShiftBit) | (fl ? kExclFlag : 0u);
                         const bool hitA = J[h] >= 0 && keep_half(I, J[h], code[h]), hitB = J[h] >= 0 && !hitA;
                         const unsigned bA = __ballot_sync(FULL, hitA), bB = __ballot_sync(FULL, hitB);

@@ -45,6 +45,7 @@ constexpr int kAdjStage = 64;  // staging capacity cap of the adjoint (its large
 struct ForceArgs {
     const SysDesc *sys;
     const int *counts;
+    int *work;                // forward tile kernel: work-unit counter (zeroed by k_pack)
     const float4 *xyzq;
     const int *tslot;
     const int *perm;
@@ -372,14 +373,16 @@ __device__ __forceinline__ void eval_pair(const PairParams &P, const float2 *__r
     const float wlj = is14 ? P.s14_lj : 1.0f;
     const float wc = is14 ? P.s14_c : 1.0f;
     // F_i = U'(r) d / r = -fs d with fs = -U'(r) / r
-    float fs = fmaf(wlj, frlj, wc * frc) * (rinv * rinv);
+    float fs = __fmul_rn(__fmaf_rn(wlj, frlj, __fmul_rn(wc, frc)), __fmul_rn(rinv, rinv));
     fs = in ? fs : 0.0f;
-    acc.elj += in ? wlj * elj : 0.0f;
-    acc.ec += in ? wc * ec : 0.0f;
-    const float fdx = fs * dx, fdy = fs * dy, fdz = fs * dz;
-    acc.fx -= fdx;
-    acc.fy -= fdy;
-    acc.fz -= fdz;
+    acc.elj = __fadd_rn(acc.elj, in ? __fmul_rn(wlj, elj) : 0.0f);
+    acc.ec = __fadd_rn(acc.ec, in ? __fmul_rn(wc, ec) : 0.0f);
+    // rounded products and sums written out (never contracted to FMA), so
+    // the result does not depend on how the caller's code was inlined
+    const float fdx = __fmul_rn(fs, dx), fdy = __fmul_rn(fs, dy), fdz = __fmul_rn(fs, dz);
+    acc.fx = __fsub_rn(acc.fx, fdx);
+    acc.fy = __fsub_rn(acc.fy, fdy);
+    acc.fz = __fsub_rn(acc.fz, fdz);
     fjx = fdx;  // F_j = -F_i
     fjy = fdy;
     fjz = fdz;
@@ -831,16 +834,367 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
     if (cur_sys >= 0) flush_energy<VIRIAL>(A, S, wacc, cur_sys, lane);
 }
 
+// ---------------------------------------------------------------------------
+// Forward kernel on cluster-pair tiles.
+//
+// One warp evaluates one listed cluster pair (I, J) at a time as an 8 x 8
+// tile: lane = jj + 8 ih holds j atom jj of J and the i atoms ih and ih + 4
+// of I, so every lane computes two pairs and the tile needs no compaction:
+// pairs beyond the cutoff (and excluded pairs, padding) are evaluated and
+// masked.  The force on i stays in the lane's registers for the whole list;
+// the force on j (two pairs per lane) is summed over the 4 lanes of that j
+// atom with shuffles and added to the global 64-bit fixed-point sums, one
+// atomic per atom and component, as is the force on i once the list is done.
+// The FP32 sums run in a fixed order and meet only in integer sums, so
+// results are run-to-run bit-identical.  A cluster's half list is cut into
+// `parts` work units, which the warps of a persistent grid claim from a
+// counter (dynamic balance of the uneven list lengths); the next unit's
+// claim, the next entry's j atoms and the next 32 list entries are loaded
+// ahead of use.
+constexpr int kTileWarps = 8;            // warps per block of the tile kernel
+#ifndef ACENB_TILE_MIN_BLOCKS
+#define ACENB_TILE_MIN_BLOCKS 3          // resident blocks per SM the register budget is cut for
+#endif
+constexpr float kFarCoord = 3.0e18f;     // i-side padding: far from every atom and from the j-side padding
+
+// One i atom of a lane: coordinates, ke q_i, type row.
+struct TileI {
+    float x, y, z, q;
+    int trow;
+    int orig;  // caller index (pair export)
+};
+
+__device__ __forceinline__ TileI load_tile_i(const ForceArgs &A, long long slot, int T, bool debug)
+{
+    float4 p = __ldg(A.xyzq + slot);
+    if (!is_real_coord(p.x)) p.x = p.y = p.z = kFarCoord;
+    TileI t;
+    t.x = p.x;
+    t.y = p.y;
+    t.z = p.z;
+    t.q = p.w * A.P.ke;
+    t.trow = __ldg(A.tslot + slot) * T;
+    t.orig = debug ? __ldg(A.perm + slot) : -1;
+    return t;
+}
+
+// Fixed-point value (2^32) of a j-force sum; a value too large for the sums
+// (or not finite) adds zero and sets ovf.
+__device__ __forceinline__ long long tile_fixed(float f, bool &ovf)
+{
+    const bool ok = fabsf(f) < 67108864.0f;
+    ovf = ovf || !ok;
+    return __float2ll_rn((ok ? f : 0.0f) * 4294967296.0f);
+}
+
+// Membership of one pair of a tile: the i atom at its image for the entry's
+// shift code (IMG: x_i - L on axes with code 2; the j side was shifted by
+// the caller), d = x_j - x_i and the FP32 predicate r2 < rc2 of the other
+// kernels.
+template <bool IMG>
+__device__ __forceinline__ bool tile_member(const ForceArgs &A, const TileI &ti, uint32_t code, float4 pj, float Lx,
+                                            float Ly, float Lz, float &dx, float &dy, float &dz, float &r2)
+{
+    float ax = ti.x, ay = ti.y, az = ti.z;
+    if (IMG) {
+        if ((code & 3u) == 2u) ax = __fsub_rn(ax, Lx);
+        if (((code >> 2) & 3u) == 2u) ay = __fsub_rn(ay, Ly);
+        if ((code >> 4) == 2u) az = __fsub_rn(az, Lz);
+    }
+    r2 = disp_r2(pj.x, pj.y, pj.z, ax, ay, az, dx, dy, dz);
+    return r2 < A.P.rc2;
+}
+
+// Masked evaluation of one pair of a tile (see eval_pair); the force on j
+// is added to fj.
+template <int RAD, bool SPECIAL, bool DEBUG>
+__device__ __forceinline__ void tile_eval(const ForceArgs &A, const float2 *__restrict__ lj, const TileI &ti, bool in,
+                                          float dx, float dy, float dz, float r2, float4 pj, int tj, bool is14,
+                                          int jorig, Acc &acc, float &fjx, float &fjy, float &fjz)
+{
+    if (DEBUG && in) {
+        atomicAdd((unsigned long long *)&A.dbg_n[0], 1ull);
+        const long long q = (long long)atomicAdd((unsigned long long *)&A.dbg_n[1], 1ull);
+        if (q < A.dbg_cap) {
+            A.dbg_ij[2 * q] = min(ti.orig, jorig);
+            A.dbg_ij[2 * q + 1] = max(ti.orig, jorig);
+        }
+    }
+    float gx, gy, gz;
+    eval_pair<RAD>(A.P, lj, A.rtab, ti.trow, ti.q, in, dx, dy, dz, in ? r2 : 1.0f, pj.w, tj, SPECIAL && is14, acc, gx,
+                   gy, gz);
+    fjx = __fadd_rn(fjx, gx);
+    fjy = __fadd_rn(fjy, gy);
+    fjz = __fadd_rn(fjz, gz);
+}
+
+// One listed cluster J against the lane's two i atoms.  The tile's i atoms
+// are z-sorted, so the lower half (atoms 0..3, pair A of every lane) and the
+// upper half (4..7, pair B) are often not both within the cutoff of J: the
+// membership of both pairs comes first, and the radial arithmetic of a half
+// runs only when one of its 32 pairs is in range (warp vote).  SPECIAL
+// entries are I's own cluster (pairs j > i only) and entries flagged as
+// holding a topology partner (exclusions removed, 1-4 pairs scaled); IMG
+// entries have a periodic shift code.  (Each kind has its own code: the
+// plain kind, most entries, then carries no weights or image selects.)
+template <int RAD, bool VIRIAL, bool DEBUG, bool SPECIAL, bool IMG>
+__device__ __forceinline__ void tile_entry(const ForceArgs &A, const float2 *__restrict__ lj,
+                                           const int *__restrict__ spart, int I, uint32_t ent, float4 pj, int tj,
+                                           const TileI &ia, const TileI &ib, int jj, int ih, float Lx, float Ly,
+                                           float Lz, Acc &acA, Acc &acB, float (&wimg)[6], bool &ovf)
+{
+    const int J = (int)(ent & kJMask);
+    const uint32_t code = IMG ? (ent >> kShiftBit) & 0x3Fu : 0u;
+    if (IMG) {  // j-side images (code 1): fl(x_j - L), as the other kernels stage them
+        if ((code & 3u) == 1u) pj.x = __fsub_rn(pj.x, Lx);
+        if (((code >> 2) & 3u) == 1u) pj.y = __fsub_rn(pj.y, Ly);
+        if ((code >> 4) == 1u) pj.z = __fsub_rn(pj.z, Lz);
+    }
+    float dxA, dyA, dzA, r2A, dxB, dyB, dzB, r2B;
+    bool inA = tile_member<IMG>(A, ia, code, pj, Lx, Ly, Lz, dxA, dyA, dzA, r2A);
+    bool inB = tile_member<IMG>(A, ib, code, pj, Lx, Ly, Lz, dxB, dyB, dzB, r2B);
+    bool s14A = false, s14B = false;
+    if (SPECIAL) {
+        if (J == I && code == 0u) {
+            inA = inA && jj > ih;
+            inB = inB && jj > ih + 4;
+        }
+        if (ent & kExclFlag) {
+            const int jslot = J * kCluster + jj;
+            for (int m = 0; m < A.K; ++m) {
+                const int pa = spart[ih * A.K + m], pb = spart[(ih + 4) * A.K + m];
+                if (pa >= 0 && (pa >> 1) == jslot) {
+                    if (pa & 1) s14A = true;
+                    else inA = false;
+                }
+                if (pb >= 0 && (pb >> 1) == jslot) {
+                    if (pb & 1) s14B = true;
+                    else inB = false;
+                }
+            }
+        }
+    }
+    const bool anyA = __any_sync(kFull, inA), anyB = __any_sync(kFull, inB);
+    if (!anyA && !anyB) return;
+    const int jorig = DEBUG ? __ldg(A.perm + (long long)J * kCluster + jj) : -1;
+    float fjx = 0.0f, fjy = 0.0f, fjz = 0.0f;
+    if (anyA) tile_eval<RAD, SPECIAL, DEBUG>(A, lj, ia, inA, dxA, dyA, dzA, r2A, pj, tj, s14A, jorig, acA, fjx, fjy, fjz);
+    if (anyB) tile_eval<RAD, SPECIAL, DEBUG>(A, lj, ib, inB, dxB, dyB, dzB, r2B, pj, tj, s14B, jorig, acB, fjx, fjy, fjz);
+    // the force on j atom jj: sum over its 4 lanes, then lanes ih = 0, 1, 2
+    // add the x, y, z components
+#pragma unroll
+    for (int o = 8; o < 32; o <<= 1) {
+        fjx = __fadd_rn(fjx, __shfl_xor_sync(kFull, fjx, o));
+        fjy = __fadd_rn(fjy, __shfl_xor_sync(kFull, fjy, o));
+        fjz = __fadd_rn(fjz, __shfl_xor_sync(kFull, fjz, o));
+    }
+    const float fc = ih == 0 ? fjx : (ih == 1 ? fjy : fjz);
+    if (ih < 3)
+        atomicAdd((unsigned long long *)&A.facc[24ll * J + 3 * jj + ih], (unsigned long long)tile_fixed(fc, ovf));
+    if (VIRIAL && IMG && ih == 0) {
+        // periodic-image part of the virial: s (x) f_j with the entry's
+        // shift s of j (code 1: -L, code 2: +L per axis)
+        const uint32_t cx = code & 3u, cy = (code >> 2) & 3u, cz = code >> 4;
+        const float sx = cx == 1u ? -Lx : (cx == 2u ? Lx : 0.0f);
+        const float sy = cy == 1u ? -Ly : (cy == 2u ? Ly : 0.0f);
+        const float sz = cz == 1u ? -Lz : (cz == 2u ? Lz : 0.0f);
+        wimg[0] = __fmaf_rn(sx, fjx, wimg[0]);
+        wimg[1] = __fmaf_rn(sy, fjy, wimg[1]);
+        wimg[2] = __fmaf_rn(sz, fjz, wimg[2]);
+        wimg[3] = __fmaf_rn(sx, fjy, wimg[3]);
+        wimg[4] = __fmaf_rn(sx, fjz, wimg[4]);
+        wimg[5] = __fmaf_rn(sy, fjz, wimg[5]);
+    }
+}
+
+// The image virial of a work unit (FP32 per lane) to the warp's fixed-point
+// sums (2^20): lane k < 6 holds component k in wv.  Rounded per unit, so the
+// sums do not depend on which warp took which unit.
+__device__ __forceinline__ void tile_virial_unit(float (&wimg)[6], long long &wv, int lane)
+{
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        long long x = __float2ll_rn(wimg[k] * (float)kVirScale);
+        wimg[k] = 0.0f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+        if (lane == k) wv += x;
+    }
+}
+
+// Warp sums of a system's energies (2^32) and image virial (2^20); clears
+// the per-lane sums.
+template <bool VIRIAL>
+__device__ __forceinline__ void tile_warp_sums(long long (&e)[2], long long &wv, long long (&out)[kTaskVals])
+{
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        long long x = e[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+        out[k] = x;
+    }
+    if (VIRIAL)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) out[2 + k] = __shfl_sync(kFull, wv, k);
+    e[0] = e[1] = 0;
+    wv = 0;
+}
+
+template <int RAD, bool VIRIAL, bool DEBUG>
+__global__ void __launch_bounds__(kTileWarps * 32, ACENB_TILE_MIN_BLOCKS) k_force_tile(ForceArgs A, int parts)
+{
+    pdl_entry();
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long s_val[kTileWarps][kTaskVals];
+    __shared__ int s_sys[kTileWarps];
+    const int T = A.P.n_types;
+    const int K = A.K;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, jj = lane & 7, ih = lane >> 3;
+    float2 *lj = reinterpret_cast<float2 *>(smem);
+    int *spart = reinterpret_cast<int *>(smem + align16((size_t)T * T * 8)) + w * kCluster * K;
+    for (int k = threadIdx.x; k < T * T; k += blockDim.x) lj[k] = A.lj_tab[k];
+    __syncthreads();
+    const int n_units = A.counts[1] * parts;
+    int cur_sys = -1;
+    float Lx = 0.0f, Ly = 0.0f, Lz = 0.0f;
+    long long esum[2] = {0, 0};  // per lane: fixed-point energies of the current system
+    float wimg[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};  // image virial of the current unit
+    long long wv = 0;  // lane k < 6: fixed-point image virial component k of the current system
+    bool ovf = false;  // a j-force sum out of the fixed-point range
+    int u = 0;
+    if (lane == 0) u = atomicAdd(A.work, 1);
+    u = __shfl_sync(kFull, u, 0);
+    while (u < n_units) {
+        int u_next = 0;
+        if (lane == 0) u_next = atomicAdd(A.work, 1);  // claimed now, used after this unit
+        const int I = u / parts, part = u - I * parts;
+        const int sys_id = __ldg(A.clus_sys + I);
+        if (sys_id != cur_sys) {
+            if (!DEBUG && cur_sys >= 0) {
+                long long v[kTaskVals];
+                tile_warp_sums<VIRIAL>(esum, wv, v);
+                if (lane == 0)
+                    for (int k = 0; k < (VIRIAL ? kTaskVals : 2); ++k)
+                        if (v[k]) atomicAdd((unsigned long long *)&A.sys_acc[cur_sys * kTaskVals + k], (unsigned long long)v[k]);
+            }
+            cur_sys = sys_id;
+            Lx = A.sys[sys_id].L[0];
+            Ly = A.sys[sys_id].L[1];
+            Lz = A.sys[sys_id].L[2];
+        }
+        const int nA = __ldg(A.list_n + 2 * I);
+        const int per = (nA + parts - 1) / parts;
+        const int e_begin = min(nA, part * per), e_end = min(nA, e_begin + per);
+        if (e_begin < e_end) {
+            const long long s0 = (long long)I * kCluster;
+            const TileI ia = load_tile_i(A, s0 + ih, T, DEBUG);
+            const TileI ib = load_tile_i(A, s0 + ih + 4, T, DEBUG);
+            for (int t = lane; t < kCluster * K; t += 32) spart[t] = __ldg(A.pslot + s0 * K + t);
+            __syncwarp();
+            Acc acA = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, acB = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+            const uint32_t *row = A.list + 2ll * I * A.cap;
+            uint32_t ents = lane < e_end - e_begin ? __ldg(row + e_begin + lane) : 0u;
+            for (int e0 = e_begin; e0 < e_end; e0 += 32) {
+                const int ne = min(32, e_end - e0);
+                const uint32_t cur_ents = ents;
+                if (e0 + 32 < e_end)  // the next 32 entries, ahead of use
+                    ents = lane < e_end - e0 - 32 ? __ldg(row + e0 + 32 + lane) : 0u;
+                uint32_t ent_n = __shfl_sync(kFull, cur_ents, 0);
+                float4 pj_n = __ldg(A.xyzq + (long long)(ent_n & kJMask) * kCluster + jj);
+                int tj_n = __ldg(A.tslot + (long long)(ent_n & kJMask) * kCluster + jj);
+                for (int k = 0; k < ne; ++k) {
+                    const uint32_t ent = ent_n;
+                    const float4 pj = pj_n;
+                    const int tj = tj_n;
+                    if (k + 1 < ne) {  // the next entry's j atoms, ahead of use
+                        ent_n = __shfl_sync(kFull, cur_ents, k + 1);
+                        pj_n = __ldg(A.xyzq + (long long)(ent_n & kJMask) * kCluster + jj);
+                        tj_n = __ldg(A.tslot + (long long)(ent_n & kJMask) * kCluster + jj);
+                    }
+                    const bool img = ((ent >> kShiftBit) & 0x3Fu) != 0u;
+                    const bool special = (ent & kExclFlag) != 0u || ((int)(ent & kJMask) == I && !img);
+                    if (img) {
+                        if (special)
+                            tile_entry<RAD, VIRIAL, DEBUG, true, true>(A, lj, spart, I, ent, pj, tj, ia, ib, jj, ih,
+                                                                      Lx, Ly, Lz, acA, acB, wimg, ovf);
+                        else
+                            tile_entry<RAD, VIRIAL, DEBUG, false, true>(A, lj, spart, I, ent, pj, tj, ia, ib, jj, ih,
+                                                                       Lx, Ly, Lz, acA, acB, wimg, ovf);
+                    } else {
+                        if (special)
+                            tile_entry<RAD, VIRIAL, DEBUG, true, false>(A, lj, spart, I, ent, pj, tj, ia, ib, jj, ih,
+                                                                       Lx, Ly, Lz, acA, acB, wimg, ovf);
+                        else
+                            tile_entry<RAD, VIRIAL, DEBUG, false, false>(A, lj, spart, I, ent, pj, tj, ia, ib, jj, ih,
+                                                                        Lx, Ly, Lz, acA, acB, wimg, ovf);
+                    }
+                }
+            }
+            // force on the i atoms: fixed point per lane, summed over the 8
+            // lanes of each atom; lanes jj < 3 add atom ih, jj = 3..5 atom ih + 4
+            long long v[6] = {to_fixed(acA.fx, A.status), to_fixed(acA.fy, A.status), to_fixed(acA.fz, A.status),
+                              to_fixed(acB.fx, A.status), to_fixed(acB.fy, A.status), to_fixed(acB.fz, A.status)};
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1)
+#pragma unroll
+                for (int c = 0; c < 6; ++c) v[c] += __shfl_xor_sync(kFull, v[c], o);
+            long long mine = v[0];
+#pragma unroll
+            for (int c = 1; c < 6; ++c) mine = jj == c ? v[c] : mine;
+            if (jj < 6 && mine != 0) {
+                const long long slot = s0 + ih + (jj < 3 ? 0 : 4);
+                atomicAdd((unsigned long long *)&A.facc[3 * slot + (jj < 3 ? jj : jj - 3)], (unsigned long long)mine);
+            }
+            esum[0] += to_fixed(acA.elj, A.status) + to_fixed(acB.elj, A.status);
+            esum[1] += to_fixed(acA.ec, A.status) + to_fixed(acB.ec, A.status);
+            if (VIRIAL) tile_virial_unit(wimg, wv, lane);
+            if (__any_sync(kFull, ovf)) {
+                if (lane == 0) atomicOr(A.status, ST_OVERFLOW);
+                ovf = false;
+            }
+            __syncwarp();  // spart is rewritten by the next unit
+        }
+        u = __shfl_sync(kFull, u_next, 0);
+    }
+    if (DEBUG) return;
+    // the block's sums: one atomic per value for the system most warps
+    // ended in, direct atomics for any other
+    long long v[kTaskVals];
+    tile_warp_sums<VIRIAL>(esum, wv, v);
+    if (lane == 0) {
+        s_sys[w] = cur_sys;
+        for (int k = 0; k < kTaskVals; ++k) s_val[w][k] = k < (VIRIAL ? kTaskVals : 2) ? v[k] : 0;
+    }
+    __syncthreads();
+    if (threadIdx.x < (VIRIAL ? kTaskVals : 2)) {
+        const int k = threadIdx.x;
+        const int nw = blockDim.x >> 5;
+        int base = -1;
+        long long sum = 0;
+        for (int q = 0; q < nw; ++q) {
+            const int sq = s_sys[q];
+            if (sq < 0) continue;
+            if (base < 0) base = sq;
+            if (sq == base) sum += s_val[q][k];
+            else if (s_val[q][k]) atomicAdd((unsigned long long *)&A.sys_acc[sq * kTaskVals + k], (unsigned long long)s_val[q][k]);
+        }
+        if (base >= 0 && sum) atomicAdd((unsigned long long *)&A.sys_acc[base * kTaskVals + k], (unsigned long long)sum);
+    }
+}
+
 // Gather charges and types into sorted order and check that the positions
 // are those of the last build.
 __global__ void k_pack(int slot_cap, const int *__restrict__ counts, const int *__restrict__ perm,
                        float4 *__restrict__ xyzq, int *__restrict__ tslot, const float *__restrict__ pos,
                        const float *__restrict__ q, const int *__restrict__ type, const SysDesc *__restrict__ sys,
                        const int *__restrict__ atom_sys, int T, int *__restrict__ status,
-                       long long *__restrict__ facc, long long *__restrict__ sys_acc, int n_acc)
+                       long long *__restrict__ facc, long long *__restrict__ sys_acc, int n_acc,
+                       int *__restrict__ work)
 {
     pdl_entry();
     int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (work && s == 0) *work = 0;  // the force kernel's work-unit counter
     // zero the force kernel's fixed-point sums (forward calls pass them)
     if (facc && s < slot_cap) {
         facc[3ll * s] = 0;
@@ -1040,6 +1394,27 @@ static void launch_force_t(nb_ctx *ctx, const ForceArgs &A)
     launch_pdl(k_force<ADJ, RAD, VIRIAL, DEBUG>, dim3(grid), dim3(nw * 32), smem, ctx->stream, A);
 }
 
+size_t tile_smem_bytes(int T, int K) { return align16((size_t)T * T * 8) + (size_t)kTileWarps * kCluster * K * 4; }
+
+template <int RAD, bool VIRIAL, bool DEBUG>
+static void launch_tile_t(nb_ctx *ctx, const ForceArgs &A)
+{
+    const size_t smem = tile_smem_bytes(A.P.n_types, A.K);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_force_tile<RAD, VIRIAL, DEBUG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
+        attr_set = true;
+    }
+    // persistent grid: never more blocks than can be resident at once
+    int resident = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_force_tile<RAD, VIRIAL, DEBUG>, kTileWarps * 32, smem);
+    const int per_sm = std::max(1, std::min(ctx->tune.blocks_per_sm, resident));
+    const int parts = ctx->tune.list_split > 0 ? ctx->tune.list_split : kDefaultListSplit;
+    launch_pdl(k_force_tile<RAD, VIRIAL, DEBUG>, dim3(ctx->num_sms * per_sm), dim3(kTileWarps * 32), smem,
+               ctx->stream, A, parts);
+}
+
 static ForceArgs make_args(nb_ctx *ctx)
 {
     auto &d = ctx->d;
@@ -1047,6 +1422,7 @@ static ForceArgs make_args(nb_ctx *ctx)
     memset(&A, 0, sizeof(A));
     A.sys = d.sys;
     A.counts = d.counts;
+    A.work = d.counts + 3;
     A.xyzq = d.xyzq;
     A.tslot = d.tslot;
     A.perm = d.perm;
@@ -1076,7 +1452,8 @@ cudaError_t launch_pack(nb_ctx *ctx, const float *d_pos, const float *d_q, const
     const int S = (int)ctx->slot_cap;
     return launch_pdl(k_pack, dim3((S + tb - 1) / tb), dim3(tb), 0, ctx->stream, S, d.counts, d.perm, d.xyzq,
                       d.tslot, d_pos, d_q, d_type, d.sys, d.atom_sys, ctx->pp.n_types, d.status,
-                      zero_sums ? d.facc : nullptr, zero_sums ? d.sys_acc : nullptr, kTaskVals * ctx->n_sys);
+                      zero_sums ? d.facc : nullptr, zero_sums ? d.sys_acc : nullptr, kTaskVals * ctx->n_sys,
+                      zero_sums ? d.counts + 3 : nullptr);
 }
 
 cudaError_t launch_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type, float *d_F,
@@ -1089,6 +1466,7 @@ cudaError_t launch_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, con
     } else {  // the debug pair export reuses the last packed values
         cudaMemsetAsync(d.sys_acc, 0, sizeof(long long) * kTaskVals * ctx->n_sys, ctx->stream);
         cudaMemsetAsync(d.facc, 0, sizeof(long long) * 3 * ctx->slot_cap, ctx->stream);
+        cudaMemsetAsync(d.counts + 3, 0, sizeof(int), ctx->stream);
     }
     // smooth PME: forked onto its own stream so that it overlaps the
     // short-range kernel; joined back before the unpack reads its sums
@@ -1105,17 +1483,17 @@ cudaError_t launch_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, con
     const bool prof = ctx->profiling && ctx->prof_n < (int)ctx->prof_ev.size() / 2;
     if (prof) cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n], ctx->stream);
     if (debug_pairs) {  // the pair set does not depend on the radial functions
-        if (ewald) launch_force_t<false, 1, false, true>(ctx, A);
-        else launch_force_t<false, 0, false, true>(ctx, A);
+        if (ewald) launch_tile_t<1, false, true>(ctx, A);
+        else launch_tile_t<0, false, true>(ctx, A);
     } else if (ctx->tab_n > 0) {
-        if (virial) launch_force_t<false, 2, true, false>(ctx, A);
-        else launch_force_t<false, 2, false, false>(ctx, A);
+        if (virial) launch_tile_t<2, true, false>(ctx, A);
+        else launch_tile_t<2, false, false>(ctx, A);
     } else if (ewald) {
-        if (virial) launch_force_t<false, 1, true, false>(ctx, A);
-        else launch_force_t<false, 1, false, false>(ctx, A);
+        if (virial) launch_tile_t<1, true, false>(ctx, A);
+        else launch_tile_t<1, false, false>(ctx, A);
     } else {
-        if (virial) launch_force_t<false, 0, true, false>(ctx, A);
-        else launch_force_t<false, 0, false, false>(ctx, A);
+        if (virial) launch_tile_t<0, true, false>(ctx, A);
+        else launch_tile_t<0, false, false>(ctx, A);
     }
     if (prof) {
         cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n + 1], ctx->stream);

@@ -16,6 +16,7 @@ constexpr int kCluster = 8;          // atoms per cluster (column chunk)
 constexpr int kMaxTypes = 64;        // type-pair table lives in shared memory
 constexpr int kMaxPartners = 16;     // exclusion + 1-4 partners per atom
 constexpr int kErfcDeg = 8;          // degree of the erfcx polynomial in t
+constexpr int kDefaultListSplit = 4; // forward kernel: work units per cluster list
 constexpr double kFixScale = 4294967296.0;   // 2^32: fixed-point scale
 constexpr int kTaskVals = 8;         // per system: E_lj, E_c (scale 2^32), W[6] (scale 2^20)
 constexpr double kVirScale = 1048576.0;      // 2^20: fixed-point scale of the virial sums
@@ -117,7 +118,7 @@ struct DevBuffers {
     int *pslot = nullptr;            // [S*K] partner slots (slot << 1) | is14, -1 pad
     int2 *zbin = nullptr;            // [zb_total] z-bin index of the columns (see SysDesc)
     long long *tab_grad = nullptr;   // [T*T*2] adjoint dL/dsig_ab, dL/deps_ab (fixed point, one ordered half)
-    int *counts = nullptr;           // [4]: n_slots, n_clusters, pair counters
+    int *counts = nullptr;           // [4]: n_slots, n_clusters, unpack ticket, forward work-unit counter
     int *status = nullptr;           // [1]
     float2 *lj_tab = nullptr;        // [T*T] (A, B)
     float4 *lj_d = nullptr;          // [T*T] 48 eps sig^11, 24 eps sig^5, 4 sig^12, 4 sig^6

@@ -3,17 +3,17 @@
 // velocity-Verlet integration, Langevin thermostat, M-SHAKE and RATTLE
 // constraints; section "Performance": the DHFR step with PME).
 //
-// One step of length dt from (x, v, F(x)), per atom unless noted:
-//   k_md_kick_drift  O: v <- c v + sigma xi (c = exp(-gamma dt/2),
-//                       sigma = sqrt((1 - c^2) kT / m)), B: v += dt/2 F/m,
-//                    A: x' = x + dt v
-//   k_md_shake       per rigid water: M-SHAKE (Newton on the 3 distance
-//                    equations with the reference bond vectors of x), then
-//                    x'' = x' + disp and v += disp / dt
+// One step of length dt from (x, v, F(x)); one thread per unconstrained atom
+// or per rigid water (its three atoms):
+//   k_md_first   O: v <- c v + sigma xi (c = exp(-gamma dt/2),
+//                sigma = sqrt((1 - c^2) kT / m)), B: v += dt/2 F/m,
+//                A: x' = x + dt v; waters then M-SHAKE (Newton on the 3
+//                distance equations with the reference bond vectors of x):
+//                x'' = x' + disp and v += disp / dt
 //   cell list, short-range forces (+ PME), k_md_bonded
-//   k_md_kick        B: v += dt/2 F/m, O: v <- c v + sigma xi'
-//   k_md_rattle      per rigid water: r_k . (v_a - v_b) = 0; kinetic energy
-//   k_md_finish      energies out; advances the device step counter
+//   k_md_second  B: v += dt/2 F/m, O: v <- c v + sigma xi'; waters then
+//                RATTLE (r_k . (v_a - v_b) = 0); kinetic energy; the last
+//                block writes the energies and advances the step counter
 // xi: Philox4x32-10 (Salmon et al. 2011) on the counter (atom, step,
 // stream, 0) and key (seed), 24-bit uniforms, Box-Muller.  Units kcal/mol,
 // A, amu, ps: F/m in kcal/mol/A/amu times 418.4 is A/ps^2.
@@ -29,7 +29,8 @@ namespace acenb {
 
 constexpr float kAccel = 418.4f;          // (A/ps)^2 per kcal/mol/amu
 constexpr double kBoltzmann = 0.0019872041;  // kcal/mol/K
-constexpr int kMdAcc = 8;                  // E_bond, E_angle, E_dihedral, E_kin (2^32), spare
+constexpr int kMdAcc = 8;                  // E_bond, E_angle, E_dihedral, E_kin (2^32), spare, ticket
+constexpr int kMdTicket = 7;               // blocks of the second half-step done
 
 struct MdState {
     int n = 0, nb = 0, na = 0, nd = 0, nw = 0;
@@ -43,7 +44,8 @@ struct MdState {
     // device
     float *mass = nullptr;                 // [N]
     float *sigv = nullptr;                 // [N] sqrt((1 - c^2) kT 418.4 / m)
-    int *water_of = nullptr;               // [N] water index or -1
+    int *free_atoms = nullptr;             // [n_free] atoms in no water (one integration thread each)
+    int n_free = 0;
     int2 *bonds = nullptr;                 // [nb]
     float2 *bond_p = nullptr;              // (k, r0)
     int4 *angles = nullptr;                // [na] (i, j, k, -)
@@ -51,7 +53,6 @@ struct MdState {
     int4 *dihedrals = nullptr;             // [nd]
     float4 *dihedral_p = nullptr;          // (k, n, delta, -)
     int4 *waters = nullptr;                // [nw] (O, H1, H2, -)
-    float *xn = nullptr;                   // [N*3] unconstrained positions of water atoms
     float *Fnb = nullptr;                  // [N*3] short-range (+ PME) forces of the last evaluation
     float *Ftot = nullptr;                 // [N*3] total forces at the current positions
     long long *bacc = nullptr;             // [N*3] bonded forces, fixed point 2^32
@@ -257,22 +258,15 @@ __global__ void k_md_collect(int n, const float *__restrict__ Fnb, long long *__
     collect_force(a, Fnb, bacc, Ftot, fx, fy, fz);
 }
 
-// O (stream 0), B, A.  Water atoms keep x and get x' in xn (for M-SHAKE);
-// the others get x' (wrapped into the box) in place.  Block 0 clears the
-// energy sums of this step.
-__global__ void k_md_kick_drift(int n, float dt, float c, bool langevin, unsigned long long seed,
-                                const unsigned long long *__restrict__ step, const float *__restrict__ mass,
-                                const float *__restrict__ sigv, const int *__restrict__ water_of,
-                                const float *__restrict__ Ftot, float *__restrict__ x, float *__restrict__ v,
-                                float *__restrict__ xn, Box3 B, long long *__restrict__ acc)
+// O (stream 0), B, A of atom a: returns x' = x + dt v (v updated in place).
+__device__ __forceinline__ float3 kick_drift(int a, float dt, float c, bool langevin, unsigned long long seed,
+                                             unsigned long long step, const float *__restrict__ mass,
+                                             const float *__restrict__ sigv, const float *__restrict__ Ftot,
+                                             const float *__restrict__ x, float *__restrict__ v)
 {
-    pdl_entry();
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (blockIdx.x == 0 && threadIdx.x < kMdAcc) acc[threadIdx.x] = 0;
-    if (a >= n) return;
     float vx = v[3ll * a], vy = v[3ll * a + 1], vz = v[3ll * a + 2];
     if (langevin) {
-        const float3 xi = md_normals((unsigned)a, step[0], 0u, seed);
+        const float3 xi = md_normals((unsigned)a, step, 0u, seed);
         const float s = sigv[a];
         vx = fmaf(c, vx, s * xi.x);
         vy = fmaf(c, vy, s * xi.y);
@@ -285,25 +279,40 @@ __global__ void k_md_kick_drift(int n, float dt, float c, bool langevin, unsigne
     v[3ll * a] = vx;
     v[3ll * a + 1] = vy;
     v[3ll * a + 2] = vz;
-    const float px = fmaf(dt, vx, x[3ll * a]), py = fmaf(dt, vy, x[3ll * a + 1]), pz = fmaf(dt, vz, x[3ll * a + 2]);
-    if (water_of[a] >= 0) {
-        xn[3ll * a] = px;
-        xn[3ll * a + 1] = py;
-        xn[3ll * a + 2] = pz;
-    } else {
-        x[3ll * a] = wrap_coord(px, B.L[0]);
-        x[3ll * a + 1] = wrap_coord(py, B.L[1]);
-        x[3ll * a + 2] = wrap_coord(pz, B.L[2]);
+    return make_float3(fmaf(dt, vx, x[3ll * a]), fmaf(dt, vy, x[3ll * a + 1]), fmaf(dt, vz, x[3ll * a + 2]));
+}
+
+// B and O (stream 1) of atom a with the new forces (v updated in place).
+__device__ __forceinline__ float3 kick(int a, float dt, float c, bool langevin, unsigned long long seed,
+                                       unsigned long long step, const float *__restrict__ mass,
+                                       const float *__restrict__ sigv, const float *__restrict__ Fnb,
+                                       long long *__restrict__ bacc, float *__restrict__ Ftot, float *__restrict__ v)
+{
+    float fx, fy, fz;
+    collect_force(a, Fnb, bacc, Ftot, fx, fy, fz);
+    const float h = 0.5f * dt * kAccel / mass[a];
+    float vx = fmaf(h, fx, v[3ll * a]), vy = fmaf(h, fy, v[3ll * a + 1]), vz = fmaf(h, fz, v[3ll * a + 2]);
+    if (langevin) {
+        const float3 xi = md_normals((unsigned)a, step, 1u, seed);
+        const float s = sigv[a];
+        vx = fmaf(c, vx, s * xi.x);
+        vy = fmaf(c, vy, s * xi.y);
+        vz = fmaf(c, vz, s * xi.z);
     }
+    v[3ll * a] = vx;
+    v[3ll * a + 1] = vy;
+    v[3ll * a + 2] = vz;
+    return make_float3(vx, vy, vz);
 }
 
 // Rigid water: constraint k joins (O, H1), (O, H2), (H1, H2).
-__device__ __constant__ int kCA[3] = {0, 0, 1};
-__device__ __constant__ int kCB[3] = {1, 2, 2};
+// (written as functions so that unrolled loops resolve them at compile time)
+__device__ __forceinline__ constexpr int con_a(int k) { return k == 2 ? 1 : 0; }
+__device__ __forceinline__ constexpr int con_b(int k) { return k == 0 ? 1 : 2; }
 
 // s(i, l): +1 if atom i (0 = O, 1 = H1, 2 = H2) is the first atom of
 // constraint l, -1 if the second, else 0.
-__device__ __forceinline__ float sgn(int i, int l) { return i == kCA[l] ? 1.0f : (i == kCB[l] ? -1.0f : 0.0f); }
+__device__ __forceinline__ float sgn(int i, int l) { return i == con_a(l) ? 1.0f : (i == con_b(l) ? -1.0f : 0.0f); }
 
 // 3 x 3 solve by the adjugate (the constraint systems are well conditioned).
 __device__ __forceinline__ void solve3(const float A[3][3], const float b[3], float x[3])
@@ -325,41 +334,70 @@ __device__ __forceinline__ void solve3(const float A[3][3], const float b[3], fl
     x[2] = i20 * b[0] + i21 * b[1] + i22 * b[2];
 }
 
-// M-SHAKE of one water per thread: lambda by Newton iterations on
-// |r_k''|^2 = d_k^2, r_k'' = u_k + sum_l lambda_l C_kl r_l (u: new, r:
-// reference vectors, C_kl = s(a_k, l)/m_{a_k} - s(b_k, l)/m_{b_k}); then
-// disp_i = sum_l lambda_l s(i, l) r_l / m_i.  Stops when every
-// |g_k| / d_k^2 < tol or after max_iter iterations.
-__global__ void k_md_shake(int nw, const int4 *__restrict__ waters, const float *__restrict__ mass, float d2oh,
-                           float d2hh, float tol, int max_iter, float dt, const float *__restrict__ xn,
-                           float *__restrict__ x, float *__restrict__ v, Box3 B, int *__restrict__ status)
+struct MdStep {
+    float dt, c;
+    bool langevin;
+    unsigned long long seed;
+    float d2oh, d2hh, tol;
+    int max_iter;
+};
+
+// First half of a step, one thread per unconstrained atom (items below
+// n_free) or per water.  A water's three atoms are kicked and drifted, then
+// M-SHAKE: lambda by Newton iterations on |r_k''|^2 = d_k^2,
+// r_k'' = u_k + sum_l lambda_l C_kl r_l (u: new, r: reference vectors of x,
+// C_kl = s(a_k, l)/m_{a_k} - s(b_k, l)/m_{b_k}), disp_i =
+// sum_l lambda_l s(i, l) r_l / m_i, until every |g_k| / d_k^2 < tol or
+// max_iter iterations.  New positions wrapped into the box.  Block 0 clears
+// the energy sums of this step.
+__global__ void __launch_bounds__(64) k_md_first(int n_free, int nw, MdStep P,
+                                                 const unsigned long long *__restrict__ step,
+                                                 const int *__restrict__ free_atoms, const int4 *__restrict__ waters,
+                                                 const float *__restrict__ mass, const float *__restrict__ sigv,
+                                                 const float *__restrict__ Ftot, float *__restrict__ x,
+                                                 float *__restrict__ v, Box3 B, long long *__restrict__ acc,
+                                                 int *__restrict__ status)
 {
     pdl_entry();
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (blockIdx.x == 0 && threadIdx.x < kMdAcc) acc[threadIdx.x] = 0;
+    const unsigned long long st = step[0];
+    if (t < n_free) {
+        const int a = free_atoms[t];
+        const float3 p = kick_drift(a, P.dt, P.c, P.langevin, P.seed, st, mass, sigv, Ftot, x, v);
+        x[3ll * a] = wrap_coord(p.x, B.L[0]);
+        x[3ll * a + 1] = wrap_coord(p.y, B.L[1]);
+        x[3ll * a + 2] = wrap_coord(p.z, B.L[2]);
+        return;
+    }
+    const int w = t - n_free;
     if (w >= nw) return;
     const int4 W = waters[w];
     const int at[3] = {W.x, W.y, W.z};
+    float3 xn[3];
     float im[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) im[i] = 1.0f / mass[at[i]];
+    for (int i = 0; i < 3; ++i) {
+        xn[i] = kick_drift(at[i], P.dt, P.c, P.langevin, P.seed, st, mass, sigv, Ftot, x, v);
+        im[i] = 1.0f / mass[at[i]];
+    }
     float3 r[3], u[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        r[k] = disp(x, at[kCB[k]], at[kCA[k]], B);  // x_a - x_b
-        const int a = at[kCA[k]], b = at[kCB[k]];
-        u[k] = make_float3(min_img(xn[3ll * a] - xn[3ll * b], B.L[0], B.h[0]),
-                           min_img(xn[3ll * a + 1] - xn[3ll * b + 1], B.L[1], B.h[1]),
-                           min_img(xn[3ll * a + 2] - xn[3ll * b + 2], B.L[2], B.h[2]));
+        r[k] = disp(x, at[con_b(k)], at[con_a(k)], B);  // x_a - x_b
+        const float3 pa = xn[con_a(k)], pb = xn[con_b(k)];
+        u[k] = make_float3(min_img(pa.x - pb.x, B.L[0], B.h[0]), min_img(pa.y - pb.y, B.L[1], B.h[1]),
+                           min_img(pa.z - pb.z, B.L[2], B.h[2]));
     }
-    const float d2[3] = {d2oh, d2oh, d2hh};
+    const float d2[3] = {P.d2oh, P.d2oh, P.d2hh};
     float C[3][3];
 #pragma unroll
     for (int k = 0; k < 3; ++k)
 #pragma unroll
-        for (int l = 0; l < 3; ++l) C[k][l] = sgn(kCA[k], l) * im[kCA[k]] - sgn(kCB[k], l) * im[kCB[k]];
+        for (int l = 0; l < 3; ++l) C[k][l] = sgn(con_a(k), l) * im[con_a(k)] - sgn(con_b(k), l) * im[con_b(k)];
     float lam[3] = {0.0f, 0.0f, 0.0f};
     bool conv = false;
-    for (int it = 0; it < max_iter; ++it) {
+    for (int it = 0; it < P.max_iter; ++it) {
         float3 rr[3];
         float g[3];
         float worst = 0.0f;
@@ -371,7 +409,7 @@ __global__ void k_md_shake(int nw, const int4 *__restrict__ waters, const float 
             g[k] = dot3(rr[k], rr[k]) - d2[k];
             worst = fmaxf(worst, fabsf(g[k]) / d2[k]);
         }
-        if (worst < tol) {
+        if (worst < P.tol) {
             conv = true;
             break;
         }
@@ -385,84 +423,69 @@ __global__ void k_md_shake(int nw, const int4 *__restrict__ waters, const float 
         for (int l = 0; l < 3; ++l) lam[l] -= dl[l];
     }
     if (!conv) atomicOr(status, ST_TIMEOUT);
-    const float idt = 1.0f / dt;
+    const float idt = 1.0f / P.dt;
+    float3 dsp[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        float3 dsp = make_float3(0.0f, 0.0f, 0.0f);
+        dsp[i] = make_float3(0.0f, 0.0f, 0.0f);
 #pragma unroll
-        for (int l = 0; l < 3; ++l) dsp = add3(dsp, scale3(lam[l] * sgn(i, l) * im[i], r[l]));
+        for (int l = 0; l < 3; ++l) dsp[i] = add3(dsp[i], scale3(lam[l] * sgn(i, l) * im[i], r[l]));
+    }
+    // the reference vectors above read x: write the new positions afterwards
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
         const int a = at[i];
-        x[3ll * a] = wrap_coord(xn[3ll * a] + dsp.x, B.L[0]);
-        x[3ll * a + 1] = wrap_coord(xn[3ll * a + 1] + dsp.y, B.L[1]);
-        x[3ll * a + 2] = wrap_coord(xn[3ll * a + 2] + dsp.z, B.L[2]);
-        v[3ll * a] = fmaf(dsp.x, idt, v[3ll * a]);
-        v[3ll * a + 1] = fmaf(dsp.y, idt, v[3ll * a + 1]);
-        v[3ll * a + 2] = fmaf(dsp.z, idt, v[3ll * a + 2]);
+        x[3ll * a] = wrap_coord(xn[i].x + dsp[i].x, B.L[0]);
+        x[3ll * a + 1] = wrap_coord(xn[i].y + dsp[i].y, B.L[1]);
+        x[3ll * a + 2] = wrap_coord(xn[i].z + dsp[i].z, B.L[2]);
+        v[3ll * a] = fmaf(dsp[i].x, idt, v[3ll * a]);
+        v[3ll * a + 1] = fmaf(dsp[i].y, idt, v[3ll * a + 1]);
+        v[3ll * a + 2] = fmaf(dsp[i].z, idt, v[3ll * a + 2]);
     }
 }
 
-// B and O (stream 1) with the new forces; kinetic energy of the atoms that
-// no constraint moves afterwards.
-__global__ void __launch_bounds__(256) k_md_kick(int n, float dt, float c, bool langevin, unsigned long long seed,
-                                                 const unsigned long long *__restrict__ step,
-                                                 const float *__restrict__ mass, const float *__restrict__ sigv,
-                                                 const int *__restrict__ water_of, const float *__restrict__ Fnb,
-                                                 long long *__restrict__ bacc, float *__restrict__ Ftot,
-                                                 float *__restrict__ v, long long *__restrict__ acc)
-{
-    pdl_entry();
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    long long ke[1] = {0};
-    if (a < n) {
-        float fx, fy, fz;
-        collect_force(a, Fnb, bacc, Ftot, fx, fy, fz);
-        const float m = mass[a];
-        const float h = 0.5f * dt * kAccel / m;
-        float vx = fmaf(h, fx, v[3ll * a]), vy = fmaf(h, fy, v[3ll * a + 1]), vz = fmaf(h, fz, v[3ll * a + 2]);
-        if (langevin) {
-            const float3 xi = md_normals((unsigned)a, step[0], 1u, seed);
-            const float s = sigv[a];
-            vx = fmaf(c, vx, s * xi.x);
-            vy = fmaf(c, vy, s * xi.y);
-            vz = fmaf(c, vz, s * xi.z);
-        }
-        v[3ll * a] = vx;
-        v[3ll * a + 1] = vy;
-        v[3ll * a + 2] = vz;
-        if (water_of[a] < 0)
-            ke[0] = __float2ll_rn(0.5f * m * fmaf(vx, vx, fmaf(vy, vy, vz * vz)) / kAccel * 4294967296.0f);
-    }
-    const int idx[1] = {3};
-    md_flush<1>(ke, acc, idx);
-}
-
-// RATTLE of one water per thread: mu from the 3 x 3 system
+// Second half of a step, same threads: B and O with the new forces; a
+// water's velocities then by RATTLE, mu from the 3 x 3 system
 // sum_l mu_l C_kl (r_k . r_l) = -r_k . (v_a - v_b), v_i += sum_l mu_l s(i,l) r_l / m_i;
-// kinetic energy of the water.
-__global__ void __launch_bounds__(256) k_md_rattle(int nw, const int4 *__restrict__ waters,
-                                                   const float *__restrict__ mass, const float *__restrict__ x,
-                                                   float *__restrict__ v, Box3 B, long long *__restrict__ acc)
+// kinetic energy of the thread's atoms.  The last block to finish writes
+// the energies (short-range + long-range from enb, the fixed-point sums of
+// acc) to energy, when given, and advances the device step counter.
+__global__ void __launch_bounds__(64) k_md_second(int n_free, int nw, MdStep P,
+                                                  unsigned long long *__restrict__ step,
+                                                  const int *__restrict__ free_atoms, const int4 *__restrict__ waters,
+                                                  const float *__restrict__ mass, const float *__restrict__ sigv,
+                                                  const float *__restrict__ Fnb, long long *__restrict__ bacc,
+                                                  float *__restrict__ Ftot, const float *__restrict__ x,
+                                                  float *__restrict__ v, Box3 B, long long *__restrict__ acc,
+                                                  const double *__restrict__ enb, double *__restrict__ energy)
 {
     pdl_entry();
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned long long st = step[0];
     long long ke[1] = {0};
-    if (w < nw) {
-        const int4 W = waters[w];
+    if (t < n_free) {
+        const int a = free_atoms[t];
+        const float3 u = kick(a, P.dt, P.c, P.langevin, P.seed, st, mass, sigv, Fnb, bacc, Ftot, v);
+        ke[0] = __float2ll_rn(0.5f * mass[a] * fmaf(u.x, u.x, fmaf(u.y, u.y, u.z * u.z)) / kAccel * 4294967296.0f);
+    } else if (t - n_free < nw) {
+        const int4 W = waters[t - n_free];
         const int at[3] = {W.x, W.y, W.z};
         float im[3], vv[3][3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
+            const float3 u = kick(at[i], P.dt, P.c, P.langevin, P.seed, st, mass, sigv, Fnb, bacc, Ftot, v);
+            vv[i][0] = u.x;
+            vv[i][1] = u.y;
+            vv[i][2] = u.z;
             im[i] = 1.0f / mass[at[i]];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) vv[i][c] = v[3ll * at[i] + c];
         }
         float3 r[3];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) r[k] = disp(x, at[kCB[k]], at[kCA[k]], B);
+        for (int k = 0; k < 3; ++k) r[k] = disp(x, at[con_b(k)], at[con_a(k)], B);
         float A[3][3], b[3], mu[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const int a = kCA[k], bb = kCB[k];
+            const int a = con_a(k), bb = con_b(k);
             const float3 dv = make_float3(vv[a][0] - vv[bb][0], vv[a][1] - vv[bb][1], vv[a][2] - vv[bb][2]);
             b[k] = -dot3(r[k], dv);
 #pragma unroll
@@ -486,19 +509,20 @@ __global__ void __launch_bounds__(256) k_md_rattle(int nw, const int4 *__restric
     }
     const int idx[1] = {3};
     md_flush<1>(ke, acc, idx);
-}
-
-__global__ void k_md_finish(const long long *__restrict__ acc, const double *__restrict__ enb,
-                            unsigned long long *__restrict__ step, double *__restrict__ energy)
-{
-    pdl_entry();
-    if (threadIdx.x == 0) {
-        if (energy) {
-            energy[0] = enb[0];
-            energy[1] = enb[1];
-            for (int k = 0; k < 4; ++k) energy[2 + k] = (double)acc[k] * (1.0 / 4294967296.0);
+    if (threadIdx.x == 0) {  // the thread that added this block's sum
+        __threadfence();
+        const unsigned long long done =
+            atomicAdd((unsigned long long *)&acc[kMdTicket], 1ull);
+        if (done == gridDim.x - 1ull) {  // every block has read step and added its sum
+            __threadfence();
+            const volatile long long *va = acc;
+            if (energy) {
+                energy[0] = enb[0];
+                energy[1] = enb[1];
+                for (int k = 0; k < 4; ++k) energy[2 + k] = (double)va[k] * (1.0 / 4294967296.0);
+            }
+            step[0] += 1ull;
         }
-        step[0] += 1ull;
     }
 }
 
@@ -527,8 +551,8 @@ void md_free(nb_ctx *ctx)
 {
     MdState *m = ctx->md;
     if (!m) return;
-    void *p[] = {m->mass, m->sigv, m->water_of, m->bonds, m->bond_p, m->angles, m->angle_p, m->dihedrals,
-                 m->dihedral_p, m->waters, m->xn, m->Fnb, m->Ftot, m->bacc, m->enb, m->acc, m->step};
+    void *p[] = {m->mass, m->sigv, m->free_atoms, m->bonds, m->bond_p, m->angles, m->angle_p, m->dihedrals,
+                 m->dihedral_p, m->waters, m->Fnb, m->Ftot, m->bacc, m->enb, m->acc, m->step};
     for (void *q : p)
         if (q) cudaFree(q);
     delete m;
@@ -643,11 +667,15 @@ extern "C" nb_status nb_md_init(nb_ctx *ctx, const nb_md_params *p)
                            p->dihedrals[4 * i + 3]);
         dp[i] = make_float4(p->dihedral_k[i], (float)p->dihedral_n[i], p->dihedral_phase[i], 0.0f);
     }
+    std::vector<int> free_atoms;
+    for (int i = 0; i < N; ++i)
+        if (water_of[i] < 0) free_atoms.push_back(i);
+    M->n_free = (int)free_atoms.size();
     std::vector<int4> wat(M->nw);
     for (int i = 0; i < M->nw; ++i) wat[i] = make_int4(p->waters[3 * i], p->waters[3 * i + 1], p->waters[3 * i + 2], 0);
     cudaError_t e = upload(&M->mass, p->mass, N);
     if (e == cudaSuccess) e = upload(&M->sigv, sig.data(), N);
-    if (e == cudaSuccess) e = upload(&M->water_of, water_of.data(), N);
+    if (e == cudaSuccess) e = upload(&M->free_atoms, free_atoms.data(), free_atoms.size());
     if (e == cudaSuccess) e = upload(&M->bonds, bonds.data(), bonds.size());
     if (e == cudaSuccess) e = upload(&M->bond_p, bp.data(), bp.size());
     if (e == cudaSuccess) e = upload(&M->angles, ang.data(), ang.size());
@@ -655,7 +683,6 @@ extern "C" nb_status nb_md_init(nb_ctx *ctx, const nb_md_params *p)
     if (e == cudaSuccess) e = upload(&M->dihedrals, dih.data(), dih.size());
     if (e == cudaSuccess) e = upload(&M->dihedral_p, dp.data(), dp.size());
     if (e == cudaSuccess) e = upload(&M->waters, wat.data(), wat.size());
-    if (e == cudaSuccess) e = cudaMalloc(&M->xn, sizeof(float) * 3 * N);
     if (e == cudaSuccess) e = cudaMalloc(&M->Fnb, sizeof(float) * 3 * N);
     if (e == cudaSuccess) e = cudaMalloc(&M->Ftot, sizeof(float) * 3 * N);
     if (e == cudaSuccess) e = cudaMalloc(&M->bacc, sizeof(long long) * 3 * N);
@@ -696,7 +723,19 @@ extern "C" nb_status nb_md_step(nb_ctx *ctx, float *d_pos, float *d_vel, const f
     const cudaStream_t st = ctx->stream;
     const Box3 B = box_of(ctx);
     const int N = M.n;
-    const int ab = (N + 255) / 256, wb = std::max(1, (M.nw + 127) / 128);
+    const int ab = (N + 255) / 256;
+    // one thread per unconstrained atom or rigid water, 64-thread blocks
+    // (the integration is latency bound: spread it over the SMs)
+    const int ib = std::max(1, (M.n_free + M.nw + 63) / 64);
+    MdStep P;
+    P.dt = M.dt;
+    P.c = M.c;
+    P.langevin = M.langevin;
+    P.seed = M.seed;
+    P.d2oh = M.d2[0];
+    P.d2hh = M.d2[1];
+    P.tol = M.shake_tol;
+    P.max_iter = M.shake_iter;
     cudaError_t e = cudaSuccess;
     if (!M.have_forces) {  // forces at the starting positions
         e = md_forces(ctx, d_pos, d_q, d_type);
@@ -706,24 +745,17 @@ extern "C" nb_status nb_md_step(nb_ctx *ctx, float *d_pos, float *d_vel, const f
         M.have_forces = true;
     }
     for (int s = 0; s < n_steps && e == cudaSuccess; ++s) {
-        e = launch_pdl(k_md_kick_drift, dim3(ab), dim3(256), 0, st, N, M.dt, M.c, M.langevin, M.seed,
-                       (const unsigned long long *)M.step, (const float *)M.mass, (const float *)M.sigv,
-                       (const int *)M.water_of, (const float *)M.Ftot, d_pos, d_vel, M.xn, B, M.acc);
-        if (e == cudaSuccess && M.nw > 0)
-            e = launch_pdl(k_md_shake, dim3(wb), dim3(128), 0, st, M.nw, (const int4 *)M.waters,
-                           (const float *)M.mass, M.d2[0], M.d2[1], M.shake_tol, M.shake_iter, M.dt,
-                           (const float *)M.xn, d_pos, d_vel, B, ctx->d.status);
+        e = launch_pdl(k_md_first, dim3(ib), dim3(64), 0, st, M.n_free, M.nw, P,
+                       (const unsigned long long *)M.step, (const int *)M.free_atoms, (const int4 *)M.waters,
+                       (const float *)M.mass, (const float *)M.sigv, (const float *)M.Ftot, d_pos, d_vel, B, M.acc,
+                       ctx->d.status);
         if (e == cudaSuccess) e = md_forces(ctx, d_pos, d_q, d_type);
         if (e == cudaSuccess)
-            e = launch_pdl(k_md_kick, dim3(ab), dim3(256), 0, st, N, M.dt, M.c, M.langevin, M.seed,
-                           (const unsigned long long *)M.step, (const float *)M.mass, (const float *)M.sigv,
-                           (const int *)M.water_of, (const float *)M.Fnb, M.bacc, M.Ftot, d_vel, M.acc);
-        if (e == cudaSuccess && M.nw > 0)
-            e = launch_pdl(k_md_rattle, dim3((M.nw + 255) / 256), dim3(256), 0, st, M.nw, (const int4 *)M.waters,
-                           (const float *)M.mass, (const float *)d_pos, d_vel, B, M.acc);
-        if (e == cudaSuccess)
-            e = launch_pdl(k_md_finish, dim3(1), dim3(32), 0, st, (const long long *)M.acc, (const double *)M.enb,
-                           M.step, s == n_steps - 1 ? d_energy : (double *)nullptr);
+            e = launch_pdl(k_md_second, dim3(ib), dim3(64), 0, st, M.n_free, M.nw, P,
+                           M.step, (const int *)M.free_atoms, (const int4 *)M.waters,
+                           (const float *)M.mass, (const float *)M.sigv, (const float *)M.Fnb, M.bacc, M.Ftot,
+                           (const float *)d_pos, d_vel, B, M.acc, (const double *)M.enb,
+                           s == n_steps - 1 ? d_energy : (double *)nullptr);
     }
     return e == cudaSuccess ? NB_OK : NB_ERR_CUDA;
 }

@@ -170,7 +170,7 @@ extern "C" nb_status nb_forces_noalloc(const nb_params *params, const float *d_p
     c.tune.blocks_per_sm = 3;
     c.tune.stage_capacity = 96;
     c.tune.list_capacity = kListCap;
-    c.tune.reserved = 0;
+    c.tune.list_split = kDefaultListSplit;
     c.stage_cap = 96;
     c.list_cap = kListCap;
     c.zb_total = host::zbin_entries(S);

@@ -50,7 +50,7 @@ class nb_params(ctypes.Structure):
 
 class nb_tuning(ctypes.Structure):
     _fields_ = [("blocks_per_sm", ctypes.c_int32), ("stage_capacity", ctypes.c_int32),
-                ("list_capacity", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("list_capacity", ctypes.c_int32), ("list_split", ctypes.c_int32)]
 
 
 class nb_pme_params(ctypes.Structure):

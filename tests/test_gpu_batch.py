@@ -83,8 +83,8 @@ def test_autotuner_picks_a_valid_configuration_and_keeps_parity():
     s = S.water_box()
     ctx = nb.Nonbonded(s)
     pos, q, t = nb.concat_inputs([s])
-    rec = autotune.autotune(ctx, pos, q, t, candidates=[dict(blocks_per_sm=b, stage_capacity=c)
-                                                        for b in (1, 3) for c in (32, 160)], reps=2)
+    rec = autotune.autotune(ctx, pos, q, t, candidates=[dict(blocks_per_sm=b, list_split=c)
+                                                        for b in (1, 3) for c in (1, 4)], reps=2)
     assert rec["best"] in [c for _, c in rec["table"]]
     assert ctx.tuning()["blocks_per_sm"] == rec["best"]["blocks_per_sm"]
     ctx.build(pos)

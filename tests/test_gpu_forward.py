@@ -113,11 +113,13 @@ def test_forces_energy_virial_parity(case):
 
 
 def test_tuning_variants_agree(case):
-    # small staging capacity forces the list of every cluster through several
-    # chunks; other grid sizes change the block-to-cluster assignment
+    # other grid sizes change the warp-to-unit assignment; list splits of 1
+    # to 8 cut every cluster's list into that many work units (most units
+    # of the 8-way split hold under 32 entries, the 1-way one several
+    # 32-entry batches)
     name, s, Fo, Eo, Wo, npairs, Es = case
-    for tune in (dict(stage_capacity=16, blocks_per_sm=1), dict(stage_capacity=64, blocks_per_sm=3),
-                 dict(stage_capacity=256, blocks_per_sm=2)):
+    for tune in (dict(list_split=1, blocks_per_sm=1), dict(list_split=3, blocks_per_sm=3),
+                 dict(list_split=8, blocks_per_sm=2)):
         ctx, inp, F, E, W = gpu_eval(s, tuning=tune)
         check_forces(F, Fo)
         check_energy(E[0], Eo, Es)
