@@ -1,21 +1,25 @@
-// nb_force.cu - the non-bonded force kernel (section "Molecular dynamics on
+// nb_force.cu - the non-bonded force kernels (section "Molecular dynamics on
 // the GPU": the non-bonded kernel computes the full Lennard-Jones and
 // electrostatic force on each particle).  The paper's kernel does not reuse
-// the reciprocal force F_ji; here the forward kernel does (Newton's third
-// law): every unique pair is evaluated once, from the atom of the lower
-// cluster, and its force goes to both atoms as 64-bit fixed point (2^32), so
-// the sums stay exact and order independent.  The adjoint kernel visits
-// every ordered pair, as in the paper.
+// the reciprocal force F_ji; here both kernels do (Newton's third law): every
+// unique pair is evaluated once, from the cluster whose half list holds it,
+// and its contribution goes to both atoms as 64-bit fixed point (2^32), so
+// the sums stay exact and order independent.
 //
-// GB300 work decomposition (the paper's one-cell-per-block staging of the
-// neighbour cells in shared memory, re-cut for this machine):
+// Forward (k_force): one warp per listed cluster pair as an 8 x 8 tile,
+// forces on i kept in registers, forces on j summed over lanes (see the
+// comment above k_force).
+//
+// Adjoint (k_adjoint), the paper's one-cell-per-block staging of the
+// neighbour cells in shared memory, re-cut for this machine:
 //   block = one 8-atom cluster I at a time (persistent grid of blocks);
 //   warp  = one i atom of I.
 // For each cluster the block stages I's cluster-pair list and, for every
-// listed cluster J, its 8 coordinates+charges, 8 types and bounding box into
-// shared memory with asynchronous copies (cp.async) issued by all threads;
-// coordinates and types are swizzled by J so that lanes reading the same atom
-// slot of different clusters hit different banks.  Each warp then
+// listed cluster J, its 8 coordinates+charges, 8 types, 8 dL/dF vectors and
+// bounding box into shared memory with asynchronous copies (cp.async) issued
+// by all threads; coordinates and types are swizzled by J so that lanes
+// reading the same atom slot of different clusters hit different banks.  Each
+// warp then
 //   (1) prunes the staged clusters whose bounding box lies beyond the cutoff
 //       of its own atom;
 //   (2) membership: one surviving cluster per lane, its 8 atoms tested with
@@ -24,15 +28,14 @@
 //   (3) compaction: a warp scan of the mask counts places every in-range
 //       (cluster, atom) item into a per-warp ring in shared memory;
 //   (4) compute: full 32-pair steps of the ring, one pair per lane, FP32.
-// Forward only: the force on j goes to a block-shared fixed-point slot of the
-// staged atom (integer atomics), flushed to the global fixed-point force array
-// when the chunk is done; the force on i is summed over the warp and added
-// once per cluster.
+// The j-atom terms go to block-shared fixed-point slots of the staged atoms
+// (integer atomics), flushed to the global fixed-point sums when the chunk
+// is done; the i-atom terms are summed over the warp and added once per
+// cluster.
 #include <cuda_runtime.h>
 #include <math.h>
 
 #include <algorithm>
-#include <type_traits>
 
 #include "nb_pair.cuh"
 
@@ -87,6 +90,7 @@ __device__ __forceinline__ long long to_fixed(float v, int *status)
     return __float2ll_rn(v * 4294967296.0f);
 }
 
+// Shared memory of the adjoint kernel.
 struct ForceSmem {
     float2 *lj;
     uint32_t *lst;             // list entries of the staged chunks [2][scap] (double buffer)
@@ -96,13 +100,10 @@ struct ForceSmem {
     float4 *bb;
     uint16_t *surv;
     uint32_t *ring;
-    unsigned long long *cacc;
-    int *jf;                   // j-atom sums of the staged chunk, [hi, lo][nc][scap * 8] (see add_jf); nc = 3
-                               // forward (force), 4 adjoint (dL/dx, dL/dq)
-    float *wimg;               // forward: per-thread periodic-image virial terms [6][blockDim]
-    float4 *gj;                // adjoint: staged dL/dF of the j atoms
-    float4 *ljd;               // adjoint: derivative factors of the type pairs
-    unsigned long long *tacc;  // adjoint: block table of fixed-point parameter gradients
+    int *jf;                   // j-atom sums of the staged chunk, [hi, lo][4][scap * 8] (see add_jf): dL/dx, dL/dq
+    float4 *gj;                // staged dL/dF of the j atoms
+    float4 *ljd;               // derivative factors of the type pairs
+    unsigned long long *tacc;  // block table of fixed-point parameter gradients
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -112,11 +113,9 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p)
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-__host__ __device__ inline size_t force_smem_bytes(int T, int scap, int nwarps, bool adj)
+__host__ __device__ inline size_t force_smem_bytes(int T, int scap, int nwarps)
 {
-    size_t b = adj ? (size_t)scap * kCluster * 16 + (size_t)T * T * 16 + (size_t)T * T * 16 +
-                         (size_t)scap * kCluster * 4 * 8
-                   : (size_t)scap * kCluster * 3 * 8 + (size_t)6 * nwarps * 32 * 4;
+    size_t b = (size_t)scap * kCluster * 16 + (size_t)T * T * 16 + (size_t)T * T * 16 + (size_t)scap * kCluster * 4 * 8;
     b += (size_t)2 * scap * 4;
     b += align16((size_t)T * T * 8);
     b += (size_t)scap * kCluster * 16;
@@ -124,36 +123,23 @@ __host__ __device__ inline size_t force_smem_bytes(int T, int scap, int nwarps, 
     b += (size_t)scap * 2 * 16;
     b += align16((size_t)nwarps * scap * 2);
     b += (size_t)nwarps * kRing * 4;
-    b += kTaskVals * 8;
     return b;
 }
 
-__device__ __forceinline__ ForceSmem carve(unsigned char *smem, int T, int scap, int nwarps, int w, bool adj)
+__device__ __forceinline__ ForceSmem carve(unsigned char *smem, int T, int scap, int nwarps, int w)
 {
     ForceSmem S;
     size_t off = 0;
     S.lst = reinterpret_cast<uint32_t *>(smem + off);
     off += (size_t)2 * scap * 4;
-    S.gj = S.ljd = nullptr;
-    S.tacc = nullptr;
-    S.jf = nullptr;
-    S.wimg = nullptr;
-    if (!adj) {
-        S.jf = reinterpret_cast<int *>(smem + off);
-        off += (size_t)scap * kCluster * 3 * 8;
-        S.wimg = reinterpret_cast<float *>(smem + off);
-        off += (size_t)6 * nwarps * 32 * 4;
-    }
-    if (adj) {
-        S.jf = reinterpret_cast<int *>(smem + off);
-        off += (size_t)scap * kCluster * 4 * 8;
-        S.gj = reinterpret_cast<float4 *>(smem + off);
-        off += (size_t)scap * kCluster * 16;
-        S.ljd = reinterpret_cast<float4 *>(smem + off);
-        off += (size_t)T * T * 16;
-        S.tacc = reinterpret_cast<unsigned long long *>(smem + off);
-        off += (size_t)T * T * 16;
-    }
+    S.jf = reinterpret_cast<int *>(smem + off);
+    off += (size_t)scap * kCluster * 4 * 8;
+    S.gj = reinterpret_cast<float4 *>(smem + off);
+    off += (size_t)scap * kCluster * 16;
+    S.ljd = reinterpret_cast<float4 *>(smem + off);
+    off += (size_t)T * T * 16;
+    S.tacc = reinterpret_cast<unsigned long long *>(smem + off);
+    off += (size_t)T * T * 16;
     S.lj = reinterpret_cast<float2 *>(smem + off);
     off += align16((size_t)T * T * 8);
     S.ent = nullptr;  // points into lst, per staged chunk
@@ -166,8 +152,6 @@ __device__ __forceinline__ ForceSmem carve(unsigned char *smem, int T, int scap,
     S.surv = reinterpret_cast<uint16_t *>(smem + off) + (size_t)w * scap;
     off += align16((size_t)nwarps * scap * 2);
     S.ring = reinterpret_cast<uint32_t *>(smem + off) + (size_t)w * kRing;
-    off += (size_t)nwarps * kRing * 4;
-    S.cacc = reinterpret_cast<unsigned long long *>(smem + off);
     return S;
 }
 
@@ -198,10 +182,9 @@ __device__ __forceinline__ uint32_t list_entry(const ForceArgs &A, int I, int nA
 }
 
 // Stage the n list entries from c0 of cluster I into S.ent, and for every
-// listed cluster J its 8 coordinates+charges, 8 types, bounding box and
-// (adjoint) 8 dL/dF vectors, with asynchronous copies issued by every thread
-// of the block.
-template <bool ADJ>
+// listed cluster J its 8 coordinates+charges, 8 types, 8 dL/dF vectors and
+// bounding box, with asynchronous copies issued by every thread of the
+// block.
 __device__ __forceinline__ void stage_chunk(const ForceArgs &A, const ForceSmem &S, int I, int nA, int c0, int n,
                                             float3 L)
 {
@@ -224,7 +207,7 @@ __device__ __forceinline__ void stage_chunk(const ForceArgs &A, const ForceSmem 
             cp_async16(S.pos + swz(e, k), A.xyzq + j);
         }
         cp_async4(S.typ + swz(e, k), A.tslot + j);
-        if (ADJ) cp_async16(S.gj + swz(e, k), A.gslot + j);
+        cp_async16(S.gj + swz(e, k), A.gslot + j);
         if (k < 2) {
             // the box is staged at J's image (shifted by -L for code 1, +L
             // for code 2 on each axis): only a filter, rounding is harmless
@@ -412,21 +395,20 @@ __device__ __forceinline__ void add_jf(const ForceArgs &A, const ForceSmem &S, l
     }
 }
 
-// Per-warp data of the i atom.
+// Per-warp data of the i atom (adjoint kernel).
 struct IAtom {
     float xi, yi, zi, xim, yim, zim;
     float qi;     // ke * q_i
     int ti_row;   // t_i * T
-    int iorig;    // caller index (debug)
-    float gix, giy, giz, gE_lj, gE_c;  // adjoint
+    float gix, giy, giz, gE_lj, gE_c;  // dL/dF_i, dL/dE_LJ, dL/dE_C
 };
 
 // One ring item: staged entry e (bits 7..15), i-side image per axis (bits
 // 4..6), atom k (bits 1..3), 1-4 flag (bit 0).  The displacement is
 // recomputed with the same operations as the membership test (same value).
-template <bool ADJ, int RAD, bool VIRIAL, bool DEBUG, class AccT>
-__device__ __forceinline__ void eval_item(const ForceArgs &A, const ForceSmem &S, float Lx, float Ly, float Lz,
-                                          const IAtom &ia, uint32_t item, bool active, AccT &acc)
+template <int RAD>
+__device__ __forceinline__ void eval_item(const ForceArgs &A, const ForceSmem &S, const IAtom &ia, uint32_t item,
+                                          bool active, AccAdj &acc)
 {
     const int e = (int)(item >> 7), k = (int)((item >> 1) & 7u);
     const float ax = (item & 0x10u) ? ia.xim : ia.xi, ay = (item & 0x20u) ? ia.yim : ia.yi,
@@ -436,54 +418,30 @@ __device__ __forceinline__ void eval_item(const ForceArgs &A, const ForceSmem &S
     const int tj = S.typ[idx];
     float dx, dy, dz;
     const float r2 = disp_r2(pj.x, pj.y, pj.z, ax, ay, az, dx, dy, dz);
-    if (DEBUG && active) {
-        // forward visits: every unique pair exactly once
-        atomicAdd((unsigned long long *)&A.dbg_n[0], 1ull);
-        const int jorig = A.perm[(int)(S.ent[e] & kJMask) * kCluster + k];
-        const long long q = (long long)atomicAdd((unsigned long long *)&A.dbg_n[1], 1ull);
-        if (q < A.dbg_cap) {
-            A.dbg_ij[2 * q] = min(ia.iorig, jorig);
-            A.dbg_ij[2 * q + 1] = max(ia.iorig, jorig);
-        }
-    }
-    if constexpr (ADJ) {
-        float jx, jy, jz, jq;
-        eval_pair_adj<RAD == 1>(A.P, S, ia.ti_row, ia.qi, ia.gix, ia.giy, ia.giz, ia.gE_lj, ia.gE_c, active, dx, dy, dz,
-                             active ? r2 : 1.0f, pj.w, tj, S.gj[idx], (item & 1u) != 0u, A.status, acc, jx, jy, jz,
-                             jq);
-        if (active) {
-            const int js = A.scap * kCluster;
-            add_jf<4>(A, S, A.gacc, e, k, idx, 0, jx);
-            add_jf<4>(A, S, A.gacc, e, k, idx + js, 1, jy);
-            add_jf<4>(A, S, A.gacc, e, k, idx + 2 * js, 2, jz);
-            add_jf<4>(A, S, A.gacc, e, k, idx + 3 * js, 3, jq);
-        }
-    } else {
-        float fjx, fjy, fjz;
-        eval_pair<RAD>(A.P, S.lj, A.rtab, ia.ti_row, ia.qi, active, dx, dy, dz, active ? r2 : 1.0f, pj.w, tj,
-                       (item & 1u) != 0u, acc, fjx, fjy, fjz);
-        if (active) {
-            const int js = A.scap * kCluster;
-            add_jf<3>(A, S, A.facc, e, k, idx, 0, fjx);
-            add_jf<3>(A, S, A.facc, e, k, idx + js, 1, fjy);
-            add_jf<3>(A, S, A.facc, e, k, idx + 2 * js, 2, fjz);
-        }
+    float jx, jy, jz, jq;
+    eval_pair_adj<RAD == 1>(A.P, S, ia.ti_row, ia.qi, ia.gix, ia.giy, ia.giz, ia.gE_lj, ia.gE_c, active, dx, dy, dz,
+                            active ? r2 : 1.0f, pj.w, tj, S.gj[idx], (item & 1u) != 0u, A.status, acc, jx, jy, jz, jq);
+    if (active) {
+        const int js = A.scap * kCluster;
+        add_jf<4>(A, S, A.gacc, e, k, idx, 0, jx);
+        add_jf<4>(A, S, A.gacc, e, k, idx + js, 1, jy);
+        add_jf<4>(A, S, A.gacc, e, k, idx + 2 * js, 2, jz);
+        add_jf<4>(A, S, A.gacc, e, k, idx + 3 * js, 3, jq);
     }
 }
 
 // Per-cluster inputs of a warp (one i atom): system, sorted coordinates and
-// charge, type, list lengths, topology partner slot of this lane and (adjoint)
+// charge, type, half-list length, topology partner slot of this lane and
 // dL/dF of the atom.
 struct ClusterHead {
     int sys_id;
     float4 pi;
     int ti;
-    int nA, nE;
+    int nA;
     int pe;
     float4 gi;
 };
 
-template <bool ADJ>
 __device__ __forceinline__ ClusterHead load_head(const ForceArgs &A, int I, int w, int lane)
 {
     ClusterHead h;
@@ -491,42 +449,12 @@ __device__ __forceinline__ ClusterHead load_head(const ForceArgs &A, int I, int 
     h.sys_id = __ldg(A.clus_sys + I);
     h.pi = __ldg(A.xyzq + islot);
     h.ti = __ldg(A.tslot + islot);
-    h.nA = __ldg(A.list_n + 2 * I);
-    h.nE = h.nA;  // the half list: every pair once (Newton's third law, both modes)
+    h.nA = __ldg(A.list_n + 2 * I);  // the half list: every pair once (Newton's third law)
     h.pe = lane < A.K ? __ldg(A.pslot + islot * A.K + lane) : -1;
-    if (ADJ) h.gi = __ldg(A.gslot + islot);
+    h.gi = __ldg(A.gslot + islot);
     return h;
 }
 
-// Add the per-lane fixed-point energies and the per-thread periodic-image
-// virial terms (scale 2^20) of a system to its global sums (warp reduction,
-// block accumulator, one atomic per value and block).
-template <bool VIRIAL>
-__device__ __forceinline__ void flush_energy(const ForceArgs &A, const ForceSmem &S, const long long *wacc, int sys,
-                                             int lane)
-{
-#pragma unroll
-    for (int k = 0; k < (VIRIAL ? kTaskVals : 2); ++k) {
-        long long x = wacc[k & 1];
-        if (k >= 2) {
-            float &wk = S.wimg[(k - 2) * blockDim.x + threadIdx.x];
-            x = __float2ll_rn(wk * (float)kVirScale);
-            wk = 0.0f;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
-        if (lane == 0) atomicAdd(&S.cacc[k], (unsigned long long)x);
-    }
-    __syncthreads();
-    if (threadIdx.x < kTaskVals) {
-        atomicAdd((unsigned long long *)&A.sys_acc[sys * kTaskVals + threadIdx.x], S.cacc[threadIdx.x]);
-        S.cacc[threadIdx.x] = 0ull;
-    }
-    __syncthreads();
-}
-
-// Forward: add the block's fixed-point forces of the n staged j clusters
-// listed at ent to the global fixed-point force array and clear them.
 // The 2^32 fixed-point value of a hi/lo slot pair (see add_jf).
 __device__ __forceinline__ unsigned long long split_sum(const int *jf, int lo_off, int i)
 {
@@ -551,54 +479,11 @@ __device__ __forceinline__ void flush_jadj(const ForceArgs &A, const ForceSmem &
     }
 }
 
-// With VIRIAL, also add the periodic-image part of the virial: a pair whose
-// j atom was taken at its image x_j + s contributes s (x) f_j beyond the
-// x (x) F sum over atoms (see k_unpack_forces); s is the entry's shift
-// (code 1: -L, code 2: +L per axis) and sum f_j over the block's i atoms is
-// the slot's value.  wimg: xx, yy, zz, xy, xz, yz.
-template <bool VIRIAL>
-__device__ __forceinline__ void flush_jf(const ForceArgs &A, const ForceSmem &S, const uint32_t *ent, int n,
-                                         float Lx, float Ly, float Lz)
-{
-    float *wimg = S.wimg + threadIdx.x;  // component c at wimg[c * blockDim.x]
-    const int wst = blockDim.x;
-    const int js = A.scap * kCluster;
-    for (int p = threadIdx.x; p < n * kCluster; p += blockDim.x) {
-        const int e = p >> 3, k = (p & 7) ^ (e & 7);  // p = swz(e, k)
-        const uint32_t en = ent[e];
-        const long long g = 3ll * ((long long)(en & kJMask) * kCluster + k);
-        const unsigned long long v0 = split_sum(S.jf, 3 * js, p), v1 = split_sum(S.jf, 3 * js, js + p),
-                                 v2 = split_sum(S.jf, 3 * js, 2 * js + p);
-        if (v0) atomicAdd((unsigned long long *)&A.facc[g], v0);
-        if (v1) atomicAdd((unsigned long long *)&A.facc[g + 1], v1);
-        if (v2) atomicAdd((unsigned long long *)&A.facc[g + 2], v2);
-        S.jf[p] = 0;
-        S.jf[js + p] = 0;
-        S.jf[2 * js + p] = 0;
-        S.jf[3 * js + p] = 0;
-        S.jf[4 * js + p] = 0;
-        S.jf[5 * js + p] = 0;
-        const uint32_t code = (en >> kShiftBit) & 0x3Fu;
-        if (VIRIAL && code) {
-            const uint32_t cx = code & 3u, cy = (code >> 2) & 3u, cz = code >> 4;
-            const float sx = cx == 1u ? -Lx : (cx == 2u ? Lx : 0.0f);
-            const float sy = cy == 1u ? -Ly : (cy == 2u ? Ly : 0.0f);
-            const float sz = cz == 1u ? -Lz : (cz == 2u ? Lz : 0.0f);
-            const float sc = 2.3283064365386963e-10f;  // 2^-32
-            const float fx = __ll2float_rn((long long)v0) * sc, fy = __ll2float_rn((long long)v1) * sc,
-                        fz = __ll2float_rn((long long)v2) * sc;
-            wimg[0] = fmaf(sx, fx, wimg[0]);
-            wimg[wst] = fmaf(sy, fy, wimg[wst]);
-            wimg[2 * wst] = fmaf(sz, fz, wimg[2 * wst]);
-            wimg[3 * wst] = fmaf(sx, fy, wimg[3 * wst]);
-            wimg[4 * wst] = fmaf(sx, fz, wimg[4 * wst]);
-            wimg[5 * wst] = fmaf(sy, fz, wimg[5 * wst]);
-        }
-    }
-}
-
-template <bool ADJ, int RAD, bool VIRIAL, bool DEBUG>
-__global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
+// Adjoint of L = sum G.F + gE_lj E_lj + gE_c E_C over the half lists (see
+// eval_pair_adj): dL/dx and dL/dq of both atoms of every pair in fixed point,
+// dL/dsig_ab and dL/deps_ab in a block table.
+template <int RAD>
+__global__ void __launch_bounds__(256, 3) k_adjoint(ForceArgs A)
 {
     pdl_entry();
     extern __shared__ __align__(16) unsigned char smem[];
@@ -607,36 +492,25 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
     const int w = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    const ForceSmem S = carve(smem, T, A.scap, nwarps, w, ADJ);
-    for (int k = threadIdx.x; k < T * T; k += blockDim.x) S.lj[k] = A.lj_tab[k];
-    if (ADJ) {
-        for (int k = threadIdx.x; k < T * T; k += blockDim.x) {
-            S.ljd[k] = A.lj_d[k];
-            S.tacc[2 * k] = 0ull;
-            S.tacc[2 * k + 1] = 0ull;
-        }
+    const ForceSmem S = carve(smem, T, A.scap, nwarps, w);
+    for (int k = threadIdx.x; k < T * T; k += blockDim.x) {
+        S.lj[k] = A.lj_tab[k];
+        S.ljd[k] = A.lj_d[k];
+        S.tacc[2 * k] = 0ull;
+        S.tacc[2 * k + 1] = 0ull;
     }
-    if (threadIdx.x < kTaskVals) S.cacc[threadIdx.x] = 0ull;
-    for (int k = threadIdx.x; k < (ADJ ? 8 : 6) * A.scap * kCluster; k += blockDim.x) S.jf[k] = 0;
-    if (!ADJ)
-        for (int k = threadIdx.x; k < 6 * (int)blockDim.x; k += blockDim.x) S.wimg[k] = 0.0f;
+    for (int k = threadIdx.x; k < 8 * A.scap * kCluster; k += blockDim.x) S.jf[k] = 0;
     __syncthreads();
-    using AccT = typename std::conditional<ADJ, AccAdj, Acc>::type;
 
     int cur_sys = -1;
     float Lx = 0.0f, Ly = 0.0f, Lz = 0.0f;
-    long long wacc[2] = {0, 0};  // per lane: fixed-point energies of the current system
     const int n_clus = A.counts[1];
     const float rcm2 = A.P.rcm2;
 
     for (int I = blockIdx.x; I < n_clus; I += gridDim.x) {
-        const ClusterHead cur = load_head<ADJ>(A, I, w, lane);
+        const ClusterHead cur = load_head(A, I, w, lane);
         const int sys_id = cur.sys_id;
         if (sys_id != cur_sys) {
-            // flush the energy/virial of the previous system through the
-            // block accumulator (integer sums: order independent)
-            if (!ADJ && cur_sys >= 0) flush_energy<VIRIAL>(A, S, wacc, cur_sys, lane);
-            wacc[0] = wacc[1] = 0;
             cur_sys = sys_id;
             Lx = A.sys[sys_id].L[0];
             Ly = A.sys[sys_id].L[1];
@@ -654,23 +528,14 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
         ia.yim = __fsub_rn(pi.y, Ly);
         ia.zim = __fsub_rn(pi.z, Lz);
         ia.qi = pi.w * A.P.ke;
-        ia.iorig = DEBUG ? A.perm[islot] : -1;
         const float xi = ia.xi, yi = ia.yi, zi = ia.zi, xim = ia.xim, yim = ia.yim, zim = ia.zim;
-        if (ADJ) {
-            const float4 gi = cur.gi;
-            ia.gix = gi.x;
-            ia.giy = gi.y;
-            ia.giz = gi.z;
-            ia.gE_lj = A.dLdE ? (float)A.dLdE[2 * sys_id] : 0.0f;
-            ia.gE_c = A.dLdE ? (float)A.dLdE[2 * sys_id + 1] : 0.0f;
-        } else {
-            ia.gix = ia.giy = ia.giz = ia.gE_lj = ia.gE_c = 0.0f;
-        }
-        AccT acc;
-        memset(&acc, 0, sizeof(acc));
-        // forward: the half list (Newton's third law); adjoint: both halves
-        const int nA = cur.nA;
-        const int nE = cur.nE;
+        ia.gix = cur.gi.x;
+        ia.giy = cur.gi.y;
+        ia.giz = cur.gi.z;
+        ia.gE_lj = A.dLdE ? (float)A.dLdE[2 * sys_id] : 0.0f;
+        ia.gE_c = A.dLdE ? (float)A.dLdE[2 * sys_id + 1] : 0.0f;
+        AccAdj acc = {0.0f, 0.0f, 0.0f, 0.0f};
+        const int nE = cur.nA;
         const int pe = cur.pe;
         __syncthreads();  // the staging buffers are free
 
@@ -678,12 +543,11 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
             const int nC = min(A.scap, nE - c0);
             if (c0 > 0) {
                 __syncthreads();  // the staging buffers are free
-                if (ADJ) flush_jadj(A, S, S.lst + ((ci - 1) & 1) * A.scap, A.scap);
-                else flush_jf<VIRIAL>(A, S, S.lst + ((ci - 1) & 1) * A.scap, A.scap, Lx, Ly, Lz);
+                flush_jadj(A, S, S.lst + ((ci - 1) & 1) * A.scap, A.scap);
             }
             ForceSmem Sc = S;
             Sc.ent = S.lst + (ci & 1) * A.scap;
-            stage_chunk<ADJ>(A, Sc, I, nA, c0, nC, make_float3(Lx, Ly, Lz));
+            stage_chunk(A, Sc, I, nE, c0, nC, make_float3(Lx, Ly, Lz));
             if (!iv) continue;
             // (1) prune staged clusters against this atom
             int ns = 0;
@@ -764,8 +628,7 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
                 tail += total;
                 __syncwarp();
                 while (tail - head >= 32) {
-                    eval_item<ADJ, RAD, VIRIAL, DEBUG>(A, Sc, Lx, Ly, Lz, ia, S.ring[(head + lane) & (kRing - 1)],
-                                                         true, acc);
+                    eval_item<RAD>(A, Sc, ia, S.ring[(head + lane) & (kRing - 1)], true, acc);
                     head += 32;
                 }
                 __syncwarp();
@@ -773,69 +636,41 @@ __global__ void __launch_bounds__(256, 3) k_force(ForceArgs A)
             if (tail > head) {  // partial step before the staged data is replaced
                 const int n = tail - head;
                 const uint32_t item = lane < n ? S.ring[(head + lane) & (kRing - 1)] : 0u;
-                eval_item<ADJ, RAD, VIRIAL, DEBUG>(A, Sc, Lx, Ly, Lz, ia, item, lane < n, acc);
+                eval_item<RAD>(A, Sc, ia, item, lane < n, acc);
             }
             __syncwarp();
         }
         if (nE > 0) {
             const int last = (nE - 1) / A.scap;
             __syncthreads();
-            if (ADJ) flush_jadj(A, S, S.lst + (last & 1) * A.scap, nE - last * A.scap);
-            else flush_jf<VIRIAL>(A, S, S.lst + (last & 1) * A.scap, nE - last * A.scap, Lx, Ly, Lz);
+            flush_jadj(A, S, S.lst + (last & 1) * A.scap, nE - last * A.scap);
         }
         if (!iv) continue;
-        if constexpr (ADJ) {
-            long long v0 = to_fixed(acc.dx, A.status), v1 = to_fixed(acc.dy, A.status),
-                      v2 = to_fixed(acc.dz, A.status), v3 = to_fixed(acc.dq, A.status);
+        long long v0 = to_fixed(acc.dx, A.status), v1 = to_fixed(acc.dy, A.status), v2 = to_fixed(acc.dz, A.status),
+                  v3 = to_fixed(acc.dq, A.status);
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                v0 += __shfl_xor_sync(kFull, v0, o);
-                v1 += __shfl_xor_sync(kFull, v1, o);
-                v2 += __shfl_xor_sync(kFull, v2, o);
-                v3 += __shfl_xor_sync(kFull, v3, o);
-            }
-            if (lane == 0) {
-                unsigned long long *g = (unsigned long long *)A.gacc + 4ll * islot;
-                atomicAdd(g, (unsigned long long)v0);
-                atomicAdd(g + 1, (unsigned long long)v1);
-                atomicAdd(g + 2, (unsigned long long)v2);
-                atomicAdd(g + 3, (unsigned long long)v3);
-            }
-        } else {
-            // force of atom i: sum of the 32 lanes in 64-bit fixed point
-            long long vx = to_fixed(acc.fx, A.status), vy = to_fixed(acc.fy, A.status),
-                      vz = to_fixed(acc.fz, A.status);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                vx += __shfl_xor_sync(kFull, vx, o);
-                vy += __shfl_xor_sync(kFull, vy, o);
-                vz += __shfl_xor_sync(kFull, vz, o);
-            }
-            if (lane == 0) {
-                atomicAdd((unsigned long long *)&A.facc[3ll * islot], (unsigned long long)vx);
-                atomicAdd((unsigned long long *)&A.facc[3ll * islot + 1], (unsigned long long)vy);
-                atomicAdd((unsigned long long *)&A.facc[3ll * islot + 2], (unsigned long long)vz);
-            }
-            // energies: per lane in fixed point (reduced when the system's
-            // sums are flushed)
-            wacc[0] += to_fixed(acc.elj, A.status);
-            wacc[1] += to_fixed(acc.ec, A.status);
+        for (int o = 16; o > 0; o >>= 1) {
+            v0 += __shfl_xor_sync(kFull, v0, o);
+            v1 += __shfl_xor_sync(kFull, v1, o);
+            v2 += __shfl_xor_sync(kFull, v2, o);
+            v3 += __shfl_xor_sync(kFull, v3, o);
+        }
+        if (lane == 0) {
+            unsigned long long *g = (unsigned long long *)A.gacc + 4ll * islot;
+            atomicAdd(g, (unsigned long long)v0);
+            atomicAdd(g + 1, (unsigned long long)v1);
+            atomicAdd(g + 2, (unsigned long long)v2);
+            atomicAdd(g + 3, (unsigned long long)v3);
         }
     }
-    if constexpr (ADJ) {
-        // block table of parameter gradients -> global (integer sums)
-        __syncthreads();
-        for (int k = threadIdx.x; k < 2 * T * T; k += blockDim.x)
-            if (S.tacc[k]) atomicAdd((unsigned long long *)&A.tab_acc[k], S.tacc[k]);
-        return;
-    }
-    // final flush of the last system (every block reaches it: cur_sys is
-    // block-uniform)
-    if (cur_sys >= 0) flush_energy<VIRIAL>(A, S, wacc, cur_sys, lane);
+    // block table of parameter gradients -> global (integer sums)
+    __syncthreads();
+    for (int k = threadIdx.x; k < 2 * T * T; k += blockDim.x)
+        if (S.tacc[k]) atomicAdd((unsigned long long *)&A.tab_acc[k], S.tacc[k]);
 }
 
 // ---------------------------------------------------------------------------
-// Forward kernel on cluster-pair tiles.
+// Forward kernel (k_force) on cluster-pair tiles.
 //
 // One warp evaluates one listed cluster pair (I, J) at a time as an 8 x 8
 // tile: lane = jj + 8 ih holds j atom jj of J and the i atoms ih and ih + 4
@@ -1042,7 +877,7 @@ __device__ __forceinline__ void tile_warp_sums(long long (&e)[2], long long &wv,
 }
 
 template <int RAD, bool VIRIAL, bool DEBUG>
-__global__ void __launch_bounds__(kTileWarps * 32, ACENB_TILE_MIN_BLOCKS) k_force_tile(ForceArgs A, int parts)
+__global__ void __launch_bounds__(kTileWarps * 32, ACENB_TILE_MIN_BLOCKS) k_force(ForceArgs A, int parts)
 {
     pdl_entry();
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1375,43 +1210,42 @@ __global__ void k_unpack_adjoint(int slot_cap, const int *__restrict__ counts, c
     if (dq) dq[a] = __ll2float_rn(gacc[4ll * s + 3]) * sc;
 }
 
-template <bool ADJ, int RAD, bool VIRIAL, bool DEBUG>
-static void launch_force_t(nb_ctx *ctx, const ForceArgs &A)
+template <int RAD>
+static void launch_adjoint_t(nb_ctx *ctx, const ForceArgs &A)
 {
     const int nw = kCluster;
-    const size_t smem = force_smem_bytes(A.P.n_types, A.scap, nw, ADJ);
+    const size_t smem = force_smem_bytes(A.P.n_types, A.scap, nw);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_force<ADJ, RAD, VIRIAL, DEBUG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             220 * 1024);
+        cudaFuncSetAttribute(k_adjoint<RAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
         attr_set = true;
     }
     // persistent grid: never more blocks than can be resident at once
     int resident = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_force<ADJ, RAD, VIRIAL, DEBUG>, nw * 32, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_adjoint<RAD>, nw * 32, smem);
     const int per_sm = std::max(1, std::min(ctx->tune.blocks_per_sm, resident));
     const int grid = ctx->num_sms * per_sm;
-    launch_pdl(k_force<ADJ, RAD, VIRIAL, DEBUG>, dim3(grid), dim3(nw * 32), smem, ctx->stream, A);
+    launch_pdl(k_adjoint<RAD>, dim3(grid), dim3(nw * 32), smem, ctx->stream, A);
 }
 
 size_t tile_smem_bytes(int T, int K) { return align16((size_t)T * T * 8) + (size_t)kTileWarps * kCluster * K * 4; }
 
 template <int RAD, bool VIRIAL, bool DEBUG>
-static void launch_tile_t(nb_ctx *ctx, const ForceArgs &A)
+static void launch_force_t(nb_ctx *ctx, const ForceArgs &A)
 {
     const size_t smem = tile_smem_bytes(A.P.n_types, A.K);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_force_tile<RAD, VIRIAL, DEBUG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_force<RAD, VIRIAL, DEBUG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              200 * 1024);
         attr_set = true;
     }
     // persistent grid: never more blocks than can be resident at once
     int resident = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_force_tile<RAD, VIRIAL, DEBUG>, kTileWarps * 32, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_force<RAD, VIRIAL, DEBUG>, kTileWarps * 32, smem);
     const int per_sm = std::max(1, std::min(ctx->tune.blocks_per_sm, resident));
     const int parts = ctx->tune.list_split > 0 ? ctx->tune.list_split : kDefaultListSplit;
-    launch_pdl(k_force_tile<RAD, VIRIAL, DEBUG>, dim3(ctx->num_sms * per_sm), dim3(kTileWarps * 32), smem,
+    launch_pdl(k_force<RAD, VIRIAL, DEBUG>, dim3(ctx->num_sms * per_sm), dim3(kTileWarps * 32), smem,
                ctx->stream, A, parts);
 }
 
@@ -1483,17 +1317,17 @@ cudaError_t launch_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, con
     const bool prof = ctx->profiling && ctx->prof_n < (int)ctx->prof_ev.size() / 2;
     if (prof) cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n], ctx->stream);
     if (debug_pairs) {  // the pair set does not depend on the radial functions
-        if (ewald) launch_tile_t<1, false, true>(ctx, A);
-        else launch_tile_t<0, false, true>(ctx, A);
+        if (ewald) launch_force_t<1, false, true>(ctx, A);
+        else launch_force_t<0, false, true>(ctx, A);
     } else if (ctx->tab_n > 0) {
-        if (virial) launch_tile_t<2, true, false>(ctx, A);
-        else launch_tile_t<2, false, false>(ctx, A);
+        if (virial) launch_force_t<2, true, false>(ctx, A);
+        else launch_force_t<2, false, false>(ctx, A);
     } else if (ewald) {
-        if (virial) launch_tile_t<1, true, false>(ctx, A);
-        else launch_tile_t<1, false, false>(ctx, A);
+        if (virial) launch_force_t<1, true, false>(ctx, A);
+        else launch_force_t<1, false, false>(ctx, A);
     } else {
-        if (virial) launch_tile_t<0, true, false>(ctx, A);
-        else launch_tile_t<0, false, false>(ctx, A);
+        if (virial) launch_force_t<0, true, false>(ctx, A);
+        else launch_force_t<0, false, false>(ctx, A);
     }
     if (prof) {
         cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n + 1], ctx->stream);
@@ -1523,9 +1357,7 @@ cudaError_t launch_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, con
 
 size_t force_smem_for(int T, int scap, int K)
 {
-    (void)K;
-    return std::max(force_smem_bytes(T, std::min(scap, kAdjStage), kCluster, true),
-                    force_smem_bytes(T, scap, kCluster, false));
+    return std::max(force_smem_bytes(T, std::min(scap, kAdjStage), kCluster), tile_smem_bytes(T, K));
 }
 
 cudaError_t launch_adjoint_tile(nb_ctx *ctx, const double *d_dLdE, float *d_dpos, float *d_dq)
@@ -1540,8 +1372,8 @@ cudaError_t launch_adjoint_tile(nb_ctx *ctx, const double *d_dLdE, float *d_dpos
     A.tab_acc = d.tab_grad;
     A.gacc = d.gacc;
     A.scap = std::min(ctx->stage_cap, kAdjStage);
-    if (ctx->pp.ewald) launch_force_t<true, 1, false, false>(ctx, A);
-    else launch_force_t<true, 0, false, false>(ctx, A);
+    if (ctx->pp.ewald) launch_adjoint_t<1>(ctx, A);
+    else launch_adjoint_t<0>(ctx, A);
     const int tb = 256;
     const int S = (int)ctx->slot_cap;
     return launch_pdl(k_unpack_adjoint, dim3((S + tb - 1) / tb), dim3(tb), 0, ctx->stream, S, d.counts, d.perm,
