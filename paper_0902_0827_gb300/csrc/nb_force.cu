@@ -336,39 +336,51 @@ __device__ __forceinline__ void eval_pair_adj(const PairParams &P, const ForceSm
     }
 }
 
-// One candidate pair: d = x_j - x_i (exact-shift image), r2 its FP32 squared
-// length; the arithmetic is done for every candidate and masked by `in`.
-// RAD: radial functions evaluated directly with plain Coulomb (0) or Ewald
-// (1), or interpolated from the tables (2).
-template <int RAD>
-__device__ __forceinline__ void eval_pair(const PairParams &P, const float2 *__restrict__ lj,
+// One candidate pair of the forward kernel: d = x_j - x_i (exact-shift
+// image), r2 its FP32 squared length; the arithmetic is done for every
+// candidate and masked by `in`.  RAD: radial functions evaluated directly
+// with plain Coulomb (0) or Ewald (1), or interpolated from the tables (2).
+// W14: the pair may be a scaled 1-4 pair (is14), else both weights are 1
+// (the same bits either way for an unscaled pair).  lj holds (A, B, 12 A,
+// 6 B) per type pair.  The force on i is subtracted from acc and the force
+// on j added to fj with explicit FMA, so that the bits do not depend on how
+// the caller was inlined.
+template <int RAD, bool W14>
+__device__ __forceinline__ void eval_pair(const PairParams &P, const float4 *__restrict__ lj,
                                           const float4 *__restrict__ rtab, int ti_row, float qi, bool in, float dx,
                                           float dy, float dz, float r2, float qj, int tj, bool is14, Acc &acc,
                                           float &fjx, float &fjy, float &fjz)
 {
     const float rinv = fast_rsqrt(r2);
-    const float2 ab = lj[ti_row + tj];
+    const float r2inv = __fmul_rn(rinv, rinv);
+    const float4 ab = lj[ti_row + tj];
     float elj, frlj, ec, frc;
     if constexpr (RAD == 2)
         pair_radial_tab(P, rtab, r2, rinv, ab.x, ab.y, qi * qj, elj, frlj, ec, frc);
     else
-        pair_radial<RAD == 1, true>(P, r2, rinv, ab.x, ab.y, qi * qj, elj, frlj, ec, frc);
-    const float wlj = is14 ? P.s14_lj : 1.0f;
-    const float wc = is14 ? P.s14_c : 1.0f;
+        pair_radial<RAD == 1, true>(P, r2, rinv, r2inv, ab, qi * qj, elj, frlj, ec, frc);
     // F_i = U'(r) d / r = -fs d with fs = -U'(r) / r
-    float fs = __fmul_rn(__fmaf_rn(wlj, frlj, __fmul_rn(wc, frc)), __fmul_rn(rinv, rinv));
+    float fs, wel, wec;
+    if (W14) {
+        const float wlj = is14 ? P.s14_lj : 1.0f;
+        const float wc = is14 ? P.s14_c : 1.0f;
+        fs = __fmul_rn(__fmaf_rn(wlj, frlj, __fmul_rn(wc, frc)), r2inv);
+        wel = __fmul_rn(wlj, elj);
+        wec = __fmul_rn(wc, ec);
+    } else {
+        fs = __fmul_rn(__fadd_rn(frlj, frc), r2inv);
+        wel = elj;
+        wec = ec;
+    }
     fs = in ? fs : 0.0f;
-    acc.elj = __fadd_rn(acc.elj, in ? __fmul_rn(wlj, elj) : 0.0f);
-    acc.ec = __fadd_rn(acc.ec, in ? __fmul_rn(wc, ec) : 0.0f);
-    // rounded products and sums written out (never contracted to FMA), so
-    // the result does not depend on how the caller's code was inlined
-    const float fdx = __fmul_rn(fs, dx), fdy = __fmul_rn(fs, dy), fdz = __fmul_rn(fs, dz);
-    acc.fx = __fsub_rn(acc.fx, fdx);
-    acc.fy = __fsub_rn(acc.fy, fdy);
-    acc.fz = __fsub_rn(acc.fz, fdz);
-    fjx = fdx;  // F_j = -F_i
-    fjy = fdy;
-    fjz = fdz;
+    acc.elj = __fadd_rn(acc.elj, in ? wel : 0.0f);
+    acc.ec = __fadd_rn(acc.ec, in ? wec : 0.0f);
+    acc.fx = __fmaf_rn(-fs, dx, acc.fx);
+    acc.fy = __fmaf_rn(-fs, dy, acc.fy);
+    acc.fz = __fmaf_rn(-fs, dz, acc.fz);
+    fjx = __fmaf_rn(fs, dx, fjx);  // F_j = -F_i
+    fjy = __fmaf_rn(fs, dy, fjy);
+    fjz = __fmaf_rn(fs, dz, fjz);
 }
 
 // Contribution to a staged j atom, exactly at the 2^32 fixed-point grid of
@@ -743,7 +755,7 @@ __device__ __forceinline__ bool tile_member(const ForceArgs &A, const TileI &ti,
 // Masked evaluation of one pair of a tile (see eval_pair); the force on j
 // is added to fj.
 template <int RAD, bool SPECIAL, bool DEBUG>
-__device__ __forceinline__ void tile_eval(const ForceArgs &A, const float2 *__restrict__ lj, const TileI &ti, bool in,
+__device__ __forceinline__ void tile_eval(const ForceArgs &A, const float4 *__restrict__ lj, const TileI &ti, bool in,
                                           float dx, float dy, float dz, float r2, float4 pj, int tj, bool is14,
                                           int jorig, Acc &acc, float &fjx, float &fjy, float &fjz)
 {
@@ -755,12 +767,9 @@ __device__ __forceinline__ void tile_eval(const ForceArgs &A, const float2 *__re
             A.dbg_ij[2 * q + 1] = max(ti.orig, jorig);
         }
     }
-    float gx, gy, gz;
-    eval_pair<RAD>(A.P, lj, A.rtab, ti.trow, ti.q, in, dx, dy, dz, in ? r2 : 1.0f, pj.w, tj, SPECIAL && is14, acc, gx,
-                   gy, gz);
-    fjx = __fadd_rn(fjx, gx);
-    fjy = __fadd_rn(fjy, gy);
-    fjz = __fadd_rn(fjz, gz);
+    // only a special entry can hold r2 = 0 (an atom and itself, masked)
+    eval_pair<RAD, SPECIAL>(A.P, lj, A.rtab, ti.trow, ti.q, in, dx, dy, dz, SPECIAL ? (in ? r2 : 1.0f) : r2, pj.w, tj,
+                            is14, acc, fjx, fjy, fjz);
 }
 
 // One listed cluster J against the lane's two i atoms.  The tile's i atoms
@@ -773,7 +782,7 @@ __device__ __forceinline__ void tile_eval(const ForceArgs &A, const float2 *__re
 // entries have a periodic shift code.  (Each kind has its own code: the
 // plain kind, most entries, then carries no weights or image selects.)
 template <int RAD, bool VIRIAL, bool DEBUG, bool SPECIAL, bool IMG>
-__device__ __forceinline__ void tile_entry(const ForceArgs &A, const float2 *__restrict__ lj,
+__device__ __forceinline__ void tile_entry(const ForceArgs &A, const float4 *__restrict__ lj,
                                            const int *__restrict__ spart, int I, uint32_t ent, float4 pj, int tj,
                                            const TileI &ia, const TileI &ib, int jj, int ih, float Lx, float Ly,
                                            float Lz, Acc &acA, Acc &acB, float (&wimg)[6], bool &ovf)
@@ -886,9 +895,17 @@ __global__ void __launch_bounds__(kTileWarps * 32, ACENB_TILE_MIN_BLOCKS) k_forc
     const int T = A.P.n_types;
     const int K = A.K;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, jj = lane & 7, ih = lane >> 3;
-    float2 *lj = reinterpret_cast<float2 *>(smem);
-    int *spart = reinterpret_cast<int *>(smem + align16((size_t)T * T * 8)) + w * kCluster * K;
-    for (int k = threadIdx.x; k < T * T; k += blockDim.x) lj[k] = A.lj_tab[k];
+    float4 *lj = reinterpret_cast<float4 *>(smem);  // (A, B, 12 A, 6 B) per type pair
+    size_t off = (size_t)T * T * 16;
+    int *spart = reinterpret_cast<int *>(smem + off) + w * kCluster * K;
+    off += align16((size_t)kTileWarps * kCluster * K * 4);
+    float4 *sjp = reinterpret_cast<float4 *>(smem + off) + w * 32 * kCluster;  // staged j coordinates + charges
+    off += (size_t)kTileWarps * 32 * kCluster * 16;
+    int *sjt = reinterpret_cast<int *>(smem + off) + w * 32 * kCluster;  // staged j types
+    for (int k = threadIdx.x; k < T * T; k += blockDim.x) {
+        const float2 ab = A.lj_tab[k];
+        lj[k] = make_float4(ab.x, ab.y, 12.0f * ab.x, 6.0f * ab.y);
+    }
     __syncthreads();
     const int n_units = A.counts[1] * parts;
     int cur_sys = -1;
@@ -935,18 +952,23 @@ __global__ void __launch_bounds__(kTileWarps * 32, ACENB_TILE_MIN_BLOCKS) k_forc
                 const uint32_t cur_ents = ents;
                 if (e0 + 32 < e_end)  // the next 32 entries, ahead of use
                     ents = lane < e_end - e0 - 32 ? __ldg(row + e0 + 32 + lane) : 0u;
-                uint32_t ent_n = __shfl_sync(kFull, cur_ents, 0);
-                float4 pj_n = __ldg(A.xyzq + (long long)(ent_n & kJMask) * kCluster + jj);
-                int tj_n = __ldg(A.tslot + (long long)(ent_n & kJMask) * kCluster + jj);
-                for (int k = 0; k < ne; ++k) {
-                    const uint32_t ent = ent_n;
-                    const float4 pj = pj_n;
-                    const int tj = tj_n;
-                    if (k + 1 < ne) {  // the next entry's j atoms, ahead of use
-                        ent_n = __shfl_sync(kFull, cur_ents, k + 1);
-                        pj_n = __ldg(A.xyzq + (long long)(ent_n & kJMask) * kCluster + jj);
-                        tj_n = __ldg(A.tslot + (long long)(ent_n & kJMask) * kCluster + jj);
+                // stage the batch's j atoms: lane k copies the 8 coordinates
+                // and types of entry k (atom a at swz(k, a): conflict-free
+                // reads of one entry's 8 atoms)
+                if (lane < ne) {
+                    const long long jb = (long long)(cur_ents & kJMask) * kCluster;
+#pragma unroll
+                    for (int a = 0; a < kCluster; ++a) {
+                        cp_async16(sjp + swz(lane, a), A.xyzq + jb + a);
+                        cp_async4(sjt + swz(lane, a), A.tslot + jb + a);
                     }
+                }
+                cp_async_wait_all();
+                __syncwarp();
+                for (int k = 0; k < ne; ++k) {
+                    const uint32_t ent = __shfl_sync(kFull, cur_ents, k);
+                    const float4 pj = sjp[swz(k, jj)];
+                    const int tj = sjt[swz(k, jj)];
                     const bool img = ((ent >> kShiftBit) & 0x3Fu) != 0u;
                     const bool special = (ent & kExclFlag) != 0u || ((int)(ent & kJMask) == I && !img);
                     if (img) {
@@ -965,6 +987,7 @@ __global__ void __launch_bounds__(kTileWarps * 32, ACENB_TILE_MIN_BLOCKS) k_forc
                                                                         Lx, Ly, Lz, acA, acB, wimg, ovf);
                     }
                 }
+                __syncwarp();  // the staging buffer is rewritten by the next batch
             }
             // force on the i atoms: fixed point per lane, summed over the 8
             // lanes of each atom; lanes jj < 3 add atom ih, jj = 3..5 atom ih + 4
@@ -1228,7 +1251,11 @@ static void launch_adjoint_t(nb_ctx *ctx, const ForceArgs &A)
     launch_pdl(k_adjoint<RAD>, dim3(grid), dim3(nw * 32), smem, ctx->stream, A);
 }
 
-size_t tile_smem_bytes(int T, int K) { return align16((size_t)T * T * 8) + (size_t)kTileWarps * kCluster * K * 4; }
+size_t tile_smem_bytes(int T, int K)
+{
+    return (size_t)T * T * 16 + align16((size_t)kTileWarps * kCluster * K * 4) +
+           (size_t)kTileWarps * 32 * kCluster * (16 + 4);
+}
 
 template <int RAD, bool VIRIAL, bool DEBUG>
 static void launch_force_t(nb_ctx *ctx, const ForceArgs &A)

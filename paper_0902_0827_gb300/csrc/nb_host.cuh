@@ -170,10 +170,14 @@ inline nb_status init_pair_params(const nb_params &P0, PairParams &pp)
         const double rc2 = (double)pp.rc2, rs2 = (double)pp.rs2;
         pp.sw_c0 = (float)(rc2 - 3.0 * rs2);
         pp.sw_inv = (float)(1.0 / ((rc2 - rs2) * (rc2 - rs2) * (rc2 - rs2)));
+        pp.sw_a = (float)(1.0 / ((rc2 - rs2) * (rc2 - rs2)));
+        pp.sw_b = (float)(-2.0 / ((rc2 - rs2) * (rc2 - rs2) * (rc2 - rs2)));
+        pp.sw_c = (float)(12.0 / ((rc2 - rs2) * (rc2 - rs2) * (rc2 - rs2)));
     } else {
         pp.rs2 = pp.rc2;  // r2 > rs2 never holds inside the cutoff
         pp.sw_c0 = 0.0f;
         pp.sw_inv = 0.0f;
+        pp.sw_a = pp.sw_b = pp.sw_c = 0.0f;
     }
     pp.ke = P0.coulomb_k > 0.0f ? P0.coulomb_k : (float)kDefaultKe;
     pp.alpha = P0.ewald_alpha;

@@ -76,6 +76,7 @@ struct PairParams {
     float rc, rs2;       // FP32 cutoff and switch distance squared
     float sw_c0;         // rc2 - 3 rs2
     float sw_inv;        // 1 / (rc2 - rs2)^3
+    float sw_a, sw_b, sw_c;  // 1 / (rc2 - rs2)^2, -2 sw_inv, 12 sw_inv (forward kernel's form of the switch)
     float ke;            // Coulomb constant
     float alpha_half;    // alpha / 2: t = 1 / (1 + (alpha/2) r)
     float alpha;         // Ewald alpha

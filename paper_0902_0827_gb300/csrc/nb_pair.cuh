@@ -55,25 +55,25 @@ __device__ __forceinline__ float disp_r2(float xj, float yj, float zj, float xi,
     return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
 }
 
-// Radial part of one pair at squared distance r2 (inside the cutoff):
+// Radial part of one pair at squared distance r2 (inside the cutoff), from
+// rinv = 1/r, r2inv = 1/r2 and the type pair's LJ coefficients
+// lj = (A, B, 12 A, 6 B):
 //   elj, ec : LJ (switched) and Coulomb energies (unweighted);
 //   frlj, frc : -dU/dr * r of each part.
 template <bool EWALD, bool SWITCH>
-__device__ __forceinline__ void pair_radial(const PairParams &P, float r2, float rinv, float A, float B,
+__device__ __forceinline__ void pair_radial(const PairParams &P, float r2, float rinv, float r2inv, float4 lj,
                                             float qq, float &elj, float &frlj, float &ec, float &frc)
 {
-    const float r2inv = rinv * rinv;
     const float ir6 = r2inv * r2inv * r2inv;
-    const float t6 = B * ir6;
-    const float t12 = A * ir6 * ir6;
-    elj = t12 - t6;
-    frlj = fmaf(12.0f, t12, -6.0f * t6);
+    elj = ir6 * fmaf(lj.x, ir6, -lj.y);   // A r^-12 - B r^-6
+    frlj = ir6 * fmaf(lj.z, ir6, -lj.w);  // 12 A r^-12 - 6 B r^-6
     if (SWITCH) {
-        // S = (rc2 - r2)^2 (rc2 + 2 r2 - 3 rs2) / (rc2 - rs2)^3 and
-        // r dS/dr = 12 r2 (rc2 - r2)(rs2 - r2) / (rc2 - rs2)^3 for r > rs.
-        const float t = P.rc2 - r2;
-        const float S = t * t * fmaf(2.0f, r2, P.sw_c0) * P.sw_inv;
-        const float rdS = 12.0f * P.sw_inv * r2 * t * (P.rs2 - r2);
+        // with t = rc2 - r2 and u = rs2 - r2, for r > rs:
+        // S = t^2 (rc2 + 2 r2 - 3 rs2) / (rc2 - rs2)^3 = t^2 (sw_a + sw_b u),
+        // r dS/dr = 12 r2 t u / (rc2 - rs2)^3 = sw_c r2 t u.
+        const float t = P.rc2 - r2, u = P.rs2 - r2;
+        const float S = (t * t) * fmaf(P.sw_b, u, P.sw_a);
+        const float rdS = P.sw_c * r2 * t * u;
         const bool sw = r2 > P.rs2;
         frlj = sw ? fmaf(S, frlj, -elj * rdS) : frlj;
         elj = sw ? S * elj : elj;
@@ -82,10 +82,10 @@ __device__ __forceinline__ void pair_radial(const PairParams &P, float r2, float
         const float r = r2 * rinv;
         const float t = fast_rcp(fmaf(P.alpha_half, r, 1.0f));
         const float ex = fast_exp2(r2 * P.neg_a2_log2e);   // exp(-alpha^2 r^2)
-        const float erfcv = ex * erfcx_poly(P, t);
-        ec = qq * erfcv * rinv;
+        const float erfcr = ex * erfcx_poly(P, t) * rinv;  // erfc(alpha r) / r
+        ec = qq * erfcr;
         // -d/dr [erfc(a r)/r] * r = erfc(a r)/r + (2a/sqrt(pi)) exp(-a^2 r^2)
-        frc = qq * fmaf(erfcv, rinv, P.two_a_sqpi * ex);
+        frc = qq * fmaf(P.two_a_sqpi, ex, erfcr);
     } else {
         ec = qq * rinv;
         frc = ec;
