@@ -527,7 +527,7 @@ __global__ void __launch_bounds__(kListWarps * 32)
     }
 }
 
-cudaError_t launch_build(nb_ctx *ctx, const float *d_pos)
+cudaError_t launch_build_cells(nb_ctx *ctx, const float *d_pos)
 {
     auto &d = ctx->d;
     cudaStream_t st = ctx->stream;
@@ -542,6 +542,15 @@ cudaError_t launch_build(nb_ctx *ctx, const float *d_pos)
     if (e == cudaSuccess)
         e = launch_pdl(k_colsort, dim3(ctx->n_cols), dim3(kSortThreads), 0, st, d.col_count, d.col_slot, d.col_sys,
                        d.sys, d.stage, d.wpos, d.xyzq, d.tslot, d.perm, d.inv, d.bb, d.clus_sys, d.zbin);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_lists(nb_ctx *ctx)
+{
+    auto &d = ctx->d;
+    cudaStream_t st = ctx->stream;
+    cudaError_t e = cudaSuccess;
     const int lw = kListWarps;
     const int lblocks = (int)std::max<int64_t>(1, (ctx->clus_cap + lw - 1) / lw);
     if (e == cudaSuccess)
@@ -550,6 +559,12 @@ cudaError_t launch_build(nb_ctx *ctx, const float *d_pos)
                        d.list, d.list_n, d.pslot, d.status);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
+}
+
+cudaError_t launch_build(nb_ctx *ctx, const float *d_pos)
+{
+    const cudaError_t e = launch_build_cells(ctx, d_pos);
+    return e != cudaSuccess ? e : launch_build_lists(ctx);
 }
 
 }  // namespace acenb

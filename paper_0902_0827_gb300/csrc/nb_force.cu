@@ -1257,8 +1257,11 @@ size_t tile_smem_bytes(int T, int K)
            (size_t)kTileWarps * 32 * kCluster * (16 + 4);
 }
 
+// beside_pme: the PME chain, forked before the list kernel, runs on its side
+// stream during this kernel; the persistent grid then leaves one block slot
+// per SM free, so that the PME kernels run alongside instead of after it.
 template <int RAD, bool VIRIAL, bool DEBUG>
-static void launch_force_t(nb_ctx *ctx, const ForceArgs &A)
+static void launch_force_t(nb_ctx *ctx, const ForceArgs &A, bool beside_pme)
 {
     const size_t smem = tile_smem_bytes(A.P.n_types, A.K);
     static bool attr_set = false;
@@ -1270,7 +1273,7 @@ static void launch_force_t(nb_ctx *ctx, const ForceArgs &A)
     // persistent grid: never more blocks than can be resident at once
     int resident = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_force<RAD, VIRIAL, DEBUG>, kTileWarps * 32, smem);
-    const int per_sm = std::max(1, std::min(ctx->tune.blocks_per_sm, resident));
+    const int per_sm = std::max(1, std::min(ctx->tune.blocks_per_sm, resident) - (beside_pme ? 1 : 0));
     const int parts = ctx->tune.list_split > 0 ? ctx->tune.list_split : kDefaultListSplit;
     launch_pdl(k_force<RAD, VIRIAL, DEBUG>, dim3(ctx->num_sms * per_sm), dim3(kTileWarps * 32), smem,
                ctx->stream, A, parts);
@@ -1336,6 +1339,13 @@ cudaError_t launch_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, con
         cudaError_t e = launch_pme_fork(ctx, d_pos, d_q);
         if (e != cudaSuccess) return e;
     }
+    return launch_forces_packed(ctx, d_F, d_energy, d_virial, debug_pairs, pme, false);
+}
+
+cudaError_t launch_forces_packed(nb_ctx *ctx, float *d_F, double *d_energy, double *d_virial, bool debug_pairs,
+                                 bool pme, bool beside_pme)
+{
+    auto &d = ctx->d;
     ForceArgs A = make_args(ctx);
     A.F = d_F;
     A.facc = d.facc;
@@ -1344,17 +1354,17 @@ cudaError_t launch_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, con
     const bool prof = ctx->profiling && ctx->prof_n < (int)ctx->prof_ev.size() / 2;
     if (prof) cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n], ctx->stream);
     if (debug_pairs) {  // the pair set does not depend on the radial functions
-        if (ewald) launch_force_t<1, false, true>(ctx, A);
-        else launch_force_t<0, false, true>(ctx, A);
+        if (ewald) launch_force_t<1, false, true>(ctx, A, beside_pme);
+        else launch_force_t<0, false, true>(ctx, A, beside_pme);
     } else if (ctx->tab_n > 0) {
-        if (virial) launch_force_t<2, true, false>(ctx, A);
-        else launch_force_t<2, false, false>(ctx, A);
+        if (virial) launch_force_t<2, true, false>(ctx, A, beside_pme);
+        else launch_force_t<2, false, false>(ctx, A, beside_pme);
     } else if (ewald) {
-        if (virial) launch_force_t<1, true, false>(ctx, A);
-        else launch_force_t<1, false, false>(ctx, A);
+        if (virial) launch_force_t<1, true, false>(ctx, A, beside_pme);
+        else launch_force_t<1, false, false>(ctx, A, beside_pme);
     } else {
-        if (virial) launch_force_t<0, true, false>(ctx, A);
-        else launch_force_t<0, false, false>(ctx, A);
+        if (virial) launch_force_t<0, true, false>(ctx, A, beside_pme);
+        else launch_force_t<0, false, false>(ctx, A, beside_pme);
     }
     if (prof) {
         cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n + 1], ctx->stream);

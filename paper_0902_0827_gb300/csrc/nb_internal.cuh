@@ -211,8 +211,17 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
 
 // Launchers implemented in the .cu files (all asynchronous on ctx->stream).
 cudaError_t launch_build(nb_ctx *ctx, const float *d_pos);
+// the two halves of launch_build: binning, column sort and cluster boxes;
+// then the cluster-pair lists
+cudaError_t launch_build_cells(nb_ctx *ctx, const float *d_pos);
+cudaError_t launch_build_lists(nb_ctx *ctx);
 cudaError_t launch_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type,
                           float *d_F, double *d_energy, double *d_virial, bool debug_pairs);
+// launch_forces after its pack (and, when pme_forked, the PME fork): the
+// short-range kernel, the PME join and the unpack; beside_pme: the PME chain
+// was forked early enough to share the SMs with the short-range kernel
+cudaError_t launch_forces_packed(nb_ctx *ctx, float *d_F, double *d_energy, double *d_virial, bool debug_pairs,
+                                 bool pme_forked, bool beside_pme);
 size_t force_smem_for(int T, int scap, int K);
 cudaError_t launch_pack(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type, bool zero_sums);
 cudaError_t launch_type_grad(nb_ctx *ctx, const double *gsig_tab, const double *geps_tab, double *gsig, double *geps);

@@ -572,13 +572,22 @@ static cudaError_t launch_bonded(nb_ctx *ctx, const float *d_pos)
 }
 
 // Cell list, short-range forces (+ PME) and bonded forces at d_pos.
+// Forces at d_pos: cell list, short-range forces, PME (when enabled) and
+// bonded terms.  The PME chain needs the sorted atoms but not the pair
+// lists, so it is forked onto its side stream right after the column sort
+// and the charge pack: it overlaps the list kernel and the short-range
+// kernel.
 static cudaError_t md_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type)
 {
     MdState &M = *ctx->md;
-    cudaError_t e = launch_build(ctx, d_pos);
+    cudaError_t e = launch_build_cells(ctx, d_pos);
+    if (e == cudaSuccess) e = launch_pack(ctx, d_pos, d_q, d_type, true);
+    const bool pme = ctx->pme != nullptr;
+    if (e == cudaSuccess && pme) e = launch_pme_fork(ctx, d_pos, d_q);
+    if (e == cudaSuccess) e = launch_build_lists(ctx);
     if (e != cudaSuccess) return e;
     ctx->built = true;
-    e = launch_forces(ctx, d_pos, d_q, d_type, M.Fnb, M.enb, nullptr, false);
+    e = launch_forces_packed(ctx, M.Fnb, M.enb, nullptr, false, pme, pme);
     if (e != cudaSuccess) return e;
     return launch_bonded(ctx, d_pos);
 }
