@@ -80,6 +80,7 @@ def parse():
                     help="time only the step with tabulated radial functions (for profiling)")
     ap.add_argument("--md-only", action="store_true", help="time only the MD leg (for profiling)")
     ap.add_argument("--large-only", action="store_true", help="time only the 1 M-atom leg (for profiling)")
+    ap.add_argument("--adjoint-only", action="store_true", help="time only the adjoint leg (for profiling)")
     return ap.parse_args()
 
 
@@ -517,9 +518,14 @@ def main():
     props = torch.cuda.get_device_properties(dev)
     n_sms = props.multi_processor_count
     s = S.solvated_chain()
-    if args.pme_only or args.tables_only or args.md_only or args.large_only:
+    if args.pme_only or args.tables_only or args.md_only or args.large_only or args.adjoint_only:
         flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)
-        if args.large_only:
+        if args.adjoint_only:
+            actx = nb.Nonbonded(s)
+            apos, aq, atyp = nb.concat_inputs([s], device=dev)
+            actx.build(apos)
+            print(json.dumps({"adjoint": adjoint_leg(actx, apos, aq, atyp, args.steps, flush, float("nan"), 0)}))
+        elif args.large_only:
             print(json.dumps({"large": large_leg(args.steps, flush, dev)}))
         elif args.pme_only:
             print(json.dumps({"pme": pme_leg(s, args.steps, flush, dev, 0, 0.0)}))

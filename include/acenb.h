@@ -100,10 +100,9 @@ typedef struct {
 
 /* Tuning knobs (chosen by the autotuner; defaults are safe). */
 typedef struct {
-    int32_t blocks_per_sm;  /* blocks per SM of the persistent force grids, 1..8 */
-    int32_t stage_capacity; /* adjoint kernel: cluster-pair entries staged in shared memory per
-                               block pass (at most 64 are used), 16..512, multiple of 4
-                               (longer lists are processed in chunks) */
+    int32_t blocks_per_sm;  /* blocks per SM of the forward kernel's persistent grid, 1..8 */
+    int32_t stage_capacity; /* no effect (both kernels stage their lists in 32-entry batches);
+                               validated as 16..512, multiple of 4 */
     int32_t list_capacity;  /* entries of each half of a cluster's pair list (the half the
                                forward kernel visits, and the other half), 64..65536,
                                multiple of 4 */

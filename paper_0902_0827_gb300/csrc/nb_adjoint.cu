@@ -2,9 +2,9 @@
 // given G = dL/dF and gE = dL/dE (per system, LJ and Coulomb parts) it returns
 // dL/dx (the Hessian-vector product -H G plus the energy term), dL/dq and the
 // gradients with respect to the type-pair parameters sig_ab, eps_ab.  The
-// pair list is recomputed from the last build (the same staging, pruning and
-// membership steps as the force kernel, in its adjoint mode); nothing per pair
-// is stored between the forward and the adjoint.
+// pairs are found again from the last build's cluster-pair lists (the same
+// tiles and membership test as the forward kernel); nothing per pair is
+// stored between the forward and the adjoint.
 #include <cuda_runtime.h>
 
 #include "nb_internal.cuh"

@@ -10,28 +10,9 @@
 // forces on i kept in registers, forces on j summed over lanes (see the
 // comment above k_force).
 //
-// Adjoint (k_adjoint), the paper's one-cell-per-block staging of the
-// neighbour cells in shared memory, re-cut for this machine:
-//   block = one 8-atom cluster I at a time (persistent grid of blocks);
-//   warp  = one i atom of I.
-// For each cluster the block stages I's cluster-pair list and, for every
-// listed cluster J, its 8 coordinates+charges, 8 types, 8 dL/dF vectors and
-// bounding box into shared memory with asynchronous copies (cp.async) issued
-// by all threads; coordinates and types are swizzled by J so that lanes
-// reading the same atom slot of different clusters hit different banks.  Each
-// warp then
-//   (1) prunes the staged clusters whose bounding box lies beyond the cutoff
-//       of its own atom;
-//   (2) membership: one surviving cluster per lane, its 8 atoms tested with
-//       the exact FP32 predicate (exclusions and the i == j case removed, the
-//       paper's "inner" test, only for flagged clusters) into an 8-bit mask;
-//   (3) compaction: a warp scan of the mask counts places every in-range
-//       (cluster, atom) item into a per-warp ring in shared memory;
-//   (4) compute: full 32-pair steps of the ring, one pair per lane, FP32.
-// The j-atom terms go to block-shared fixed-point slots of the staged atoms
-// (integer atomics), flushed to the global fixed-point sums when the chunk
-// is done; the i-atom terms are summed over the warp and added once per
-// cluster.
+// Adjoint (k_adjoint): the same tiles, work units and staging, with the
+// pair adjoint; the type-pair gradients go to a block table in shared
+// memory.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -42,8 +23,6 @@
 namespace acenb {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kRing = 512;  // per-warp ring of in-range (cluster, atom) items
-constexpr int kAdjStage = 64;  // staging capacity cap of the adjoint (its larger shared footprint)
 
 struct ForceArgs {
     const SysDesc *sys;
@@ -58,7 +37,6 @@ struct ForceArgs {
     const int *list_n;        // [NC*2]
     const int *pslot;         // [S*K] partner slots (slot << 1) | is14, -1 pad
     int cap;                  // entries per half list
-    int scap;
     int K;
     const float2 *lj_tab;
     const float4 *rtab;       // [n*3] tabulated radial functions, or null
@@ -90,70 +68,12 @@ __device__ __forceinline__ long long to_fixed(float v, int *status)
     return __float2ll_rn(v * 4294967296.0f);
 }
 
-// Shared memory of the adjoint kernel.
-struct ForceSmem {
-    float2 *lj;
-    uint32_t *lst;             // list entries of the staged chunks [2][scap] (double buffer)
-    uint32_t *ent;             // entries of the current chunk
-    float4 *pos;
-    int *typ;
-    float4 *bb;
-    uint16_t *surv;
-    uint32_t *ring;
-    int *jf;                   // j-atom sums of the staged chunk, [hi, lo][4][scap * 8] (see add_jf): dL/dx, dL/dq
-    float4 *gj;                // staged dL/dF of the j atoms
-    float4 *ljd;               // derivative factors of the type pairs
-    unsigned long long *tacc;  // block table of fixed-point parameter gradients
-};
-
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
-
-__host__ __device__ inline size_t force_smem_bytes(int T, int scap, int nwarps)
-{
-    size_t b = (size_t)scap * kCluster * 16 + (size_t)T * T * 16 + (size_t)T * T * 16 + (size_t)scap * kCluster * 4 * 8;
-    b += (size_t)2 * scap * 4;
-    b += align16((size_t)T * T * 8);
-    b += (size_t)scap * kCluster * 16;
-    b += (size_t)scap * kCluster * 4;
-    b += (size_t)scap * 2 * 16;
-    b += align16((size_t)nwarps * scap * 2);
-    b += (size_t)nwarps * kRing * 4;
-    return b;
-}
-
-__device__ __forceinline__ ForceSmem carve(unsigned char *smem, int T, int scap, int nwarps, int w)
-{
-    ForceSmem S;
-    size_t off = 0;
-    S.lst = reinterpret_cast<uint32_t *>(smem + off);
-    off += (size_t)2 * scap * 4;
-    S.jf = reinterpret_cast<int *>(smem + off);
-    off += (size_t)scap * kCluster * 4 * 8;
-    S.gj = reinterpret_cast<float4 *>(smem + off);
-    off += (size_t)scap * kCluster * 16;
-    S.ljd = reinterpret_cast<float4 *>(smem + off);
-    off += (size_t)T * T * 16;
-    S.tacc = reinterpret_cast<unsigned long long *>(smem + off);
-    off += (size_t)T * T * 16;
-    S.lj = reinterpret_cast<float2 *>(smem + off);
-    off += align16((size_t)T * T * 8);
-    S.ent = nullptr;  // points into lst, per staged chunk
-    S.pos = reinterpret_cast<float4 *>(smem + off);
-    off += (size_t)scap * kCluster * 16;
-    S.typ = reinterpret_cast<int *>(smem + off);
-    off += (size_t)scap * kCluster * 4;
-    S.bb = reinterpret_cast<float4 *>(smem + off);
-    off += (size_t)scap * 2 * 16;
-    S.surv = reinterpret_cast<uint16_t *>(smem + off) + (size_t)w * scap;
-    off += align16((size_t)nwarps * scap * 2);
-    S.ring = reinterpret_cast<uint32_t *>(smem + off) + (size_t)w * kRing;
-    return S;
-}
 
 __device__ __forceinline__ void cp_async16(void *dst, const void *src)
 {
@@ -172,61 +92,6 @@ __device__ __forceinline__ void cp_async_wait_all()
 
 // Slot of atom k of staged entry e (swizzle by e, conflict-free lane access).
 __device__ __forceinline__ int swz(int e, int k) { return e * kCluster + (k ^ (e & (kCluster - 1))); }
-
-// List entry e of cluster I: the half list first, then (adjoint) the other
-// half.
-__device__ __forceinline__ uint32_t list_entry(const ForceArgs &A, int I, int nA, int e)
-{
-    const long long row = 2ll * I * A.cap;
-    return __ldg(A.list + (e < nA ? row + e : row + A.cap + (e - nA)));
-}
-
-// Stage the n list entries from c0 of cluster I into S.ent, and for every
-// listed cluster J its 8 coordinates+charges, 8 types, 8 dL/dF vectors and
-// bounding box, with asynchronous copies issued by every thread of the
-// block.
-__device__ __forceinline__ void stage_chunk(const ForceArgs &A, const ForceSmem &S, int I, int nA, int c0, int n,
-                                            float3 L)
-{
-    for (int p = threadIdx.x; p < n * kCluster; p += blockDim.x) {
-        const int e = p >> 3, k = p & 7;
-        const uint32_t ent = list_entry(A, I, nA, c0 + e);
-        if (k == 0) S.ent[e] = ent;
-        const long long j = (long long)(ent & kJMask) * kCluster + k;
-        // axes with a j-side image (code 1) are staged as fl(x_j - L): the
-        // first operation of the exact displacement (x_j - L) - x_i
-        const uint32_t code = (ent >> kShiftBit) & 0x3Fu;
-        const uint32_t jside = code & ~(code >> 1) & 0x15u;  // bit 2a set: axis a has code 1
-        if (jside) {
-            float4 v = __ldg(A.xyzq + j);
-            if (jside & 0x01u) v.x = __fsub_rn(v.x, L.x);
-            if (jside & 0x04u) v.y = __fsub_rn(v.y, L.y);
-            if (jside & 0x10u) v.z = __fsub_rn(v.z, L.z);
-            S.pos[swz(e, k)] = v;
-        } else {
-            cp_async16(S.pos + swz(e, k), A.xyzq + j);
-        }
-        cp_async4(S.typ + swz(e, k), A.tslot + j);
-        cp_async16(S.gj + swz(e, k), A.gslot + j);
-        if (k < 2) {
-            // the box is staged at J's image (shifted by -L for code 1, +L
-            // for code 2 on each axis): only a filter, rounding is harmless
-            const float4 *src = A.bb + (long long)(ent & kJMask) * 2 + k;
-            if (code) {
-                float4 v = __ldg(src);
-                const uint32_t cx = code & 3u, cy = (code >> 2) & 3u, cz = code >> 4;
-                v.x += cx == 1u ? -L.x : (cx == 2u ? L.x : 0.0f);
-                v.y += cy == 1u ? -L.y : (cy == 2u ? L.y : 0.0f);
-                v.z += cz == 1u ? -L.z : (cz == 2u ? L.z : 0.0f);
-                S.bb[2 * e + k] = v;
-            } else {
-                cp_async16(S.bb + 2 * e + k, src);
-            }
-        }
-    }
-    cp_async_wait_all();
-    __syncthreads();
-}
 
 struct Acc {
     float fx, fy, fz, elj, ec;
@@ -255,11 +120,18 @@ __device__ __forceinline__ long long to_fixed_tab(float v, int *status)
 // through dU/dA = w S r^-12, dU/dB = -w S r^-6 and the chain factors
 // dA/dsig = 48 eps sig^11, dB/dsig = 24 eps sig^5, dA/deps = 4 sig^12,
 // dB/deps = 4 sig^6 of the type pair.
+struct AdjTables {
+    const float2 *lj;           // (A, B) per type pair
+    const float4 *ljd;          // derivative factors per type pair
+    unsigned long long *tacc;   // block table of fixed-point parameter gradients
+};
+
 template <bool EWALD>
-__device__ __forceinline__ void eval_pair_adj(const PairParams &P, const ForceSmem &S, int ti_row, float qi_ke, float gix,
+__device__ __forceinline__ void eval_pair_adj(const PairParams &P, const AdjTables &S, int ti_row, float qi_ke, float gix,
                                               float giy, float giz, float gE_lj, float gE_c, bool in, float dx,
                                               float dy, float dz, float r2, float qj, int tj, float4 gj, bool is14,
-                                              int *status, AccAdj &acc, float &jx, float &jy, float &jz, float &jq)
+                                              int *status, AccAdj &acc, float &jx, float &jy, float &jz, float &jq,
+                                              float &dsig, float &deps)
 {
     if (!in) {  // masked lanes: keep every product finite (padding sits far away)
         dx = 0.0f;
@@ -328,11 +200,36 @@ __device__ __forceinline__ void eval_pair_adj(const PairParams &P, const ForceSm
     const float uA1 = wlj * fmaf(S1, ir12, -12.0f * Sw * ir12 * rinv);
     const float uB1 = -wlj * fmaf(S1, ir6, -6.0f * Sw * ir6 * rinv);
     const float gA = fmaf(uA1 * rinv, gd, gE_lj * uA), gB = fmaf(uB1 * rinv, gd, gE_lj * uB);
-    if (in) {
-        const float4 c = S.ljd[ti_row + tj];
-        const float dsig = fmaf(gA, c.x, gB * c.y), deps = fmaf(gA, c.z, gB * c.w);
-        atomicAdd(&S.tacc[2 * (ti_row + tj)], (unsigned long long)to_fixed_tab(dsig, status));
-        atomicAdd(&S.tacc[2 * (ti_row + tj) + 1], (unsigned long long)to_fixed_tab(deps, status));
+    const float4 c = S.ljd[ti_row + tj];
+    dsig = in ? fmaf(gA, c.x, gB * c.y) : 0.0f;
+    deps = in ? fmaf(gA, c.z, gB * c.w) : 0.0f;
+}
+
+// 64-bit integer add to shared memory by two native 32-bit atomics: the low
+// word's carry (seen from the value the first atomic returns) goes into the
+// high word, so the 64-bit sum is exact and order independent.  (A 64-bit
+// shared-memory atomic add is a compare-and-swap loop here, and many lanes
+// of a warp hit the same few type-pair slots: the loop's retries cost more
+// than the whole pair adjoint.)
+__device__ __forceinline__ void shared_add64(unsigned long long *p, unsigned long long v)
+{
+    unsigned int *w = reinterpret_cast<unsigned int *>(p);  // little endian: low word first
+    const unsigned int lo = (unsigned int)v, hi = (unsigned int)(v >> 32);
+    const unsigned int old = atomicAdd(w, lo);
+    const unsigned int h = hi + ((unsigned int)(old + lo) < old ? 1u : 0u);
+    if (h) atomicAdd(w + 1, h);
+}
+
+// Add a lane's type-pair derivatives (key = t_i T + t_j, -1 for a masked
+// lane) to the block table.  (Summing equal keys over the warp first, by
+// match/ballot rounds or by the warp's integer reduction on 21-bit parts, was
+// slower than the atomics: 0.37 and 0.50 ms against 0.19 ms per adjoint
+// step.)
+__device__ __forceinline__ void add_type_grads(const AdjTables &S, int key, float dsig, float deps, int *status)
+{
+    if (key >= 0) {
+        shared_add64(&S.tacc[2 * key], (unsigned long long)to_fixed_tab(dsig, status));
+        shared_add64(&S.tacc[2 * key + 1], (unsigned long long)to_fixed_tab(deps, status));
     }
 }
 
@@ -381,304 +278,6 @@ __device__ __forceinline__ void eval_pair(const PairParams &P, const float4 *__r
     fjx = __fmaf_rn(fs, dx, fjx);  // F_j = -F_i
     fjy = __fmaf_rn(fs, dy, fjy);
     fjz = __fmaf_rn(fs, dz, fjz);
-}
-
-// Contribution to a staged j atom, exactly at the 2^32 fixed-point grid of
-// the global sums, with two 32-bit shared-memory integer atomics:
-// f 2^32 = hi 2^24 + lo with hi = rint(f 2^8) and lo = rint((f 2^8 - hi) 2^24)
-// (the products and the difference are exact in FP32, and lo is an integer
-// whenever |f 2^8| >= 1).  A chunk adds at most 8 contributions (one per i
-// atom of the block's cluster) to a slot, so for |f| < 2^19 neither 32-bit
-// sum can overflow; larger (or non-finite) values go straight to the global
-// 64-bit sums (nc components per slot there).  The hi array is at slot, the
-// lo array nc * js further.
-template <int NC>
-__device__ __forceinline__ void add_jf(const ForceArgs &A, const ForceSmem &S, long long *gsum, int e, int k, int slot,
-                                       int comp, float f)
-{
-    if (fabsf(f) < 524288.0f) {
-        const float t = f * 256.0f;
-        const float hf = rintf(t);
-        atomicAdd(S.jf + slot, (int)hf);
-        atomicAdd(S.jf + slot + NC * A.scap * kCluster, __float2int_rn((t - hf) * 16777216.0f));
-    } else {
-        long long *g = gsum + (long long)NC * ((long long)(S.ent[e] & kJMask) * kCluster + k) + comp;
-        atomicAdd((unsigned long long *)g, (unsigned long long)to_fixed(f, A.status));
-    }
-}
-
-// Per-warp data of the i atom (adjoint kernel).
-struct IAtom {
-    float xi, yi, zi, xim, yim, zim;
-    float qi;     // ke * q_i
-    int ti_row;   // t_i * T
-    float gix, giy, giz, gE_lj, gE_c;  // dL/dF_i, dL/dE_LJ, dL/dE_C
-};
-
-// One ring item: staged entry e (bits 7..15), i-side image per axis (bits
-// 4..6), atom k (bits 1..3), 1-4 flag (bit 0).  The displacement is
-// recomputed with the same operations as the membership test (same value).
-template <int RAD>
-__device__ __forceinline__ void eval_item(const ForceArgs &A, const ForceSmem &S, const IAtom &ia, uint32_t item,
-                                          bool active, AccAdj &acc)
-{
-    const int e = (int)(item >> 7), k = (int)((item >> 1) & 7u);
-    const float ax = (item & 0x10u) ? ia.xim : ia.xi, ay = (item & 0x20u) ? ia.yim : ia.yi,
-                az = (item & 0x40u) ? ia.zim : ia.zi;
-    const int idx = swz(e, k);
-    const float4 pj = S.pos[idx];  // j-side images already applied at staging
-    const int tj = S.typ[idx];
-    float dx, dy, dz;
-    const float r2 = disp_r2(pj.x, pj.y, pj.z, ax, ay, az, dx, dy, dz);
-    float jx, jy, jz, jq;
-    eval_pair_adj<RAD == 1>(A.P, S, ia.ti_row, ia.qi, ia.gix, ia.giy, ia.giz, ia.gE_lj, ia.gE_c, active, dx, dy, dz,
-                            active ? r2 : 1.0f, pj.w, tj, S.gj[idx], (item & 1u) != 0u, A.status, acc, jx, jy, jz, jq);
-    if (active) {
-        const int js = A.scap * kCluster;
-        add_jf<4>(A, S, A.gacc, e, k, idx, 0, jx);
-        add_jf<4>(A, S, A.gacc, e, k, idx + js, 1, jy);
-        add_jf<4>(A, S, A.gacc, e, k, idx + 2 * js, 2, jz);
-        add_jf<4>(A, S, A.gacc, e, k, idx + 3 * js, 3, jq);
-    }
-}
-
-// Per-cluster inputs of a warp (one i atom): system, sorted coordinates and
-// charge, type, half-list length, topology partner slot of this lane and
-// dL/dF of the atom.
-struct ClusterHead {
-    int sys_id;
-    float4 pi;
-    int ti;
-    int nA;
-    int pe;
-    float4 gi;
-};
-
-__device__ __forceinline__ ClusterHead load_head(const ForceArgs &A, int I, int w, int lane)
-{
-    ClusterHead h;
-    const long long islot = (long long)I * kCluster + w;
-    h.sys_id = __ldg(A.clus_sys + I);
-    h.pi = __ldg(A.xyzq + islot);
-    h.ti = __ldg(A.tslot + islot);
-    h.nA = __ldg(A.list_n + 2 * I);  // the half list: every pair once (Newton's third law)
-    h.pe = lane < A.K ? __ldg(A.pslot + islot * A.K + lane) : -1;
-    h.gi = __ldg(A.gslot + islot);
-    return h;
-}
-
-// The 2^32 fixed-point value of a hi/lo slot pair (see add_jf).
-__device__ __forceinline__ unsigned long long split_sum(const int *jf, int lo_off, int i)
-{
-    return (unsigned long long)(((long long)jf[i] << 24) + (long long)jf[lo_off + i]);
-}
-
-// Adjoint: add the block's j-atom sums (dL/dx, dL/dq) of the n staged
-// clusters listed at ent to the global fixed-point sums and clear them.
-__device__ __forceinline__ void flush_jadj(const ForceArgs &A, const ForceSmem &S, const uint32_t *ent, int n)
-{
-    const int js = A.scap * kCluster;
-    for (int p = threadIdx.x; p < n * kCluster; p += blockDim.x) {
-        const int e = p >> 3, k = (p & 7) ^ (e & 7);  // p = swz(e, k)
-        long long *g = A.gacc + 4ll * ((long long)(ent[e] & kJMask) * kCluster + k);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const unsigned long long v = split_sum(S.jf, 4 * js, c * js + p);
-            if (v) atomicAdd((unsigned long long *)&g[c], v);
-            S.jf[c * js + p] = 0;
-            S.jf[4 * js + c * js + p] = 0;
-        }
-    }
-}
-
-// Adjoint of L = sum G.F + gE_lj E_lj + gE_c E_C over the half lists (see
-// eval_pair_adj): dL/dx and dL/dq of both atoms of every pair in fixed point,
-// dL/dsig_ab and dL/deps_ab in a block table.
-template <int RAD>
-__global__ void __launch_bounds__(256, 3) k_adjoint(ForceArgs A)
-{
-    pdl_entry();
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int T = A.P.n_types;
-    const int nwarps = blockDim.x >> 5;
-    const int w = threadIdx.x >> 5;
-    const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
-    const ForceSmem S = carve(smem, T, A.scap, nwarps, w);
-    for (int k = threadIdx.x; k < T * T; k += blockDim.x) {
-        S.lj[k] = A.lj_tab[k];
-        S.ljd[k] = A.lj_d[k];
-        S.tacc[2 * k] = 0ull;
-        S.tacc[2 * k + 1] = 0ull;
-    }
-    for (int k = threadIdx.x; k < 8 * A.scap * kCluster; k += blockDim.x) S.jf[k] = 0;
-    __syncthreads();
-
-    int cur_sys = -1;
-    float Lx = 0.0f, Ly = 0.0f, Lz = 0.0f;
-    const int n_clus = A.counts[1];
-    const float rcm2 = A.P.rcm2;
-
-    for (int I = blockIdx.x; I < n_clus; I += gridDim.x) {
-        const ClusterHead cur = load_head(A, I, w, lane);
-        const int sys_id = cur.sys_id;
-        if (sys_id != cur_sys) {
-            cur_sys = sys_id;
-            Lx = A.sys[sys_id].L[0];
-            Ly = A.sys[sys_id].L[1];
-            Lz = A.sys[sys_id].L[2];
-        }
-        const int islot = I * kCluster + w;
-        const float4 pi = cur.pi;
-        const bool iv = is_real_coord(pi.x);
-        IAtom ia;
-        ia.ti_row = cur.ti * T;
-        ia.xi = pi.x;
-        ia.yi = pi.y;
-        ia.zi = pi.z;
-        ia.xim = __fsub_rn(pi.x, Lx);
-        ia.yim = __fsub_rn(pi.y, Ly);
-        ia.zim = __fsub_rn(pi.z, Lz);
-        ia.qi = pi.w * A.P.ke;
-        const float xi = ia.xi, yi = ia.yi, zi = ia.zi, xim = ia.xim, yim = ia.yim, zim = ia.zim;
-        ia.gix = cur.gi.x;
-        ia.giy = cur.gi.y;
-        ia.giz = cur.gi.z;
-        ia.gE_lj = A.dLdE ? (float)A.dLdE[2 * sys_id] : 0.0f;
-        ia.gE_c = A.dLdE ? (float)A.dLdE[2 * sys_id + 1] : 0.0f;
-        AccAdj acc = {0.0f, 0.0f, 0.0f, 0.0f};
-        const int nE = cur.nA;
-        const int pe = cur.pe;
-        __syncthreads();  // the staging buffers are free
-
-        for (int c0 = 0, ci = 0; c0 < nE; c0 += A.scap, ++ci) {
-            const int nC = min(A.scap, nE - c0);
-            if (c0 > 0) {
-                __syncthreads();  // the staging buffers are free
-                flush_jadj(A, S, S.lst + ((ci - 1) & 1) * A.scap, A.scap);
-            }
-            ForceSmem Sc = S;
-            Sc.ent = S.lst + (ci & 1) * A.scap;
-            stage_chunk(A, Sc, I, nE, c0, nC, make_float3(Lx, Ly, Lz));
-            if (!iv) continue;
-            // (1) prune staged clusters against this atom
-            int ns = 0;
-            for (int e0 = 0; e0 < nC; e0 += 32) {
-                const int e = e0 + lane;
-                bool keep = false;
-                if (e < nC) {
-                    const float4 lo = S.bb[2 * e], hi = S.bb[2 * e + 1];  // at J's image
-                    const float gx = fmaxf(fmaxf(lo.x - xi, xi - hi.x), 0.0f);
-                    const float gy = fmaxf(fmaxf(lo.y - yi, yi - hi.y), 0.0f);
-                    const float gz = fmaxf(fmaxf(lo.z - zi, zi - hi.z), 0.0f);
-                    keep = gx * gx + gy * gy + gz * gz < rcm2;
-                }
-                const unsigned b = __ballot_sync(kFull, keep);
-                if (keep) S.surv[ns + __popc(b & lt)] = (uint16_t)e;
-                ns += __popc(b);
-            }
-            __syncwarp();
-            // (2) membership: one surviving cluster per lane -> 8-bit mask
-            // (3) compaction into the ring, (4) full 32-pair compute steps
-            int head = 0, tail = 0;
-            for (int s0 = 0; s0 < ns; s0 += 32) {
-                const int si = s0 + lane;
-                const bool sv = si < ns;
-                const int e = sv ? (int)S.surv[si] : 0;
-                const uint32_t ent = Sc.ent[e];
-                const int J = (int)(ent & kJMask);
-                const int cx = (ent >> kShiftBit) & 3, cy = (ent >> (kShiftBit + 2)) & 3,
-                          cz = (ent >> (kShiftBit + 4)) & 3;
-                // j-side images are already in the staged coordinates; the
-                // i side uses x_i - L on axes with code 2
-                const float ax = cx == 2 ? xim : xi, ay = cy == 2 ? yim : yi, az = cz == 2 ? zim : zi;
-                const uint32_t ishift = (cx == 2 ? 1u : 0u) | (cy == 2 ? 2u : 0u) | (cz == 2 ? 4u : 0u);
-                const uint32_t ibase = ((uint32_t)e << 7) | (ishift << 4);
-                uint32_t exm = sv ? 0u : 0xFFu, m14 = 0u;
-                if (J == I && ((ent >> kShiftBit) & 0x3Fu) == 0u)
-                    exm |= (2u << w) - 1u;  // pairs of I itself: j > i only
-                const bool fl = sv && (ent & kExclFlag) != 0u;
-                if (__any_sync(kFull, fl)) {
-                    for (int m = 0; m < A.K; ++m) {
-                        const int pv = __shfl_sync(kFull, pe, m);
-                        if (fl && pv >= 0 && ((pv >> 1) >> 3) == J) {
-                            const uint32_t b = 1u << ((pv >> 1) & (kCluster - 1));
-                            if (pv & 1) m14 |= b;
-                            else exm |= b;
-                        }
-                    }
-                }
-                uint32_t mask = 0u;
-                const int sw = e & (kCluster - 1);
-#pragma unroll
-                for (int k = 0; k < kCluster; ++k) {
-                    const float4 pj = S.pos[e * kCluster + (k ^ sw)];
-                    float dx, dy, dz;
-                    const float r2 = disp_r2(pj.x, pj.y, pj.z, ax, ay, az, dx, dy, dz);
-                    mask |= (r2 < A.P.rc2) ? (1u << k) : 0u;
-                }
-                mask &= ~exm;
-                // exclusive scan of the per-lane counts
-                const int cnt = __popc(mask);
-                int incl = cnt;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(kFull, incl, o);
-                    if (lane >= o) incl += y;
-                }
-                const int total = __shfl_sync(kFull, incl, 31);
-                int pos = tail + incl - cnt;
-                uint32_t mm = mask;
-#pragma unroll
-                for (int m = 0; m < kCluster; ++m) {
-                    if (mm) {
-                        const int k = __ffs(mm) - 1;
-                        mm &= mm - 1u;
-                        S.ring[(pos++) & (kRing - 1)] = ibase | ((uint32_t)k << 1) | ((m14 >> k) & 1u);
-                    }
-                }
-                tail += total;
-                __syncwarp();
-                while (tail - head >= 32) {
-                    eval_item<RAD>(A, Sc, ia, S.ring[(head + lane) & (kRing - 1)], true, acc);
-                    head += 32;
-                }
-                __syncwarp();
-            }
-            if (tail > head) {  // partial step before the staged data is replaced
-                const int n = tail - head;
-                const uint32_t item = lane < n ? S.ring[(head + lane) & (kRing - 1)] : 0u;
-                eval_item<RAD>(A, Sc, ia, item, lane < n, acc);
-            }
-            __syncwarp();
-        }
-        if (nE > 0) {
-            const int last = (nE - 1) / A.scap;
-            __syncthreads();
-            flush_jadj(A, S, S.lst + (last & 1) * A.scap, nE - last * A.scap);
-        }
-        if (!iv) continue;
-        long long v0 = to_fixed(acc.dx, A.status), v1 = to_fixed(acc.dy, A.status), v2 = to_fixed(acc.dz, A.status),
-                  v3 = to_fixed(acc.dq, A.status);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            v0 += __shfl_xor_sync(kFull, v0, o);
-            v1 += __shfl_xor_sync(kFull, v1, o);
-            v2 += __shfl_xor_sync(kFull, v2, o);
-            v3 += __shfl_xor_sync(kFull, v3, o);
-        }
-        if (lane == 0) {
-            unsigned long long *g = (unsigned long long *)A.gacc + 4ll * islot;
-            atomicAdd(g, (unsigned long long)v0);
-            atomicAdd(g + 1, (unsigned long long)v1);
-            atomicAdd(g + 2, (unsigned long long)v2);
-            atomicAdd(g + 3, (unsigned long long)v3);
-        }
-    }
-    // block table of parameter gradients -> global (integer sums)
-    __syncthreads();
-    for (int k = threadIdx.x; k < 2 * T * T; k += blockDim.x)
-        if (S.tacc[k]) atomicAdd((unsigned long long *)&A.tab_acc[k], S.tacc[k]);
 }
 
 // ---------------------------------------------------------------------------
@@ -1041,6 +640,222 @@ __global__ void __launch_bounds__(kTileWarps * 32, ACENB_TILE_MIN_BLOCKS) k_forc
     }
 }
 
+// ---------------------------------------------------------------------------
+// Adjoint kernel on cluster-pair tiles (k_adjoint): the forward
+// kernel's tiles, half-tile votes, work units and staging, with the pair
+// adjoint of eval_pair_adj.  The j-side terms of an entry (dL/dx_j, dL/dq_j)
+// are summed over the 4 lanes of each j atom and lane ih adds component ih
+// (x, y, z, q) to the fixed-point sums; the i-side terms stay in registers
+// for the unit; the type-pair gradients go to a block table in shared
+// memory (integer atomics) flushed at the end.
+constexpr int kAdjWarps = 4;             // warps per block of the adjoint tile kernel
+
+template <int RAD, bool SPECIAL, bool IMG>
+__device__ __forceinline__ void tile_adj_entry(const ForceArgs &A, const AdjTables &tab, const int *__restrict__ spart,
+                                               int I, uint32_t ent, float4 pj, int tj, float4 gj, const TileI &ia,
+                                               const TileI &ib, float4 gia, float4 gib, float gE_lj, float gE_c,
+                                               int jj, int ih, float Lx, float Ly, float Lz, AccAdj &acA, AccAdj &acB,
+                                               bool &ovf)
+{
+    const int J = (int)(ent & kJMask);
+    const uint32_t code = IMG ? (ent >> kShiftBit) & 0x3Fu : 0u;
+    if (IMG) {
+        if ((code & 3u) == 1u) pj.x = __fsub_rn(pj.x, Lx);
+        if (((code >> 2) & 3u) == 1u) pj.y = __fsub_rn(pj.y, Ly);
+        if ((code >> 4) == 1u) pj.z = __fsub_rn(pj.z, Lz);
+    }
+    float dxA, dyA, dzA, r2A, dxB, dyB, dzB, r2B;
+    bool inA = tile_member<IMG>(A, ia, code, pj, Lx, Ly, Lz, dxA, dyA, dzA, r2A);
+    bool inB = tile_member<IMG>(A, ib, code, pj, Lx, Ly, Lz, dxB, dyB, dzB, r2B);
+    bool s14A = false, s14B = false;
+    if (SPECIAL) {
+        if (J == I && code == 0u) {
+            inA = inA && jj > ih;
+            inB = inB && jj > ih + 4;
+        }
+        if (ent & kExclFlag) {
+            const int jslot = J * kCluster + jj;
+            for (int m = 0; m < A.K; ++m) {
+                const int pa = spart[ih * A.K + m], pb = spart[(ih + 4) * A.K + m];
+                if (pa >= 0 && (pa >> 1) == jslot) {
+                    if (pa & 1) s14A = true;
+                    else inA = false;
+                }
+                if (pb >= 0 && (pb >> 1) == jslot) {
+                    if (pb & 1) s14B = true;
+                    else inB = false;
+                }
+            }
+        }
+    }
+    const bool anyA = __any_sync(kFull, inA), anyB = __any_sync(kFull, inB);
+    if (!anyA && !anyB) return;
+    float jx = 0.0f, jy = 0.0f, jz = 0.0f, jq = 0.0f;
+    if (anyA) {
+        float a, b, c, d, ds, de;
+        eval_pair_adj<RAD == 1>(A.P, tab, ia.trow, ia.q, gia.x, gia.y, gia.z, gE_lj, gE_c, inA, dxA, dyA, dzA,
+                                inA ? r2A : 1.0f, pj.w, tj, gj, s14A, A.status, acA, a, b, c, d, ds, de);
+        add_type_grads(tab, inA ? ia.trow + tj : -1, ds, de, A.status);
+        jx = a;
+        jy = b;
+        jz = c;
+        jq = d;
+    }
+    if (anyB) {
+        float a, b, c, d, ds, de;
+        eval_pair_adj<RAD == 1>(A.P, tab, ib.trow, ib.q, gib.x, gib.y, gib.z, gE_lj, gE_c, inB, dxB, dyB, dzB,
+                                inB ? r2B : 1.0f, pj.w, tj, gj, s14B, A.status, acB, a, b, c, d, ds, de);
+        add_type_grads(tab, inB ? ib.trow + tj : -1, ds, de, A.status);
+        jx = __fadd_rn(jx, a);
+        jy = __fadd_rn(jy, b);
+        jz = __fadd_rn(jz, c);
+        jq = __fadd_rn(jq, d);
+    }
+#pragma unroll
+    for (int o = 8; o < 32; o <<= 1) {
+        jx = __fadd_rn(jx, __shfl_xor_sync(kFull, jx, o));
+        jy = __fadd_rn(jy, __shfl_xor_sync(kFull, jy, o));
+        jz = __fadd_rn(jz, __shfl_xor_sync(kFull, jz, o));
+        jq = __fadd_rn(jq, __shfl_xor_sync(kFull, jq, o));
+    }
+    const float gc = ih == 0 ? jx : (ih == 1 ? jy : (ih == 2 ? jz : jq));
+    atomicAdd((unsigned long long *)&A.gacc[32ll * J + 4 * jj + ih], (unsigned long long)tile_fixed(gc, ovf));
+}
+
+template <int RAD>
+__global__ void __launch_bounds__(kAdjWarps * 32) k_adjoint(ForceArgs A, int parts)
+{
+    pdl_entry();
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int T = A.P.n_types;
+    const int K = A.K;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, jj = lane & 7, ih = lane >> 3;
+    size_t off = 0;
+    unsigned long long *tacc = reinterpret_cast<unsigned long long *>(smem + off);
+    off += (size_t)T * T * 16;
+    float4 *ljd = reinterpret_cast<float4 *>(smem + off);
+    off += (size_t)T * T * 16;
+    float2 *lj = reinterpret_cast<float2 *>(smem + off);
+    off += align16((size_t)T * T * 8);
+    int *spart = reinterpret_cast<int *>(smem + off) + w * kCluster * K;
+    off += align16((size_t)kAdjWarps * kCluster * K * 4);
+    float4 *sjp = reinterpret_cast<float4 *>(smem + off) + w * 32 * kCluster;  // staged j coordinates + charges
+    off += (size_t)kAdjWarps * 32 * kCluster * 16;
+    float4 *sjg = reinterpret_cast<float4 *>(smem + off) + w * 32 * kCluster;  // staged j dL/dF
+    off += (size_t)kAdjWarps * 32 * kCluster * 16;
+    int *sjt = reinterpret_cast<int *>(smem + off) + w * 32 * kCluster;  // staged j types
+    for (int k = threadIdx.x; k < T * T; k += blockDim.x) {
+        lj[k] = A.lj_tab[k];
+        ljd[k] = A.lj_d[k];
+        tacc[2 * k] = 0ull;
+        tacc[2 * k + 1] = 0ull;
+    }
+    __syncthreads();
+    const AdjTables tab{lj, ljd, tacc};
+    const int n_units = A.counts[1] * parts;
+    int cur_sys = -1;
+    float Lx = 0.0f, Ly = 0.0f, Lz = 0.0f, gE_lj = 0.0f, gE_c = 0.0f;
+    bool ovf = false;
+    int u = 0;
+    if (lane == 0) u = atomicAdd(A.work, 1);
+    u = __shfl_sync(kFull, u, 0);
+    while (u < n_units) {
+        int u_next = 0;
+        if (lane == 0) u_next = atomicAdd(A.work, 1);
+        const int I = u / parts, part = u - I * parts;
+        const int sys_id = __ldg(A.clus_sys + I);
+        if (sys_id != cur_sys) {
+            cur_sys = sys_id;
+            Lx = A.sys[sys_id].L[0];
+            Ly = A.sys[sys_id].L[1];
+            Lz = A.sys[sys_id].L[2];
+            gE_lj = A.dLdE ? (float)A.dLdE[2 * sys_id] : 0.0f;
+            gE_c = A.dLdE ? (float)A.dLdE[2 * sys_id + 1] : 0.0f;
+        }
+        const int nA = __ldg(A.list_n + 2 * I);
+        const int per = (nA + parts - 1) / parts;
+        const int e_begin = min(nA, part * per), e_end = min(nA, e_begin + per);
+        if (e_begin < e_end) {
+            const long long s0 = (long long)I * kCluster;
+            const TileI ia = load_tile_i(A, s0 + ih, T, false);
+            const TileI ib = load_tile_i(A, s0 + ih + 4, T, false);
+            const float4 gia = __ldg(A.gslot + s0 + ih), gib = __ldg(A.gslot + s0 + ih + 4);
+            for (int t = lane; t < kCluster * K; t += 32) spart[t] = __ldg(A.pslot + s0 * K + t);
+            __syncwarp();
+            AccAdj acA = {0.0f, 0.0f, 0.0f, 0.0f}, acB = {0.0f, 0.0f, 0.0f, 0.0f};
+            const uint32_t *row = A.list + 2ll * I * A.cap;
+            uint32_t ents = lane < e_end - e_begin ? __ldg(row + e_begin + lane) : 0u;
+            for (int e0 = e_begin; e0 < e_end; e0 += 32) {
+                const int ne = min(32, e_end - e0);
+                const uint32_t cur_ents = ents;
+                if (e0 + 32 < e_end) ents = lane < e_end - e0 - 32 ? __ldg(row + e0 + 32 + lane) : 0u;
+                if (lane < ne) {
+                    const long long jb = (long long)(cur_ents & kJMask) * kCluster;
+#pragma unroll
+                    for (int a = 0; a < kCluster; ++a) {
+                        cp_async16(sjp + swz(lane, a), A.xyzq + jb + a);
+                        cp_async16(sjg + swz(lane, a), A.gslot + jb + a);
+                        cp_async4(sjt + swz(lane, a), A.tslot + jb + a);
+                    }
+                }
+                cp_async_wait_all();
+                __syncwarp();
+                for (int k = 0; k < ne; ++k) {
+                    const uint32_t ent = __shfl_sync(kFull, cur_ents, k);
+                    const float4 pj = sjp[swz(k, jj)];
+                    const float4 gj = sjg[swz(k, jj)];
+                    const int tj = sjt[swz(k, jj)];
+                    const bool img = ((ent >> kShiftBit) & 0x3Fu) != 0u;
+                    const bool special = (ent & kExclFlag) != 0u || ((int)(ent & kJMask) == I && !img);
+                    if (img) {
+                        if (special)
+                            tile_adj_entry<RAD, true, true>(A, tab, spart, I, ent, pj, tj, gj, ia, ib, gia, gib, gE_lj,
+                                                            gE_c, jj, ih, Lx, Ly, Lz, acA, acB, ovf);
+                        else
+                            tile_adj_entry<RAD, false, true>(A, tab, spart, I, ent, pj, tj, gj, ia, ib, gia, gib,
+                                                             gE_lj, gE_c, jj, ih, Lx, Ly, Lz, acA, acB, ovf);
+                    } else {
+                        if (special)
+                            tile_adj_entry<RAD, true, false>(A, tab, spart, I, ent, pj, tj, gj, ia, ib, gia, gib,
+                                                             gE_lj, gE_c, jj, ih, Lx, Ly, Lz, acA, acB, ovf);
+                        else
+                            tile_adj_entry<RAD, false, false>(A, tab, spart, I, ent, pj, tj, gj, ia, ib, gia, gib,
+                                                              gE_lj, gE_c, jj, ih, Lx, Ly, Lz, acA, acB, ovf);
+                    }
+                }
+                __syncwarp();  // the staging buffers are rewritten by the next batch
+            }
+            // i-side terms: fixed point per lane, summed over the 8 lanes of
+            // each atom; lane jj < 4 adds component jj of atom ih, jj >= 4
+            // component jj - 4 of atom ih + 4
+            long long v[8] = {to_fixed(acA.dx, A.status), to_fixed(acA.dy, A.status), to_fixed(acA.dz, A.status),
+                              to_fixed(acA.dq, A.status), to_fixed(acB.dx, A.status), to_fixed(acB.dy, A.status),
+                              to_fixed(acB.dz, A.status), to_fixed(acB.dq, A.status)};
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1)
+#pragma unroll
+                for (int c = 0; c < 8; ++c) v[c] += __shfl_xor_sync(kFull, v[c], o);
+            long long mine = v[0];
+#pragma unroll
+            for (int c = 1; c < 8; ++c) mine = jj == c ? v[c] : mine;
+            if (mine != 0) {
+                const long long slot = s0 + ih + (jj < 4 ? 0 : 4);
+                atomicAdd((unsigned long long *)&A.gacc[4 * slot + (jj & 3)], (unsigned long long)mine);
+            }
+            if (__any_sync(kFull, ovf)) {
+                if (lane == 0) atomicOr(A.status, ST_OVERFLOW);
+                ovf = false;
+            }
+            __syncwarp();  // spart is rewritten by the next unit
+        }
+        u = __shfl_sync(kFull, u_next, 0);
+    }
+    // block table of parameter gradients -> global (integer sums)
+    __syncthreads();
+    for (int k = threadIdx.x; k < 2 * T * T; k += blockDim.x)
+        if (tacc[k]) atomicAdd((unsigned long long *)&A.tab_acc[k], tacc[k]);
+}
+
 // Gather charges and types into sorted order and check that the positions
 // are those of the last build.
 __global__ void k_pack(int slot_cap, const int *__restrict__ counts, const int *__restrict__ perm,
@@ -1233,24 +1048,6 @@ __global__ void k_unpack_adjoint(int slot_cap, const int *__restrict__ counts, c
     if (dq) dq[a] = __ll2float_rn(gacc[4ll * s + 3]) * sc;
 }
 
-template <int RAD>
-static void launch_adjoint_t(nb_ctx *ctx, const ForceArgs &A)
-{
-    const int nw = kCluster;
-    const size_t smem = force_smem_bytes(A.P.n_types, A.scap, nw);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_adjoint<RAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-        attr_set = true;
-    }
-    // persistent grid: never more blocks than can be resident at once
-    int resident = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_adjoint<RAD>, nw * 32, smem);
-    const int per_sm = std::max(1, std::min(ctx->tune.blocks_per_sm, resident));
-    const int grid = ctx->num_sms * per_sm;
-    launch_pdl(k_adjoint<RAD>, dim3(grid), dim3(nw * 32), smem, ctx->stream, A);
-}
-
 size_t tile_smem_bytes(int T, int K)
 {
     return (size_t)T * T * 16 + align16((size_t)kTileWarps * kCluster * K * 4) +
@@ -1296,7 +1093,6 @@ static ForceArgs make_args(nb_ctx *ctx)
     A.list_n = d.list_n;
     A.pslot = d.pslot;
     A.cap = ctx->list_cap;
-    A.scap = ctx->stage_cap;
     A.K = ctx->K;
     A.lj_tab = d.lj_tab;
     A.rtab = d.rtab;
@@ -1317,7 +1113,7 @@ cudaError_t launch_pack(nb_ctx *ctx, const float *d_pos, const float *d_q, const
     return launch_pdl(k_pack, dim3((S + tb - 1) / tb), dim3(tb), 0, ctx->stream, S, d.counts, d.perm, d.xyzq,
                       d.tslot, d_pos, d_q, d_type, d.sys, d.atom_sys, ctx->pp.n_types, d.status,
                       zero_sums ? d.facc : nullptr, zero_sums ? d.sys_acc : nullptr, kTaskVals * ctx->n_sys,
-                      zero_sums ? d.counts + 3 : nullptr);
+                      d.counts + 3);
 }
 
 cudaError_t launch_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type, float *d_F,
@@ -1392,9 +1188,32 @@ cudaError_t launch_forces_packed(nb_ctx *ctx, float *d_F, double *d_energy, doub
     return cudaGetLastError();
 }
 
+size_t adjoint_smem_bytes(int T, int K)
+{
+    return (size_t)T * T * 32 + align16((size_t)T * T * 8) + align16((size_t)kAdjWarps * kCluster * K * 4) +
+           (size_t)kAdjWarps * 32 * kCluster * (16 + 16 + 4);
+}
+
+template <int RAD>
+static void launch_adjoint_t(nb_ctx *ctx, const ForceArgs &A)
+{
+    const size_t smem = adjoint_smem_bytes(A.P.n_types, A.K);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_adjoint<RAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        attr_set = true;
+    }
+    int resident = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_adjoint<RAD>, kAdjWarps * 32, smem);
+    const int parts = ctx->tune.list_split > 0 ? ctx->tune.list_split : kDefaultListSplit;
+    launch_pdl(k_adjoint<RAD>, dim3(ctx->num_sms * std::max(1, resident)), dim3(kAdjWarps * 32), smem,
+               ctx->stream, A, parts);
+}
+
 size_t force_smem_for(int T, int scap, int K)
 {
-    return std::max(force_smem_bytes(T, std::min(scap, kAdjStage), kCluster), tile_smem_bytes(T, K));
+    (void)scap;  // unused: the kernels stage per 32-entry batch
+    return std::max(tile_smem_bytes(T, K), adjoint_smem_bytes(T, K));
 }
 
 cudaError_t launch_adjoint_tile(nb_ctx *ctx, const double *d_dLdE, float *d_dpos, float *d_dq)
@@ -1408,7 +1227,6 @@ cudaError_t launch_adjoint_tile(nb_ctx *ctx, const double *d_dLdE, float *d_dpos
     A.dq = d_dq;
     A.tab_acc = d.tab_grad;
     A.gacc = d.gacc;
-    A.scap = std::min(ctx->stage_cap, kAdjStage);
     if (ctx->pp.ewald) launch_adjoint_t<1>(ctx, A);
     else launch_adjoint_t<0>(ctx, A);
     const int tb = 256;

@@ -143,7 +143,7 @@ struct nb_ctx {
     int64_t clus_cap = 0;
     int K = 1;                     // partners per atom (>= 1)
     int comb_rule = 0;
-    int stage_cap = 96;            // list entries staged per block pass
+    int stage_cap = 96;            // nb_tuning.stage_capacity (no effect on the kernels)
     int list_cap = 512;            // entries per half list of a cluster
     int tab_n = 0;                 // radial-function table intervals (0: direct evaluation)
     int64_t zb_total = 0;          // entries of the z-bin index
