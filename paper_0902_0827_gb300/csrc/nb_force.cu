@@ -650,25 +650,31 @@ __global__ void __launch_bounds__(kTileWarps * 32, ACENB_TILE_MIN_BLOCKS) k_forc
 // memory (integer atomics) flushed at the end.
 constexpr int kAdjWarps = 4;             // warps per block of the adjoint tile kernel
 
-template <int RAD, bool SPECIAL, bool IMG>
-__device__ __forceinline__ void tile_adj_entry(const ForceArgs &A, const AdjTables &tab, const int *__restrict__ spart,
-                                               int I, uint32_t ent, float4 pj, int tj, float4 gj, const TileI &ia,
-                                               const TileI &ib, float4 gia, float4 gib, float gE_lj, float gE_c,
-                                               int jj, int ih, float Lx, float Ly, float Lz, AccAdj &acA, AccAdj &acB,
-                                               bool &ovf)
+// One instance serves every kind of entry (special and image entries as
+// uniform branches): the pair adjoint is long, and an instance per kind, as
+// in the forward kernel, overflowed the instruction cache (0.188 against
+// 0.168 ms per adjoint step).
+template <int RAD>
+__device__ __forceinline__ void tile_adj_entry(bool special, bool img, const ForceArgs &A, const AdjTables &tab,
+                                               const int *__restrict__ spart, int I, uint32_t ent, float4 pj, int tj,
+                                               float4 gj, const TileI &ia, const TileI &ib, float4 gia, float4 gib,
+                                               float gE_lj, float gE_c, int jj, int ih, float Lx, float Ly, float Lz,
+                                               AccAdj &acA, AccAdj &acB, bool &ovf)
 {
     const int J = (int)(ent & kJMask);
-    const uint32_t code = IMG ? (ent >> kShiftBit) & 0x3Fu : 0u;
-    if (IMG) {
+    const uint32_t code = img ? (ent >> kShiftBit) & 0x3Fu : 0u;
+    if (img) {
         if ((code & 3u) == 1u) pj.x = __fsub_rn(pj.x, Lx);
         if (((code >> 2) & 3u) == 1u) pj.y = __fsub_rn(pj.y, Ly);
         if ((code >> 4) == 1u) pj.z = __fsub_rn(pj.z, Lz);
     }
     float dxA, dyA, dzA, r2A, dxB, dyB, dzB, r2B;
-    bool inA = tile_member<IMG>(A, ia, code, pj, Lx, Ly, Lz, dxA, dyA, dzA, r2A);
-    bool inB = tile_member<IMG>(A, ib, code, pj, Lx, Ly, Lz, dxB, dyB, dzB, r2B);
+    bool inA = img ? tile_member<true>(A, ia, code, pj, Lx, Ly, Lz, dxA, dyA, dzA, r2A)
+                   : tile_member<false>(A, ia, code, pj, Lx, Ly, Lz, dxA, dyA, dzA, r2A);
+    bool inB = img ? tile_member<true>(A, ib, code, pj, Lx, Ly, Lz, dxB, dyB, dzB, r2B)
+                   : tile_member<false>(A, ib, code, pj, Lx, Ly, Lz, dxB, dyB, dzB, r2B);
     bool s14A = false, s14B = false;
-    if (SPECIAL) {
+    if (special) {
         if (J == I && code == 0u) {
             inA = inA && jj > ih;
             inB = inB && jj > ih + 4;
@@ -807,21 +813,8 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_adjoint(ForceArgs A, int par
                     const int tj = sjt[swz(k, jj)];
                     const bool img = ((ent >> kShiftBit) & 0x3Fu) != 0u;
                     const bool special = (ent & kExclFlag) != 0u || ((int)(ent & kJMask) == I && !img);
-                    if (img) {
-                        if (special)
-                            tile_adj_entry<RAD, true, true>(A, tab, spart, I, ent, pj, tj, gj, ia, ib, gia, gib, gE_lj,
-                                                            gE_c, jj, ih, Lx, Ly, Lz, acA, acB, ovf);
-                        else
-                            tile_adj_entry<RAD, false, true>(A, tab, spart, I, ent, pj, tj, gj, ia, ib, gia, gib,
-                                                             gE_lj, gE_c, jj, ih, Lx, Ly, Lz, acA, acB, ovf);
-                    } else {
-                        if (special)
-                            tile_adj_entry<RAD, true, false>(A, tab, spart, I, ent, pj, tj, gj, ia, ib, gia, gib,
-                                                             gE_lj, gE_c, jj, ih, Lx, Ly, Lz, acA, acB, ovf);
-                        else
-                            tile_adj_entry<RAD, false, false>(A, tab, spart, I, ent, pj, tj, gj, ia, ib, gia, gib,
-                                                              gE_lj, gE_c, jj, ih, Lx, Ly, Lz, acA, acB, ovf);
-                    }
+                    tile_adj_entry<RAD>(special, img, A, tab, spart, I, ent, pj, tj, gj, ia, ib, gia, gib, gE_lj, gE_c,
+                                        jj, ih, Lx, Ly, Lz, acA, acB, ovf);
                 }
                 __syncwarp();  // the staging buffers are rewritten by the next batch
             }
