@@ -564,7 +564,25 @@ __global__ void __launch_bounds__(kTileWarps * 32, ACENB_TILE_MIN_BLOCKS) k_forc
                 }
                 cp_async_wait_all();
                 __syncwarp();
-                for (int k = 0; k < ne; ++k) {
+                // the batch's plain entries first (no image code, no partner
+                // flag, not I itself: one code path without a dispatch), then
+                // the others
+                const bool my_img = ((cur_ents >> kShiftBit) & 0x3Fu) != 0u;
+                const bool my_spc = (cur_ents & kExclFlag) != 0u || ((int)(cur_ents & kJMask) == I && !my_img);
+                const unsigned in_batch = lane < ne;
+                unsigned plain = __ballot_sync(kFull, in_batch && !my_img && !my_spc);
+                unsigned other = __ballot_sync(kFull, in_batch) & ~plain;
+                while (plain) {
+                    const int k = __ffs(plain) - 1;
+                    plain &= plain - 1u;
+                    const uint32_t ent = __shfl_sync(kFull, cur_ents, k);
+                    tile_entry<RAD, VIRIAL, DEBUG, false, false>(A, lj, spart, I, ent, sjp[swz(k, jj)],
+                                                                sjt[swz(k, jj)], ia, ib, jj, ih, Lx, Ly, Lz, acA, acB,
+                                                                wimg, ovf);
+                }
+                while (other) {
+                    const int k = __ffs(other) - 1;
+                    other &= other - 1u;
                     const uint32_t ent = __shfl_sync(kFull, cur_ents, k);
                     const float4 pj = sjp[swz(k, jj)];
                     const int tj = sjt[swz(k, jj)];
@@ -578,12 +596,8 @@ __global__ void __launch_bounds__(kTileWarps * 32, ACENB_TILE_MIN_BLOCKS) k_forc
                             tile_entry<RAD, VIRIAL, DEBUG, false, true>(A, lj, spart, I, ent, pj, tj, ia, ib, jj, ih,
                                                                        Lx, Ly, Lz, acA, acB, wimg, ovf);
                     } else {
-                        if (special)
-                            tile_entry<RAD, VIRIAL, DEBUG, true, false>(A, lj, spart, I, ent, pj, tj, ia, ib, jj, ih,
-                                                                       Lx, Ly, Lz, acA, acB, wimg, ovf);
-                        else
-                            tile_entry<RAD, VIRIAL, DEBUG, false, false>(A, lj, spart, I, ent, pj, tj, ia, ib, jj, ih,
-                                                                        Lx, Ly, Lz, acA, acB, wimg, ovf);
+                        tile_entry<RAD, VIRIAL, DEBUG, true, false>(A, lj, spart, I, ent, pj, tj, ia, ib, jj, ih, Lx,
+                                                                   Ly, Lz, acA, acB, wimg, ovf);
                     }
                 }
                 __syncwarp();  // the staging buffer is rewritten by the next batch
