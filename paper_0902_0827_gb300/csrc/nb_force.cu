@@ -432,8 +432,8 @@ __device__ __forceinline__ void tile_entry(const ForceArgs &A, const float4 *__r
         fjz = __fadd_rn(fjz, __shfl_xor_sync(kFull, fjz, o));
     }
     const float fc = ih == 0 ? fjx : (ih == 1 ? fjy : fjz);
-    if (ih < 3)
-        atomicAdd((unsigned long long *)&A.facc[24ll * J + 3 * jj + ih], (unsigned long long)tile_fixed(fc, ovf));
+    const long long fv = tile_fixed(fc, ovf);  // every lane (lane ih = 3 holds z again): no branch
+    if (ih < 3) atomicAdd((unsigned long long *)&A.facc[24ll * J + 3 * jj + ih], (unsigned long long)fv);
     if (VIRIAL && IMG && ih == 0) {
         // periodic-image part of the virial: s (x) f_j with the entry's
         // shift s of j (code 1: -L, code 2: +L per axis)
@@ -546,6 +546,7 @@ __global__ void __launch_bounds__(kTileWarps * 32, ACENB_TILE_MIN_BLOCKS) k_forc
             Acc acA = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, acB = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
             const uint32_t *row = A.list + 2ll * I * A.cap;
             uint32_t ents = lane < e_end - e_begin ? __ldg(row + e_begin + lane) : 0u;
+            bool unit_img = false;  // the unit holds an image entry (warp uniform)
             for (int e0 = e_begin; e0 < e_end; e0 += 32) {
                 const int ne = min(32, e_end - e0);
                 const uint32_t cur_ents = ents;
@@ -572,6 +573,7 @@ __global__ void __launch_bounds__(kTileWarps * 32, ACENB_TILE_MIN_BLOCKS) k_forc
                 const unsigned in_batch = lane < ne;
                 unsigned plain = __ballot_sync(kFull, in_batch && !my_img && !my_spc);
                 unsigned other = __ballot_sync(kFull, in_batch) & ~plain;
+                unit_img = unit_img || __ballot_sync(kFull, in_batch && my_img) != 0u;
                 while (plain) {
                     const int k = __ffs(plain) - 1;
                     plain &= plain - 1u;
@@ -602,24 +604,25 @@ __global__ void __launch_bounds__(kTileWarps * 32, ACENB_TILE_MIN_BLOCKS) k_forc
                 }
                 __syncwarp();  // the staging buffer is rewritten by the next batch
             }
-            // force on the i atoms: fixed point per lane, summed over the 8
-            // lanes of each atom; lanes jj < 3 add atom ih, jj = 3..5 atom ih + 4
-            long long v[6] = {to_fixed(acA.fx, A.status), to_fixed(acA.fy, A.status), to_fixed(acA.fz, A.status),
-                              to_fixed(acB.fx, A.status), to_fixed(acB.fy, A.status), to_fixed(acB.fz, A.status)};
+            // force on the i atoms: the 8 lanes of each atom summed in FP32
+            // (a fixed butterfly: every lane ends with the same bits), then
+            // lanes jj < 3 add atom ih, jj = 3..5 atom ih + 4 in fixed point
+            float v[6] = {acA.fx, acA.fy, acA.fz, acB.fx, acB.fy, acB.fz};
 #pragma unroll
             for (int o = 1; o < 8; o <<= 1)
 #pragma unroll
-                for (int c = 0; c < 6; ++c) v[c] += __shfl_xor_sync(kFull, v[c], o);
-            long long mine = v[0];
+                for (int c = 0; c < 6; ++c) v[c] = __fadd_rn(v[c], __shfl_xor_sync(kFull, v[c], o));
+            float mine = v[0];
 #pragma unroll
             for (int c = 1; c < 6; ++c) mine = jj == c ? v[c] : mine;
-            if (jj < 6 && mine != 0) {
+            const long long fi = tile_fixed(mine, ovf);
+            if (jj < 6 && fi != 0) {
                 const long long slot = s0 + ih + (jj < 3 ? 0 : 4);
-                atomicAdd((unsigned long long *)&A.facc[3 * slot + (jj < 3 ? jj : jj - 3)], (unsigned long long)mine);
+                atomicAdd((unsigned long long *)&A.facc[3 * slot + (jj < 3 ? jj : jj - 3)], (unsigned long long)fi);
             }
             esum[0] += to_fixed(acA.elj, A.status) + to_fixed(acB.elj, A.status);
             esum[1] += to_fixed(acA.ec, A.status) + to_fixed(acB.ec, A.status);
-            if (VIRIAL) tile_virial_unit(wimg, wv, lane);
+            if (VIRIAL && unit_img) tile_virial_unit(wimg, wv, lane);  // image entries only add to wimg
             if (__any_sync(kFull, ovf)) {
                 if (lane == 0) atomicOr(A.status, ST_OVERFLOW);
                 ovf = false;
