@@ -620,8 +620,8 @@ __global__ void __launch_bounds__(kTileWarps * 32, ACENB_TILE_MIN_BLOCKS) k_forc
                 const long long slot = s0 + ih + (jj < 3 ? 0 : 4);
                 atomicAdd((unsigned long long *)&A.facc[3 * slot + (jj < 3 ? jj : jj - 3)], (unsigned long long)fi);
             }
-            esum[0] += to_fixed(acA.elj, A.status) + to_fixed(acB.elj, A.status);
-            esum[1] += to_fixed(acA.ec, A.status) + to_fixed(acB.ec, A.status);
+            esum[0] += tile_fixed(acA.elj, ovf) + tile_fixed(acB.elj, ovf);
+            esum[1] += tile_fixed(acA.ec, ovf) + tile_fixed(acB.ec, ovf);
             if (VIRIAL && unit_img) tile_virial_unit(wimg, wv, lane);  // image entries only add to wimg
             if (__any_sync(kFull, ovf)) {
                 if (lane == 0) atomicOr(A.status, ST_OVERFLOW);
@@ -835,19 +835,18 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_adjoint(ForceArgs A, int par
                 }
                 __syncwarp();  // the staging buffers are rewritten by the next batch
             }
-            // i-side terms: fixed point per lane, summed over the 8 lanes of
-            // each atom; lane jj < 4 adds component jj of atom ih, jj >= 4
-            // component jj - 4 of atom ih + 4
-            long long v[8] = {to_fixed(acA.dx, A.status), to_fixed(acA.dy, A.status), to_fixed(acA.dz, A.status),
-                              to_fixed(acA.dq, A.status), to_fixed(acB.dx, A.status), to_fixed(acB.dy, A.status),
-                              to_fixed(acB.dz, A.status), to_fixed(acB.dq, A.status)};
+            // i-side terms: the 8 lanes of each atom summed in FP32 (fixed
+            // butterfly), then lane jj < 4 adds component jj of atom ih,
+            // jj >= 4 component jj - 4 of atom ih + 4, in fixed point
+            float v[8] = {acA.dx, acA.dy, acA.dz, acA.dq, acB.dx, acB.dy, acB.dz, acB.dq};
 #pragma unroll
             for (int o = 1; o < 8; o <<= 1)
 #pragma unroll
-                for (int c = 0; c < 8; ++c) v[c] += __shfl_xor_sync(kFull, v[c], o);
-            long long mine = v[0];
+                for (int c = 0; c < 8; ++c) v[c] = __fadd_rn(v[c], __shfl_xor_sync(kFull, v[c], o));
+            float vm = v[0];
 #pragma unroll
-            for (int c = 1; c < 8; ++c) mine = jj == c ? v[c] : mine;
+            for (int c = 1; c < 8; ++c) vm = jj == c ? v[c] : vm;
+            const long long mine = tile_fixed(vm, ovf);
             if (mine != 0) {
                 const long long slot = s0 + ih + (jj < 4 ? 0 : 4);
                 atomicAdd((unsigned long long *)&A.gacc[4 * slot + (jj & 3)], (unsigned long long)mine);
