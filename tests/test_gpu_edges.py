@@ -137,3 +137,26 @@ def test_list_capacity_overflow_is_reported():
     ctx.build(pos)
     ctx.forces(pos, q, t)
     assert ctx.status(raise_on_error=False) == 10  # NB_ERR_CAPACITY
+
+
+def test_tuning_is_validated_and_default_split_is_four():
+    s = S.water_box()
+    ctx = nb.Nonbonded(s)
+    for bad in (dict(list_split=-1), dict(list_split=9), dict(blocks_per_sm=0), dict(blocks_per_sm=9)):
+        with pytest.raises(nb.NbError):
+            ctx.set_tuning(**bad)
+    pos, q, t = nb.concat_inputs([s])
+    outs = {}
+    for split in (0, 4, 4, 1):  # 0 selects the default split (4); every split repeats bit for bit
+        ctx.set_tuning(list_split=split)
+        ctx.build(pos)
+        F, E, W = ctx.forces(pos, q, t)
+        torch.cuda.synchronize()
+        outs.setdefault(split, []).append((F.clone(), E.clone(), W.clone()))
+    ctx.status()
+    a, b, c = outs[0][0], outs[4][0], outs[4][1]
+    for x, y in ((a, b), (b, c)):
+        assert all(torch.equal(u, v) for u, v in zip(x, y))
+    # another split only moves where the FP32 sums are cut
+    F1, F4 = outs[1][0][0].double(), a[0].double()
+    assert (torch.linalg.norm(F1 - F4) / torch.linalg.norm(F4)).item() < 1e-6
