@@ -27,12 +27,11 @@ constexpr unsigned kFull = 0xffffffffu;
 struct ForceArgs {
     const SysDesc *sys;
     const int *counts;
-    int *work;                // forward tile kernel: work-unit counter (zeroed by k_pack)
+    int *work;                // work-unit counter of the tile kernels (zeroed by k_pack)
     const float4 *xyzq;
     const int *tslot;
     const int *perm;
     const int *clus_sys;
-    const float4 *bb;
     const uint32_t *list;     // [NC*2*cap] per cluster: half list, other half
     const int *list_n;        // [NC*2]
     const int *pslot;         // [S*K] partner slots (slot << 1) | is14, -1 pad
@@ -40,7 +39,6 @@ struct ForceArgs {
     int K;
     const float2 *lj_tab;
     const float4 *rtab;       // [n*3] tabulated radial functions, or null
-    float *F;
     long long *facc;          // [S*3] fixed-point forces in sorted order (forward)
     long long *sys_acc;
     int *status;
@@ -52,8 +50,6 @@ struct ForceArgs {
     const float4 *gslot;     // [S] dL/dF in sorted order (x, y, z, 0)
     const double *dLdE;      // [n_sys*2] dL/dE_LJ, dL/dE_C, or null
     const float4 *lj_d;      // [T*T] 48 eps sig^11, 24 eps sig^5, 4 sig^12, 4 sig^6
-    float *dpos;             // [N*3] dL/dx (caller order), or null
-    float *dq;               // [N] dL/dq (caller order), or null
     long long *tab_acc;      // [T*T*2] fixed-point dL/dsig_ab, dL/deps_ab (each unique pair in one order)
     long long *gacc;         // [S*4] fixed-point dL/dx, dL/dq in sorted order (both atoms of each pair)
 };
@@ -287,16 +283,17 @@ __device__ __forceinline__ void eval_pair(const PairParams &P, const float4 *__r
 // tile: lane = jj + 8 ih holds j atom jj of J and the i atoms ih and ih + 4
 // of I, so every lane computes two pairs and the tile needs no compaction:
 // pairs beyond the cutoff (and excluded pairs, padding) are evaluated and
-// masked.  The force on i stays in the lane's registers for the whole list;
-// the force on j (two pairs per lane) is summed over the 4 lanes of that j
-// atom with shuffles and added to the global 64-bit fixed-point sums, one
-// atomic per atom and component, as is the force on i once the list is done.
-// The FP32 sums run in a fixed order and meet only in integer sums, so
-// results are run-to-run bit-identical.  A cluster's half list is cut into
-// `parts` work units, which the warps of a persistent grid claim from a
-// counter (dynamic balance of the uneven list lengths); the next unit's
-// claim, the next entry's j atoms and the next 32 list entries are loaded
-// ahead of use.
+// masked.  The force on i stays in the lane's registers for the whole work
+// unit; the force on j (two pairs per lane) is summed over the 4 lanes of
+// that j atom with shuffles and added to the global 64-bit fixed-point sums,
+// one atomic per atom and component, as is the force on i (summed over its 8
+// lanes) when the unit is done.  The FP32 sums run in a fixed order and meet
+// only in integer sums, so results are run-to-run bit-identical.  A
+// cluster's half list is cut into `parts` work units, which the warps of a
+// persistent grid claim from a counter (dynamic balance of the uneven list
+// lengths), the next claim issued while the current unit runs.  Each batch
+// of up to 32 entries has the listed clusters' atoms staged in the warp's
+// shared memory (cp.async) and is then walked, plain entries first.
 constexpr int kTileWarps = 8;            // warps per block of the tile kernel
 #ifndef ACENB_TILE_MIN_BLOCKS
 #define ACENB_TILE_MIN_BLOCKS 3          // resident blocks per SM the register budget is cut for
@@ -324,7 +321,7 @@ __device__ __forceinline__ TileI load_tile_i(const ForceArgs &A, long long slot,
     return t;
 }
 
-// Fixed-point value (2^32) of a j-force sum; a value too large for the sums
+// Fixed-point value (2^32) of an FP32 sum; a value too large for the sums
 // (or not finite) adds zero and sets ovf.
 __device__ __forceinline__ long long tile_fixed(float f, bool &ovf)
 {
@@ -1097,7 +1094,6 @@ static ForceArgs make_args(nb_ctx *ctx)
     A.tslot = d.tslot;
     A.perm = d.perm;
     A.clus_sys = d.clus_sys;
-    A.bb = d.bb;
     A.list = d.list;
     A.list_n = d.list_n;
     A.pslot = d.pslot;
@@ -1152,7 +1148,6 @@ cudaError_t launch_forces_packed(nb_ctx *ctx, float *d_F, double *d_energy, doub
 {
     auto &d = ctx->d;
     ForceArgs A = make_args(ctx);
-    A.F = d_F;
     A.facc = d.facc;
     const bool ewald = ctx->pp.ewald != 0;
     const bool virial = d_virial != nullptr;
@@ -1232,8 +1227,6 @@ cudaError_t launch_adjoint_tile(nb_ctx *ctx, const double *d_dLdE, float *d_dpos
     A.gslot = d.gslot;
     A.dLdE = d_dLdE;
     A.lj_d = d.lj_d;
-    A.dpos = d_dpos;
-    A.dq = d_dq;
     A.tab_acc = d.tab_grad;
     A.gacc = d.gacc;
     if (ctx->pp.ewald) launch_adjoint_t<1>(ctx, A);
