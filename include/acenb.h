@@ -103,8 +103,8 @@ typedef struct {
     int32_t blocks_per_sm;  /* blocks per SM of the forward kernel's persistent grid, 1..8 */
     int32_t stage_capacity; /* no effect (both kernels stage their lists in 32-entry batches);
                                validated as 16..512, multiple of 4 */
-    int32_t list_capacity;  /* entries of each half of a cluster's pair list (the half the
-                               forward kernel visits, and the other half), 64..65536,
+    int32_t list_capacity;  /* entries of a cluster's pair list (its half of the cluster pairs:
+                               each pair is listed for one of its two clusters), 64..65536,
                                multiple of 4 */
     int32_t list_split;     /* forward kernel: work units (warps) per cluster's half list,
                                1..8; 0 = default (4) */

@@ -86,8 +86,8 @@ nb_status allocate(nb_ctx *c)
     ALLOC(d.sys_acc, (int64_t)c->n_sys * kTaskVals);
     ALLOC(d.facc, S * 3);
     ALLOC(d.gacc, S * 4);
-    ALLOC(d.list, NC * 2 * c->list_cap);
-    ALLOC(d.list_n, NC * 2);
+    ALLOC(d.list, NC * c->list_cap);
+    ALLOC(d.list_n, NC);
     ALLOC(d.pslot, S * c->K);
     ALLOC(d.zbin, c->zb_total);
     ALLOC(d.tab_grad, (int64_t)T * T * 2);
@@ -474,7 +474,7 @@ nb_status nb_set_tuning(nb_ctx *ctx, const nb_tuning *t)
         // new list storage: the lists of the last build are gone
         uint32_t *nl = nullptr;
         if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return NB_ERR_CUDA;
-        if (dalloc(&nl, (size_t)ctx->clus_cap * 2 * t->list_capacity) != cudaSuccess) return NB_ERR_OOM;
+        if (dalloc(&nl, (size_t)ctx->clus_cap * t->list_capacity) != cudaSuccess) return NB_ERR_OOM;
         cudaFree(ctx->d.list);
         ctx->d.list = nl;
         ctx->list_cap = t->list_capacity;

@@ -341,10 +341,10 @@ constexpr int kPartnerRounds = (kCluster * kMaxPartners + 31) / 32;
 // +L, concatenated as virtual indices -nj..2nj-1) comes within the cutoff of
 // I form one window per column; the windows of all lanes are flattened and
 // every candidate (J, image) is tested by bounding-box gap < rc + margin.
-// Kept entries go to the half list (Newton's third law, used by the forward
-// kernel) or to the other half (the adjoint visits both), each compacted in
-// (column round, candidate round, lane) order, so the lists are
-// deterministic.  Also writes the partner slots of I's atoms and flags the
+// Of the entries kept, those of I's half (Newton's third law: every cluster
+// pair appears in the list of exactly one of its two clusters, see
+// keep_half) are compacted in (column round, candidate round, lane) order,
+// so the lists are deterministic.  Also writes the partner slots of I's atoms and flags the
 // entries whose cluster may hold a topology partner of I (a Bloom filter of
 // the partners' clusters: never a missed partner, rarely a spurious flag).
 __global__ void __launch_bounds__(kListWarps * 32)
@@ -405,9 +405,8 @@ __global__ void __launch_bounds__(kListWarps * 32)
         // conservative margin of the column-geometry test (binning rounds in FP32)
         const float cmarg = 1e-3f + 1e-6f * fmaxf(S.L[0], S.L[1]);
         const int ncx = cxb - cxa + 1, ncand = ncx * (cyb - cya + 1);
-        int nA = 0, nB = 0;
-        uint32_t *LA = list + (long long)(2 * I) * cap;
-        uint32_t *LB = LA + cap;
+        int nA = 0;
+        uint32_t *LA = list + (long long)I * cap;
         for (int g0 = 0; g0 < ncand; g0 += kListGroup) {
             // the candidate columns of this group whose geometry (a lower bound of
             // the xy gap) passes, compacted in order
@@ -501,18 +500,13 @@ __global__ void __launch_bounds__(kListWarps * 32)
                     for (int h = 0; h < 2; ++h) {
                         const bool fl = J[h] >= 0 && ((bloom >> bloom_bit(J[h] - S.clus_begin)) & 1ull);
                         const uint32_t ent = (uint32_t)J[h] | (code[h] << kShiftBit) | (fl ? kExclFlag : 0u);
-                        const bool hitA = J[h] >= 0 && keep_half(I, J[h], code[h]), hitB = J[h] >= 0 && !hitA;
-                        const unsigned bA = __ballot_sync(FULL, hitA), bB = __ballot_sync(FULL, hitB);
-                        if (hitA) {
-                            const int q = nA + __popc(bA & lt);
+                        const bool hit = J[h] >= 0 && keep_half(I, J[h], code[h]);
+                        const unsigned b = __ballot_sync(FULL, hit);
+                        if (hit) {
+                            const int q = nA + __popc(b & lt);
                             if (q < cap) LA[q] = ent;
                         }
-                        if (hitB) {
-                            const int q = nB + __popc(bB & lt);
-                            if (q < cap) LB[q] = ent;
-                        }
-                        nA += __popc(bA);
-                        nB += __popc(bB);
+                        nA += __popc(b);
                     }
                 }
                 __syncwarp();  // the owner table is rewritten by the next round
@@ -520,9 +514,8 @@ __global__ void __launch_bounds__(kListWarps * 32)
             __syncwarp();
         }
         if (lane == 0) {
-            list_n[2 * I] = min(nA, cap);
-            list_n[2 * I + 1] = min(nB, cap);
-            if (nA > cap || nB > cap) atomicOr(status, ST_CAPACITY);
+            list_n[I] = min(nA, cap);
+            if (nA > cap) atomicOr(status, ST_CAPACITY);
         }
     }
 }

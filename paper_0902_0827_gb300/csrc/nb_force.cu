@@ -32,10 +32,10 @@ struct ForceArgs {
     const int *tslot;
     const int *perm;
     const int *clus_sys;
-    const uint32_t *list;     // [NC*2*cap] per cluster: half list, other half
-    const int *list_n;        // [NC*2]
+    const uint32_t *list;     // [NC*cap] per cluster: its half list (Newton's third law)
+    const int *list_n;        // [NC] lengths
     const int *pslot;         // [S*K] partner slots (slot << 1) | is14, -1 pad
-    int cap;                  // entries per half list
+    int cap;                  // entries per list
     int K;
     const float2 *lj_tab;
     const float4 *rtab;       // [n*3] tabulated radial functions, or null
@@ -531,7 +531,7 @@ __global__ void __launch_bounds__(kTileWarps * 32, ACENB_TILE_MIN_BLOCKS) k_forc
             Ly = A.sys[sys_id].L[1];
             Lz = A.sys[sys_id].L[2];
         }
-        const int nA = __ldg(A.list_n + 2 * I);
+        const int nA = __ldg(A.list_n + I);
         const int per = (nA + parts - 1) / parts;
         const int e_begin = min(nA, part * per), e_end = min(nA, e_begin + per);
         if (e_begin < e_end) {
@@ -541,7 +541,7 @@ __global__ void __launch_bounds__(kTileWarps * 32, ACENB_TILE_MIN_BLOCKS) k_forc
             for (int t = lane; t < kCluster * K; t += 32) spart[t] = __ldg(A.pslot + s0 * K + t);
             __syncwarp();
             Acc acA = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, acB = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-            const uint32_t *row = A.list + 2ll * I * A.cap;
+            const uint32_t *row = A.list + (long long)I * A.cap;
             uint32_t ents = lane < e_end - e_begin ? __ldg(row + e_begin + lane) : 0u;
             bool unit_img = false;  // the unit holds an image entry (warp uniform)
             for (int e0 = e_begin; e0 < e_end; e0 += 32) {
@@ -792,7 +792,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_adjoint(ForceArgs A, int par
             gE_lj = A.dLdE ? (float)A.dLdE[2 * sys_id] : 0.0f;
             gE_c = A.dLdE ? (float)A.dLdE[2 * sys_id + 1] : 0.0f;
         }
-        const int nA = __ldg(A.list_n + 2 * I);
+        const int nA = __ldg(A.list_n + I);
         const int per = (nA + parts - 1) / parts;
         const int e_begin = min(nA, part * per), e_end = min(nA, e_begin + per);
         if (e_begin < e_end) {
@@ -803,7 +803,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_adjoint(ForceArgs A, int par
             for (int t = lane; t < kCluster * K; t += 32) spart[t] = __ldg(A.pslot + s0 * K + t);
             __syncwarp();
             AccAdj acA = {0.0f, 0.0f, 0.0f, 0.0f}, acB = {0.0f, 0.0f, 0.0f, 0.0f};
-            const uint32_t *row = A.list + 2ll * I * A.cap;
+            const uint32_t *row = A.list + (long long)I * A.cap;
             uint32_t ents = lane < e_end - e_begin ? __ldg(row + e_begin + lane) : 0u;
             for (int e0 = e_begin; e0 < e_end; e0 += 32) {
                 const int ne = min(32, e_end - e0);

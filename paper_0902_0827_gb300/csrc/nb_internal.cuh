@@ -114,8 +114,8 @@ struct DevBuffers {
     long long *sys_acc = nullptr;    // [n_sys*kTaskVals] per-system fixed-point energies (2^32) and virial (2^20)
     long long *facc = nullptr;       // [S*3] fixed-point forces in sorted order (both atoms of each pair)
     long long *gacc = nullptr;       // [S*4] adjoint: fixed-point dL/dx, dL/dq in sorted order
-    uint32_t *list = nullptr;        // [NC*2*list_cap] per cluster: half list, then the other half
-    int *list_n = nullptr;           // [NC*2] lengths of the two halves
+    uint32_t *list = nullptr;        // [NC*list_cap] per cluster: its half list (Newton's third law)
+    int *list_n = nullptr;           // [NC] lengths
     int *pslot = nullptr;            // [S*K] partner slots (slot << 1) | is14, -1 pad
     int2 *zbin = nullptr;            // [zb_total] z-bin index of the columns (see SysDesc)
     long long *tab_grad = nullptr;   // [T*T*2] adjoint dL/dsig_ab, dL/deps_ab (fixed point, one ordered half)
@@ -144,7 +144,7 @@ struct nb_ctx {
     int K = 1;                     // partners per atom (>= 1)
     int comb_rule = 0;
     int stage_cap = 96;            // nb_tuning.stage_capacity (no effect on the kernels)
-    int list_cap = 512;            // entries per half list of a cluster
+    int list_cap = 512;            // entries per cluster list
     int tab_n = 0;                 // radial-function table intervals (0: direct evaluation)
     int64_t zb_total = 0;          // entries of the z-bin index
     int smem_optin = 0;            // device opt-in shared memory per block

@@ -38,7 +38,7 @@ namespace {
 
 constexpr int kMaxAtoms = NB_NOALLOC_MAX_ATOMS;
 constexpr int kMaxCols = NB_NOALLOC_MAX_COLUMNS;
-constexpr int kListCap = 256;  // entries per half list
+constexpr int kListCap = 256;  // entries per cluster list
 constexpr int kZbEntries = 65536;  // z-bin index entries (bins per column shrink to fit)
 constexpr int kMaxDevices = 64;
 constexpr long long kSlots = ((long long)kMaxAtoms + (kCluster - 1) * (long long)kMaxCols + kCluster - 1) /
@@ -67,8 +67,8 @@ constexpr size_t oClusSys = oBb + a256(32ull * kClus);
 constexpr size_t oSysAcc = oClusSys + a256(4ull * kClus);
 constexpr size_t oFacc = oSysAcc + a256(8ull * kTaskVals);
 constexpr size_t oList = oFacc + a256(24ull * kSlots);
-constexpr size_t oListN = oList + a256(8ull * kClus * kListCap);
-constexpr size_t oPslot = oListN + a256(8ull * kClus);
+constexpr size_t oListN = oList + a256(4ull * kClus * kListCap);
+constexpr size_t oPslot = oListN + a256(4ull * kClus);
 constexpr size_t oZbin = oPslot + a256(4ull * kSlots * kMaxPartners);
 constexpr size_t oCounts = oZbin + a256(8ull * kZbEntries);
 constexpr size_t oStatus = oCounts + a256(16);
