@@ -9,7 +9,7 @@
 // runs the same binning and force kernels as nb_build_cells + nb_forces for
 // one system of at most NB_NOALLOC_MAX_ATOMS atoms, with every scratch buffer
 // carved from one file-scope device array (g_noalloc_scratch below, about
-// 4.5 MiB).  That array exists on every GPU that loads this library, for as
+// 3.6 MiB).  That array exists on every GPU that loads this library, for as
 // long as the library stays loaded.
 //
 // In host code the name g_noalloc_scratch only stands for the device symbol;
