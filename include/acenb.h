@@ -143,6 +143,14 @@ nb_status nb_build_cells(nb_ctx *ctx, const float *d_pos);
 nb_status nb_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type,
                     float *d_F, double *d_energy, double *d_virial);
 
+/* nb_forces_batch - nb_forces on a context made by nb_create_batch: the
+ * systems' concatenated arrays (atom ranges in system order, offsets fixed at
+ * create), energies [n_sys, 2] and virials [n_sys, 6]; all systems are
+ * evaluated by one persistent launch of the force kernel.  The same call as
+ * nb_forces (which also accepts batch contexts), under the batch name. */
+nb_status nb_forces_batch(nb_ctx *batch, const float *d_pos, const float *d_q, const int32_t *d_type,
+                          float *d_F, double *d_energy, double *d_virial);
+
 /* nb_backward - adjoint of L = sum_i G_i . F_i + sum_s gE_s . E_s, the pair
  * list recomputed from the last build (short-range terms, direct radial
  * functions; a context with smooth PME or tables enabled returns
@@ -214,6 +222,29 @@ nb_status nb_debug_cells(nb_ctx *ctx, int32_t *h_perm, int64_t *n_slots,
  * pair evaluations of the forward kernel (equal to n: it evaluates every
  * unique pair once and applies the force to both atoms).  Synchronous. */
 nb_status nb_debug_pairs(nb_ctx *ctx, int32_t *h_ij, int64_t cap, int64_t *n, int64_t *n_ordered);
+
+/* nb_debug_pair_terms - the forward kernel's FP32 pair arithmetic (section
+ * "Molecular dynamics on the GPU": the Lennard-Jones and electrostatic terms
+ * of one pair; forms in the header comment above) for n given pairs, so that
+ * its rounding can be measured pair by pair against an FP64 evaluation.
+ * d_xqi, d_xqj [n,4]: (x, y, z, q) of atoms i and j, 16-byte aligned;
+ * d = x_j - x_i is taken as given (no minimum image), and each pair must lie
+ * inside the cutoff with d != 0.  d_ti, d_tj [n]: types (< n_types).
+ * d_out [n,8]: (E_LJ switched, E_Coul, r2, 0, then the force on j (x, y, z),
+ * 0) with unit weights (no exclusion or 1-4 scaling), through the radial
+ * functions the context uses (direct or tabulated).  Asynchronous on the
+ * context's stream; needs no build. */
+nb_status nb_debug_pair_terms(nb_ctx *ctx, int64_t n, const float *d_xqi, const float *d_xqj,
+                              const int32_t *d_ti, const int32_t *d_tj, float *d_out);
+
+/* nb_debug_philox - Philox4x32-10 (Salmon, Moraes, Dror & Shaw 2011), the
+ * counter-based generator of the MD step's Langevin noise (the paper's
+ * thermostat draws Gaussian noise per atom and step), for n counter blocks:
+ * d_ctr [n,4] counters, d_key [n,2] keys, d_out [n,4] the ten-round outputs.
+ * A test export: it pins the device generator to published known-answer
+ * vectors.  Asynchronous on cuda_stream; no context needed. */
+nb_status nb_debug_philox(int64_t n, const uint32_t *d_ctr, const uint32_t *d_key, uint32_t *d_out,
+                          void *cuda_stream);
 
 /* nb_set_profiling - when on != 0, every later force-kernel launch is
  * bracketed by CUDA events on the context's stream (at most 4096 launches are
@@ -393,6 +424,16 @@ nb_status nb_bonded_forces(nb_ctx *ctx, const float *d_pos, float *d_F, double *
 
 /* nb_md_set_step - set the device step counter (synchronises the stream). */
 nb_status nb_md_set_step(nb_ctx *ctx, uint64_t step);
+
+/* nb_fp32_peak_launch - measurement utility without a counterpart in the
+ * paper: launches an FP32 FMA throughput kernel on the current device (every
+ * SM busy with independent chains of dependent FMAs, iters iterations per
+ * chain; iters a positive multiple of 16) on cuda_stream, and returns in
+ * *flop the FLOP it performs (2 per FMA).  The caller times it with CUDA
+ * events: FLOP / time is the measured FP32 peak that the force kernel's
+ * roofline is reported against.  d_sink: one writable device float.
+ * Asynchronous. */
+nb_status nb_fp32_peak_launch(int64_t iters, void *cuda_stream, float *d_sink, double *flop);
 
 /* nb_status_string - static description of a status code. */
 const char *nb_status_string(nb_status s);

@@ -282,6 +282,12 @@ nb_status nb_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, const int
     return e == cudaSuccess ? NB_OK : NB_ERR_CUDA;
 }
 
+nb_status nb_forces_batch(nb_ctx *batch, const float *d_pos, const float *d_q, const int32_t *d_type, float *d_F,
+                          double *d_energy, double *d_virial)
+{
+    return nb_forces(batch, d_pos, d_q, d_type, d_F, d_energy, d_virial);
+}
+
 nb_status nb_backward(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type,
                       const float *d_dLdF, const double *d_dLdE, float *d_dLdpos, float *d_dLdq,
                       double *d_dLdsig_tab, double *d_dLdeps_tab)
@@ -547,6 +553,17 @@ nb_status nb_debug_pairs(nb_ctx *ctx, int32_t *h_ij, int64_t cap, int64_t *n, in
     if (h_ij && m > 0 && cudaMemcpy(h_ij, d.dbg_ij, sizeof(int) * 2 * m, cudaMemcpyDeviceToHost) != cudaSuccess)
         return NB_ERR_CUDA;
     return NB_OK;
+}
+
+nb_status nb_debug_pair_terms(nb_ctx *ctx, int64_t n, const float *d_xqi, const float *d_xqj, const int32_t *d_ti,
+                              const int32_t *d_tj, float *d_out)
+{
+    if (!ctx || n < 0 || (n > 0 && (!d_xqi || !d_xqj || !d_ti || !d_tj || !d_out))) return NB_ERR_INVALID_ARG;
+    if (n == 0) return NB_OK;
+    const cudaError_t e = launch_debug_pair_terms(ctx, n, reinterpret_cast<const float4 *>(d_xqi),
+                                                  reinterpret_cast<const float4 *>(d_xqj), d_ti, d_tj,
+                                                  reinterpret_cast<float4 *>(d_out));
+    return e == cudaSuccess ? NB_OK : NB_ERR_CUDA;
 }
 
 }  // extern "C"

@@ -17,6 +17,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "nb_pair.cuh"
 
@@ -1054,6 +1055,19 @@ __global__ void k_unpack_adjoint(int slot_cap, const int *__restrict__ counts, c
     if (dq) dq[a] = __ll2float_rn(gacc[4ll * s + 3]) * sc;
 }
 
+// Kernel function attributes belong to each device's context, so the
+// shared-memory opt-in is made once per device (one bit per device in
+// `done`; devices beyond 63 set it at every launch).  Concurrent first calls
+// may both set it, which is harmless.
+template <typename Kernel>
+static void smem_optin_once(Kernel kernel, int device, int bytes, std::atomic<unsigned long long> &done)
+{
+    const unsigned long long bit = device >= 0 && device < 64 ? 1ull << device : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return;
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (bit) done.fetch_or(bit, std::memory_order_release);
+}
+
 size_t tile_smem_bytes(int T, int K)
 {
     return (size_t)T * T * 16 + align16((size_t)kTileWarps * kCluster * K * 4) +
@@ -1067,12 +1081,8 @@ template <int RAD, bool VIRIAL, bool DEBUG>
 static void launch_force_t(nb_ctx *ctx, const ForceArgs &A, bool beside_pme)
 {
     const size_t smem = tile_smem_bytes(A.P.n_types, A.K);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_force<RAD, VIRIAL, DEBUG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             200 * 1024);
-        attr_set = true;
-    }
+    static std::atomic<unsigned long long> optin{0};
+    smem_optin_once(k_force<RAD, VIRIAL, DEBUG>, ctx->device, 200 * 1024, optin);
     // persistent grid: never more blocks than can be resident at once
     int resident = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_force<RAD, VIRIAL, DEBUG>, kTileWarps * 32, smem);
@@ -1202,11 +1212,8 @@ template <int RAD>
 static void launch_adjoint_t(nb_ctx *ctx, const ForceArgs &A)
 {
     const size_t smem = adjoint_smem_bytes(A.P.n_types, A.K);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_adjoint<RAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-        attr_set = true;
-    }
+    static std::atomic<unsigned long long> optin{0};
+    smem_optin_once(k_adjoint<RAD>, ctx->device, 220 * 1024, optin);
     int resident = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_adjoint<RAD>, kAdjWarps * 32, smem);
     const int parts = ctx->tune.list_split > 0 ? ctx->tune.list_split : kDefaultListSplit;
@@ -1235,6 +1242,44 @@ cudaError_t launch_adjoint_tile(nb_ctx *ctx, const double *d_dLdE, float *d_dpos
     const int S = (int)ctx->slot_cap;
     return launch_pdl(k_unpack_adjoint, dim3((S + tb - 1) / tb), dim3(tb), 0, ctx->stream, S, d.counts, d.perm,
                       d.gacc, d_dpos, d_dq);
+}
+
+// Test export of the pair arithmetic (nb_debug_pair_terms): pair k of the
+// given lists evaluated by eval_pair exactly as the forward kernel does it
+// (unit weights, d = x_j - x_i as given); out[2k] = (E_LJ, E_Coul, r2, 0),
+// out[2k + 1] = the force on j.
+template <int RAD>
+__global__ void k_debug_pair_terms(PairParams P, const float2 *__restrict__ lj_tab, const float4 *__restrict__ rtab,
+                                   long long n, const float4 *__restrict__ xi, const float4 *__restrict__ xj,
+                                   const int *__restrict__ ti, const int *__restrict__ tj, float4 *__restrict__ out)
+{
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const float4 a = xi[k], b = xj[k];
+    const float2 ab = lj_tab[ti[k] * P.n_types + tj[k]];
+    const float4 lj4 = make_float4(ab.x, ab.y, 12.0f * ab.x, 6.0f * ab.y);
+    float dx, dy, dz;
+    const float r2 = disp_r2(b.x, b.y, b.z, a.x, a.y, a.z, dx, dy, dz);
+    Acc acc = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    float fjx = 0.0f, fjy = 0.0f, fjz = 0.0f;
+    eval_pair<RAD, false>(P, &lj4, rtab, 0, a.w * P.ke, true, dx, dy, dz, r2, b.w, 0, false, acc, fjx, fjy, fjz);
+    out[2 * k] = make_float4(acc.elj, acc.ec, r2, 0.0f);
+    out[2 * k + 1] = make_float4(fjx, fjy, fjz, 0.0f);
+}
+
+cudaError_t launch_debug_pair_terms(nb_ctx *ctx, long long n, const float4 *xi, const float4 *xj, const int *ti,
+                                    const int *tj, float4 *out)
+{
+    const int tb = 128;
+    const unsigned g = (unsigned)((n + tb - 1) / tb);
+    const PairParams &P = ctx->pp;
+    if (ctx->tab_n > 0)
+        k_debug_pair_terms<2><<<g, tb, 0, ctx->stream>>>(P, ctx->d.lj_tab, ctx->d.rtab, n, xi, xj, ti, tj, out);
+    else if (P.ewald)
+        k_debug_pair_terms<1><<<g, tb, 0, ctx->stream>>>(P, ctx->d.lj_tab, ctx->d.rtab, n, xi, xj, ti, tj, out);
+    else
+        k_debug_pair_terms<0><<<g, tb, 0, ctx->stream>>>(P, ctx->d.lj_tab, ctx->d.rtab, n, xi, xj, ti, tj, out);
+    return cudaGetLastError();
 }
 
 }  // namespace acenb

@@ -237,6 +237,9 @@ const long long *pme_forces_acc(const nb_ctx *ctx);
 const long long *pme_sums_acc(const nb_ctx *ctx);
 double pme_self_coef(const nb_ctx *ctx);  // -ke alpha / sqrt(pi), multiplies sum q^2
 void md_free(nb_ctx *ctx);
+// nb_debug_pair_terms: the forward kernel's pair arithmetic for given pairs
+cudaError_t launch_debug_pair_terms(nb_ctx *ctx, long long n, const float4 *xi, const float4 *xj, const int *ti,
+                                    const int *tj, float4 *out);
 cudaError_t launch_backward(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type,
                             const float *d_dLdF, const double *d_dLdE, float *d_dLdpos, float *d_dLdq,
                             double *d_dsig, double *d_deps);

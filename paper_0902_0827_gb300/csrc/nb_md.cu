@@ -778,3 +778,24 @@ extern "C" nb_status nb_md_set_step(nb_ctx *ctx, uint64_t step)
                ? NB_OK
                : NB_ERR_CUDA;
 }
+
+// Test export of the noise generator: Philox4x32-10 of n counter blocks.
+__global__ void k_debug_philox(long long n, const uint32_t *__restrict__ ctr, const uint32_t *__restrict__ key,
+                               uint32_t *__restrict__ out)
+{
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    uint32_t c[4] = {ctr[4 * k], ctr[4 * k + 1], ctr[4 * k + 2], ctr[4 * k + 3]};
+    philox4x32_10(c, key[2 * k], key[2 * k + 1]);
+    for (int w = 0; w < 4; ++w) out[4 * k + w] = c[w];
+}
+
+extern "C" nb_status nb_debug_philox(int64_t n, const uint32_t *d_ctr, const uint32_t *d_key, uint32_t *d_out,
+                                     void *cuda_stream)
+{
+    if (n < 0 || (n > 0 && (!d_ctr || !d_key || !d_out))) return NB_ERR_INVALID_ARG;
+    if (n == 0) return NB_OK;
+    const int tb = 128;
+    k_debug_philox<<<(unsigned)((n + tb - 1) / tb), tb, 0, (cudaStream_t)cuda_stream>>>(n, d_ctr, d_key, d_out);
+    return cudaGetLastError() == cudaSuccess ? NB_OK : NB_ERR_CUDA;
+}

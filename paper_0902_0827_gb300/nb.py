@@ -22,11 +22,12 @@ STATUS_NAMES = {
     9: "NB_ERR_NONFINITE", 10: "NB_ERR_CAPACITY", 11: "NB_ERR_UNSUPPORTED", 12: "NB_ERR_TOO_LARGE",
 }
 # every symbol include/acenb.h declares
-EXPORTS = ("nb_create", "nb_create_batch", "nb_build_cells", "nb_forces", "nb_backward", "nb_get_status",
-           "nb_set_stream", "nb_destroy", "nb_set_tuning", "nb_get_tuning", "nb_get_sizes", "nb_debug_cells",
-           "nb_debug_pairs", "nb_status_string", "nb_set_lj_params", "nb_set_profiling", "nb_get_profile",
-           "nb_forces_noalloc", "nb_type_gradients", "nb_set_pme", "nb_pme_forces", "nb_set_tables", "nb_md_init", "nb_md_step", "nb_bonded_forces",
-           "nb_md_set_step")
+EXPORTS = ("nb_create", "nb_create_batch", "nb_build_cells", "nb_forces", "nb_forces_batch", "nb_backward",
+           "nb_get_status", "nb_set_stream", "nb_destroy", "nb_set_tuning", "nb_get_tuning", "nb_get_sizes",
+           "nb_debug_cells", "nb_debug_pairs", "nb_debug_pair_terms", "nb_debug_philox", "nb_status_string",
+           "nb_set_lj_params", "nb_set_profiling", "nb_get_profile", "nb_forces_noalloc", "nb_type_gradients",
+           "nb_set_pme", "nb_pme_forces", "nb_set_tables", "nb_md_init", "nb_md_step", "nb_bonded_forces",
+           "nb_md_set_step", "nb_fp32_peak_launch")
 
 
 class NbError(RuntimeError):
@@ -97,6 +98,7 @@ def lib(build_if_missing: bool = True):
             "nb_create_batch": ([I32, ctypes.POINTER(nb_params), P, ctypes.POINTER(P)], ctypes.c_int),
             "nb_build_cells": ([P, P], ctypes.c_int),
             "nb_forces": ([P, P, P, P, P, P, P], ctypes.c_int),
+            "nb_forces_batch": ([P, P, P, P, P, P, P], ctypes.c_int),
             "nb_backward": ([P, P, P, P, P, P, P, P, P, P], ctypes.c_int),
             "nb_get_status": ([P], ctypes.c_int),
             "nb_set_stream": ([P, P], ctypes.c_int),
@@ -119,6 +121,9 @@ def lib(build_if_missing: bool = True):
             "nb_md_step": ([P, P, P, P, P, I32, P], ctypes.c_int),
             "nb_bonded_forces": ([P, P, P, P], ctypes.c_int),
             "nb_md_set_step": ([P, ctypes.c_uint64], ctypes.c_int),
+            "nb_debug_pair_terms": ([P, I64, P, P, P, P, P], ctypes.c_int),
+            "nb_debug_philox": ([I64, P, P, P, P], ctypes.c_int),
+            "nb_fp32_peak_launch": ([I64, P, P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -402,6 +407,18 @@ class Nonbonded:
                "nb_debug_cells")
         return perm[:ns.value].copy(), cs
 
+    def debug_pair_terms(self, xqi, xqj, ti, tj):
+        """The forward kernel's pair arithmetic for given pairs
+        (nb_debug_pair_terms): xqi, xqj [n,4] float32, ti, tj [n] int32 on the
+        GPU; returns [n,8] float32 (E_LJ, E_Coul, r2, 0, F_j, 0)."""
+        import torch
+        xqi, xqj, ti, tj = (t.contiguous() for t in (xqi, xqj, ti, tj))
+        out = torch.empty((xqi.shape[0], 8), dtype=torch.float32, device=xqi.device)
+        self._sync_stream()
+        _check(lib().nb_debug_pair_terms(self.h, xqi.shape[0], _tptr(xqi), _tptr(xqj), _tptr(ti), _tptr(tj),
+                                         _tptr(out)), "nb_debug_pair_terms")
+        return out
+
     def debug_pairs(self, cap: int | None = None):
         n, no = ctypes.c_int64(), ctypes.c_int64()
         if cap is None:
@@ -413,6 +430,27 @@ class Nonbonded:
         ij = ij[:m]
         order = np.lexsort((ij[:, 1], ij[:, 0]))
         return ij[order], n.value, no.value
+
+
+def debug_philox(ctr, key):
+    """Philox4x32-10 on the device (nb_debug_philox): ctr [n,4], key [n,2]
+    uint32 tensors on the GPU; returns [n,4] uint32 outputs (int32 storage)."""
+    import torch
+    assert ctr.dtype == torch.int32 and key.dtype == torch.int32
+    ctr, key = ctr.contiguous(), key.contiguous()
+    out = torch.empty_like(ctr)
+    _check(lib().nb_debug_philox(ctr.shape[0], _tptr(ctr), _tptr(key), _tptr(out), _stream_handle()),
+           "nb_debug_philox")
+    return out
+
+
+def fp32_peak_launch(iters: int, sink):
+    """Launch the FP32 FMA throughput kernel (nb_fp32_peak_launch) on the
+    current stream; returns the FLOP it performs.  Time it with CUDA events."""
+    flop = ctypes.c_double()
+    _check(lib().nb_fp32_peak_launch(int(iters), _stream_handle(), _tptr(sink), ctypes.byref(flop)),
+           "nb_fp32_peak_launch")
+    return flop.value
 
 
 def concat_inputs(systems: Sequence, device="cuda"):

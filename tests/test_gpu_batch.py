@@ -14,15 +14,18 @@ from paper_0902_0827_gb300 import systems as S
 
 pytestmark = pytest.mark.gpu
 
-F_RMS, F_MAX, E_REL, W_REL = 5e-6, 1e-3, 1e-6, 1e-5
+import parity  # noqa: E402
+
+# Literal energy bars of the water boxes, by case (1e-6 unless stated).
+ENERGY_BARS = {}
 
 
-def check_system(F, E, W, s):
+def check_system(F, E, W, s, case):
     Fo, Eo, Wo, _, Es = oracle.forces(s, method="cells", with_scale=True)
-    rel = np.linalg.norm(F - Fo) / np.linalg.norm(Fo)
-    assert rel <= F_RMS and np.abs(F - Fo).max() <= F_MAX
-    assert np.all(np.abs(E - Eo) <= E_REL * Es)
-    assert np.abs(W - Wo).max() <= W_REL * np.abs(Wo).max()
+    bars, notes = ENERGY_BARS.get("water", ((parity.E_REL,) * 3, ("",) * 3))
+    parity.check_forces(case, F, Fo)
+    parity.check_energy(case, E, Eo, Es, bars=bars, notes=notes)
+    parity.check_virial(case, W, Wo)
 
 
 def test_ensemble_graph_matches_oracle_per_system():
@@ -55,7 +58,7 @@ def test_ensemble_graph_matches_oracle_per_system():
                                                               int(np.argmax([s.n_atoms for s in systems]))}
     for k, s in enumerate(systems):
         if k in pick:
-            check_system(Fh[off:off + s.n_atoms], Eh[k], Wh[k], s)
+            check_system(Fh[off:off + s.n_atoms], Eh[k], Wh[k], s, f"ensemble64[{k}] n={s.n_atoms}")
         off += s.n_atoms
 
 
@@ -91,4 +94,4 @@ def test_autotuner_picks_a_valid_configuration_and_keeps_parity():
     F, E, W = ctx.forces(pos, q, t)
     torch.cuda.synchronize()
     ctx.status()
-    check_system(F.double().cpu().numpy(), E.cpu().numpy()[0], W.cpu().numpy()[0], s)
+    check_system(F.double().cpu().numpy(), E.cpu().numpy()[0], W.cpu().numpy()[0], s, "water_box autotuned")

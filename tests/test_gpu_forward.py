@@ -2,10 +2,11 @@
 
 Bars (from the target specification): cell sets and per-atom neighbour sets
 bit-exact; forces relative RMS <= 5e-6 and max |dF| <= 1e-3 kcal/mol/A;
-energies relative error <= 1e-6 per component, measured against the sum of
-|pair energy| of that component (the scale of the rounding error of a summed
-energy; it equals |E| when the sum does not cancel); virial relative error
-<= 1e-5 of the largest component; reruns bitwise identical.
+energies: the literal relative error |E_k - E_k^o| / |E_k^o| per component
+and in total (the bars of each case are in ENERGY_BARS with their reasons),
+and the error against the summation scale sum |e_ij| <= 1e-6 as a
+diagnostic; virial relative error <= 1e-5 of the largest component; reruns
+bitwise identical.  Every number is printed in the run's parity summary.
 """
 
 import numpy as np
@@ -19,7 +20,15 @@ from paper_0902_0827_gb300 import systems as S
 
 pytestmark = pytest.mark.gpu
 
-F_RMS, F_MAX, E_REL, W_REL = 5e-6, 1e-3, 1e-6, 1e-5
+from parity import E_REL, F_MAX, F_RMS, W_REL, check_virial  # noqa: E402
+import parity  # noqa: E402
+
+# Literal energy bars per case: 1e-6 (the target) unless the case says why not.
+ENERGY_BARS = {}
+
+
+def energy_bars(case):
+    return ENERGY_BARS.get(case, ((E_REL, E_REL, E_REL), ("", "", "")))
 
 
 def small_water(nw=216, k=11, alpha=0.32):
@@ -40,26 +49,13 @@ def gpu_eval(systems, tuning=None, virial=True):
         (W.cpu().numpy() if W is not None else None)
 
 
-def check_forces(F, Fo):
-    rel = np.linalg.norm(F - Fo) / np.linalg.norm(Fo)
-    mx = np.abs(F - Fo).max()
-    assert rel <= F_RMS, f"force rel RMS {rel:.3e}"
-    assert mx <= F_MAX, f"force max abs {mx:.3e}"
-    return rel, mx
+def check_forces(F, Fo, case="forward"):
+    return parity.check_forces(case, F, Fo)
 
 
-def check_energy(E, Eo, Es):
-    for k in range(2):
-        if Es[k] != 0:
-            assert abs(E[k] - Eo[k]) <= E_REL * Es[k], (k, E[k], Eo[k], Es[k])
-        else:
-            assert E[k] == 0.0
-    assert abs(E.sum() - Eo.sum()) <= E_REL * Es.sum()
-
-
-def check_virial(W, Wo):
-    scale = np.abs(Wo).max()
-    assert np.abs(W - Wo).max() <= W_REL * scale, (W, Wo)
+def check_energy(E, Eo, Es, case="forward", bars=None):
+    b, n = energy_bars(case) if bars is None else bars
+    return parity.check_energy(case, E, Eo, Es, bars=b, notes=n)
 
 
 CASES = {
@@ -107,9 +103,9 @@ def test_pairs_bit_exact(case):
 def test_forces_energy_virial_parity(case):
     name, s, Fo, Eo, Wo, npairs, Es = case
     ctx, inp, F, E, W = gpu_eval(s)
-    check_forces(F, Fo)
-    check_energy(E[0], Eo, Es)
-    check_virial(W[0], Wo)
+    check_forces(F, Fo, name)
+    check_energy(E[0], Eo, Es, name)
+    check_virial(name, W[0], Wo)
 
 
 def test_tuning_variants_agree(case):
@@ -121,9 +117,10 @@ def test_tuning_variants_agree(case):
     for tune in (dict(list_split=1, blocks_per_sm=1), dict(list_split=3, blocks_per_sm=3),
                  dict(list_split=8, blocks_per_sm=2)):
         ctx, inp, F, E, W = gpu_eval(s, tuning=tune)
-        check_forces(F, Fo)
-        check_energy(E[0], Eo, Es)
-        check_virial(W[0], Wo)
+        tag = f"{name} split{tune['list_split']}/bps{tune['blocks_per_sm']}"
+        check_forces(F, Fo, tag)
+        check_energy(E[0], Eo, Es, tag, bars=energy_bars(name))
+        check_virial(tag, W[0], Wo)
 
 
 def test_reruns_bitwise_identical():
@@ -151,7 +148,7 @@ def test_forces_without_energy_or_virial():
     torch.cuda.synchronize()
     ctx.status()
     assert E is None and W is None
-    check_forces(F.cpu().numpy().astype(np.float64), Fo)
+    check_forces(F.cpu().numpy().astype(np.float64), Fo, "water_no_energy")
 
 
 def test_unwrapped_input_positions():
@@ -172,8 +169,8 @@ def test_unwrapped_input_positions():
     F, E, W = ctx.forces(pos, q, t)
     torch.cuda.synchronize()
     ctx.status()
-    check_forces(F.cpu().numpy().astype(np.float64), Fo)
-    check_energy(E.cpu().numpy()[0], Eo, Es)
+    check_forces(F.cpu().numpy().astype(np.float64), Fo, "water_unwrapped")
+    check_energy(E.cpu().numpy()[0], Eo, Es, "water_unwrapped")
 
 
 def test_batch_matches_per_system_oracle():
@@ -184,9 +181,9 @@ def test_batch_matches_per_system_oracle():
     off = 0
     for k, s in enumerate(systems):
         Fo, Eo, Wo, _, Es = oracle.forces(s, method="cells", with_scale=True)
-        check_forces(F[off:off + s.n_atoms], Fo)
-        check_energy(E[k], Eo, Es)
-        check_virial(W[k], Wo)
+        check_forces(F[off:off + s.n_atoms], Fo, f"batch6[{k}]")
+        check_energy(E[k], Eo, Es, f"batch6[{k}]")
+        check_virial(f"batch6[{k}]", W[k], Wo)
         off += s.n_atoms
     perm, cs = ctx.debug_cells()
     # the batched binning is the per-system binning, concatenated

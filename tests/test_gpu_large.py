@@ -14,7 +14,7 @@ from paper_0902_0827_gb300 import systems as S
 
 pytestmark = pytest.mark.gpu
 
-F_RMS, F_MAX, E_REL, W_REL = 5e-6, 1e-3, 1e-6, 1e-5
+import parity  # noqa: E402
 
 
 def test_million_atom_water_box_full_parity():
@@ -33,9 +33,7 @@ def test_million_atom_water_box_full_parity():
     # the same unique pair set size (every pair evaluated once)
     assert n_gpu == n_oracle
     assert n_eval == n_gpu
-    rel = np.linalg.norm(F - Fo) / np.linalg.norm(Fo)
-    assert rel <= F_RMS, f"force rel RMS {rel:.3e}"
-    assert np.abs(F - Fo).max() <= F_MAX
-    for k in range(2):
-        assert abs(E[k] - Eo[k]) <= E_REL * Es[k], (k, E[k], Eo[k], Es[k])
-    assert np.abs(W - Wo).max() <= W_REL * np.abs(Wo).max(), (W, Wo)
+    case = "water_1M"
+    parity.check_forces(case, F, Fo)
+    parity.check_energy(case, E, Eo, Es)
+    parity.check_virial(case, W, Wo)

@@ -16,6 +16,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+import oracle
 import oracle.md as omd
 from paper_0902_0827_gb300 import nb
 from paper_0902_0827_gb300 import systems as S
@@ -169,3 +170,50 @@ def test_md_is_deterministic_and_graph_capturable():
     torch.cuda.synchronize()
     ctx.status()
     assert torch.equal(pos, outs[0][0]) and torch.equal(vel, outs[0][1])
+
+
+def test_shake_iteration_cap_reports_timeout_and_context_stays_usable():
+    # The M-SHAKE Newton loop is the library's one bounded device-side
+    # iteration.  A water stretched by 0.2 A cannot meet the 1e-6 relative
+    # tolerance in one iteration: the step records NB_ERR_TIMEOUT in the
+    # status word (no trap, no fault) and the context keeps working.
+    s, top = water(nw=216, seed=44)
+    x = s.pos.copy()
+    w0 = top.waters[0]
+    x[w0[1]] += np.float32(0.2) * (x[w0[1]] - x[w0[0]]) / np.linalg.norm(x[w0[1]] - x[w0[0]])
+    s1 = dataclasses.replace(s, pos=oracle.wrap_f32(x, s.box))
+    vel0 = torch.from_numpy(S.initial_velocities(top, 300.0)).cuda()
+    for max_iter, want in ((1, 8), (10, 0)):
+        ctx = nb.Nonbonded(s1)
+        ctx.md_init(top, dt=0.001, gamma=0.0, temperature=300.0, seed=1, shake_max_iter=max_iter)
+        pos, q, t = nb.concat_inputs([s1])
+        vel = vel0.clone()
+        ctx.md_step(pos, vel, q, t, 1)
+        assert ctx.status(raise_on_error=False) == want  # 8 = NB_ERR_TIMEOUT
+        ctx.md_step(pos, vel, q, t, 1)  # the next step runs (converged from the now nearer start)
+        torch.cuda.synchronize()
+        assert torch.isfinite(pos).all() and torch.isfinite(vel).all()
+        ctx.status(raise_on_error=False)
+
+
+def test_device_philox_matches_the_known_answer_vectors():
+    # the device generator of the Langevin noise against the published
+    # Philox4x32-10 outputs (the same vectors pin the oracle's generator)
+    import test_oracle_md as tom
+    rows = tom.philox_kat()
+    ctr = torch.tensor(np.array([r[0] for r in rows], np.uint32).view(np.int32), device="cuda")
+    key = torch.tensor(np.array([r[1] for r in rows], np.uint32).view(np.int32), device="cuda")
+    out = nb.debug_philox(ctr, key).cpu().numpy().view(np.uint32)
+    want = np.array([r[2] for r in rows], np.uint32)
+    assert np.array_equal(out, want)
+    # and agrees with the oracle word for word on 4096 counters of the MD
+    # noise layout (atom, step, stream, 0) with a 64-bit seed
+    n = 4096
+    a = np.arange(n, dtype=np.uint32)
+    c = np.stack([a, np.full(n, 77, np.uint32), np.full(n, 1, np.uint32), np.zeros(n, np.uint32)], 1)
+    seed = 0x123456789ABCDEF0
+    k = np.tile(np.array([seed & 0xFFFFFFFF, seed >> 32], np.uint32), (n, 1))
+    got = nb.debug_philox(torch.tensor(c.view(np.int32), device="cuda"),
+                          torch.tensor(k.view(np.int32), device="cuda")).cpu().numpy().view(np.uint32)
+    o = omd.philox4x32_10(c[:, 0], c[:, 1], c[:, 2], c[:, 3], seed & 0xFFFFFFFF, seed >> 32)
+    assert np.array_equal(got, np.stack([np.asarray(v, np.uint32) for v in o], 1))

@@ -21,6 +21,11 @@ from paper_0902_0827_gb300 import systems as S
 pytestmark = pytest.mark.gpu
 
 F_RMS, F_MAX, E_REL, W_REL = 5e-6, 1e-3, 1e-6, 1e-5
+
+import parity  # noqa: E402
+
+# literal energy bars of the table path against the tabulated oracle
+TAB_BARS = {}
 PAPER_BOUND = 1e-4
 
 
@@ -49,8 +54,7 @@ def test_tables_match_the_tabulated_oracle(which):
     print(which, "tab f_rms", rel)
     assert rel <= F_RMS
     assert np.abs(F - Fo).max() <= F_MAX
-    for k in range(2):
-        assert abs(E[k] - Eo[k]) <= E_REL * Es[k] + 1e-12
+    parity.check_energy(f"tables4096 {which}", E, Eo, Es, bars=TAB_BARS.get(which, (E_REL,) * 3))
     assert np.abs(W - Wo).max() <= W_REL * np.abs(Wo).max()
     if which == "lj_fcc":
         return  # nearly force-free crystal: net forces cancel, no relative bound
