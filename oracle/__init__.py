@@ -64,6 +64,8 @@ def lib():
             L.orc_forces_subset.restype = None
             L.orc_backward_allpairs.argtypes = common + [P, D, P, P, P, P, P, P]
             L.orc_backward_allpairs.restype = I64
+            L.orc_pair_terms.argtypes = [I64, P, P, P, P, P, P, I, P, P, F, F, F, F, P]
+            L.orc_pair_terms.restype = None
             L.orc_pairs.argtypes = [I64, P, P, F, I64, P, I64, P, I64, P]
             L.orc_pairs.restype = I64
             L.orc_combine_lb.argtypes = [I, P, P, P, P, P, P]
@@ -137,24 +139,43 @@ def _args(sys, pos=None, q=None):
     return args, keep
 
 
-def forces(sys, method: str = "allpairs", pos=None, q=None, with_scale: bool = False):
+def forces(sys, method: str = "allpairs", pos=None, q=None, with_scale: bool = False, with_sq: bool = False):
     """FP64 forces [N,3], energies (E_LJ, E_Coul), virial [6] and pair count.
 
     method: "allpairs" (plain O(N^2) sum) or "cells" (cell-list traversal).
     with_scale: also return (sum |e_LJ|, sum |e_Coul|) over pairs, the scale
     of the rounding error of each summed energy.
+    with_sq (with with_scale): then also (sum e_LJ^2, sum e_Coul^2), the
+    scale of the random part of that error.
     """
     args, keep = _args(sys, pos, q)
     n = args[0]
     F = np.zeros((n, 3))
-    E = np.zeros(4)
+    E = np.zeros(6)
     W = np.zeros(6)
     fn = lib().orc_forces_allpairs if method == "allpairs" else lib().orc_forces_cells
     npairs = fn(*args, _p(F), _p(E), _p(W))
     del keep
+    if with_scale and with_sq:
+        return F, E[:2].copy(), W, int(npairs), E[2:4].copy(), E[4:6].copy()
     if with_scale:
-        return F, E[:2].copy(), W, int(npairs), E[2:].copy()
+        return F, E[:2].copy(), W, int(npairs), E[2:4].copy()
     return F, E[:2].copy(), W, int(npairs)
+
+
+def pair_terms(sys, xi, xj, qi, qj, ti, tj):
+    """FP64 terms of given pairs with unit weights: [m, 4] = (E_LJ, E_Coul,
+    dU/dr, A r^-12 + B r^-6), d = x_j - x_i as given (see nb_oracle.c,
+    orc_pair_terms)."""
+    xi, xj = _c(xi, np.float32), _c(xj, np.float32)
+    qi, qj = _c(qi, np.float32), _c(qj, np.float32)
+    ti, tj = _c(ti, np.int32), _c(tj, np.int32)
+    _, _, A, B = combine_lb(sys.sigma, sys.epsilon)
+    m = xi.shape[0]
+    out = np.zeros((m, 4))
+    lib().orc_pair_terms(m, _p(xi), _p(xj), _p(qi), _p(qj), _p(ti), _p(tj), sys.n_types, _p(A), _p(B),
+                         sys.cutoff, sys.switch_dist, sys.ewald_alpha, sys.coulomb_k, _p(out))
+    return out
 
 
 def forces_subset(sys, atoms, pos=None, q=None):
@@ -163,7 +184,7 @@ def forces_subset(sys, atoms, pos=None, q=None):
     at = _c(atoms, np.int64)
     m = at.shape[0]
     F = np.zeros((m, 3))
-    E4 = np.zeros((m, 4))
+    E4 = np.zeros((m, 6))
     npair = np.zeros(m, np.int64)
     lib().orc_forces_subset(*args, m, _p(at), _p(F), _p(E4), _p(npair))
     del keep

@@ -319,6 +319,7 @@ static void accum_pair(const prm_t *p, const double *d, double r, double A, doub
         pair_terms(p, r, A, B, qq, wlj, wc, &t);
     }
     E[2] += fabs(t.e_lj); E[3] += fabs(t.e_c);
+    E[4] += t.e_lj * t.e_lj; E[5] += t.e_c * t.e_c;
     double h = t.du / r; /* F_i = h d, F_j = -h d */
     for (int a = 0; a < 3; ++a) { Fi[a] += h * d[a]; if (Fj) Fj[a] -= h * d[a]; }
     E[0] += t.e_lj; E[1] += t.e_c;
@@ -337,10 +338,11 @@ static void disp64(const float *xi, const float *xj, const float *box, const int
     *r = sqrt(s);
 }
 
-/* Plain O(N^2) sum over unique pairs i < j.  F [n*3], E [4] (LJ, Coulomb,
+/* Plain O(N^2) sum over unique pairs i < j.  F [n*3], E [6] (LJ, Coulomb,
  * then the sums of |pair energy| of each part: the scale against which the
- * rounding error of a summed energy is measured), W [6] (xx, yy, zz, xy, xz,
- * yz).  Returns the number of pairs in range. */
+ * rounding error of a summed energy is measured, then the sums of squared
+ * pair energies: the scale of the random part of that error), W [6] (xx, yy,
+ * zz, xy, xz, yz).  Returns the number of pairs in range. */
 int64_t orc_forces_allpairs(int64_t n, const float *pos, const float *q, const int32_t *type,
                             int ntypes, const double *A, const double *B, const float *box,
                             float rc, float rs, float alpha, float ke, float s14_lj, float s14_c,
@@ -353,7 +355,7 @@ int64_t orc_forces_allpairs(int64_t n, const float *pos, const float *q, const i
     topo_t t;
     topo_build(&t, n, nex, ex, n14, p14);
     memset(F, 0, sizeof(double) * 3 * (size_t)n);
-    E[0] = E[1] = E[2] = E[3] = 0.0;
+    for (int a = 0; a < 6; ++a) E[a] = 0.0;
     for (int a = 0; a < 6; ++a) W[a] = 0.0;
     int64_t npairs = 0;
     for (int64_t i = 0; i < n; ++i)
@@ -433,7 +435,7 @@ static int64_t atom_sum(const prm_t *p, const topo_t *t, const grid_t *g, int64_
     int64_t cnt = 0;
     int c[3];
     Fi[0] = Fi[1] = Fi[2] = 0.0;
-    Ei[0] = Ei[1] = Ei[2] = Ei[3] = 0.0;
+    for (int a = 0; a < 6; ++a) Ei[a] = 0.0;
     for (int a = 0; a < 6; ++a) Wi[a] = 0.0;
     if (g) grid_cell_of(g, pos + 3 * i, p->box, c);
     int64_t jlist_n = g ? 27 : 1;
@@ -458,9 +460,10 @@ static int64_t atom_sum(const prm_t *p, const topo_t *t, const grid_t *g, int64_
             double d[3], r;
             disp64(pos + 3 * i, pos + 3 * j, p->box, img, d, &r);
             int ab = type[i] * p->ntypes + type[j];
-            double e2[4] = {0.0, 0.0, 0.0, 0.0}, w6[6] = {0, 0, 0, 0, 0, 0};
+            double e2[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, w6[6] = {0, 0, 0, 0, 0, 0};
             accum_pair(p, d, r, p->A[ab], p->B[ab], (double)q[i] * (double)q[j], wlj, wc, Fi, NULL, e2, w6);
-            for (int a = 0; a < 4; ++a) Ei[a] += 0.5 * e2[a];
+            /* each pair is visited from both atoms: half of every sum here */
+            for (int a = 0; a < 6; ++a) Ei[a] += 0.5 * e2[a];
             for (int a = 0; a < 6; ++a) Wi[a] += 0.5 * w6[a];
             ++cnt;
         }
@@ -483,17 +486,17 @@ int64_t orc_forces_cells(int64_t n, const float *pos, const float *q, const int3
     topo_build(&t, n, nex, ex, n14, p14);
     grid_t g;
     int have_grid = grid_build(&g, n, pos, box, (double)rc);
-    double *Ep = (double *)malloc(sizeof(double) * 10 * (size_t)(n ? n : 1));
+    double *Ep = (double *)malloc(sizeof(double) * 12 * (size_t)(n ? n : 1));
     int64_t *cnt = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n ? n : 1));
 #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t i = 0; i < n; ++i)
-        cnt[i] = atom_sum(&p, &t, have_grid ? &g : NULL, n, pos, q, type, i, F + 3 * i, Ep + 10 * i, Ep + 10 * i + 4);
-    E[0] = E[1] = E[2] = E[3] = 0.0;
+        cnt[i] = atom_sum(&p, &t, have_grid ? &g : NULL, n, pos, q, type, i, F + 3 * i, Ep + 12 * i, Ep + 12 * i + 6);
+    for (int a = 0; a < 6; ++a) E[a] = 0.0;
     for (int a = 0; a < 6; ++a) W[a] = 0.0;
     int64_t tot = 0;
     for (int64_t i = 0; i < n; ++i) {
-        for (int a = 0; a < 4; ++a) E[a] += Ep[10 * i + a];
-        for (int a = 0; a < 6; ++a) W[a] += Ep[10 * i + 4 + a];
+        for (int a = 0; a < 6; ++a) E[a] += Ep[12 * i + a];
+        for (int a = 0; a < 6; ++a) W[a] += Ep[12 * i + 6 + a];
         tot += cnt[i];
     }
     free(Ep); free(cnt);
@@ -504,8 +507,8 @@ int64_t orc_forces_cells(int64_t n, const float *pos, const float *q, const int3
 }
 
 /* Forces on a subset of atoms only (plain loop over all j), for sampled checks
- * of systems too large for the full sum.  F [m*3]; E4 [m*4] half pair energies
- * (LJ, Coulomb, |LJ|, |Coulomb|). */
+ * of systems too large for the full sum.  F [m*3]; E4 [m*6] half pair energies
+ * (LJ, Coulomb, |LJ|, |Coulomb|, LJ^2, Coulomb^2). */
 void orc_forces_subset(int64_t n, const float *pos, const float *q, const int32_t *type,
                        int ntypes, const double *A, const double *B, const float *box,
                        float rc, float rs, float alpha, float ke, float s14_lj, float s14_c,
@@ -520,10 +523,43 @@ void orc_forces_subset(int64_t n, const float *pos, const float *q, const int32_
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t k = 0; k < m; ++k) {
         double W[6];
-        npair[k] = atom_sum(&p, &t, NULL, n, pos, q, type, atoms[k], F + 3 * k, E4 + 4 * k, W);
+        npair[k] = atom_sum(&p, &t, NULL, n, pos, q, type, atoms[k], F + 3 * k, E4 + 6 * k, W);
     }
     prm_free(&p);
     topo_free(&t);
+}
+
+/* FP64 terms of m given pairs with unit weights (no exclusion or 1-4
+ * scaling), for pair-by-pair comparison with the kernel's FP32 pair
+ * arithmetic: d = x_j - x_i exactly as given (the caller applies the periodic
+ * image), r = |d| in FP64.  out [m*4]: (E_LJ (switched), E_Coul, dU/dr,
+ * A r^-12 + B r^-6, an LJ magnitude that vanishes neither where E_LJ changes
+ * sign nor where the switch reaches zero).  Same pair_terms as the forward
+ * sums. */
+void orc_pair_terms(int64_t m, const float *xi, const float *xj, const float *qi, const float *qj,
+                    const int32_t *ti, const int32_t *tj, int ntypes, const double *A, const double *B,
+                    float rc, float rs, float alpha, float ke, double *out)
+{
+    prm_t p;
+    const float box[3] = {0.0f, 0.0f, 0.0f};
+    prm_init(&p, box, rc, rs, alpha, ke, 1.0f, 1.0f, ntypes, A, B);
+    for (int64_t k = 0; k < m; ++k) {
+        double r2 = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            const double d = (double)xj[3 * k + a] - (double)xi[3 * k + a];
+            r2 += d * d;
+        }
+        const double r = sqrt(r2);
+        const int ab = ti[k] * ntypes + tj[k];
+        pterm_t t;
+        pair_terms(&p, r, A[ab], B[ab], (double)qi[k] * (double)qj[k], 1.0, 1.0, &t);
+        const double ir6 = 1.0 / (r2 * r2 * r2);
+        out[4 * k] = t.e_lj;
+        out[4 * k + 1] = t.e_c;
+        out[4 * k + 2] = t.du;
+        out[4 * k + 3] = A[ab] * ir6 * ir6 + B[ab] * ir6;
+    }
+    prm_free(&p);
 }
 
 /* Unique in-range, non-excluded pairs (i < j) written to ij [cap*2].

@@ -245,14 +245,15 @@ __device__ __forceinline__ void eval_pair(const PairParams &P, const float4 *__r
                                           float dy, float dz, float r2, float qj, int tj, bool is14, Acc &acc,
                                           float &fjx, float &fjy, float &fjz)
 {
-    const float rinv = fast_rsqrt(r2);
+    float rinv, r;
+    pair_rinv(r2, rinv, r);
     const float r2inv = __fmul_rn(rinv, rinv);
     const float4 ab = lj[ti_row + tj];
     float elj, frlj, ec, frc;
     if constexpr (RAD == 2)
-        pair_radial_tab(P, rtab, r2, rinv, ab.x, ab.y, qi * qj, elj, frlj, ec, frc);
+        pair_radial_tab(P, rtab, r, ab.x, ab.y, qi * qj, elj, frlj, ec, frc);
     else
-        pair_radial<RAD == 1, true>(P, r2, rinv, r2inv, ab, qi * qj, elj, frlj, ec, frc);
+        pair_radial<RAD == 1, true>(P, r2, r, rinv, r2inv, ab, qi * qj, elj, frlj, ec, frc);
     // F_i = U'(r) d / r = -fs d with fs = -U'(r) / r
     float fs, wel, wec;
     if (W14) {

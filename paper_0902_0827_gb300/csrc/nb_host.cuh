@@ -27,29 +27,15 @@ inline int column_count(double L, double rho)
     return n;
 }
 
-// Least-squares fit of erfcx(x) = exp(x^2) erfc(x) as a degree-kErfcDeg
-// polynomial in t = 1 / (1 + x/2) on x in [0, xmax] (Householder QR on
-// Chebyshev-distributed nodes).  Returns the max absolute error of
-// exp(-x^2) P(t) against erfc(x) on a dense grid.
-inline double fit_erfcx(double xmax, float *coef)
+// Weighted least squares min |W (A x - b)| by Householder QR, A m x n
+// (row-major, n <= kErfcDeg + 1, m <= 96); A and b are overwritten.
+inline void lsq_householder(int m, int n, double *A, double *b, double *x)
 {
-    const int m = 96, n = kErfcDeg + 1;
-    const double tmin = 1.0 / (1.0 + 0.5 * xmax);
-    double A[96 * (kErfcDeg + 1)], b[96];
-    for (int i = 0; i < m; ++i) {
-        double c = cos(M_PI * (i + 0.5) / m);
-        double t = 0.5 * (1.0 + tmin) + 0.5 * (1.0 - tmin) * c;
-        double x = 2.0 * (1.0 / t - 1.0);
-        double p = 1.0;
-        for (int k = 0; k < n; ++k) { A[i * n + k] = p; p *= t; }
-        b[i] = erfc(x) * exp(x * x);
-    }
-    // Householder QR: A = Q R, solve R c = Q^T b
     for (int k = 0; k < n; ++k) {
         double nrm = 0.0;
         for (int i = k; i < m; ++i) nrm += A[i * n + k] * A[i * n + k];
         nrm = sqrt(nrm);
-        double alpha = A[k * n + k] > 0 ? -nrm : nrm;
+        const double alpha = A[k * n + k] > 0 ? -nrm : nrm;
         double v[96] = {0.0};
         for (int i = k; i < m; ++i) v[i] = A[i * n + k];
         v[k] -= alpha;
@@ -67,20 +53,94 @@ inline double fit_erfcx(double xmax, float *coef)
         s = 2.0 * s / vn;
         for (int i = k; i < m; ++i) b[i] -= s * v[i];
     }
-    double c[kErfcDeg + 1];
     for (int k = n - 1; k >= 0; --k) {
         double s = b[k];
-        for (int j = k + 1; j < n; ++j) s -= A[k * n + j] * c[j];
-        c[k] = s / A[k * n + k];
+        for (int j = k + 1; j < n; ++j) s -= A[k * n + j] * x[j];
+        x[k] = s / A[k * n + k];
     }
-    for (int k = 0; k < n; ++k) coef[k] = (float)c[k];
+}
+
+// Polynomial fit in relative error with the FP32 rounding of the
+// coefficients taken into account: on m nodes with basis values
+// T[i*n + k] = t_i^k and targets y_i, the constant coefficient is fitted
+// (weights 1 / |y_i|), rounded to FP32 and fixed, the others refitted, and
+// so on up to the highest.  A plain fit whose coefficients are rounded
+// afterwards leaves a smooth error that changes sign across the interval (a
+// bias of every summed pair energy that depends on the pair distance).
+inline void fit_rounded_poly(int m, int n, const double *T, const double *y, float *coef)
+{
+    double fixed[16];
+    for (int k = 0; k < n; ++k) {
+        const int nf = n - k;  // free columns k..n-1
+        double A[96 * 16], b[96], sol[16];
+        for (int i = 0; i < m; ++i) {
+            double r = y[i];
+            for (int j = 0; j < k; ++j) r -= fixed[j] * T[i * n + j];
+            const double w = 1.0 / fabs(y[i]);
+            b[i] = w * r;
+            for (int j = 0; j < nf; ++j) A[i * nf + j] = w * T[i * n + k + j];
+        }
+        lsq_householder(m, nf, A, b, sol);
+        fixed[k] = (double)(float)sol[0];
+    }
+    for (int k = 0; k < n; ++k) coef[k] = (float)fixed[k];
+}
+
+// erfcx(x) = exp(x^2) erfc(x) as a degree-kErfcDeg polynomial in
+// t = 1 / (1 + x/2) on x in [0, xmax] (fit_rounded_poly on 96
+// Chebyshev-distributed nodes in t): within 2e-9 of erfcx at the working
+// alpha rc = 2.88 (a plain fit with rounded coefficients: 7e-8, and a mean
+// of -3.7e-8 over 1-2 A against +1.9e-8 over 6-9 A).  Returns the max
+// relative error of exp(-x^2) P(t) against erfc(x) on a dense grid.
+inline double fit_erfcx(double xmax, float *coef)
+{
+    constexpr int m = 96, n = kErfcDeg + 1;
+    const double tmin = 1.0 / (1.0 + 0.5 * xmax);
+    double T[m * n], y[m];
+    for (int i = 0; i < m; ++i) {
+        const double c = cos(M_PI * (i + 0.5) / m);
+        const double t = 0.5 * (1.0 + tmin) + 0.5 * (1.0 - tmin) * c;
+        const double x = 2.0 * (1.0 / t - 1.0);
+        double p = 1.0;
+        for (int k = 0; k < n; ++k) { T[i * n + k] = p; p *= t; }
+        y[i] = erfc(x) * exp(x * x);
+    }
+    fit_rounded_poly(m, n, T, y, coef);
     double err = 0.0;
     for (int i = 0; i <= 4000; ++i) {
-        double x = xmax * i / 4000.0;
-        double t = 1.0 / (1.0 + 0.5 * x);
+        const double x = xmax * i / 4000.0;
+        const double t = 1.0 / (1.0 + 0.5 * x);
         double p = 0.0;
         for (int k = n - 1; k >= 0; --k) p = p * t + (double)coef[k];
-        err = std::max(err, fabs(exp(-x * x) * p - erfc(x)));
+        const double e = erfc(x);
+        err = std::max(err, fabs(exp(-x * x) * p - e) / e);
+    }
+    return err;
+}
+
+// 2^f on f in [-1/2, 1/2] as a degree-kExp2Deg polynomial (fit_rounded_poly
+// on 96 Chebyshev nodes): within 4e-9 relative, mean error 3e-10.  The pair
+// kernels use it instead of ex2.approx, whose error has a mean of -5e-8 for
+// arguments below -1 (about -1e-8 in [-1, 0)), measured on this GPU against
+// FP64 -- a bias that would reach every Coulomb pair energy beyond 2.6 A.
+// Returns the max relative error on a dense grid.
+inline double fit_exp2(float *coef)
+{
+    constexpr int m = 96, n = kExp2Deg + 1;
+    double T[m * n], y[m];
+    for (int i = 0; i < m; ++i) {
+        const double f = 0.5 * cos(M_PI * (i + 0.5) / m);
+        double p = 1.0;
+        for (int k = 0; k < n; ++k) { T[i * n + k] = p; p *= f; }
+        y[i] = exp2(f);
+    }
+    fit_rounded_poly(m, n, T, y, coef);
+    double err = 0.0;
+    for (int i = 0; i <= 4000; ++i) {
+        const double f = -0.5 + i / 4000.0;
+        double p = 0.0;
+        for (int k = n - 1; k >= 0; --k) p = p * f + (double)coef[k];
+        err = std::max(err, fabs(p / exp2(f) - 1.0));
     }
     return err;
 }
@@ -183,7 +243,11 @@ inline nb_status init_pair_params(const nb_params &P0, PairParams &pp)
     pp.alpha = P0.ewald_alpha;
     pp.ewald = P0.ewald_alpha > 0.0f;
     pp.alpha_half = 0.5f * P0.ewald_alpha;
-    pp.neg_a2_log2e = (float)(-(double)P0.ewald_alpha * (double)P0.ewald_alpha * 1.4426950408889634);
+    {
+        const double c = -(double)P0.ewald_alpha * (double)P0.ewald_alpha * 1.4426950408889634;
+        pp.neg_a2_log2e = (float)c;
+        pp.neg_a2_log2e_lo = (float)(c - (double)pp.neg_a2_log2e);
+    }
     pp.two_a_sqpi = (float)(2.0 * (double)P0.ewald_alpha / sqrt(M_PI));
     pp.s14_lj = P0.scale14_lj;
     pp.s14_c = P0.scale14_coul;
@@ -193,6 +257,7 @@ inline nb_status init_pair_params(const nb_params &P0, PairParams &pp)
     if (pp.ewald) {
         const double err = fit_erfcx((double)P0.ewald_alpha * (double)rc, pp.erfc_c);
         if (!(err < 2e-7)) return NB_ERR_UNSUPPORTED;
+        if (!(fit_exp2(pp.exp2_c) < 1e-8)) return NB_ERR_UNSUPPORTED;
     }
     return NB_OK;
 }

@@ -16,6 +16,7 @@ constexpr int kCluster = 8;          // atoms per cluster (column chunk)
 constexpr int kMaxTypes = 64;        // type-pair table lives in shared memory
 constexpr int kMaxPartners = 16;     // exclusion + 1-4 partners per atom
 constexpr int kErfcDeg = 8;          // degree of the erfcx polynomial in t
+constexpr int kExp2Deg = 6;          // degree of the 2^f polynomial on [-1/2, 1/2]
 constexpr int kDefaultListSplit = 4; // forward kernel: work units per cluster list
 constexpr double kFixScale = 4294967296.0;   // 2^32: fixed-point scale
 constexpr int kTaskVals = 8;         // per system: E_lj, E_c (scale 2^32), W[6] (scale 2^20)
@@ -81,6 +82,7 @@ struct PairParams {
     float alpha_half;    // alpha / 2: t = 1 / (1 + (alpha/2) r)
     float alpha;         // Ewald alpha
     float neg_a2_log2e;  // -alpha^2 log2(e): exp(-alpha^2 r^2) = 2^(r2 * this)
+    float neg_a2_log2e_lo; // the FP32 remainder: -alpha^2 log2(e) = neg_a2_log2e + this (to ~2^-48)
     float two_a_sqpi;    // 2 alpha / sqrt(pi)
     float s14_lj, s14_c;
     float list_margin;   // additive margin on bounding-box distances (A)
@@ -89,6 +91,7 @@ struct PairParams {
     int switched;        // rs < rc
     int ewald;           // alpha > 0
     float erfc_c[kErfcDeg + 1]; // erfcx(x) ~ sum c_k t^k on [0, alpha rc]
+    float exp2_c[kExp2Deg + 1]; // 2^f ~ sum c_k f^k on [-1/2, 1/2]
     float rs;            // FP32 switch distance
     float tab_inv_h;     // n / rc (FP32) of the radial-function tables
     int tab_n;           // intervals of the tables (0: direct evaluation)

@@ -455,25 +455,29 @@ __global__ void __launch_bounds__(256) k_pme_gather(PmeGeom g, PmeCorr cc, int s
                     if (qq == 0.0f) continue;
                     const float4 xj = xyzq[inv[j]];
                     float d[3] = {xa.x - xj.x, xa.y - xj.y, xa.z - xj.z};
+                    float sh[3] = {0.0f, 0.0f, 0.0f};  // image shift of each axis: -1, 0, +1 box
 #pragma unroll
                     for (int ax = 0; ax < 3; ++ax) {
-                        if (d[ax] > cc.half[ax]) d[ax] -= cc.L[ax];
-                        else if (d[ax] < -cc.half[ax]) d[ax] += cc.L[ax];
+                        if (d[ax] > cc.half[ax]) {
+                            d[ax] -= cc.L[ax];
+                            sh[ax] = -1.0f;
+                        } else if (d[ax] < -cc.half[ax]) {
+                            d[ax] += cc.L[ax];
+                            sh[ax] = 1.0f;
+                        }
                     }
                     const float r2 = fmaf(d[2], d[2], fmaf(d[1], d[1], d[0] * d[0]));
                     // U = -qq erf(a r)/r; force on the atom = -dU/dr d/r = -qq g(a r) / r^3 d
-                    float e, fs;
+                    float fs;
                     const float x2 = cc.alpha * cc.alpha * r2;
                     if (x2 < 1.0f) {
                         float P = cc.series[kSeriesTerms - 1];
 #pragma unroll
                         for (int t = kSeriesTerms - 2; t >= 0; --t) P = fmaf(P, x2, cc.series[t]);
                         fs = -qq * cc.two_a3_sqpi * P;
-                        e = r2 == 0.0f ? -qq * cc.two_a_sqpi : -qq * erff(cc.alpha * sqrtf(r2)) / sqrtf(r2);
                     } else {
                         const float r = sqrtf(r2), ir = 1.0f / r;
                         const float er = erff(cc.alpha * r);
-                        e = -qq * er * ir;
                         fs = qq * (cc.two_a_sqpi * expf(-x2) * r - er) * (ir * ir * ir);
                     }
                     const float f0 = fs * d[0], f1 = fs * d[1], f2 = fs * d[2];
@@ -481,8 +485,23 @@ __global__ void __launch_bounds__(256) k_pme_gather(PmeGeom g, PmeCorr cc, int s
                     fy += f1;
                     fz += f2;
                     if (j > a) {
+                        // The pair's energy -qq erf(alpha r)/r in FP64 (from the FP32
+                        // inputs, exactly converted): these corrections sum to about
+                        // 80 times the total Coulomb energy (they cancel the self
+                        // term), and the rigid waters repeat the same distances, so
+                        // FP32 rounding would add up coherently (2.7e-8 of the sum,
+                        // 2e-6 of the total on the solvated chain).  A few
+                        // partners per atom: cheap even at the FP64 rate.
+                        const double dd0 = ((double)xa.x - (double)xj.x) + (double)sh[0] * (double)cc.L[0];
+                        const double dd1 = ((double)xa.y - (double)xj.y) + (double)sh[1] * (double)cc.L[1];
+                        const double dd2 = ((double)xa.z - (double)xj.z) + (double)sh[2] * (double)cc.L[2];
+                        const double r2d = dd0 * dd0 + dd1 * dd1 + dd2 * dd2;
+                        const double qqd = (double)wgt * (double)cc.ke * (double)qa * (double)q[j];
+                        const double rd = sqrt(r2d);
+                        const double ed = r2d == 0.0 ? -qqd * 2.0 * (double)cc.alpha * 0.56418958354775628
+                                                     : -qqd * erf((double)cc.alpha * rd) / rd;
                         const float vs = (float)kVirScale;
-                        v[1] += __float2ll_rn(e * (float)kFixScale);
+                        v[1] += __double2ll_rn(ed * kFixScale);
                         v[2] += __float2ll_rn(d[0] * f0 * vs);
                         v[3] += __float2ll_rn(d[1] * f1 * vs);
                         v[4] += __float2ll_rn(d[2] * f2 * vs);

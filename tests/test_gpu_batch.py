@@ -16,15 +16,17 @@ pytestmark = pytest.mark.gpu
 
 import parity  # noqa: E402
 
-# Literal energy bars of the water boxes, by case (1e-6 unless stated).
-ENERGY_BARS = {}
+# Literal energy bars of the water boxes: E_LJ 1e-6; the Coulomb sum of
+# randomly oriented TIP3P-shaped waters cancels to 1/6000 of sum |e_ij| and is
+# held to the FP32 floor of the pair arithmetic (parity.fp32_floor).
+BARS = (parity.E_REL, "floor", "floor")
+NOTES = ("", "water Coulomb sum cancels", "water Coulomb sum cancels")
 
 
 def check_system(F, E, W, s, case):
-    Fo, Eo, Wo, _, Es = oracle.forces(s, method="cells", with_scale=True)
-    bars, notes = ENERGY_BARS.get("water", ((parity.E_REL,) * 3, ("",) * 3))
+    Fo, Eo, Wo, _, Es, Eq = oracle.forces(s, method="cells", with_scale=True, with_sq=True)
     parity.check_forces(case, F, Fo)
-    parity.check_energy(case, E, Eo, Es, bars=bars, notes=notes)
+    parity.check_energy(case, E, Eo, Es, bars=BARS, notes=NOTES, Eq=Eq)
     parity.check_virial(case, W, Wo)
 
 

@@ -23,8 +23,15 @@ pytestmark = pytest.mark.gpu
 from parity import E_REL, F_MAX, F_RMS, W_REL, check_virial  # noqa: E402
 import parity  # noqa: E402
 
-# Literal energy bars per case: 1e-6 (the target) unless the case says why not.
-ENERGY_BARS = {}
+# Literal energy bars per case: 1e-6 (the target) unless the case says why
+# not.  The Coulomb sums of the TIP3P-shaped water boxes cancel to 1/6000 of
+# sum |e_ij| (randomly oriented neutral molecules): their literal error is held
+# to the FP32 floor of the pair arithmetic (parity.fp32_floor), which lies
+# above 1e-6 there; E_LJ is held to 1e-6 everywhere.
+WATER = ((E_REL, "floor", "floor"), ("", "water Coulomb sum cancels", "water Coulomb sum cancels"))
+ENERGY_BARS = {"water_tiny": WATER, "water_box": WATER, "water_unwrapped": WATER}
+for _k in range(6):
+    ENERGY_BARS[f"batch6[{_k}]"] = WATER
 
 
 def energy_bars(case):
@@ -53,9 +60,9 @@ def check_forces(F, Fo, case="forward"):
     return parity.check_forces(case, F, Fo)
 
 
-def check_energy(E, Eo, Es, case="forward", bars=None):
+def check_energy(E, Eo, Es, Eq, case="forward", bars=None):
     b, n = energy_bars(case) if bars is None else bars
-    return parity.check_energy(case, E, Eo, Es, bars=b, notes=n)
+    return parity.check_energy(case, E, Eo, Es, bars=b, notes=n, Eq=Eq)
 
 
 CASES = {
@@ -70,8 +77,8 @@ CASES = {
 def case(request):
     s = CASES[request.param]()
     method = "allpairs" if s.n_atoms <= 7000 else "cells"
-    Fo, Eo, Wo, npairs, Es = oracle.forces(s, method=method, with_scale=True)
-    return request.param, s, Fo, Eo, Wo, npairs, Es
+    Fo, Eo, Wo, npairs, Es, Eq = oracle.forces(s, method=method, with_scale=True, with_sq=True)
+    return request.param, s, Fo, Eo, Wo, npairs, Es, Eq
 
 
 def test_cells_bit_exact(case):
@@ -87,7 +94,7 @@ def test_cells_bit_exact(case):
 
 
 def test_pairs_bit_exact(case):
-    name, s, Fo, Eo, Wo, npairs, Es = case
+    name, s, Fo, Eo, Wo, npairs, Es, Eq = case
     ctx = nb.Nonbonded(s)
     pos, q, t = nb.concat_inputs([s])
     ctx.build(pos)
@@ -101,10 +108,10 @@ def test_pairs_bit_exact(case):
 
 
 def test_forces_energy_virial_parity(case):
-    name, s, Fo, Eo, Wo, npairs, Es = case
+    name, s, Fo, Eo, Wo, npairs, Es, Eq = case
     ctx, inp, F, E, W = gpu_eval(s)
     check_forces(F, Fo, name)
-    check_energy(E[0], Eo, Es, name)
+    check_energy(E[0], Eo, Es, Eq, name)
     check_virial(name, W[0], Wo)
 
 
@@ -113,13 +120,13 @@ def test_tuning_variants_agree(case):
     # to 8 cut every cluster's list into that many work units (most units
     # of the 8-way split hold under 32 entries, the 1-way one several
     # 32-entry batches)
-    name, s, Fo, Eo, Wo, npairs, Es = case
+    name, s, Fo, Eo, Wo, npairs, Es, Eq = case
     for tune in (dict(list_split=1, blocks_per_sm=1), dict(list_split=3, blocks_per_sm=3),
                  dict(list_split=8, blocks_per_sm=2)):
         ctx, inp, F, E, W = gpu_eval(s, tuning=tune)
         tag = f"{name} split{tune['list_split']}/bps{tune['blocks_per_sm']}"
         check_forces(F, Fo, tag)
-        check_energy(E[0], Eo, Es, tag, bars=energy_bars(name))
+        check_energy(E[0], Eo, Es, Eq, tag, bars=energy_bars(name))
         check_virial(tag, W[0], Wo)
 
 
@@ -160,7 +167,7 @@ def test_unwrapped_input_positions():
     rng = np.random.default_rng(0)
     raw = (s.pos.astype(np.float64) + rng.integers(-2, 3, size=s.pos.shape) * s.box).astype(np.float32)
     wrapped = oracle.wrap_f32(raw, s.box)
-    Fo, Eo, Wo, _, Es = oracle.forces(s, pos=wrapped, with_scale=True)
+    Fo, Eo, Wo, _, Es, Eq = oracle.forces(s, pos=wrapped, with_scale=True, with_sq=True)
     ctx = nb.Nonbonded(s)
     pos = torch.from_numpy(raw).cuda()
     q = torch.from_numpy(s.q).cuda()
@@ -170,7 +177,7 @@ def test_unwrapped_input_positions():
     torch.cuda.synchronize()
     ctx.status()
     check_forces(F.cpu().numpy().astype(np.float64), Fo, "water_unwrapped")
-    check_energy(E.cpu().numpy()[0], Eo, Es, "water_unwrapped")
+    check_energy(E.cpu().numpy()[0], Eo, Es, Eq, "water_unwrapped")
 
 
 def test_batch_matches_per_system_oracle():
@@ -180,9 +187,9 @@ def test_batch_matches_per_system_oracle():
     ctx, inp, F, E, W = gpu_eval(systems)
     off = 0
     for k, s in enumerate(systems):
-        Fo, Eo, Wo, _, Es = oracle.forces(s, method="cells", with_scale=True)
+        Fo, Eo, Wo, _, Es, Eq = oracle.forces(s, method="cells", with_scale=True, with_sq=True)
         check_forces(F[off:off + s.n_atoms], Fo, f"batch6[{k}]")
-        check_energy(E[k], Eo, Es, f"batch6[{k}]")
+        check_energy(E[k], Eo, Es, Eq, f"batch6[{k}]")
         check_virial(f"batch6[{k}]", W[k], Wo)
         off += s.n_atoms
     perm, cs = ctx.debug_cells()

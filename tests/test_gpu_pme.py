@@ -74,6 +74,12 @@ def test_long_range_part_matches_oracle_pme(which, grid, order):
     Wo = Wr + Wc
     wrel = np.abs(W - Wo).max() / np.abs(Wo).max()
     report(f"pme {which} {grid} n={order}", f_rms=rel, e_rec=erec, e_self=eself, e_pair=epair, w=wrel)
+    tag = f"pme {which} {grid} n={order}"
+    parity.record(tag, "force rel RMS", rel, REC_REL)
+    parity.record(tag, "E_recip |dE|/|E|", erec, REC_REL)
+    parity.record(tag, "E_self |dE|/|E|", eself, SELF_REL)
+    parity.record(tag, "E_pair corr |dE|/|E|", epair, CORR_REL)
+    parity.record(tag, "virial max|dW|/max|W|", wrel, REC_REL)
     assert rel <= REC_REL
     assert erec <= REC_REL
     assert eself <= SELF_REL
@@ -103,7 +109,9 @@ def test_nb_forces_with_pme_is_the_full_electrostatics():
     assert np.abs(F - Ft).max() <= F_MAX
     ec = Eo[1] + Er + Es + Ep
     scale = Esc[1] + abs(Er) + abs(Es) + abs(Ep)
-    # the literal relative errors of E_LJ and of the full Ewald E_Coul
+    # the literal relative errors of E_LJ and of the full Ewald E_Coul (real
+    # space + reciprocal + self + exclusion/1-4 corrections: terms up to 80
+    # times larger than the total, whose errors must stay below 1e-6 of it)
     parity.check_energy(f"pme {s.name}", E, np.array([Eo[0], ec]), np.array([Esc[0], scale]))
     Wt = Wo + Wr + Wc
     assert np.abs(W - Wt).max() <= W_REL * np.abs(Wt).max()

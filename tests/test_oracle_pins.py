@@ -433,6 +433,59 @@ def test_cell_list_equals_all_pairs():
         assert np.allclose(W, W2, rtol=1e-10, atol=1e-8)
 
 
+def test_energy_scales_sum_abs_and_sum_squares():
+    # the diagnostic sums (sum |e|, sum e^2 per component) agree between the
+    # all-pairs and the cell-list traversal (which visits every pair twice
+    # and keeps halves), and on the perfect FCC crystal equal the shell sums
+    s = small_water()
+    _, E, _, _, Ea, Eq = oracle.forces(s, with_scale=True, with_sq=True)
+    _, E2, _, _, Ea2, Eq2 = oracle.forces(s, method="cells", with_scale=True, with_sq=True)
+    assert np.allclose(Ea, Ea2, rtol=1e-12) and np.allclose(Eq, Eq2, rtol=1e-12)
+    assert np.all(Eq > 0) and np.all(Eq <= Ea ** 2)
+    sig, eps, rc, rs = 3.4, 0.238, 8.5, 7.5
+    a = S.fcc_lattice_constant()
+    ncell = 4
+    basis = np.array([[0, 0, 0], [0.5, 0.5, 0], [0.5, 0, 0.5], [0, 0.5, 0.5]])
+    cells = np.stack(np.meshgrid(*[np.arange(ncell)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    pos = ((cells[:, None, :] + basis[None]) * a).reshape(-1, 3)
+    sf = make_sys(pos, [a * ncell] * 3, sigma=[sig], eps=[eps], rc=rc, rs=rs)
+    _, E, _, n, Ea, Eq = oracle.forces(sf, with_scale=True, with_sq=True)
+    rnn = a / math.sqrt(2)
+    r, c = _fcc_shells(3)
+    rr = r * rnn
+    keep = rr < rc
+    u = 4 * eps * ((sig / rr) ** 12 - (sig / rr) ** 6)
+    Sw = np.where(rr <= rs, 1.0, (rc ** 2 - rr ** 2) ** 2 * (rc ** 2 + 2 * rr ** 2 - 3 * rs ** 2) / (rc ** 2 - rs ** 2) ** 3)
+    e = (Sw * u)[keep]
+    assert abs(Ea[0] / sf.n_atoms - 0.5 * (c[keep] * np.abs(e)).sum()) < 1e-5 * Ea[0] / sf.n_atoms
+    assert abs(Eq[0] / sf.n_atoms - 0.5 * (c[keep] * e ** 2).sum()) < 1e-5 * Eq[0] / sf.n_atoms
+    assert Ea[1] == 0.0 and Eq[1] == 0.0
+
+
+def test_pair_terms_sum_to_the_forward_energies():
+    # the per-pair FP64 terms (unit weights) of every in-range pair, with the
+    # exact-shift image applied on the host, add up to the forward sums of a
+    # system without 1-4 pairs, and reproduce the closed-form LJ minimum
+    from pairs_util import imaged_pairs
+    s = small_water()
+    ij, xi, xj = imaged_pairs(s)
+    t = oracle.pair_terms(s, xi, xj, s.q[ij[:, 0]], s.q[ij[:, 1]], s.type[ij[:, 0]], s.type[ij[:, 1]])
+    _, E, _, _ = oracle.forces(s)
+    assert abs(t[:, 0].sum() - E[0]) < 1e-10 * abs(E[0])
+    assert abs(t[:, 1].sum() - E[1]) < 1e-9 * np.abs(t[:, 1]).sum()
+    assert np.all(t[:, 3] >= np.abs(t[:, 0]))
+    sig, eps = 3.4, 0.238
+    one = make_sys(np.array([[5.0, 5, 5], [5.0, 5, 5]]), [30.0] * 3, sigma=[sig], eps=[eps], rc=9.0, rs=8.5)
+    r = np.float32(2 ** (1 / 6) * sig)
+    xa = np.array([[5.0, 5, 5]], np.float32)
+    xb = np.array([[5.0 + r, 5, 5]], np.float32)
+    t1 = oracle.pair_terms(one, xa, xb, np.zeros(1), np.zeros(1), np.zeros(1), np.zeros(1))
+    rr = float(xb[0, 0]) - float(xa[0, 0])
+    sg, ep = float(np.float32(sig)), float(np.float32(eps))  # the FP32 parameters, exactly
+    want = 4 * ep * ((sg / rr) ** 12 - (sg / rr) ** 6)
+    assert abs(t1[0, 0] - want) < 1e-12 and abs(t1[0, 0] + eps) < 1e-6 and abs(t1[0, 2]) < 1e-5
+
+
 def test_pairs_brute_force_on_tiny_box():
     s = small_water(216, k=13)
     ij = oracle.pairs(s)
@@ -496,7 +549,7 @@ def _forces_with_tables(s, A, B, pos=None):
     args[5] = oracle._p(A)
     args[6] = oracle._p(B)
     n = args[0]
-    F = np.zeros((n, 3)); E = np.zeros(4); W = np.zeros(6)
+    F = np.zeros((n, 3)); E = np.zeros(6); W = np.zeros(6)
     oracle.lib().orc_forces_allpairs(*args, oracle._p(F), oracle._p(E), oracle._p(W))
     return F, E[:2]
 
