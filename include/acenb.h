@@ -54,7 +54,7 @@
 extern "C" {
 #endif
 
-#define ACENB_VERSION 1
+#define ACENB_VERSION 2
 
 typedef enum {
     NB_OK = 0,
@@ -103,11 +103,16 @@ typedef struct {
     int32_t blocks_per_sm;  /* blocks per SM of the forward kernel's persistent grid, 1..8 */
     int32_t stage_capacity; /* no effect (both kernels stage their lists in 32-entry batches);
                                validated as 16..512, multiple of 4 */
-    int32_t list_capacity;  /* entries of a cluster's pair list (its half of the cluster pairs:
-                               each pair is listed for one of its two clusters), 64..65536,
-                               multiple of 4 */
-    int32_t list_split;     /* forward kernel: work units (warps) per cluster's half list,
-                               1..8; 0 = default (4) */
+    int32_t list_capacity;  /* entries of an i-group's list (its share of the cluster pairs:
+                               every pair of clusters is listed by one of its two groups),
+                               64..65536, multiple of 4 */
+    int32_t list_split;     /* tile kernels: work units (warps) per segment of a group's list
+                               (4 segments per group), 1..8; 0 = default (1) */
+    int32_t group_clusters; /* clusters per i-group, 1, 4 or 8: the tile shape of the forward
+                               kernel (1: one 8 x 8 tile per list entry, the i atoms in
+                               registers; 4 or 8: a warp works on 32 or 64 i atoms against one
+                               listed 8-atom cluster at a time); 0 = default (1).  A change
+                               takes effect at the next nb_build_cells. */
 } nb_tuning;
 
 /* nb_create - one system.  Copies params, validates them (box/cutoff ratio,

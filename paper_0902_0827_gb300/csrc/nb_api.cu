@@ -35,7 +35,8 @@ void free_all(nb_ctx *c)
     auto &d = c->d;
     void *ptrs[] = {d.sys, d.atom_sys, d.atom_col, d.wpos, d.part_orig, d.col_sys, d.col_count, d.col_fill,
                     d.col_slot, d.stage, d.xyzq, d.tslot, d.perm, d.inv, d.bb,
-                    d.clus_sys, d.sys_acc, d.facc, d.gacc, d.list, d.list_n, d.pslot, d.zbin, d.tab_grad, d.counts, d.status, d.lj_tab,
+                    d.clus_sys, d.sys_acc, d.facc, d.gacc, d.col_grp, d.grp, d.clus_grp, d.glist, d.glist_n, d.gmask,
+                    d.zbin, d.tab_grad, d.counts, d.status, d.lj_tab,
                     d.dbg_n, d.dbg_ij, d.scratch_f, d.scratch_g, d.lj_d, d.gslot, d.eps_type, d.rtab};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -86,12 +87,15 @@ nb_status allocate(nb_ctx *c)
     ALLOC(d.sys_acc, (int64_t)c->n_sys * kTaskVals);
     ALLOC(d.facc, S * 3);
     ALLOC(d.gacc, S * 4);
-    ALLOC(d.list, NC * c->list_cap);
-    ALLOC(d.list_n, NC);
-    ALLOC(d.pslot, S * c->K);
+    ALLOC(d.col_grp, C + 1);
+    ALLOC(d.grp, c->grp_cap);
+    ALLOC(d.clus_grp, NC);
+    ALLOC(d.glist, c->grp_cap * c->list_cap);
+    ALLOC(d.glist_n, c->grp_cap * kListSegs);
+    ALLOC(d.gmask, c->mask_cap * kMaxGroup);
     ALLOC(d.zbin, c->zb_total);
     ALLOC(d.tab_grad, (int64_t)T * T * 2);
-    ALLOC(d.counts, 4);
+    ALLOC(d.counts, 8);
     ALLOC(d.status, 1);
     ALLOC(d.lj_tab, (int64_t)T * T);
     ALLOC(d.lj_d, (int64_t)T * T);
@@ -102,7 +106,7 @@ nb_status allocate(nb_ctx *c)
     if (e != cudaSuccess) return cuda_status(e);
     e = cudaMemset(d.tslot, 0, sizeof(int) * S);
     if (e == cudaSuccess) e = cudaMemset(d.status, 0, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(d.counts, 0, sizeof(int) * 4);
+    if (e == cudaSuccess) e = cudaMemset(d.counts, 0, sizeof(int) * 8);
     return cuda_status(e);
 }
 
@@ -156,7 +160,7 @@ nb_status nb_create_batch(int32_t n_sys, const nb_params *params, void *cuda_str
     const nb_params &P0 = params[0];
     const int T = P0.n_types;
     // type-pair tables in FP64, then (A, B) in FP32
-    std::vector<float2> lj((size_t)T * T);
+    std::vector<float4> lj((size_t)T * T);
     std::vector<float4> ljd((size_t)T * T);
     c->sig_tab.assign((size_t)T * T, 0.0);
     c->eps_tab.assign((size_t)T * T, 0.0);
@@ -191,6 +195,8 @@ nb_status nb_create_batch(int32_t n_sys, const nb_params *params, void *cuda_str
     c->slot_cap = N + (int64_t)(kCluster - 1) * col;
     c->slot_cap = (c->slot_cap + kCluster - 1) / kCluster * kCluster;
     c->clus_cap = c->slot_cap / kCluster;
+    c->grp_cap = group_capacity(c->clus_cap);
+    c->mask_cap = mask_capacity(c->clus_cap);
     // topology: per-atom partner lists (global indices), (orig << 1) | is14
     std::vector<std::vector<int>> part(N);
     for (int s = 0; s < n_sys; ++s) {
@@ -231,6 +237,8 @@ nb_status nb_create_batch(int32_t n_sys, const nb_params *params, void *cuda_str
     c->tune.stage_capacity = 96;
     c->tune.list_capacity = 512;
     c->tune.list_split = kDefaultListSplit;
+    c->tune.group_clusters = kDefaultGroup;
+    c->group = kDefaultGroup;
     c->stage_cap = c->tune.stage_capacity;
     c->list_cap = c->tune.list_capacity;
     int smem_optin = 0;
@@ -244,7 +252,7 @@ nb_status nb_create_batch(int32_t n_sys, const nb_params *params, void *cuda_str
         if (e == cudaSuccess) e = cudaMemcpy(c->d.col_sys, col_sys.data(), sizeof(int) * col, cudaMemcpyHostToDevice);
         if (e == cudaSuccess)
             e = cudaMemcpy(c->d.part_orig, part_flat.data(), sizeof(int) * part_flat.size(), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(c->d.lj_tab, lj.data(), sizeof(float2) * lj.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(c->d.lj_tab, lj.data(), sizeof(float4) * lj.size(), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(c->d.lj_d, ljd.data(), sizeof(float4) * ljd.size(), cudaMemcpyHostToDevice);
         if (e == cudaSuccess && P0.comb_rule == 0)
             e = cudaMemcpy(c->d.eps_type, P0.epsilon, sizeof(float) * T, cudaMemcpyHostToDevice);
@@ -380,12 +388,12 @@ nb_status nb_set_lj_params(nb_ctx *ctx, const float *h_sigma, const float *h_eps
         for (int k = 0; k < T * T; ++k)
             if (!(h_sigma_tab[k] >= 0.0f) || !(h_eps_tab[k] >= 0.0f)) return NB_ERR_INVALID_ARG;
     }
-    std::vector<float2> lj((size_t)T * T);
+    std::vector<float4> lj((size_t)T * T);
     std::vector<float4> ljd((size_t)T * T);
     make_tables(T, ctx->comb_rule, h_sigma, h_epsilon, h_sigma_tab, h_eps_tab, ctx->sig_tab.data(),
                 ctx->eps_tab.data(), lj.data(), ljd.data());
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return NB_ERR_CUDA;
-    if (cudaMemcpy(ctx->d.lj_tab, lj.data(), sizeof(float2) * lj.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    if (cudaMemcpy(ctx->d.lj_tab, lj.data(), sizeof(float4) * lj.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         return NB_ERR_CUDA;
     if (cudaMemcpy(ctx->d.lj_d, ljd.data(), sizeof(float4) * ljd.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         return NB_ERR_CUDA;
@@ -472,21 +480,29 @@ nb_status nb_set_tuning(nb_ctx *ctx, const nb_tuning *t)
 {
     if (!ctx || !t) return NB_ERR_INVALID_ARG;
     if (t->blocks_per_sm < 1 || t->blocks_per_sm > 8 || t->list_split < 0 || t->list_split > 8) return NB_ERR_INVALID_ARG;
+    if (t->group_clusters != 0 && t->group_clusters != 1 && t->group_clusters != 4 && t->group_clusters != 8)
+        return NB_ERR_INVALID_ARG;
     if (t->stage_capacity < 16 || t->stage_capacity > 512 || t->stage_capacity % 4) return NB_ERR_INVALID_ARG;
     if (t->list_capacity < 64 || t->list_capacity > 65536 || t->list_capacity % 4) return NB_ERR_INVALID_ARG;
     if (ctx->smem_optin > 0 && force_smem_for(ctx->pp.n_types, t->stage_capacity, ctx->K) > (size_t)ctx->smem_optin)
         return NB_ERR_UNSUPPORTED;
     if (t->list_capacity != ctx->list_cap) {
         // new list storage: the lists of the last build are gone
-        uint32_t *nl = nullptr;
+        uint2 *nl = nullptr;
         if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return NB_ERR_CUDA;
-        if (dalloc(&nl, (size_t)ctx->clus_cap * t->list_capacity) != cudaSuccess) return NB_ERR_OOM;
-        cudaFree(ctx->d.list);
-        ctx->d.list = nl;
+        if (dalloc(&nl, (size_t)ctx->grp_cap * t->list_capacity) != cudaSuccess) return NB_ERR_OOM;
+        cudaFree(ctx->d.glist);
+        ctx->d.glist = nl;
         ctx->list_cap = t->list_capacity;
         ctx->built = false;
     }
+    const int gsize = t->group_clusters > 0 ? t->group_clusters : kDefaultGroup;
+    if (gsize != ctx->group) {
+        ctx->group = gsize;  // the lists are built for a group size: a new build is needed
+        ctx->built = false;
+    }
     ctx->tune = *t;
+    ctx->tune.group_clusters = gsize;
     ctx->stage_cap = t->stage_capacity;
     return NB_OK;
 }

@@ -40,18 +40,22 @@ __device__ __forceinline__ int warp_aggregated_add(int *counter_base, int key)
 
 // Block-wide exclusive scan of the padded column sizes (one block).  Fills
 // the column slot offsets, the scatter cursors, the totals and the
-// per-system slot/cluster ranges.
+// per-system slot/cluster ranges; then the first i-group of every column
+// (ceil(clusters / group) groups per column).
 __device__ void scan_columns(int n_cols, int n_sys, const int *__restrict__ col_count, int *__restrict__ col_slot,
-                             int *__restrict__ col_fill, SysDesc *__restrict__ sys, int *__restrict__ counts)
+                             int *__restrict__ col_fill, SysDesc *__restrict__ sys, int *__restrict__ counts,
+                             int group, int *__restrict__ col_grp)
 {
     __shared__ int warp_sum[32];
     __shared__ int carry;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int pass = 0; pass < 2; ++pass) {
     for (int base = 0; base < n_cols; base += blockDim.x) {
         int c = base + threadIdx.x;
-        int v = c < n_cols ? (__ldcg(&col_count[c]) + kCluster - 1) / kCluster * kCluster : 0;
+        const int ncl = c < n_cols ? (__ldcg(&col_count[c]) + kCluster - 1) / kCluster : 0;
+        int v = pass == 0 ? ncl * kCluster : (ncl + group - 1) / group;
         int x = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -71,17 +75,32 @@ __device__ void scan_columns(int n_cols, int n_sys, const int *__restrict__ col_
         }
         __syncthreads();
         int excl = carry + (wid ? warp_sum[wid - 1] : 0) + x - v;
-        if (c < n_cols) { col_slot[c] = excl; col_fill[c] = excl; }
+        if (c < n_cols) {
+            if (pass == 0) {
+                col_slot[c] = excl;
+                col_fill[c] = excl;
+            } else {
+                col_grp[c] = excl;
+            }
+        }
         __syncthreads();
         if (threadIdx.x == blockDim.x - 1) carry = excl + v;
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        col_slot[n_cols] = carry;
-        counts[0] = carry;
-        counts[1] = carry / kCluster;
+        if (pass == 0) {
+            col_slot[n_cols] = carry;
+            counts[0] = carry;
+            counts[1] = carry / kCluster;
+        } else {
+            col_grp[n_cols] = carry;
+            counts[4] = carry;  // groups
+            counts[5] = 0;      // exclusion-mask records used by the list kernel
+        }
+        carry = 0;
     }
     __syncthreads();
+    }
     for (int s = threadIdx.x; s < n_sys; s += blockDim.x) {
         int c0 = sys[s].col_begin, c1 = c0 + sys[s].nx * sys[s].ny;
         sys[s].slot_begin = col_slot[c0];
@@ -96,7 +115,8 @@ __device__ void scan_columns(int n_cols, int n_sys, const int *__restrict__ col_
 __global__ void k_bin(int n, const float *__restrict__ pos, SysDesc *__restrict__ sys,
                       const int *__restrict__ atom_sys, float4 *__restrict__ wpos, int *__restrict__ atom_col,
                       int *__restrict__ col_count, int n_cols, int n_sys, int *__restrict__ col_slot,
-                      int *__restrict__ col_fill, int *__restrict__ counts, int *__restrict__ status)
+                      int *__restrict__ col_fill, int *__restrict__ counts, int *__restrict__ status, int group,
+                      int *__restrict__ col_grp)
 {
     pdl_entry();
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
@@ -134,7 +154,7 @@ __global__ void k_bin(int n, const float *__restrict__ pos, SysDesc *__restrict_
     __syncthreads();
     if (!last) return;
     __threadfence();
-    scan_columns(n_cols, n_sys, col_count, col_slot, col_fill, sys, counts);
+    scan_columns(n_cols, n_sys, col_count, col_slot, col_fill, sys, counts, group, col_grp);
     if (threadIdx.x == 0) col_count[n_cols] = 0;
 }
 
@@ -183,7 +203,8 @@ __global__ void __launch_bounds__(kSortThreads) k_colsort(
     const int *__restrict__ col_count, const int *__restrict__ col_slot, const int *__restrict__ col_sys,
     const SysDesc *__restrict__ sys, const int *__restrict__ stage, const float4 *__restrict__ wpos,
     float4 *__restrict__ xyzq, int *__restrict__ tslot, int *__restrict__ perm, int *__restrict__ inv,
-    float4 *__restrict__ bb, int *__restrict__ clus_sys, int2 *__restrict__ zbin)
+    float4 *__restrict__ bb, int *__restrict__ clus_sys, int2 *__restrict__ zbin, int group,
+    const int *__restrict__ col_grp, int2 *__restrict__ grp, int *__restrict__ clus_grp)
 {
     pdl_entry();
     __shared__ unsigned long long skey[kSortSmem];
@@ -263,6 +284,10 @@ __global__ void __launch_bounds__(kSortThreads) k_colsort(
         bb[2 * I] = make_float4(lx, ly, lz, 0.0f);
         bb[2 * I + 1] = make_float4(hx, hy, hz, 0.0f);
         clus_sys[I] = col_sys[c];
+        // i-groups: runs of `group` consecutive clusters of the column
+        const int gi = col_grp[c] + q / group;
+        clus_grp[I] = gi;
+        if (q % group == 0) grp[gi] = make_int2(I, min(group, nclus - q));
     }
     __syncthreads();
     // z-bin index: for b = 0..nzb, (first cluster with z_hi >= b dz, first
@@ -295,228 +320,378 @@ __global__ void __launch_bounds__(kSortThreads) k_colsort(
 // Opposite periodic image of a list entry's shift code: 1 <-> 2 on every axis.
 __device__ __forceinline__ uint32_t opposite_code(uint32_t c) { return ((c & 0x15u) << 1) | ((c & 0x2Au) >> 1); }
 
-// Half list for Newton's third law: of the two entries (I, J, c) and
-// (J, I, opposite c) of one cluster pair exactly one is kept, chosen by a
-// checkerboard on the indices so that every cluster keeps about half of its
-// neighbours; of a cluster's own periodic images the smaller code of each
-// opposite pair, and the direct self entry (whose pairs j > i the force kernel
-// takes).
-__device__ __forceinline__ bool keep_half(int I, int J, uint32_t code)
+// Newton's third law at group level.  Every pair of clusters (I, J) of two
+// different i-groups is listed by exactly one of the two groups, chosen by a
+// checkerboard on the group indices (so that every group lists about half of
+// its neighbours): all tiles between two groups sit in one group's list.
+// The parity and the order of two indices do not change when both are
+// offset by the same amount, so a system's lists are the same in a batch as
+// alone.
+__device__ __forceinline__ bool keep_groups(int gA, int gB) { return ((gA ^ gB) & 1) ? (gA < gB) : (gA > gB); }
+
+// Within one group, of the tiles (I, J, c) and (J, I, opposite c) the one
+// with I < J; for I == J the direct tile (whose pairs j > i are taken) and
+// of a cluster's own periodic images the smaller code of each opposite pair.
+__device__ __forceinline__ bool keep_in_group(int I, int J, uint32_t code)
 {
-    if (J == I) return code == 0u || code < opposite_code(code);
-    return ((I ^ J) & 1) ? (I < J) : (I > J);
+    if (I != J) return I < J;
+    return code == 0u || code < opposite_code(code);
 }
 
 // Candidate v of a column window (virtual index: image -L below 0, +L from
-// nj): J when its bounding box comes within rc + margin of I's, else -1;
-// code receives the entry's shift code.
-__device__ __forceinline__ int window_candidate(const float4 *__restrict__ bb, float4 lo, float4 hi, int v, int jb,
-                                                int nj, uint32_t code_xy, float ox, float oy, float Lz, float rcm2,
-                                                uint32_t &code)
+// nj): J, its shift code and its bounding box at that image.
+__device__ __forceinline__ int window_cluster(const float4 *__restrict__ bb, int v, int jb, int nj, uint32_t code_xy,
+                                              float ox, float oy, float Lz, uint32_t &code, float4 &jl, float4 &jh)
 {
     const uint32_t zimg = v < 0 ? 1u : (v >= nj ? 2u : 0u);
     const int J = jb + v + (zimg == 1u ? nj : (zimg == 2u ? -nj : 0));
     const float oz = zimg == 1u ? -Lz : (zimg == 2u ? Lz : 0.0f);
-    const float4 jl = bb[2 * J], jh = bb[2 * J + 1];
-    const float gx = fmaxf(fmaxf((jl.x + ox) - hi.x, lo.x - (jh.x + ox)), 0.0f);
-    const float gy = fmaxf(fmaxf((jl.y + oy) - hi.y, lo.y - (jh.y + oy)), 0.0f);
-    const float gz = fmaxf(fmaxf((jl.z + oz) - hi.z, lo.z - (jh.z + oz)), 0.0f);
+    jl = bb[2 * J];
+    jh = bb[2 * J + 1];
+    jl.x += ox; jh.x += ox;
+    jl.y += oy; jh.y += oy;
+    jl.z += oz; jh.z += oz;
     code = code_xy | (zimg << 4);
-    return gx * gx + gy * gy + gz * gz < rcm2 ? J : -1;
+    return J;
 }
 
-// Bit of a cluster index in the 64-bit partner-cluster filter (multiplicative
-// hash of the index within the cluster's system, so that a system's lists
-// and flags do not depend on the other systems of a batch).
-__device__ __forceinline__ unsigned bloom_bit(int c) { return ((unsigned)c * 0x9E3779B1u) >> 26; }
+// Squared gap between two boxes (0 when they overlap).
+__device__ __forceinline__ float box_gap2(float4 al, float4 ah, float4 bl, float4 bh)
+{
+    const float gx = fmaxf(fmaxf(bl.x - ah.x, al.x - bh.x), 0.0f);
+    const float gy = fmaxf(fmaxf(bl.y - ah.y, al.y - bh.y), 0.0f);
+    const float gz = fmaxf(fmaxf(bl.z - ah.z, al.z - bh.z), 0.0f);
+    return gx * gx + gy * gy + gz * gz;
+}
 
-constexpr int kListWarps = 8;   // warps (clusters in flight) per block of the list kernel
-constexpr int kListGroup = 64;  // candidate columns compacted per pass
+// The block's set of clusters that hold a topology partner of a group atom:
+// open addressing in shared memory, bounded probing; insert returns the
+// key's slot (-1 when the table is full: the caller then flags every entry),
+// find returns it or -1.
+constexpr int kHashSlots = 256;
+__device__ __forceinline__ unsigned hset_slot(int key) { return ((unsigned)key * 0x9E3779B1u) >> 24; }
+
+__device__ __forceinline__ int hset_insert(int *h, int key)
+{
+    unsigned s = hset_slot(key);
+    for (int probe = 0; probe < kHashSlots; ++probe) {
+        const int old = atomicCAS(&h[s], -1, key);
+        if (old == -1 || old == key) return (int)s;
+        s = (s + 1) & (kHashSlots - 1);
+    }
+    return -1;
+}
+
+__device__ __forceinline__ int hset_find(const int *h, int key)
+{
+    unsigned s = hset_slot(key);
+    for (int probe = 0; probe < kHashSlots; ++probe) {
+        const int v = h[s];
+        if (v == key) return (int)s;
+        if (v == -1) return -1;
+        s = (s + 1) & (kHashSlots - 1);
+    }
+    return -1;
+}
+
 constexpr int kOwnCap = 512;    // flattened candidates whose owner lane is tabulated
-constexpr int kPartnerRounds = (kCluster * kMaxPartners + 31) / 32;
 
-// A4: cluster-pair lists, one warp per cluster I.  The columns within reach
-// of I's bounding box (with periodic images) go to the lanes.  Clusters of a
-// column are z-sorted, so the ones whose z-range (under the z images -L, 0,
-// +L, concatenated as virtual indices -nj..2nj-1) comes within the cutoff of
-// I form one window per column; the windows of all lanes are flattened and
-// every candidate (J, image) is tested by bounding-box gap < rc + margin.
-// Of the entries kept, those of I's half (Newton's third law: every cluster
-// pair appears in the list of exactly one of its two clusters, see
-// keep_half) are compacted in (column round, candidate round, lane) order,
-// so the lists are deterministic.  Also writes the partner slots of I's atoms and flags the
-// entries whose cluster may hold a topology partner of I (a Bloom filter of
-// the partners' clusters: never a missed partner, rarely a spurious flag).
-__global__ void __launch_bounds__(kListWarps * 32)
-    k_list(const SysDesc *__restrict__ sys, const int *__restrict__ counts, const float4 *__restrict__ bb,
-           const int *__restrict__ clus_sys, const int *__restrict__ col_slot, const int2 *__restrict__ zbin,
-           const int *__restrict__ perm, const int *__restrict__ part_orig, const int *__restrict__ inv, int K,
-           float rcm, int cap, uint32_t *__restrict__ list, int *__restrict__ list_n, int *__restrict__ pslot,
-           int *__restrict__ status)
+// Bits jj <= ia of an 8 x 8 tile (bit 8 ia + jj): the pairs of the direct
+// self tile that are not evaluated (each unique pair once, j > i).
+constexpr unsigned long long kSelfTriangle = 0xFF7F3F1F0F070301ull;
+
+// Exclusion bitmasks of one flagged entry (section "Molecular dynamics on
+// the GPU": bitmaps select the non-bonded terms to exclude or scale), by one
+// lane into record rec: for every group cluster c in cm, bit 8 ia + jj of
+// (excluded, scaled 1-4) for i atom ia of cluster c0 + c and j atom jj of J;
+// the direct self tile (J = c0 + c, no shift) also excludes jj <= ia.  The
+// partners of the group's atoms that lie in J are the chain of J's slot in
+// the block's partner-cluster table (s_head / s_next over s_pslot, entry t =
+// atom t / K of the group).
+__device__ void entry_masks(const int *__restrict__ s_pslot, const int *__restrict__ s_next, int head, int K,
+                            int c0, int n, unsigned cm, int J, uint32_t code, ulonglong2 *__restrict__ rec)
+{
+    // per cluster of the mask: walk J's chain, keep that cluster's bits in
+    // registers, one store (the chains are a few partners long)
+    for (unsigned cc = cm; cc; cc &= cc - 1u) {
+        const int c = __ffs(cc) - 1;
+        unsigned long long ex = 0ull, s14 = 0ull;
+        for (int t = head, guard = 0; t >= 0 && guard < kCluster * kMaxGroup * kMaxPartners; t = s_next[t], ++guard) {
+            const int a = t / K;
+            if (a / kCluster != c) continue;
+            const int v = s_pslot[t];
+            const unsigned long long bit = 1ull << ((a % kCluster) * kCluster + ((v >> 1) & (kCluster - 1)));
+            if (v & 1) s14 |= bit;
+            else ex |= bit;
+        }
+        if (code == 0u && J == c0 + c) ex |= kSelfTriangle;
+        rec[c] = make_ulonglong2(ex, s14);
+    }
+    (void)n;
+}
+
+// A4: i-group lists, one warp per group of up to 8 consecutive clusters of a
+// column (clusters c0 .. c0 + n - 1), kGListWarps groups per block.  The
+// columns within reach of the group's bounding box (with periodic images)
+// are dealt round-robin to the kListSegs segments of the group's list
+// (list_cap / kListSegs entries each); within a segment the entries follow
+// the scan order, so the lists are deterministic.  Clusters of a column are
+// z-sorted, so the ones whose z-range (under the z images -L, 0, +L,
+// concatenated as virtual indices -nj..2nj-1) comes within the cutoff of the
+// group form one window per column; the windows of 32 columns are flattened
+// and every candidate (J, image) gets the mask of the group clusters whose
+// boxes come within rc + margin of J's and whose tile the group keeps
+// (keep_groups, keep_in_group); a non-empty mask makes an entry.  Entries
+// whose J holds a topology partner of a group atom (found in the warp's
+// partner-cluster table), or that contain the direct self tile, are flagged
+// and get a record of exclusion bitmasks (entry_masks).
+struct GListArgs {
+    const SysDesc *sys;
+    const int *counts;
+    int *mask_count;         // records used (counts[5], zeroed by the binning kernel)
+    const float4 *bb;
+    const int *clus_sys;
+    const int *col_slot;
+    const int2 *zbin;
+    const int *perm;
+    const int *part_orig;
+    const int *inv;
+    const int2 *grp;
+    const int *clus_grp;
+    uint2 *glist;
+    int *glist_n;
+    ulonglong2 *gmask;
+    int *status;
+    long long mask_cap;
+    int K;
+    float rcm;
+    int cap;                 // entries per group (all segments)
+    int group;               // clusters per group of this build
+};
+
+constexpr int kGListWarps = 4;  // groups (warps) per block of the list kernel
+
+__host__ __device__ inline size_t glist_warp_ints(int K) { return 2 * (size_t)kCluster * kMaxGroup * K; }
+
+__global__ void __launch_bounds__(kGListWarps * 32) k_glist(GListArgs A)
 {
     pdl_entry();
     const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = blockIdx.x * kGListWarps + w;
+    if (g >= A.counts[4]) return;  // the whole warp
     const unsigned lt = (1u << lane) - 1u;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    const int n_clus = counts[1];
-    const float rcm2 = rcm * rcm;
-    __shared__ int s_col[kListWarps][kListGroup];  // compacted candidate columns per warp
-    __shared__ unsigned char s_own[kListWarps][kOwnCap];  // owner lane of each flattened candidate
-    const int wib = threadIdx.x >> 5;
-    for (int I = gw; I < n_clus; I += nw) {
-        const SysDesc &S = sys[clus_sys[I]];
-        const float4 lo = bb[2 * I], hi = bb[2 * I + 1];
-        // partner slots of I's atoms, and a 64-bit Bloom filter of the
-        // clusters that hold them: an entry is flagged when its cluster's
-        // bit is set (false positives only cost the force kernel a partner
-        // check, a real partner is never missed)
-        unsigned long long bloom = 0ull;
-        const int np = kCluster * K;
-        // the loads of all rounds first (three dependent levels, not three per round)
-        int pv[kPartnerRounds];
-#pragma unroll
-        for (int r = 0; r < kPartnerRounds; ++r) {
-            const int t = r * 32 + lane;
-            pv[r] = t < np ? perm[I * kCluster + t / K] : -1;
+    const int2 gr = A.grp[g];
+    const int c0 = gr.x, n = gr.y, K = A.K;
+    __shared__ float4 s_lo_all[kGListWarps][kMaxGroup], s_hi_all[kGListWarps][kMaxGroup];
+    __shared__ int s_hash_all[kGListWarps][kHashSlots];
+    __shared__ int s_head_all[kGListWarps][kHashSlots];
+    __shared__ int s_col_all[kGListWarps][32];
+    __shared__ unsigned char s_own_all[kGListWarps][kOwnCap];
+    extern __shared__ int s_dyn[];
+    float4 *s_lo = s_lo_all[w], *s_hi = s_hi_all[w];
+    int *s_hash = s_hash_all[w], *s_head = s_head_all[w], *s_col = s_col_all[w];
+    unsigned char *s_own = s_own_all[w];
+    int *s_pslot = s_dyn + (size_t)w * glist_warp_ints(K);  // [8 n K] partner slots (slot << 1) | is14
+    int *s_next = s_pslot + kCluster * kMaxGroup * K;       // [8 n K] chains of the partner-cluster table
+    for (int t = lane; t < kHashSlots; t += 32) {
+        s_hash[t] = -1;
+        s_head[t] = -1;
+    }
+    if (lane < n) {
+        s_lo[lane] = A.bb[2 * (c0 + lane)];
+        s_hi[lane] = A.bb[2 * (c0 + lane) + 1];
+    }
+    __syncwarp();
+    const int np = kCluster * n * K;
+    bool full = false;  // the partner table overflowed: flag every entry
+    for (int t = lane; t < np; t += 32) {
+        int v = A.perm[c0 * kCluster + t / K];
+        v = v >= 0 ? A.part_orig[(long long)v * K + t % K] : -1;
+        v = v >= 0 ? (A.inv[v >> 1] << 1) | (v & 1) : -1;
+        s_pslot[t] = v;
+        if (v >= 0) {
+            const int hs = hset_insert(s_hash, (v >> 1) / kCluster);
+            if (hs < 0) full = true;
+            else s_next[t] = atomicExch(&s_head[hs], t);
         }
-#pragma unroll
-        for (int r = 0; r < kPartnerRounds; ++r) {
-            const int t = r * 32 + lane;
-            pv[r] = pv[r] >= 0 ? part_orig[(long long)pv[r] * K + t % K] : -1;
+    }
+    const bool all_flag = __any_sync(FULL, full);
+    __syncwarp();
+    const SysDesc &S = A.sys[A.clus_sys[c0]];
+    float4 lo = s_lo[0], hi = s_hi[0];
+    for (int c = 1; c < n; ++c) {
+        const float4 a = s_lo[c], b = s_hi[c];
+        lo.x = fminf(lo.x, a.x); lo.y = fminf(lo.y, a.y); lo.z = fminf(lo.z, a.z);
+        hi.x = fmaxf(hi.x, b.x); hi.y = fmaxf(hi.y, b.y); hi.z = fmaxf(hi.z, b.z);
+    }
+    const float rcm = A.rcm, rcm2 = rcm * rcm;
+    const int cxa = max(-S.nx, (int)floorf((lo.x - rcm) * S.inv_w[0]));
+    const int cxb = min(2 * S.nx - 1, (int)floorf((hi.x + rcm) * S.inv_w[0]));
+    const int cya = max(-S.ny, (int)floorf((lo.y - rcm) * S.inv_w[1]));
+    const int cyb = min(2 * S.ny - 1, (int)floorf((hi.y + rcm) * S.inv_w[1]));
+    const float Lz = S.L[2];
+    // conservative margin of the column-geometry test (binning rounds in FP32)
+    const float cmarg = 1e-3f + 1e-6f * fmaxf(S.L[0], S.L[1]);
+    const int ncx = cxb - cxa + 1, ncand = ncx * (cyb - cya + 1);
+    const int seg_cap = A.cap / kListSegs;
+    uint2 *LA = A.glist + (long long)g * A.cap;
+    int nseg[kListSegs] = {0, 0, 0, 0};  // entries of each segment
+    int gpass = 0;                        // passing columns so far (decides their segment)
+    for (int c_lo = 0; c_lo < ncand; c_lo += 32) {
+        // the candidate columns of this round whose geometry (a lower bound
+        // of the xy gap) passes, compacted in order
+        const int cc = c_lo + lane;
+        bool pass = false;
+        if (cc < ncand) {
+            const int cy = cya + cc / ncx, cx = cxa + cc % ncx;
+            const float gcx = fmaxf(fmaxf(cx * S.w[0] - hi.x, lo.x - (cx + 1) * S.w[0]) - cmarg, 0.0f);
+            const float gcy = fmaxf(fmaxf(cy * S.w[1] - hi.y, lo.y - (cy + 1) * S.w[1]) - cmarg, 0.0f);
+            pass = gcx * gcx + gcy * gcy < rcm2;
         }
-#pragma unroll
-        for (int r = 0; r < kPartnerRounds; ++r) {
-            const int t = r * 32 + lane;
-            pv[r] = pv[r] >= 0 ? (inv[pv[r] >> 1] << 1) | (pv[r] & 1) : -1;
-            if (t < np) pslot[(long long)I * np + t] = pv[r];
-        }
-#pragma unroll
-        for (int r = 0; r < kPartnerRounds; ++r)
-            if (pv[r] >= 0) bloom |= 1ull << bloom_bit((pv[r] >> 1) / kCluster - S.clus_begin);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) bloom |= __shfl_xor_sync(FULL, bloom, o);
-        const int cxa = max(-S.nx, (int)floorf((lo.x - rcm) * S.inv_w[0]));
-        const int cxb = min(2 * S.nx - 1, (int)floorf((hi.x + rcm) * S.inv_w[0]));
-        const int cya = max(-S.ny, (int)floorf((lo.y - rcm) * S.inv_w[1]));
-        const int cyb = min(2 * S.ny - 1, (int)floorf((hi.y + rcm) * S.inv_w[1]));
-        const float Lz = S.L[2];
-        // conservative margin of the column-geometry test (binning rounds in FP32)
-        const float cmarg = 1e-3f + 1e-6f * fmaxf(S.L[0], S.L[1]);
-        const int ncx = cxb - cxa + 1, ncand = ncx * (cyb - cya + 1);
-        int nA = 0;
-        uint32_t *LA = list + (long long)I * cap;
-        for (int g0 = 0; g0 < ncand; g0 += kListGroup) {
-            // the candidate columns of this group whose geometry (a lower bound of
-            // the xy gap) passes, compacted in order
-            int npass = 0;
-            for (int h = 0; h < kListGroup; h += 32) {
-                const int c = g0 + h + lane;
-                bool pass = false;
-                if (c < ncand) {
-                    const int cy = cya + c / ncx, cx = cxa + c % ncx;
-                    const float gcx = fmaxf(fmaxf(cx * S.w[0] - hi.x, lo.x - (cx + 1) * S.w[0]) - cmarg, 0.0f);
-                    const float gcy = fmaxf(fmaxf(cy * S.w[1] - hi.y, lo.y - (cy + 1) * S.w[1]) - cmarg, 0.0f);
-                    pass = gcx * gcx + gcy * gcy < rcm2;
-                }
-                const unsigned b = __ballot_sync(FULL, pass);
-                if (pass) s_col[wib][npass + __popc(b & lt)] = c;
-                npass += __popc(b);
+        const unsigned b = __ballot_sync(FULL, pass);
+        if (pass) s_col[__popc(b & lt)] = cc;
+        const int npass = __popc(b);
+        __syncwarp();
+        if (npass == 0) continue;
+        const int c = lane < npass ? s_col[lane] : -1;
+        const int seg = (gpass + lane) % kListSegs;  // segment of the lane's column
+        gpass += npass;
+        int jb = 0, nj = 0, va = 0, cnt = 0;
+        uint32_t code_xy = 0u;
+        float ox = 0.0f, oy = 0.0f;
+        if (c >= 0) {
+            const int cy = cya + c / ncx, cx = cxa + c % ncx;
+            const int ccy = cy < 0 ? cy + S.ny : (cy >= S.ny ? cy - S.ny : cy);
+            const int ccx = cx < 0 ? cx + S.nx : (cx >= S.nx ? cx - S.nx : cx);
+            const uint32_t sy = cy < 0 ? 1u : (cy >= S.ny ? 2u : 0u);
+            const uint32_t sx = cx < 0 ? 1u : (cx >= S.nx ? 2u : 0u);
+            ox = sx == 1u ? -S.L[0] : (sx == 2u ? S.L[0] : 0.0f);
+            oy = sy == 1u ? -S.L[1] : (sy == 2u ? S.L[1] : 0.0f);
+            code_xy = sx | (sy << 2);
+            const int col = S.col_begin + ccy * S.nx + ccx;
+            jb = A.col_slot[col] / kCluster;
+            nj = A.col_slot[col + 1] / kCluster - jb;
+            // z window over the virtual indices v (image -L: v - nj, 0: v, +L: v + nj)
+            // from the column's z-bin index, one bin wider on each side
+            // than the FP32 bin arithmetic needs
+            const int2 *zt = A.zbin + S.zb_begin + (long long)(col - S.col_begin) * (S.nzb + 1);
+            const float za = lo.z - rcm, zb = hi.z + rcm;
+            const int ba = (int)floorf((za < 0.0f ? za + Lz : za) * S.inv_dz) - 1;
+            const int bz = (int)floorf((zb >= Lz ? zb - Lz : zb) * S.inv_dz) + 1;
+            const int vlo = zt[min(max(ba, 0), S.nzb)].x - (za < 0.0f ? nj : 0);
+            const int vhi = zt[min(max(bz, 0), S.nzb)].y + (zb >= Lz ? nj : 0);  // one past
+            if (vhi > vlo) {
+                va = vlo;
+                cnt = vhi - vlo;
             }
-            __syncwarp();
-            for (int r0 = 0; r0 < npass; r0 += 32) {
-                const int c = r0 + lane < npass ? s_col[wib][r0 + lane] : -1;
-                int jb = 0, nj = 0, va = 0, cnt = 0;
-                uint32_t code_xy = 0u;
-                float ox = 0.0f, oy = 0.0f;
-                if (c >= 0) {
-                    const int cy = cya + c / ncx, cx = cxa + c % ncx;
-                    const int ccy = cy < 0 ? cy + S.ny : (cy >= S.ny ? cy - S.ny : cy);
-                    const int ccx = cx < 0 ? cx + S.nx : (cx >= S.nx ? cx - S.nx : cx);
-                    const uint32_t sy = cy < 0 ? 1u : (cy >= S.ny ? 2u : 0u);
-                    const uint32_t sx = cx < 0 ? 1u : (cx >= S.nx ? 2u : 0u);
-                    ox = sx == 1u ? -S.L[0] : (sx == 2u ? S.L[0] : 0.0f);
-                    oy = sy == 1u ? -S.L[1] : (sy == 2u ? S.L[1] : 0.0f);
-                    code_xy = sx | (sy << 2);
-                    const int col = S.col_begin + ccy * S.nx + ccx;
-                    jb = col_slot[col] / kCluster;
-                    nj = col_slot[col + 1] / kCluster - jb;
-                    // z window over the virtual indices v (image -L: v - nj, 0: v, +L: v + nj)
-                    // from the column's z-bin index, one bin wider on each side
-                    // than the FP32 bin arithmetic needs
-                    const int2 *zt = zbin + S.zb_begin + (long long)(col - S.col_begin) * (S.nzb + 1);
-                    const float za = lo.z - rcm, zb = hi.z + rcm;
-                    const int ba = (int)floorf((za < 0.0f ? za + Lz : za) * S.inv_dz) - 1;
-                    const int bz = (int)floorf((zb >= Lz ? zb - Lz : zb) * S.inv_dz) + 1;
-                    const int vlo = zt[min(max(ba, 0), S.nzb)].x - (za < 0.0f ? nj : 0);
-                    const int vhi = zt[min(max(bz, 0), S.nzb)].y + (zb >= Lz ? nj : 0);  // one past
-                    if (vhi > vlo) {
-                        va = vlo;
-                        cnt = vhi - vlo;
-                    }
-                }
-                // flatten the windows of the 32 lanes
-                int incl = cnt;
+        }
+        // flatten the windows of the 32 lanes
+        int incl = cnt;
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(FULL, incl, o);
-                    if (lane >= o) incl += y;
-                }
-                const int off = incl - cnt, total = __shfl_sync(FULL, incl, 31);
-                // owner lane of each flattened candidate, for the first kOwnCap
-                for (int t = off; t < min(off + cnt, kOwnCap); ++t) s_own[wib][t] = (unsigned char)lane;
-                __syncwarp();
-                // two candidate rounds at a time: both rounds' box loads are in
-                // flight together; entries are appended in round order
-                for (int p0 = 0; p0 < total; p0 += 64) {
-                    int J[2];
-                    uint32_t code[2];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int off = incl - cnt, total = __shfl_sync(FULL, incl, 31);
+        for (int t = off; t < min(off + cnt, kOwnCap); ++t) s_own[t] = (unsigned char)lane;
+        __syncwarp();
+        for (int p0 = 0; p0 < total; p0 += 32) {
+            const int p = p0 + lane;
+            int src = 0;
+            if (p0 + 31 < kOwnCap) {
+                src = p < total ? s_own[p] : 0;
+            } else {
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int p = p0 + 32 * h + lane;
-                        // owner lane: the last lane whose window starts at or before p
-                        int src = 0;
-                        if (p0 + 32 * h + 31 < kOwnCap) {
-                            src = p < total ? s_own[wib][p] : 0;
+                for (int step = 16; step >= 1; step >>= 1) {
+                    const int o2 = __shfl_sync(FULL, off, src + step);
+                    if (o2 <= p) src += step;
+                }
+            }
+            const int s_off = __shfl_sync(FULL, off, src), s_va = __shfl_sync(FULL, va, src);
+            const int s_jb = __shfl_sync(FULL, jb, src), s_nj = __shfl_sync(FULL, nj, src);
+            const uint32_t s_code = __shfl_sync(FULL, code_xy, src);
+            const float s_ox = __shfl_sync(FULL, ox, src), s_oy = __shfl_sync(FULL, oy, src);
+            const int s_seg = __shfl_sync(FULL, seg, src);
+            unsigned cm = 0u;
+            int J = -1, hs = -1;
+            uint32_t code = 0u;
+            bool flag = false;
+            if (p < total) {
+                float4 jl, jh;
+                J = window_cluster(A.bb, s_va + (p - s_off), s_jb, s_nj, s_code, s_ox, s_oy, Lz, code, jl, jh);
+                if (box_gap2(lo, hi, jl, jh) < rcm2) {
+                    const int gJ = A.group == 1 ? J : A.clus_grp[J];  // groups of one cluster: the same index
+                    const bool other = gJ != g;
+                    if (!other || keep_groups(g, gJ)) {
+                        if (n == 1) {
+                            cm = other || keep_in_group(c0, J, code) ? 1u : 0u;
                         } else {
-#pragma unroll
-                            for (int step = 16; step >= 1; step >>= 1) {
-                                const int o2 = __shfl_sync(FULL, off, src + step);
-                                if (o2 <= p) src += step;
-                            }
+                            for (int q = 0; q < n; ++q)
+                                if (box_gap2(s_lo[q], s_hi[q], jl, jh) < rcm2 &&
+                                    (other || keep_in_group(c0 + q, J, code)))
+                                    cm |= 1u << q;
                         }
-                        const int s_off = __shfl_sync(FULL, off, src), s_va = __shfl_sync(FULL, va, src);
-                        const int s_jb = __shfl_sync(FULL, jb, src), s_nj = __shfl_sync(FULL, nj, src);
-                        const uint32_t s_code = __shfl_sync(FULL, code_xy, src);
-                        const float s_ox = __shfl_sync(FULL, ox, src), s_oy = __shfl_sync(FULL, oy, src);
-                        J[h] = -1;
-                        code[h] = 0u;
-                        if (p < total)
-                            J[h] = window_candidate(bb, lo, hi, s_va + (p - s_off), s_jb, s_nj, s_code, s_ox, s_oy, Lz,
-                                                    rcm2, code[h]);
                     }
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const bool fl = J[h] >= 0 && ((bloom >> bloom_bit(J[h] - S.clus_begin)) & 1ull);
-                        const uint32_t ent = (uint32_t)J[h] | (code[h] << kShiftBit) | (fl ? kExclFlag : 0u);
-                        const bool hit = J[h] >= 0 && keep_half(I, J[h], code[h]);
-                        const unsigned b = __ballot_sync(FULL, hit);
-                        if (hit) {
-                            const int q = nA + __popc(b & lt);
-                            if (q < cap) LA[q] = ent;
-                        }
-                        nA += __popc(b);
+                    if (cm) {
+                        const bool self = !other && code == 0u && ((cm >> (J - c0)) & 1u);
+                        hs = hset_find(s_hash, J);
+                        flag = all_flag || self || hs >= 0;
                     }
                 }
-                __syncwarp();  // the owner table is rewritten by the next round
             }
-            __syncwarp();
+            const bool hit = cm != 0u;
+            uint2 ent = make_uint2((uint32_t)J | (code << kShiftBit) | (flag ? kExclFlag : 0u), cm);
+            // flagged entries: a mask record each, filled by its own lane
+            const bool fl = hit && flag;
+            const unsigned fb = __ballot_sync(FULL, fl);
+            int mbase = 0;
+            if (fb && lane == 0) mbase = atomicAdd(A.mask_count, __popc(fb));
+            mbase = __shfl_sync(FULL, mbase, 0);
+            if (fl) {
+                const int slot = mbase + __popc(fb & lt);
+                if (slot < A.mask_cap) {
+                    ulonglong2 *rec = A.gmask + (long long)slot * kMaxGroup;
+                    entry_masks(s_pslot, s_next, hs >= 0 ? s_head[hs] : -1, K, c0, n, cm, J, code, rec);
+                    if (all_flag) {  // the table overflowed: scan every partner
+                        for (unsigned cc = cm; cc; cc &= cc - 1u) {
+                            const int q = __ffs(cc) - 1;
+                            ulonglong2 r = rec[q];
+                            for (int t = q * kCluster * K; t < (q + 1) * kCluster * K; ++t) {
+                                const int v = s_pslot[t];
+                                if (v < 0 || ((v >> 1) / kCluster) != J) continue;
+                                const unsigned long long bit = 1ull << (((t / K) % kCluster) * kCluster + ((v >> 1) & 7));
+                                if (v & 1) r.y |= bit;
+                                else r.x |= bit;
+                            }
+                            rec[q] = r;
+                        }
+                    }
+                    ent.y |= (uint32_t)slot << kMaskSlotBit;
+                } else {
+                    atomicOr(A.status, ST_CAPACITY);
+                    ent.x &= ~kExclFlag;
+                }
+            }
+            // append to the lane's segment, in lane order within each segment
+#pragma unroll
+            for (int sg = 0; sg < kListSegs; ++sg) {
+                const unsigned bs = __ballot_sync(FULL, hit && s_seg == sg);
+                if (hit && s_seg == sg) {
+                    const int q = nseg[sg] + __popc(bs & lt);
+                    if (q < seg_cap) LA[(long long)sg * seg_cap + q] = ent;
+                }
+                nseg[sg] += __popc(bs);
+            }
         }
-        if (lane == 0) {
-            list_n[I] = min(nA, cap);
-            if (nA > cap) atomicOr(status, ST_CAPACITY);
-        }
+        __syncwarp();  // the owner table and column list are rewritten by the next round
+    }
+    if (lane < kListSegs) {
+        int m = nseg[0];
+#pragma unroll
+        for (int sg = 1; sg < kListSegs; ++sg) m = lane == sg ? nseg[sg] : m;
+        A.glist_n[(long long)g * kListSegs + lane] = min(m, seg_cap);
+        if (m > seg_cap) atomicOr(A.status, ST_CAPACITY);
     }
 }
 
@@ -529,27 +704,47 @@ cudaError_t launch_build_cells(nb_ctx *ctx, const float *d_pos)
     if (e != cudaSuccess) return e;
     const int tb = 256;
     e = launch_pdl(k_bin, dim3((N + tb - 1) / tb), dim3(tb), 0, st, N, d_pos, d.sys, d.atom_sys, d.wpos, d.atom_col,
-                   d.col_count, ctx->n_cols, ctx->n_sys, d.col_slot, d.col_fill, d.counts, d.status);
+                   d.col_count, ctx->n_cols, ctx->n_sys, d.col_slot, d.col_fill, d.counts, d.status, ctx->group,
+                   d.col_grp);
     if (e == cudaSuccess)
         e = launch_pdl(k_scatter, dim3((N + tb - 1) / tb), dim3(tb), 0, st, N, d.atom_col, d.col_fill, d.stage);
     if (e == cudaSuccess)
         e = launch_pdl(k_colsort, dim3(ctx->n_cols), dim3(kSortThreads), 0, st, d.col_count, d.col_slot, d.col_sys,
-                       d.sys, d.stage, d.wpos, d.xyzq, d.tslot, d.perm, d.inv, d.bb, d.clus_sys, d.zbin);
+                       d.sys, d.stage, d.wpos, d.xyzq, d.tslot, d.perm, d.inv, d.bb, d.clus_sys, d.zbin, ctx->group,
+                       d.col_grp, d.grp, d.clus_grp);
     if (e != cudaSuccess) return e;
+    ctx->built_group = ctx->group;
     return cudaGetLastError();
 }
 
 cudaError_t launch_build_lists(nb_ctx *ctx)
 {
     auto &d = ctx->d;
-    cudaStream_t st = ctx->stream;
-    cudaError_t e = cudaSuccess;
-    const int lw = kListWarps;
-    const int lblocks = (int)std::max<int64_t>(1, (ctx->clus_cap + lw - 1) / lw);
-    if (e == cudaSuccess)
-        e = launch_pdl(k_list, dim3(lblocks), dim3(lw * 32), 0, st, d.sys, d.counts, d.bb, d.clus_sys, d.col_slot,
-                       d.zbin, d.perm, d.part_orig, d.inv, ctx->K, ctx->pp.rc + ctx->pp.list_margin, ctx->list_cap,
-                       d.list, d.list_n, d.pslot, d.status);
+    GListArgs A;
+    A.sys = d.sys;
+    A.counts = d.counts;
+    A.mask_count = d.counts + 5;
+    A.bb = d.bb;
+    A.clus_sys = d.clus_sys;
+    A.col_slot = d.col_slot;
+    A.zbin = d.zbin;
+    A.perm = d.perm;
+    A.part_orig = d.part_orig;
+    A.inv = d.inv;
+    A.grp = d.grp;
+    A.clus_grp = d.clus_grp;
+    A.glist = d.glist;
+    A.glist_n = d.glist_n;
+    A.gmask = d.gmask;
+    A.status = d.status;
+    A.mask_cap = ctx->mask_cap;
+    A.K = ctx->K;
+    A.rcm = ctx->pp.rc + ctx->pp.list_margin;
+    A.cap = ctx->list_cap;
+    A.group = ctx->group;
+    const size_t smem = sizeof(int) * kGListWarps * glist_warp_ints(ctx->K);
+    const int64_t blocks = std::max<int64_t>(1, (ctx->grp_cap + kGListWarps - 1) / kGListWarps);
+    cudaError_t e = launch_pdl(k_glist, dim3((unsigned)blocks), dim3(kGListWarps * 32), smem, ctx->stream, A);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }

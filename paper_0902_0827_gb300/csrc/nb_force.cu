@@ -33,12 +33,13 @@ struct ForceArgs {
     const int *tslot;
     const int *perm;
     const int *clus_sys;
-    const uint32_t *list;     // [NC*cap] per cluster: its half list (Newton's third law)
-    const int *list_n;        // [NC] lengths
-    const int *pslot;         // [S*K] partner slots (slot << 1) | is14, -1 pad
-    int cap;                  // entries per list
+    const int2 *grp;          // [GC] i-groups: (first cluster, clusters)
+    const uint2 *glist;       // [GC*cap] per group: its list, kListSegs segments of cap / kListSegs
+    const int *glist_n;       // [GC*kListSegs] segment lengths
+    const ulonglong2 *gmask;  // exclusion bitmask records of the flagged entries
+    int cap;                  // entries per group list
     int K;
-    const float2 *lj_tab;
+    const float4 *lj_tab;     // [T*T] (A, B, A - fl(A), B - fl(B))
     const float4 *rtab;       // [n*3] tabulated radial functions, or null
     long long *facc;          // [S*3] fixed-point forces in sorted order (forward)
     long long *sys_acc;
@@ -239,21 +240,23 @@ __device__ __forceinline__ void add_type_grads(const AdjTables &S, int key, floa
 // 6 B) per type pair.  The force on i is subtracted from acc and the force
 // on j added to fj with explicit FMA, so that the bits do not depend on how
 // the caller was inlined.
+// The LJ coefficients of the forward kernels in shared memory: lj (A, B,
+// 12 A, 6 B) per type pair, followed by lo (the FP32 remainders of A, B).
 template <int RAD, bool W14>
-__device__ __forceinline__ void eval_pair(const PairParams &P, const float4 *__restrict__ lj,
-                                          const float4 *__restrict__ rtab, int ti_row, float qi, bool in, float dx,
-                                          float dy, float dz, float r2, float qj, int tj, bool is14, Acc &acc,
-                                          float &fjx, float &fjy, float &fjz)
+__device__ __forceinline__ float pair_fs(const PairParams &P, const float4 *__restrict__ lj,
+                                         const float4 *__restrict__ rtab, int ti_row, float qi, bool in, float r2,
+                                         float qj, int tj, bool is14, float &elj_acc, float &ec_acc)
 {
     float rinv, r;
     pair_rinv(r2, rinv, r);
     const float r2inv = __fmul_rn(rinv, rinv);
     const float4 ab = lj[ti_row + tj];
+    const float2 lo = reinterpret_cast<const float2 *>(lj + P.n_types * P.n_types)[ti_row + tj];
     float elj, frlj, ec, frc;
     if constexpr (RAD == 2)
-        pair_radial_tab(P, rtab, r, ab.x, ab.y, qi * qj, elj, frlj, ec, frc);
+        pair_radial_tab(P, rtab, r, ab.x, ab.y, lo, qi * qj, elj, frlj, ec, frc);
     else
-        pair_radial<RAD == 1, true>(P, r2, r, rinv, r2inv, ab, qi * qj, elj, frlj, ec, frc);
+        pair_radial<RAD == 1, true>(P, r2, r, rinv, r2inv, ab, lo, qi * qj, elj, frlj, ec, frc);
     // F_i = U'(r) d / r = -fs d with fs = -U'(r) / r
     float fs, wel, wec;
     if (W14) {
@@ -267,9 +270,20 @@ __device__ __forceinline__ void eval_pair(const PairParams &P, const float4 *__r
         wel = elj;
         wec = ec;
     }
-    fs = in ? fs : 0.0f;
-    acc.elj = __fadd_rn(acc.elj, in ? wel : 0.0f);
-    acc.ec = __fadd_rn(acc.ec, in ? wec : 0.0f);
+    elj_acc = __fadd_rn(elj_acc, in ? wel : 0.0f);
+    ec_acc = __fadd_rn(ec_acc, in ? wec : 0.0f);
+    return in ? fs : 0.0f;
+}
+
+// One pair: fs as above, the force on i subtracted from acc and the force on
+// j added to fj with explicit FMA (bits independent of inlining).
+template <int RAD, bool W14>
+__device__ __forceinline__ void eval_pair(const PairParams &P, const float4 *__restrict__ lj,
+                                          const float4 *__restrict__ rtab, int ti_row, float qi, bool in, float dx,
+                                          float dy, float dz, float r2, float qj, int tj, bool is14, Acc &acc,
+                                          float &fjx, float &fjy, float &fjz)
+{
+    const float fs = pair_fs<RAD, W14>(P, lj, rtab, ti_row, qi, in, r2, qj, tj, is14, acc.elj, acc.ec);
     acc.fx = __fmaf_rn(-fs, dx, acc.fx);
     acc.fy = __fmaf_rn(-fs, dy, acc.fy);
     acc.fz = __fmaf_rn(-fs, dz, acc.fz);
@@ -279,49 +293,47 @@ __device__ __forceinline__ void eval_pair(const PairParams &P, const float4 *__r
 }
 
 // ---------------------------------------------------------------------------
-// Forward kernel (k_force) on cluster-pair tiles.
+// Pair export of the debug instantiation: every evaluated pair inside the
+// cutoff and not excluded, as caller indices (i < j).
+__device__ __forceinline__ void record_pair(const ForceArgs &A, int io, int jo)
+{
+    atomicAdd((unsigned long long *)&A.dbg_n[0], 1ull);
+    const long long q = (long long)atomicAdd((unsigned long long *)&A.dbg_n[1], 1ull);
+    if (q < A.dbg_cap) {
+        A.dbg_ij[2 * q] = min(io, jo);
+        A.dbg_ij[2 * q + 1] = max(io, jo);
+    }
+}
+
+// Forward kernel (k_force) on i-group tiles.
 //
-// One warp evaluates one listed cluster pair (I, J) at a time as an 8 x 8
-// tile: lane = jj + 8 ih holds j atom jj of J and the i atoms ih and ih + 4
-// of I, so every lane computes two pairs and the tile needs no compaction:
-// pairs beyond the cutoff (and excluded pairs, padding) are evaluated and
-// masked.  The force on i stays in the lane's registers for the whole work
-// unit; the force on j (two pairs per lane) is summed over the 4 lanes of
-// that j atom with shuffles and added to the global 64-bit fixed-point sums,
-// one atomic per atom and component, as is the force on i (summed over its 8
-// lanes) when the unit is done.  The FP32 sums run in a fixed order and meet
-// only in integer sums, so results are run-to-run bit-identical.  A
-// cluster's half list is cut into `parts` work units, which the warps of a
-// persistent grid claim from a counter (dynamic balance of the uneven list
-// lengths), the next claim issued while the current unit runs.  Each batch
-// of up to 32 entries has the listed clusters' atoms staged in the warp's
-// shared memory (cp.async) and is then walked, plain entries first.
+// A work unit is one part of one segment of an i-group's list (the group:
+// G consecutive clusters of a column, 8 G atoms).  A warp holds the group's
+// atoms in its shared memory and walks the entries; an entry (J, image,
+// cluster mask) stands for the tiles (group cluster c, J) of the clusters c
+// in its mask.  Lane = ia + 8 jb computes, for every tile, the pairs of i
+// atom ia of cluster c with j atoms jb and jb + 4 of J (an 8 x 8 tile, two
+// pairs per lane, nothing compacted: pairs beyond the cutoff, excluded pairs
+// and padding are evaluated and masked).  J's atoms are read once per entry
+// and the force on them is summed over all tiles of the entry in registers,
+// then over the 8 lanes of each j atom and added to the global 64-bit
+// fixed-point sums (one atomic per atom and component), so the per-entry
+// cost (staging, decode, j-force reduction and atomics) is shared by the
+// entry's tiles.  The force on i accumulates per lane and cluster in shared
+// memory and is summed and added when the unit is done.  J's z-sorted atoms
+// form a lower half (jb) and an upper half (jb + 4), which are often not
+// both within reach of cluster c: the membership of both pairs comes first
+// and the radial arithmetic of a half runs only when one of its 32 pairs is
+// in range (warp vote).  Flagged entries carry exclusion bitmasks per tile
+// (excluded pairs dropped, 1-4 pairs scaled; the direct self tile's pairs
+// j <= i excluded).  The FP32 sums run in a fixed order and meet only in
+// integer sums, so results are run-to-run bit-identical.
 constexpr int kTileWarps = 8;            // warps per block of the tile kernel
+constexpr int kBatch = 16;               // entries staged per batch
 #ifndef ACENB_TILE_MIN_BLOCKS
 #define ACENB_TILE_MIN_BLOCKS 3          // resident blocks per SM the register budget is cut for
 #endif
 constexpr float kFarCoord = 3.0e18f;     // i-side padding: far from every atom and from the j-side padding
-
-// One i atom of a lane: coordinates, ke q_i, type row.
-struct TileI {
-    float x, y, z, q;
-    int trow;
-    int orig;  // caller index (pair export)
-};
-
-__device__ __forceinline__ TileI load_tile_i(const ForceArgs &A, long long slot, int T, bool debug)
-{
-    float4 p = __ldg(A.xyzq + slot);
-    if (!is_real_coord(p.x)) p.x = p.y = p.z = kFarCoord;
-    TileI t;
-    t.x = p.x;
-    t.y = p.y;
-    t.z = p.z;
-    t.q = p.w * A.P.ke;
-    t.trow = __ldg(A.tslot + slot) * T;
-    t.orig = debug ? __ldg(A.perm + slot) : -1;
-    return t;
-}
 
 // Fixed-point value (2^32) of an FP32 sum; a value too large for the sums
 // (or not finite) adds zero and sets ovf.
@@ -332,120 +344,142 @@ __device__ __forceinline__ long long tile_fixed(float f, bool &ovf)
     return __float2ll_rn((ok ? f : 0.0f) * 4294967296.0f);
 }
 
-// Membership of one pair of a tile: the i atom at its image for the entry's
-// shift code (IMG: x_i - L on axes with code 2; the j side was shifted by
-// the caller), d = x_j - x_i and the FP32 predicate r2 < rc2 of the other
-// kernels.
-template <bool IMG>
-__device__ __forceinline__ bool tile_member(const ForceArgs &A, const TileI &ti, uint32_t code, float4 pj, float Lx,
-                                            float Ly, float Lz, float &dx, float &dy, float &dz, float &r2)
+// Work unit u of the tile kernels: group, segment of its list, part of the
+// segment, and the entry range [e_begin, e_end) of that part.
+struct Unit {
+    int g, e_begin, e_end;
+    long long base;  // first entry of the segment in the group lists
+};
+
+__device__ __forceinline__ Unit unit_of(const ForceArgs &A, int u, int parts)
 {
-    float ax = ti.x, ay = ti.y, az = ti.z;
+    Unit U;
+    const int per_g = kListSegs * parts;
+    U.g = u / per_g;
+    const int r = u - U.g * per_g;
+    const int seg = r / parts, part = r - seg * parts;
+    const int n = __ldg(A.glist_n + (long long)U.g * kListSegs + seg);
+    const int per = (n + parts - 1) / parts;
+    U.e_begin = min(n, part * per);
+    U.e_end = min(n, U.e_begin + per);
+    U.base = (long long)U.g * A.cap + (long long)seg * (A.cap / kListSegs);
+    return U;
+}
+
+// The exclusion and 1-4 bits of a lane's two pairs (i atom ia, j atoms jb
+// and jb + 4) in a flagged tile.
+__device__ __forceinline__ void tile_mask_bits(ulonglong2 m, int ia, int jb, bool &inA, bool &inB, bool &s14A,
+                                               bool &s14B)
+{
+    const int bA = ia * kCluster + jb, bB = bA + 4;
+    inA = inA && !((m.x >> bA) & 1ull);
+    inB = inB && !((m.x >> bB) & 1ull);
+    s14A = (m.y >> bA) & 1ull;
+    s14B = (m.y >> bB) & 1ull;
+}
+
+// One tile (group cluster c, entry J) of a lane: i atom ia of cluster c at
+// its image (IMG: x_i - L on axes with code 2), the pairs with the lane's
+// j atoms pjA (jb) and pjB (jb + 4), already at their image (code 1 axes).
+// SPECIAL: the entry carries exclusion bitmasks (gm).
+template <int RAD, bool DEBUG, bool SPECIAL, bool IMG>
+__device__ __forceinline__ void tile_pair2(const ForceArgs &A, const float4 *__restrict__ lj, float4 pi, int trow,
+                                           int iorig, float4 pjA, float4 pjB, int tjA, int tjB, int jorigA,
+                                           int jorigB, uint32_t code, float Lx, float Ly, float Lz, ulonglong2 gm,
+                                           int ia, int jb, float4 &fi, float &elj, float &ec, float &fjAx,
+                                           float &fjAy, float &fjAz, float &fjBx, float &fjBy, float &fjBz)
+{
     if (IMG) {
-        if ((code & 3u) == 2u) ax = __fsub_rn(ax, Lx);
-        if (((code >> 2) & 3u) == 2u) ay = __fsub_rn(ay, Ly);
-        if ((code >> 4) == 2u) az = __fsub_rn(az, Lz);
+        if ((code & 3u) == 2u) pi.x = __fsub_rn(pi.x, Lx);
+        if (((code >> 2) & 3u) == 2u) pi.y = __fsub_rn(pi.y, Ly);
+        if ((code >> 4) == 2u) pi.z = __fsub_rn(pi.z, Lz);
     }
-    r2 = disp_r2(pj.x, pj.y, pj.z, ax, ay, az, dx, dy, dz);
-    return r2 < A.P.rc2;
-}
-
-// Masked evaluation of one pair of a tile (see eval_pair); the force on j
-// is added to fj.
-template <int RAD, bool SPECIAL, bool DEBUG>
-__device__ __forceinline__ void tile_eval(const ForceArgs &A, const float4 *__restrict__ lj, const TileI &ti, bool in,
-                                          float dx, float dy, float dz, float r2, float4 pj, int tj, bool is14,
-                                          int jorig, Acc &acc, float &fjx, float &fjy, float &fjz)
-{
-    if (DEBUG && in) {
-        atomicAdd((unsigned long long *)&A.dbg_n[0], 1ull);
-        const long long q = (long long)atomicAdd((unsigned long long *)&A.dbg_n[1], 1ull);
-        if (q < A.dbg_cap) {
-            A.dbg_ij[2 * q] = min(ti.orig, jorig);
-            A.dbg_ij[2 * q + 1] = max(ti.orig, jorig);
-        }
-    }
-    // only a special entry can hold r2 = 0 (an atom and itself, masked)
-    eval_pair<RAD, SPECIAL>(A.P, lj, A.rtab, ti.trow, ti.q, in, dx, dy, dz, SPECIAL ? (in ? r2 : 1.0f) : r2, pj.w, tj,
-                            is14, acc, fjx, fjy, fjz);
-}
-
-// One listed cluster J against the lane's two i atoms.  The tile's i atoms
-// are z-sorted, so the lower half (atoms 0..3, pair A of every lane) and the
-// upper half (4..7, pair B) are often not both within the cutoff of J: the
-// membership of both pairs comes first, and the radial arithmetic of a half
-// runs only when one of its 32 pairs is in range (warp vote).  SPECIAL
-// entries are I's own cluster (pairs j > i only) and entries flagged as
-// holding a topology partner (exclusions removed, 1-4 pairs scaled); IMG
-// entries have a periodic shift code.  (Each kind has its own code: the
-// plain kind, most entries, then carries no weights or image selects.)
-template <int RAD, bool VIRIAL, bool DEBUG, bool SPECIAL, bool IMG>
-__device__ __forceinline__ void tile_entry(const ForceArgs &A, const float4 *__restrict__ lj,
-                                           const int *__restrict__ spart, int I, uint32_t ent, float4 pj, int tj,
-                                           const TileI &ia, const TileI &ib, int jj, int ih, float Lx, float Ly,
-                                           float Lz, Acc &acA, Acc &acB, float (&wimg)[6], bool &ovf)
-{
-    const int J = (int)(ent & kJMask);
-    const uint32_t code = IMG ? (ent >> kShiftBit) & 0x3Fu : 0u;
-    if (IMG) {  // j-side images (code 1): fl(x_j - L), as the other kernels stage them
-        if ((code & 3u) == 1u) pj.x = __fsub_rn(pj.x, Lx);
-        if (((code >> 2) & 3u) == 1u) pj.y = __fsub_rn(pj.y, Ly);
-        if ((code >> 4) == 1u) pj.z = __fsub_rn(pj.z, Lz);
-    }
-    float dxA, dyA, dzA, r2A, dxB, dyB, dzB, r2B;
-    bool inA = tile_member<IMG>(A, ia, code, pj, Lx, Ly, Lz, dxA, dyA, dzA, r2A);
-    bool inB = tile_member<IMG>(A, ib, code, pj, Lx, Ly, Lz, dxB, dyB, dzB, r2B);
+    float dxA, dyA, dzA, dxB, dyB, dzB;
+    const float r2A = disp_r2(pjA.x, pjA.y, pjA.z, pi.x, pi.y, pi.z, dxA, dyA, dzA);
+    const float r2B = disp_r2(pjB.x, pjB.y, pjB.z, pi.x, pi.y, pi.z, dxB, dyB, dzB);
+    bool inA = r2A < A.P.rc2, inB = r2B < A.P.rc2;
     bool s14A = false, s14B = false;
-    if (SPECIAL) {
-        if (J == I && code == 0u) {
-            inA = inA && jj > ih;
-            inB = inB && jj > ih + 4;
-        }
-        if (ent & kExclFlag) {
-            const int jslot = J * kCluster + jj;
-            for (int m = 0; m < A.K; ++m) {
-                const int pa = spart[ih * A.K + m], pb = spart[(ih + 4) * A.K + m];
-                if (pa >= 0 && (pa >> 1) == jslot) {
-                    if (pa & 1) s14A = true;
-                    else inA = false;
-                }
-                if (pb >= 0 && (pb >> 1) == jslot) {
-                    if (pb & 1) s14B = true;
-                    else inB = false;
-                }
-            }
-        }
-    }
+    if (SPECIAL) tile_mask_bits(gm, ia, jb, inA, inB, s14A, s14B);
     const bool anyA = __any_sync(kFull, inA), anyB = __any_sync(kFull, inB);
     if (!anyA && !anyB) return;
-    const int jorig = DEBUG ? __ldg(A.perm + (long long)J * kCluster + jj) : -1;
-    float fjx = 0.0f, fjy = 0.0f, fjz = 0.0f;
-    if (anyA) tile_eval<RAD, SPECIAL, DEBUG>(A, lj, ia, inA, dxA, dyA, dzA, r2A, pj, tj, s14A, jorig, acA, fjx, fjy, fjz);
-    if (anyB) tile_eval<RAD, SPECIAL, DEBUG>(A, lj, ib, inB, dxB, dyB, dzB, r2B, pj, tj, s14B, jorig, acB, fjx, fjy, fjz);
-    // the force on j atom jj: sum over its 4 lanes, then lanes ih = 0, 1, 2
-    // add the x, y, z components
-#pragma unroll
-    for (int o = 8; o < 32; o <<= 1) {
-        fjx = __fadd_rn(fjx, __shfl_xor_sync(kFull, fjx, o));
-        fjy = __fadd_rn(fjy, __shfl_xor_sync(kFull, fjy, o));
-        fjz = __fadd_rn(fjz, __shfl_xor_sync(kFull, fjz, o));
+    Acc acc = {fi.x, fi.y, fi.z, elj, ec};
+    if (anyA) {
+        if (DEBUG && inA) record_pair(A, iorig, jorigA);
+        // only a special (flagged) tile can hold r2 = 0 (the self tile's diagonal, masked)
+        eval_pair<RAD, SPECIAL>(A.P, lj, A.rtab, trow, pi.w, inA, dxA, dyA, dzA, SPECIAL ? (inA ? r2A : 1.0f) : r2A,
+                                pjA.w, tjA, s14A, acc, fjAx, fjAy, fjAz);
     }
-    const float fc = ih == 0 ? fjx : (ih == 1 ? fjy : fjz);
-    const long long fv = tile_fixed(fc, ovf);  // every lane (lane ih = 3 holds z again): no branch
-    if (ih < 3) atomicAdd((unsigned long long *)&A.facc[24ll * J + 3 * jj + ih], (unsigned long long)fv);
-    if (VIRIAL && IMG && ih == 0) {
+    if (anyB) {
+        if (DEBUG && inB) record_pair(A, iorig, jorigB);
+        eval_pair<RAD, SPECIAL>(A.P, lj, A.rtab, trow, pi.w, inB, dxB, dyB, dzB, SPECIAL ? (inB ? r2B : 1.0f) : r2B,
+                                pjB.w, tjB, s14B, acc, fjBx, fjBy, fjBz);
+    }
+    fi = make_float4(acc.fx, acc.fy, acc.fz, 0.0f);
+    elj = acc.elj;
+    ec = acc.ec;
+}
+
+// One entry: J's atoms for the lane (jb, jb + 4) from the staged batch, the
+// tiles of every group cluster in its mask, then the force on J's atoms.
+template <int G, int RAD, bool VIRIAL, bool DEBUG, bool SPECIAL, bool IMG>
+__device__ __forceinline__ void tile_entry(const ForceArgs &A, const float4 *__restrict__ lj,
+                                           const float4 *__restrict__ s_ix, const int *__restrict__ s_it,
+                                           const int *__restrict__ s_io, float4 *__restrict__ s_fi, uint2 ent,
+                                           float4 pjA, float4 pjB, int tjA, int tjB, int ia, int jb, int lane, float Lx,
+                                           float Ly, float Lz, float &elj, float &ec, float (&wimg)[6], bool &ovf)
+{
+    const int J = (int)(ent.x & kJMask);
+    const uint32_t code = IMG ? (ent.x >> kShiftBit) & 0x3Fu : 0u;
+    if (IMG) {  // j-side images (code 1): fl(x_j - L), as the other kernels stage them
+        if ((code & 3u) == 1u) { pjA.x = __fsub_rn(pjA.x, Lx); pjB.x = __fsub_rn(pjB.x, Lx); }
+        if (((code >> 2) & 3u) == 1u) { pjA.y = __fsub_rn(pjA.y, Ly); pjB.y = __fsub_rn(pjB.y, Ly); }
+        if ((code >> 4) == 1u) { pjA.z = __fsub_rn(pjA.z, Lz); pjB.z = __fsub_rn(pjB.z, Lz); }
+    }
+    const int jorigA = DEBUG ? __ldg(A.perm + (long long)J * kCluster + jb) : -1;
+    const int jorigB = DEBUG ? __ldg(A.perm + (long long)J * kCluster + jb + 4) : -1;
+    const ulonglong2 *rec = SPECIAL ? A.gmask + (long long)(ent.y >> kMaskSlotBit) * kMaxGroup : nullptr;
+    float fjAx = 0.0f, fjAy = 0.0f, fjAz = 0.0f, fjBx = 0.0f, fjBy = 0.0f, fjBz = 0.0f;
+    for (unsigned cm = ent.y & 0xFFu; cm; cm &= cm - 1u) {
+        const int c = __ffs(cm) - 1;
+        const int ii = c * kCluster + ia;
+        const ulonglong2 gm = SPECIAL ? rec[c] : make_ulonglong2(0ull, 0ull);
+        float4 fi = s_fi[c * 32 + lane];
+        tile_pair2<RAD, DEBUG, SPECIAL, IMG>(A, lj, s_ix[ii], s_it[ii], DEBUG ? s_io[ii] : -1, pjA, pjB, tjA, tjB,
+                                             jorigA, jorigB, code, Lx, Ly, Lz, gm, ia, jb, fi, elj, ec, fjAx, fjAy,
+                                             fjAz, fjBx, fjBy, fjBz);
+        s_fi[c * 32 + lane] = fi;
+    }
+    // the force on J's atoms: sum over the 8 lanes of each (lanes ia), then
+    // lanes ia = 0, 1, 2 add atom jb's x, y, z and ia = 3, 4, 5 atom jb + 4's
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+        fjAx = __fadd_rn(fjAx, __shfl_xor_sync(kFull, fjAx, o));
+        fjAy = __fadd_rn(fjAy, __shfl_xor_sync(kFull, fjAy, o));
+        fjAz = __fadd_rn(fjAz, __shfl_xor_sync(kFull, fjAz, o));
+        fjBx = __fadd_rn(fjBx, __shfl_xor_sync(kFull, fjBx, o));
+        fjBy = __fadd_rn(fjBy, __shfl_xor_sync(kFull, fjBy, o));
+        fjBz = __fadd_rn(fjBz, __shfl_xor_sync(kFull, fjBz, o));
+    }
+    const float fv = ia == 0 ? fjAx : ia == 1 ? fjAy : ia == 2 ? fjAz : ia == 3 ? fjBx : ia == 4 ? fjBy : fjBz;
+    const long long fx = tile_fixed(fv, ovf);  // every lane (ia = 6, 7 hold z of B again): no branch
+    if (ia < 6 && fx != 0) {
+        const int j = ia < 3 ? jb : jb + 4;
+        atomicAdd((unsigned long long *)&A.facc[24ll * J + 3 * j + (ia < 3 ? ia : ia - 3)], (unsigned long long)fx);
+    }
+    if (VIRIAL && IMG && ia == 0) {
         // periodic-image part of the virial: s (x) f_j with the entry's
         // shift s of j (code 1: -L, code 2: +L per axis)
         const uint32_t cx = code & 3u, cy = (code >> 2) & 3u, cz = code >> 4;
         const float sx = cx == 1u ? -Lx : (cx == 2u ? Lx : 0.0f);
         const float sy = cy == 1u ? -Ly : (cy == 2u ? Ly : 0.0f);
         const float sz = cz == 1u ? -Lz : (cz == 2u ? Lz : 0.0f);
-        wimg[0] = __fmaf_rn(sx, fjx, wimg[0]);
-        wimg[1] = __fmaf_rn(sy, fjy, wimg[1]);
-        wimg[2] = __fmaf_rn(sz, fjz, wimg[2]);
-        wimg[3] = __fmaf_rn(sx, fjy, wimg[3]);
-        wimg[4] = __fmaf_rn(sx, fjz, wimg[4]);
-        wimg[5] = __fmaf_rn(sy, fjz, wimg[5]);
+        const float gx = __fadd_rn(fjAx, fjBx), gy = __fadd_rn(fjAy, fjBy), gz = __fadd_rn(fjAz, fjBz);
+        wimg[0] = __fmaf_rn(sx, gx, wimg[0]);
+        wimg[1] = __fmaf_rn(sy, gy, wimg[1]);
+        wimg[2] = __fmaf_rn(sz, gz, wimg[2]);
+        wimg[3] = __fmaf_rn(sx, gy, wimg[3]);
+        wimg[4] = __fmaf_rn(sx, gz, wimg[4]);
+        wimg[5] = __fmaf_rn(sy, gz, wimg[5]);
     }
 }
 
@@ -483,7 +517,20 @@ __device__ __forceinline__ void tile_warp_sums(long long (&e)[2], long long &wv,
     wv = 0;
 }
 
-template <int RAD, bool VIRIAL, bool DEBUG>
+// Bytes of the forward kernels' LJ table: (A, B, 12 A, 6 B) and (A, B)
+// remainders per type pair, rounded up to 16.
+__host__ __device__ inline size_t lj_table_bytes(int T) { return align16((size_t)T * T * 24); }
+
+// Shared memory of the forward kernel: the type-pair table (A, B, 12 A, 6 B)
+// and per warp the unit's i atoms (coordinates + ke q, type row, caller
+// index), the lanes' i-force partials per cluster, and one staged batch of
+// entries' j atoms (coordinates + charge, type).
+__host__ __device__ inline size_t tile_warp_bytes(int G)
+{
+    return (size_t)kCluster * G * (16 + 4 + 4) + (size_t)G * 32 * 16 + (size_t)kBatch * kCluster * (16 + 4);
+}
+
+template <int G, int RAD, bool VIRIAL, bool DEBUG>
 __global__ void __launch_bounds__(kTileWarps * 32, ACENB_TILE_MIN_BLOCKS) k_force(ForceArgs A, int parts)
 {
     pdl_entry();
@@ -491,142 +538,159 @@ __global__ void __launch_bounds__(kTileWarps * 32, ACENB_TILE_MIN_BLOCKS) k_forc
     __shared__ long long s_val[kTileWarps][kTaskVals];
     __shared__ int s_sys[kTileWarps];
     const int T = A.P.n_types;
-    const int K = A.K;
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, jj = lane & 7, ih = lane >> 3;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, ia = lane & 7, jb = lane >> 3;
     float4 *lj = reinterpret_cast<float4 *>(smem);  // (A, B, 12 A, 6 B) per type pair
-    size_t off = (size_t)T * T * 16;
-    int *spart = reinterpret_cast<int *>(smem + off) + w * kCluster * K;
-    off += align16((size_t)kTileWarps * kCluster * K * 4);
-    float4 *sjp = reinterpret_cast<float4 *>(smem + off) + w * 32 * kCluster;  // staged j coordinates + charges
-    off += (size_t)kTileWarps * 32 * kCluster * 16;
-    int *sjt = reinterpret_cast<int *>(smem + off) + w * 32 * kCluster;  // staged j types
+    unsigned char *wbase = smem + lj_table_bytes(T) + (size_t)w * tile_warp_bytes(G);
+    float4 *s_ix = reinterpret_cast<float4 *>(wbase);                          // [8 G]
+    float4 *s_fi = s_ix + kCluster * G;                                          // [G * 32]
+    float4 *sjp = s_fi + G * 32;                                                 // [kBatch * 8]
+    int *s_it = reinterpret_cast<int *>(sjp + kBatch * kCluster);                // [8 G]
+    int *s_io = s_it + kCluster * G;                                             // [8 G]
+    int *sjt = s_io + kCluster * G;                                              // [kBatch * 8]
     for (int k = threadIdx.x; k < T * T; k += blockDim.x) {
-        const float2 ab = A.lj_tab[k];
+        const float4 ab = A.lj_tab[k];
         lj[k] = make_float4(ab.x, ab.y, 12.0f * ab.x, 6.0f * ab.y);
+        reinterpret_cast<float2 *>(lj + T * T)[k] = make_float2(ab.z, ab.w);
     }
     __syncthreads();
-    const int n_units = A.counts[1] * parts;
+    const int n_units = A.counts[4] * kListSegs * parts;
     int cur_sys = -1;
     float Lx = 0.0f, Ly = 0.0f, Lz = 0.0f;
     long long esum[2] = {0, 0};  // per lane: fixed-point energies of the current system
     float wimg[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};  // image virial of the current unit
     long long wv = 0;  // lane k < 6: fixed-point image virial component k of the current system
-    bool ovf = false;  // a j-force sum out of the fixed-point range
+    bool ovf = false;  // a force sum out of the fixed-point range
     int u = 0;
     if (lane == 0) u = atomicAdd(A.work, 1);
     u = __shfl_sync(kFull, u, 0);
     while (u < n_units) {
         int u_next = 0;
         if (lane == 0) u_next = atomicAdd(A.work, 1);  // claimed now, used after this unit
-        const int I = u / parts, part = u - I * parts;
-        const int sys_id = __ldg(A.clus_sys + I);
-        if (sys_id != cur_sys) {
-            if (!DEBUG && cur_sys >= 0) {
-                long long v[kTaskVals];
-                tile_warp_sums<VIRIAL>(esum, wv, v);
-                if (lane == 0)
-                    for (int k = 0; k < (VIRIAL ? kTaskVals : 2); ++k)
-                        if (v[k]) atomicAdd((unsigned long long *)&A.sys_acc[cur_sys * kTaskVals + k], (unsigned long long)v[k]);
+        const Unit U = unit_of(A, u, parts);
+        if (U.e_begin < U.e_end) {
+            const int2 gr = __ldg(A.grp + U.g);
+            const int c0 = gr.x, ncl = gr.y;
+            const int sys_id = __ldg(A.clus_sys + c0);
+            if (sys_id != cur_sys) {
+                if (!DEBUG && cur_sys >= 0) {
+                    long long v[kTaskVals];
+                    tile_warp_sums<VIRIAL>(esum, wv, v);
+                    if (lane == 0)
+                        for (int k = 0; k < (VIRIAL ? kTaskVals : 2); ++k)
+                            if (v[k]) atomicAdd((unsigned long long *)&A.sys_acc[cur_sys * kTaskVals + k], (unsigned long long)v[k]);
+                }
+                cur_sys = sys_id;
+                Lx = A.sys[sys_id].L[0];
+                Ly = A.sys[sys_id].L[1];
+                Lz = A.sys[sys_id].L[2];
             }
-            cur_sys = sys_id;
-            Lx = A.sys[sys_id].L[0];
-            Ly = A.sys[sys_id].L[1];
-            Lz = A.sys[sys_id].L[2];
-        }
-        const int nA = __ldg(A.list_n + I);
-        const int per = (nA + parts - 1) / parts;
-        const int e_begin = min(nA, part * per), e_end = min(nA, e_begin + per);
-        if (e_begin < e_end) {
-            const long long s0 = (long long)I * kCluster;
-            const TileI ia = load_tile_i(A, s0 + ih, T, DEBUG);
-            const TileI ib = load_tile_i(A, s0 + ih + 4, T, DEBUG);
-            for (int t = lane; t < kCluster * K; t += 32) spart[t] = __ldg(A.pslot + s0 * K + t);
+            // the group's atoms (padding slots and absent clusters far away)
+            for (int t = lane; t < kCluster * G; t += 32) {
+                const long long slot = (long long)c0 * kCluster + t;
+                float4 p = make_float4(kFarCoord, kFarCoord, kFarCoord, 0.0f);
+                int tr = 0, orig = -1;
+                if (t < kCluster * ncl) {
+                    p = __ldg(A.xyzq + slot);
+                    if (!is_real_coord(p.x)) p.x = p.y = p.z = kFarCoord;
+                    p.w *= A.P.ke;
+                    tr = __ldg(A.tslot + slot) * T;
+                    orig = DEBUG ? __ldg(A.perm + slot) : -1;
+                }
+                s_ix[t] = p;
+                s_it[t] = tr;
+                s_io[t] = orig;
+            }
+#pragma unroll
+            for (int c = 0; c < G; ++c) s_fi[c * 32 + lane] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             __syncwarp();
-            Acc acA = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, acB = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-            const uint32_t *row = A.list + (long long)I * A.cap;
-            uint32_t ents = lane < e_end - e_begin ? __ldg(row + e_begin + lane) : 0u;
+            float elj = 0.0f, ec = 0.0f;
+            const uint2 *row = A.glist + U.base;
             bool unit_img = false;  // the unit holds an image entry (warp uniform)
-            for (int e0 = e_begin; e0 < e_end; e0 += 32) {
-                const int ne = min(32, e_end - e0);
-                const uint32_t cur_ents = ents;
-                if (e0 + 32 < e_end)  // the next 32 entries, ahead of use
-                    ents = lane < e_end - e0 - 32 ? __ldg(row + e0 + 32 + lane) : 0u;
+            for (int e0 = U.e_begin; e0 < U.e_end; e0 += kBatch) {
+                const int ne = min(kBatch, U.e_end - e0);
+                const uint2 my = lane < ne ? __ldg(row + e0 + lane) : make_uint2(0u, 0u);
                 // stage the batch's j atoms: lane k copies the 8 coordinates
-                // and types of entry k (atom a at swz(k, a): conflict-free
-                // reads of one entry's 8 atoms)
+                // and types of entry k (atom a at swz(k, a))
                 if (lane < ne) {
-                    const long long jb = (long long)(cur_ents & kJMask) * kCluster;
+                    const long long jbase = (long long)(my.x & kJMask) * kCluster;
 #pragma unroll
                     for (int a = 0; a < kCluster; ++a) {
-                        cp_async16(sjp + swz(lane, a), A.xyzq + jb + a);
-                        cp_async4(sjt + swz(lane, a), A.tslot + jb + a);
+                        cp_async16(sjp + swz(lane, a), A.xyzq + jbase + a);
+                        cp_async4(sjt + swz(lane, a), A.tslot + jbase + a);
                     }
                 }
                 cp_async_wait_all();
                 __syncwarp();
-                // the batch's plain entries first (no image code, no partner
-                // flag, not I itself: one code path without a dispatch), then
-                // the others
-                const bool my_img = ((cur_ents >> kShiftBit) & 0x3Fu) != 0u;
-                const bool my_spc = (cur_ents & kExclFlag) != 0u || ((int)(cur_ents & kJMask) == I && !my_img);
-                const unsigned in_batch = lane < ne;
+                // the batch's plain entries first (no image code, no masks:
+                // one code path without a dispatch), then the others
+                const bool my_img = ((my.x >> kShiftBit) & 0x3Fu) != 0u;
+                const bool my_spc = (my.x & kExclFlag) != 0u;
+                const bool in_batch = lane < ne;
                 unsigned plain = __ballot_sync(kFull, in_batch && !my_img && !my_spc);
                 unsigned other = __ballot_sync(kFull, in_batch) & ~plain;
                 unit_img = unit_img || __ballot_sync(kFull, in_batch && my_img) != 0u;
                 while (plain) {
                     const int k = __ffs(plain) - 1;
                     plain &= plain - 1u;
-                    const uint32_t ent = __shfl_sync(kFull, cur_ents, k);
-                    tile_entry<RAD, VIRIAL, DEBUG, false, false>(A, lj, spart, I, ent, sjp[swz(k, jj)],
-                                                                sjt[swz(k, jj)], ia, ib, jj, ih, Lx, Ly, Lz, acA, acB,
-                                                                wimg, ovf);
+                    const uint2 ent = make_uint2(__shfl_sync(kFull, my.x, k), __shfl_sync(kFull, my.y, k));
+                    tile_entry<G, RAD, VIRIAL, DEBUG, false, false>(
+                        A, lj, s_ix, s_it, s_io, s_fi, ent, sjp[swz(k, jb)], sjp[swz(k, jb + 4)], sjt[swz(k, jb)],
+                        sjt[swz(k, jb + 4)], ia, jb, lane, Lx, Ly, Lz, elj, ec, wimg, ovf);
                 }
                 while (other) {
                     const int k = __ffs(other) - 1;
                     other &= other - 1u;
-                    const uint32_t ent = __shfl_sync(kFull, cur_ents, k);
-                    const float4 pj = sjp[swz(k, jj)];
-                    const int tj = sjt[swz(k, jj)];
-                    const bool img = ((ent >> kShiftBit) & 0x3Fu) != 0u;
-                    const bool special = (ent & kExclFlag) != 0u || ((int)(ent & kJMask) == I && !img);
+                    const uint2 ent = make_uint2(__shfl_sync(kFull, my.x, k), __shfl_sync(kFull, my.y, k));
+                    const float4 pjA = sjp[swz(k, jb)], pjB = sjp[swz(k, jb + 4)];
+                    const int tjA = sjt[swz(k, jb)], tjB = sjt[swz(k, jb + 4)];
+                    const bool img = ((ent.x >> kShiftBit) & 0x3Fu) != 0u;
+                    const bool special = (ent.x & kExclFlag) != 0u;
                     if (img) {
                         if (special)
-                            tile_entry<RAD, VIRIAL, DEBUG, true, true>(A, lj, spart, I, ent, pj, tj, ia, ib, jj, ih,
-                                                                      Lx, Ly, Lz, acA, acB, wimg, ovf);
+                            tile_entry<G, RAD, VIRIAL, DEBUG, true, true>(A, lj, s_ix, s_it, s_io, s_fi, ent, pjA, pjB,
+                                                                         tjA, tjB, ia, jb, lane, Lx, Ly, Lz, elj, ec,
+                                                                         wimg, ovf);
                         else
-                            tile_entry<RAD, VIRIAL, DEBUG, false, true>(A, lj, spart, I, ent, pj, tj, ia, ib, jj, ih,
-                                                                       Lx, Ly, Lz, acA, acB, wimg, ovf);
+                            tile_entry<G, RAD, VIRIAL, DEBUG, false, true>(A, lj, s_ix, s_it, s_io, s_fi, ent, pjA,
+                                                                          pjB, tjA, tjB, ia, jb, lane, Lx, Ly, Lz, elj,
+                                                                          ec, wimg, ovf);
                     } else {
-                        tile_entry<RAD, VIRIAL, DEBUG, true, false>(A, lj, spart, I, ent, pj, tj, ia, ib, jj, ih, Lx,
-                                                                   Ly, Lz, acA, acB, wimg, ovf);
+                        tile_entry<G, RAD, VIRIAL, DEBUG, true, false>(A, lj, s_ix, s_it, s_io, s_fi, ent, pjA, pjB,
+                                                                      tjA, tjB, ia, jb, lane, Lx, Ly, Lz, elj, ec, wimg,
+                                                                      ovf);
                     }
                 }
                 __syncwarp();  // the staging buffer is rewritten by the next batch
             }
-            // force on the i atoms: the 8 lanes of each atom summed in FP32
-            // (a fixed butterfly: every lane ends with the same bits), then
-            // lanes jj < 3 add atom ih, jj = 3..5 atom ih + 4 in fixed point
-            float v[6] = {acA.fx, acA.fy, acA.fz, acB.fx, acB.fy, acB.fz};
+            // force on the group's atoms: each lane's partials summed over the
+            // 4 lanes of the same atom (jb) in FP32 (a fixed butterfly: every
+            // lane ends with the same bits), then lane jb adds clusters c with
+            // c % 4 == jb in fixed point
 #pragma unroll
-            for (int o = 1; o < 8; o <<= 1)
+            for (int c = 0; c < G; ++c) {
+                float4 f = s_fi[c * 32 + lane];
 #pragma unroll
-                for (int c = 0; c < 6; ++c) v[c] = __fadd_rn(v[c], __shfl_xor_sync(kFull, v[c], o));
-            float mine = v[0];
-#pragma unroll
-            for (int c = 1; c < 6; ++c) mine = jj == c ? v[c] : mine;
-            const long long fi = tile_fixed(mine, ovf);
-            if (jj < 6 && fi != 0) {
-                const long long slot = s0 + ih + (jj < 3 ? 0 : 4);
-                atomicAdd((unsigned long long *)&A.facc[3 * slot + (jj < 3 ? jj : jj - 3)], (unsigned long long)fi);
+                for (int o = 8; o < 32; o <<= 1) {
+                    f.x = __fadd_rn(f.x, __shfl_xor_sync(kFull, f.x, o));
+                    f.y = __fadd_rn(f.y, __shfl_xor_sync(kFull, f.y, o));
+                    f.z = __fadd_rn(f.z, __shfl_xor_sync(kFull, f.z, o));
+                }
+                if ((c & 3) == jb && c < ncl) {
+                    const long long slot = (long long)c0 * kCluster + c * kCluster + ia;
+                    const long long fx = tile_fixed(f.x, ovf), fy = tile_fixed(f.y, ovf), fz = tile_fixed(f.z, ovf);
+                    if (fx) atomicAdd((unsigned long long *)&A.facc[3 * slot], (unsigned long long)fx);
+                    if (fy) atomicAdd((unsigned long long *)&A.facc[3 * slot + 1], (unsigned long long)fy);
+                    if (fz) atomicAdd((unsigned long long *)&A.facc[3 * slot + 2], (unsigned long long)fz);
+                }
             }
-            esum[0] += tile_fixed(acA.elj, ovf) + tile_fixed(acB.elj, ovf);
-            esum[1] += tile_fixed(acA.ec, ovf) + tile_fixed(acB.ec, ovf);
+            esum[0] += tile_fixed(elj, ovf);
+            esum[1] += tile_fixed(ec, ovf);
             if (VIRIAL && unit_img) tile_virial_unit(wimg, wv, lane);  // image entries only add to wimg
             if (__any_sync(kFull, ovf)) {
                 if (lane == 0) atomicOr(A.status, ST_OVERFLOW);
                 ovf = false;
             }
-            __syncwarp();  // spart is rewritten by the next unit
+            __syncwarp();  // the i atoms and partials are rewritten by the next unit
         }
         u = __shfl_sync(kFull, u_next, 0);
     }
@@ -657,101 +721,376 @@ __global__ void __launch_bounds__(kTileWarps * 32, ACENB_TILE_MIN_BLOCKS) k_forc
 }
 
 // ---------------------------------------------------------------------------
-// Adjoint kernel on cluster-pair tiles (k_adjoint): the forward
-// kernel's tiles, half-tile votes, work units and staging, with the pair
-// adjoint of eval_pair_adj.  The j-side terms of an entry (dL/dx_j, dL/dq_j)
-// are summed over the 4 lanes of each j atom and lane ih adds component ih
-// (x, y, z, q) to the fixed-point sums; the i-side terms stay in registers
-// for the unit; the type-pair gradients go to a block table in shared
-// memory (integer atomics) flushed at the end.
-constexpr int kAdjWarps = 4;             // warps per block of the adjoint tile kernel
+// Forward kernel for i-groups of one cluster (k_force1): the lists are the
+// same, each entry holds one tile (I, J).  Lane = jj + 8 ih holds j atom jj
+// of J and the i atoms ih and ih + 4 of I in registers, so every lane
+// computes two pairs of the 8 x 8 tile and the force on j is summed over only
+// 4 lanes; the i atoms' z-sorted lower half (pair A) and upper half (pair B)
+// are voted separately.  With one cluster per group the per-entry work is
+// per tile, but the i side needs no shared memory and the j-force sum is
+// short; which of this and the group kernel is faster depends on the system
+// (the autotuner measures it).
+constexpr int kBatch1 = 32;  // entries staged per batch (one per lane)
 
-// One instance serves every kind of entry (special and image entries as
-// uniform branches): the pair adjoint is long, and an instance per kind, as
-// in the forward kernel, overflowed the instruction cache (0.188 against
-// 0.168 ms per adjoint step).
-template <int RAD>
-__device__ __forceinline__ void tile_adj_entry(bool special, bool img, const ForceArgs &A, const AdjTables &tab,
-                                               const int *__restrict__ spart, int I, uint32_t ent, float4 pj, int tj,
-                                               float4 gj, const TileI &ia, const TileI &ib, float4 gia, float4 gib,
-                                               float gE_lj, float gE_c, int jj, int ih, float Lx, float Ly, float Lz,
-                                               AccAdj &acA, AccAdj &acB, bool &ovf)
+struct TileI {
+    float x, y, z, q;
+    int trow;
+    int orig;  // caller index (pair export)
+};
+
+__device__ __forceinline__ TileI load_tile_i(const ForceArgs &A, long long slot, int T, bool debug)
 {
-    const int J = (int)(ent & kJMask);
-    const uint32_t code = img ? (ent >> kShiftBit) & 0x3Fu : 0u;
-    if (img) {
+    float4 p = __ldg(A.xyzq + slot);
+    if (!is_real_coord(p.x)) p.x = p.y = p.z = kFarCoord;
+    TileI t;
+    t.x = p.x;
+    t.y = p.y;
+    t.z = p.z;
+    t.q = p.w * A.P.ke;
+    t.trow = __ldg(A.tslot + slot) * T;
+    t.orig = debug ? __ldg(A.perm + slot) : -1;
+    return t;
+}
+
+// Membership of one pair: the i atom at its image for the entry's shift code
+// (IMG: x_i - L on axes with code 2; the j side was shifted by the caller),
+// d = x_j - x_i and the FP32 predicate r2 < rc2.
+template <bool IMG>
+__device__ __forceinline__ bool tile1_member(const ForceArgs &A, const TileI &ti, uint32_t code, float4 pj, float Lx,
+                                             float Ly, float Lz, float &dx, float &dy, float &dz, float &r2)
+{
+    float ax = ti.x, ay = ti.y, az = ti.z;
+    if (IMG) {
+        if ((code & 3u) == 2u) ax = __fsub_rn(ax, Lx);
+        if (((code >> 2) & 3u) == 2u) ay = __fsub_rn(ay, Ly);
+        if ((code >> 4) == 2u) az = __fsub_rn(az, Lz);
+    }
+    r2 = disp_r2(pj.x, pj.y, pj.z, ax, ay, az, dx, dy, dz);
+    return r2 < A.P.rc2;
+}
+
+template <int RAD, bool VIRIAL, bool DEBUG, bool SPECIAL, bool IMG>
+__device__ __forceinline__ void tile1_entry(const ForceArgs &A, const float4 *__restrict__ lj, uint2 ent, float4 pj,
+                                            int tj, const TileI &ia, const TileI &ib, int jj, int ih, float Lx,
+                                            float Ly, float Lz, Acc &acA, Acc &acB, float (&wimg)[6], bool &ovf)
+{
+    const int J = (int)(ent.x & kJMask);
+    const uint32_t code = IMG ? (ent.x >> kShiftBit) & 0x3Fu : 0u;
+    if (IMG) {  // j-side images (code 1): fl(x_j - L), as the other kernels stage them
         if ((code & 3u) == 1u) pj.x = __fsub_rn(pj.x, Lx);
         if (((code >> 2) & 3u) == 1u) pj.y = __fsub_rn(pj.y, Ly);
         if ((code >> 4) == 1u) pj.z = __fsub_rn(pj.z, Lz);
     }
     float dxA, dyA, dzA, r2A, dxB, dyB, dzB, r2B;
-    bool inA = img ? tile_member<true>(A, ia, code, pj, Lx, Ly, Lz, dxA, dyA, dzA, r2A)
-                   : tile_member<false>(A, ia, code, pj, Lx, Ly, Lz, dxA, dyA, dzA, r2A);
-    bool inB = img ? tile_member<true>(A, ib, code, pj, Lx, Ly, Lz, dxB, dyB, dzB, r2B)
-                   : tile_member<false>(A, ib, code, pj, Lx, Ly, Lz, dxB, dyB, dzB, r2B);
+    bool inA = tile1_member<IMG>(A, ia, code, pj, Lx, Ly, Lz, dxA, dyA, dzA, r2A);
+    bool inB = tile1_member<IMG>(A, ib, code, pj, Lx, Ly, Lz, dxB, dyB, dzB, r2B);
     bool s14A = false, s14B = false;
-    if (special) {
-        if (J == I && code == 0u) {
-            inA = inA && jj > ih;
-            inB = inB && jj > ih + 4;
-        }
-        if (ent & kExclFlag) {
-            const int jslot = J * kCluster + jj;
-            for (int m = 0; m < A.K; ++m) {
-                const int pa = spart[ih * A.K + m], pb = spart[(ih + 4) * A.K + m];
-                if (pa >= 0 && (pa >> 1) == jslot) {
-                    if (pa & 1) s14A = true;
-                    else inA = false;
-                }
-                if (pb >= 0 && (pb >> 1) == jslot) {
-                    if (pb & 1) s14B = true;
-                    else inB = false;
-                }
-            }
-        }
+    if (SPECIAL) {  // exclusion bitmask of the tile: bit 8 i + j
+        const ulonglong2 m = A.gmask[(long long)(ent.y >> kMaskSlotBit) * kMaxGroup];
+        const int bA = ih * kCluster + jj, bB = bA + 4 * kCluster;
+        inA = inA && !((m.x >> bA) & 1ull);
+        inB = inB && !((m.x >> bB) & 1ull);
+        s14A = (m.y >> bA) & 1ull;
+        s14B = (m.y >> bB) & 1ull;
     }
     const bool anyA = __any_sync(kFull, inA), anyB = __any_sync(kFull, inB);
     if (!anyA && !anyB) return;
-    float jx = 0.0f, jy = 0.0f, jz = 0.0f, jq = 0.0f;
+    const int jorig = DEBUG ? __ldg(A.perm + (long long)J * kCluster + jj) : -1;
+    float fjx = 0.0f, fjy = 0.0f, fjz = 0.0f;
     if (anyA) {
-        float a, b, c, d, ds, de;
-        eval_pair_adj<RAD == 1>(A.P, tab, ia.trow, ia.q, gia.x, gia.y, gia.z, gE_lj, gE_c, inA, dxA, dyA, dzA,
-                                inA ? r2A : 1.0f, pj.w, tj, gj, s14A, A.status, acA, a, b, c, d, ds, de);
-        add_type_grads(tab, inA ? ia.trow + tj : -1, ds, de, A.status);
-        jx = a;
-        jy = b;
-        jz = c;
-        jq = d;
+        if (DEBUG && inA) record_pair(A, ia.orig, jorig);
+        // only a special (flagged) tile can hold r2 = 0 (the self tile's diagonal, masked)
+        eval_pair<RAD, SPECIAL>(A.P, lj, A.rtab, ia.trow, ia.q, inA, dxA, dyA, dzA, SPECIAL ? (inA ? r2A : 1.0f) : r2A,
+                                pj.w, tj, s14A, acA, fjx, fjy, fjz);
     }
     if (anyB) {
-        float a, b, c, d, ds, de;
-        eval_pair_adj<RAD == 1>(A.P, tab, ib.trow, ib.q, gib.x, gib.y, gib.z, gE_lj, gE_c, inB, dxB, dyB, dzB,
-                                inB ? r2B : 1.0f, pj.w, tj, gj, s14B, A.status, acB, a, b, c, d, ds, de);
-        add_type_grads(tab, inB ? ib.trow + tj : -1, ds, de, A.status);
-        jx = __fadd_rn(jx, a);
-        jy = __fadd_rn(jy, b);
-        jz = __fadd_rn(jz, c);
-        jq = __fadd_rn(jq, d);
+        if (DEBUG && inB) record_pair(A, ib.orig, jorig);
+        eval_pair<RAD, SPECIAL>(A.P, lj, A.rtab, ib.trow, ib.q, inB, dxB, dyB, dzB, SPECIAL ? (inB ? r2B : 1.0f) : r2B,
+                                pj.w, tj, s14B, acB, fjx, fjy, fjz);
     }
+    // the force on j atom jj: sum over its 4 lanes, then lanes ih = 0, 1, 2
+    // add the x, y, z components
 #pragma unroll
     for (int o = 8; o < 32; o <<= 1) {
-        jx = __fadd_rn(jx, __shfl_xor_sync(kFull, jx, o));
-        jy = __fadd_rn(jy, __shfl_xor_sync(kFull, jy, o));
-        jz = __fadd_rn(jz, __shfl_xor_sync(kFull, jz, o));
-        jq = __fadd_rn(jq, __shfl_xor_sync(kFull, jq, o));
+        fjx = __fadd_rn(fjx, __shfl_xor_sync(kFull, fjx, o));
+        fjy = __fadd_rn(fjy, __shfl_xor_sync(kFull, fjy, o));
+        fjz = __fadd_rn(fjz, __shfl_xor_sync(kFull, fjz, o));
     }
-    const float gc = ih == 0 ? jx : (ih == 1 ? jy : (ih == 2 ? jz : jq));
-    atomicAdd((unsigned long long *)&A.gacc[32ll * J + 4 * jj + ih], (unsigned long long)tile_fixed(gc, ovf));
+    const float fc = ih == 0 ? fjx : (ih == 1 ? fjy : fjz);
+    const long long fv = tile_fixed(fc, ovf);  // every lane (lane ih = 3 holds z again): no branch
+    if (ih < 3 && fv != 0) atomicAdd((unsigned long long *)&A.facc[24ll * J + 3 * jj + ih], (unsigned long long)fv);
+    if (VIRIAL && IMG && ih == 0) {
+        const uint32_t cx = code & 3u, cy = (code >> 2) & 3u, cz = code >> 4;
+        const float sx = cx == 1u ? -Lx : (cx == 2u ? Lx : 0.0f);
+        const float sy = cy == 1u ? -Ly : (cy == 2u ? Ly : 0.0f);
+        const float sz = cz == 1u ? -Lz : (cz == 2u ? Lz : 0.0f);
+        wimg[0] = __fmaf_rn(sx, fjx, wimg[0]);
+        wimg[1] = __fmaf_rn(sy, fjy, wimg[1]);
+        wimg[2] = __fmaf_rn(sz, fjz, wimg[2]);
+        wimg[3] = __fmaf_rn(sx, fjy, wimg[3]);
+        wimg[4] = __fmaf_rn(sx, fjz, wimg[4]);
+        wimg[5] = __fmaf_rn(sy, fjz, wimg[5]);
+    }
 }
 
-template <int RAD>
+__host__ __device__ inline size_t tile1_warp_bytes() { return (size_t)kBatch1 * kCluster * (16 + 4); }
+
+template <int RAD, bool VIRIAL, bool DEBUG>
+__global__ void __launch_bounds__(kTileWarps * 32, ACENB_TILE_MIN_BLOCKS) k_force1(ForceArgs A, int parts)
+{
+    pdl_entry();
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long s_val[kTileWarps][kTaskVals];
+    __shared__ int s_sys[kTileWarps];
+    const int T = A.P.n_types;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, jj = lane & 7, ih = lane >> 3;
+    float4 *lj = reinterpret_cast<float4 *>(smem);  // (A, B, 12 A, 6 B) per type pair
+    float4 *sjp = reinterpret_cast<float4 *>(smem + lj_table_bytes(T) + (size_t)w * tile1_warp_bytes());
+    int *sjt = reinterpret_cast<int *>(sjp + kBatch1 * kCluster);
+    for (int k = threadIdx.x; k < T * T; k += blockDim.x) {
+        const float4 ab = A.lj_tab[k];
+        lj[k] = make_float4(ab.x, ab.y, 12.0f * ab.x, 6.0f * ab.y);
+        reinterpret_cast<float2 *>(lj + T * T)[k] = make_float2(ab.z, ab.w);
+    }
+    __syncthreads();
+    const int n_units = A.counts[4] * kListSegs * parts;
+    int cur_sys = -1;
+    float Lx = 0.0f, Ly = 0.0f, Lz = 0.0f;
+    long long esum[2] = {0, 0};
+    float wimg[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    long long wv = 0;
+    bool ovf = false;
+    int u = 0;
+    if (lane == 0) u = atomicAdd(A.work, 1);
+    u = __shfl_sync(kFull, u, 0);
+    while (u < n_units) {
+        int u_next = 0;
+        if (lane == 0) u_next = atomicAdd(A.work, 1);
+        const Unit U = unit_of(A, u, parts);
+        if (U.e_begin < U.e_end) {
+            const int I = __ldg(A.grp + U.g).x;
+            const int sys_id = __ldg(A.clus_sys + I);
+            if (sys_id != cur_sys) {
+                if (!DEBUG && cur_sys >= 0) {
+                    long long v[kTaskVals];
+                    tile_warp_sums<VIRIAL>(esum, wv, v);
+                    if (lane == 0)
+                        for (int k = 0; k < (VIRIAL ? kTaskVals : 2); ++k)
+                            if (v[k]) atomicAdd((unsigned long long *)&A.sys_acc[cur_sys * kTaskVals + k], (unsigned long long)v[k]);
+                }
+                cur_sys = sys_id;
+                Lx = A.sys[sys_id].L[0];
+                Ly = A.sys[sys_id].L[1];
+                Lz = A.sys[sys_id].L[2];
+            }
+            const long long s0 = (long long)I * kCluster;
+            const TileI ia = load_tile_i(A, s0 + ih, T, DEBUG);
+            const TileI ib = load_tile_i(A, s0 + ih + 4, T, DEBUG);
+            Acc acA = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, acB = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+            const uint2 *row = A.glist + U.base;
+            bool unit_img = false;
+            for (int e0 = U.e_begin; e0 < U.e_end; e0 += kBatch1) {
+                const int ne = min(kBatch1, U.e_end - e0);
+                const uint2 my = lane < ne ? __ldg(row + e0 + lane) : make_uint2(0u, 0u);
+                if (lane < ne) {
+                    const long long jbase = (long long)(my.x & kJMask) * kCluster;
+#pragma unroll
+                    for (int a = 0; a < kCluster; ++a) {
+                        cp_async16(sjp + swz(lane, a), A.xyzq + jbase + a);
+                        cp_async4(sjt + swz(lane, a), A.tslot + jbase + a);
+                    }
+                }
+                cp_async_wait_all();
+                __syncwarp();
+                const bool my_img = ((my.x >> kShiftBit) & 0x3Fu) != 0u;
+                const bool my_spc = (my.x & kExclFlag) != 0u;
+                const bool in_batch = lane < ne;
+                unsigned plain = __ballot_sync(kFull, in_batch && !my_img && !my_spc);
+                unsigned other = __ballot_sync(kFull, in_batch) & ~plain;
+                unit_img = unit_img || __ballot_sync(kFull, in_batch && my_img) != 0u;
+                while (plain) {
+                    const int k = __ffs(plain) - 1;
+                    plain &= plain - 1u;
+                    const uint2 ent = make_uint2(__shfl_sync(kFull, my.x, k), __shfl_sync(kFull, my.y, k));
+                    tile1_entry<RAD, VIRIAL, DEBUG, false, false>(A, lj, ent, sjp[swz(k, jj)], sjt[swz(k, jj)], ia, ib,
+                                                                  jj, ih, Lx, Ly, Lz, acA, acB, wimg, ovf);
+                }
+                while (other) {
+                    const int k = __ffs(other) - 1;
+                    other &= other - 1u;
+                    const uint2 ent = make_uint2(__shfl_sync(kFull, my.x, k), __shfl_sync(kFull, my.y, k));
+                    const float4 pj = sjp[swz(k, jj)];
+                    const int tj = sjt[swz(k, jj)];
+                    const bool img = ((ent.x >> kShiftBit) & 0x3Fu) != 0u;
+                    const bool special = (ent.x & kExclFlag) != 0u;
+                    if (img) {
+                        if (special)
+                            tile1_entry<RAD, VIRIAL, DEBUG, true, true>(A, lj, ent, pj, tj, ia, ib, jj, ih, Lx, Ly, Lz,
+                                                                        acA, acB, wimg, ovf);
+                        else
+                            tile1_entry<RAD, VIRIAL, DEBUG, false, true>(A, lj, ent, pj, tj, ia, ib, jj, ih, Lx, Ly,
+                                                                         Lz, acA, acB, wimg, ovf);
+                    } else {
+                        tile1_entry<RAD, VIRIAL, DEBUG, true, false>(A, lj, ent, pj, tj, ia, ib, jj, ih, Lx, Ly, Lz,
+                                                                     acA, acB, wimg, ovf);
+                    }
+                }
+                __syncwarp();  // the staging buffer is rewritten by the next batch
+            }
+            // force on the i atoms: the 8 lanes of each atom summed in FP32
+            // (a fixed butterfly), then lanes jj < 3 add atom ih, jj = 3..5
+            // atom ih + 4 in fixed point
+            float v[6] = {acA.fx, acA.fy, acA.fz, acB.fx, acB.fy, acB.fz};
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1)
+#pragma unroll
+                for (int c = 0; c < 6; ++c) v[c] = __fadd_rn(v[c], __shfl_xor_sync(kFull, v[c], o));
+            float mine = v[0];
+#pragma unroll
+            for (int c = 1; c < 6; ++c) mine = jj == c ? v[c] : mine;
+            const long long fi = tile_fixed(mine, ovf);
+            if (jj < 6 && fi != 0) {
+                const long long slot = s0 + ih + (jj < 3 ? 0 : 4);
+                atomicAdd((unsigned long long *)&A.facc[3 * slot + (jj < 3 ? jj : jj - 3)], (unsigned long long)fi);
+            }
+            esum[0] += tile_fixed(acA.elj, ovf) + tile_fixed(acB.elj, ovf);
+            esum[1] += tile_fixed(acA.ec, ovf) + tile_fixed(acB.ec, ovf);
+            if (VIRIAL && unit_img) tile_virial_unit(wimg, wv, lane);
+            if (__any_sync(kFull, ovf)) {
+                if (lane == 0) atomicOr(A.status, ST_OVERFLOW);
+                ovf = false;
+            }
+        }
+        u = __shfl_sync(kFull, u_next, 0);
+    }
+    if (DEBUG) return;
+    long long v[kTaskVals];
+    tile_warp_sums<VIRIAL>(esum, wv, v);
+    if (lane == 0) {
+        s_sys[w] = cur_sys;
+        for (int k = 0; k < kTaskVals; ++k) s_val[w][k] = k < (VIRIAL ? kTaskVals : 2) ? v[k] : 0;
+    }
+    __syncthreads();
+    if (threadIdx.x < (VIRIAL ? kTaskVals : 2)) {
+        const int k = threadIdx.x;
+        const int nw = blockDim.x >> 5;
+        int base = -1;
+        long long sum = 0;
+        for (int q = 0; q < nw; ++q) {
+            const int sq = s_sys[q];
+            if (sq < 0) continue;
+            if (base < 0) base = sq;
+            if (sq == base) sum += s_val[q][k];
+            else if (s_val[q][k]) atomicAdd((unsigned long long *)&A.sys_acc[sq * kTaskVals + k], (unsigned long long)s_val[q][k]);
+        }
+        if (base >= 0 && sum) atomicAdd((unsigned long long *)&A.sys_acc[base * kTaskVals + k], (unsigned long long)sum);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint kernel on i-group tiles (k_adjoint): the forward kernel's units,
+// entries, tiles, half-tile votes and staging, with the pair adjoint of
+// eval_pair_adj.  Per entry the j-side terms (dL/dx_j, dL/dq_j) of all its
+// tiles are summed in registers, then over the 8 lanes of each j atom, and
+// lane ia adds component ia % 4 of atom jb (ia < 4) or jb + 4 to the
+// fixed-point sums; the i-side terms accumulate per lane and cluster in
+// shared memory until the unit is done; the type-pair gradients go to a
+// block table in shared memory (integer atomics) flushed at the end.  One
+// inlined instance of the entry code serves every entry kind (the pair
+// adjoint is long; an instance per kind overflowed the instruction cache).
+constexpr int kAdjWarps = 4;             // warps per block of the adjoint tile kernel
+
+__host__ __device__ inline size_t adj_warp_bytes(int G)
+{
+    return (size_t)kCluster * G * (16 + 16 + 4) + (size_t)G * 32 * 16 + (size_t)kBatch * kCluster * (16 + 16 + 4);
+}
+
+template <int G, int RAD>
+__device__ __forceinline__ void adj_entry(const ForceArgs &A, const AdjTables &tab, const float4 *__restrict__ s_ix,
+                                          const int *__restrict__ s_it, const float4 *__restrict__ s_ig,
+                                          float4 *__restrict__ s_ai, uint2 ent, float4 pjA, float4 pjB, float4 gjA,
+                                          float4 gjB, int tjA, int tjB, float gE_lj, float gE_c, int ia, int jb,
+                                          int lane, float Lx, float Ly, float Lz, bool &ovf)
+{
+    const int J = (int)(ent.x & kJMask);
+    const uint32_t code = (ent.x >> kShiftBit) & 0x3Fu;
+    const bool img = code != 0u, special = (ent.x & kExclFlag) != 0u;
+    if (img) {
+        if ((code & 3u) == 1u) { pjA.x = __fsub_rn(pjA.x, Lx); pjB.x = __fsub_rn(pjB.x, Lx); }
+        if (((code >> 2) & 3u) == 1u) { pjA.y = __fsub_rn(pjA.y, Ly); pjB.y = __fsub_rn(pjB.y, Ly); }
+        if ((code >> 4) == 1u) { pjA.z = __fsub_rn(pjA.z, Lz); pjB.z = __fsub_rn(pjB.z, Lz); }
+    }
+    const ulonglong2 *rec = special ? A.gmask + (long long)(ent.y >> kMaskSlotBit) * kMaxGroup : nullptr;
+    float jA[4] = {0.0f, 0.0f, 0.0f, 0.0f}, jB[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (unsigned cm = ent.y & 0xFFu; cm; cm &= cm - 1u) {
+        const int c = __ffs(cm) - 1;
+        const int ii = c * kCluster + ia;
+        float4 pi = s_ix[ii];
+        if (img) {
+            if ((code & 3u) == 2u) pi.x = __fsub_rn(pi.x, Lx);
+            if (((code >> 2) & 3u) == 2u) pi.y = __fsub_rn(pi.y, Ly);
+            if ((code >> 4) == 2u) pi.z = __fsub_rn(pi.z, Lz);
+        }
+        float dxA, dyA, dzA, dxB, dyB, dzB;
+        const float r2A = disp_r2(pjA.x, pjA.y, pjA.z, pi.x, pi.y, pi.z, dxA, dyA, dzA);
+        const float r2B = disp_r2(pjB.x, pjB.y, pjB.z, pi.x, pi.y, pi.z, dxB, dyB, dzB);
+        bool inA = r2A < A.P.rc2, inB = r2B < A.P.rc2;
+        bool s14A = false, s14B = false;
+        if (special) tile_mask_bits(rec[c], ia, jb, inA, inB, s14A, s14B);
+        const bool anyA = __any_sync(kFull, inA), anyB = __any_sync(kFull, inB);
+        if (!anyA && !anyB) continue;
+        const int trow = s_it[ii];
+        const float4 gi = s_ig[ii];
+        float4 ai = s_ai[c * 32 + lane];
+        AccAdj acc = {ai.x, ai.y, ai.z, ai.w};
+        if (anyA) {
+            float a, b, cc, d, ds, de;
+            eval_pair_adj<RAD == 1>(A.P, tab, trow, pi.w, gi.x, gi.y, gi.z, gE_lj, gE_c, inA, dxA, dyA, dzA,
+                                    inA ? r2A : 1.0f, pjA.w, tjA, gjA, s14A, A.status, acc, a, b, cc, d, ds, de);
+            add_type_grads(tab, inA ? trow + tjA : -1, ds, de, A.status);
+            jA[0] = __fadd_rn(jA[0], a);
+            jA[1] = __fadd_rn(jA[1], b);
+            jA[2] = __fadd_rn(jA[2], cc);
+            jA[3] = __fadd_rn(jA[3], d);
+        }
+        if (anyB) {
+            float a, b, cc, d, ds, de;
+            eval_pair_adj<RAD == 1>(A.P, tab, trow, pi.w, gi.x, gi.y, gi.z, gE_lj, gE_c, inB, dxB, dyB, dzB,
+                                    inB ? r2B : 1.0f, pjB.w, tjB, gjB, s14B, A.status, acc, a, b, cc, d, ds, de);
+            add_type_grads(tab, inB ? trow + tjB : -1, ds, de, A.status);
+            jB[0] = __fadd_rn(jB[0], a);
+            jB[1] = __fadd_rn(jB[1], b);
+            jB[2] = __fadd_rn(jB[2], cc);
+            jB[3] = __fadd_rn(jB[3], d);
+        }
+        s_ai[c * 32 + lane] = make_float4(acc.dx, acc.dy, acc.dz, acc.dq);
+    }
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            jA[k] = __fadd_rn(jA[k], __shfl_xor_sync(kFull, jA[k], o));
+            jB[k] = __fadd_rn(jB[k], __shfl_xor_sync(kFull, jB[k], o));
+        }
+    float gv = jA[0];
+#pragma unroll
+    for (int k = 1; k < 4; ++k) gv = ia == k ? jA[k] : gv;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) gv = ia == 4 + k ? jB[k] : gv;
+    const long long gx = tile_fixed(gv, ovf);
+    if (gx != 0) {
+        const int j = ia < 4 ? jb : jb + 4;
+        atomicAdd((unsigned long long *)&A.gacc[32ll * J + 4 * j + (ia & 3)], (unsigned long long)gx);
+    }
+}
+
+template <int G, int RAD>
 __global__ void __launch_bounds__(kAdjWarps * 32) k_adjoint(ForceArgs A, int parts)
 {
     pdl_entry();
     extern __shared__ __align__(16) unsigned char smem[];
     const int T = A.P.n_types;
-    const int K = A.K;
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, jj = lane & 7, ih = lane >> 3;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, ia = lane & 7, jb = lane >> 3;
     size_t off = 0;
     unsigned long long *tacc = reinterpret_cast<unsigned long long *>(smem + off);
     off += (size_t)T * T * 16;
@@ -759,22 +1098,23 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_adjoint(ForceArgs A, int par
     off += (size_t)T * T * 16;
     float2 *lj = reinterpret_cast<float2 *>(smem + off);
     off += align16((size_t)T * T * 8);
-    int *spart = reinterpret_cast<int *>(smem + off) + w * kCluster * K;
-    off += align16((size_t)kAdjWarps * kCluster * K * 4);
-    float4 *sjp = reinterpret_cast<float4 *>(smem + off) + w * 32 * kCluster;  // staged j coordinates + charges
-    off += (size_t)kAdjWarps * 32 * kCluster * 16;
-    float4 *sjg = reinterpret_cast<float4 *>(smem + off) + w * 32 * kCluster;  // staged j dL/dF
-    off += (size_t)kAdjWarps * 32 * kCluster * 16;
-    int *sjt = reinterpret_cast<int *>(smem + off) + w * 32 * kCluster;  // staged j types
+    unsigned char *wbase = smem + off + (size_t)w * adj_warp_bytes(G);
+    float4 *s_ix = reinterpret_cast<float4 *>(wbase);    // [8 G] x, y, z, ke q
+    float4 *s_ig = s_ix + kCluster * G;                    // [8 G] dL/dF of the i atoms
+    float4 *s_ai = s_ig + kCluster * G;                    // [G * 32] i-side partials
+    float4 *sjp = s_ai + G * 32;                           // [kBatch * 8]
+    float4 *sjg = sjp + kBatch * kCluster;                 // [kBatch * 8]
+    int *s_it = reinterpret_cast<int *>(sjg + kBatch * kCluster);  // [8 G]
+    int *sjt = s_it + kCluster * G;                        // [kBatch * 8]
     for (int k = threadIdx.x; k < T * T; k += blockDim.x) {
-        lj[k] = A.lj_tab[k];
+        lj[k] = make_float2(A.lj_tab[k].x, A.lj_tab[k].y);
         ljd[k] = A.lj_d[k];
         tacc[2 * k] = 0ull;
         tacc[2 * k + 1] = 0ull;
     }
     __syncthreads();
     const AdjTables tab{lj, ljd, tacc};
-    const int n_units = A.counts[1] * parts;
+    const int n_units = A.counts[4] * kListSegs * parts;
     int cur_sys = -1;
     float Lx = 0.0f, Ly = 0.0f, Lz = 0.0f, gE_lj = 0.0f, gE_c = 0.0f;
     bool ovf = false;
@@ -784,77 +1124,88 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_adjoint(ForceArgs A, int par
     while (u < n_units) {
         int u_next = 0;
         if (lane == 0) u_next = atomicAdd(A.work, 1);
-        const int I = u / parts, part = u - I * parts;
-        const int sys_id = __ldg(A.clus_sys + I);
-        if (sys_id != cur_sys) {
-            cur_sys = sys_id;
-            Lx = A.sys[sys_id].L[0];
-            Ly = A.sys[sys_id].L[1];
-            Lz = A.sys[sys_id].L[2];
-            gE_lj = A.dLdE ? (float)A.dLdE[2 * sys_id] : 0.0f;
-            gE_c = A.dLdE ? (float)A.dLdE[2 * sys_id + 1] : 0.0f;
-        }
-        const int nA = __ldg(A.list_n + I);
-        const int per = (nA + parts - 1) / parts;
-        const int e_begin = min(nA, part * per), e_end = min(nA, e_begin + per);
-        if (e_begin < e_end) {
-            const long long s0 = (long long)I * kCluster;
-            const TileI ia = load_tile_i(A, s0 + ih, T, false);
-            const TileI ib = load_tile_i(A, s0 + ih + 4, T, false);
-            const float4 gia = __ldg(A.gslot + s0 + ih), gib = __ldg(A.gslot + s0 + ih + 4);
-            for (int t = lane; t < kCluster * K; t += 32) spart[t] = __ldg(A.pslot + s0 * K + t);
+        const Unit U = unit_of(A, u, parts);
+        if (U.e_begin < U.e_end) {
+            const int2 gr = __ldg(A.grp + U.g);
+            const int c0 = gr.x, ncl = gr.y;
+            const int sys_id = __ldg(A.clus_sys + c0);
+            if (sys_id != cur_sys) {
+                cur_sys = sys_id;
+                Lx = A.sys[sys_id].L[0];
+                Ly = A.sys[sys_id].L[1];
+                Lz = A.sys[sys_id].L[2];
+                gE_lj = A.dLdE ? (float)A.dLdE[2 * sys_id] : 0.0f;
+                gE_c = A.dLdE ? (float)A.dLdE[2 * sys_id + 1] : 0.0f;
+            }
+            for (int t = lane; t < kCluster * G; t += 32) {
+                const long long slot = (long long)c0 * kCluster + t;
+                float4 p = make_float4(kFarCoord, kFarCoord, kFarCoord, 0.0f);
+                float4 gi = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                int tr = 0;
+                if (t < kCluster * ncl) {
+                    p = __ldg(A.xyzq + slot);
+                    if (!is_real_coord(p.x)) p.x = p.y = p.z = kFarCoord;
+                    p.w *= A.P.ke;
+                    gi = __ldg(A.gslot + slot);
+                    tr = __ldg(A.tslot + slot) * T;
+                }
+                s_ix[t] = p;
+                s_ig[t] = gi;
+                s_it[t] = tr;
+            }
+#pragma unroll
+            for (int c = 0; c < G; ++c) s_ai[c * 32 + lane] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             __syncwarp();
-            AccAdj acA = {0.0f, 0.0f, 0.0f, 0.0f}, acB = {0.0f, 0.0f, 0.0f, 0.0f};
-            const uint32_t *row = A.list + (long long)I * A.cap;
-            uint32_t ents = lane < e_end - e_begin ? __ldg(row + e_begin + lane) : 0u;
-            for (int e0 = e_begin; e0 < e_end; e0 += 32) {
-                const int ne = min(32, e_end - e0);
-                const uint32_t cur_ents = ents;
-                if (e0 + 32 < e_end) ents = lane < e_end - e0 - 32 ? __ldg(row + e0 + 32 + lane) : 0u;
+            const uint2 *row = A.glist + U.base;
+            for (int e0 = U.e_begin; e0 < U.e_end; e0 += kBatch) {
+                const int ne = min(kBatch, U.e_end - e0);
+                const uint2 my = lane < ne ? __ldg(row + e0 + lane) : make_uint2(0u, 0u);
                 if (lane < ne) {
-                    const long long jb = (long long)(cur_ents & kJMask) * kCluster;
+                    const long long jbase = (long long)(my.x & kJMask) * kCluster;
 #pragma unroll
                     for (int a = 0; a < kCluster; ++a) {
-                        cp_async16(sjp + swz(lane, a), A.xyzq + jb + a);
-                        cp_async16(sjg + swz(lane, a), A.gslot + jb + a);
-                        cp_async4(sjt + swz(lane, a), A.tslot + jb + a);
+                        cp_async16(sjp + swz(lane, a), A.xyzq + jbase + a);
+                        cp_async16(sjg + swz(lane, a), A.gslot + jbase + a);
+                        cp_async4(sjt + swz(lane, a), A.tslot + jbase + a);
                     }
                 }
                 cp_async_wait_all();
                 __syncwarp();
                 for (int k = 0; k < ne; ++k) {
-                    const uint32_t ent = __shfl_sync(kFull, cur_ents, k);
-                    const float4 pj = sjp[swz(k, jj)];
-                    const float4 gj = sjg[swz(k, jj)];
-                    const int tj = sjt[swz(k, jj)];
-                    const bool img = ((ent >> kShiftBit) & 0x3Fu) != 0u;
-                    const bool special = (ent & kExclFlag) != 0u || ((int)(ent & kJMask) == I && !img);
-                    tile_adj_entry<RAD>(special, img, A, tab, spart, I, ent, pj, tj, gj, ia, ib, gia, gib, gE_lj, gE_c,
-                                        jj, ih, Lx, Ly, Lz, acA, acB, ovf);
+                    const uint2 ent = make_uint2(__shfl_sync(kFull, my.x, k), __shfl_sync(kFull, my.y, k));
+                    adj_entry<G, RAD>(A, tab, s_ix, s_it, s_ig, s_ai, ent, sjp[swz(k, jb)], sjp[swz(k, jb + 4)],
+                                      sjg[swz(k, jb)], sjg[swz(k, jb + 4)], sjt[swz(k, jb)], sjt[swz(k, jb + 4)],
+                                      gE_lj, gE_c, ia, jb, lane, Lx, Ly, Lz, ovf);
                 }
                 __syncwarp();  // the staging buffers are rewritten by the next batch
             }
-            // i-side terms: the 8 lanes of each atom summed in FP32 (fixed
-            // butterfly), then lane jj < 4 adds component jj of atom ih,
-            // jj >= 4 component jj - 4 of atom ih + 4, in fixed point
-            float v[8] = {acA.dx, acA.dy, acA.dz, acA.dq, acB.dx, acB.dy, acB.dz, acB.dq};
+            // i-side terms: the 4 lanes of each atom summed in FP32 (fixed
+            // butterfly), then lane jb adds clusters c with c % 4 == jb
 #pragma unroll
-            for (int o = 1; o < 8; o <<= 1)
+            for (int c = 0; c < G; ++c) {
+                float4 a = s_ai[c * 32 + lane];
 #pragma unroll
-                for (int c = 0; c < 8; ++c) v[c] = __fadd_rn(v[c], __shfl_xor_sync(kFull, v[c], o));
-            float vm = v[0];
-#pragma unroll
-            for (int c = 1; c < 8; ++c) vm = jj == c ? v[c] : vm;
-            const long long mine = tile_fixed(vm, ovf);
-            if (mine != 0) {
-                const long long slot = s0 + ih + (jj < 4 ? 0 : 4);
-                atomicAdd((unsigned long long *)&A.gacc[4 * slot + (jj & 3)], (unsigned long long)mine);
+                for (int o = 8; o < 32; o <<= 1) {
+                    a.x = __fadd_rn(a.x, __shfl_xor_sync(kFull, a.x, o));
+                    a.y = __fadd_rn(a.y, __shfl_xor_sync(kFull, a.y, o));
+                    a.z = __fadd_rn(a.z, __shfl_xor_sync(kFull, a.z, o));
+                    a.w = __fadd_rn(a.w, __shfl_xor_sync(kFull, a.w, o));
+                }
+                if ((c & 3) == jb && c < ncl) {
+                    const long long slot = (long long)c0 * kCluster + c * kCluster + ia;
+                    const long long v0 = tile_fixed(a.x, ovf), v1 = tile_fixed(a.y, ovf), v2 = tile_fixed(a.z, ovf),
+                                    v3 = tile_fixed(a.w, ovf);
+                    if (v0) atomicAdd((unsigned long long *)&A.gacc[4 * slot], (unsigned long long)v0);
+                    if (v1) atomicAdd((unsigned long long *)&A.gacc[4 * slot + 1], (unsigned long long)v1);
+                    if (v2) atomicAdd((unsigned long long *)&A.gacc[4 * slot + 2], (unsigned long long)v2);
+                    if (v3) atomicAdd((unsigned long long *)&A.gacc[4 * slot + 3], (unsigned long long)v3);
+                }
             }
             if (__any_sync(kFull, ovf)) {
                 if (lane == 0) atomicOr(A.status, ST_OVERFLOW);
                 ovf = false;
             }
-            __syncwarp();  // spart is rewritten by the next unit
+            __syncwarp();
         }
         u = __shfl_sync(kFull, u_next, 0);
     }
@@ -1069,28 +1420,46 @@ static void smem_optin_once(Kernel kernel, int device, int bytes, std::atomic<un
     if (bit) done.fetch_or(bit, std::memory_order_release);
 }
 
-size_t tile_smem_bytes(int T, int K)
-{
-    return (size_t)T * T * 16 + align16((size_t)kTileWarps * kCluster * K * 4) +
-           (size_t)kTileWarps * 32 * kCluster * (16 + 4);
-}
+size_t tile_smem_bytes(int T, int G) { return lj_table_bytes(T) + (size_t)kTileWarps * tile_warp_bytes(G); }
 
 // beside_pme: the PME chain, forked before the list kernel, runs on its side
 // stream during this kernel; the persistent grid then leaves one block slot
 // per SM free, so that the PME kernels run alongside instead of after it.
+template <int G, int RAD, bool VIRIAL, bool DEBUG>
+static void launch_force_g(nb_ctx *ctx, const ForceArgs &A, bool beside_pme)
+{
+    const size_t smem = tile_smem_bytes(A.P.n_types, G);
+    static std::atomic<unsigned long long> optin{0};
+    smem_optin_once(k_force<G, RAD, VIRIAL, DEBUG>, ctx->device, 200 * 1024, optin);
+    // persistent grid: never more blocks than can be resident at once
+    int resident = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_force<G, RAD, VIRIAL, DEBUG>, kTileWarps * 32, smem);
+    const int per_sm = std::max(1, std::min(ctx->tune.blocks_per_sm, resident) - (beside_pme ? 1 : 0));
+    const int parts = ctx->tune.list_split > 0 ? ctx->tune.list_split : kDefaultListSplit;
+    launch_pdl(k_force<G, RAD, VIRIAL, DEBUG>, dim3(ctx->num_sms * per_sm), dim3(kTileWarps * 32), smem,
+               ctx->stream, A, parts);
+}
+
+template <int RAD, bool VIRIAL, bool DEBUG>
+static void launch_force_1(nb_ctx *ctx, const ForceArgs &A, bool beside_pme)
+{
+    const size_t smem = lj_table_bytes(A.P.n_types) + (size_t)kTileWarps * tile1_warp_bytes();
+    static std::atomic<unsigned long long> optin{0};
+    smem_optin_once(k_force1<RAD, VIRIAL, DEBUG>, ctx->device, 200 * 1024, optin);
+    int resident = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_force1<RAD, VIRIAL, DEBUG>, kTileWarps * 32, smem);
+    const int per_sm = std::max(1, std::min(ctx->tune.blocks_per_sm, resident) - (beside_pme ? 1 : 0));
+    const int parts = ctx->tune.list_split > 0 ? ctx->tune.list_split : kDefaultListSplit;
+    launch_pdl(k_force1<RAD, VIRIAL, DEBUG>, dim3(ctx->num_sms * per_sm), dim3(kTileWarps * 32), smem, ctx->stream,
+               A, parts);
+}
+
 template <int RAD, bool VIRIAL, bool DEBUG>
 static void launch_force_t(nb_ctx *ctx, const ForceArgs &A, bool beside_pme)
 {
-    const size_t smem = tile_smem_bytes(A.P.n_types, A.K);
-    static std::atomic<unsigned long long> optin{0};
-    smem_optin_once(k_force<RAD, VIRIAL, DEBUG>, ctx->device, 200 * 1024, optin);
-    // persistent grid: never more blocks than can be resident at once
-    int resident = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_force<RAD, VIRIAL, DEBUG>, kTileWarps * 32, smem);
-    const int per_sm = std::max(1, std::min(ctx->tune.blocks_per_sm, resident) - (beside_pme ? 1 : 0));
-    const int parts = ctx->tune.list_split > 0 ? ctx->tune.list_split : kDefaultListSplit;
-    launch_pdl(k_force<RAD, VIRIAL, DEBUG>, dim3(ctx->num_sms * per_sm), dim3(kTileWarps * 32), smem,
-               ctx->stream, A, parts);
+    if (ctx->built_group == 1) launch_force_1<RAD, VIRIAL, DEBUG>(ctx, A, beside_pme);
+    else if (ctx->built_group == 4) launch_force_g<4, RAD, VIRIAL, DEBUG>(ctx, A, beside_pme);
+    else launch_force_g<8, RAD, VIRIAL, DEBUG>(ctx, A, beside_pme);
 }
 
 static ForceArgs make_args(nb_ctx *ctx)
@@ -1105,9 +1474,10 @@ static ForceArgs make_args(nb_ctx *ctx)
     A.tslot = d.tslot;
     A.perm = d.perm;
     A.clus_sys = d.clus_sys;
-    A.list = d.list;
-    A.list_n = d.list_n;
-    A.pslot = d.pslot;
+    A.grp = d.grp;
+    A.glist = d.glist;
+    A.glist_n = d.glist_n;
+    A.gmask = d.gmask;
     A.cap = ctx->list_cap;
     A.K = ctx->K;
     A.lj_tab = d.lj_tab;
@@ -1203,29 +1573,37 @@ cudaError_t launch_forces_packed(nb_ctx *ctx, float *d_F, double *d_energy, doub
     return cudaGetLastError();
 }
 
-size_t adjoint_smem_bytes(int T, int K)
+size_t adjoint_smem_bytes(int T, int G)
 {
-    return (size_t)T * T * 32 + align16((size_t)T * T * 8) + align16((size_t)kAdjWarps * kCluster * K * 4) +
-           (size_t)kAdjWarps * 32 * kCluster * (16 + 16 + 4);
+    return (size_t)T * T * 32 + align16((size_t)T * T * 8) + (size_t)kAdjWarps * adj_warp_bytes(G);
+}
+
+template <int G, int RAD>
+static void launch_adjoint_g(nb_ctx *ctx, const ForceArgs &A)
+{
+    const size_t smem = adjoint_smem_bytes(A.P.n_types, G);
+    static std::atomic<unsigned long long> optin{0};
+    smem_optin_once(k_adjoint<G, RAD>, ctx->device, 220 * 1024, optin);
+    int resident = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_adjoint<G, RAD>, kAdjWarps * 32, smem);
+    const int parts = ctx->tune.list_split > 0 ? ctx->tune.list_split : kDefaultListSplit;
+    launch_pdl(k_adjoint<G, RAD>, dim3(ctx->num_sms * std::max(1, resident)), dim3(kAdjWarps * 32), smem,
+               ctx->stream, A, parts);
 }
 
 template <int RAD>
 static void launch_adjoint_t(nb_ctx *ctx, const ForceArgs &A)
 {
-    const size_t smem = adjoint_smem_bytes(A.P.n_types, A.K);
-    static std::atomic<unsigned long long> optin{0};
-    smem_optin_once(k_adjoint<RAD>, ctx->device, 220 * 1024, optin);
-    int resident = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_adjoint<RAD>, kAdjWarps * 32, smem);
-    const int parts = ctx->tune.list_split > 0 ? ctx->tune.list_split : kDefaultListSplit;
-    launch_pdl(k_adjoint<RAD>, dim3(ctx->num_sms * std::max(1, resident)), dim3(kAdjWarps * 32), smem,
-               ctx->stream, A, parts);
+    if (ctx->built_group == 1) launch_adjoint_g<1, RAD>(ctx, A);
+    else if (ctx->built_group == 4) launch_adjoint_g<4, RAD>(ctx, A);
+    else launch_adjoint_g<8, RAD>(ctx, A);
 }
 
 size_t force_smem_for(int T, int scap, int K)
 {
-    (void)scap;  // unused: the kernels stage per 32-entry batch
-    return std::max(tile_smem_bytes(T, K), adjoint_smem_bytes(T, K));
+    (void)scap;  // unused: the kernels stage per batch of entries
+    (void)K;     // the exclusion masks are built by the list kernel
+    return std::max(tile_smem_bytes(T, kMaxGroup), adjoint_smem_bytes(T, kMaxGroup));
 }
 
 cudaError_t launch_adjoint_tile(nb_ctx *ctx, const double *d_dLdE, float *d_dpos, float *d_dq)
@@ -1250,20 +1628,24 @@ cudaError_t launch_adjoint_tile(nb_ctx *ctx, const double *d_dLdE, float *d_dpos
 // (unit weights, d = x_j - x_i as given); out[2k] = (E_LJ, E_Coul, r2, 0),
 // out[2k + 1] = the force on j.
 template <int RAD>
-__global__ void k_debug_pair_terms(PairParams P, const float2 *__restrict__ lj_tab, const float4 *__restrict__ rtab,
+__global__ void k_debug_pair_terms(PairParams P, const float4 *__restrict__ lj_tab, const float4 *__restrict__ rtab,
                                    long long n, const float4 *__restrict__ xi, const float4 *__restrict__ xj,
                                    const int *__restrict__ ti, const int *__restrict__ tj, float4 *__restrict__ out)
 {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const float4 a = xi[k], b = xj[k];
-    const float2 ab = lj_tab[ti[k] * P.n_types + tj[k]];
-    const float4 lj4 = make_float4(ab.x, ab.y, 12.0f * ab.x, 6.0f * ab.y);
+    const float4 ab = lj_tab[ti[k] * P.n_types + tj[k]];
+    float4 lj4[2];  // one type pair: (A, B, 12 A, 6 B), then the remainders at lj4 + n_types^2
+    lj4[0] = make_float4(ab.x, ab.y, 12.0f * ab.x, 6.0f * ab.y);
+    lj4[1] = make_float4(ab.z, ab.w, 0.0f, 0.0f);
     float dx, dy, dz;
     const float r2 = disp_r2(b.x, b.y, b.z, a.x, a.y, a.z, dx, dy, dz);
     Acc acc = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
     float fjx = 0.0f, fjy = 0.0f, fjz = 0.0f;
-    eval_pair<RAD, false>(P, &lj4, rtab, 0, a.w * P.ke, true, dx, dy, dz, r2, b.w, 0, false, acc, fjx, fjy, fjz);
+    PairParams P1 = P;
+    P1.n_types = 1;  // the one-pair table above
+    eval_pair<RAD, false>(P1, lj4, rtab, 0, a.w * P.ke, true, dx, dy, dz, r2, b.w, 0, false, acc, fjx, fjy, fjz);
     out[2 * k] = make_float4(acc.elj, acc.ec, r2, 0.0f);
     out[2 * k + 1] = make_float4(fjx, fjy, fjz, 0.0f);
 }

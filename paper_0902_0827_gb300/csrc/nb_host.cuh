@@ -191,8 +191,12 @@ inline nb_status validate_one(const nb_params *p)
 
 // (A, B) = (4 eps sig^12, 4 eps sig^6) per type pair, from per-type
 // Lorentz-Berthelot parameters (comb_rule 0) or explicit pair tables.
+// Type-pair tables: sigma_ab, eps_ab in FP64 and, per pair, (A, B, A - fl(A),
+// B - fl(B)) with A = 4 eps sig^12, B = 4 eps sig^6 rounded to FP32 and
+// their FP32 remainders (the energy adds them: a constant relative offset
+// of up to 3e-8 per type pair would not cancel in a summed LJ energy).
 inline void make_tables(int T, int comb_rule, const float *sigma, const float *eps, const float *sig_tab,
-                        const float *eps_tab, double *sg_out, double *ep_out, float2 *lj, float4 *lj_d = nullptr)
+                        const float *eps_tab, double *sg_out, double *ep_out, float4 *lj, float4 *lj_d = nullptr)
 {
     for (int a = 0; a < T; ++a)
         for (int b = 0; b < T; ++b) {
@@ -207,7 +211,9 @@ inline void make_tables(int T, int comb_rule, const float *sigma, const float *e
             sg_out[a * T + b] = sg;
             ep_out[a * T + b] = ep;
             double s6 = sg * sg * sg * sg * sg * sg;
-            lj[a * T + b] = make_float2((float)(4.0 * ep * s6 * s6), (float)(4.0 * ep * s6));
+            const double A = 4.0 * ep * s6 * s6, B = 4.0 * ep * s6;
+            const float Af = (float)A, Bf = (float)B;
+            lj[a * T + b] = make_float4(Af, Bf, (float)(A - (double)Af), (float)(B - (double)Bf));
             if (lj_d) {  // dA/dsig, dB/dsig, dA/deps, dB/deps
                 const double s5 = sg * sg * sg * sg * sg, s11 = s6 * s5;
                 lj_d[a * T + b] = make_float4((float)(48.0 * ep * s11), (float)(24.0 * ep * s5),

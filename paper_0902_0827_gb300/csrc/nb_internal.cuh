@@ -17,7 +17,11 @@ constexpr int kMaxTypes = 64;        // type-pair table lives in shared memory
 constexpr int kMaxPartners = 16;     // exclusion + 1-4 partners per atom
 constexpr int kErfcDeg = 8;          // degree of the erfcx polynomial in t
 constexpr int kExp2Deg = 6;          // degree of the 2^f polynomial on [-1/2, 1/2]
-constexpr int kDefaultListSplit = 4; // forward kernel: work units per cluster list
+constexpr int kDefaultListSplit = 1; // tile kernels: work units per segment of a group list
+constexpr int kMaxGroup = 8;         // clusters per i-group, largest (the masks hold 8 bits)
+constexpr int kDefaultGroup = 1;     // clusters per i-group, default (the autotuner may choose 4 or 8)
+constexpr int kMaskRecsPerCluster = 6; // exclusion-mask records allocated per cluster
+constexpr int kListSegs = 4;         // segments of a group's list (one per list-kernel warp)
 constexpr double kFixScale = 4294967296.0;   // 2^32: fixed-point scale
 constexpr int kTaskVals = 8;         // per system: E_lj, E_c (scale 2^32), W[6] (scale 2^20)
 constexpr double kVirScale = 1048576.0;      // 2^20: fixed-point scale of the virial sums
@@ -31,12 +35,15 @@ struct MdState;                      // molecular-dynamics state of a single-sys
 constexpr float kPadCoord = -1.0e18f;
 __host__ __device__ inline bool is_real_coord(float x) { return x > -1.0e17f; }
 
-// List entry encoding: J (bits 0..24) | shift codes x,y,z (2 bits each,
-// bits 25..30: 0 none, 1 = j-side shift x_j - L, 2 = i-side shift x_i - L)
-// | exclusion flag (bit 31: J holds a topology partner of I).
+// Group list entry (uint2).  x: J (bits 0..24) | shift codes x,y,z (2 bits
+// each, bits 25..30: 0 none, 1 = j-side shift x_j - L, 2 = i-side shift
+// x_i - L) | mask flag (bit 31: the entry's tiles have exclusion masks).
+// y: the group's clusters in reach of J (bits 0..7, bit c = cluster c of the
+// group) | mask record (bits 8..31, when flagged).
 constexpr uint32_t kJMask = 0x01FFFFFFu;
 constexpr int kShiftBit = 25;
 constexpr uint32_t kExclFlag = 0x80000000u;
+constexpr int kMaskSlotBit = 8;
 
 // Device status bits (first error wins when reported).
 enum : int {
@@ -117,14 +124,18 @@ struct DevBuffers {
     long long *sys_acc = nullptr;    // [n_sys*kTaskVals] per-system fixed-point energies (2^32) and virial (2^20)
     long long *facc = nullptr;       // [S*3] fixed-point forces in sorted order (both atoms of each pair)
     long long *gacc = nullptr;       // [S*4] adjoint: fixed-point dL/dx, dL/dq in sorted order
-    uint32_t *list = nullptr;        // [NC*list_cap] per cluster: its half list (Newton's third law)
-    int *list_n = nullptr;           // [NC] lengths
-    int *pslot = nullptr;            // [S*K] partner slots (slot << 1) | is14, -1 pad
+    int *col_grp = nullptr;          // [C+1] first i-group of each column
+    int2 *grp = nullptr;             // [GC] i-group: (first cluster, clusters)
+    int *clus_grp = nullptr;         // [NC] i-group of each cluster
+    uint2 *glist = nullptr;          // [GC*list_cap] per i-group: its list (Newton's third law at group level)
+    int *glist_n = nullptr;          // [GC*kListSegs] lengths of the segments (list_cap / kListSegs entries each)
+    ulonglong2 *gmask = nullptr;     // [MC*kMaxGroup] per flagged entry and group cluster: (excluded, 1-4) bits
     int2 *zbin = nullptr;            // [zb_total] z-bin index of the columns (see SysDesc)
     long long *tab_grad = nullptr;   // [T*T*2] adjoint dL/dsig_ab, dL/deps_ab (fixed point, one ordered half)
-    int *counts = nullptr;           // [4]: n_slots, n_clusters, unpack ticket, forward work-unit counter
+    int *counts = nullptr;           // [8]: n_slots, n_clusters, unpack ticket, work-unit counter,
+                                     //      n_groups, mask records used, -, -
     int *status = nullptr;           // [1]
-    float2 *lj_tab = nullptr;        // [T*T] (A, B)
+    float4 *lj_tab = nullptr;        // [T*T] (A, B, A - fl(A), B - fl(B)): FP32 and the FP32 remainders
     float4 *lj_d = nullptr;          // [T*T] 48 eps sig^11, 24 eps sig^5, 4 sig^12, 4 sig^6
     float4 *rtab = nullptr;          // [tab_n*3] tabulated radial functions (nb_set_tables)
     float4 *gslot = nullptr;         // [S] adjoint input dL/dF in sorted order
@@ -147,7 +158,11 @@ struct nb_ctx {
     int K = 1;                     // partners per atom (>= 1)
     int comb_rule = 0;
     int stage_cap = 96;            // nb_tuning.stage_capacity (no effect on the kernels)
-    int list_cap = 512;            // entries per cluster list
+    int list_cap = 512;            // entries per group list
+    int group = acenb::kDefaultGroup;  // clusters per i-group of the last/next build (4 or 8)
+    int built_group = 0;           // the group size the current lists were built with
+    int64_t grp_cap = 0;           // i-group slots (enough for groups of 4)
+    int64_t mask_cap = 0;          // exclusion-mask records
     int tab_n = 0;                 // radial-function table intervals (0: direct evaluation)
     int64_t zb_total = 0;          // entries of the z-bin index
     int smem_optin = 0;            // device opt-in shared memory per block
@@ -211,6 +226,14 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
+
+// i-group slots for a context: every column's clusters form groups of
+// `group` clusters, the last one partial, so at most NC / group + C; the
+// capacity covers every supported group size (groups of one cluster: NC).
+inline int64_t group_capacity(int64_t clus_cap) { return clus_cap + 1; }
+// exclusion-mask records: the self tiles (one per cluster) and the entries
+// whose cluster holds a topology partner of a group atom (a few per cluster)
+inline int64_t mask_capacity(int64_t clus_cap) { return clus_cap * kMaskRecsPerCluster + 64; }
 
 // Launchers implemented in the .cu files (all asynchronous on ctx->stream).
 cudaError_t launch_build(nb_ctx *ctx, const float *d_pos);

@@ -38,12 +38,14 @@ namespace {
 
 constexpr int kMaxAtoms = NB_NOALLOC_MAX_ATOMS;
 constexpr int kMaxCols = NB_NOALLOC_MAX_COLUMNS;
-constexpr int kListCap = 256;  // entries per cluster list
+constexpr int kListCap = 384;  // entries per i-group list
 constexpr int kZbEntries = 65536;  // z-bin index entries (bins per column shrink to fit)
 constexpr int kMaxDevices = 64;
 constexpr long long kSlots = ((long long)kMaxAtoms + (kCluster - 1) * (long long)kMaxCols + kCluster - 1) /
                              kCluster * kCluster;
 constexpr long long kClus = kSlots / kCluster;
+constexpr long long kGrp = kClus + 1;                          // i-group slots (group_capacity)
+constexpr long long kMaskRecs = kClus * kMaskRecsPerCluster + 64;  // exclusion-mask records (mask_capacity)
 
 constexpr size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -66,14 +68,17 @@ constexpr size_t oBb = oInv + a256(4ull * kMaxAtoms);
 constexpr size_t oClusSys = oBb + a256(32ull * kClus);
 constexpr size_t oSysAcc = oClusSys + a256(4ull * kClus);
 constexpr size_t oFacc = oSysAcc + a256(8ull * kTaskVals);
-constexpr size_t oList = oFacc + a256(24ull * kSlots);
-constexpr size_t oListN = oList + a256(4ull * kClus * kListCap);
-constexpr size_t oPslot = oListN + a256(4ull * kClus);
-constexpr size_t oZbin = oPslot + a256(4ull * kSlots * kMaxPartners);
+constexpr size_t oColGrp = oFacc + a256(24ull * kSlots);
+constexpr size_t oGrp = oColGrp + a256(4ull * (kMaxCols + 1));
+constexpr size_t oClusGrp = oGrp + a256(8ull * kGrp);
+constexpr size_t oGlist = oClusGrp + a256(4ull * kClus);
+constexpr size_t oGlistN = oGlist + a256(8ull * kGrp * kListCap);
+constexpr size_t oGmask = oGlistN + a256(4ull * kGrp * kListSegs);
+constexpr size_t oZbin = oGmask + a256(16ull * kMaskRecs * kMaxGroup);
 constexpr size_t oCounts = oZbin + a256(8ull * kZbEntries);
-constexpr size_t oStatus = oCounts + a256(16);
+constexpr size_t oStatus = oCounts + a256(32);
 constexpr size_t oLj = oStatus + a256(16);
-constexpr size_t oDbg = oLj + a256(8ull * kMaxTypes * kMaxTypes);
+constexpr size_t oDbg = oLj + a256(16ull * kMaxTypes * kMaxTypes);
 constexpr size_t kScratchBytes = oDbg + a256(16);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
@@ -83,7 +88,7 @@ SysDesc h_sys;
 int h_part[kMaxAtoms * kMaxPartners];
 int h_cnt[kMaxAtoms];
 double h_sg[kMaxTypes * kMaxTypes], h_ep[kMaxTypes * kMaxTypes];
-float2 h_lj[kMaxTypes * kMaxTypes];
+float4 h_lj[kMaxTypes * kMaxTypes];
 unsigned char *g_dev_scratch[kMaxDevices];  // cached device address per device
 
 template <class T>
@@ -171,6 +176,10 @@ extern "C" nb_status nb_forces_noalloc(const nb_params *params, const float *d_p
     c.tune.stage_capacity = 96;
     c.tune.list_capacity = kListCap;
     c.tune.list_split = kDefaultListSplit;
+    c.tune.group_clusters = kDefaultGroup;
+    c.group = kDefaultGroup;
+    c.grp_cap = kGrp;
+    c.mask_cap = kMaskRecs;
     c.stage_cap = 96;
     c.list_cap = kListCap;
     c.zb_total = host::zbin_entries(S);
@@ -194,13 +203,16 @@ extern "C" nb_status nb_forces_noalloc(const nb_params *params, const float *d_p
     d.clus_sys = at<int>(base, oClusSys);
     d.sys_acc = at<long long>(base, oSysAcc);
     d.facc = at<long long>(base, oFacc);
-    d.list = at<uint32_t>(base, oList);
-    d.list_n = at<int>(base, oListN);
-    d.pslot = at<int>(base, oPslot);
+    d.col_grp = at<int>(base, oColGrp);
+    d.grp = at<int2>(base, oGrp);
+    d.clus_grp = at<int>(base, oClusGrp);
+    d.glist = at<uint2>(base, oGlist);
+    d.glist_n = at<int>(base, oGlistN);
+    d.gmask = at<ulonglong2>(base, oGmask);
     d.zbin = at<int2>(base, oZbin);
     d.counts = at<int>(base, oCounts);
     d.status = at<int>(base, oStatus);
-    d.lj_tab = at<float2>(base, oLj);
+    d.lj_tab = at<float4>(base, oLj);
     d.dbg_n = at<long long>(base, oDbg);
 
     // per-call inputs of the scratch; zero what the kernels expect zeroed
@@ -209,7 +221,7 @@ extern "C" nb_status nb_forces_noalloc(const nb_params *params, const float *d_p
     if (e == cudaSuccess) e = cudaMemsetAsync(d.atom_sys, 0, sizeof(int) * N, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.col_sys, 0, sizeof(int) * C, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d.part_orig, h_part, sizeof(int) * N * K, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d.lj_tab, h_lj, sizeof(float2) * T * T, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d.lj_tab, h_lj, sizeof(float4) * T * T, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.status, 0, sizeof(int), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.tslot, 0, sizeof(int) * c.slot_cap, s);
     if (e == cudaSuccess) e = launch_build(&c, d_pos);

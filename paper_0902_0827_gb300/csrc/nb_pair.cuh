@@ -108,15 +108,20 @@ __device__ __forceinline__ float exp_neg_a2r2(const PairParams &P, float r2)
 
 // Radial part of one pair at squared distance r2 (inside the cutoff), from
 // r, rinv = 1/r (pair_rinv), r2inv = 1/r2 and the type pair's LJ
-// coefficients lj = (A, B, 12 A, 6 B):
+// coefficients lj = (A, B, 12 A, 6 B) and the FP32 remainders lo of A and B
+// (the energy adds them; the force does not need them):
 //   elj, ec : LJ (switched) and Coulomb energies (unweighted);
 //   frlj, frc : -dU/dr * r of each part.
 template <bool EWALD, bool SWITCH>
 __device__ __forceinline__ void pair_radial(const PairParams &P, float r2, float r, float rinv, float r2inv,
-                                            float4 lj, float qq, float &elj, float &frlj, float &ec, float &frc)
+                                            float4 lj, float2 lo, float qq, float &elj, float &frlj, float &ec,
+                                            float &frc)
 {
     const float ir6 = r2inv * r2inv * r2inv;
-    elj = ir6 * fmaf(lj.x, ir6, -lj.y);   // A r^-12 - B r^-6
+    // A r^-12 - B r^-6: the remainders' term (below half an ulp of the
+    // result) enters the last FMA beside the exact product, before its one
+    // rounding; added to an already rounded value it would vanish
+    elj = fmaf(ir6, fmaf(lj.x, ir6, -lj.y), ir6 * fmaf(lo.x, ir6, -lo.y));
     frlj = ir6 * fmaf(lj.z, ir6, -lj.w);  // 12 A r^-12 - 6 B r^-6
     if (SWITCH) {
         // with t = rc2 - r2 and u = rs2 - r2, for r > rs:
@@ -152,8 +157,8 @@ __device__ __forceinline__ void pair_radial(const PairParams &P, float r2, float
 // pair_radial.  The interpolation is FP32 (one FMA per function) on the
 // caller's r = r2 rsqrt(r2).
 __device__ __forceinline__ void pair_radial_tab(const PairParams &P, const float4 *__restrict__ tab, float r,
-                                                float A, float B, float qq, float &elj, float &frlj, float &ec,
-                                                float &frc)
+                                                float A, float B, float2 lo, float qq, float &elj, float &frlj,
+                                                float &ec, float &frc)
 {
     const float x = r * P.tab_inv_h;
     const int k = max(0, min((int)x, P.tab_n - 1));
@@ -162,7 +167,7 @@ __device__ __forceinline__ void pair_radial_tab(const PairParams &P, const float
     const float e12 = fmaf(t, a.y, a.x), e6 = fmaf(t, a.w, a.z);
     const float ecv = fmaf(t, b.y, b.x), f12 = fmaf(t, b.w, b.z);
     const float f6 = fmaf(t, c.y, c.x), fcv = fmaf(t, c.w, c.z);
-    elj = fmaf(A, e12, -B * e6);
+    elj = fmaf(A, e12, fmaf(-B, e6, fmaf(lo.x, e12, -lo.y * e6)));
     frlj = fmaf(A, f12, -B * f6);
     ec = qq * ecv;
     frc = qq * fcv;

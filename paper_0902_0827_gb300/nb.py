@@ -51,7 +51,8 @@ class nb_params(ctypes.Structure):
 
 class nb_tuning(ctypes.Structure):
     _fields_ = [("blocks_per_sm", ctypes.c_int32), ("stage_capacity", ctypes.c_int32),
-                ("list_capacity", ctypes.c_int32), ("list_split", ctypes.c_int32)]
+                ("list_capacity", ctypes.c_int32), ("list_split", ctypes.c_int32),
+                ("group_clusters", ctypes.c_int32)]
 
 
 class nb_pme_params(ctypes.Structure):

@@ -144,24 +144,50 @@ def test_list_capacity_overflow_is_reported():
     assert ctx.status(raise_on_error=False) == 10  # NB_ERR_CAPACITY
 
 
-def test_tuning_is_validated_and_default_split_is_four():
+def test_tuning_is_validated_and_default_split_is_one():
     s = S.water_box()
     ctx = nb.Nonbonded(s)
-    for bad in (dict(list_split=-1), dict(list_split=9), dict(blocks_per_sm=0), dict(blocks_per_sm=9)):
+    for bad in (dict(list_split=-1), dict(list_split=9), dict(blocks_per_sm=0), dict(blocks_per_sm=9),
+                dict(group_clusters=2), dict(group_clusters=3), dict(group_clusters=16)):
         with pytest.raises(nb.NbError):
             ctx.set_tuning(**bad)
     pos, q, t = nb.concat_inputs([s])
     outs = {}
-    for split in (0, 4, 4, 1):  # 0 selects the default split (4); every split repeats bit for bit
+    for split in (0, 1, 1, 2):  # 0 selects the default split (1); every split repeats bit for bit
         ctx.set_tuning(list_split=split)
         ctx.build(pos)
         F, E, W = ctx.forces(pos, q, t)
         torch.cuda.synchronize()
         outs.setdefault(split, []).append((F.clone(), E.clone(), W.clone()))
     ctx.status()
-    a, b, c = outs[0][0], outs[4][0], outs[4][1]
+    a, b, c = outs[0][0], outs[1][0], outs[1][1]
     for x, y in ((a, b), (b, c)):
         assert all(torch.equal(u, v) for u, v in zip(x, y))
     # another split only moves where the FP32 sums are cut
-    F1, F4 = outs[1][0][0].double(), a[0].double()
-    assert (torch.linalg.norm(F1 - F4) / torch.linalg.norm(F4)).item() < 1e-6
+    F2, F1 = outs[2][0][0].double(), a[0].double()
+    assert (torch.linalg.norm(F2 - F1) / torch.linalg.norm(F1)).item() < 1e-6
+
+
+def test_group_size_change_needs_a_new_build_and_keeps_parity():
+    # the i-group size (4 or 8 clusters) is a build parameter: after a change
+    # the forces are refused until the next build, which then agrees with the
+    # oracle at the same bars
+    s = S.water_box()
+    ctx = nb.Nonbonded(s)
+    pos, q, t = nb.concat_inputs([s])
+    ctx.build(pos)
+    ctx.forces(pos, q, t)
+    ctx.set_tuning(group_clusters=4)
+    with pytest.raises(nb.NbError) as e:
+        ctx.forces(pos, q, t)
+    assert e.value.code == 5  # NB_ERR_NOT_BUILT
+    ctx.build(pos)
+    F, E, W = ctx.forces(pos, q, t)
+    _, n, _ = ctx.debug_pairs(cap=0)
+    torch.cuda.synchronize()
+    ctx.status()
+    Fo, Eo, Wo, no, Es, Eq = oracle.forces(s, method="allpairs", with_scale=True, with_sq=True)
+    assert n == no
+    parity.check_forces("water_box group4", F.double().cpu().numpy(), Fo)
+    parity.check_energy("water_box group4", E[0].cpu().numpy(), Eo, Es, bars=(E_REL, "floor", "floor"), Eq=Eq)
+    assert ctx.tuning()["group_clusters"] == 4

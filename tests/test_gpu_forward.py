@@ -117,14 +117,14 @@ def test_forces_energy_virial_parity(case):
 
 def test_tuning_variants_agree(case):
     # other grid sizes change the warp-to-unit assignment; list splits of 1
-    # to 8 cut every cluster's list into that many work units (most units
-    # of the 8-way split hold under 32 entries, the 1-way one several
-    # 32-entry batches)
+    # to 8 cut every list segment into that many work units; groups of 4
+    # and 8 clusters run the group kernel on lists built for them
     name, s, Fo, Eo, Wo, npairs, Es, Eq = case
     for tune in (dict(list_split=1, blocks_per_sm=1), dict(list_split=3, blocks_per_sm=3),
-                 dict(list_split=8, blocks_per_sm=2)):
+                 dict(list_split=8, blocks_per_sm=2), dict(list_split=2, blocks_per_sm=3, group_clusters=4),
+                 dict(list_split=4, blocks_per_sm=3, group_clusters=8)):
         ctx, inp, F, E, W = gpu_eval(s, tuning=tune)
-        tag = f"{name} split{tune['list_split']}/bps{tune['blocks_per_sm']}"
+        tag = f"{name} split{tune['list_split']}/bps{tune['blocks_per_sm']}/g{tune.get('group_clusters', 1)}"
         check_forces(F, Fo, tag)
         check_energy(E[0], Eo, Es, Eq, tag, bars=energy_bars(name))
         check_virial(tag, W[0], Wo)

@@ -10,13 +10,14 @@ distance, not only small.  Bars, per 1 A bin of r:
 * mean relative error of E_Coul and of E_LJ (the latter relative to
   A r^-12 + B r^-6, which vanishes neither where E_LJ changes sign nor where
   the switch reaches zero) within 1e-8 (or 5 standard errors of the bin mean
-  when the bin is small); for E_LJ plus the FP32 rounding of the type-pair
-  coefficients A, B (up to 6e-8 here, constant per type pair);
+  when the bin is small);
 * rms relative error below 5e-7, and of the pair force below 1e-6.
 The MUFU approximations of rsqrt, rcp and ex2 carry mean errors of -5e-9,
 up to +6e-9 and -5e-8 on this GPU (amplified twelvefold in r^-12 for
-rsqrt); the pair arithmetic refines or replaces them, which this test
-guards.
+rsqrt), and the FP32 type-pair coefficients A, B differ from their FP64
+values by up to 6e-8 (constant per type pair); the pair arithmetic refines
+or replaces the approximations and adds the coefficients' FP32 remainders
+in the energy, which this test guards.
 """
 
 import numpy as np
@@ -34,17 +35,6 @@ from pairs_util import imaged_pairs  # noqa: E402
 pytestmark = pytest.mark.gpu
 
 BIAS, RMS, F_RMS_PAIR = 1e-8, 5e-7, 1e-6
-
-
-def coefficient_rounding(s):
-    """Largest relative FP32 rounding of the type-pair coefficients A, B of a
-    system: the library stores them in FP32, a constant relative offset of
-    every pair of that type pair (the oracle uses them in FP64)."""
-    _, _, A, B = oracle.combine_lb(s.sigma, s.epsilon)
-    m = A > 0
-    ra = np.abs(A[m].astype(np.float32).astype(np.float64) / A[m] - 1)
-    rb = np.abs(B[m].astype(np.float32).astype(np.float64) / B[m] - 1)
-    return float(max(ra.max(initial=0.0), rb.max(initial=0.0)))
 
 
 def gpu_pair_terms(s, ij, xi, xj):
@@ -72,16 +62,15 @@ def test_pair_terms_are_unbiased_at_every_distance(which):
     frel = np.linalg.norm(fj - fj_ref) / np.linalg.norm(fj_ref)
     parity.record(f"pairs {which}", "pair force rel RMS", frel, F_RMS_PAIR)
     assert frel <= F_RMS_PAIR
-    cr = coefficient_rounding(s)
     for b in range(1, 9):
         m = (r >= b) & (r < b + 1)
-        for lab, col, scale, extra in (("E_Coul", 1, np.abs(o[:, 1]), 0.0), ("E_LJ", 0, o[:, 3], cr)):
+        for lab, col, scale in (("E_Coul", 1, np.abs(o[:, 1])), ("E_LJ", 0, o[:, 3])):
             mm = m & (scale > 0)
             if mm.sum() < 100:
                 continue
             rel = (g[mm, col] - o[mm, col]) / scale[mm]
             mean, rms = rel.mean(), np.sqrt((rel ** 2).mean())
-            bar = max(BIAS, 5 * rms / np.sqrt(mm.sum())) + extra
+            bar = max(BIAS, 5 * rms / np.sqrt(mm.sum()))
             parity.record(f"pairs {which} r {b}-{b + 1} A", f"{lab} mean rel err", mean, bar)
             parity.record(f"pairs {which} r {b}-{b + 1} A", f"{lab} rms rel err", rms, RMS)
             assert abs(mean) <= bar, (which, b, lab, mean, bar)
