@@ -95,7 +95,7 @@ __device__ void scan_columns(int n_cols, int n_sys, const int *__restrict__ col_
         } else {
             col_grp[n_cols] = carry;
             counts[4] = carry;  // groups
-            counts[5] = 0;      // exclusion-mask records used by the list kernel
+            counts[5] = 0;      // exclusion-mask pool records used by the list kernel
         }
         carry = 0;
     }
@@ -406,49 +406,74 @@ constexpr unsigned long long kSelfTriangle = 0xFF7F3F1F0F070301ull;
 // (excluded, scaled 1-4) for i atom ia of cluster c0 + c and j atom jj of J;
 // the direct self tile (J = c0 + c, no shift) also excludes jj <= ia.  The
 // partners of the group's atoms that lie in J are the chain of J's slot in
-// the block's partner-cluster table (s_head / s_next over s_pslot, entry t =
-// atom t / K of the group).
-__device__ void entry_masks(const int *__restrict__ s_pslot, const int *__restrict__ s_next, int head, int K,
-                            int c0, int n, unsigned cm, int J, uint32_t code, ulonglong2 *__restrict__ rec)
+// the warp's partner-cluster table: s_pslot[t] is a partner slot
+// ((slot << 1) | is14) and s_link[t] packs the next entry of the chain
+// (kLinkEnd at its end) with the group atom the partner belongs to (<< 16).
+constexpr int kLinkEnd = 0xFFFF;
+
+__device__ void entry_masks(const int *__restrict__ s_pslot, const int *__restrict__ s_link, int head, int c0,
+                            unsigned cm, int J, uint32_t code, ulonglong2 *__restrict__ rec)
 {
     // per cluster of the mask: walk J's chain, keep that cluster's bits in
     // registers, one store (the chains are a few partners long)
     for (unsigned cc = cm; cc; cc &= cc - 1u) {
         const int c = __ffs(cc) - 1;
         unsigned long long ex = 0ull, s14 = 0ull;
-        for (int t = head, guard = 0; t >= 0 && guard < kCluster * kMaxGroup * kMaxPartners; t = s_next[t], ++guard) {
-            const int a = t / K;
-            if (a / kCluster != c) continue;
-            const int v = s_pslot[t];
-            const unsigned long long bit = 1ull << ((a % kCluster) * kCluster + ((v >> 1) & (kCluster - 1)));
-            if (v & 1) s14 |= bit;
-            else ex |= bit;
+        for (int t = head, guard = 0; t != kLinkEnd && guard < kCluster * kMaxGroup * kMaxPartners; ++guard) {
+            const int lk = s_link[t];
+            const int a = lk >> 16;
+            if (a / kCluster == c) {
+                const int v = s_pslot[t];
+                const unsigned long long bit = 1ull << ((a % kCluster) * kCluster + ((v >> 1) & (kCluster - 1)));
+                if (v & 1) s14 |= bit;
+                else ex |= bit;
+            }
+            t = lk & kLinkEnd;
         }
         if (code == 0u && J == c0 + c) ex |= kSelfTriangle;
         rec[c] = make_ulonglong2(ex, s14);
     }
-    (void)n;
+}
+
+// q = a / b and r = a % b for 0 <= a < 2^20, b >= 1: a rounded FP32 quotient
+// estimate (within 1/4 of the true one there) and one correction each way.
+__device__ __forceinline__ int div_small(int a, int b, float inv_b, int &r)
+{
+    int q = __float2int_rz(((float)a + 0.5f) * inv_b);
+    r = a - q * b;
+    if (r < 0) {
+        --q;
+        r += b;
+    } else if (r >= b) {
+        ++q;
+        r -= b;
+    }
+    return q;
 }
 
 // A4: i-group lists, one warp per group of up to 8 consecutive clusters of a
 // column (clusters c0 .. c0 + n - 1), kGListWarps groups per block.  The
 // columns within reach of the group's bounding box (with periodic images)
-// are dealt round-robin to the kListSegs segments of the group's list
-// (list_cap / kListSegs entries each); within a segment the entries follow
-// the scan order, so the lists are deterministic.  Clusters of a column are
+// are scanned in order.  Clusters of a column are
 // z-sorted, so the ones whose z-range (under the z images -L, 0, +L,
 // concatenated as virtual indices -nj..2nj-1) comes within the cutoff of the
 // group form one window per column; the windows of 32 columns are flattened
 // and every candidate (J, image) gets the mask of the group clusters whose
 // boxes come within rc + margin of J's and whose tile the group keeps
-// (keep_groups, keep_in_group); a non-empty mask makes an entry.  Entries
-// whose J holds a topology partner of a group atom (found in the warp's
-// partner-cluster table), or that contain the direct self tile, are flagged
-// and get a record of exclusion bitmasks (entry_masks).
+// (keep_groups, keep_in_group); a non-empty mask makes an entry.  Two rounds
+// of 32 candidates are in flight at a time (their box loads overlap).  The
+// entries are dealt round-robin, in scan order, to the kListSegs segments of
+// the group's list (entry r to segment r % kListSegs, position r / kListSegs),
+// so the segments are equally long and the lists deterministic.
+// Entries whose J holds a topology partner of a group atom (found in the
+// warp's partner-cluster table), or that contain the direct self tile, are
+// flagged and get a record of exclusion bitmasks (entry_masks): the group's
+// own records first (kMaskRecsPerCluster per cluster, taken in scan order
+// without atomics), then the shared pool.
 struct GListArgs {
     const SysDesc *sys;
     const int *counts;
-    int *mask_count;         // records used (counts[5], zeroed by the binning kernel)
+    int *pool_count;         // pool records used (counts[5], zeroed by the binning kernel)
     const float4 *bb;
     const int *clus_sys;
     const int *col_slot;
@@ -462,18 +487,23 @@ struct GListArgs {
     int *glist_n;
     ulonglong2 *gmask;
     int *status;
+    long long pool_base;     // first pool record (after every group's own records)
     long long mask_cap;
     int K;
     float rcm;
     int cap;                 // entries per group (all segments)
-    int group;               // clusters per group of this build
+    int group;               // clusters per group of this build (records hold `group` mask pairs)
 };
 
 constexpr int kGListWarps = 4;  // groups (warps) per block of the list kernel
+#ifndef ACENB_GLIST_MIN_BLOCKS
+#define ACENB_GLIST_MIN_BLOCKS 6  // resident blocks per SM the register budget allows
+#endif
+constexpr int kPartnerBatch = 4;  // rounds of partner loads in flight
 
-__host__ __device__ inline size_t glist_warp_ints(int K) { return 2 * (size_t)kCluster * kMaxGroup * K; }
+__host__ __device__ inline size_t glist_warp_ints(int K, int group) { return 2 * (size_t)kCluster * group * K; }
 
-__global__ void __launch_bounds__(kGListWarps * 32) k_glist(GListArgs A)
+__global__ void __launch_bounds__(kGListWarps * 32, ACENB_GLIST_MIN_BLOCKS) k_glist(GListArgs A)
 {
     pdl_entry();
     const unsigned FULL = 0xffffffffu;
@@ -487,16 +517,20 @@ __global__ void __launch_bounds__(kGListWarps * 32) k_glist(GListArgs A)
     __shared__ int s_hash_all[kGListWarps][kHashSlots];
     __shared__ int s_head_all[kGListWarps][kHashSlots];
     __shared__ int s_col_all[kGListWarps][32];
+    __shared__ int4 s_ci_all[kGListWarps][32];    // per window: jb, nj, first virtual index - offset, code
+    __shared__ float2 s_co_all[kGListWarps][32];  // per window: x, y image shift
     __shared__ unsigned char s_own_all[kGListWarps][kOwnCap];
     extern __shared__ int s_dyn[];
     float4 *s_lo = s_lo_all[w], *s_hi = s_hi_all[w];
     int *s_hash = s_hash_all[w], *s_head = s_head_all[w], *s_col = s_col_all[w];
+    int4 *s_ci = s_ci_all[w];
+    float2 *s_co = s_co_all[w];
     unsigned char *s_own = s_own_all[w];
-    int *s_pslot = s_dyn + (size_t)w * glist_warp_ints(K);  // [8 n K] partner slots (slot << 1) | is14
-    int *s_next = s_pslot + kCluster * kMaxGroup * K;       // [8 n K] chains of the partner-cluster table
+    int *s_pslot = s_dyn + (size_t)w * glist_warp_ints(K, A.group);  // [8 n K] partner slots (slot << 1) | is14
+    int *s_link = s_pslot + kCluster * A.group * K;                   // [8 n K] chains of the partner-cluster table
     for (int t = lane; t < kHashSlots; t += 32) {
         s_hash[t] = -1;
-        s_head[t] = -1;
+        s_head[t] = kLinkEnd;
     }
     if (lane < n) {
         s_lo[lane] = A.bb[2 * (c0 + lane)];
@@ -504,16 +538,39 @@ __global__ void __launch_bounds__(kGListWarps * 32) k_glist(GListArgs A)
     }
     __syncwarp();
     const int np = kCluster * n * K;
+    const float inv_K = 1.0f / (float)K;
     bool full = false;  // the partner table overflowed: flag every entry
-    for (int t = lane; t < np; t += 32) {
-        int v = A.perm[c0 * kCluster + t / K];
-        v = v >= 0 ? A.part_orig[(long long)v * K + t % K] : -1;
-        v = v >= 0 ? (A.inv[v >> 1] << 1) | (v & 1) : -1;
-        s_pslot[t] = v;
-        if (v >= 0) {
-            const int hs = hset_insert(s_hash, (v >> 1) / kCluster);
-            if (hs < 0) full = true;
-            else s_next[t] = atomicExch(&s_head[hs], t);
+    for (int t0 = 0; t0 < np; t0 += kPartnerBatch * 32) {
+        // the three dependent loads of kPartnerBatch rounds at a time
+        int pv[kPartnerBatch];
+#pragma unroll
+        for (int r = 0; r < kPartnerBatch; ++r) {
+            const int t = t0 + r * 32 + lane;
+            int rr;
+            pv[r] = t < np ? A.perm[c0 * kCluster + div_small(t, K, inv_K, rr)] : -1;
+        }
+#pragma unroll
+        for (int r = 0; r < kPartnerBatch; ++r) {
+            const int t = t0 + r * 32 + lane;
+            int rr;
+            const int a = div_small(t, K, inv_K, rr);
+            pv[r] = pv[r] >= 0 ? A.part_orig[(long long)pv[r] * K + rr] : -1;
+            (void)a;
+        }
+#pragma unroll
+        for (int r = 0; r < kPartnerBatch; ++r) pv[r] = pv[r] >= 0 ? (A.inv[pv[r] >> 1] << 1) | (pv[r] & 1) : -1;
+#pragma unroll
+        for (int r = 0; r < kPartnerBatch; ++r) {
+            const int t = t0 + r * 32 + lane;
+            if (t >= np) continue;
+            s_pslot[t] = pv[r];
+            if (pv[r] >= 0) {
+                const int hs = hset_insert(s_hash, (pv[r] >> 1) / kCluster);
+                int rr;
+                const int a = div_small(t, K, inv_K, rr);  // group atom of entry t
+                if (hs < 0) full = true;
+                else s_link[t] = (atomicExch(&s_head[hs], t) & kLinkEnd) | (a << 16);
+            }
         }
     }
     const bool all_flag = __any_sync(FULL, full);
@@ -536,40 +593,43 @@ __global__ void __launch_bounds__(kGListWarps * 32) k_glist(GListArgs A)
     const int ncx = cxb - cxa + 1, ncand = ncx * (cyb - cya + 1);
     const int seg_cap = A.cap / kListSegs;
     uint2 *LA = A.glist + (long long)g * A.cap;
-    int nseg[kListSegs] = {0, 0, 0, 0};  // entries of each segment
-    int gpass = 0;                        // passing columns so far (decides their segment)
+    int ntot = 0;  // entries so far (entry r goes to segment r % kListSegs)
+    const long long loc_base = (long long)c0 * kMaskRecsPerCluster;  // the group's own mask records
+    const int loc_cap = n * kMaskRecsPerCluster;
+    int nloc = 0;
+    const float inv_ncx = 1.0f / (float)ncx;
     for (int c_lo = 0; c_lo < ncand; c_lo += 32) {
         // the candidate columns of this round whose geometry (a lower bound
         // of the xy gap) passes, compacted in order
         const int cc = c_lo + lane;
         bool pass = false;
+        int ccx = 0, ccy = 0;
         if (cc < ncand) {
-            const int cy = cya + cc / ncx, cx = cxa + cc % ncx;
+            ccy = div_small(cc, ncx, inv_ncx, ccx);
+            const int cy = cya + ccy, cx = cxa + ccx;
             const float gcx = fmaxf(fmaxf(cx * S.w[0] - hi.x, lo.x - (cx + 1) * S.w[0]) - cmarg, 0.0f);
             const float gcy = fmaxf(fmaxf(cy * S.w[1] - hi.y, lo.y - (cy + 1) * S.w[1]) - cmarg, 0.0f);
             pass = gcx * gcx + gcy * gcy < rcm2;
         }
         const unsigned b = __ballot_sync(FULL, pass);
-        if (pass) s_col[__popc(b & lt)] = cc;
+        if (pass) s_col[__popc(b & lt)] = ccx | (ccy << 16);
         const int npass = __popc(b);
         __syncwarp();
         if (npass == 0) continue;
         const int c = lane < npass ? s_col[lane] : -1;
-        const int seg = (gpass + lane) % kListSegs;  // segment of the lane's column
-        gpass += npass;
         int jb = 0, nj = 0, va = 0, cnt = 0;
         uint32_t code_xy = 0u;
         float ox = 0.0f, oy = 0.0f;
         if (c >= 0) {
-            const int cy = cya + c / ncx, cx = cxa + c % ncx;
-            const int ccy = cy < 0 ? cy + S.ny : (cy >= S.ny ? cy - S.ny : cy);
-            const int ccx = cx < 0 ? cx + S.nx : (cx >= S.nx ? cx - S.nx : cx);
+            const int cy = cya + (c >> 16), cx = cxa + (c & 0xFFFF);
+            const int ky = cy < 0 ? cy + S.ny : (cy >= S.ny ? cy - S.ny : cy);
+            const int kx = cx < 0 ? cx + S.nx : (cx >= S.nx ? cx - S.nx : cx);
             const uint32_t sy = cy < 0 ? 1u : (cy >= S.ny ? 2u : 0u);
             const uint32_t sx = cx < 0 ? 1u : (cx >= S.nx ? 2u : 0u);
             ox = sx == 1u ? -S.L[0] : (sx == 2u ? S.L[0] : 0.0f);
             oy = sy == 1u ? -S.L[1] : (sy == 2u ? S.L[1] : 0.0f);
             code_xy = sx | (sy << 2);
-            const int col = S.col_begin + ccy * S.nx + ccx;
+            const int col = S.col_begin + ky * S.nx + kx;
             jb = A.col_slot[col] / kCluster;
             nj = A.col_slot[col + 1] / kCluster - jb;
             // z window over the virtual indices v (image -L: v - nj, 0: v, +L: v + nj)
@@ -594,102 +654,121 @@ __global__ void __launch_bounds__(kGListWarps * 32) k_glist(GListArgs A)
             if (lane >= o) incl += y;
         }
         const int off = incl - cnt, total = __shfl_sync(FULL, incl, 31);
+        s_ci[lane] = make_int4(jb, nj, va - off, (int)code_xy);
+        s_co[lane] = make_float2(ox, oy);
         for (int t = off; t < min(off + cnt, kOwnCap); ++t) s_own[t] = (unsigned char)lane;
         __syncwarp();
-        for (int p0 = 0; p0 < total; p0 += 32) {
-            const int p = p0 + lane;
-            int src = 0;
-            if (p0 + 31 < kOwnCap) {
-                src = p < total ? s_own[p] : 0;
-            } else {
+        for (int p0 = 0; p0 < total; p0 += 64) {
+            // both rounds' candidates and box loads first
+            int J[2];
+            uint32_t code[2];
+            float4 jl[2], jh[2];
 #pragma unroll
-                for (int step = 16; step >= 1; step >>= 1) {
-                    const int o2 = __shfl_sync(FULL, off, src + step);
-                    if (o2 <= p) src += step;
+            for (int h = 0; h < 2; ++h) {
+                const int p = p0 + 32 * h + lane;
+                // owner lane: the last lane whose window starts at or before p
+                int src = 0;
+                if (p0 + 32 * h + 31 < kOwnCap) {
+                    src = p < total ? s_own[p] : 0;
+                } else {
+#pragma unroll
+                    for (int step = 16; step >= 1; step >>= 1) {
+                        const int o2 = __shfl_sync(FULL, off, src + step);
+                        if (o2 <= p) src += step;
+                    }
+                }
+                J[h] = -1;
+                code[h] = 0u;
+                jl[h] = jh[h] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                if (p < total) {
+                    const int4 ci = s_ci[src];
+                    const float2 co = s_co[src];
+                    J[h] = window_cluster(A.bb, p + ci.z, ci.x, ci.y, (uint32_t)ci.w, co.x, co.y, Lz, code[h], jl[h],
+                                          jh[h]);
                 }
             }
-            const int s_off = __shfl_sync(FULL, off, src), s_va = __shfl_sync(FULL, va, src);
-            const int s_jb = __shfl_sync(FULL, jb, src), s_nj = __shfl_sync(FULL, nj, src);
-            const uint32_t s_code = __shfl_sync(FULL, code_xy, src);
-            const float s_ox = __shfl_sync(FULL, ox, src), s_oy = __shfl_sync(FULL, oy, src);
-            const int s_seg = __shfl_sync(FULL, seg, src);
-            unsigned cm = 0u;
-            int J = -1, hs = -1;
-            uint32_t code = 0u;
-            bool flag = false;
-            if (p < total) {
-                float4 jl, jh;
-                J = window_cluster(A.bb, s_va + (p - s_off), s_jb, s_nj, s_code, s_ox, s_oy, Lz, code, jl, jh);
-                if (box_gap2(lo, hi, jl, jh) < rcm2) {
-                    const int gJ = A.group == 1 ? J : A.clus_grp[J];  // groups of one cluster: the same index
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (p0 + 32 * h >= total) break;  // the whole warp
+                unsigned cm = 0u;
+                int hs = -1;
+                bool flag = false;
+                if (J[h] >= 0 && box_gap2(lo, hi, jl[h], jh[h]) < rcm2) {
+                    const int gJ = A.group == 1 ? J[h] : A.clus_grp[J[h]];  // groups of one cluster: the same index
                     const bool other = gJ != g;
                     if (!other || keep_groups(g, gJ)) {
                         if (n == 1) {
-                            cm = other || keep_in_group(c0, J, code) ? 1u : 0u;
+                            cm = other || keep_in_group(c0, J[h], code[h]) ? 1u : 0u;
                         } else {
                             for (int q = 0; q < n; ++q)
-                                if (box_gap2(s_lo[q], s_hi[q], jl, jh) < rcm2 &&
-                                    (other || keep_in_group(c0 + q, J, code)))
+                                if (box_gap2(s_lo[q], s_hi[q], jl[h], jh[h]) < rcm2 &&
+                                    (other || keep_in_group(c0 + q, J[h], code[h])))
                                     cm |= 1u << q;
                         }
                     }
                     if (cm) {
-                        const bool self = !other && code == 0u && ((cm >> (J - c0)) & 1u);
-                        hs = hset_find(s_hash, J);
+                        const bool self = !other && code[h] == 0u && ((cm >> (J[h] - c0)) & 1u);
+                        hs = hset_find(s_hash, J[h]);
                         flag = all_flag || self || hs >= 0;
                     }
                 }
-            }
-            const bool hit = cm != 0u;
-            uint2 ent = make_uint2((uint32_t)J | (code << kShiftBit) | (flag ? kExclFlag : 0u), cm);
-            // flagged entries: a mask record each, filled by its own lane
-            const bool fl = hit && flag;
-            const unsigned fb = __ballot_sync(FULL, fl);
-            int mbase = 0;
-            if (fb && lane == 0) mbase = atomicAdd(A.mask_count, __popc(fb));
-            mbase = __shfl_sync(FULL, mbase, 0);
-            if (fl) {
-                const int slot = mbase + __popc(fb & lt);
-                if (slot < A.mask_cap) {
-                    ulonglong2 *rec = A.gmask + (long long)slot * kMaxGroup;
-                    entry_masks(s_pslot, s_next, hs >= 0 ? s_head[hs] : -1, K, c0, n, cm, J, code, rec);
-                    if (all_flag) {  // the table overflowed: scan every partner
-                        for (unsigned cc = cm; cc; cc &= cc - 1u) {
-                            const int q = __ffs(cc) - 1;
-                            ulonglong2 r = rec[q];
-                            for (int t = q * kCluster * K; t < (q + 1) * kCluster * K; ++t) {
-                                const int v = s_pslot[t];
-                                if (v < 0 || ((v >> 1) / kCluster) != J) continue;
-                                const unsigned long long bit = 1ull << (((t / K) % kCluster) * kCluster + ((v >> 1) & 7));
-                                if (v & 1) r.y |= bit;
-                                else r.x |= bit;
+                const bool hit = cm != 0u;
+                uint2 ent = make_uint2((uint32_t)J[h] | (code[h] << kShiftBit) | (flag ? kExclFlag : 0u), cm);
+                // flagged entries: a mask record each, filled by its own lane
+                const bool fl = hit && flag;
+                const unsigned fb = __ballot_sync(FULL, fl);
+                if (fb) {
+                    long long slot = -1;
+                    const int q = nloc + __popc(fb & lt);
+                    if (fl && q < loc_cap) slot = loc_base + q;
+                    nloc += __popc(fb);
+                    const unsigned ob = __ballot_sync(FULL, fl && slot < 0);
+                    if (ob) {  // the group's own records are used up: the pool
+                        int pb = 0;
+                        if (lane == 0) pb = atomicAdd(A.pool_count, __popc(ob));
+                        pb = __shfl_sync(FULL, pb, 0);
+                        if (fl && slot < 0) slot = A.pool_base + pb + __popc(ob & lt);
+                    }
+                    if (fl) {
+                        if (slot < A.mask_cap) {
+                            ulonglong2 *rec = A.gmask + slot * A.group;
+                            entry_masks(s_pslot, s_link, hs >= 0 ? s_head[hs] : kLinkEnd, c0, cm, J[h], code[h], rec);
+                            if (all_flag) {  // the table overflowed: scan every partner
+                                for (unsigned ccm = cm; ccm; ccm &= ccm - 1u) {
+                                    const int q2 = __ffs(ccm) - 1;
+                                    ulonglong2 r = rec[q2];
+                                    for (int t = q2 * kCluster * K; t < (q2 + 1) * kCluster * K; ++t) {
+                                        const int v = s_pslot[t];
+                                        if (v < 0 || ((v >> 1) / kCluster) != J[h]) continue;
+                                        const unsigned long long bit =
+                                            1ull << (((t / K) % kCluster) * kCluster + ((v >> 1) & 7));
+                                        if (v & 1) r.y |= bit;
+                                        else r.x |= bit;
+                                    }
+                                    rec[q2] = r;
+                                }
                             }
-                            rec[q] = r;
+                            ent.y |= (uint32_t)slot << kMaskSlotBit;
+                        } else {
+                            atomicOr(A.status, ST_CAPACITY);
+                            ent.x &= ~kExclFlag;
                         }
                     }
-                    ent.y |= (uint32_t)slot << kMaskSlotBit;
-                } else {
-                    atomicOr(A.status, ST_CAPACITY);
-                    ent.x &= ~kExclFlag;
                 }
-            }
-            // append to the lane's segment, in lane order within each segment
-#pragma unroll
-            for (int sg = 0; sg < kListSegs; ++sg) {
-                const unsigned bs = __ballot_sync(FULL, hit && s_seg == sg);
-                if (hit && s_seg == sg) {
-                    const int q = nseg[sg] + __popc(bs & lt);
-                    if (q < seg_cap) LA[(long long)sg * seg_cap + q] = ent;
+                // entry r (in scan order) to segment r % kListSegs, position r / kListSegs
+                const unsigned bh = __ballot_sync(FULL, hit);
+                if (hit) {
+                    const int r = ntot + __popc(bh & lt);
+                    const int q = r / kListSegs;
+                    if (q < seg_cap) LA[(long long)(r % kListSegs) * seg_cap + q] = ent;
                 }
-                nseg[sg] += __popc(bs);
+                ntot += __popc(bh);
             }
         }
-        __syncwarp();  // the owner table and column list are rewritten by the next round
+        __syncwarp();  // the owner table and column lists are rewritten by the next round
     }
     if (lane < kListSegs) {
-        int m = nseg[0];
-#pragma unroll
-        for (int sg = 1; sg < kListSegs; ++sg) m = lane == sg ? nseg[sg] : m;
+        const int m = (ntot + kListSegs - 1 - lane) / kListSegs;
         A.glist_n[(long long)g * kListSegs + lane] = min(m, seg_cap);
         if (m > seg_cap) atomicOr(A.status, ST_CAPACITY);
     }
@@ -723,7 +802,7 @@ cudaError_t launch_build_lists(nb_ctx *ctx)
     GListArgs A;
     A.sys = d.sys;
     A.counts = d.counts;
-    A.mask_count = d.counts + 5;
+    A.pool_count = d.counts + 5;
     A.bb = d.bb;
     A.clus_sys = d.clus_sys;
     A.col_slot = d.col_slot;
@@ -737,12 +816,13 @@ cudaError_t launch_build_lists(nb_ctx *ctx)
     A.glist_n = d.glist_n;
     A.gmask = d.gmask;
     A.status = d.status;
+    A.pool_base = mask_pool_base(ctx->clus_cap);
     A.mask_cap = ctx->mask_cap;
     A.K = ctx->K;
     A.rcm = ctx->pp.rc + ctx->pp.list_margin;
     A.cap = ctx->list_cap;
-    A.group = ctx->group;
-    const size_t smem = sizeof(int) * kGListWarps * glist_warp_ints(ctx->K);
+    A.group = ctx->built_group;
+    const size_t smem = sizeof(int) * kGListWarps * glist_warp_ints(ctx->K, ctx->built_group);
     const int64_t blocks = std::max<int64_t>(1, (ctx->grp_cap + kGListWarps - 1) / kGListWarps);
     cudaError_t e = launch_pdl(k_glist, dim3((unsigned)blocks), dim3(kGListWarps * 32), smem, ctx->stream, A);
     if (e != cudaSuccess) return e;

@@ -437,7 +437,7 @@ __device__ __forceinline__ void tile_entry(const ForceArgs &A, const float4 *__r
     }
     const int jorigA = DEBUG ? __ldg(A.perm + (long long)J * kCluster + jb) : -1;
     const int jorigB = DEBUG ? __ldg(A.perm + (long long)J * kCluster + jb + 4) : -1;
-    const ulonglong2 *rec = SPECIAL ? A.gmask + (long long)(ent.y >> kMaskSlotBit) * kMaxGroup : nullptr;
+    const ulonglong2 *rec = SPECIAL ? A.gmask + (long long)(ent.y >> kMaskSlotBit) * G : nullptr;
     float fjAx = 0.0f, fjAy = 0.0f, fjAz = 0.0f, fjBx = 0.0f, fjBy = 0.0f, fjBz = 0.0f;
     for (unsigned cm = ent.y & 0xFFu; cm; cm &= cm - 1u) {
         const int c = __ffs(cm) - 1;
@@ -786,7 +786,7 @@ __device__ __forceinline__ void tile1_entry(const ForceArgs &A, const float4 *__
     bool inB = tile1_member<IMG>(A, ib, code, pj, Lx, Ly, Lz, dxB, dyB, dzB, r2B);
     bool s14A = false, s14B = false;
     if (SPECIAL) {  // exclusion bitmask of the tile: bit 8 i + j
-        const ulonglong2 m = A.gmask[(long long)(ent.y >> kMaskSlotBit) * kMaxGroup];
+        const ulonglong2 m = A.gmask[ent.y >> kMaskSlotBit];  // records of one cluster
         const int bA = ih * kCluster + jj, bB = bA + 4 * kCluster;
         inA = inA && !((m.x >> bA) & 1ull);
         inB = inB && !((m.x >> bB) & 1ull);
@@ -1020,7 +1020,7 @@ __device__ __forceinline__ void adj_entry(const ForceArgs &A, const AdjTables &t
         if (((code >> 2) & 3u) == 1u) { pjA.y = __fsub_rn(pjA.y, Ly); pjB.y = __fsub_rn(pjB.y, Ly); }
         if ((code >> 4) == 1u) { pjA.z = __fsub_rn(pjA.z, Lz); pjB.z = __fsub_rn(pjB.z, Lz); }
     }
-    const ulonglong2 *rec = special ? A.gmask + (long long)(ent.y >> kMaskSlotBit) * kMaxGroup : nullptr;
+    const ulonglong2 *rec = special ? A.gmask + (long long)(ent.y >> kMaskSlotBit) * G : nullptr;
     float jA[4] = {0.0f, 0.0f, 0.0f, 0.0f}, jB[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     for (unsigned cm = ent.y & 0xFFu; cm; cm &= cm - 1u) {
         const int c = __ffs(cm) - 1;

@@ -231,9 +231,14 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
 // `group` clusters, the last one partial, so at most NC / group + C; the
 // capacity covers every supported group size (groups of one cluster: NC).
 inline int64_t group_capacity(int64_t clus_cap) { return clus_cap + 1; }
-// exclusion-mask records: the self tiles (one per cluster) and the entries
-// whose cluster holds a topology partner of a group atom (a few per cluster)
-inline int64_t mask_capacity(int64_t clus_cap) { return clus_cap * kMaskRecsPerCluster + 64; }
+// exclusion-mask records (one 16-byte mask pair per cluster of the group, so
+// `group` of them per record): the self tiles (one per cluster) and the
+// entries whose cluster holds a topology partner of a group atom (a few per
+// cluster).  Group (c0, n) fills records c0 kMaskRecsPerCluster ..
+// (c0 + n) kMaskRecsPerCluster - 1, the rest come from a shared pool behind
+// them.
+inline int64_t mask_pool_base(int64_t clus_cap) { return clus_cap * kMaskRecsPerCluster; }
+inline int64_t mask_capacity(int64_t clus_cap) { return mask_pool_base(clus_cap) + clus_cap / 2 + 64; }
 
 // Launchers implemented in the .cu files (all asynchronous on ctx->stream).
 cudaError_t launch_build(nb_ctx *ctx, const float *d_pos);

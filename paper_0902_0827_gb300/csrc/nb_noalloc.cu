@@ -45,7 +45,7 @@ constexpr long long kSlots = ((long long)kMaxAtoms + (kCluster - 1) * (long long
                              kCluster * kCluster;
 constexpr long long kClus = kSlots / kCluster;
 constexpr long long kGrp = kClus + 1;                          // i-group slots (group_capacity)
-constexpr long long kMaskRecs = kClus * kMaskRecsPerCluster + 64;  // exclusion-mask records (mask_capacity)
+constexpr long long kMaskRecs = kClus * kMaskRecsPerCluster + kClus / 2 + 64;  // exclusion-mask records (mask_capacity)
 
 constexpr size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
