@@ -539,7 +539,11 @@ __global__ void __launch_bounds__(kGListWarps * 32, ACENB_GLIST_MIN_BLOCKS) k_gl
     __syncwarp();
     const int np = kCluster * n * K;
     const float inv_K = 1.0f / (float)K;
-    bool full = false;  // the partner table overflowed: flag every entry
+    bool full = false;
+    // groups of one cluster (8 K <= 128 partner entries, one batch): every
+    // lane keeps its entries (partner cluster << 7 | is14 << 6 | bit 8 a + jj)
+    // for the warp-cooperative masks
+    int pk[kPartnerBatch] = {-1, -1, -1, -1};  // the partner table overflowed: flag every entry
     for (int t0 = 0; t0 < np; t0 += kPartnerBatch * 32) {
         // the three dependent loads of kPartnerBatch rounds at a time
         int pv[kPartnerBatch];
@@ -570,6 +574,8 @@ __global__ void __launch_bounds__(kGListWarps * 32, ACENB_GLIST_MIN_BLOCKS) k_gl
                 const int a = div_small(t, K, inv_K, rr);  // group atom of entry t
                 if (hs < 0) full = true;
                 else s_link[t] = (atomicExch(&s_head[hs], t) & kLinkEnd) | (a << 16);
+                if (t0 == 0 && A.group == 1)
+                    pk[r] = (((pv[r] >> 1) / kCluster) << 7) | ((pv[r] & 1) << 6) | (a * kCluster + ((pv[r] >> 1) & 7));
             }
         }
     }
@@ -729,11 +735,48 @@ __global__ void __launch_bounds__(kGListWarps * 32, ACENB_GLIST_MIN_BLOCKS) k_gl
                         pb = __shfl_sync(FULL, pb, 0);
                         if (fl && slot < 0) slot = A.pool_base + pb + __popc(ob & lt);
                     }
+                    const bool ok = fl && slot < A.mask_cap;
+                    if (A.group == 1) {
+                        // warp-cooperative: for each flagged lane L, every lane
+                        // tests its partner entries against L's cluster and the
+                        // bits are OR-reduced over the warp
+                        for (unsigned f = fb; f; f &= f - 1u) {
+                            const int L = __ffs(f) - 1;
+                            const int JL = __shfl_sync(FULL, J[h], L);
+                            unsigned e0 = 0u, e1 = 0u, s0 = 0u, s1 = 0u;
+#pragma unroll
+                            for (int r = 0; r < kPartnerBatch; ++r) {
+                                const int v = pk[r];
+                                if (v >= 0 && (v >> 7) == JL) {
+                                    const int bit = v & 63;
+                                    const unsigned m = 1u << (bit & 31);
+                                    if (v & 64) {
+                                        if (bit < 32) s0 |= m;
+                                        else s1 |= m;
+                                    } else {
+                                        if (bit < 32) e0 |= m;
+                                        else e1 |= m;
+                                    }
+                                }
+                            }
+                            e0 = __reduce_or_sync(FULL, e0);
+                            e1 = __reduce_or_sync(FULL, e1);
+                            s0 = __reduce_or_sync(FULL, s0);
+                            s1 = __reduce_or_sync(FULL, s1);
+                            if (lane == L && ok) {
+                                unsigned long long ex = ((unsigned long long)e1 << 32) | e0;
+                                if (code[h] == 0u && J[h] == c0) ex |= kSelfTriangle;
+                                A.gmask[slot] = make_ulonglong2(ex, ((unsigned long long)s1 << 32) | s0);
+                            }
+                        }
+                    }
                     if (fl) {
-                        if (slot < A.mask_cap) {
+                        if (ok) {
                             ulonglong2 *rec = A.gmask + slot * A.group;
-                            entry_masks(s_pslot, s_link, hs >= 0 ? s_head[hs] : kLinkEnd, c0, cm, J[h], code[h], rec);
-                            if (all_flag) {  // the table overflowed: scan every partner
+                            if (A.group != 1)
+                                entry_masks(s_pslot, s_link, hs >= 0 ? s_head[hs] : kLinkEnd, c0, cm, J[h], code[h],
+                                            rec);
+                            if (all_flag && A.group != 1) {  // the table overflowed: scan every partner
                                 for (unsigned ccm = cm; ccm; ccm &= ccm - 1u) {
                                     const int q2 = __ffs(ccm) - 1;
                                     ulonglong2 r = rec[q2];
