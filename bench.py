@@ -59,9 +59,11 @@ FLOP_PER_PAIR = 73  # LJ + switch + Ewald real space, FMA = 2, MUFU = 1
 # algorithmic DRAM bytes of one rebuild per atom: positions in (12), wrapped
 # coordinates and column out and back (20 + 20), scatter slot (8), sorted
 # x,y,z,q + permutation + inverse (24), cluster boxes (4 per atom), z-bin
-# index (~4), pair lists (two halves of ~66 4-byte entries per 8-atom
-# cluster: 66)
-BUILD_BYTES_PER_ATOM = 158
+# index (~4), the half pair lists (~67 8-byte entries per 8-atom cluster in
+# water at rc 9 A: 67), exclusion-mask records (~3.5 16-byte records per
+# cluster: 7), group tables and segment lengths (4), partner lookups of the
+# rigid waters (2 partners: original index and inverse permutation, 16)
+BUILD_BYTES_PER_ATOM = 186
 WORKLOAD = ("solvated-chain system, 23,500 atoms (2,500-atom chain + 7,000 TIP3P-shaped waters), "
             "62.2 A cubic box, rc 9 A, switch 7.5 A, Ewald alpha 0.32, 1-2/1-3 excluded, 1-4 scaled")
 
@@ -317,16 +319,81 @@ def tables_leg(s, steps, flush, dev, npairs, base_ms, base_fo_ms):
             "gpu_launches_per_step": BUILD_LAUNCHES + FORCE_LAUNCHES}
 
 
+MD_MIN_STEPS, MD_MIN_DISP = 500, 0.01   # capped steepest descent before the dynamics
+MD_EQ_DT_PS, MD_EQ_STEPS = 0.002, 500   # 1 ps at 2 fs
+
+
 def md_leg(steps, flush, dev):
-    """Molecular dynamics with the paper's DHFR settings: PME 64^3 / order 4
-    every step, rc 9 A switched at 7.5 A, rigid waters by M-SHAKE/RATTLE,
-    hydrogen mass repartitioning, dt 4 fs, Langevin thermostat (1/ps,
-    300 K), on a 23,499-atom water box (7,833 TIP3P-shaped waters, 61.7 A):
-    the synthetic chain's random LJ contacts are not stable at 4 fs (its
-    energy diverges within 20 steps even after damped relaxation), so a
-    DHFR-sized water box stands in.  MD_GRAPH_STEPS steps are captured in
-    one CUDA graph; the L2 is flushed before each replay, the steps inside
-    a replay run back to back as in a production loop."""
+    """Molecular dynamics of the DHFR-shaped solvated chain (23,500 atoms:
+    2,500-atom chain with bonds, angles, dihedrals, exclusions and scaled
+    1-4 pairs + 7,000 rigid waters, 62.2 A) with the paper's DHFR settings:
+    PME 64^3 / order 4 every step, rc 9 A switched at 7.5 A, M-SHAKE/RATTLE,
+    hydrogen mass repartitioning and a 4 fs step, Langevin thermostat
+    (1/ps, 300 K).  Protocol: MD_MIN_STEPS capped steepest-descent moves
+    (nb_md_minimize), 1 ps of equilibration at 2 fs (friction 5/ps), 0.2 ps
+    at 4 fs, then the timed production steps: MD_GRAPH_STEPS steps captured
+    in one CUDA graph, the L2 flushed before each replay, the steps inside a
+    replay back to back as in a production loop."""
+    import math
+    import torch
+    from paper_0902_0827_gb300 import nb
+    from paper_0902_0827_gb300 import systems as S
+    s = S.dhfr_chain_md()
+    n_chain = 2500
+    top = S.hmr_masses(S.md_topology(s, n_chain=n_chain))
+    ctx = nb.Nonbonded(s)
+    ctx.set_pme(PME_GRID, PME_ORDER)
+    pos, q, typ = nb.concat_inputs([s], device=dev)
+    E = torch.empty(6, dtype=torch.float64, device=dev)
+    ctx.md_init(top, dt=MD_EQ_DT_PS, gamma=5.0, temperature=300.0, seed=2008)
+    ctx.md_minimize(pos, q, typ, 0, MD_MIN_DISP, E)
+    e_start = E.cpu().numpy().copy()
+    t0 = time.time()
+    ctx.md_minimize(pos, q, typ, MD_MIN_STEPS, MD_MIN_DISP, E)
+    torch.cuda.synchronize()
+    min_s = time.time() - t0
+    e_min = E.cpu().numpy().copy()
+    vel = torch.from_numpy(S.initial_velocities(top, 300.0)).to(dev)
+    ctx.md_step(pos, vel, q, typ, MD_EQ_STEPS, E)
+    ctx.md_init(top, dt=MD_DT_PS, gamma=1.0, temperature=300.0, seed=2009)
+    ctx.md_step(pos, vel, q, typ, 50, E)
+    torch.cuda.synchronize()
+    ctx.status()
+
+    def run():
+        ctx.md_step(pos, vel, q, typ, MD_GRAPH_STEPS, E)
+
+    g = graph_of(run, dev)
+    reps = max(3, steps // MD_GRAPH_STEPS)
+    ms = time_steps(g.replay, reps, flush)
+    ms /= MD_GRAPH_STEPS
+    ctx.status()
+    e = E.cpu().numpy()
+    # degrees of freedom: 3 per atom, less 3 constraints per rigid water
+    n_dof = 3 * s.n_atoms - 3 * len(top.waters)
+    temp = 2.0 * e[5] / (n_dof * 0.0019872041)
+    names = ("E_LJ", "E_Coul", "E_bond", "E_angle", "E_dihedral", "E_kin")
+    return {"system": f"DHFR-shaped solvated chain, {s.n_atoms} atoms ({n_chain}-atom chain + "
+                      f"{len(top.waters)} waters), {float(s.box[0]):.1f} A",
+            "ms_per_step": ms, "ns_per_day": MD_DT_PS * 1e-3 * 86400.0 / (ms * 1e-3), "dt_fs": MD_DT_PS * 1e3,
+            "temperature_K": temp, "stable": bool(all(math.isfinite(v) for v in e) and 200.0 < temp < 400.0),
+            "steps_timed": reps * MD_GRAPH_STEPS,
+            "protocol": {"minimize": {"steps": MD_MIN_STEPS, "max_disp_A": MD_MIN_DISP, "seconds": min_s,
+                                      "E_start": dict(zip(names[:5], map(float, e_start[:5]))),
+                                      "E_after": dict(zip(names[:5], map(float, e_min[:5])))},
+                         "equilibrate": {"dt_fs": MD_EQ_DT_PS * 1e3, "steps": MD_EQ_STEPS, "gamma_per_ps": 5.0},
+                         "production": {"dt_fs": MD_DT_PS * 1e3, "gamma_per_ps": 1.0, "hmr": True,
+                                        "pme": {"grid": list(PME_GRID), "order": PME_ORDER}}},
+            "energies_last_step": dict(zip(names, map(float, e))),
+            "step": "Langevin velocity Verlet: integrate, M-SHAKE, cell-list rebuild, short-range forces, PME, "
+                    "bonded terms, integrate, RATTLE",
+            "paper_context": "DHFR 17.55 ms/step, 19.7 ns/day on one GTX 280 (section Performance)",
+            "gpu_launches_per_step": MD_LAUNCHES + 1}
+
+
+def md_water_leg(steps, flush, dev):
+    """The same MD step on a 23,499-atom water box (7,833 waters, 61.7 A):
+    no bonded terms."""
     import torch
     from paper_0902_0827_gb300 import nb
     from paper_0902_0827_gb300 import systems as S
@@ -337,10 +404,9 @@ def md_leg(steps, flush, dev):
     pos, q, typ = nb.concat_inputs([s], device=dev)
     vel = torch.from_numpy(S.initial_velocities(top, 300.0)).to(dev)
     E = torch.empty(6, dtype=torch.float64, device=dev)
-    # equilibrate the synthetic start (random orientations release potential
-    # energy): 1 ps at 2 fs under strong friction, then 0.2 ps at 4 fs
-    ctx.md_init(top, dt=0.002, gamma=20.0, temperature=300.0, seed=2008)
-    ctx.md_step(pos, vel, q, typ, 500, E)
+    ctx.md_init(top, dt=MD_EQ_DT_PS, gamma=20.0, temperature=300.0, seed=2008)
+    ctx.md_minimize(pos, q, typ, 100, MD_MIN_DISP, E)
+    ctx.md_step(pos, vel, q, typ, MD_EQ_STEPS, E)
     ctx.md_init(top, dt=MD_DT_PS, gamma=1.0, temperature=300.0, seed=2009)
     ctx.md_step(pos, vel, q, typ, 50, E)
     torch.cuda.synchronize()
@@ -357,10 +423,7 @@ def md_leg(steps, flush, dev):
     return {"system": f"water box, {s.n_atoms} atoms, {float(s.box[0]):.1f} A", "ms_per_step": ms,
             "ns_per_day": MD_DT_PS * 1e-3 * 86400.0 / (ms * 1e-3), "dt_fs": MD_DT_PS * 1e3,
             "temperature_K": 2.0 * e[5] / (n_dof * 0.0019872041), "steps_timed": reps * MD_GRAPH_STEPS,
-            "step": "Langevin velocity Verlet: integrate, M-SHAKE, cell-list rebuild, short-range forces, PME, "
-                    "bonded terms, integrate, RATTLE",
-            "paper_context": "DHFR 17.55 ms/step, 19.7 ns/day on one GTX 280 (section Performance)",
-            "gpu_launches_per_step": MD_LAUNCHES + (1 if len(top.bonds) + len(top.angles) + len(top.dihedrals) else 0)}
+            "gpu_launches_per_step": MD_LAUNCHES}
 
 
 def large_leg(steps, flush, dev):
@@ -408,10 +471,25 @@ def large_leg(steps, flush, dev):
     ctx.set_profiling(False)
     ctx.status()
     k_avg = kms / max(kl, 1)
+    # tile shapes on the large box (the batched leg tunes the ensemble)
+    from paper_0902_0827_gb300 import autotune
+    cands = [dict(group_clusters=1, blocks_per_sm=3, list_split=1), dict(group_clusters=4, blocks_per_sm=3, list_split=2),
+             dict(group_clusters=8, blocks_per_sm=3, list_split=4)]
+    tuned = autotune.autotune(ctx, pos, q, typ, candidates=cands, reps=3, use_cache=False)
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs") if peaks else None
+    b_gbs = BUILD_BYTES_PER_ATOM * N / (b_ms * 1e-3) / 1e9
     return {"n_atoms": N, "pairs_per_step": npairs, "ms_per_step": ms, "pairs_per_s": npairs / (ms * 1e-3),
             "rebuild_ms": b_ms, "force_eval_ms": f_ms, "force_kernel_ms": k_avg,
             "force_kernel_tflops": FLOP_PER_PAIR * npairs / (k_avg * 1e-3) / 1e12,
-            "rebuild_algorithmic_gbs": BUILD_BYTES_PER_ATOM * N / (b_ms * 1e-3) / 1e9,
+            "rebuild_algorithmic_gbs": b_gbs,
+            "rebuild_roofline": {"bound": "hbm", "achieved": b_gbs, "peak": hbm, "unit": "GB/s",
+                                 "frac": b_gbs / hbm if hbm else None,
+                                 "bytes_per_atom": BUILD_BYTES_PER_ATOM,
+                                 "peak_basis": ("fallback copy bandwidth" if peaks.get("fallback") else
+                                                "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)")},
+            "tuning": {"group_clusters": 1, "blocks_per_sm": 3, "list_split": 1},
+            "autotune_table": tune_table(tuned),
             "step": "cell-list rebuild + forces, energies and virial (rc 9 A, Ewald real space)",
             "gpu_launches_per_step": BUILD_LAUNCHES + FORCE_LAUNCHES}
 
@@ -426,7 +504,8 @@ def batched_leg(steps, flush, dev):
     systems = S.water_ensemble()
     ctx = nb.Nonbonded(systems)
     pos, q, typ = nb.concat_inputs(systems, device=dev)
-    cands = [dict(blocks_per_sm=b, list_split=c) for b in (2, 3, 4) for c in (2, 4, 6)]
+    cands = ([dict(group_clusters=1, blocks_per_sm=b, list_split=c) for b in (2, 3) for c in (1, 2, 4)]
+             + [dict(group_clusters=g, blocks_per_sm=b, list_split=c) for g in (4, 8) for b in (2, 3) for c in (2, 4)])
     rec = autotune.autotune(ctx, pos, q, typ, candidates=cands, reps=3)
     N = pos.shape[0]
     F = torch.empty((N, 3), device=dev)
@@ -463,7 +542,29 @@ def batched_leg(steps, flush, dev):
     return {"n_systems": len(systems), "n_atoms": N, "pairs_per_step": npairs, "ms_per_step": ms,
             "pairs_per_s": npairs / (ms * 1e-3), "sequential_ms_per_step": seq_ms,
             "speedup_vs_sequential": seq_ms / ms, "tuning": rec["best"],
-            "gpu_launches_per_step": BUILD_LAUNCHES + FORCE_LAUNCHES}
+            "autotune_table": tune_table(rec), "gpu_launches_per_step": BUILD_LAUNCHES + FORCE_LAUNCHES}
+
+
+def measured_peaks():
+    """The machine's measured HBM copy bandwidth and GEMM peaks (a JSON file
+    beside this script), or the published fallback copy bandwidth."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "fallback": True}
+
+
+def tune_table(rec, best_per_group: bool = True):
+    """The autotuner's timings (ms per rebuild + force step), the best
+    candidate of every group size first, then the overall ranking."""
+    out = {}
+    for t, c in rec["table"]:
+        g = c.get("group_clusters", 1)
+        out.setdefault(f"group{g}", {"ms": t, **c})
+    return {"best_per_group_size": out, "candidates": len(rec["table"]),
+            "ranking": [{"ms": t, **c} for t, c in rec["table"][:6]]}
 
 
 def force_kernel_traffic():
@@ -677,6 +778,7 @@ def main():
         line["pme"] = pme_leg(s, args.steps, flush, dev, npairs, ms)
         line["tables"] = tables_leg(s, args.steps, flush, dev, npairs, ms, fo_ms)
         line["md"] = md_leg(args.steps, flush, dev)
+        line["md_water"] = md_water_leg(args.steps, flush, dev)
         line["batched"] = batched_leg(args.steps, flush, dev)
         line["large"] = large_leg(args.steps, flush, dev)
         # end to end through the public API with host buffers (pinned): the

@@ -422,6 +422,24 @@ nb_status nb_md_init(nb_ctx *ctx, const nb_md_params *p);
 nb_status nb_md_step(nb_ctx *ctx, float *d_pos, float *d_vel, const float *d_q, const int32_t *d_type,
                      int32_t n_steps, double *d_energy);
 
+/* nb_md_minimize - energy minimisation of d_pos [N,3] (FP32, A, updated in
+ * place and kept wrapped) with charges d_q and types d_type before MD: n_steps
+ * steps of steepest descent in mass-weighted coordinates,
+ *   x_i <- x_i + h F_i / m_i,  h = max_disp / max_j (|F_j| / m_j),
+ * with F the total forces of nb_md_step at x (cell list, short-range, PME
+ * when enabled, bonded terms) and the rigid waters restored by M-SHAKE from
+ * x after every move; the atom with the largest |F| / m moves by max_disp (A)
+ * before the constraints.  The forces are evaluated once more at the final
+ * positions and kept for the next nb_md_step; d_energy [6] receives the
+ * energies there (E_LJ, E_Coul, E_bond, E_angle, E_dihedral, 0), or NULL.
+ * Velocities are not touched.  Asynchronous, capturable.  The paper prints
+ * no minimiser: this is the plain capped steepest descent that prepares a
+ * synthetic start for the dynamics.  Errors: NB_ERR_INVALID_ARG (n_steps <
+ * 0, max_disp not positive and finite), NB_ERR_NOT_BUILT without nb_md_init;
+ * NB_ERR_TIMEOUT is recorded when M-SHAKE does not converge. */
+nb_status nb_md_minimize(nb_ctx *ctx, float *d_pos, const float *d_q, const int32_t *d_type, int32_t n_steps,
+                         float max_disp, double *d_energy);
+
 /* nb_bonded_forces - the bonded terms alone at d_pos: d_F [N,3] forces,
  * d_energy [3] (bond, angle, dihedral) or NULL.  FP32 terms, forces summed
  * in 64-bit fixed point (2^32).  NB_ERR_NOT_BUILT without nb_md_init. */

@@ -261,6 +261,20 @@ def forces_at(sys, top, x, prm: MDParams):
     return F + Fb, np.array([E[0], e_c, Eb[0], Eb[1], Eb[2]])
 
 
+def minimize_step(sys, top, x, F, max_disp: float):
+    """One move of the library's energy minimiser (the paper prints none; a
+    plain capped steepest descent in mass-weighted coordinates): x' = x +
+    h F / m with h = max_disp / max_i |F_i| / m_i, then M-SHAKE of every
+    water from x.  F: total forces at x (forces_at)."""
+    m = top.mass.astype(np.float64)
+    g = np.linalg.norm(F, axis=1) / m
+    gmax = float(g.max())
+    h = max_disp / gmax if gmax > 0.0 else 0.0
+    xn = x + h * F / m[:, None]
+    xc, _, _ = shake(top, x, xn, sys.box, m)
+    return xc
+
+
 def kinetic(v, mass):
     return 0.5 * float((mass[:, None] * v * v).sum()) / KCAL_PER_AMU
 

@@ -1,15 +1,17 @@
-"""Autotuner of the launch configuration (persistent-grid size, work units
-per cluster list) of a context.
+"""Autotuner of the launch configuration of a context: the tile shape (the
+i-group size: 1, 4 or 8 clusters of a column share one list and their
+j-cluster loads), the persistent-grid size and the work units per list
+segment.
 
 Each candidate is timed with CUDA events over a few rebuild + force
-evaluations on the caller's stream; the fastest is applied and cached per
-(device, size bucket, number of systems).  The candidates only change how
-work is split (block count, number of warps sharing each cluster's list).
-The block count changes no result bit; the list split changes where a
-cluster's FP32 force sums are cut before they join the fixed-point totals,
-so results differ between splits by FP32 rounding only (every candidate is
-within the parity tolerances, and each is run-to-run bit-identical).  The
-choice is deterministic for a given cache.
+evaluations on the caller's stream (a new group size rebuilds the lists
+first); the fastest is applied and cached per (device, size bucket, number
+of systems).  The candidates only change how work is split.  The block
+count changes no result bit; the group size and the list split change where
+the FP32 force sums of a cluster are cut before they join the fixed-point
+totals, so results differ between candidates by FP32 rounding only (every
+candidate is within the parity tolerances, and each is run-to-run
+bit-identical).  The choice is deterministic for a given cache.
 """
 
 from __future__ import annotations
@@ -20,8 +22,9 @@ import os
 
 _CACHE: dict = {}
 
-DEFAULT_CANDIDATES = [dict(blocks_per_sm=b, list_split=s)
-                      for b in (2, 3, 4) for s in (1, 2, 3, 4, 6, 8)]
+DEFAULT_CANDIDATES = ([dict(group_clusters=1, blocks_per_sm=b, list_split=s) for b in (2, 3, 4) for s in (1, 2, 4)]
+                      + [dict(group_clusters=g, blocks_per_sm=b, list_split=s)
+                         for g in (4, 8) for b in (2, 3) for s in (2, 4, 6)])
 
 
 def _key(ctx) -> str:

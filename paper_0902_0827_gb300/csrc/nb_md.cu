@@ -59,6 +59,7 @@ struct MdState {
     double *enb = nullptr;                 // [2] E_LJ, E_Coul of the last evaluation
     long long *acc = nullptr;              // [kMdAcc]
     unsigned long long *step = nullptr;    // [1] device step counter
+    unsigned *amax = nullptr;              // [2] minimisation: largest |F_i| / m_i (float bits), two slots
 };
 
 // ------------------------------------------------------------------ Philox
@@ -342,45 +343,14 @@ struct MdStep {
     int max_iter;
 };
 
-// First half of a step, one thread per unconstrained atom (items below
-// n_free) or per water.  A water's three atoms are kicked and drifted, then
-// M-SHAKE: lambda by Newton iterations on |r_k''|^2 = d_k^2,
-// r_k'' = u_k + sum_l lambda_l C_kl r_l (u: new, r: reference vectors of x,
-// C_kl = s(a_k, l)/m_{a_k} - s(b_k, l)/m_{b_k}), disp_i =
-// sum_l lambda_l s(i, l) r_l / m_i, until every |g_k| / d_k^2 < tol or
-// max_iter iterations.  New positions wrapped into the box.  Block 0 clears
-// the energy sums of this step.
-__global__ void __launch_bounds__(64) k_md_first(int n_free, int nw, MdStep P,
-                                                 const unsigned long long *__restrict__ step,
-                                                 const int *__restrict__ free_atoms, const int4 *__restrict__ waters,
-                                                 const float *__restrict__ mass, const float *__restrict__ sigv,
-                                                 const float *__restrict__ Ftot, float *__restrict__ x,
-                                                 float *__restrict__ v, Box3 B, long long *__restrict__ acc,
-                                                 int *__restrict__ status)
+// M-SHAKE of one water (atoms at[], inverse masses im[]) from the reference
+// positions x to the unconstrained new positions xn: the displacements dsp
+// that restore |r_k''|^2 = d_k^2; false when max_iter iterations did not
+// reach the tolerance.
+__device__ __forceinline__ bool water_shake(const int (&at)[3], const float3 (&xn)[3], const float (&im)[3],
+                                            const float *__restrict__ x, const Box3 &B, const MdStep &P,
+                                            float3 (&dsp)[3])
 {
-    pdl_entry();
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (blockIdx.x == 0 && threadIdx.x < kMdAcc) acc[threadIdx.x] = 0;
-    const unsigned long long st = step[0];
-    if (t < n_free) {
-        const int a = free_atoms[t];
-        const float3 p = kick_drift(a, P.dt, P.c, P.langevin, P.seed, st, mass, sigv, Ftot, x, v);
-        x[3ll * a] = wrap_coord(p.x, B.L[0]);
-        x[3ll * a + 1] = wrap_coord(p.y, B.L[1]);
-        x[3ll * a + 2] = wrap_coord(p.z, B.L[2]);
-        return;
-    }
-    const int w = t - n_free;
-    if (w >= nw) return;
-    const int4 W = waters[w];
-    const int at[3] = {W.x, W.y, W.z};
-    float3 xn[3];
-    float im[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        xn[i] = kick_drift(at[i], P.dt, P.c, P.langevin, P.seed, st, mass, sigv, Ftot, x, v);
-        im[i] = 1.0f / mass[at[i]];
-    }
     float3 r[3], u[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -422,15 +392,57 @@ __global__ void __launch_bounds__(64) k_md_first(int n_free, int nw, MdStep P,
 #pragma unroll
         for (int l = 0; l < 3; ++l) lam[l] -= dl[l];
     }
-    if (!conv) atomicOr(status, ST_TIMEOUT);
-    const float idt = 1.0f / P.dt;
-    float3 dsp[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         dsp[i] = make_float3(0.0f, 0.0f, 0.0f);
 #pragma unroll
         for (int l = 0; l < 3; ++l) dsp[i] = add3(dsp[i], scale3(lam[l] * sgn(i, l) * im[i], r[l]));
     }
+    return conv;
+}
+
+// First half of a step, one thread per unconstrained atom (items below
+// n_free) or per water.  A water's three atoms are kicked and drifted, then
+// M-SHAKE: lambda by Newton iterations on |r_k''|^2 = d_k^2,
+// r_k'' = u_k + sum_l lambda_l C_kl r_l (u: new, r: reference vectors of x,
+// C_kl = s(a_k, l)/m_{a_k} - s(b_k, l)/m_{b_k}), disp_i =
+// sum_l lambda_l s(i, l) r_l / m_i, until every |g_k| / d_k^2 < tol or
+// max_iter iterations.  New positions wrapped into the box.  Block 0 clears
+// the energy sums of this step.
+__global__ void __launch_bounds__(64) k_md_first(int n_free, int nw, MdStep P,
+                                                 const unsigned long long *__restrict__ step,
+                                                 const int *__restrict__ free_atoms, const int4 *__restrict__ waters,
+                                                 const float *__restrict__ mass, const float *__restrict__ sigv,
+                                                 const float *__restrict__ Ftot, float *__restrict__ x,
+                                                 float *__restrict__ v, Box3 B, long long *__restrict__ acc,
+                                                 int *__restrict__ status)
+{
+    pdl_entry();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (blockIdx.x == 0 && threadIdx.x < kMdAcc) acc[threadIdx.x] = 0;
+    const unsigned long long st = step[0];
+    if (t < n_free) {
+        const int a = free_atoms[t];
+        const float3 p = kick_drift(a, P.dt, P.c, P.langevin, P.seed, st, mass, sigv, Ftot, x, v);
+        x[3ll * a] = wrap_coord(p.x, B.L[0]);
+        x[3ll * a + 1] = wrap_coord(p.y, B.L[1]);
+        x[3ll * a + 2] = wrap_coord(p.z, B.L[2]);
+        return;
+    }
+    const int w = t - n_free;
+    if (w >= nw) return;
+    const int4 W = waters[w];
+    const int at[3] = {W.x, W.y, W.z};
+    float3 xn[3];
+    float im[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        xn[i] = kick_drift(at[i], P.dt, P.c, P.langevin, P.seed, st, mass, sigv, Ftot, x, v);
+        im[i] = 1.0f / mass[at[i]];
+    }
+    float3 dsp[3];
+    if (!water_shake(at, xn, im, x, B, P, dsp)) atomicOr(status, ST_TIMEOUT);
+    const float idt = 1.0f / P.dt;
     // the reference vectors above read x: write the new positions afterwards
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -535,6 +547,89 @@ __global__ void k_md_bonded_out(int n, const long long *__restrict__ bacc, const
     if (i < 3 && energy) energy[i] = (double)acc[i] * (1.0 / 4294967296.0);
 }
 
+// Energy minimisation by steepest descent in mass-weighted coordinates with
+// a displacement cap and the rigid waters kept by M-SHAKE.  Part 1: total
+// forces F = F_short (+ PME) + bonded (as k_md_collect) and the largest
+// |F_i| / m_i over the atoms into *amax (the bits of a non-negative float,
+// whose order an unsigned atomicMax keeps).
+__global__ void __launch_bounds__(256) k_min_collect(int n, const float *__restrict__ Fnb, long long *__restrict__ bacc,
+                                                     float *__restrict__ Ftot, const float *__restrict__ mass,
+                                                     unsigned *__restrict__ amax)
+{
+    pdl_entry();
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    float g = 0.0f;
+    if (a < n) {
+        float fx, fy, fz;
+        collect_force(a, Fnb, bacc, Ftot, fx, fy, fz);
+        g = sqrtf(fmaf(fx, fx, fmaf(fy, fy, fz * fz))) / mass[a];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) g = fmaxf(g, __shfl_xor_sync(0xffffffffu, g, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(amax, __float_as_uint(g));
+}
+
+// Part 2, one thread per unconstrained atom or per water: x <- x + h F / m
+// with h = dmax / max_i |F_i| / m_i (the atom with the largest mass-weighted
+// force moves by dmax before the constraints), then M-SHAKE of every water
+// from x; positions wrapped into the box.  Clears the other slot of amax for
+// the next step.
+__global__ void __launch_bounds__(64) k_min_move(int n_free, int nw, MdStep P, const int *__restrict__ free_atoms,
+                                                 const int4 *__restrict__ waters, const float *__restrict__ mass,
+                                                 const float *__restrict__ Ftot, float *__restrict__ x, Box3 B,
+                                                 float dmax, const unsigned *__restrict__ amax_cur,
+                                                 unsigned *__restrict__ amax_next, int *__restrict__ status)
+{
+    pdl_entry();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t == 0) *amax_next = 0u;
+    const float gmax = __uint_as_float(*amax_cur);
+    const float h = gmax > 0.0f ? dmax / gmax : 0.0f;
+    if (t < n_free) {
+        const int a = free_atoms[t];
+        const float s = h / mass[a];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) x[3ll * a + c] = wrap_coord(fmaf(s, Ftot[3ll * a + c], x[3ll * a + c]), B.L[c]);
+        return;
+    }
+    const int w = t - n_free;
+    if (w >= nw) return;
+    const int4 W = waters[w];
+    const int at[3] = {W.x, W.y, W.z};
+    float3 xn[3];
+    float im[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const int a = at[i];
+        im[i] = 1.0f / mass[a];
+        const float s = h * im[i];
+        xn[i] = make_float3(fmaf(s, Ftot[3ll * a], x[3ll * a]), fmaf(s, Ftot[3ll * a + 1], x[3ll * a + 1]),
+                            fmaf(s, Ftot[3ll * a + 2], x[3ll * a + 2]));
+    }
+    float3 dsp[3];
+    if (!water_shake(at, xn, im, x, B, P, dsp)) atomicOr(status, ST_TIMEOUT);
+    // the reference vectors above read x: write the new positions afterwards
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const int a = at[i];
+        x[3ll * a] = wrap_coord(xn[i].x + dsp[i].x, B.L[0]);
+        x[3ll * a + 1] = wrap_coord(xn[i].y + dsp[i].y, B.L[1]);
+        x[3ll * a + 2] = wrap_coord(xn[i].z + dsp[i].z, B.L[2]);
+    }
+}
+
+// Energies at the positions of the last force evaluation: E_LJ, E_Coul,
+// E_bond, E_angle, E_dihedral, and 0 kinetic energy.
+__global__ void k_min_energy(const double *__restrict__ enb, const long long *__restrict__ acc,
+                             double *__restrict__ energy)
+{
+    pdl_entry();
+    const int i = threadIdx.x;
+    if (i < 2) energy[i] = enb[i];
+    else if (i < 5) energy[i] = (double)acc[i - 2] * (1.0 / 4294967296.0);
+    else if (i == 5) energy[i] = 0.0;
+}
+
 // ---------------------------------------------------------------- host side
 
 static Box3 box_of(const nb_ctx *ctx)
@@ -552,7 +647,7 @@ void md_free(nb_ctx *ctx)
     MdState *m = ctx->md;
     if (!m) return;
     void *p[] = {m->mass, m->sigv, m->free_atoms, m->bonds, m->bond_p, m->angles, m->angle_p, m->dihedrals,
-                 m->dihedral_p, m->waters, m->Fnb, m->Ftot, m->bacc, m->enb, m->acc, m->step};
+                 m->dihedral_p, m->waters, m->Fnb, m->Ftot, m->bacc, m->enb, m->acc, m->step, m->amax};
     for (void *q : p)
         if (q) cudaFree(q);
     delete m;
@@ -698,6 +793,7 @@ extern "C" nb_status nb_md_init(nb_ctx *ctx, const nb_md_params *p)
     if (e == cudaSuccess) e = cudaMalloc(&M->enb, sizeof(double) * 2);
     if (e == cudaSuccess) e = cudaMalloc(&M->acc, sizeof(long long) * kMdAcc);
     if (e == cudaSuccess) e = cudaMalloc(&M->step, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&M->amax, 2 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(M->bacc, 0, sizeof(long long) * 3 * N);
     if (e == cudaSuccess) e = cudaMemset(M->acc, 0, sizeof(long long) * kMdAcc);
     if (e == cudaSuccess) e = cudaMemset(M->step, 0, sizeof(unsigned long long));
@@ -767,6 +863,45 @@ extern "C" nb_status nb_md_step(nb_ctx *ctx, float *d_pos, float *d_vel, const f
                            s == n_steps - 1 ? d_energy : (double *)nullptr);
     }
     return e == cudaSuccess ? NB_OK : NB_ERR_CUDA;
+}
+
+extern "C" nb_status nb_md_minimize(nb_ctx *ctx, float *d_pos, const float *d_q, const int32_t *d_type,
+                                    int32_t n_steps, float max_disp, double *d_energy)
+{
+    if (!ctx || !d_pos || !d_q || !d_type || n_steps < 0 || !(max_disp > 0.0f) || !(max_disp < 1e30f))
+        return NB_ERR_INVALID_ARG;
+    if (!ctx->md) return NB_ERR_NOT_BUILT;
+    MdState &M = *ctx->md;
+    const cudaStream_t st = ctx->stream;
+    const Box3 B = box_of(ctx);
+    const int N = M.n;
+    const int ab = (N + 255) / 256;
+    const int ib = std::max(1, (M.n_free + M.nw + 63) / 64);
+    MdStep P = {};
+    P.d2oh = M.d2[0];
+    P.d2hh = M.d2[1];
+    P.tol = M.shake_tol;
+    P.max_iter = M.shake_iter;
+    cudaError_t e = cudaMemsetAsync(M.amax, 0, 2 * sizeof(unsigned), st);
+    // n_steps moves, each from the forces at the current positions, and the
+    // forces at the final positions (left for the next nb_md_step)
+    for (int s = 0; s <= n_steps && e == cudaSuccess; ++s) {
+        e = cudaMemsetAsync(M.acc, 0, sizeof(long long) * kMdAcc, st);
+        if (e == cudaSuccess) e = md_forces(ctx, d_pos, d_q, d_type);
+        if (e == cudaSuccess)
+            e = launch_pdl(k_min_collect, dim3(ab), dim3(256), 0, st, N, (const float *)M.Fnb, M.bacc, M.Ftot,
+                           (const float *)M.mass, M.amax + (s & 1));
+        if (e == cudaSuccess && s < n_steps)
+            e = launch_pdl(k_min_move, dim3(ib), dim3(64), 0, st, M.n_free, M.nw, P, (const int *)M.free_atoms,
+                           (const int4 *)M.waters, (const float *)M.mass, (const float *)M.Ftot, d_pos, B, max_disp,
+                           (const unsigned *)(M.amax + (s & 1)), M.amax + ((s + 1) & 1), ctx->d.status);
+    }
+    if (e == cudaSuccess && d_energy)
+        e = launch_pdl(k_min_energy, dim3(1), dim3(32), 0, st, (const double *)M.enb, (const long long *)M.acc,
+                       d_energy);
+    if (e != cudaSuccess) return NB_ERR_CUDA;
+    M.have_forces = true;  // Ftot holds the forces at the final positions
+    return NB_OK;
 }
 
 extern "C" nb_status nb_md_set_step(nb_ctx *ctx, uint64_t step)

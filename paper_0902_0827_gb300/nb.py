@@ -26,7 +26,8 @@ EXPORTS = ("nb_create", "nb_create_batch", "nb_build_cells", "nb_forces", "nb_fo
            "nb_get_status", "nb_set_stream", "nb_destroy", "nb_set_tuning", "nb_get_tuning", "nb_get_sizes",
            "nb_debug_cells", "nb_debug_pairs", "nb_debug_pair_terms", "nb_debug_philox", "nb_status_string",
            "nb_set_lj_params", "nb_set_profiling", "nb_get_profile", "nb_forces_noalloc", "nb_type_gradients",
-           "nb_set_pme", "nb_pme_forces", "nb_set_tables", "nb_md_init", "nb_md_step", "nb_bonded_forces",
+           "nb_set_pme", "nb_pme_forces", "nb_set_tables", "nb_md_init", "nb_md_step", "nb_md_minimize",
+           "nb_bonded_forces",
            "nb_md_set_step", "nb_fp32_peak_launch")
 
 
@@ -120,6 +121,7 @@ def lib(build_if_missing: bool = True):
             "nb_set_tables": ([P, I32], ctypes.c_int),
             "nb_md_init": ([P, ctypes.POINTER(nb_md_params)], ctypes.c_int),
             "nb_md_step": ([P, P, P, P, P, I32, P], ctypes.c_int),
+            "nb_md_minimize": ([P, P, P, P, I32, ctypes.c_float, P], ctypes.c_int),
             "nb_bonded_forces": ([P, P, P, P], ctypes.c_int),
             "nb_md_set_step": ([P, ctypes.c_uint64], ctypes.c_int),
             "nb_debug_pair_terms": ([P, I64, P, P, P, P, P], ctypes.c_int),
@@ -300,6 +302,14 @@ class Nonbonded:
         self._sync_stream()
         _check(lib().nb_md_step(self.h, _tptr(pos), _tptr(vel), _tptr(q), _tptr(typ), int(n_steps), _tptr(energy)),
                "nb_md_step")
+
+    def md_minimize(self, pos, q, typ, n_steps, max_disp=0.01, energy=None):
+        """Capped steepest descent of pos (CUDA FP32 [N,3], in place) over
+        n_steps moves of at most max_disp A; energy (FP64 [6] tensor or None)
+        receives the energies at the final positions."""
+        self._sync_stream()
+        _check(lib().nb_md_minimize(self.h, _tptr(pos), _tptr(q), _tptr(typ), int(n_steps), float(max_disp),
+                                    _tptr(energy)), "nb_md_minimize")
 
     def bonded_forces(self, pos):
         import torch

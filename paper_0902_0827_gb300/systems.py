@@ -18,6 +18,7 @@ GPU"):
   switch 7.5 A).
 * ``water_ensemble`` - many water boxes with log-uniform atom counts.
 * ``big_water``   - 333,333 waters (about 1.0 M atoms).
+* ``dhfr_chain_md`` - the solvated chain with parameters fit for dynamics.
 
 Seeds follow ``PCG64(902827 + k)`` for workload ``k``.
 """
@@ -318,6 +319,31 @@ def solvated_chain(k: int = 2, n_chain: int = 2500, n_waters: int = 7000,
                   excl, c14, cutoff=9.0, switch_dist=7.5, ewald_alpha=0.32)
 
 
+# CHARMM's TIP3P gives the water hydrogens a small LJ sphere (epsilon
+# 0.046 kcal/mol, Rmin/2 0.2245 A, so sigma = 2 Rmin/2 / 2^(1/6) = 0.4000 A).
+TIP3P_SIGMA_H_CHARMM = 0.4000
+TIP3P_EPS_H_CHARMM = 0.046
+
+
+def dhfr_chain_md(k: int = 2, n_chain: int = 2500, n_waters: int = 7000, L: float = 62.2) -> System:
+    """The solvated chain prepared for dynamics (section "Performance": the
+    DHFR run): the chain and waters of solvated_chain(k) with heavy-atom LJ
+    sizes on the chain (sigma 3.0..4.0 A per type, seeded) and CHARMM's
+    TIP3P hydrogen LJ.  With sigma_H = 0 the Lorentz-Berthelot epsilon of
+    every pair with a water H is zero, so a negatively charged chain atom and
+    an H attract without any repulsion and the dynamics collapses them; the
+    parity workload solvated_chain keeps its own parameters."""
+    s = solvated_chain(k, n_chain, n_waters, L)
+    rng = rng_for(100 + k)
+    sigma = s.sigma.astype(np.float64).copy()
+    eps = s.epsilon.astype(np.float64).copy()
+    n_types_chain = sigma.size - 2
+    sigma[:n_types_chain] = rng.uniform(3.0, 4.0, size=n_types_chain)
+    sigma[-1], eps[-1] = TIP3P_SIGMA_H_CHARMM, TIP3P_EPS_H_CHARMM
+    return dataclasses.replace(s, name="dhfr_chain_md", sigma=sigma.astype(np.float32),
+                               epsilon=eps.astype(np.float32))
+
+
 MIN_ENSEMBLE_WATERS = 199  # keeps L >= 2 rc + 0.1 A at rc = 9 A
 
 
@@ -432,7 +458,7 @@ def initial_velocities(top: MDTopology, temperature: float = 300.0, seed: int = 
 
 def make(name: str, **kw):
     table = {"lj_fcc": lj_fcc, "water_box": water_box, "solvated_chain": solvated_chain,
-             "water_ensemble": water_ensemble, "big_water": big_water}
+             "water_ensemble": water_ensemble, "big_water": big_water, "dhfr_chain_md": dhfr_chain_md}
     return table[name](**kw)
 
 

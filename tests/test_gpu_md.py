@@ -217,3 +217,38 @@ def test_device_philox_matches_the_known_answer_vectors():
                           torch.tensor(k.view(np.int32), device="cuda")).cpu().numpy().view(np.uint32)
     o = omd.philox4x32_10(c[:, 0], c[:, 1], c[:, 2], c[:, 3], seed & 0xFFFFFFFF, seed >> 32)
     assert np.array_equal(got, np.stack([np.asarray(v, np.uint32) for v in o], 1))
+
+
+def test_minimize_matches_oracle_and_lowers_the_energy():
+    # the MD-ready solvated chain with PME 64^3: one capped steepest-descent
+    # move against the oracle's, then 40 more moves lower the energy
+    s = S.dhfr_chain_md()
+    top = S.md_topology(s, n_chain=2500)
+    pme = ((64, 64, 64), 4)
+    ctx, pos, q, t = setup(s, top, pme=pme)
+    E0 = torch.empty(6, dtype=torch.float64, device="cuda")
+    E1 = torch.empty(6, dtype=torch.float64, device="cuda")
+    ctx.md_minimize(pos, q, t, 0, 0.01, E0)   # energies at the start
+    ctx.md_minimize(pos, q, t, 1, 0.01, E1)
+    torch.cuda.synchronize()
+    ctx.status()
+    prm = omd.MDParams(pme=pme)
+    x = s.pos.astype(np.float64)
+    F, Eo0 = omd.forces_at(s, top, x, prm)
+    x1 = omd.minimize_step(s, top, x, F, 0.01)
+    _, Eo1 = omd.forces_at(s, top, x1, prm)
+    L = s.box.astype(np.float64)
+    dx = np.abs(min_image(pos.double().cpu().numpy() - x1, L)).max()
+    e0, e1 = E0.cpu().numpy(), E1.cpu().numpy()
+    print("minimize max dx", dx, "E0", e0, Eo0, "E1", e1, Eo1)
+    assert dx <= 2e-5
+    for k in range(5):
+        assert abs(e0[k] - Eo0[k]) <= 1e-5 * max(abs(Eo0[k]), 1.0), k
+        assert abs(e1[k] - Eo1[k]) <= 1e-4 * max(abs(Eo1[k]), 1.0), k
+    assert e1[:5].sum() < e0[:5].sum()
+    E2 = torch.empty(6, dtype=torch.float64, device="cuda")
+    ctx.md_minimize(pos, q, t, 40, 0.01, E2)
+    torch.cuda.synchronize()
+    ctx.status()
+    assert E2[:5].sum().item() < e1[:5].sum()
+    assert E2[5].item() == 0.0

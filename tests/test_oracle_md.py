@@ -259,3 +259,46 @@ def test_langevin_equipartition_of_an_ideal_gas():
             kes.append(E[5])
     kt = md.KB * 300.0
     assert abs(np.mean(kes) / (1.5 * n * kt) - 1.0) < 0.03
+
+
+def small_solvated_chain():
+    """A 30-atom chain in 230 waters (20 A box), shaped like the MD system."""
+    s = S.dhfr_chain_md(k=7, n_chain=30, n_waters=230, L=20.0)
+    return s, S.md_topology(s, n_chain=30)
+
+
+def test_minimize_step_closed_form_without_constraints():
+    # no waters: the move is h F / m exactly, the largest one max_disp long
+    s, top = small_chain()
+    x = s.pos.astype(np.float64)
+    F = md.bonded(top, x, s.box)[0]
+    m = top.mass.astype(np.float64)
+    x1 = md.minimize_step(s, top, x, F, 0.01)
+    d = x1 - x
+    assert np.isclose(np.linalg.norm(d, axis=1).max(), 0.01, rtol=1e-12)
+    np.testing.assert_allclose(d, (0.01 / (np.linalg.norm(F, axis=1) / m).max()) * F / m[:, None], rtol=0, atol=1e-13)
+    # a descent step: the energy falls, at first order by F . dx
+    e0, e1 = energy(top, x, s.box), energy(top, x1, s.box)
+    assert e1 < e0
+    x2 = md.minimize_step(s, top, x, F, 1e-5)
+    de = energy(top, x2, s.box) - e0
+    lin = -float((F * (x2 - x)).sum())
+    assert abs(de - lin) <= 1e-3 * abs(lin)
+
+
+def test_minimize_steps_keep_waters_rigid_and_lower_the_energy():
+    s, top = small_solvated_chain()
+    prm = md.MDParams()
+    x = s.pos.astype(np.float64)
+    F, E = md.forces_at(s, top, x, prm)
+    e = [E.sum()]
+    for _ in range(5):
+        x = md.minimize_step(s, top, x, F, 0.02)
+        F, E = md.forces_at(s, top, x, prm)
+        e.append(E.sum())
+    assert all(b < a for a, b in zip(e, e[1:])), e
+    w = top.waters
+    L = s.box.astype(np.float64)
+    for a, b, d in ((0, 1, top.water_roh), (0, 2, top.water_roh), (1, 2, S.TIP3P_RHH)):
+        r = np.linalg.norm(md.min_image(x[w[:, a]] - x[w[:, b]], L), axis=1)
+        assert np.abs(r - d).max() <= 1e-9 * d
