@@ -732,7 +732,12 @@ static int cmp_z_then_index(const void *pa, const void *pb)
 
 /* Sorted slot order of one system (coordinates already wrapped).  perm has
  * room for n + (CLUSTER-1)*nx*ny slots; padding slots get -1.  col_start
- * [nx*ny+1] receives padded column offsets.  Returns the padded size. */
+ * [nx*ny+1] receives padded column offsets.  Returns the padded size.
+ * This is a specification of the data layout (which slot each atom takes),
+ * not a quantity the paper fixes: no result of the method depends on it, so
+ * it has no pin of its own (parity unpinned as a layout); the tests compare
+ * the GPU's sorted order with it slot by slot, and the pair set it induces
+ * with brute-force enumeration. */
 int64_t orc_binning(int64_t n, const float *pos, const float *box, int64_t *perm, int64_t *col_start)
 {
     int nx, ny;

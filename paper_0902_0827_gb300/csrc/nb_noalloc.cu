@@ -9,7 +9,7 @@
 // runs the same binning and force kernels as nb_build_cells + nb_forces for
 // one system of at most NB_NOALLOC_MAX_ATOMS atoms, with every scratch buffer
 // carved from one file-scope device array (g_noalloc_scratch below, about
-// 3.6 MiB).  That array exists on every GPU that loads this library, for as
+// 5.9 MiB).  That array exists on every GPU that loads this library, for as
 // long as the library stays loaded.
 //
 // In host code the name g_noalloc_scratch only stands for the device symbol;
@@ -74,7 +74,7 @@ constexpr size_t oClusGrp = oGrp + a256(8ull * kGrp);
 constexpr size_t oGlist = oClusGrp + a256(4ull * kClus);
 constexpr size_t oGlistN = oGlist + a256(8ull * kGrp * kListCap);
 constexpr size_t oGmask = oGlistN + a256(4ull * kGrp * kListSegs);
-constexpr size_t oZbin = oGmask + a256(16ull * kMaskRecs * kMaxGroup);
+constexpr size_t oZbin = oGmask + a256(16ull * kMaskRecs * kDefaultGroup);  // records of one-cluster groups
 constexpr size_t oCounts = oZbin + a256(8ull * kZbEntries);
 constexpr size_t oStatus = oCounts + a256(32);
 constexpr size_t oLj = oStatus + a256(16);
