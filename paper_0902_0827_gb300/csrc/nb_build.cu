@@ -193,12 +193,35 @@ __device__ __forceinline__ void rank_keys(const unsigned long long *skey, int n,
     }
 }
 
-// A3b: one block per column: rank sort by (z, atom index), write the sorted
-// slot arrays and padding, the cluster bounding boxes and the column's z-bin
+// Sort the P (a power of two) shared keys ascending by a bitonic network:
+// log2(P) (log2(P) + 1) / 2 compare-exchange stages of P / 2 pairs each.
+__device__ void bitonic_sort(unsigned long long *skey, int P)
+{
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < (P >> 1); i += blockDim.x) {
+                const int l = 2 * i - (i & (j - 1)), r = l + j;  // the pair (l, l + j), l with bit j clear
+                const unsigned long long a = skey[l], b = skey[r];
+                if ((a > b) == ((l & k) == 0)) {
+                    skey[l] = b;
+                    skey[r] = a;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+constexpr int kRankSortMax = 256;  // columns up to this many atoms are rank-sorted (no barriers)
+
+// A3b: one block per column: sort by (z, atom index), write the sorted slot
+// arrays and padding, the cluster bounding boxes and the column's z-bin
 // index (the clusters are z-sorted, so their z_lo and z_hi never decrease).
-// Columns of up to kSortSmem atoms sort from shared memory: every thread
-// holds up to kSortPer keys and counts, per broadcast key, how many are
-// smaller.
+// Columns of up to kSortSmem atoms sort from shared memory: up to
+// kRankSortMax atoms by rank (every thread holds up to kSortPer keys and
+// counts, per broadcast key, how many are smaller: n^2 compares), longer
+// ones by a bitonic network (n log^2 n).  The keys are unique, so both give
+// the same order.
 __global__ void __launch_bounds__(kSortThreads) k_colsort(
     const int *__restrict__ col_count, const int *__restrict__ col_slot, const int *__restrict__ col_sys,
     const SysDesc *__restrict__ sys, const int *__restrict__ stage, const float4 *__restrict__ wpos,
@@ -215,7 +238,29 @@ __global__ void __launch_bounds__(kSortThreads) k_colsort(
     const int base = col_slot[c];
     const int npad = (n + kCluster - 1) / kCluster * kCluster;
     const bool small = n <= kSortSmem;
-    if (small) {
+    if (small && n > kRankSortMax) {
+        int P = 1;
+        while (P < n) P <<= 1;
+        for (int k = tid; k < P; k += blockDim.x) {
+            unsigned long long key = ~0ull;  // padding sorts last
+            if (k < n) {
+                const int a = stage[base + k];
+                key = zkey(wpos[a].z, a);
+            }
+            skey[k] = key;
+        }
+        __syncthreads();
+        bitonic_sort(skey, P);
+        for (int k = tid; k < n; k += blockDim.x) {
+            const int a = (int)(unsigned)(skey[k] & 0xffffffffull);
+            const float4 pa = wpos[a];
+            const int slot = base + k;
+            perm[slot] = a;
+            inv[a] = slot;
+            xyzq[slot] = make_float4(pa.x, pa.y, pa.z, 0.0f);
+            sp[k] = pa;
+        }
+    } else if (small) {
         const int nper = (n + kSortThreads - 1) / kSortThreads;
         unsigned long long key[kSortPer];
         float4 p[kSortPer];
@@ -497,7 +542,7 @@ struct GListArgs {
 
 constexpr int kGListWarps = 4;  // groups (warps) per block of the list kernel
 #ifndef ACENB_GLIST_MIN_BLOCKS
-#define ACENB_GLIST_MIN_BLOCKS 6  // resident blocks per SM the register budget allows
+#define ACENB_GLIST_MIN_BLOCKS 7  // resident blocks per SM the register budget allows (72 registers)
 #endif
 constexpr int kPartnerBatch = 4;  // rounds of partner loads in flight
 

@@ -818,7 +818,7 @@ __device__ __forceinline__ void tile1_entry(const ForceArgs &A, const float4 *__
     }
     const float fc = ih == 0 ? fjx : (ih == 1 ? fjy : fjz);
     const long long fv = tile_fixed(fc, ovf);  // every lane (lane ih = 3 holds z again): no branch
-    if (ih < 3 && fv != 0) atomicAdd((unsigned long long *)&A.facc[24ll * J + 3 * jj + ih], (unsigned long long)fv);
+    if (ih < 3) atomicAdd((unsigned long long *)&A.facc[24ll * J + 3 * jj + ih], (unsigned long long)fv);
     if (VIRIAL && IMG && ih == 0) {
         const uint32_t cx = code & 3u, cy = (code >> 2) & 3u, cz = code >> 4;
         const float sx = cx == 1u ? -Lx : (cx == 2u ? Lx : 0.0f);

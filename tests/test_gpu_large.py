@@ -39,3 +39,21 @@ def test_million_atom_water_box_full_parity():
     parity.check_energy(case, E, Eo, Es, bars=(parity.E_REL, "floor", "floor"),
                         notes=("", "water Coulomb sum cancels", "water Coulomb sum cancels"), Eq=Eq)
     parity.check_virial(case, W, Wo)
+
+
+@pytest.mark.parametrize("n_waters", [100_000, 333_333])
+def test_long_columns_sort_bit_exact(n_waters):
+    # columns of about 8 nx atoms: 264 (100,000 waters: columns on both
+    # sides of the 256-atom switch from rank sort to the bitonic network in
+    # one build) and 400 (the 1 M-atom box: all bitonic)
+    s = S.big_water() if n_waters == 333_333 else S._water_system(S.rng_for(44), n_waters, "w100k")
+    ctx = nb.Nonbonded(s)
+    pos, q, t = nb.concat_inputs([s])
+    ctx.build(pos)
+    perm, cs = ctx.debug_cells()
+    ctx.status()
+    operm, ocs, _ = oracle.binning(s.pos, s.box)
+    sizes = np.diff(ocs)
+    print("column sizes", sizes.min(), sizes.max())
+    assert np.array_equal(cs, ocs)
+    assert np.array_equal(perm.astype(np.int64), operm)
