@@ -81,6 +81,10 @@ def parse():
     ap.add_argument("--tables-only", action="store_true",
                     help="time only the step with tabulated radial functions (for profiling)")
     ap.add_argument("--md-only", action="store_true", help="time only the MD leg (for profiling)")
+    ap.add_argument("--md-prep-steps", type=int, default=None,
+                    help="minimiser moves and 2 fs equilibration steps before the timed MD steps "
+                         f"(default {MD_MIN_STEPS} each; profiling runs use fewer so that a launch list "
+                         "reaches the production steps)")
     ap.add_argument("--large-only", action="store_true", help="time only the 1 M-atom leg (for profiling)")
     ap.add_argument("--adjoint-only", action="store_true", help="time only the adjoint leg (for profiling)")
     ap.add_argument("--peak", action="store_true", help="only measure the FP32 FMA peak and print it")
@@ -323,7 +327,7 @@ MD_MIN_STEPS, MD_MIN_DISP = 500, 0.01   # capped steepest descent before the dyn
 MD_EQ_DT_PS, MD_EQ_STEPS = 0.002, 500   # 1 ps at 2 fs
 
 
-def md_leg(steps, flush, dev):
+def md_leg(steps, flush, dev, prep_steps=None):
     """Molecular dynamics of the DHFR-shaped solvated chain (23,500 atoms:
     2,500-atom chain with bonds, angles, dihedrals, exclusions and scaled
     1-4 pairs + 7,000 rigid waters, 62.2 A) with the paper's DHFR settings:
@@ -349,12 +353,14 @@ def md_leg(steps, flush, dev):
     ctx.md_minimize(pos, q, typ, 0, MD_MIN_DISP, E)
     e_start = E.cpu().numpy().copy()
     t0 = time.time()
-    ctx.md_minimize(pos, q, typ, MD_MIN_STEPS, MD_MIN_DISP, E)
+    n_min = MD_MIN_STEPS if prep_steps is None else prep_steps
+    n_eq = MD_EQ_STEPS if prep_steps is None else prep_steps
+    ctx.md_minimize(pos, q, typ, n_min, MD_MIN_DISP, E)
     torch.cuda.synchronize()
     min_s = time.time() - t0
     e_min = E.cpu().numpy().copy()
     vel = torch.from_numpy(S.initial_velocities(top, 300.0)).to(dev)
-    ctx.md_step(pos, vel, q, typ, MD_EQ_STEPS, E)
+    ctx.md_step(pos, vel, q, typ, n_eq, E)
     ctx.md_init(top, dt=MD_DT_PS, gamma=1.0, temperature=300.0, seed=2009)
     ctx.md_step(pos, vel, q, typ, 50, E)
     torch.cuda.synchronize()
@@ -378,10 +384,10 @@ def md_leg(steps, flush, dev):
             "ms_per_step": ms, "ns_per_day": MD_DT_PS * 1e-3 * 86400.0 / (ms * 1e-3), "dt_fs": MD_DT_PS * 1e3,
             "temperature_K": temp, "stable": bool(all(math.isfinite(v) for v in e) and 200.0 < temp < 400.0),
             "steps_timed": reps * MD_GRAPH_STEPS,
-            "protocol": {"minimize": {"steps": MD_MIN_STEPS, "max_disp_A": MD_MIN_DISP, "seconds": min_s,
+            "protocol": {"minimize": {"steps": n_min, "max_disp_A": MD_MIN_DISP, "seconds": min_s,
                                       "E_start": dict(zip(names[:5], map(float, e_start[:5]))),
                                       "E_after": dict(zip(names[:5], map(float, e_min[:5])))},
-                         "equilibrate": {"dt_fs": MD_EQ_DT_PS * 1e3, "steps": MD_EQ_STEPS, "gamma_per_ps": 5.0},
+                         "equilibrate": {"dt_fs": MD_EQ_DT_PS * 1e3, "steps": n_eq, "gamma_per_ps": 5.0},
                          "production": {"dt_fs": MD_DT_PS * 1e3, "gamma_per_ps": 1.0, "hmr": True,
                                         "pme": {"grid": list(PME_GRID), "order": PME_ORDER}}},
             "energies_last_step": dict(zip(names, map(float, e))),
@@ -663,7 +669,7 @@ def main():
         elif args.pme_only:
             print(json.dumps({"pme": pme_leg(s, args.steps, flush, dev, 0, 0.0)}))
         elif args.md_only:
-            print(json.dumps({"md": md_leg(args.steps, flush, dev)}))
+            print(json.dumps({"md": md_leg(args.steps, flush, dev, args.md_prep_steps)}))
         else:
             print(json.dumps({"tables": tables_leg(s, args.steps, flush, dev, 0, float("nan"), float("nan"))}))
         return 0

@@ -49,6 +49,7 @@ struct PmeGeom {
 };
 
 constexpr int kSeriesTerms = 12;
+constexpr int kErfxTerms = 26;  // erf(x)/x series terms for x^2 <= 4 (last term below 4e-13 of the sum)
 
 struct PmeCorr {
     float ke, alpha, one_m_s14;  // Coulomb constant, Ewald alpha, 1 - s14_coul
@@ -60,7 +61,52 @@ struct PmeCorr {
     // erf and of x exp(-x^2); used for x < 1, where the direct difference
     // loses digits
     float series[kSeriesTerms];
+    // erf(x)/x = sum_n e_n x^(2n), e_n = (2/sqrt(pi)) (-1)^n / (n! (2n+1)), as
+    // (hi, lo) pairs, and alpha^2 as a pair: the pair energies in
+    // double-FP32 arithmetic (x^2 = alpha^2 r^2 needs no square root)
+    float2 erfx[kErfxTerms];
+    float2 a2;
 };
+
+// Double-FP32 arithmetic (Dekker 1971; Knuth, TAOCP vol. 2): a value is
+// hi + lo, about 48 significant bits.  two_sum and two_prod give the exact
+// rounding error of a sum and (by FMA) of a product; the intrinsics keep the
+// compiler from contracting or reordering them.
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DF df_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+
+__device__ __forceinline__ DF df_fast_two_sum(float a, float b)  // |a| >= |b| or a = 0
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ DF df_add(DF a, DF b)
+{
+    const DF s = df_two_sum(a.hi, b.hi);
+    return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ DF df_mul(DF a, DF b)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    const float e = __fmaf_rn(a.hi, b.hi, -p);
+    return df_fast_two_sum(p, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e)));
+}
+
+__device__ __forceinline__ DF df_mul_f(DF a, float b)
+{
+    const float p = __fmul_rn(a.hi, b);
+    return df_fast_two_sum(p, __fmaf_rn(a.lo, b, __fmaf_rn(a.hi, b, -p)));
+}
 
 struct PmeState {
     int K[3] = {0, 0, 0};
@@ -485,21 +531,42 @@ __global__ void __launch_bounds__(256) k_pme_gather(PmeGeom g, PmeCorr cc, int s
                     fy += f1;
                     fz += f2;
                     if (j > a) {
-                        // The pair's energy -qq erf(alpha r)/r in FP64 (from the FP32
-                        // inputs, exactly converted): these corrections sum to about
-                        // 80 times the total Coulomb energy (they cancel the self
-                        // term), and the rigid waters repeat the same distances, so
-                        // FP32 rounding would add up coherently (2.7e-8 of the sum,
-                        // 2e-6 of the total on the solvated chain).  A few
-                        // partners per atom: cheap even at the FP64 rate.
-                        const double dd0 = ((double)xa.x - (double)xj.x) + (double)sh[0] * (double)cc.L[0];
-                        const double dd1 = ((double)xa.y - (double)xj.y) + (double)sh[1] * (double)cc.L[1];
-                        const double dd2 = ((double)xa.z - (double)xj.z) + (double)sh[2] * (double)cc.L[2];
-                        const double r2d = dd0 * dd0 + dd1 * dd1 + dd2 * dd2;
-                        const double qqd = (double)wgt * (double)cc.ke * (double)qa * (double)q[j];
-                        const double rd = sqrt(r2d);
-                        const double ed = r2d == 0.0 ? -qqd * 2.0 * (double)cc.alpha * 0.56418958354775628
-                                                     : -qqd * erf((double)cc.alpha * rd) / rd;
+                        // The pair's energy -qq erf(alpha r)/r = -qq alpha erf(x)/x,
+                        // x^2 = alpha^2 r^2, in double-FP32 arithmetic from the exact
+                        // displacement of the FP32 inputs: these corrections sum to
+                        // about 80 times the total Coulomb energy (they cancel the
+                        // self term), and the rigid waters repeat the same distances,
+                        // so FP32 rounding would add up coherently (2.7e-8 of the
+                        // sum, 2e-6 of the total on the solvated chain).  Partners
+                        // beyond 2 / alpha (where the series needs more terms) take
+                        // FP64, which is slow on this GPU but rare.
+                        DF r2df = {0.0f, 0.0f};
+                        double dd[3];
+#pragma unroll
+                        for (int ax = 0; ax < 3; ++ax) {
+                            const float xi = ax == 0 ? xa.x : (ax == 1 ? xa.y : xa.z);
+                            const float xo = ax == 0 ? xj.x : (ax == 1 ? xj.y : xj.z);
+                            DF da = df_two_sum(xi, -xo);  // exact
+                            if (sh[ax] != 0.0f) da = df_add(da, DF{sh[ax] * cc.L[ax], 0.0f});
+                            r2df = df_add(r2df, df_mul(da, da));
+                            dd[ax] = (double)da.hi + (double)da.lo;
+                        }
+                        const DF x2 = df_mul(DF{cc.a2.x, cc.a2.y}, r2df);
+                        DF kq = df_mul_f(df_mul_f(df_mul_f(DF{cc.ke, 0.0f}, qa), q[j]), wgt);
+                        kq = df_mul_f(kq, cc.alpha);
+                        double ed;
+                        if (x2.hi <= 4.0f) {
+                            DF S = {cc.erfx[kErfxTerms - 1].x, cc.erfx[kErfxTerms - 1].y};
+#pragma unroll 1
+                            for (int t = kErfxTerms - 2; t >= 0; --t)
+                                S = df_add(df_mul(S, x2), DF{cc.erfx[t].x, cc.erfx[t].y});
+                            const DF e = df_mul(kq, S);
+                            ed = -((double)e.hi + (double)e.lo);
+                        } else {
+                            const double rd = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+                            const double qqd = (double)wgt * (double)cc.ke * (double)qa * (double)q[j];
+                            ed = -qqd * erf((double)cc.alpha * rd) / rd;
+                        }
                         const float vs = (float)kVirScale;
                         v[1] += __double2ll_rn(ed * kFixScale);
                         v[2] += __float2ll_rn(d[0] * f0 * vs);
@@ -725,6 +792,17 @@ extern "C" nb_status nb_set_pme(nb_ctx *ctx, const nb_pme_params *p)
             fact *= (double)(n + 1);
             cc.series[n] = (float)((n % 2 ? -2.0 : 2.0) * (double)(n + 1) / ((double)(2 * n + 3) * fact));
         }
+    }
+    {
+        double fact = 1.0;  // n!
+        for (int n = 0; n < kErfxTerms; ++n) {
+            if (n > 0) fact *= (double)n;
+            const double c = (n % 2 ? -2.0 : 2.0) / (sqrt(M_PI) * fact * (double)(2 * n + 1));
+            const float hi = (float)c;
+            cc.erfx[n] = make_float2(hi, (float)(c - (double)hi));
+        }
+        const double a2 = (double)ctx->pp.alpha * (double)ctx->pp.alpha;  // exact: 24-bit alpha squared
+        cc.a2 = make_float2((float)a2, (float)(a2 - (double)(float)a2));
     }
     for (int a = 0; a < 3; ++a) {
         cc.L[a] = Lf[a];
