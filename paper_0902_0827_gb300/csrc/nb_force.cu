@@ -1215,6 +1215,209 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_adjoint(ForceArgs A, int par
         if (tacc[k]) atomicAdd((unsigned long long *)&A.tab_acc[k], tacc[k]);
 }
 
+// Adjoint kernel for i-groups of one cluster (k_adjoint1): the structure of
+// k_force1.  Lane = jj + 8 ih holds j atom jj of the entry's cluster J and i
+// atoms ih and ih + 4 of the unit's cluster, whose positions, dL/dF and
+// type rows stay in registers for the whole unit; the i-side terms (dL/dx_i,
+// dL/dq_i) accumulate per lane in registers.  Per entry the j-side terms of
+// the lane's two pairs share its j atom: they are summed over the 4 lanes of
+// that atom (two shuffle levels) and lane ih adds component ih (x, y, z, q)
+// to the fixed-point sums.  The type-pair gradients go to the block table
+// as in k_adjoint.
+struct TileIA {
+    float x, y, z, qk;  // position, ke q
+    float4 g;           // dL/dF of the atom
+    int trow;           // type row (t T)
+};
+
+__device__ __forceinline__ TileIA load_tile_ia(const ForceArgs &A, long long slot, int T)
+{
+    TileIA t;
+    const float4 p = __ldg(A.xyzq + slot);
+    const bool real = is_real_coord(p.x);
+    t.x = real ? p.x : kFarCoord;
+    t.y = real ? p.y : kFarCoord;
+    t.z = real ? p.z : kFarCoord;
+    t.qk = p.w * A.P.ke;
+    t.g = __ldg(A.gslot + slot);
+    t.trow = __ldg(A.tslot + slot) * T;
+    return t;
+}
+
+template <int RAD>
+__device__ __forceinline__ void adj1_entry(const ForceArgs &A, const AdjTables &tab, uint2 ent, float4 pj, float4 gj,
+                                           int tj, const TileIA &ia, const TileIA &ib, int jj, int ih, float Lx,
+                                           float Ly, float Lz, float gE_lj, float gE_c, AccAdj &acA, AccAdj &acB,
+                                           bool &ovf)
+{
+    const int J = (int)(ent.x & kJMask);
+    const uint32_t code = (ent.x >> kShiftBit) & 0x3Fu;
+    const bool img = code != 0u, special = (ent.x & kExclFlag) != 0u;
+    float ax = ia.x, ay = ia.y, az = ia.z, bx = ib.x, by = ib.y, bz = ib.z;
+    if (img) {  // j side: x_j - L on code-1 axes; i side: x_i - L on code-2 axes
+        if ((code & 3u) == 1u) pj.x = __fsub_rn(pj.x, Lx);
+        if (((code >> 2) & 3u) == 1u) pj.y = __fsub_rn(pj.y, Ly);
+        if ((code >> 4) == 1u) pj.z = __fsub_rn(pj.z, Lz);
+        if ((code & 3u) == 2u) { ax = __fsub_rn(ax, Lx); bx = __fsub_rn(bx, Lx); }
+        if (((code >> 2) & 3u) == 2u) { ay = __fsub_rn(ay, Ly); by = __fsub_rn(by, Ly); }
+        if ((code >> 4) == 2u) { az = __fsub_rn(az, Lz); bz = __fsub_rn(bz, Lz); }
+    }
+    float dxA, dyA, dzA, dxB, dyB, dzB;
+    const float r2A = disp_r2(pj.x, pj.y, pj.z, ax, ay, az, dxA, dyA, dzA);
+    const float r2B = disp_r2(pj.x, pj.y, pj.z, bx, by, bz, dxB, dyB, dzB);
+    bool inA = r2A < A.P.rc2, inB = r2B < A.P.rc2;
+    bool s14A = false, s14B = false;
+    if (special) {  // exclusion bitmask of the tile: bit 8 i + j
+        const ulonglong2 m = A.gmask[ent.y >> kMaskSlotBit];
+        const int bA = ih * kCluster + jj, bB = bA + 4 * kCluster;
+        inA = inA && !((m.x >> bA) & 1ull);
+        inB = inB && !((m.x >> bB) & 1ull);
+        s14A = (m.y >> bA) & 1ull;
+        s14B = (m.y >> bB) & 1ull;
+    }
+    const bool anyA = __any_sync(kFull, inA), anyB = __any_sync(kFull, inB);
+    if (!anyA && !anyB) return;
+    float jt[4] = {0.0f, 0.0f, 0.0f, 0.0f};  // the j atom's terms (x, y, z, q)
+    if (anyA) {
+        float a, b, c, d, ds, de;
+        eval_pair_adj<RAD == 1>(A.P, tab, ia.trow, ia.qk, ia.g.x, ia.g.y, ia.g.z, gE_lj, gE_c, inA, dxA, dyA, dzA,
+                                inA ? r2A : 1.0f, pj.w, tj, gj, s14A, A.status, acA, a, b, c, d, ds, de);
+        add_type_grads(tab, inA ? ia.trow + tj : -1, ds, de, A.status);
+        jt[0] = a;
+        jt[1] = b;
+        jt[2] = c;
+        jt[3] = d;
+    }
+    if (anyB) {
+        float a, b, c, d, ds, de;
+        eval_pair_adj<RAD == 1>(A.P, tab, ib.trow, ib.qk, ib.g.x, ib.g.y, ib.g.z, gE_lj, gE_c, inB, dxB, dyB, dzB,
+                                inB ? r2B : 1.0f, pj.w, tj, gj, s14B, A.status, acB, a, b, c, d, ds, de);
+        add_type_grads(tab, inB ? ib.trow + tj : -1, ds, de, A.status);
+        jt[0] = __fadd_rn(jt[0], a);
+        jt[1] = __fadd_rn(jt[1], b);
+        jt[2] = __fadd_rn(jt[2], c);
+        jt[3] = __fadd_rn(jt[3], d);
+    }
+#pragma unroll
+    for (int o = 8; o < 32; o <<= 1)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) jt[k] = __fadd_rn(jt[k], __shfl_xor_sync(kFull, jt[k], o));
+    const float gv = ih == 0 ? jt[0] : (ih == 1 ? jt[1] : (ih == 2 ? jt[2] : jt[3]));
+    const long long gx = tile_fixed(gv, ovf);
+    if (gx != 0) atomicAdd((unsigned long long *)&A.gacc[32ll * J + 4 * jj + ih], (unsigned long long)gx);
+}
+
+constexpr int kBatchA = 16;  // entries staged per batch of the single-cluster adjoint (shared memory per block)
+
+__host__ __device__ inline size_t adj1_warp_bytes() { return (size_t)kBatchA * kCluster * (16 + 16 + 4); }
+
+size_t adjoint1_smem_bytes(int T)
+{
+    return (size_t)T * T * 32 + align16((size_t)T * T * 8) + (size_t)kAdjWarps * adj1_warp_bytes();
+}
+
+template <int RAD>
+__global__ void __launch_bounds__(kAdjWarps * 32) k_adjoint1(ForceArgs A, int parts)
+{
+    pdl_entry();
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int T = A.P.n_types;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, jj = lane & 7, ih = lane >> 3;
+    size_t off = 0;
+    unsigned long long *tacc = reinterpret_cast<unsigned long long *>(smem + off);
+    off += (size_t)T * T * 16;
+    float4 *ljd = reinterpret_cast<float4 *>(smem + off);
+    off += (size_t)T * T * 16;
+    float2 *lj = reinterpret_cast<float2 *>(smem + off);
+    off += align16((size_t)T * T * 8);
+    float4 *sjp = reinterpret_cast<float4 *>(smem + off + (size_t)w * adj1_warp_bytes());  // [kBatchA * 8]
+    float4 *sjg = sjp + kBatchA * kCluster;                                                // [kBatchA * 8]
+    int *sjt = reinterpret_cast<int *>(sjg + kBatchA * kCluster);                          // [kBatchA * 8]
+    for (int k = threadIdx.x; k < T * T; k += blockDim.x) {
+        lj[k] = make_float2(A.lj_tab[k].x, A.lj_tab[k].y);
+        ljd[k] = A.lj_d[k];
+        tacc[2 * k] = 0ull;
+        tacc[2 * k + 1] = 0ull;
+    }
+    __syncthreads();
+    const AdjTables tab{lj, ljd, tacc};
+    const int n_units = A.counts[4] * kListSegs * parts;
+    int cur_sys = -1;
+    float Lx = 0.0f, Ly = 0.0f, Lz = 0.0f, gE_lj = 0.0f, gE_c = 0.0f;
+    bool ovf = false;
+    int u = 0;
+    if (lane == 0) u = atomicAdd(A.work, 1);
+    u = __shfl_sync(kFull, u, 0);
+    while (u < n_units) {
+        int u_next = 0;
+        if (lane == 0) u_next = atomicAdd(A.work, 1);
+        const Unit U = unit_of(A, u, parts);
+        if (U.e_begin < U.e_end) {
+            const int I = __ldg(A.grp + U.g).x;
+            const int sys_id = __ldg(A.clus_sys + I);
+            if (sys_id != cur_sys) {
+                cur_sys = sys_id;
+                Lx = A.sys[sys_id].L[0];
+                Ly = A.sys[sys_id].L[1];
+                Lz = A.sys[sys_id].L[2];
+                gE_lj = A.dLdE ? (float)A.dLdE[2 * sys_id] : 0.0f;
+                gE_c = A.dLdE ? (float)A.dLdE[2 * sys_id + 1] : 0.0f;
+            }
+            const long long s0 = (long long)I * kCluster;
+            const TileIA ia = load_tile_ia(A, s0 + ih, T);
+            const TileIA ib = load_tile_ia(A, s0 + ih + 4, T);
+            AccAdj acA = {0.0f, 0.0f, 0.0f, 0.0f}, acB = {0.0f, 0.0f, 0.0f, 0.0f};
+            const uint2 *row = A.glist + U.base;
+            for (int e0 = U.e_begin; e0 < U.e_end; e0 += kBatchA) {
+                const int ne = min(kBatchA, U.e_end - e0);
+                const uint2 my = lane < ne ? __ldg(row + e0 + lane) : make_uint2(0u, 0u);
+                if (lane < ne) {
+                    const long long jbase = (long long)(my.x & kJMask) * kCluster;
+#pragma unroll
+                    for (int a = 0; a < kCluster; ++a) {
+                        cp_async16(sjp + swz(lane, a), A.xyzq + jbase + a);
+                        cp_async16(sjg + swz(lane, a), A.gslot + jbase + a);
+                        cp_async4(sjt + swz(lane, a), A.tslot + jbase + a);
+                    }
+                }
+                cp_async_wait_all();
+                __syncwarp();
+                for (int k = 0; k < ne; ++k) {
+                    const uint2 ent = make_uint2(__shfl_sync(kFull, my.x, k), __shfl_sync(kFull, my.y, k));
+                    adj1_entry<RAD>(A, tab, ent, sjp[swz(k, jj)], sjg[swz(k, jj)], sjt[swz(k, jj)], ia, ib, jj, ih,
+                                    Lx, Ly, Lz, gE_lj, gE_c, acA, acB, ovf);
+                }
+                __syncwarp();  // the staging buffers are rewritten by the next batch
+            }
+            // i-side terms: the 8 lanes of each atom summed in FP32 (a fixed
+            // butterfly), then lanes jj < 4 add component jj of atom ih and
+            // lanes jj >= 4 component jj - 4 of atom ih + 4
+            float v[8] = {acA.dx, acA.dy, acA.dz, acA.dq, acB.dx, acB.dy, acB.dz, acB.dq};
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1)
+#pragma unroll
+                for (int c = 0; c < 8; ++c) v[c] = __fadd_rn(v[c], __shfl_xor_sync(kFull, v[c], o));
+            float mine = v[0];
+#pragma unroll
+            for (int c = 1; c < 8; ++c) mine = jj == c ? v[c] : mine;
+            const long long gi = tile_fixed(mine, ovf);
+            if (gi != 0) {
+                const long long slot = s0 + ih + (jj < 4 ? 0 : 4);
+                atomicAdd((unsigned long long *)&A.gacc[4 * slot + (jj & 3)], (unsigned long long)gi);
+            }
+            if (__any_sync(kFull, ovf)) {
+                if (lane == 0) atomicOr(A.status, ST_OVERFLOW);
+                ovf = false;
+            }
+        }
+        u = __shfl_sync(kFull, u_next, 0);
+    }
+    // block table of parameter gradients -> global (integer sums)
+    __syncthreads();
+    for (int k = threadIdx.x; k < 2 * T * T; k += blockDim.x)
+        if (tacc[k]) atomicAdd((unsigned long long *)&A.tab_acc[k], tacc[k]);
+}
+
 // Gather charges and types into sorted order and check that the positions
 // are those of the last build.
 __global__ void k_pack(int slot_cap, const int *__restrict__ counts, const int *__restrict__ perm,
@@ -1592,9 +1795,22 @@ static void launch_adjoint_g(nb_ctx *ctx, const ForceArgs &A)
 }
 
 template <int RAD>
+static void launch_adjoint_1(nb_ctx *ctx, const ForceArgs &A)
+{
+    const size_t smem = adjoint1_smem_bytes(A.P.n_types);
+    static std::atomic<unsigned long long> optin{0};
+    smem_optin_once(k_adjoint1<RAD>, ctx->device, 220 * 1024, optin);
+    int resident = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_adjoint1<RAD>, kAdjWarps * 32, smem);
+    const int parts = ctx->tune.list_split > 0 ? ctx->tune.list_split : kDefaultListSplit;
+    launch_pdl(k_adjoint1<RAD>, dim3(ctx->num_sms * std::max(1, resident)), dim3(kAdjWarps * 32), smem, ctx->stream,
+               A, parts);
+}
+
+template <int RAD>
 static void launch_adjoint_t(nb_ctx *ctx, const ForceArgs &A)
 {
-    if (ctx->built_group == 1) launch_adjoint_g<1, RAD>(ctx, A);
+    if (ctx->built_group == 1) launch_adjoint_1<RAD>(ctx, A);
     else if (ctx->built_group == 4) launch_adjoint_g<4, RAD>(ctx, A);
     else launch_adjoint_g<8, RAD>(ctx, A);
 }
