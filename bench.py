@@ -41,9 +41,11 @@ METRIC = "pair interactions/s and ms per force eval at 23.5k atoms; % FP32 roofl
 UNIT = "pairs/s"
 # kernels of this library per step: binning and lists (bin + scan, scatter,
 # column sort, pair lists); forward (pack, force, unpack + energy/virial);
-# adjoint (pack, dL/dF gather, adjoint kernel, unpack, type-pair gradients)
+# adjoint (pack, dL/dF gather, adjoint kernel, unpack, type-pair gradients);
+# nb_step (rebuild + forces in one call: the column sort packs, no pack kernel)
 BUILD_LAUNCHES = 4
 FORCE_LAUNCHES = 3
+STEP_LAUNCHES = BUILD_LAUNCHES + FORCE_LAUNCHES - 1
 ADJOINT_LAUNCHES = 5
 # smooth PME adds spread, solve, gather (+ the FFT library's forward and
 # inverse transforms, not counted as this library's kernels)
@@ -54,7 +56,7 @@ MD_DT_PS, MD_GRAPH_STEPS = 0.004, 10  # the paper's 4 fs step with mass repartit
 MD_WATERS = 7833  # 23,499 atoms in 61.7 A, the size of the paper's DHFR system
 # MD step: kick/drift + M-SHAKE, rebuild, forces, PME, (bonded),
 # kick + RATTLE + energies
-MD_LAUNCHES = 1 + BUILD_LAUNCHES + FORCE_LAUNCHES + PME_LAUNCHES + 1
+MD_LAUNCHES = 1 + STEP_LAUNCHES + PME_LAUNCHES + 1
 FLOP_PER_PAIR = 73  # LJ + switch + Ewald real space, FMA = 2, MUFU = 1
 # algorithmic DRAM bytes of one rebuild per atom: positions in (12), wrapped
 # coordinates and column out and back (20 + 20), scatter slot (8), sorted
@@ -265,8 +267,7 @@ def pme_leg(s, steps, flush, dev, npairs, base_ms):
     W6 = torch.empty((6,), dtype=torch.float64, device=dev)
 
     def step():
-        ctx.build(pos)
-        ctx.forces(pos, q, typ, F=F, energy=E, virial=W)
+        ctx.step(pos, q, typ, F=F, energy=E, virial=W)
 
     def lr_step():
         ctx._sync_stream()
@@ -285,7 +286,7 @@ def pme_leg(s, steps, flush, dev, npairs, base_ms):
             "pairs_per_s": npairs / (ms * 1e-3), "added_ms_vs_short_range": ms - base_ms,
             "long_range_only_ms": lr_ms,
             "step": "cell-list rebuild + short-range forces + smooth PME + Ewald self/exclusion corrections",
-            "gpu_launches_per_step": BUILD_LAUNCHES + FORCE_LAUNCHES + PME_LAUNCHES}
+            "gpu_launches_per_step": STEP_LAUNCHES + PME_LAUNCHES}
 
 
 def tables_leg(s, steps, flush, dev, npairs, base_ms, base_fo_ms):
@@ -303,8 +304,7 @@ def tables_leg(s, steps, flush, dev, npairs, base_ms, base_fo_ms):
     W = torch.empty((1, 6), dtype=torch.float64, device=dev)
 
     def step():
-        ctx.build(pos)
-        ctx.forces(pos, q, typ, F=F, energy=E, virial=W)
+        ctx.step(pos, q, typ, F=F, energy=E, virial=W)
 
     def fstep():
         ctx.forces(pos, q, typ, F=F, energy=E, virial=W)
@@ -320,7 +320,7 @@ def tables_leg(s, steps, flush, dev, npairs, base_ms, base_fo_ms):
     return {"intervals": TABLE_INTERVALS, "ms_per_step": ms, "pairs_per_s": npairs / (ms * 1e-3),
             "force_only_ms": fo_ms, "speedup_vs_direct": base_ms / ms, "force_only_speedup_vs_direct": base_fo_ms / fo_ms,
             "step": "cell-list rebuild + forces with tabulated radial functions (linear interpolation)",
-            "gpu_launches_per_step": BUILD_LAUNCHES + FORCE_LAUNCHES}
+            "gpu_launches_per_step": STEP_LAUNCHES}
 
 
 MD_MIN_STEPS, MD_MIN_DISP = 500, 0.01   # capped steepest descent before the dynamics
@@ -450,8 +450,7 @@ def large_leg(steps, flush, dev):
     W = torch.empty((1, 6), dtype=torch.float64, device=dev)
 
     def step():
-        ctx.build(pos)
-        ctx.forces(pos, q, typ, F=F, energy=E, virial=W)
+        ctx.step(pos, q, typ, F=F, energy=E, virial=W)
 
     def bstep():
         ctx.build(pos)
@@ -497,7 +496,7 @@ def large_leg(steps, flush, dev):
             "tuning": {"group_clusters": 1, "blocks_per_sm": 3, "list_split": 1},
             "autotune_table": tune_table(tuned),
             "step": "cell-list rebuild + forces, energies and virial (rc 9 A, Ewald real space)",
-            "gpu_launches_per_step": BUILD_LAUNCHES + FORCE_LAUNCHES}
+            "gpu_launches_per_step": STEP_LAUNCHES}
 
 
 def batched_leg(steps, flush, dev):
@@ -519,8 +518,7 @@ def batched_leg(steps, flush, dev):
     W = torch.empty((len(systems), 6), dtype=torch.float64, device=dev)
 
     def step():
-        ctx.build(pos)
-        ctx.forces(pos, q, typ, F=F, energy=E, virial=W)
+        ctx.step(pos, q, typ, F=F, energy=E, virial=W)
 
     for _ in range(3):
         step()
@@ -538,8 +536,7 @@ def batched_leg(steps, flush, dev):
 
     def seq_step():
         for c, p1, q1, t1 in seq:
-            c.build(p1)
-            c.forces(p1, q1, t1)
+            c.step(p1, q1, t1)
 
     for _ in range(2):
         seq_step()
@@ -548,7 +545,7 @@ def batched_leg(steps, flush, dev):
     return {"n_systems": len(systems), "n_atoms": N, "pairs_per_step": npairs, "ms_per_step": ms,
             "pairs_per_s": npairs / (ms * 1e-3), "sequential_ms_per_step": seq_ms,
             "speedup_vs_sequential": seq_ms / ms, "tuning": rec["best"],
-            "autotune_table": tune_table(rec), "gpu_launches_per_step": BUILD_LAUNCHES + FORCE_LAUNCHES}
+            "autotune_table": tune_table(rec), "gpu_launches_per_step": STEP_LAUNCHES}
 
 
 def measured_peaks():
@@ -681,8 +678,7 @@ def main():
     W = torch.empty((1, 6), dtype=torch.float64, device=dev)
 
     def step():
-        ctx.build(pos)
-        ctx.forces(pos, q, typ, F=F, energy=E, virial=W)
+        ctx.step(pos, q, typ, F=F, energy=E, virial=W)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -776,7 +772,7 @@ def main():
         "force_only": force_only,
         "roofline": roofline,
         "clocks": clk,
-        "gpu_launches": (BUILD_LAUNCHES + FORCE_LAUNCHES) * args.steps,
+        "gpu_launches": (STEP_LAUNCHES) * args.steps,
     }
 
     if not args.no_extras:
@@ -810,8 +806,7 @@ def main():
 
         def e2e_step():
             d_in.copy_(h_in, non_blocking=True)
-            ctx.build(dpos)
-            ctx.forces(dpos, dq, dt, F=oF, energy=oE, virial=oW)
+            ctx.step(dpos, dq, dt, F=oF, energy=oE, virial=oW)
             h_out.copy_(d_out, non_blocking=True)
 
         for _ in range(3):
@@ -824,7 +819,7 @@ def main():
         bi, bo = nb_in, nb_out
         line["e2e"] = {"value": world * npairs / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": bi,
                        "d2h_bytes_per_step": bo, "ms_per_step": e2e_ms}
-        line["gpu_launches"] += (BUILD_LAUNCHES + FORCE_LAUNCHES) * args.steps
+        line["gpu_launches"] += (STEP_LAUNCHES) * args.steps
         ctx.status()
     if rank == 0 and not args.no_cpu and world == 1:
         times, cp, cores = cpu_oracle_run(s)

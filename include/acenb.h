@@ -156,6 +156,17 @@ nb_status nb_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, const int
 nb_status nb_forces_batch(nb_ctx *batch, const float *d_pos, const float *d_q, const int32_t *d_type,
                           float *d_F, double *d_energy, double *d_virial);
 
+/* nb_step - one evaluation from positions: nb_build_cells followed by
+ * nb_forces on the same arrays (section "Molecular dynamics on the GPU":
+ * the cell list is rebuilt and the forces evaluated every step), in fewer
+ * kernels: the column sort also gathers the charges and types into sorted
+ * order, and with PME the reciprocal chain starts before the pair lists.
+ * Arguments, outputs and errors as for nb_forces; the context is built
+ * afterwards, so nb_forces and nb_backward may follow on the same
+ * positions.  Results are bit-identical to nb_build_cells + nb_forces. */
+nb_status nb_step(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type, float *d_F,
+                  double *d_energy, double *d_virial);
+
 /* nb_backward - adjoint of L = sum_i G_i . F_i + sum_s gE_s . E_s, the pair
  * list recomputed from the last build (short-range terms, direct radial
  * functions; a context with smooth PME or tables enabled returns

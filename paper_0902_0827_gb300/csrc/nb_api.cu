@@ -296,6 +296,22 @@ nb_status nb_forces_batch(nb_ctx *batch, const float *d_pos, const float *d_q, c
     return nb_forces(batch, d_pos, d_q, d_type, d_F, d_energy, d_virial);
 }
 
+nb_status nb_step(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type, float *d_F,
+                  double *d_energy, double *d_virial)
+{
+    if (!ctx || !d_pos || !d_q || !d_type || !d_F) return NB_ERR_INVALID_ARG;
+    // the column sort packs charges and types; PME (which needs only the
+    // sorted atoms) is forked before the lists, beside the list and force kernels
+    cudaError_t e = launch_build_cells(ctx, d_pos, d_q, d_type);
+    const bool pme = ctx->pme != nullptr;
+    if (e == cudaSuccess && pme) e = launch_pme_fork(ctx, d_pos, d_q);
+    if (e == cudaSuccess) e = launch_build_lists(ctx);
+    if (e != cudaSuccess) return NB_ERR_CUDA;
+    ctx->built = true;
+    e = launch_forces_packed(ctx, d_F, d_energy, d_virial, false, pme, pme);
+    return e == cudaSuccess ? NB_OK : NB_ERR_CUDA;
+}
+
 nb_status nb_backward(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type,
                       const float *d_dLdF, const double *d_dLdE, float *d_dLdpos, float *d_dLdq,
                       double *d_dLdsig_tab, double *d_dLdeps_tab)

@@ -214,6 +214,32 @@ __device__ void bitonic_sort(unsigned long long *skey, int P)
 
 constexpr int kRankSortMax = 256;  // columns up to this many atoms are rank-sorted (no barriers)
 
+// Per-atom inputs of the force kernels packed by the column sort when the
+// caller passes them with the positions (nb_step): charges into xyzq.w,
+// checked types into tslot, and the force kernels' sums and work counter
+// zeroed (k_pack's work, without its stale-position check: the positions
+// were just binned).  q == nullptr: the column sort leaves that to k_pack.
+struct ColPack {
+    const float *q;
+    const int *type;
+    int T;
+    long long *facc;     // [3 slots] fixed-point forces
+    long long *sys_acc;  // [n_acc] per-system energy and virial sums
+    int n_acc;
+    int *work;           // the force kernels' work-unit counter
+    int *status;
+};
+
+__device__ __forceinline__ int packed_type(const ColPack &pk, int a)
+{
+    int t = pk.type[a];
+    if (t < 0 || t >= pk.T) {
+        atomicOr(pk.status, ST_BADTYPE);
+        t = 0;
+    }
+    return t;
+}
+
 // A3b: one block per column: sort by (z, atom index), write the sorted slot
 // arrays and padding, the cluster bounding boxes and the column's z-bin
 // index (the clusters are z-sorted, so their z_lo and z_hi never decrease).
@@ -227,7 +253,7 @@ __global__ void __launch_bounds__(kSortThreads) k_colsort(
     const SysDesc *__restrict__ sys, const int *__restrict__ stage, const float4 *__restrict__ wpos,
     float4 *__restrict__ xyzq, int *__restrict__ tslot, int *__restrict__ perm, int *__restrict__ inv,
     float4 *__restrict__ bb, int *__restrict__ clus_sys, int2 *__restrict__ zbin, int group,
-    const int *__restrict__ col_grp, int2 *__restrict__ grp, int *__restrict__ clus_grp)
+    const int *__restrict__ col_grp, int2 *__restrict__ grp, int *__restrict__ clus_grp, ColPack pk)
 {
     pdl_entry();
     __shared__ unsigned long long skey[kSortSmem];
@@ -257,7 +283,8 @@ __global__ void __launch_bounds__(kSortThreads) k_colsort(
             const int slot = base + k;
             perm[slot] = a;
             inv[a] = slot;
-            xyzq[slot] = make_float4(pa.x, pa.y, pa.z, 0.0f);
+            xyzq[slot] = make_float4(pa.x, pa.y, pa.z, pk.q ? pk.q[a] : 0.0f);
+            if (pk.q) tslot[slot] = packed_type(pk, a);
             sp[k] = pa;
         }
     } else if (small) {
@@ -290,7 +317,8 @@ __global__ void __launch_bounds__(kSortThreads) k_colsort(
                 const int slot = base + rank[u];
                 perm[slot] = a;
                 inv[a] = slot;
-                xyzq[slot] = make_float4(p[u].x, p[u].y, p[u].z, 0.0f);
+                xyzq[slot] = make_float4(p[u].x, p[u].y, p[u].z, pk.q ? pk.q[a] : 0.0f);
+                if (pk.q) tslot[slot] = packed_type(pk, a);
                 sp[rank[u]] = p[u];
             }
         }
@@ -307,13 +335,21 @@ __global__ void __launch_bounds__(kSortThreads) k_colsort(
             const int slot = base + rank;
             perm[slot] = a;
             inv[a] = slot;
-            xyzq[slot] = make_float4(pa.x, pa.y, pa.z, 0.0f);
+            xyzq[slot] = make_float4(pa.x, pa.y, pa.z, pk.q ? pk.q[a] : 0.0f);
+            if (pk.q) tslot[slot] = packed_type(pk, a);
         }
     }
     for (int k = n + tid; k < npad; k += blockDim.x) {
         perm[base + k] = -1;
         tslot[base + k] = 0;
         xyzq[base + k] = make_float4(kPadCoord, kPadCoord, kPadCoord, 0.0f);
+    }
+    if (pk.q) {
+        for (int k = tid; k < 3 * npad; k += blockDim.x) pk.facc[3ll * base + k] = 0;
+        if (c == 0) {
+            for (int k = tid; k < pk.n_acc; k += blockDim.x) pk.sys_acc[k] = 0;
+            if (tid == 0) *pk.work = 0;
+        }
     }
     __syncthreads();
     // cluster bounding boxes over the real atoms of each 8-slot cluster
@@ -862,7 +898,7 @@ __global__ void __launch_bounds__(kGListWarps * 32, ACENB_GLIST_MIN_BLOCKS) k_gl
     }
 }
 
-cudaError_t launch_build_cells(nb_ctx *ctx, const float *d_pos)
+cudaError_t launch_build_cells(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type)
 {
     auto &d = ctx->d;
     cudaStream_t st = ctx->stream;
@@ -878,7 +914,9 @@ cudaError_t launch_build_cells(nb_ctx *ctx, const float *d_pos)
     if (e == cudaSuccess)
         e = launch_pdl(k_colsort, dim3(ctx->n_cols), dim3(kSortThreads), 0, st, d.col_count, d.col_slot, d.col_sys,
                        d.sys, d.stage, d.wpos, d.xyzq, d.tslot, d.perm, d.inv, d.bb, d.clus_sys, d.zbin, ctx->group,
-                       d.col_grp, d.grp, d.clus_grp);
+                       d.col_grp, d.grp, d.clus_grp,
+                       ColPack{d_q, d_type, ctx->pp.n_types, d.facc, d.sys_acc, kTaskVals * ctx->n_sys, d.counts + 3,
+                               d.status});
     if (e != cudaSuccess) return e;
     ctx->built_group = ctx->group;
     return cudaGetLastError();

@@ -244,7 +244,8 @@ inline int64_t mask_capacity(int64_t clus_cap) { return mask_pool_base(clus_cap)
 cudaError_t launch_build(nb_ctx *ctx, const float *d_pos);
 // the two halves of launch_build: binning, column sort and cluster boxes;
 // then the cluster-pair lists
-cudaError_t launch_build_cells(nb_ctx *ctx, const float *d_pos);
+cudaError_t launch_build_cells(nb_ctx *ctx, const float *d_pos, const float *d_q = nullptr,
+                               const int32_t *d_type = nullptr);
 cudaError_t launch_build_lists(nb_ctx *ctx);
 cudaError_t launch_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type,
                           float *d_F, double *d_energy, double *d_virial, bool debug_pairs);

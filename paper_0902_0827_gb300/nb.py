@@ -22,7 +22,7 @@ STATUS_NAMES = {
     9: "NB_ERR_NONFINITE", 10: "NB_ERR_CAPACITY", 11: "NB_ERR_UNSUPPORTED", 12: "NB_ERR_TOO_LARGE",
 }
 # every symbol include/acenb.h declares
-EXPORTS = ("nb_create", "nb_create_batch", "nb_build_cells", "nb_forces", "nb_forces_batch", "nb_backward",
+EXPORTS = ("nb_create", "nb_create_batch", "nb_build_cells", "nb_forces", "nb_forces_batch", "nb_step", "nb_backward",
            "nb_get_status", "nb_set_stream", "nb_destroy", "nb_set_tuning", "nb_get_tuning", "nb_get_sizes",
            "nb_debug_cells", "nb_debug_pairs", "nb_debug_pair_terms", "nb_debug_philox", "nb_status_string",
            "nb_set_lj_params", "nb_set_profiling", "nb_get_profile", "nb_forces_noalloc", "nb_type_gradients",
@@ -101,6 +101,7 @@ def lib(build_if_missing: bool = True):
             "nb_build_cells": ([P, P], ctypes.c_int),
             "nb_forces": ([P, P, P, P, P, P, P], ctypes.c_int),
             "nb_forces_batch": ([P, P, P, P, P, P, P], ctypes.c_int),
+            "nb_step": ([P, P, P, P, P, P, P], ctypes.c_int),
             "nb_backward": ([P, P, P, P, P, P, P, P, P, P], ctypes.c_int),
             "nb_get_status": ([P], ctypes.c_int),
             "nb_set_stream": ([P, P], ctypes.c_int),
@@ -259,6 +260,21 @@ class Nonbonded:
         W = W if W is not False else None
         _check(lib().nb_forces(self.h, _tptr(pos), _tptr(q), _tptr(typ), _tptr(F), _tptr(E), _tptr(W)),
                "nb_forces")
+        return F, E, W
+
+    def step(self, pos, q, typ, F=None, energy=True, virial=True):
+        """Rebuild from pos and evaluate (nb_step): the results of
+        build(pos) followed by forces(pos, q, typ), in fewer kernels."""
+        import torch
+        self._sync_stream()
+        dev = pos.device
+        if F is None:
+            F = torch.empty((self.n_atoms, 3), dtype=torch.float32, device=dev)
+        E = torch.empty((self.n_sys, 2), dtype=torch.float64, device=dev) if energy is True else energy
+        W = torch.empty((self.n_sys, 6), dtype=torch.float64, device=dev) if virial is True else virial
+        E = E if E is not False else None
+        W = W if W is not False else None
+        _check(lib().nb_step(self.h, _tptr(pos), _tptr(q), _tptr(typ), _tptr(F), _tptr(E), _tptr(W)), "nb_step")
         return F, E, W
 
     def set_tables(self, n_intervals: int = 4096):

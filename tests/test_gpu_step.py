@@ -1,0 +1,74 @@
+"""nb_step (rebuild + forces in one call, the charges and types packed by the
+column sort) against nb_build_cells + nb_forces on the same inputs: forces,
+energies and virial bit for bit, alone, in a batch, with smooth PME and with
+tables; the context is built afterwards; a bad type index is reported."""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_0902_0827_gb300 import nb
+from paper_0902_0827_gb300 import systems as S
+
+pytestmark = pytest.mark.gpu
+
+
+def _two_calls(systems, setup=None):
+    ctx = nb.Nonbonded(systems if len(systems) > 1 else systems[0])
+    if setup:
+        setup(ctx)
+    pos, q, t = nb.concat_inputs(systems)
+    ctx.build(pos)
+    F, E, W = ctx.forces(pos, q, t)
+    torch.cuda.synchronize()
+    ctx.status()
+    return (pos, q, t), F.clone(), E.clone(), W.clone()
+
+
+def _one_call(systems, inp, setup=None):
+    ctx = nb.Nonbonded(systems if len(systems) > 1 else systems[0])
+    if setup:
+        setup(ctx)
+    pos, q, t = inp
+    F, E, W = ctx.step(pos, q, t)
+    torch.cuda.synchronize()
+    ctx.status()
+    return ctx, F, E, W
+
+
+CASES = {
+    "solvated_chain": (lambda: [S.solvated_chain()], None),
+    "water_box": (lambda: [S.water_box()], None),
+    "batch3": (lambda: S.water_ensemble()[:3], None),
+    "chain_pme": (lambda: [S.solvated_chain()], lambda c: c.set_pme((64, 64, 64), 4)),
+    "water_tables": (lambda: [S.water_box()], lambda c: c.set_tables(4096)),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_step_equals_build_then_forces(name):
+    make, setup = CASES[name]
+    systems = make()
+    inp, F0, E0, W0 = _two_calls(systems, setup)
+    ctx, F1, E1, W1 = _one_call(systems, inp, setup)
+    assert torch.equal(F1, F0), name
+    assert torch.equal(E1, E0), name
+    assert torch.equal(W1, W0), name
+    # the step leaves the context built on these positions
+    F2, E2, W2 = ctx.forces(*inp)
+    torch.cuda.synchronize()
+    ctx.status()
+    assert torch.equal(F2, F0) and torch.equal(E2, E0) and torch.equal(W2, W0)
+
+
+def test_step_reports_a_bad_type():
+    s = S.water_box()
+    ctx = nb.Nonbonded(s)
+    pos, q, t = nb.concat_inputs([s])
+    t[5] = s.n_types  # out of range
+    ctx.step(pos, q, t)
+    torch.cuda.synchronize()
+    with pytest.raises(nb.NbError) as e:
+        ctx.status()
+    assert e.value.code == 1  # NB_ERR_INVALID_ARG (a type index outside [0, T))
