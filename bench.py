@@ -685,6 +685,7 @@ def main():
     torch.cuda.synchronize()
     ctx.status()
     _, npairs, n_ordered = ctx.debug_pairs(cap=0)
+    n_tiles, n_halves = ctx.debug_fill()
 
     # CUDA graph of one step, captured on a side stream
     side = torch.cuda.Stream(device=dev)
@@ -758,7 +759,10 @@ def main():
                                f"(median SM clock sampled during the timed steps)"),
                 "peak_at_max_clock": peak_at_max, "sm_max_mhz": sm_max, "sm_mhz_used": sm_med,
                 "peak_measured": fpk["tflops"], "frac_measured": achieved / fpk["tflops"],
-                "peak_measured_basis": fpk["how"], "peak_measured_clocks": fpk["clocks"]}
+                "peak_measured_basis": fpk["how"], "peak_measured_clocks": fpk["clocks"],
+                "tile_fill": npairs / (64.0 * max(n_tiles, 1)), "lane_fill": npairs / (32.0 * max(n_halves, 1)),
+                "fill_basis": (f"{npairs} pairs in {n_tiles} 8x8 tiles visited, {n_halves} 4x8 tile halves "
+                               "evaluated: the useful fraction of the lanes that run the pair arithmetic")}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -239,6 +239,15 @@ nb_status nb_debug_cells(nb_ctx *ctx, int32_t *h_perm, int64_t *n_slots,
  * unique pair once and applies the force to both atoms).  Synchronous. */
 nb_status nb_debug_pairs(nb_ctx *ctx, int32_t *h_ij, int64_t cap, int64_t *n, int64_t *n_ordered);
 
+/* nb_debug_fill - tile fill of the last nb_debug_pairs run: *tiles receives
+ * the number of 8 x 8 cluster-pair tiles the forward kernel visited and
+ * *halves the number of 4 x 8 tile halves whose pair arithmetic ran (at
+ * least one of their 32 pairs inside the cutoff and not excluded).  With the
+ * pair count n of nb_debug_pairs, n / (64 tiles) is the tile fill and
+ * n / (32 halves) the fraction of evaluated lanes doing useful work.
+ * Measurement export without a counterpart in the paper.  Synchronous. */
+nb_status nb_debug_fill(nb_ctx *ctx, int64_t *tiles, int64_t *halves);
+
 /* nb_debug_pair_terms - the forward kernel's FP32 pair arithmetic (section
  * "Molecular dynamics on the GPU": the Lennard-Jones and electrostatic terms
  * of one pair; forms in the header comment above) for n given pairs, so that

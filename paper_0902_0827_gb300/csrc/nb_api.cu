@@ -101,7 +101,7 @@ nb_status allocate(nb_ctx *c)
     ALLOC(d.lj_d, (int64_t)T * T);
     ALLOC(d.gslot, S);
     ALLOC(d.eps_type, T);
-    ALLOC(d.dbg_n, 2);
+    ALLOC(d.dbg_n, 4);
 #undef ALLOC
     if (e != cudaSuccess) return cuda_status(e);
     e = cudaMemset(d.tslot, 0, sizeof(int) * S);
@@ -572,7 +572,7 @@ nb_status nb_debug_pairs(nb_ctx *ctx, int32_t *h_ij, int64_t cap, int64_t *n, in
         d.dbg_cap = cap;
     }
     if (!d.scratch_f && dalloc(&d.scratch_f, (size_t)ctx->n_atoms * 3) != cudaSuccess) return NB_ERR_OOM;
-    if (cudaMemsetAsync(d.dbg_n, 0, 2 * sizeof(long long), ctx->stream) != cudaSuccess) return NB_ERR_CUDA;
+    if (cudaMemsetAsync(d.dbg_n, 0, 4 * sizeof(long long), ctx->stream) != cudaSuccess) return NB_ERR_CUDA;
     // positions/charges/types of the last build are already in sorted order
     cudaError_t e = launch_forces(ctx, nullptr, nullptr, nullptr, d.scratch_f, nullptr, nullptr, true);
     if (e != cudaSuccess) return NB_ERR_CUDA;
@@ -584,6 +584,17 @@ nb_status nb_debug_pairs(nb_ctx *ctx, int32_t *h_ij, int64_t cap, int64_t *n, in
     int64_t m = std::min<int64_t>(hn[1], cap);
     if (h_ij && m > 0 && cudaMemcpy(h_ij, d.dbg_ij, sizeof(int) * 2 * m, cudaMemcpyDeviceToHost) != cudaSuccess)
         return NB_ERR_CUDA;
+    return NB_OK;
+}
+
+nb_status nb_debug_fill(nb_ctx *ctx, int64_t *tiles, int64_t *halves)
+{
+    if (!ctx || !tiles || !halves) return NB_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return NB_ERR_CUDA;
+    long long hn[4];
+    if (cudaMemcpy(hn, ctx->d.dbg_n, sizeof(hn), cudaMemcpyDeviceToHost) != cudaSuccess) return NB_ERR_CUDA;
+    *tiles = hn[3];
+    *halves = hn[2];
     return NB_OK;
 }
 

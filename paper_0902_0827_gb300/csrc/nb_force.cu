@@ -305,6 +305,18 @@ __device__ __forceinline__ void record_pair(const ForceArgs &A, int io, int jo)
     }
 }
 
+// Tile fill counters of the debug instantiation: tiles visited (dbg_n[3])
+// and tile halves whose radial arithmetic runs (dbg_n[2]); with the pair
+// count they give the fraction of evaluated lanes inside the cutoff.
+__device__ __forceinline__ void count_tile(const ForceArgs &A, bool anyA, bool anyB)
+{
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd((unsigned long long *)&A.dbg_n[3], 1ull);
+        const unsigned long long h = (anyA ? 1ull : 0ull) + (anyB ? 1ull : 0ull);
+        if (h) atomicAdd((unsigned long long *)&A.dbg_n[2], h);
+    }
+}
+
 // Forward kernel (k_force) on i-group tiles.
 //
 // A work unit is one part of one segment of an i-group's list (the group:
@@ -401,6 +413,7 @@ __device__ __forceinline__ void tile_pair2(const ForceArgs &A, const float4 *__r
     bool s14A = false, s14B = false;
     if (SPECIAL) tile_mask_bits(gm, ia, jb, inA, inB, s14A, s14B);
     const bool anyA = __any_sync(kFull, inA), anyB = __any_sync(kFull, inB);
+    if (DEBUG) count_tile(A, anyA, anyB);
     if (!anyA && !anyB) return;
     Acc acc = {fi.x, fi.y, fi.z, elj, ec};
     if (anyA) {
@@ -794,6 +807,7 @@ __device__ __forceinline__ void tile1_entry(const ForceArgs &A, const float4 *__
         s14B = (m.y >> bB) & 1ull;
     }
     const bool anyA = __any_sync(kFull, inA), anyB = __any_sync(kFull, inB);
+    if (DEBUG) count_tile(A, anyA, anyB);
     if (!anyA && !anyB) return;
     const int jorig = DEBUG ? __ldg(A.perm + (long long)J * kCluster + jj) : -1;
     float fjx = 0.0f, fjy = 0.0f, fjz = 0.0f;

@@ -140,7 +140,7 @@ struct DevBuffers {
     float4 *rtab = nullptr;          // [tab_n*3] tabulated radial functions (nb_set_tables)
     float4 *gslot = nullptr;         // [S] adjoint input dL/dF in sorted order
     float *eps_type = nullptr;       // [T] per-type epsilon (Lorentz-Berthelot chain)
-    long long *dbg_n = nullptr;      // [2] debug pair counters
+    long long *dbg_n = nullptr;      // [4] debug counters: pair evaluations, pairs, evaluated tile halves, tiles
     int *dbg_ij = nullptr;           // [cap*2]
     int64_t dbg_cap = 0;
     float *scratch_f = nullptr;      // [N*3] debug force sink

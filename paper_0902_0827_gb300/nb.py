@@ -24,7 +24,7 @@ STATUS_NAMES = {
 # every symbol include/acenb.h declares
 EXPORTS = ("nb_create", "nb_create_batch", "nb_build_cells", "nb_forces", "nb_forces_batch", "nb_step", "nb_backward",
            "nb_get_status", "nb_set_stream", "nb_destroy", "nb_set_tuning", "nb_get_tuning", "nb_get_sizes",
-           "nb_debug_cells", "nb_debug_pairs", "nb_debug_pair_terms", "nb_debug_philox", "nb_status_string",
+           "nb_debug_cells", "nb_debug_pairs", "nb_debug_fill", "nb_debug_pair_terms", "nb_debug_philox", "nb_status_string",
            "nb_set_lj_params", "nb_set_profiling", "nb_get_profile", "nb_forces_noalloc", "nb_type_gradients",
            "nb_set_pme", "nb_pme_forces", "nb_set_tables", "nb_md_init", "nb_md_step", "nb_md_minimize",
            "nb_bonded_forces",
@@ -111,6 +111,7 @@ def lib(build_if_missing: bool = True):
             "nb_get_sizes": ([P, ctypes.POINTER(I64), ctypes.POINTER(I32), ctypes.POINTER(I64)], ctypes.c_int),
             "nb_debug_cells": ([P, P, ctypes.POINTER(I64), P, ctypes.POINTER(I64)], ctypes.c_int),
             "nb_debug_pairs": ([P, P, I64, ctypes.POINTER(I64), ctypes.POINTER(I64)], ctypes.c_int),
+            "nb_debug_fill": ([P, ctypes.POINTER(I64), ctypes.POINTER(I64)], ctypes.c_int),
             "nb_status_string": ([ctypes.c_int], ctypes.c_char_p),
             "nb_set_lj_params": ([P, P, P, P, P], ctypes.c_int),
             "nb_set_profiling": ([P, I32], ctypes.c_int),
@@ -457,6 +458,12 @@ class Nonbonded:
         ij = ij[:m]
         order = np.lexsort((ij[:, 1], ij[:, 0]))
         return ij[order], n.value, no.value
+
+    def debug_fill(self):
+        """(tiles visited, tile halves evaluated) of the last debug_pairs run."""
+        t, h = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().nb_debug_fill(self.h, ctypes.byref(t), ctypes.byref(h)), "nb_debug_fill")
+        return t.value, h.value
 
 
 def debug_philox(ctr, key):

@@ -72,3 +72,21 @@ def test_step_reports_a_bad_type():
     with pytest.raises(nb.NbError) as e:
         ctx.status()
     assert e.value.code == 1  # NB_ERR_INVALID_ARG (a type index outside [0, T))
+
+
+@pytest.mark.parametrize("group", [1, 4])
+def test_fill_counters_are_consistent(group):
+    # every pair sits in an evaluated half, every evaluated half in a visited
+    # tile; the tiles visited are the same for every tile shape
+    s = S.solvated_chain()
+    ctx = nb.Nonbonded(s)
+    ctx.set_tuning(group_clusters=group)
+    pos, q, t = nb.concat_inputs([s])
+    ctx.step(pos, q, t)
+    _, n, _ = ctx.debug_pairs(cap=0)
+    tiles, halves = ctx.debug_fill()
+    ctx.status()
+    print("group", group, "pairs", n, "tiles", tiles, "halves", halves, "lane fill", n / (32 * halves))
+    assert 0 < n <= 32 * halves <= 64 * tiles
+    assert halves <= 2 * tiles
+    assert 0.2 < n / (32 * halves) < 0.9
