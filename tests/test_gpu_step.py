@@ -77,7 +77,7 @@ def test_step_reports_a_bad_type():
 @pytest.mark.parametrize("group", [1, 4])
 def test_fill_counters_are_consistent(group):
     # every pair sits in an evaluated half, every evaluated half in a visited
-    # tile; the tiles visited are the same for every tile shape
+    # tile, for single-cluster and four-cluster i-groups
     s = S.solvated_chain()
     ctx = nb.Nonbonded(s)
     ctx.set_tuning(group_clusters=group)
