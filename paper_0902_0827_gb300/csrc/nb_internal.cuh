@@ -262,7 +262,8 @@ cudaError_t launch_adjoint_tile(nb_ctx *ctx, const double *d_dLdE, float *d_dpos
 // force and energy sums; the sums' device arrays (NULL when PME is off).
 cudaError_t launch_pme(nb_ctx *ctx, const float *d_pos, const float *d_q);
 // the same chain forked onto the PME side stream, and the join back
-cudaError_t launch_pme_fork(nb_ctx *ctx, const float *d_pos, const float *d_q);
+// sums: also the pair-correction energy and virial (the forces always)
+cudaError_t launch_pme_fork(nb_ctx *ctx, const float *d_pos, const float *d_q, bool sums = true);
 cudaError_t launch_pme_join(nb_ctx *ctx);
 void pme_free(nb_ctx *ctx);
 const long long *pme_forces_acc(const nb_ctx *ctx);

@@ -671,13 +671,14 @@ static cudaError_t launch_bonded(nb_ctx *ctx, const float *d_pos)
 // bonded terms.  The PME chain needs the sorted atoms but not the pair
 // lists, so it is forked onto its side stream right after the column sort
 // and the charge pack: it overlaps the list kernel and the short-range
-// kernel.
-static cudaError_t md_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type)
+// kernel.  sums: the energies of this evaluation are reported (the PME
+// pair-correction energies are summed only then).
+static cudaError_t md_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type, bool sums)
 {
     MdState &M = *ctx->md;
     cudaError_t e = launch_build_cells(ctx, d_pos, d_q, d_type);  // the column sort packs q, types
     const bool pme = ctx->pme != nullptr;
-    if (e == cudaSuccess && pme) e = launch_pme_fork(ctx, d_pos, d_q);
+    if (e == cudaSuccess && pme) e = launch_pme_fork(ctx, d_pos, d_q, sums);
     if (e == cudaSuccess) e = launch_build_lists(ctx);
     if (e != cudaSuccess) return e;
     ctx->built = true;
@@ -842,7 +843,7 @@ extern "C" nb_status nb_md_step(nb_ctx *ctx, float *d_pos, float *d_vel, const f
     P.max_iter = M.shake_iter;
     cudaError_t e = cudaSuccess;
     if (!M.have_forces) {  // forces at the starting positions
-        e = md_forces(ctx, d_pos, d_q, d_type);
+        e = md_forces(ctx, d_pos, d_q, d_type, false);
         if (e == cudaSuccess)
             e = launch_pdl(k_md_collect, dim3(ab), dim3(256), 0, st, N, (const float *)M.Fnb, M.bacc, M.Ftot);
         if (e != cudaSuccess) return NB_ERR_CUDA;
@@ -853,7 +854,7 @@ extern "C" nb_status nb_md_step(nb_ctx *ctx, float *d_pos, float *d_vel, const f
                        (const unsigned long long *)M.step, (const int *)M.free_atoms, (const int4 *)M.waters,
                        (const float *)M.mass, (const float *)M.sigv, (const float *)M.Ftot, d_pos, d_vel, B, M.acc,
                        ctx->d.status);
-        if (e == cudaSuccess) e = md_forces(ctx, d_pos, d_q, d_type);
+        if (e == cudaSuccess) e = md_forces(ctx, d_pos, d_q, d_type, d_energy && s == n_steps - 1);
         if (e == cudaSuccess)
             e = launch_pdl(k_md_second, dim3(ib), dim3(64), 0, st, M.n_free, M.nw, P,
                            M.step, (const int *)M.free_atoms, (const int4 *)M.waters,
@@ -886,7 +887,7 @@ extern "C" nb_status nb_md_minimize(nb_ctx *ctx, float *d_pos, const float *d_q,
     // forces at the final positions (left for the next nb_md_step)
     for (int s = 0; s <= n_steps && e == cudaSuccess; ++s) {
         e = cudaMemsetAsync(M.acc, 0, sizeof(long long) * kMdAcc, st);
-        if (e == cudaSuccess) e = md_forces(ctx, d_pos, d_q, d_type);
+        if (e == cudaSuccess) e = md_forces(ctx, d_pos, d_q, d_type, d_energy && s == n_steps);
         if (e == cudaSuccess)
             e = launch_pdl(k_min_collect, dim3(ab), dim3(256), 0, st, N, (const float *)M.Fnb, M.bacc, M.Ftot,
                            (const float *)M.mass, M.amax + (s & 1));

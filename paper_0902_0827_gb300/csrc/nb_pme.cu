@@ -427,7 +427,7 @@ __global__ void __launch_bounds__(256) k_pme_gather(PmeGeom g, PmeCorr cc, int s
                                                    const int *__restrict__ perm, const int *__restrict__ inv,
                                                    const float4 *__restrict__ xyzq, const float *__restrict__ pos,
                                                    const float *__restrict__ q, const float *__restrict__ theta,
-                                                   const int *__restrict__ part, int K, long long *__restrict__ pacc,
+                                                   const int *__restrict__ part, int K, int sums, long long *__restrict__ pacc,
                                                    long long *__restrict__ acc, int *__restrict__ status)
 {
     pdl_entry();
@@ -530,7 +530,7 @@ __global__ void __launch_bounds__(256) k_pme_gather(PmeGeom g, PmeCorr cc, int s
                     fx += f0;
                     fy += f1;
                     fz += f2;
-                    if (j > a) {
+                    if (sums && j > a) {
                         // The pair's energy -qq erf(alpha r)/r = -qq alpha erf(x)/x,
                         // x^2 = alpha^2 r^2, in double-FP32 arithmetic from the exact
                         // displacement of the FP32 inputs: these corrections sum to
@@ -679,7 +679,7 @@ const long long *pme_sums_acc(const nb_ctx *ctx) { return ctx->pme ? ctx->pme->a
 double pme_self_coef(const nb_ctx *ctx) { return ctx->pme ? ctx->pme->self_coef : 0.0; }
 
 template <int N>
-static cudaError_t launch_pme_t(nb_ctx *ctx, cudaStream_t st, const float *d_pos, const float *d_q)
+static cudaError_t launch_pme_t(nb_ctx *ctx, cudaStream_t st, const float *d_pos, const float *d_q, bool sums)
 {
     PmeState &P = *ctx->pme;
     const PmeGeom &g = P.g;
@@ -705,30 +705,30 @@ static cudaError_t launch_pme_t(nb_ctx *ctx, cudaStream_t st, const float *d_pos
     const int gb = std::max(1, std::min((S * G + gt - 1) / gt, 16 * ctx->num_sms));
     return launch_pdl(k_pme_gather<N>, dim3(gb), dim3(gt), 0, st, g, P.c, S, (const int *)d.counts,
                       (const int *)d.perm, (const int *)d.inv, (const float4 *)d.xyzq, d_pos, d_q,
-                      (const float *)P.grid, (const int *)d.part_orig, ctx->K, P.pacc, P.acc, d.status);
+                      (const float *)P.grid, (const int *)d.part_orig, ctx->K, sums ? 1 : 0, P.pacc, P.acc, d.status);
 }
 
-static cudaError_t launch_pme_on(nb_ctx *ctx, cudaStream_t st, const float *d_pos, const float *d_q)
+static cudaError_t launch_pme_on(nb_ctx *ctx, cudaStream_t st, const float *d_pos, const float *d_q, bool sums)
 {
     switch (ctx->pme->order) {
-    case 4: return launch_pme_t<4>(ctx, st, d_pos, d_q);
-    case 6: return launch_pme_t<6>(ctx, st, d_pos, d_q);
-    case 8: return launch_pme_t<8>(ctx, st, d_pos, d_q);
+    case 4: return launch_pme_t<4>(ctx, st, d_pos, d_q, sums);
+    case 6: return launch_pme_t<6>(ctx, st, d_pos, d_q, sums);
+    case 8: return launch_pme_t<8>(ctx, st, d_pos, d_q, sums);
     default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_pme(nb_ctx *ctx, const float *d_pos, const float *d_q)
 {
-    return launch_pme_on(ctx, ctx->stream, d_pos, d_q);
+    return launch_pme_on(ctx, ctx->stream, d_pos, d_q, true);
 }
 
-cudaError_t launch_pme_fork(nb_ctx *ctx, const float *d_pos, const float *d_q)
+cudaError_t launch_pme_fork(nb_ctx *ctx, const float *d_pos, const float *d_q, bool sums)
 {
     PmeState &P = *ctx->pme;
     cudaError_t e = cudaEventRecord(P.fork, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(P.side, P.fork, 0);
-    if (e == cudaSuccess) e = launch_pme_on(ctx, P.side, d_pos, d_q);
+    if (e == cudaSuccess) e = launch_pme_on(ctx, P.side, d_pos, d_q, sums);
     if (e == cudaSuccess) e = cudaEventRecord(P.join, P.side);
     return e;
 }
