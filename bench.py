@@ -754,7 +754,7 @@ def main():
 
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": traffic,
-                "kernel": "k_force (FP32 pair arithmetic)", "ms_per_launch": f_avg,
+                "kernel": "k_force1 (FP32 pair arithmetic, i-groups of one cluster)", "ms_per_launch": f_avg,
                 "peak_basis": (f"nominal: {n_sms} SMs x 128 FP32 lanes x 2 FLOP x {sm_med:.0f} MHz "
                                f"(median SM clock sampled during the timed steps)"),
                 "peak_at_max_clock": peak_at_max, "sm_max_mhz": sm_max, "sm_mhz_used": sm_med,

@@ -2,17 +2,19 @@
 // the GPU": the non-bonded kernel computes the full Lennard-Jones and
 // electrostatic force on each particle).  The paper's kernel does not reuse
 // the reciprocal force F_ji; here both kernels do (Newton's third law): every
-// unique pair is evaluated once, from the cluster whose half list holds it,
-// and its contribution goes to both atoms as 64-bit fixed point (2^32), so
-// the sums stay exact and order independent.
+// unique pair is evaluated once, from the i-group whose list holds it, and
+// its contribution goes to both atoms as 64-bit fixed point (2^32), so the
+// sums stay exact and order independent.
 //
-// Forward (k_force): one warp per listed cluster pair as an 8 x 8 tile,
-// forces on i kept in registers, forces on j summed over lanes (see the
-// comment above k_force).
+// Forward: k_force1 for i-groups of one cluster (one warp per listed
+// cluster pair as an 8 x 8 tile, the i cluster and its forces in registers,
+// forces on j summed over lanes; see the comment above k_force1), k_force<G>
+// for groups of 4 or 8 clusters (the group's atoms and i-force partials in
+// shared memory; see the comment above k_force).
 //
-// Adjoint (k_adjoint): the same tiles, work units and staging, with the
-// pair adjoint; the type-pair gradients go to a block table in shared
-// memory.
+// Adjoint: k_adjoint1 and k_adjoint<G>, the same tiles, work units and
+// staging with the pair adjoint; the type-pair gradients go to a block table
+// in shared memory.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -28,7 +30,7 @@ constexpr unsigned kFull = 0xffffffffu;
 struct ForceArgs {
     const SysDesc *sys;
     const int *counts;
-    int *work;                // work-unit counter of the tile kernels (zeroed by k_pack)
+    int *work;                // work-unit counter of the tile kernels (zeroed by k_pack or the column sort)
     const float4 *xyzq;
     const int *tslot;
     const int *perm;
