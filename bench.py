@@ -602,6 +602,43 @@ def cpu_oracle_run(system, budget_s: float = 12.0, max_reps: int = 50):
     return times, npairs, oracle.num_threads()
 
 
+def cpu_context():
+    """The FP64 oracle on every configuration, for context: the all-pairs
+    sum (one thread: the oracle parallelises only the cell-list traversal)
+    on the 256-atom crystal, the 6,144-atom water box and the 23,500-atom
+    chain, and the cell-list traversal on all cores on the chain, the
+    64-box ensemble and the 999,999-atom box; one or a few evaluations each
+    (about half a minute in all)."""
+    import oracle
+    from paper_0902_0827_gb300 import systems as S
+    oracle.build()
+    cores = oracle.num_threads()
+    rows = []
+
+    def run(name, systems, method, threads, reps):
+        oracle.set_threads(threads)
+        best, npairs = None, 0
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            npairs = sum(oracle.forces(s, method=method)[3] for s in systems)
+            dt = time.perf_counter() - t0
+            best = dt if best is None else min(best, dt)
+        rows.append({"config": name, "method": method, "threads": threads, "ms_per_eval": best * 1e3,
+                     "pairs_per_s": npairs / best, "evaluations": reps})
+
+    try:
+        fcc, water, chain = S.lj_fcc(), S.water_box(k=1, n_waters=2048), S.solvated_chain()
+        for name, s, reps in (("lj_fcc 256", fcc, 20), ("water_box 6,144", water, 2),
+                              ("solvated_chain 23,500", chain, 1)):
+            run(name, [s], "allpairs", 1, reps)
+        run("solvated_chain 23,500", [chain], "cells", cores, 5)
+        run("water_ensemble 64 boxes", S.water_ensemble(), "cells", cores, 1)
+        run("big_water 999,999", [S.big_water()], "cells", cores, 1)
+    finally:
+        oracle.set_threads(cores)
+    return {"kind": "oracle", "cores": cores, "rows": rows}
+
+
 def reference_arm(args, world, rank):
     """--impl reference: the FP64 CPU oracle on the same workload and metric."""
     if rank != 0:
@@ -831,6 +868,7 @@ def main():
         line["cpu_baseline"] = {"value": cp / per, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"{len(times)} full FP64 cell-list evaluations of the {N}-atom system",
                                 "ms_per_eval": per * 1e3}
+        line["cpu_context"] = cpu_context()
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

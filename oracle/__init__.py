@@ -80,6 +80,8 @@ def lib():
             L.orc_grid_dims.restype = None
             L.orc_num_threads.argtypes = []
             L.orc_num_threads.restype = I
+            L.orc_set_threads.argtypes = [I]
+            L.orc_set_threads.restype = None
             L.orc_set_table.argtypes = [I]
             L.orc_set_table.restype = None
             L.orc_ewald_recip.argtypes = [I64, P, P, P, D, D, I, I, I, P, P, P]
@@ -100,6 +102,11 @@ def _c(a, dtype):
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's OpenMP loops from now on (timing only)."""
+    lib().orc_set_threads(int(n))
 
 
 @contextlib.contextmanager
