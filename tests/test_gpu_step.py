@@ -90,3 +90,37 @@ def test_fill_counters_are_consistent(group):
     assert 0 < n <= 32 * halves <= 64 * tiles
     assert halves <= 2 * tiles
     assert 0.2 < n / (32 * halves) < 0.9
+
+
+@pytest.mark.parametrize("pme", [False, True])
+def test_step_replays_from_a_cuda_graph(pme):
+    # the bench's timed step: nb_step captured once on a side stream and
+    # replayed; the results equal those of plain calls bit for bit
+    s = S.solvated_chain()
+    ctx = nb.Nonbonded(s)
+    if pme:
+        ctx.set_pme((64, 64, 64), 4)
+    pos, q, t = nb.concat_inputs([s])
+    F = torch.empty((s.n_atoms, 3), dtype=torch.float32, device="cuda")
+    E = torch.empty((1, 2), dtype=torch.float64, device="cuda")
+    W = torch.empty((1, 6), dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        ctx.step(pos, q, t, F=F, energy=E, virial=W)
+    torch.cuda.synchronize()
+    F0, E0, W0 = F.clone(), E.clone(), W.clone()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        ctx.step(pos, q, t, F=F, energy=E, virial=W)  # the context moves to this stream outside the capture
+        with torch.cuda.graph(g, stream=side):
+            ctx.step(pos, q, t, F=F, energy=E, virial=W)
+    torch.cuda.current_stream().wait_stream(side)
+    F.zero_()
+    E.zero_()
+    W.zero_()
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    ctx.status()
+    assert torch.equal(F, F0) and torch.equal(E, E0) and torch.equal(W, W0)
