@@ -252,3 +252,31 @@ def test_minimize_matches_oracle_and_lowers_the_energy():
     ctx.status()
     assert E2[:5].sum().item() < e1[:5].sum()
     assert E2[5].item() == 0.0
+
+
+def test_step_with_tabulated_radial_functions_matches_oracle():
+    # the MD step on the 4096-interval tables (the paper's production
+    # setting) against the oracle's step on its own tables
+    s, top = water()
+    ctx, pos, q, t = setup(s, top, gamma=5.0)
+    ctx.set_tables(4096)
+    v0 = S.initial_velocities(top, 300.0)
+    vel = torch.from_numpy(v0).cuda()
+    E = torch.empty(6, dtype=torch.float64, device="cuda")
+    ctx.md_step(pos, vel, q, t, 2, E)
+    torch.cuda.synchronize()
+    ctx.status()
+    prm = omd.MDParams(dt=0.001, gamma=5.0, temperature=300.0, seed=2009)
+    x, v = s.pos.astype(np.float64), v0.astype(np.float64)
+    with oracle.tabulated(4096):
+        F, _ = omd.forces_at(s, top, x, prm)
+        for k in range(2):
+            x, v, F, Eo = omd.step(s, top, x, v, F, k, prm)
+    L = s.box.astype(np.float64)
+    dx = np.abs(min_image(pos.double().cpu().numpy() - x, L)).max()
+    rv = np.linalg.norm(vel.double().cpu().numpy() - v) / np.linalg.norm(v)
+    Eg = E.cpu().numpy()
+    print("tables: max dx", dx, "v rel", rv, "E", Eg[:2], Eo[:2])
+    assert dx <= 4e-5
+    assert rv <= 2e-5
+    assert abs(Eg[0] - Eo[0]) <= 1e-5 * abs(Eo[0])
