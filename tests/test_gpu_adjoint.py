@@ -27,8 +27,10 @@ def rel_rms(a, b):
     return np.linalg.norm(a[ok] - b[ok]) / max(np.linalg.norm(b[ok]), 1e-300)
 
 
-def gpu_backward(s, G, gE):
+def gpu_backward(s, G, gE, group=1):
     ctx = nb.Nonbonded(s)
+    if group != 1:
+        ctx.set_tuning(group_clusters=group, list_split=2)
     pos, q, t = nb.concat_inputs([s])
     ctx.build(pos)
     Gd = torch.from_numpy(np.ascontiguousarray(G, np.float32)).cuda()
@@ -89,6 +91,21 @@ def test_adjoint_matches_oracle(name, gE):
     assert rel_rms(gpos, dx) <= ADJ_RMS
     if np.any(s.q != 0):
         assert rel_rms(gq, dq) <= ADJ_RMS
+    check_params(s, gs_tab, ge_tab, gs, ge, dst, det, ds, de, aA, aB)
+
+
+@pytest.mark.parametrize("group", [4, 8])
+def test_adjoint_of_group_tiles_matches_oracle(group):
+    # the adjoint kernel of 4- and 8-cluster i-groups (the autotuner's other
+    # tile shapes), on the chain with exclusions and 1-4 pairs
+    s = CASES["chain_small"]()
+    rng = np.random.default_rng(6)
+    G = rng.normal(0.0, 1.0, size=(s.n_atoms, 3)).astype(np.float32)
+    gpos, gq, gs_tab, ge_tab, gs, ge = gpu_backward(s, G, 0.7, group=group)
+    dx, dq, dA, dB, aA, aB = oracle.backward(s, G.astype(np.float64), 0.7, with_scale=True)
+    dst, det, ds, de = oracle.lb_chain(s, dA, dB)
+    assert rel_rms(gpos, dx) <= ADJ_RMS
+    assert rel_rms(gq, dq) <= ADJ_RMS
     check_params(s, gs_tab, ge_tab, gs, ge, dst, det, ds, de, aA, aB)
 
 
