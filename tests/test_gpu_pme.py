@@ -205,3 +205,30 @@ def test_neutral_pair_of_excluded_charges_alone():
     Fr, Er, Wr, Fc, Es, Ep, Wc = pme_oracle(s, (48, 48, 48), 6)
     assert abs(E.sum() - (Er + Es + Ep)) <= REC_REL * (abs(Er) + abs(Es) + abs(Ep))
     assert np.abs(F - (Fr + Fc)).max() <= REC_REL * np.abs(Fr).max()
+
+
+@pytest.mark.parametrize("group", [4, 8])
+def test_pme_with_group_tiles(group):
+    # nb_forces with PME when the short-range kernel runs 4- or 8-cluster
+    # i-groups (and nb_step, which forks PME before the lists): the same
+    # full electrostatics as with single-cluster groups, to FP32 rounding
+    s = S.solvated_chain()
+    pos, q, t = nb.concat_inputs([s])
+    out = []
+    for g in (1, group):
+        ctx = nb.Nonbonded(s)
+        ctx.set_pme((64, 64, 64), 4)
+        if g != 1:
+            ctx.set_tuning(group_clusters=g, list_split=2)
+        ctx.build(pos)
+        F, E, W = ctx.forces(pos, q, t)
+        F2, E2, W2 = ctx.step(pos, q, t)
+        torch.cuda.synchronize()
+        ctx.status()
+        assert torch.equal(F, F2) and torch.equal(E, E2) and torch.equal(W, W2)
+        out.append((F.double().cpu().numpy(), E[0].cpu().numpy(), W[0].cpu().numpy()))
+    (F1, E1, W1), (Fg, Eg, Wg) = out
+    assert np.linalg.norm(Fg - F1) / np.linalg.norm(F1) <= 1e-6
+    # FP32 partial sums cut at different places: within the literal bar
+    assert np.all(np.abs(Eg - E1) <= 1e-6 * np.abs(E1))
+    assert np.abs(Wg - W1).max() <= 1e-6 * np.abs(W1).max()
