@@ -30,6 +30,11 @@
  *              "Molecular dynamics on the GPU", one particle per thread).
  * All values are FP64 over the exactly up-cast FP32 inputs.  Compile with
  * -ffp-contract=off so that the FP32 predicates round exactly as written.
+ *
+ * Parity unpinned: orc_binning, a specification of the sorted data layout
+ * (no result depends on it; the pair set it induces is pinned by brute
+ * force), and the conventions above that the paper does not fix (switch
+ * form, ke, the 1-4/exclusion weights under Ewald, the combination rule).
  */
 #include <math.h>
 #include <stdint.h>
