@@ -89,7 +89,8 @@ typedef struct {
     int32_t comb_rule;      /* 0: Lorentz-Berthelot; 1: explicit pair tables */
     const float *sigma_tab; /* host [T*T] symmetric sig_ab, comb_rule 1 */
     const float *eps_tab;   /* host [T*T] symmetric eps_ab, comb_rule 1 */
-    int32_t n_excl;         /* number of excluded pairs */
+    int32_t n_excl;         /* number of excluded pairs; every atom has at most 16 topology
+                               partners (excluded + scaled 1-4), NB_ERR_UNSUPPORTED otherwise */
     const int32_t *excl;    /* host [n_excl*2] atom pairs (i, j), i != j, 0-based */
     int32_t n_14;           /* number of scaled 1-4 pairs */
     const int32_t *pairs14; /* host [n_14*2], disjoint from excl */

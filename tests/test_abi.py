@@ -79,6 +79,12 @@ def test_host_validation_without_gpu():
     p, keep = _params(s)
     p.flags = 1
     assert _create(p)[0] == 1
+    # more than 16 topology partners (excluded + scaled 1-4) of one atom
+    s20 = S._water_system(S.rng_for(31), 7, "w21")
+    p, keep = _params(s20)
+    ex17 = np.array([[0, j] for j in range(1, 18)], np.int32)
+    p.n_excl, p.excl = 17, ex17.ctypes.data_as(ctypes.c_void_p)
+    assert _create(p)[0] == 11  # NB_ERR_UNSUPPORTED
     h = ctypes.c_void_p()
     assert nb.lib().nb_create(None, None, ctypes.byref(h)) == 1
     assert nb.lib().nb_build_cells(None, None) == 1

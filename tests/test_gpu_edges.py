@@ -216,3 +216,41 @@ def test_orthorhombic_boxes(which):
     ctx.status()
     assert np.array_equal(ij, oracle.pairs(s))
     check_forward(s, bars=(E_REL, "floor", "floor"), notes=("", "water Coulomb sum cancels", "water Coulomb sum cancels"))
+
+
+def sixteen_partners():
+    """A 200-atom chain in 600 waters where every interior chain atom has the
+    maximum of 16 topology partners: excluded (i, i +- 1..4) and scaled 1-4
+    (i, i +- 5..8), partners spread over several clusters."""
+    c = S.solvated_chain(k=25, n_chain=200, n_waters=600, L=26.0)
+    n = 200
+    ex = [(i, i + d) for d in range(1, 5) for i in range(n - d)]
+    p14 = [(i, i + d) for d in range(5, 9) for i in range(n - d)]
+    wex = c.excl[c.excl.min(axis=1) >= n]  # the waters' own exclusions
+    excl = np.concatenate([np.array(ex, np.int32), wex.astype(np.int32)])
+    return dataclasses.replace(c, name="chain_k16", excl=excl, pairs14=np.array(p14, np.int32))
+
+
+@pytest.mark.parametrize("group", [1, 8])
+def test_sixteen_topology_partners_per_atom(group):
+    s = sixteen_partners()
+    counts = np.bincount(np.concatenate([s.excl.ravel(), s.pairs14.ravel()]), minlength=s.n_atoms)
+    assert counts.max() == 16
+    ctx = nb.Nonbonded(s)
+    if group != 1:
+        ctx.set_tuning(group_clusters=group, list_split=2)
+    pos, q, t = nb.concat_inputs([s])
+    ctx.build(pos)
+    F, E, W = ctx.forces(pos, q, t)
+    ij, n, _ = ctx.debug_pairs()
+    torch.cuda.synchronize()
+    ctx.status()
+    assert np.array_equal(ij, oracle.pairs(s))
+    Fo, Eo, Wo, no, Es, Eq = oracle.forces(s, method="allpairs", with_scale=True, with_sq=True)
+    F = F.double().cpu().numpy()
+    assert np.linalg.norm(F - Fo) / np.linalg.norm(Fo) <= F_RMS
+    assert np.abs(F - Fo).max() <= F_MAX
+    parity.check_energy(f"chain_k16 g{group}", E[0].cpu().numpy(), Eo, Es, bars=(E_REL, "floor", "floor"),
+                        notes=("", "water Coulomb sum cancels", "water Coulomb sum cancels"), Eq=Eq)
+    W = W[0].cpu().numpy()
+    assert np.abs(W - Wo).max() <= W_REL * np.abs(Wo).max()
