@@ -39,11 +39,11 @@ if ROOT not in sys.path:
 
 METRIC = "pair interactions/s and ms per force eval at 23.5k atoms; % FP32 roofline"
 UNIT = "pairs/s"
-# kernels of this library per step: binning and lists (bin + scan, scatter,
+# kernels of this library per step: binning and lists (bin + scan + staging,
 # column sort, pair lists); forward (pack, force, unpack + energy/virial);
 # adjoint (pack, dL/dF gather, adjoint kernel, unpack, type-pair gradients);
 # nb_step (rebuild + forces in one call: the column sort packs, no pack kernel)
-BUILD_LAUNCHES = 4
+BUILD_LAUNCHES = 3
 FORCE_LAUNCHES = 3
 STEP_LAUNCHES = BUILD_LAUNCHES + FORCE_LAUNCHES - 1
 ADJOINT_LAUNCHES = 5

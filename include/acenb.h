@@ -290,7 +290,7 @@ nb_status nb_get_profile(nb_ctx *ctx, double *force_ms, int64_t *launches);
  *   d_pos, d_q, d_type, d_F, d_energy [2], d_virial [6]: as for nb_forces
  *            (d_energy / d_virial may be NULL);
  *   cuda_stream: the stream the work runs on.
- * All scratch lives in one static device array of about 5.9 MiB that every
+ * All scratch lives in one static device array of about 6.0 MiB that every
  * GPU loading this library holds until the library is unloaded; it bounds
  * the system to NB_NOALLOC_MAX_ATOMS atoms and NB_NOALLOC_MAX_COLUMNS x-y
  * columns (NB_ERR_TOO_LARGE otherwise).  The call allocates nothing (no

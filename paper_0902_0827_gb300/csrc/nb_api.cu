@@ -33,8 +33,8 @@ cudaError_t dalloc(T **p, size_t count)
 void free_all(nb_ctx *c)
 {
     auto &d = c->d;
-    void *ptrs[] = {d.sys, d.atom_sys, d.atom_col, d.wpos, d.part_orig, d.col_sys, d.col_count, d.col_fill,
-                    d.col_slot, d.stage, d.xyzq, d.tslot, d.perm, d.inv, d.bb,
+    void *ptrs[] = {d.sys, d.atom_sys, d.atom_col, d.wpos, d.part_orig, d.col_sys, d.col_count,
+                    d.col_slot, d.stage, d.stage_fix, d.xyzq, d.tslot, d.perm, d.inv, d.bb,
                     d.clus_sys, d.sys_acc, d.facc, d.gacc, d.col_grp, d.grp, d.clus_grp, d.glist, d.glist_n, d.gmask,
                     d.zbin, d.tab_grad, d.counts, d.status, d.lj_tab,
                     d.dbg_n, d.dbg_ij, d.scratch_f, d.scratch_g, d.lj_d, d.gslot, d.eps_type, d.rtab};
@@ -75,9 +75,9 @@ nb_status allocate(nb_ctx *c)
     ALLOC(d.part_orig, N * c->K);
     ALLOC(d.col_sys, C);
     ALLOC(d.col_count, C + 1);
-    ALLOC(d.col_fill, C);
     ALLOC(d.col_slot, C + 1);
     ALLOC(d.stage, S);
+    ALLOC(d.stage_fix, (int64_t)C * c->col_cap);
     ALLOC(d.xyzq, S);
     ALLOC(d.tslot, S);
     ALLOC(d.perm, S);
@@ -176,6 +176,7 @@ nb_status nb_create_batch(int32_t n_sys, const nb_params *params, void *cuda_str
     int col = 0, atom = 0;
     int64_t zb = 0;
     std::vector<int> atom_sys(N), col_sys;
+    double mean_col = 1.0;  // largest mean column population of the systems
     for (int s = 0; s < n_sys; ++s) {
         const nb_params &p = params[s];
         SysDesc &S = c->sys_h[s];
@@ -187,6 +188,7 @@ nb_status nb_create_batch(int32_t n_sys, const nb_params *params, void *cuda_str
         zb += zbin_entries(S);
         for (int a = 0; a < p.n_atoms; ++a) atom_sys[atom + a] = s;
         for (int k = 0; k < S.nx * S.ny; ++k) col_sys.push_back(s);
+        mean_col = std::max(mean_col, (double)p.n_atoms / (double)(S.nx * S.ny));
         atom += p.n_atoms;
         col += S.nx * S.ny;
     }
@@ -197,6 +199,7 @@ nb_status nb_create_batch(int32_t n_sys, const nb_params *params, void *cuda_str
     c->clus_cap = c->slot_cap / kCluster;
     c->grp_cap = group_capacity(c->clus_cap);
     c->mask_cap = mask_capacity(c->clus_cap);
+    c->col_cap = column_capacity(mean_col);
     // topology: per-atom partner lists (global indices), (orig << 1) | is14
     std::vector<std::vector<int>> part(N);
     for (int s = 0; s < n_sys; ++s) {

@@ -39,12 +39,12 @@ __device__ __forceinline__ int warp_aggregated_add(int *counter_base, int key)
 }
 
 // Block-wide exclusive scan of the padded column sizes (one block).  Fills
-// the column slot offsets, the scatter cursors, the totals and the
-// per-system slot/cluster ranges; then the first i-group of every column
-// (ceil(clusters / group) groups per column).
+// the column slot offsets, the totals and the per-system slot/cluster
+// ranges; then the first i-group of every column (ceil(clusters / group)
+// groups per column).
 __device__ void scan_columns(int n_cols, int n_sys, const int *__restrict__ col_count, int *__restrict__ col_slot,
-                             int *__restrict__ col_fill, SysDesc *__restrict__ sys, int *__restrict__ counts,
-                             int group, int *__restrict__ col_grp)
+                             SysDesc *__restrict__ sys, int *__restrict__ counts, int group,
+                             int *__restrict__ col_grp)
 {
     __shared__ int warp_sum[32];
     __shared__ int carry;
@@ -78,7 +78,6 @@ __device__ void scan_columns(int n_cols, int n_sys, const int *__restrict__ col_
         if (c < n_cols) {
             if (pass == 0) {
                 col_slot[c] = excl;
-                col_fill[c] = excl;
             } else {
                 col_grp[c] = excl;
             }
@@ -109,14 +108,18 @@ __device__ void scan_columns(int n_cols, int n_sys, const int *__restrict__ col_
     }
 }
 
-// A1 + A2: one atom per thread: wrap, column index, column histogram
-// (warp-aggregated atomics); the last block to finish scans the histogram.
-// col_count[n_cols] is the completion ticket (zero on entry, reset on exit).
+// A1 + A2 + A3a: one atom per thread: wrap, column index, column histogram
+// (warp-aggregated atomics, whose returned counts are the atoms' places in
+// their column): each atom goes to its place in its column's fixed-capacity
+// staging row (stage_fix[col * col_cap + place]; a place at or beyond
+// col_cap is left to the column sort's fallback).  The last block to finish
+// scans the histogram.  col_count[n_cols] is the completion ticket (zero on
+// entry, reset on exit).
 __global__ void k_bin(int n, const float *__restrict__ pos, SysDesc *__restrict__ sys,
                       const int *__restrict__ atom_sys, float4 *__restrict__ wpos, int *__restrict__ atom_col,
                       int *__restrict__ col_count, int n_cols, int n_sys, int *__restrict__ col_slot,
-                      int *__restrict__ col_fill, int *__restrict__ counts, int *__restrict__ status, int group,
-                      int *__restrict__ col_grp)
+                      int *__restrict__ stage_fix, int col_cap, int *__restrict__ counts, int *__restrict__ status,
+                      int group, int *__restrict__ col_grp)
 {
     pdl_entry();
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
@@ -141,7 +144,8 @@ __global__ void k_bin(int n, const float *__restrict__ pos, SysDesc *__restrict_
         atom_col[a] = col;
         wpos[a] = make_float4(x, y, z, 0.0f);
     }
-    warp_aggregated_add(col_count, col);
+    const int place = warp_aggregated_add(col_count, col);
+    if (col >= 0 && place < col_cap) stage_fix[(long long)col * col_cap + place] = a;
     // last block: the histogram is complete.  The barrier orders the block's
     // counter updates before thread 0's fence, which (cumulatively) orders
     // them before the ticket.
@@ -154,19 +158,8 @@ __global__ void k_bin(int n, const float *__restrict__ pos, SysDesc *__restrict_
     __syncthreads();
     if (!last) return;
     __threadfence();
-    scan_columns(n_cols, n_sys, col_count, col_slot, col_fill, sys, counts, group, col_grp);
+    scan_columns(n_cols, n_sys, col_count, col_slot, sys, counts, group, col_grp);
     if (threadIdx.x == 0) col_count[n_cols] = 0;
-}
-
-// A3a: place atoms into their column segment (order fixed by the sort below).
-__global__ void k_scatter(int n, const int *__restrict__ atom_col, int *__restrict__ col_fill,
-                          int *__restrict__ stage)
-{
-    pdl_entry();
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    const int col = a < n ? atom_col[a] : -1;
-    const int p = warp_aggregated_add(col_fill, col);
-    if (a < n) stage[p] = a;
 }
 
 constexpr int kSortSmem = 1024;  // atoms per column sorted from shared memory
@@ -250,7 +243,8 @@ __device__ __forceinline__ int packed_type(const ColPack &pk, int a)
 // the same order.
 __global__ void __launch_bounds__(kSortThreads) k_colsort(
     const int *__restrict__ col_count, const int *__restrict__ col_slot, const int *__restrict__ col_sys,
-    const SysDesc *__restrict__ sys, const int *__restrict__ stage, const float4 *__restrict__ wpos,
+    const SysDesc *__restrict__ sys, const int *__restrict__ stage_fix, int col_cap, int *__restrict__ stage,
+    const int *__restrict__ atom_col, const float4 *__restrict__ wpos,
     float4 *__restrict__ xyzq, int *__restrict__ tslot, int *__restrict__ perm, int *__restrict__ inv,
     float4 *__restrict__ bb, int *__restrict__ clus_sys, int2 *__restrict__ zbin, int group,
     const int *__restrict__ col_grp, int2 *__restrict__ grp, int *__restrict__ clus_grp, ColPack pk)
@@ -263,6 +257,20 @@ __global__ void __launch_bounds__(kSortThreads) k_colsort(
     const int n = col_count[c];
     const int base = col_slot[c];
     const int npad = (n + kCluster - 1) / kCluster * kCluster;
+    // the column's atoms: its staging row, or, when the column outgrew the
+    // row's capacity (strongly uneven density), gathered here from the
+    // system's atoms into the column's own slots (slow, rare)
+    const int *src = stage_fix + (long long)c * col_cap;
+    if (n > col_cap) {
+        __shared__ int s_fill;
+        if (tid == 0) s_fill = 0;
+        __syncthreads();
+        const SysDesc &S0 = sys[col_sys[c]];
+        for (int a = S0.atom_begin + tid; a < S0.atom_begin + S0.n_atoms; a += blockDim.x)
+            if (atom_col[a] == c) stage[base + atomicAdd(&s_fill, 1)] = a;
+        __syncthreads();
+        src = stage + base;
+    }
     const bool small = n <= kSortSmem;
     if (small && n > kRankSortMax) {
         int P = 1;
@@ -270,7 +278,7 @@ __global__ void __launch_bounds__(kSortThreads) k_colsort(
         for (int k = tid; k < P; k += blockDim.x) {
             unsigned long long key = ~0ull;  // padding sorts last
             if (k < n) {
-                const int a = stage[base + k];
+                const int a = src[k];
                 key = zkey(wpos[a].z, a);
             }
             skey[k] = key;
@@ -298,7 +306,7 @@ __global__ void __launch_bounds__(kSortThreads) k_colsort(
             key[u] = ~0ull;
             rank[u] = 0;
             if (k < n) {
-                const int a = stage[base + k];
+                const int a = src[k];
                 p[u] = wpos[a];
                 key[u] = zkey(p[u].z, a);
                 skey[k] = key[u];
@@ -324,12 +332,12 @@ __global__ void __launch_bounds__(kSortThreads) k_colsort(
         }
     } else {
         for (int k = tid; k < n; k += blockDim.x) {
-            const int a = stage[base + k];
+            const int a = src[k];
             const float4 pa = wpos[a];
             const unsigned long long ka = zkey(pa.z, a);
             int rank = 0;
             for (int m = 0; m < n; ++m) {
-                const int b = stage[base + m];
+                const int b = src[m];
                 rank += zkey(wpos[b].z, b) < ka;
             }
             const int slot = base + rank;
@@ -907,13 +915,11 @@ cudaError_t launch_build_cells(nb_ctx *ctx, const float *d_pos, const float *d_q
     if (e != cudaSuccess) return e;
     const int tb = 256;
     e = launch_pdl(k_bin, dim3((N + tb - 1) / tb), dim3(tb), 0, st, N, d_pos, d.sys, d.atom_sys, d.wpos, d.atom_col,
-                   d.col_count, ctx->n_cols, ctx->n_sys, d.col_slot, d.col_fill, d.counts, d.status, ctx->group,
-                   d.col_grp);
-    if (e == cudaSuccess)
-        e = launch_pdl(k_scatter, dim3((N + tb - 1) / tb), dim3(tb), 0, st, N, d.atom_col, d.col_fill, d.stage);
+                   d.col_count, ctx->n_cols, ctx->n_sys, d.col_slot, d.stage_fix, ctx->col_cap, d.counts, d.status,
+                   ctx->group, d.col_grp);
     if (e == cudaSuccess)
         e = launch_pdl(k_colsort, dim3(ctx->n_cols), dim3(kSortThreads), 0, st, d.col_count, d.col_slot, d.col_sys,
-                       d.sys, d.stage, d.wpos, d.xyzq, d.tslot, d.perm, d.inv, d.bb, d.clus_sys, d.zbin, ctx->group,
+                       d.sys, (const int *)d.stage_fix, ctx->col_cap, d.stage, (const int *)d.atom_col, d.wpos, d.xyzq, d.tslot, d.perm, d.inv, d.bb, d.clus_sys, d.zbin, ctx->group,
                        d.col_grp, d.grp, d.clus_grp,
                        ColPack{d_q, d_type, ctx->pp.n_types, d.facc, d.sys_acc, kTaskVals * ctx->n_sys, d.counts + 3,
                                d.status});

@@ -112,9 +112,9 @@ struct DevBuffers {
     int *part_orig = nullptr;        // [N*K] partner (orig << 1) | is14, -1 pad (static)
     int *col_sys = nullptr;          // [C] system of each column (static)
     int *col_count = nullptr;        // [C+1] column histogram; [C] = completion ticket of the binning kernel
-    int *col_fill = nullptr;         // [C] scatter cursor
     int *col_slot = nullptr;         // [C+1] padded slot offsets
-    int *stage = nullptr;            // [S] unsorted atoms per column
+    int *stage = nullptr;            // [S] unsorted atoms of a column whose staging row overflowed
+    int *stage_fix = nullptr;        // [C * col_cap] unsorted atoms per column, fixed capacity
     float4 *xyzq = nullptr;          // [S] sorted x, y, z, q (kPadCoord for padding)
     int *tslot = nullptr;            // [S] sorted types
     int *perm = nullptr;             // [S] slot -> atom (-1 padding)
@@ -163,6 +163,7 @@ struct nb_ctx {
     int built_group = 0;           // the group size the current lists were built with
     int64_t grp_cap = 0;           // i-group slots (enough for groups of 4)
     int64_t mask_cap = 0;          // exclusion-mask records
+    int col_cap = 0;               // atoms per column staging row (about twice the mean column)
     int tab_n = 0;                 // radial-function table intervals (0: direct evaluation)
     int64_t zb_total = 0;          // entries of the z-bin index
     int smem_optin = 0;            // device opt-in shared memory per block
@@ -239,6 +240,10 @@ inline int64_t group_capacity(int64_t clus_cap) { return clus_cap + 1; }
 // them.
 inline int64_t mask_pool_base(int64_t clus_cap) { return clus_cap * kMaskRecsPerCluster; }
 inline int64_t mask_capacity(int64_t clus_cap) { return mask_pool_base(clus_cap) + clus_cap / 2 + 64; }
+// atoms per column staging row for a mean column population: twice the mean
+// and 32 more, in whole warps (rows that overflow are gathered by the column
+// sort's slow fallback)
+inline int column_capacity(double mean_atoms) { return ((int)(2.0 * mean_atoms) + 32 + 31) / 32 * 32; }
 
 // Launchers implemented in the .cu files (all asynchronous on ctx->stream).
 cudaError_t launch_build(nb_ctx *ctx, const float *d_pos);

@@ -9,7 +9,7 @@
 // runs the same binning and force kernels as nb_build_cells + nb_forces for
 // one system of at most NB_NOALLOC_MAX_ATOMS atoms, with every scratch buffer
 // carved from one file-scope device array (g_noalloc_scratch below, about
-// 5.9 MiB).  That array exists on every GPU that loads this library, for as
+// 6.0 MiB).  That array exists on every GPU that loads this library, for as
 // long as the library stays loaded.
 //
 // In host code the name g_noalloc_scratch only stands for the device symbol;
@@ -27,6 +27,8 @@
 // serialise them.
 #include <cuda_runtime.h>
 #include <string.h>
+
+#include <algorithm>
 
 #include "acenb.h"
 #include "nb_host.cuh"
@@ -57,8 +59,9 @@ constexpr size_t oWpos = oAtomCol + a256(4ull * kMaxAtoms);
 constexpr size_t oPart = oWpos + a256(16ull * kMaxAtoms);
 constexpr size_t oColSys = oPart + a256(4ull * kMaxAtoms * kMaxPartners);
 constexpr size_t oColCount = oColSys + a256(4ull * kMaxCols);
-constexpr size_t oColFill = oColCount + a256(4ull * (kMaxCols + 1));
-constexpr size_t oColSlot = oColFill + a256(4ull * kMaxCols);
+constexpr long long kStageFix = 4 * kSlots;  // column staging rows (col_cap per column, fitted to the system)
+constexpr size_t oStageFix = oColCount + a256(4ull * (kMaxCols + 1));
+constexpr size_t oColSlot = oStageFix + a256(4ull * kStageFix);
 constexpr size_t oStage = oColSlot + a256(4ull * (kMaxCols + 1));
 constexpr size_t oXyzq = oStage + a256(4ull * kSlots);
 constexpr size_t oTslot = oXyzq + a256(16ull * kSlots);
@@ -180,6 +183,7 @@ extern "C" nb_status nb_forces_noalloc(const nb_params *params, const float *d_p
     c.group = kDefaultGroup;
     c.grp_cap = kGrp;
     c.mask_cap = kMaskRecs;
+    c.col_cap = std::max(1, std::min(column_capacity((double)N / (double)C), (int)(kStageFix / C)));
     c.stage_cap = 96;
     c.list_cap = kListCap;
     c.zb_total = host::zbin_entries(S);
@@ -192,7 +196,7 @@ extern "C" nb_status nb_forces_noalloc(const nb_params *params, const float *d_p
     d.part_orig = at<int>(base, oPart);
     d.col_sys = at<int>(base, oColSys);
     d.col_count = at<int>(base, oColCount);
-    d.col_fill = at<int>(base, oColFill);
+    d.stage_fix = at<int>(base, oStageFix);
     d.col_slot = at<int>(base, oColSlot);
     d.stage = at<int>(base, oStage);
     d.xyzq = at<float4>(base, oXyzq);
