@@ -107,6 +107,7 @@ nb_status allocate(nb_ctx *c)
     e = cudaMemset(d.tslot, 0, sizeof(int) * S);
     if (e == cudaSuccess) e = cudaMemset(d.status, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(d.counts, 0, sizeof(int) * 8);
+    if (e == cudaSuccess) e = cudaMemset(d.col_count, 0, sizeof(int) * (C + 1));  // kept zero between builds
     return cuda_status(e);
 }
 

@@ -242,7 +242,7 @@ __device__ __forceinline__ int packed_type(const ColPack &pk, int a)
 // ones by a bitonic network (n log^2 n).  The keys are unique, so both give
 // the same order.
 __global__ void __launch_bounds__(kSortThreads) k_colsort(
-    const int *__restrict__ col_count, const int *__restrict__ col_slot, const int *__restrict__ col_sys,
+    int *__restrict__ col_count, const int *__restrict__ col_slot, const int *__restrict__ col_sys,
     const SysDesc *__restrict__ sys, const int *__restrict__ stage_fix, int col_cap, int *__restrict__ stage,
     const int *__restrict__ atom_col, const float4 *__restrict__ wpos,
     float4 *__restrict__ xyzq, int *__restrict__ tslot, int *__restrict__ perm, int *__restrict__ inv,
@@ -404,6 +404,9 @@ __global__ void __launch_bounds__(kSortThreads) k_colsort(
         }
         zt[b] = make_int2(lo, lo2);
     }
+    // the column's count is used: zero it for the next build (every thread
+    // read it before the barriers above), so no memset precedes the binning
+    if (tid == 0) col_count[c] = 0;
 }
 
 // Opposite periodic image of a list entry's shift code: 1 <-> 2 on every axis.
@@ -911,10 +914,10 @@ cudaError_t launch_build_cells(nb_ctx *ctx, const float *d_pos, const float *d_q
     auto &d = ctx->d;
     cudaStream_t st = ctx->stream;
     const int N = (int)ctx->n_atoms;
-    cudaError_t e = cudaMemsetAsync(d.col_count, 0, sizeof(int) * (ctx->n_cols + 1), st);
-    if (e != cudaSuccess) return e;
+    // the column counts are zero here: zeroed at create and by the column
+    // sort of the previous build (the completion ticket by the binning)
     const int tb = 256;
-    e = launch_pdl(k_bin, dim3((N + tb - 1) / tb), dim3(tb), 0, st, N, d_pos, d.sys, d.atom_sys, d.wpos, d.atom_col,
+    cudaError_t e = launch_pdl(k_bin, dim3((N + tb - 1) / tb), dim3(tb), 0, st, N, d_pos, d.sys, d.atom_sys, d.wpos, d.atom_col,
                    d.col_count, ctx->n_cols, ctx->n_sys, d.col_slot, d.stage_fix, ctx->col_cap, d.counts, d.status,
                    ctx->group, d.col_grp);
     if (e == cudaSuccess)

@@ -227,6 +227,7 @@ extern "C" nb_status nb_forces_noalloc(const nb_params *params, const float *d_p
     if (e == cudaSuccess) e = cudaMemcpyAsync(d.part_orig, h_part, sizeof(int) * N * K, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d.lj_tab, h_lj, sizeof(float4) * T * T, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.status, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.col_count, 0, sizeof(int) * (C + 1), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.tslot, 0, sizeof(int) * c.slot_cap, s);
     if (e == cudaSuccess) e = launch_build(&c, d_pos);
     if (e == cudaSuccess) e = launch_forces(&c, d_pos, d_q, d_type, d_F, d_energy, d_virial, false);
