@@ -597,17 +597,21 @@ __host__ __device__ inline size_t glist_warp_ints(int K, int group) { return 2 *
 
 __global__ void __launch_bounds__(kGListWarps * 32, ACENB_GLIST_MIN_BLOCKS) k_glist(GListArgs A)
 {
-    pdl_entry();
     const unsigned FULL = 0xffffffffu;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = blockIdx.x * kGListWarps + w;
+    __shared__ int s_hash_all[kGListWarps][kHashSlots];
+    __shared__ int s_head_all[kGListWarps][kHashSlots];
+    for (int t = lane; t < kHashSlots; t += 32) {  // cleared before the wait: no input needed
+        s_hash_all[w][t] = -1;
+        s_head_all[w][t] = kLinkEnd;
+    }
+    pdl_entry();
     if (g >= A.counts[4]) return;  // the whole warp
     const unsigned lt = (1u << lane) - 1u;
     const int2 gr = A.grp[g];
     const int c0 = gr.x, n = gr.y, K = A.K;
     __shared__ float4 s_lo_all[kGListWarps][kMaxGroup], s_hi_all[kGListWarps][kMaxGroup];
-    __shared__ int s_hash_all[kGListWarps][kHashSlots];
-    __shared__ int s_head_all[kGListWarps][kHashSlots];
     __shared__ int s_col_all[kGListWarps][32];
     __shared__ int4 s_ci_all[kGListWarps][32];    // per window: jb, nj, first virtual index - offset, code
     __shared__ float2 s_co_all[kGListWarps][32];  // per window: x, y image shift
@@ -620,10 +624,6 @@ __global__ void __launch_bounds__(kGListWarps * 32, ACENB_GLIST_MIN_BLOCKS) k_gl
     unsigned char *s_own = s_own_all[w];
     int *s_pslot = s_dyn + (size_t)w * glist_warp_ints(K, A.group);  // [8 n K] partner slots (slot << 1) | is14
     int *s_link = s_pslot + kCluster * A.group * K;                   // [8 n K] chains of the partner-cluster table
-    for (int t = lane; t < kHashSlots; t += 32) {
-        s_hash[t] = -1;
-        s_head[t] = kLinkEnd;
-    }
     if (lane < n) {
         s_lo[lane] = A.bb[2 * (c0 + lane)];
         s_hi[lane] = A.bb[2 * (c0 + lane) + 1];

@@ -548,7 +548,6 @@ __host__ __device__ inline size_t tile_warp_bytes(int G)
 template <int G, int RAD, bool VIRIAL, bool DEBUG>
 __global__ void __launch_bounds__(kTileWarps * 32, ACENB_TILE_MIN_BLOCKS) k_force(ForceArgs A, int parts)
 {
-    pdl_entry();
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long s_val[kTileWarps][kTaskVals];
     __shared__ int s_sys[kTileWarps];
@@ -567,6 +566,7 @@ __global__ void __launch_bounds__(kTileWarps * 32, ACENB_TILE_MIN_BLOCKS) k_forc
         lj[k] = make_float4(ab.x, ab.y, 12.0f * ab.x, 6.0f * ab.y);
         reinterpret_cast<float2 *>(lj + T * T)[k] = make_float2(ab.z, ab.w);
     }
+    pdl_entry();  // the type-pair tables do not depend on the preceding kernels
     __syncthreads();
     const int n_units = A.counts[4] * kListSegs * parts;
     int cur_sys = -1;
@@ -854,7 +854,6 @@ __host__ __device__ inline size_t tile1_warp_bytes() { return (size_t)kBatch1 * 
 template <int RAD, bool VIRIAL, bool DEBUG>
 __global__ void __launch_bounds__(kTileWarps * 32, ACENB_TILE_MIN_BLOCKS) k_force1(ForceArgs A, int parts)
 {
-    pdl_entry();
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long s_val[kTileWarps][kTaskVals];
     __shared__ int s_sys[kTileWarps];
@@ -868,6 +867,7 @@ __global__ void __launch_bounds__(kTileWarps * 32, ACENB_TILE_MIN_BLOCKS) k_forc
         lj[k] = make_float4(ab.x, ab.y, 12.0f * ab.x, 6.0f * ab.y);
         reinterpret_cast<float2 *>(lj + T * T)[k] = make_float2(ab.z, ab.w);
     }
+    pdl_entry();  // the type-pair tables do not depend on the preceding kernels
     __syncthreads();
     const int n_units = A.counts[4] * kListSegs * parts;
     int cur_sys = -1;
@@ -1103,7 +1103,6 @@ __device__ __forceinline__ void adj_entry(const ForceArgs &A, const AdjTables &t
 template <int G, int RAD>
 __global__ void __launch_bounds__(kAdjWarps * 32) k_adjoint(ForceArgs A, int parts)
 {
-    pdl_entry();
     extern __shared__ __align__(16) unsigned char smem[];
     const int T = A.P.n_types;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, ia = lane & 7, jb = lane >> 3;
@@ -1128,6 +1127,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_adjoint(ForceArgs A, int par
         tacc[2 * k] = 0ull;
         tacc[2 * k + 1] = 0ull;
     }
+    pdl_entry();  // the type-pair tables do not depend on the preceding kernels
     __syncthreads();
     const AdjTables tab{lj, ljd, tacc};
     const int n_units = A.counts[4] * kListSegs * parts;
@@ -1335,7 +1335,6 @@ size_t adjoint1_smem_bytes(int T)
 template <int RAD>
 __global__ void __launch_bounds__(kAdjWarps * 32) k_adjoint1(ForceArgs A, int parts)
 {
-    pdl_entry();
     extern __shared__ __align__(16) unsigned char smem[];
     const int T = A.P.n_types;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, jj = lane & 7, ih = lane >> 3;
@@ -1355,6 +1354,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_adjoint1(ForceArgs A, int pa
         tacc[2 * k] = 0ull;
         tacc[2 * k + 1] = 0ull;
     }
+    pdl_entry();  // the type-pair tables do not depend on the preceding kernels
     __syncthreads();
     const AdjTables tab{lj, ljd, tacc};
     const int n_units = A.counts[4] * kListSegs * parts;

@@ -199,11 +199,14 @@ __device__ __forceinline__ float wrap_coord(float x, float L)
     return x;
 }
 
-// Programmatic dependent launch.  Every kernel of the library starts with
-// pdl_entry(): griddepcontrol.wait blocks until the preceding kernel in the
-// stream has completed and its memory is visible (a no-op for a plain
-// launch), then launch_dependents lets the next kernel's blocks be scheduled
-// while this one runs, so consecutive launches do not leave the GPU idle.
+// Programmatic dependent launch.  Every kernel of the library calls
+// pdl_entry() before it reads or writes anything that another kernel writes
+// (at its start, or after a prologue that only fills shared memory from
+// tables set at creation): griddepcontrol.wait blocks until the preceding
+// kernel in the stream has completed and its memory is visible (a no-op for
+// a plain launch), then launch_dependents lets the next kernel's blocks be
+// scheduled while this one runs, so consecutive launches do not leave the
+// GPU idle.
 __device__ __forceinline__ void pdl_entry()
 {
     asm volatile("griddepcontrol.wait;" ::: "memory");
