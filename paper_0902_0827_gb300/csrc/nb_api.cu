@@ -74,7 +74,7 @@ nb_status allocate(nb_ctx *c)
     ALLOC(d.wpos, N);
     ALLOC(d.part_orig, N * c->K);
     ALLOC(d.col_sys, C);
-    ALLOC(d.col_count, C + 1);
+    ALLOC(d.col_count, 2 * C + 1);
     ALLOC(d.col_slot, C + 1);
     ALLOC(d.stage, S);
     ALLOC(d.stage_fix, (int64_t)C * c->col_cap);
@@ -107,7 +107,7 @@ nb_status allocate(nb_ctx *c)
     e = cudaMemset(d.tslot, 0, sizeof(int) * S);
     if (e == cudaSuccess) e = cudaMemset(d.status, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(d.counts, 0, sizeof(int) * 8);
-    if (e == cudaSuccess) e = cudaMemset(d.col_count, 0, sizeof(int) * (C + 1));  // kept zero between builds
+    if (e == cudaSuccess) e = cudaMemset(d.col_count, 0, sizeof(int) * (2 * C + 1));  // kept zero between builds
     return cuda_status(e);
 }
 

@@ -41,8 +41,9 @@ __device__ __forceinline__ int warp_aggregated_add(int *counter_base, int key)
 // Block-wide exclusive scan of the padded column sizes (one block).  Fills
 // the column slot offsets, the totals and the per-system slot/cluster
 // ranges; then the first i-group of every column (ceil(clusters / group)
-// groups per column).
-__device__ void scan_columns(int n_cols, int n_sys, const int *__restrict__ col_count, int *__restrict__ col_slot,
+// groups per column), copying each column's count behind the histogram for
+// the column sort and zeroing the histogram for the next build.
+__device__ void scan_columns(int n_cols, int n_sys, int *__restrict__ col_count, int *__restrict__ col_slot,
                              SysDesc *__restrict__ sys, int *__restrict__ counts, int group,
                              int *__restrict__ col_grp)
 {
@@ -54,7 +55,12 @@ __device__ void scan_columns(int n_cols, int n_sys, const int *__restrict__ col_
     for (int pass = 0; pass < 2; ++pass) {
     for (int base = 0; base < n_cols; base += blockDim.x) {
         int c = base + threadIdx.x;
-        const int ncl = c < n_cols ? (__ldcg(&col_count[c]) + kCluster - 1) / kCluster : 0;
+        const int cnt = c < n_cols ? __ldcg(&col_count[c]) : 0;
+        const int ncl = (cnt + kCluster - 1) / kCluster;
+        if (pass == 1 && c < n_cols) {  // the count for the column sort; the histogram is zero again
+            col_count[n_cols + 1 + c] = cnt;
+            col_count[c] = 0;
+        }
         int v = pass == 0 ? ncl * kCluster : (ncl + group - 1) / group;
         int x = v;
 #pragma unroll
@@ -125,7 +131,7 @@ __global__ void k_bin(int n, const float *__restrict__ pos, SysDesc *__restrict_
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     int col = -1;
     if (a < n) {
-        const SysDesc &S = sys[atom_sys[a]];
+        const SysDesc &S = sys[n_sys == 1 ? 0 : atom_sys[a]];  // one system: no dependent load
         float x = pos[3ll * a], y = pos[3ll * a + 1], z = pos[3ll * a + 2];
         if (!(isfinite(x) && isfinite(y) && isfinite(z))) {
             atomicOr(status, ST_NONFINITE);
@@ -242,7 +248,7 @@ __device__ __forceinline__ int packed_type(const ColPack &pk, int a)
 // ones by a bitonic network (n log^2 n).  The keys are unique, so both give
 // the same order.
 __global__ void __launch_bounds__(kSortThreads) k_colsort(
-    int *__restrict__ col_count, const int *__restrict__ col_slot, const int *__restrict__ col_sys,
+    const int *__restrict__ col_count, const int *__restrict__ col_slot, const int *__restrict__ col_sys,
     const SysDesc *__restrict__ sys, const int *__restrict__ stage_fix, int col_cap, int *__restrict__ stage,
     const int *__restrict__ atom_col, const float4 *__restrict__ wpos,
     float4 *__restrict__ xyzq, int *__restrict__ tslot, int *__restrict__ perm, int *__restrict__ inv,
@@ -404,9 +410,6 @@ __global__ void __launch_bounds__(kSortThreads) k_colsort(
         }
         zt[b] = make_int2(lo, lo2);
     }
-    // the column's count is used: zero it for the next build (every thread
-    // read it before the barriers above), so no memset precedes the binning
-    if (tid == 0) col_count[c] = 0;
 }
 
 // Opposite periodic image of a list entry's shift code: 1 <-> 2 on every axis.
@@ -914,14 +917,14 @@ cudaError_t launch_build_cells(nb_ctx *ctx, const float *d_pos, const float *d_q
     auto &d = ctx->d;
     cudaStream_t st = ctx->stream;
     const int N = (int)ctx->n_atoms;
-    // the column counts are zero here: zeroed at create and by the column
-    // sort of the previous build (the completion ticket by the binning)
+    // the column counts are zero here: zeroed at create and by the scan of
+    // the previous build's binning kernel, which leaves a copy for the sort
     const int tb = 256;
     cudaError_t e = launch_pdl(k_bin, dim3((N + tb - 1) / tb), dim3(tb), 0, st, N, d_pos, d.sys, d.atom_sys, d.wpos, d.atom_col,
                    d.col_count, ctx->n_cols, ctx->n_sys, d.col_slot, d.stage_fix, ctx->col_cap, d.counts, d.status,
                    ctx->group, d.col_grp);
     if (e == cudaSuccess)
-        e = launch_pdl(k_colsort, dim3(ctx->n_cols), dim3(kSortThreads), 0, st, d.col_count, d.col_slot, d.col_sys,
+        e = launch_pdl(k_colsort, dim3(ctx->n_cols), dim3(kSortThreads), 0, st, (const int *)d.col_count + ctx->n_cols + 1, d.col_slot, d.col_sys,
                        d.sys, (const int *)d.stage_fix, ctx->col_cap, d.stage, (const int *)d.atom_col, d.wpos, d.xyzq, d.tslot, d.perm, d.inv, d.bb, d.clus_sys, d.zbin, ctx->group,
                        d.col_grp, d.grp, d.clus_grp,
                        ColPack{d_q, d_type, ctx->pp.n_types, d.facc, d.sys_acc, kTaskVals * ctx->n_sys, d.counts + 3,

@@ -111,7 +111,8 @@ struct DevBuffers {
     float4 *wpos = nullptr;          // [N] wrapped coordinates
     int *part_orig = nullptr;        // [N*K] partner (orig << 1) | is14, -1 pad (static)
     int *col_sys = nullptr;          // [C] system of each column (static)
-    int *col_count = nullptr;        // [C+1] column histogram; [C] = completion ticket of the binning kernel
+    int *col_count = nullptr;        // [2C+1] column histogram (zero between builds); [C] = completion ticket
+                                     // of the binning kernel; [C+1+c] = column c's count for the column sort
     int *col_slot = nullptr;         // [C+1] padded slot offsets
     int *stage = nullptr;            // [S] unsorted atoms of a column whose staging row overflowed
     int *stage_fix = nullptr;        // [C * col_cap] unsorted atoms per column, fixed capacity

@@ -60,7 +60,7 @@ constexpr size_t oPart = oWpos + a256(16ull * kMaxAtoms);
 constexpr size_t oColSys = oPart + a256(4ull * kMaxAtoms * kMaxPartners);
 constexpr size_t oColCount = oColSys + a256(4ull * kMaxCols);
 constexpr long long kStageFix = 4 * kSlots;  // column staging rows (col_cap per column, fitted to the system)
-constexpr size_t oStageFix = oColCount + a256(4ull * (kMaxCols + 1));
+constexpr size_t oStageFix = oColCount + a256(4ull * (2 * kMaxCols + 1));
 constexpr size_t oColSlot = oStageFix + a256(4ull * kStageFix);
 constexpr size_t oStage = oColSlot + a256(4ull * (kMaxCols + 1));
 constexpr size_t oXyzq = oStage + a256(4ull * kSlots);
