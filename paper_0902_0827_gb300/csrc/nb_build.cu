@@ -229,15 +229,16 @@ struct ColPack {
     int *status;
 };
 
-__device__ __forceinline__ int packed_type(const ColPack &pk, int a)
+__device__ __forceinline__ int checked_type(const ColPack &pk, int t)
 {
-    int t = pk.type[a];
     if (t < 0 || t >= pk.T) {
         atomicOr(pk.status, ST_BADTYPE);
         t = 0;
     }
     return t;
 }
+
+__device__ __forceinline__ int packed_type(const ColPack &pk, int a) { return checked_type(pk, pk.type[a]); }
 
 // A3b: one block per column: sort by (z, atom index), write the sorted slot
 // arrays and padding, the cluster bounding boxes and the column's z-bin
@@ -304,16 +305,22 @@ __global__ void __launch_bounds__(kSortThreads) k_colsort(
     } else if (small) {
         const int nper = (n + kSortThreads - 1) / kSortThreads;
         unsigned long long key[kSortPer];
-        float4 p[kSortPer];
+        float4 p[kSortPer];  // w: the charge when packing
+        int typ[kSortPer];
         int rank[kSortPer];
 #pragma unroll
         for (int u = 0; u < kSortPer; ++u) {
             const int k = tid + u * kSortThreads;
             key[u] = ~0ull;
             rank[u] = 0;
+            typ[u] = 0;
             if (k < n) {
                 const int a = src[k];
                 p[u] = wpos[a];
+                if (pk.q) {  // loaded now, written after the sort
+                    p[u].w = pk.q[a];
+                    typ[u] = pk.type[a];
+                }
                 key[u] = zkey(p[u].z, a);
                 skey[k] = key[u];
             }
@@ -331,8 +338,8 @@ __global__ void __launch_bounds__(kSortThreads) k_colsort(
                 const int slot = base + rank[u];
                 perm[slot] = a;
                 inv[a] = slot;
-                xyzq[slot] = make_float4(p[u].x, p[u].y, p[u].z, pk.q ? pk.q[a] : 0.0f);
-                if (pk.q) tslot[slot] = packed_type(pk, a);
+                xyzq[slot] = make_float4(p[u].x, p[u].y, p[u].z, pk.q ? p[u].w : 0.0f);
+                if (pk.q) tslot[slot] = checked_type(pk, typ[u]);
                 sp[rank[u]] = p[u];
             }
         }
@@ -612,7 +619,9 @@ __global__ void __launch_bounds__(kGListWarps * 32, ACENB_GLIST_MIN_BLOCKS) k_gl
     pdl_entry();
     if (g >= A.counts[4]) return;  // the whole warp
     const unsigned lt = (1u << lane) - 1u;
-    const int2 gr = A.grp[g];
+    // one-cluster groups are numbered like their clusters (the scans of
+    // cluster and group counts per column coincide): no load
+    const int2 gr = A.group == 1 ? make_int2(g, 1) : A.grp[g];
     const int c0 = gr.x, n = gr.y, K = A.K;
     __shared__ float4 s_lo_all[kGListWarps][kMaxGroup], s_hi_all[kGListWarps][kMaxGroup];
     __shared__ int s_col_all[kGListWarps][32];

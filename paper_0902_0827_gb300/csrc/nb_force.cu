@@ -883,9 +883,17 @@ __global__ void __launch_bounds__(kTileWarps * 32, ACENB_TILE_MIN_BLOCKS) k_forc
         int u_next = 0;
         if (lane == 0) u_next = atomicAdd(A.work, 1);
         const Unit U = unit_of(A, u, parts);
+        // what needs only the unit's group and segment is loaded before the
+        // segment's length is known: one-cluster groups are numbered like
+        // their clusters, and a segment holds at least its first batch
+        const int I = U.g;
+        const int sys_id = __ldg(A.clus_sys + I);
+        const long long s0 = (long long)I * kCluster;
+        const TileI ia = load_tile_i(A, s0 + ih, T, DEBUG);
+        const TileI ib = load_tile_i(A, s0 + ih + 4, T, DEBUG);
+        const uint2 *row = A.glist + U.base;
+        const uint2 first = lane < A.cap / kListSegs ? __ldg(row + lane) : make_uint2(0u, 0u);
         if (U.e_begin < U.e_end) {
-            const int I = __ldg(A.grp + U.g).x;
-            const int sys_id = __ldg(A.clus_sys + I);
             if (sys_id != cur_sys) {
                 if (!DEBUG && cur_sys >= 0) {
                     long long v[kTaskVals];
@@ -899,15 +907,11 @@ __global__ void __launch_bounds__(kTileWarps * 32, ACENB_TILE_MIN_BLOCKS) k_forc
                 Ly = A.sys[sys_id].L[1];
                 Lz = A.sys[sys_id].L[2];
             }
-            const long long s0 = (long long)I * kCluster;
-            const TileI ia = load_tile_i(A, s0 + ih, T, DEBUG);
-            const TileI ib = load_tile_i(A, s0 + ih + 4, T, DEBUG);
             Acc acA = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, acB = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-            const uint2 *row = A.glist + U.base;
             bool unit_img = false;
             for (int e0 = U.e_begin; e0 < U.e_end; e0 += kBatch1) {
                 const int ne = min(kBatch1, U.e_end - e0);
-                const uint2 my = lane < ne ? __ldg(row + e0 + lane) : make_uint2(0u, 0u);
+                const uint2 my = lane < ne ? (e0 == 0 ? first : __ldg(row + e0 + lane)) : make_uint2(0u, 0u);
                 if (lane < ne) {
                     const long long jbase = (long long)(my.x & kJMask) * kCluster;
 #pragma unroll
@@ -1369,7 +1373,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_adjoint1(ForceArgs A, int pa
         if (lane == 0) u_next = atomicAdd(A.work, 1);
         const Unit U = unit_of(A, u, parts);
         if (U.e_begin < U.e_end) {
-            const int I = __ldg(A.grp + U.g).x;
+            const int I = U.g;  // one-cluster groups are numbered like their clusters
             const int sys_id = __ldg(A.clus_sys + I);
             if (sys_id != cur_sys) {
                 cur_sys = sys_id;
