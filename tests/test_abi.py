@@ -79,6 +79,10 @@ def test_host_validation_without_gpu():
     p, keep = _params(s)
     p.flags = 1
     assert _create(p)[0] == 1
+    # an empty system (N >= 1 is required)
+    p, keep = _params(s)
+    p.n_atoms = 0
+    assert _create(p)[0] == 1
     # more than 16 topology partners (excluded + scaled 1-4) of one atom
     s20 = S._water_system(S.rng_for(31), 7, "w21")
     p, keep = _params(s20)
