@@ -42,7 +42,7 @@ UNIT = "pairs/s"
 # kernels of this library per step: binning and lists (bin + scan + staging,
 # column sort, pair lists); forward (pack, force, unpack + energy/virial);
 # adjoint (pack, dL/dF gather, adjoint kernel, unpack, type-pair gradients);
-# nb_step (rebuild + forces in one call: the column sort packs, no pack kernel)
+# nb_step (rebuild + forces in one call: binning and column sort pack, no pack kernel)
 BUILD_LAUNCHES = 3
 FORCE_LAUNCHES = 3
 STEP_LAUNCHES = BUILD_LAUNCHES + FORCE_LAUNCHES - 1
@@ -845,22 +845,39 @@ def main():
         oE = d_out[out_e:out_e + 16].view(torch.float64).view(1, 2)
         oW = d_out[out_e + 16:].view(torch.float64).view(1, 6)
 
-        def e2e_step():
+        hpos = h_in[:N * 12].view(torch.float32).view(N, 3)
+        hq = h_in[N * 12:N * 16].view(torch.float32)
+        ht = h_in[N * 16:].view(torch.int32)
+        hF = h_out[:out_f].view(torch.float32).view(N, 3)
+        hE = h_out[out_e:out_e + 16].view(torch.float64).view(1, 2)
+        hW = h_out[out_e + 16:].view(torch.float64).view(1, 6)
+
+        def e2e_copy_step():  # copy engine: one copy in, one copy out
             d_in.copy_(h_in, non_blocking=True)
             ctx.step(dpos, dq, dt, F=oF, energy=oE, virial=oW)
             h_out.copy_(d_out, non_blocking=True)
 
-        for _ in range(3):
-            e2e_step()
-        torch.cuda.synchronize()
-        # the same CUDA-graph replay as the device-side step (copies included)
-        ge = graph_of(e2e_step, dev)
-        tt = [time_steps(ge.replay, 1, flush) for _ in range(args.steps)]
-        e2e_ms = max_over_ranks(sum(tt) / len(tt), world)
+        def e2e_step():  # the kernels read the inputs and write the results in the pinned buffers
+            ctx.step(hpos, hq, ht, F=hF, energy=hE, virial=hW)
+
         bi, bo = nb_in, nb_out
-        line["e2e"] = {"value": world * npairs / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": bi,
-                       "d2h_bytes_per_step": bo, "ms_per_step": e2e_ms}
-        line["gpu_launches"] += (STEP_LAUNCHES) * args.steps
+        for name, fn in (("e2e_copy_engine", e2e_copy_step), ("e2e", e2e_step)):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            # the same CUDA-graph replay as the device-side step (transfers included)
+            ge = graph_of(fn, dev)
+            tt = [time_steps(ge.replay, 1, flush) for _ in range(args.steps)]
+            e_ms = max_over_ranks(sum(tt) / len(tt), world)
+            line[name] = {"value": world * npairs / (e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": bi,
+                          "d2h_bytes_per_step": bo, "ms_per_step": e_ms}
+            line["gpu_launches"] += (STEP_LAUNCHES) * args.steps
+        line["e2e"]["transfer"] = ("inputs read and results written by the kernels in page-locked host memory "
+                                   "across the host link (no copy-engine transfer); e2e_copy_engine: one "
+                                   "host-to-device and one device-to-host copy per step")
+        torch.cuda.synchronize()
+        line["e2e"]["results_equal_device_step"] = bool(
+            torch.equal(hF, F.cpu()) and torch.equal(hE, E.cpu()) and torch.equal(hW, W.cpu()))
         ctx.status()
     if rank == 0 and not args.no_cpu and world == 1:
         times, cp, cores = cpu_oracle_run(s)

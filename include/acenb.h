@@ -160,11 +160,17 @@ nb_status nb_forces_batch(nb_ctx *batch, const float *d_pos, const float *d_q, c
 /* nb_step - one evaluation from positions: nb_build_cells followed by
  * nb_forces on the same arrays (section "Molecular dynamics on the GPU":
  * the cell list is rebuilt and the forces evaluated every step), in fewer
- * kernels: the column sort also gathers the charges and types into sorted
- * order, and with PME the reciprocal chain starts before the pair lists.
+ * kernels: the binning kernel reads the charges and types beside the
+ * positions and the column sort carries them into sorted order, and with
+ * PME the reciprocal chain starts before the pair lists.
  * Arguments, outputs and errors as for nb_forces; the context is built
  * afterwards, so nb_forces and nb_backward may follow on the same
- * positions.  Results are bit-identical to nb_build_cells + nb_forces. */
+ * positions.  Results are bit-identical to nb_build_cells + nb_forces.
+ * Each array may also be page-locked host memory that the device addresses
+ * at the same address (cudaHostAlloc under unified addressing): the kernels
+ * then read the inputs and write the results across the host link, with
+ * no separate copy, and the results are in host memory once the stream has
+ * completed.  Other host memory must not be passed. */
 nb_status nb_step(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type, float *d_F,
                   double *d_energy, double *d_virial);
 

@@ -33,7 +33,7 @@ cudaError_t dalloc(T **p, size_t count)
 void free_all(nb_ctx *c)
 {
     auto &d = c->d;
-    void *ptrs[] = {d.sys, d.atom_sys, d.atom_col, d.wpos, d.part_orig, d.col_sys, d.col_count,
+    void *ptrs[] = {d.sys, d.atom_sys, d.atom_col, d.wpos, d.atom_t, d.part_orig, d.col_sys, d.col_count,
                     d.col_slot, d.stage, d.stage_fix, d.xyzq, d.tslot, d.perm, d.inv, d.bb,
                     d.clus_sys, d.sys_acc, d.facc, d.gacc, d.col_grp, d.grp, d.clus_grp, d.glist, d.glist_n, d.gmask,
                     d.zbin, d.tab_grad, d.counts, d.status, d.lj_tab,
@@ -72,6 +72,7 @@ nb_status allocate(nb_ctx *c)
     ALLOC(d.atom_sys, N);
     ALLOC(d.atom_col, N);
     ALLOC(d.wpos, N);
+    ALLOC(d.atom_t, N);
     ALLOC(d.part_orig, N * c->K);
     ALLOC(d.col_sys, C);
     ALLOC(d.col_count, 2 * C + 1);
@@ -304,7 +305,7 @@ nb_status nb_step(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32
                   double *d_energy, double *d_virial)
 {
     if (!ctx || !d_pos || !d_q || !d_type || !d_F) return NB_ERR_INVALID_ARG;
-    // the column sort packs charges and types; PME (which needs only the
+    // the binning kernel and the column sort pack charges and types; PME (which needs only the
     // sorted atoms) is forked before the lists, beside the list and force kernels
     cudaError_t e = launch_build_cells(ctx, d_pos, d_q, d_type);
     const bool pme = ctx->pme != nullptr;

@@ -114,6 +114,19 @@ __device__ void scan_columns(int n_cols, int n_sys, int *__restrict__ col_count,
     }
 }
 
+// The step's charges and types when they are in host memory, read by the
+// binning kernel beside the positions (coalesced, in caller order, across
+// the host link): the charge goes to the wrapped position's w, the
+// range-checked type to atom_t, and the column sort carries both into sorted
+// order.  q = null: positions only (w = 0); device-resident charges and
+// types are gathered by the column sort instead (faster there).
+struct AtomPack {
+    const float *q;
+    const int *type;
+    int T;
+    int *atom_t;  // [N] checked types in caller order
+};
+
 // A1 + A2 + A3a: one atom per thread: wrap, column index, column histogram
 // (warp-aggregated atomics, whose returned counts are the atoms' places in
 // their column): each atom goes to its place in its column's fixed-capacity
@@ -125,7 +138,7 @@ __global__ void k_bin(int n, const float *__restrict__ pos, SysDesc *__restrict_
                       const int *__restrict__ atom_sys, float4 *__restrict__ wpos, int *__restrict__ atom_col,
                       int *__restrict__ col_count, int n_cols, int n_sys, int *__restrict__ col_slot,
                       int *__restrict__ stage_fix, int col_cap, int *__restrict__ counts, int *__restrict__ status,
-                      int group, int *__restrict__ col_grp)
+                      int group, int *__restrict__ col_grp, AtomPack ap)
 {
     pdl_entry();
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
@@ -148,7 +161,17 @@ __global__ void k_bin(int n, const float *__restrict__ pos, SysDesc *__restrict_
         }
         col = S.col_begin + column_of(y, S.inv_w[1], S.ny) * S.nx + column_of(x, S.inv_w[0], S.nx);
         atom_col[a] = col;
-        wpos[a] = make_float4(x, y, z, 0.0f);
+        float qa = 0.0f;
+        if (ap.q) {  // charge and checked type, read beside the position
+            qa = ap.q[a];
+            int t = ap.type[a];
+            if (t < 0 || t >= ap.T) {
+                atomicOr(status, ST_BADTYPE);
+                t = 0;
+            }
+            ap.atom_t[a] = t;
+        }
+        wpos[a] = make_float4(x, y, z, qa);
     }
     const int place = warp_aggregated_add(col_count, col);
     if (col >= 0 && place < col_cap) stage_fix[(long long)col * col_cap + place] = a;
@@ -219,14 +242,16 @@ constexpr int kRankSortMax = 256;  // columns up to this many atoms are rank-sor
 // zeroed (k_pack's work, without its stale-position check: the positions
 // were just binned).  q == nullptr: the column sort leaves that to k_pack.
 struct ColPack {
-    const float *q;
-    const int *type;
+    const float *q;      // charges and types in caller order, gathered here (device inputs),
+    const int *type;     // or null
     int T;
+    const int *atom_t;   // or: checked types from the binning kernel, charges in wpos.w (host inputs)
     long long *facc;     // [3 slots] fixed-point forces
     long long *sys_acc;  // [n_acc] per-system energy and virial sums
     int n_acc;
     int *work;           // the force kernels' work-unit counter
     int *status;
+    __device__ bool packs() const { return q != nullptr || atom_t != nullptr; }
 };
 
 __device__ __forceinline__ int checked_type(const ColPack &pk, int t)
@@ -238,7 +263,18 @@ __device__ __forceinline__ int checked_type(const ColPack &pk, int t)
     return t;
 }
 
-__device__ __forceinline__ int packed_type(const ColPack &pk, int a) { return checked_type(pk, pk.type[a]); }
+// Charge (into p.w) and type of atom a for the sorted arrays, as loaded: a
+// type from the caller's array is range-checked by sorted_type when it is
+// written (so that no load is waited for before the sort).
+__device__ __forceinline__ int pack_atom(const ColPack &pk, int a, float4 &p)
+{
+    if (pk.atom_t) return pk.atom_t[a];  // p.w holds the charge already
+    if (!pk.q) return 0;
+    p.w = pk.q[a];
+    return pk.type[a];
+}
+
+__device__ __forceinline__ int sorted_type(const ColPack &pk, int t) { return pk.atom_t ? t : checked_type(pk, t); }
 
 // A3b: one block per column: sort by (z, atom index), write the sorted slot
 // arrays and padding, the cluster bounding boxes and the column's z-bin
@@ -294,18 +330,19 @@ __global__ void __launch_bounds__(kSortThreads) k_colsort(
         bitonic_sort(skey, P);
         for (int k = tid; k < n; k += blockDim.x) {
             const int a = (int)(unsigned)(skey[k] & 0xffffffffull);
-            const float4 pa = wpos[a];
+            float4 pa = wpos[a];
             const int slot = base + k;
             perm[slot] = a;
             inv[a] = slot;
-            xyzq[slot] = make_float4(pa.x, pa.y, pa.z, pk.q ? pk.q[a] : 0.0f);
-            if (pk.q) tslot[slot] = packed_type(pk, a);
+            const int t = pack_atom(pk, a, pa);
+            xyzq[slot] = pa;  // w: the charge (0 without packing)
+            if (pk.packs()) tslot[slot] = sorted_type(pk, t);
             sp[k] = pa;
         }
     } else if (small) {
         const int nper = (n + kSortThreads - 1) / kSortThreads;
         unsigned long long key[kSortPer];
-        float4 p[kSortPer];  // w: the charge when packing
+        float4 p[kSortPer];  // w: the charge (0 without packing)
         int typ[kSortPer];
         int rank[kSortPer];
 #pragma unroll
@@ -317,10 +354,7 @@ __global__ void __launch_bounds__(kSortThreads) k_colsort(
             if (k < n) {
                 const int a = src[k];
                 p[u] = wpos[a];
-                if (pk.q) {  // loaded now, written after the sort
-                    p[u].w = pk.q[a];
-                    typ[u] = pk.type[a];
-                }
+                typ[u] = pack_atom(pk, a, p[u]);  // loaded now, written after the sort
                 key[u] = zkey(p[u].z, a);
                 skey[k] = key[u];
             }
@@ -338,15 +372,15 @@ __global__ void __launch_bounds__(kSortThreads) k_colsort(
                 const int slot = base + rank[u];
                 perm[slot] = a;
                 inv[a] = slot;
-                xyzq[slot] = make_float4(p[u].x, p[u].y, p[u].z, pk.q ? p[u].w : 0.0f);
-                if (pk.q) tslot[slot] = checked_type(pk, typ[u]);
+                xyzq[slot] = p[u];
+                if (pk.packs()) tslot[slot] = sorted_type(pk, typ[u]);
                 sp[rank[u]] = p[u];
             }
         }
     } else {
         for (int k = tid; k < n; k += blockDim.x) {
             const int a = src[k];
-            const float4 pa = wpos[a];
+            float4 pa = wpos[a];
             const unsigned long long ka = zkey(pa.z, a);
             int rank = 0;
             for (int m = 0; m < n; ++m) {
@@ -356,8 +390,9 @@ __global__ void __launch_bounds__(kSortThreads) k_colsort(
             const int slot = base + rank;
             perm[slot] = a;
             inv[a] = slot;
-            xyzq[slot] = make_float4(pa.x, pa.y, pa.z, pk.q ? pk.q[a] : 0.0f);
-            if (pk.q) tslot[slot] = packed_type(pk, a);
+            const int t = pack_atom(pk, a, pa);
+            xyzq[slot] = pa;
+            if (pk.packs()) tslot[slot] = sorted_type(pk, t);
         }
     }
     for (int k = n + tid; k < npad; k += blockDim.x) {
@@ -365,7 +400,7 @@ __global__ void __launch_bounds__(kSortThreads) k_colsort(
         tslot[base + k] = 0;
         xyzq[base + k] = make_float4(kPadCoord, kPadCoord, kPadCoord, 0.0f);
     }
-    if (pk.q) {
+    if (pk.packs()) {
         for (int k = tid; k < 3 * npad; k += blockDim.x) pk.facc[3ll * base + k] = 0;
         if (c == 0) {
             for (int k = tid; k < pk.n_acc; k += blockDim.x) pk.sys_acc[k] = 0;
@@ -921,23 +956,47 @@ __global__ void __launch_bounds__(kGListWarps * 32, ACENB_GLIST_MIN_BLOCKS) k_gl
     }
 }
 
+// Whether the charges are in page-locked host memory (then the binning
+// kernel reads charges and types beside the positions, coalesced, instead of
+// the column sort gathering them across the host link).  The pointer is
+// queried outside stream capture; during a capture the last answer stands
+// (it only selects between two ways of reading that give the same result).
+static bool inputs_in_host_memory(nb_ctx *ctx, const void *p)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(ctx->stream, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return ctx->host_inputs;
+    }
+    if (cs != cudaStreamCaptureStatusNone) return ctx->host_inputs;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return ctx->host_inputs = false;
+    }
+    return ctx->host_inputs = at.type == cudaMemoryTypeHost;
+}
+
 cudaError_t launch_build_cells(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type)
 {
     auto &d = ctx->d;
     cudaStream_t st = ctx->stream;
     const int N = (int)ctx->n_atoms;
+    const bool host_in = d_q && inputs_in_host_memory(ctx, d_q);
     // the column counts are zero here: zeroed at create and by the scan of
     // the previous build's binning kernel, which leaves a copy for the sort
     const int tb = 256;
     cudaError_t e = launch_pdl(k_bin, dim3((N + tb - 1) / tb), dim3(tb), 0, st, N, d_pos, d.sys, d.atom_sys, d.wpos, d.atom_col,
                    d.col_count, ctx->n_cols, ctx->n_sys, d.col_slot, d.stage_fix, ctx->col_cap, d.counts, d.status,
-                   ctx->group, d.col_grp);
+                   ctx->group, d.col_grp,
+                   host_in ? AtomPack{d_q, d_type, ctx->pp.n_types, d.atom_t} : AtomPack{nullptr, nullptr, 0, nullptr});
     if (e == cudaSuccess)
         e = launch_pdl(k_colsort, dim3(ctx->n_cols), dim3(kSortThreads), 0, st, (const int *)d.col_count + ctx->n_cols + 1, d.col_slot, d.col_sys,
                        d.sys, (const int *)d.stage_fix, ctx->col_cap, d.stage, (const int *)d.atom_col, d.wpos, d.xyzq, d.tslot, d.perm, d.inv, d.bb, d.clus_sys, d.zbin, ctx->group,
                        d.col_grp, d.grp, d.clus_grp,
-                       ColPack{d_q, d_type, ctx->pp.n_types, d.facc, d.sys_acc, kTaskVals * ctx->n_sys, d.counts + 3,
-                               d.status});
+                       ColPack{host_in ? nullptr : d_q, host_in ? nullptr : d_type, ctx->pp.n_types,
+                               host_in ? (const int *)d.atom_t : nullptr, d.facc, d.sys_acc, kTaskVals * ctx->n_sys,
+                               d.counts + 3, d.status});
     if (e != cudaSuccess) return e;
     ctx->built_group = ctx->group;
     return cudaGetLastError();

@@ -1503,24 +1503,25 @@ __device__ __forceinline__ void flush_virial_warp(long long *w, int sys, long lo
     for (int k = 0; k < 6; ++k) w[k] = 0;
 }
 
-// Fixed-point forces (sorted order) to FP32 in the caller's order.  With
+// Fixed-point forces (sorted order) to FP32 in the caller's order, one
+// thread per atom in caller order (gathers from the sorted sums, and
+// coalesced writes of F, which may be page-locked host memory).  With
 // VIRIAL, also the atom part of the virial: for central pair forces
 // W_ab = sum_pairs d_a f_b (d = x_j' - x_i, f the force on j) equals
 // sum_atoms x_a F_b over the wrapped coordinates x and total forces F, plus
 // the periodic-image terms added by the force kernel.  Each atom's terms are
 // rounded to the 2^20 fixed-point grid in FP64 and summed as integers per
-// thread (grid-stride loop, slots in system order) and per warp.
+// thread (grid-stride loop, atoms in system order) and per warp.
 template <bool VIRIAL>
-__global__ void __launch_bounds__(256) k_unpack_forces(int slot_cap, int *__restrict__ counts,
-                                                       const int *__restrict__ perm, const long long *__restrict__ facc,
+__global__ void __launch_bounds__(256) k_unpack_forces(int n_atoms, int *__restrict__ counts,
+                                                       const int *__restrict__ inv, const long long *__restrict__ facc,
                                                        float *__restrict__ F, const float4 *__restrict__ xyzq,
-                                                       const int *__restrict__ clus_sys, long long *__restrict__ sys_acc,
+                                                       const int *__restrict__ atom_sys, long long *__restrict__ sys_acc,
                                                        int n_sys, double *__restrict__ energy, double *__restrict__ virial,
                                                        const long long *__restrict__ pme_f,
                                                        const long long *__restrict__ pme_s, double pme_self)
 {
     pdl_entry();
-    const int nslots = min(slot_cap, counts[0]);
     long long w[6] = {0, 0, 0, 0, 0, 0};
     int wsys = -1;
     __shared__ unsigned long long blk_w[6];
@@ -1528,17 +1529,17 @@ __global__ void __launch_bounds__(256) k_unpack_forces(int slot_cap, int *__rest
     if (VIRIAL) {
         if (threadIdx.x < 6) blk_w[threadIdx.x] = 0ull;
         if (threadIdx.x == 0) {
-            const int s0 = blockIdx.x * blockDim.x;
-            blk_sys = s0 < nslots ? clus_sys[s0 / kCluster] : -1;
+            const int a0 = blockIdx.x * blockDim.x;
+            blk_sys = a0 < n_atoms ? atom_sys[a0] : -1;
         }
         __syncthreads();
     }
-    for (int s0 = blockIdx.x * blockDim.x; s0 < nslots; s0 += gridDim.x * blockDim.x) {
-        const int s = s0 + threadIdx.x;
-        const int a = s < nslots ? perm[s] : -1;
+    for (int a0 = blockIdx.x * blockDim.x; a0 < n_atoms; a0 += gridDim.x * blockDim.x) {
+        const int a = a0 + threadIdx.x;
+        const int s = a < n_atoms ? inv[a] : -1;
         int sys = -1;
         long long c[6];
-        if (a >= 0) {
+        if (s >= 0) {
             const long long v0 = facc[3ll * s], v1 = facc[3ll * s + 1], v2 = facc[3ll * s + 2];
             const float sc = 2.3283064365386963e-10f;  // 2^-32
             // PME forces (same slot order) join the sum before the one
@@ -1558,11 +1559,11 @@ __global__ void __launch_bounds__(256) k_unpack_forces(int slot_cap, int *__rest
                 c[3] = __double2ll_rn(x.x * fy);
                 c[4] = __double2ll_rn(x.x * fz);
                 c[5] = __double2ll_rn(x.y * fz);
-                sys = clus_sys[s / kCluster];
+                sys = atom_sys[a];
             }
         }
         if (VIRIAL) {
-            // slots come in system order: flush a lane's sums before it moves on
+            // atoms come in system order: flush a lane's sums before it moves on
             if (__any_sync(kFull, sys >= 0 && wsys >= 0 && sys != wsys)) {
                 flush_virial_warp(w, wsys, sys_acc, blk_sys, blk_w);
                 wsys = -1;
@@ -1780,18 +1781,18 @@ cudaError_t launch_forces_packed(nb_ctx *ctx, float *d_F, double *d_energy, doub
     }
     {
         const int tb = 256;
-        const int S = (int)ctx->slot_cap;
+        const int S = (int)ctx->n_atoms;
         const int blocks = std::max(1, std::min((S + tb - 1) / tb, 4 * ctx->num_sms));
         double *en = debug_pairs ? nullptr : d_energy;
         double *vi = debug_pairs ? nullptr : d_virial;
         const long long *pf = pme ? pme_forces_acc(ctx) : nullptr, *ps = pme ? pme_sums_acc(ctx) : nullptr;
         const double pself = pme ? pme_self_coef(ctx) : 0.0;
         if (virial)
-            launch_pdl(k_unpack_forces<true>, dim3(blocks), dim3(tb), 0, ctx->stream, S, d.counts, d.perm, d.facc, d_F,
-                       d.xyzq, d.clus_sys, d.sys_acc, ctx->n_sys, en, vi, pf, ps, pself);
+            launch_pdl(k_unpack_forces<true>, dim3(blocks), dim3(tb), 0, ctx->stream, S, d.counts, d.inv, d.facc, d_F,
+                       d.xyzq, d.atom_sys, d.sys_acc, ctx->n_sys, en, vi, pf, ps, pself);
         else
-            launch_pdl(k_unpack_forces<false>, dim3(blocks), dim3(tb), 0, ctx->stream, S, d.counts, d.perm, d.facc,
-                       d_F, d.xyzq, d.clus_sys, d.sys_acc, ctx->n_sys, en, vi, pf, ps, pself);
+            launch_pdl(k_unpack_forces<false>, dim3(blocks), dim3(tb), 0, ctx->stream, S, d.counts, d.inv, d.facc,
+                       d_F, d.xyzq, d.atom_sys, d.sys_acc, ctx->n_sys, en, vi, pf, ps, pself);
     }
     return cudaGetLastError();
 }

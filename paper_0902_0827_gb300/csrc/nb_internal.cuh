@@ -108,7 +108,8 @@ struct DevBuffers {
     SysDesc *sys = nullptr;          // [n_sys]
     int *atom_sys = nullptr;         // [N]
     int *atom_col = nullptr;         // [N] global column of each atom
-    float4 *wpos = nullptr;          // [N] wrapped coordinates
+    float4 *wpos = nullptr;          // [N] wrapped coordinates (w: the charge when the step packs them)
+    int *atom_t = nullptr;           // [N] range-checked types in caller order (nb_step and MD steps)
     int *part_orig = nullptr;        // [N*K] partner (orig << 1) | is14, -1 pad (static)
     int *col_sys = nullptr;          // [C] system of each column (static)
     int *col_count = nullptr;        // [2C+1] column histogram (zero between builds); [C] = completion ticket
@@ -172,6 +173,7 @@ struct nb_ctx {
     int device = 0;
     int num_sms = 0;
     bool built = false;
+    bool host_inputs = false;      // the step's charges and types were in host memory at the last query
     acenb::PairParams pp{};
     nb_tuning tune{};
     std::vector<acenb::SysDesc> sys_h;

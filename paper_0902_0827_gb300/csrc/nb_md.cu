@@ -676,7 +676,7 @@ static cudaError_t launch_bonded(nb_ctx *ctx, const float *d_pos)
 static cudaError_t md_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type, bool sums)
 {
     MdState &M = *ctx->md;
-    cudaError_t e = launch_build_cells(ctx, d_pos, d_q, d_type);  // the column sort packs q, types
+    cudaError_t e = launch_build_cells(ctx, d_pos, d_q, d_type);  // q and types packed on the way
     const bool pme = ctx->pme != nullptr;
     if (e == cudaSuccess && pme) e = launch_pme_fork(ctx, d_pos, d_q, sums);
     if (e == cudaSuccess) e = launch_build_lists(ctx);

@@ -155,12 +155,16 @@ def _ptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p) if a.size else None
 
 
-def _tptr(t):
-    """Device pointer of a contiguous CUDA tensor (None passes NULL)."""
+def _tptr(t, host_ok=False):
+    """Device pointer of a contiguous CUDA tensor (None passes NULL).  With
+    host_ok, a contiguous page-locked CPU tensor is accepted too: under
+    unified addressing its address is also its device address, and the
+    kernels read and write it across the host link."""
     if t is None:
         return None
-    if not t.is_cuda or not t.is_contiguous():
-        raise ValueError("expected a contiguous CUDA tensor")
+    ok = t.is_cuda or (host_ok and t.device.type == "cpu" and t.is_pinned())
+    if not ok or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor" + (" or page-locked CPU tensor" if host_ok else ""))
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -265,17 +269,26 @@ class Nonbonded:
 
     def step(self, pos, q, typ, F=None, energy=True, virial=True):
         """Rebuild from pos and evaluate (nb_step): the results of
-        build(pos) followed by forces(pos, q, typ), in fewer kernels."""
+        build(pos) followed by forces(pos, q, typ), in fewer kernels.  The
+        arrays may be CUDA tensors or page-locked CPU tensors (read and
+        written by the kernels in place; results are there once the stream
+        has completed); new outputs go where pos is."""
         import torch
         self._sync_stream()
         dev = pos.device
+        pin = dev.type == "cpu"
+
+        def new(shape, dtype):
+            return torch.empty(shape, dtype=dtype, device=dev, pin_memory=pin)
+
         if F is None:
-            F = torch.empty((self.n_atoms, 3), dtype=torch.float32, device=dev)
-        E = torch.empty((self.n_sys, 2), dtype=torch.float64, device=dev) if energy is True else energy
-        W = torch.empty((self.n_sys, 6), dtype=torch.float64, device=dev) if virial is True else virial
+            F = new((self.n_atoms, 3), torch.float32)
+        E = new((self.n_sys, 2), torch.float64) if energy is True else energy
+        W = new((self.n_sys, 6), torch.float64) if virial is True else virial
         E = E if E is not False else None
         W = W if W is not False else None
-        _check(lib().nb_step(self.h, _tptr(pos), _tptr(q), _tptr(typ), _tptr(F), _tptr(E), _tptr(W)), "nb_step")
+        _check(lib().nb_step(self.h, _tptr(pos, True), _tptr(q, True), _tptr(typ, True), _tptr(F, True),
+                             _tptr(E, True), _tptr(W, True)), "nb_step")
         return F, E, W
 
     def set_tables(self, n_intervals: int = 4096):

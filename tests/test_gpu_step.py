@@ -1,7 +1,8 @@
 """nb_step (rebuild + forces in one call, the charges and types packed by the
 column sort) against nb_build_cells + nb_forces on the same inputs: forces,
 energies and virial bit for bit, alone, in a batch, with smooth PME and with
-tables; the context is built afterwards; a bad type index is reported."""
+tables; the context is built afterwards; a bad type index is reported; the
+arrays may be page-locked host memory (same bits)."""
 
 import numpy as np
 import pytest
@@ -124,3 +125,46 @@ def test_step_replays_from_a_cuda_graph(pme):
     torch.cuda.synchronize()
     ctx.status()
     assert torch.equal(F, F0) and torch.equal(E, E0) and torch.equal(W, W0)
+
+
+@pytest.mark.parametrize("pme", [False, True])
+def test_step_on_page_locked_host_arrays(pme):
+    # inputs and outputs in page-locked host memory, read and written by the
+    # kernels in place: the same bits as with device arrays, plain and from
+    # a CUDA graph
+    s = S.solvated_chain()
+    ctx = nb.Nonbonded(s)
+    if pme:
+        ctx.set_pme((64, 64, 64), 4)
+    pos, q, t = nb.concat_inputs([s])
+    F0, E0, W0 = ctx.step(pos, q, t)
+    torch.cuda.synchronize()
+    hpos, hq, ht = (x.cpu().pin_memory() for x in (pos, q, t))
+    F, E, W = ctx.step(hpos, hq, ht)
+    torch.cuda.synchronize()
+    ctx.status()
+    assert F.device.type == "cpu" and F.is_pinned()
+    assert torch.equal(F, F0.cpu()) and torch.equal(E, E0.cpu()) and torch.equal(W, W0.cpu())
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        ctx.step(hpos, hq, ht, F=F, energy=E, virial=W)
+        with torch.cuda.graph(g, stream=side):
+            ctx.step(hpos, hq, ht, F=F, energy=E, virial=W)
+    torch.cuda.current_stream().wait_stream(side)
+    F.zero_()
+    E.zero_()
+    W.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    ctx.status()
+    assert torch.equal(F, F0.cpu()) and torch.equal(E, E0.cpu()) and torch.equal(W, W0.cpu())
+
+
+def test_step_rejects_pageable_host_arrays():
+    s = S.water_box()
+    ctx = nb.Nonbonded(s)
+    pos, q, t = nb.concat_inputs([s])
+    with pytest.raises(ValueError):
+        ctx.step(pos.cpu(), q, t)
