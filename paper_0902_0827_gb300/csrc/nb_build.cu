@@ -242,17 +242,19 @@ constexpr int kRankSortMax = 256;  // columns up to this many atoms are rank-sor
 // zeroed (k_pack's work, without its stale-position check: the positions
 // were just binned).  q == nullptr: the column sort leaves that to k_pack.
 struct ColPack {
-    const float *q;      // charges and types in caller order, gathered here (device inputs),
-    const int *type;     // or null
+    const float *q;      // kPackGather: charges and types in caller order, gathered here
+    const int *type;
     int T;
-    const int *atom_t;   // or: checked types from the binning kernel, charges in wpos.w (host inputs)
+    const int *atom_t;   // kPackAtomT: checked types from the binning kernel, charges in wpos.w
     long long *facc;     // [3 slots] fixed-point forces
     long long *sys_acc;  // [n_acc] per-system energy and virial sums
     int n_acc;
     int *work;           // the force kernels' work-unit counter
     int *status;
-    __device__ bool packs() const { return q != nullptr || atom_t != nullptr; }
 };
+
+// What the column sort packs (a template parameter: no per-atom branches).
+enum PackMode { kPackNone = 0, kPackGather = 1, kPackAtomT = 2 };
 
 __device__ __forceinline__ int checked_type(const ColPack &pk, int t)
 {
@@ -266,15 +268,20 @@ __device__ __forceinline__ int checked_type(const ColPack &pk, int t)
 // Charge (into p.w) and type of atom a for the sorted arrays, as loaded: a
 // type from the caller's array is range-checked by sorted_type when it is
 // written (so that no load is waited for before the sort).
+template <int PACK>
 __device__ __forceinline__ int pack_atom(const ColPack &pk, int a, float4 &p)
 {
-    if (pk.atom_t) return pk.atom_t[a];  // p.w holds the charge already
-    if (!pk.q) return 0;
+    if (PACK == kPackAtomT) return pk.atom_t[a];  // p.w holds the charge already
+    if (PACK == kPackNone) return 0;
     p.w = pk.q[a];
     return pk.type[a];
 }
 
-__device__ __forceinline__ int sorted_type(const ColPack &pk, int t) { return pk.atom_t ? t : checked_type(pk, t); }
+template <int PACK>
+__device__ __forceinline__ int sorted_type(const ColPack &pk, int t)
+{
+    return PACK == kPackAtomT ? t : checked_type(pk, t);
+}
 
 // A3b: one block per column: sort by (z, atom index), write the sorted slot
 // arrays and padding, the cluster bounding boxes and the column's z-bin
@@ -283,8 +290,12 @@ __device__ __forceinline__ int sorted_type(const ColPack &pk, int t) { return pk
 // kRankSortMax atoms by rank (every thread holds up to kSortPer keys and
 // counts, per broadcast key, how many are smaller: n^2 compares), longer
 // ones by a bitonic network (n log^2 n).  The keys are unique, so both give
-// the same order.
-__global__ void __launch_bounds__(kSortThreads) k_colsort(
+// the same order.  PACK selects how the step's charges and types are packed
+// (a template parameter: no per-atom branches); the register budget of 6
+// blocks per SM (80 registers) measured faster than the compiler's choice
+// (94 for the gathering instance) in both the step and the MD step.
+template <int PACK>
+__global__ void __launch_bounds__(kSortThreads, 6) k_colsort(
     const int *__restrict__ col_count, const int *__restrict__ col_slot, const int *__restrict__ col_sys,
     const SysDesc *__restrict__ sys, const int *__restrict__ stage_fix, int col_cap, int *__restrict__ stage,
     const int *__restrict__ atom_col, const float4 *__restrict__ wpos,
@@ -334,9 +345,9 @@ __global__ void __launch_bounds__(kSortThreads) k_colsort(
             const int slot = base + k;
             perm[slot] = a;
             inv[a] = slot;
-            const int t = pack_atom(pk, a, pa);
+            const int t = pack_atom<PACK>(pk, a, pa);
             xyzq[slot] = pa;  // w: the charge (0 without packing)
-            if (pk.packs()) tslot[slot] = sorted_type(pk, t);
+            if (PACK != kPackNone) tslot[slot] = sorted_type<PACK>(pk, t);
             sp[k] = pa;
         }
     } else if (small) {
@@ -354,7 +365,7 @@ __global__ void __launch_bounds__(kSortThreads) k_colsort(
             if (k < n) {
                 const int a = src[k];
                 p[u] = wpos[a];
-                typ[u] = pack_atom(pk, a, p[u]);  // loaded now, written after the sort
+                typ[u] = pack_atom<PACK>(pk, a, p[u]);  // loaded now, written after the sort
                 key[u] = zkey(p[u].z, a);
                 skey[k] = key[u];
             }
@@ -373,7 +384,7 @@ __global__ void __launch_bounds__(kSortThreads) k_colsort(
                 perm[slot] = a;
                 inv[a] = slot;
                 xyzq[slot] = p[u];
-                if (pk.packs()) tslot[slot] = sorted_type(pk, typ[u]);
+                if (PACK != kPackNone) tslot[slot] = sorted_type<PACK>(pk, typ[u]);
                 sp[rank[u]] = p[u];
             }
         }
@@ -390,9 +401,9 @@ __global__ void __launch_bounds__(kSortThreads) k_colsort(
             const int slot = base + rank;
             perm[slot] = a;
             inv[a] = slot;
-            const int t = pack_atom(pk, a, pa);
+            const int t = pack_atom<PACK>(pk, a, pa);
             xyzq[slot] = pa;
-            if (pk.packs()) tslot[slot] = sorted_type(pk, t);
+            if (PACK != kPackNone) tslot[slot] = sorted_type<PACK>(pk, t);
         }
     }
     for (int k = n + tid; k < npad; k += blockDim.x) {
@@ -400,7 +411,7 @@ __global__ void __launch_bounds__(kSortThreads) k_colsort(
         tslot[base + k] = 0;
         xyzq[base + k] = make_float4(kPadCoord, kPadCoord, kPadCoord, 0.0f);
     }
-    if (pk.packs()) {
+    if (PACK != kPackNone) {
         for (int k = tid; k < 3 * npad; k += blockDim.x) pk.facc[3ll * base + k] = 0;
         if (c == 0) {
             for (int k = tid; k < pk.n_acc; k += blockDim.x) pk.sys_acc[k] = 0;
@@ -991,11 +1002,12 @@ cudaError_t launch_build_cells(nb_ctx *ctx, const float *d_pos, const float *d_q
                    ctx->group, d.col_grp,
                    host_in ? AtomPack{d_q, d_type, ctx->pp.n_types, d.atom_t} : AtomPack{nullptr, nullptr, 0, nullptr});
     if (e == cudaSuccess)
-        e = launch_pdl(k_colsort, dim3(ctx->n_cols), dim3(kSortThreads), 0, st, (const int *)d.col_count + ctx->n_cols + 1, d.col_slot, d.col_sys,
-                       d.sys, (const int *)d.stage_fix, ctx->col_cap, d.stage, (const int *)d.atom_col, d.wpos, d.xyzq, d.tslot, d.perm, d.inv, d.bb, d.clus_sys, d.zbin, ctx->group,
-                       d.col_grp, d.grp, d.clus_grp,
-                       ColPack{host_in ? nullptr : d_q, host_in ? nullptr : d_type, ctx->pp.n_types,
-                               host_in ? (const int *)d.atom_t : nullptr, d.facc, d.sys_acc, kTaskVals * ctx->n_sys,
+        e = launch_pdl(!d_q ? k_colsort<kPackNone> : (host_in ? k_colsort<kPackAtomT> : k_colsort<kPackGather>),
+                       dim3(ctx->n_cols), dim3(kSortThreads), 0, st, (const int *)d.col_count + ctx->n_cols + 1,
+                       d.col_slot, d.col_sys, d.sys, (const int *)d.stage_fix, ctx->col_cap, d.stage,
+                       (const int *)d.atom_col, d.wpos, d.xyzq, d.tslot, d.perm, d.inv, d.bb, d.clus_sys, d.zbin,
+                       ctx->group, d.col_grp, d.grp, d.clus_grp,
+                       ColPack{d_q, d_type, ctx->pp.n_types, d.atom_t, d.facc, d.sys_acc, kTaskVals * ctx->n_sys,
                                d.counts + 3, d.status});
     if (e != cudaSuccess) return e;
     ctx->built_group = ctx->group;
