@@ -1779,7 +1779,7 @@ cudaError_t launch_forces_packed(nb_ctx *ctx, float *d_F, double *d_energy, doub
         cudaError_t e = launch_pme_join(ctx);
         if (e != cudaSuccess) return e;
     }
-    {
+    if (d_F) {  // else the caller's next kernel reads the fixed-point sums (the MD step)
         const int tb = 256;
         const int S = (int)ctx->n_atoms;
         const int blocks = std::max(1, std::min((S + tb - 1) / tb, 4 * ctx->num_sms));

@@ -11,9 +11,11 @@
 //                distance equations with the reference bond vectors of x):
 //                x'' = x' + disp and v += disp / dt
 //   cell list, short-range forces (+ PME), k_md_bonded
-//   k_md_second  B: v += dt/2 F/m, O: v <- c v + sigma xi'; waters then
-//                RATTLE (r_k . (v_a - v_b) = 0); kinetic energy; the last
-//                block writes the energies and advances the step counter
+//   k_md_second  reads the short-range (+ PME) forces from their
+//                fixed-point sums (no unpack kernel), B: v += dt/2 F/m,
+//                O: v <- c v + sigma xi'; waters then RATTLE
+//                (r_k . (v_a - v_b) = 0); kinetic energy; the last block
+//                writes the energies and advances the step counter
 // xi: Philox4x32-10 (Salmon et al. 2011) on the counter (atom, step,
 // stream, 0) and key (seed), 24-bit uniforms, Box-Muller.  Units kcal/mol,
 // A, amu, ps: F/m in kcal/mol/A/amu times 418.4 is A/ps^2.
@@ -233,6 +235,25 @@ __global__ void __launch_bounds__(256) k_md_bonded(int nb, int na, int nd, const
     md_flush<3>(v, acc, idx);
 }
 
+// The short-range (+ PME) forces of atom a straight from the fixed-point
+// sums in sorted order, converted as the unpack kernel converts them (the
+// same bits): the MD step reads them here instead of running the unpack.
+struct NbSums {
+    const int *inv;           // atom -> sorted slot
+    const long long *facc;    // [S*3] short-range sums (2^32)
+    const long long *pme_f;   // [S*3] PME sums, or null
+};
+
+__device__ __forceinline__ float3 nb_force_of(const NbSums &N, int a)
+{
+    const float sc = 2.3283064365386963e-10f;  // 2^-32
+    const long long s = N.inv[a];
+    const long long p0 = N.pme_f ? N.pme_f[3 * s] : 0, p1 = N.pme_f ? N.pme_f[3 * s + 1] : 0,
+                    p2 = N.pme_f ? N.pme_f[3 * s + 2] : 0;
+    return make_float3(__ll2float_rn(N.facc[3 * s] + p0) * sc, __ll2float_rn(N.facc[3 * s + 1] + p1) * sc,
+                       __ll2float_rn(N.facc[3 * s + 2] + p2) * sc);
+}
+
 // Total forces F = F_short + bonded (the fixed-point bonded sums are cleared).
 __device__ __forceinline__ void collect_force(int a, const float *__restrict__ Fnb, long long *__restrict__ bacc,
                                               float *__restrict__ Ftot, float &fx, float &fy, float &fz)
@@ -286,11 +307,20 @@ __device__ __forceinline__ float3 kick_drift(int a, float dt, float c, bool lang
 // B and O (stream 1) of atom a with the new forces (v updated in place).
 __device__ __forceinline__ float3 kick(int a, float dt, float c, bool langevin, unsigned long long seed,
                                        unsigned long long step, const float *__restrict__ mass,
-                                       const float *__restrict__ sigv, const float *__restrict__ Fnb,
+                                       const float *__restrict__ sigv, const NbSums &Nb,
                                        long long *__restrict__ bacc, float *__restrict__ Ftot, float *__restrict__ v)
 {
-    float fx, fy, fz;
-    collect_force(a, Fnb, bacc, Ftot, fx, fy, fz);
+    const float sc = 2.3283064365386963e-10f;  // 2^-32
+    const float3 fn = nb_force_of(Nb, a);
+    const float fx = fn.x + __ll2float_rn(bacc[3ll * a]) * sc;
+    const float fy = fn.y + __ll2float_rn(bacc[3ll * a + 1]) * sc;
+    const float fz = fn.z + __ll2float_rn(bacc[3ll * a + 2]) * sc;
+    bacc[3ll * a] = 0;
+    bacc[3ll * a + 1] = 0;
+    bacc[3ll * a + 2] = 0;
+    Ftot[3ll * a] = fx;
+    Ftot[3ll * a + 1] = fy;
+    Ftot[3ll * a + 2] = fz;
     const float h = 0.5f * dt * kAccel / mass[a];
     float vx = fmaf(h, fx, v[3ll * a]), vy = fmaf(h, fy, v[3ll * a + 1]), vz = fmaf(h, fz, v[3ll * a + 2]);
     if (langevin) {
@@ -466,10 +496,11 @@ __global__ void __launch_bounds__(64) k_md_second(int n_free, int nw, MdStep P,
                                                   unsigned long long *__restrict__ step,
                                                   const int *__restrict__ free_atoms, const int4 *__restrict__ waters,
                                                   const float *__restrict__ mass, const float *__restrict__ sigv,
-                                                  const float *__restrict__ Fnb, long long *__restrict__ bacc,
+                                                  NbSums Nb, long long *__restrict__ bacc,
                                                   float *__restrict__ Ftot, const float *__restrict__ x,
                                                   float *__restrict__ v, Box3 B, long long *__restrict__ acc,
-                                                  const double *__restrict__ enb, double *__restrict__ energy)
+                                                  const long long *__restrict__ sys_acc, const long long *__restrict__ pme_s,
+                                                  double pme_self, double *__restrict__ energy)
 {
     pdl_entry();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -477,7 +508,7 @@ __global__ void __launch_bounds__(64) k_md_second(int n_free, int nw, MdStep P,
     long long ke[1] = {0};
     if (t < n_free) {
         const int a = free_atoms[t];
-        const float3 u = kick(a, P.dt, P.c, P.langevin, P.seed, st, mass, sigv, Fnb, bacc, Ftot, v);
+        const float3 u = kick(a, P.dt, P.c, P.langevin, P.seed, st, mass, sigv, Nb, bacc, Ftot, v);
         ke[0] = __float2ll_rn(0.5f * mass[a] * fmaf(u.x, u.x, fmaf(u.y, u.y, u.z * u.z)) / kAccel * 4294967296.0f);
     } else if (t - n_free < nw) {
         const int4 W = waters[t - n_free];
@@ -485,7 +516,7 @@ __global__ void __launch_bounds__(64) k_md_second(int n_free, int nw, MdStep P,
         float im[3], vv[3][3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-            const float3 u = kick(at[i], P.dt, P.c, P.langevin, P.seed, st, mass, sigv, Fnb, bacc, Ftot, v);
+            const float3 u = kick(at[i], P.dt, P.c, P.langevin, P.seed, st, mass, sigv, Nb, bacc, Ftot, v);
             vv[i][0] = u.x;
             vv[i][1] = u.y;
             vv[i][2] = u.z;
@@ -528,9 +559,11 @@ __global__ void __launch_bounds__(64) k_md_second(int n_free, int nw, MdStep P,
         if (done == gridDim.x - 1ull) {  // every block has read step and added its sum
             __threadfence();
             const volatile long long *va = acc;
-            if (energy) {
-                energy[0] = enb[0];
-                energy[1] = enb[1];
+            if (energy) {  // the short-range (+ PME) energies as the unpack kernel converts them
+                long long e_lj = sys_acc[0], e_c = sys_acc[1];
+                if (pme_s) e_c += pme_s[0] + pme_s[2] + __double2ll_rn(pme_self * (double)pme_s[1] * (1.0 / 16.0));
+                energy[0] = (double)e_lj * (1.0 / kFixScale);
+                energy[1] = (double)e_c * (1.0 / kFixScale);
                 for (int k = 0; k < 4; ++k) energy[2 + k] = (double)va[k] * (1.0 / 4294967296.0);
             }
             step[0] += 1ull;
@@ -673,7 +706,8 @@ static cudaError_t launch_bonded(nb_ctx *ctx, const float *d_pos)
 // and the charge pack: it overlaps the list kernel and the short-range
 // kernel.  sums: the energies of this evaluation are reported (the PME
 // pair-correction energies are summed only then).
-static cudaError_t md_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type, bool sums)
+static cudaError_t md_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type, bool sums,
+                             bool unpack = true)
 {
     MdState &M = *ctx->md;
     cudaError_t e = launch_build_cells(ctx, d_pos, d_q, d_type);  // q and types packed on the way
@@ -682,7 +716,7 @@ static cudaError_t md_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, 
     if (e == cudaSuccess) e = launch_build_lists(ctx);
     if (e != cudaSuccess) return e;
     ctx->built = true;
-    e = launch_forces_packed(ctx, M.Fnb, M.enb, nullptr, false, pme, pme);
+    e = launch_forces_packed(ctx, unpack ? M.Fnb : nullptr, unpack ? M.enb : nullptr, nullptr, false, pme, pme);
     if (e != cudaSuccess) return e;
     return launch_bonded(ctx, d_pos);
 }
@@ -854,12 +888,15 @@ extern "C" nb_status nb_md_step(nb_ctx *ctx, float *d_pos, float *d_vel, const f
                        (const unsigned long long *)M.step, (const int *)M.free_atoms, (const int4 *)M.waters,
                        (const float *)M.mass, (const float *)M.sigv, (const float *)M.Ftot, d_pos, d_vel, B, M.acc,
                        ctx->d.status);
-        if (e == cudaSuccess) e = md_forces(ctx, d_pos, d_q, d_type, d_energy && s == n_steps - 1);
+        // the second half reads the short-range sums itself (no unpack kernel)
+        if (e == cudaSuccess) e = md_forces(ctx, d_pos, d_q, d_type, d_energy && s == n_steps - 1, false);
         if (e == cudaSuccess)
             e = launch_pdl(k_md_second, dim3(ib), dim3(64), 0, st, M.n_free, M.nw, P,
                            M.step, (const int *)M.free_atoms, (const int4 *)M.waters,
-                           (const float *)M.mass, (const float *)M.sigv, (const float *)M.Fnb, M.bacc, M.Ftot,
-                           (const float *)d_pos, d_vel, B, M.acc, (const double *)M.enb,
+                           (const float *)M.mass, (const float *)M.sigv,
+                           NbSums{ctx->d.inv, ctx->d.facc, ctx->pme ? pme_forces_acc(ctx) : nullptr}, M.bacc,
+                           M.Ftot, (const float *)d_pos, d_vel, B, M.acc, (const long long *)ctx->d.sys_acc,
+                           ctx->pme ? pme_sums_acc(ctx) : nullptr, ctx->pme ? pme_self_coef(ctx) : 0.0,
                            s == n_steps - 1 ? d_energy : (double *)nullptr);
     }
     return e == cudaSuccess ? NB_OK : NB_ERR_CUDA;
