@@ -3,8 +3,8 @@
 // velocity-Verlet integration, Langevin thermostat, M-SHAKE and RATTLE
 // constraints; section "Performance": the DHFR step with PME).
 //
-// One step of length dt from (x, v, F(x)); one thread per unconstrained atom
-// or per rigid water (its three atoms):
+// One step of length dt from (x, v, F(x)); one lane per unconstrained atom,
+// three per rigid water (one per atom, the constraints solved on all three):
 //   k_md_first   O: v <- c v + sigma xi (c = exp(-gamma dt/2),
 //                sigma = sqrt((1 - c^2) kT / m)), B: v += dt/2 F/m,
 //                A: x' = x + dt v; waters then M-SHAKE (Newton on the 3
@@ -431,14 +431,60 @@ __device__ __forceinline__ bool water_shake(const int (&at)[3], const float3 (&x
     return conv;
 }
 
-// First half of a step, one thread per unconstrained atom (items below
-// n_free) or per water.  A water's three atoms are kicked and drifted, then
-// M-SHAKE: lambda by Newton iterations on |r_k''|^2 = d_k^2,
+// Lanes of the two half-step kernels: the first ceil(n_free / 32) warps take
+// one unconstrained atom per lane; every later warp takes kWatersPerWarp
+// rigid waters, three lanes each (lane 3 j + i: atom i of water j; lanes 30
+// and 31 idle), so that a water's three atoms are kicked on three lanes and
+// the constraint solve, done redundantly on the three lanes with the same
+// inputs, gives every lane the same result.
+constexpr int kWatersPerWarp = 10;
+
+struct MdLane {
+    bool water_warp;  // the warp takes waters (warp-uniform)
+    bool active;      // the lane holds an atom
+    int item;         // free: index into free_atoms; water: water index
+    int i;            // water: atom of the water (0 = O, 1, 2 = H)
+};
+
+__device__ __forceinline__ MdLane md_lane(int n_free, int nw)
+{
+    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    const int free_warps = (n_free + 31) >> 5;
+    MdLane L;
+    L.water_warp = gw >= free_warps;
+    if (!L.water_warp) {
+        L.item = gw * 32 + lane;
+        L.i = 0;
+        L.active = L.item < n_free;
+    } else {
+        L.item = (gw - free_warps) * kWatersPerWarp + lane / 3;
+        L.i = lane % 3;
+        L.active = lane < 3 * kWatersPerWarp && L.item < nw;
+    }
+    return L;
+}
+
+inline int md_lane_blocks(int n_free, int nw)
+{
+    const int warps = (n_free + 31) / 32 + (nw + kWatersPerWarp - 1) / kWatersPerWarp;
+    return std::max(1, (warps + 1) / 2);  // 64-thread blocks
+}
+
+// Value v of lane base + k of this warp, for k = 0, 1, 2 (the water's atoms).
+__device__ __forceinline__ float3 water_lanes3(float3 v, int base, int k)
+{
+    return make_float3(__shfl_sync(0xffffffffu, v.x, base + k), __shfl_sync(0xffffffffu, v.y, base + k),
+                       __shfl_sync(0xffffffffu, v.z, base + k));
+}
+
+// First half of a step.  An unconstrained atom: O, B, A.  A water: each of
+// its three lanes kicks and drifts its atom, then M-SHAKE on the three
+// lanes: lambda by Newton iterations on |r_k''|^2 = d_k^2,
 // r_k'' = u_k + sum_l lambda_l C_kl r_l (u: new, r: reference vectors of x,
 // C_kl = s(a_k, l)/m_{a_k} - s(b_k, l)/m_{b_k}), disp_i =
 // sum_l lambda_l s(i, l) r_l / m_i, until every |g_k| / d_k^2 < tol or
-// max_iter iterations.  New positions wrapped into the box.  Block 0 clears
-// the energy sums of this step.
+// max_iter iterations; each lane moves its atom.  New positions wrapped into
+// the box.  Block 0 clears the energy sums of this step.
 __global__ void __launch_bounds__(64) k_md_first(int n_free, int nw, MdStep P,
                                                  const unsigned long long *__restrict__ step,
                                                  const int *__restrict__ free_atoms, const int4 *__restrict__ waters,
@@ -448,50 +494,58 @@ __global__ void __launch_bounds__(64) k_md_first(int n_free, int nw, MdStep P,
                                                  int *__restrict__ status)
 {
     pdl_entry();
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (blockIdx.x == 0 && threadIdx.x < kMdAcc) acc[threadIdx.x] = 0;
     const unsigned long long st = step[0];
-    if (t < n_free) {
-        const int a = free_atoms[t];
+    const MdLane L = md_lane(n_free, nw);
+    if (!L.water_warp) {
+        if (!L.active) return;
+        const int a = free_atoms[L.item];
         const float3 p = kick_drift(a, P.dt, P.c, P.langevin, P.seed, st, mass, sigv, Ftot, x, v);
         x[3ll * a] = wrap_coord(p.x, B.L[0]);
         x[3ll * a + 1] = wrap_coord(p.y, B.L[1]);
         x[3ll * a + 2] = wrap_coord(p.z, B.L[2]);
         return;
     }
-    const int w = t - n_free;
-    if (w >= nw) return;
-    const int4 W = waters[w];
+    // water warp: every lane stays to the end (shuffles, warp barrier)
+    const int4 W = L.active ? waters[L.item] : make_int4(0, 0, 0, 0);
     const int at[3] = {W.x, W.y, W.z};
+    const int a = L.i == 0 ? at[0] : (L.i == 1 ? at[1] : at[2]);
+    float3 mine = make_float3(0.0f, 0.0f, 0.0f);
+    float im_mine = 1.0f;
+    if (L.active) {
+        mine = kick_drift(a, P.dt, P.c, P.langevin, P.seed, st, mass, sigv, Ftot, x, v);
+        im_mine = 1.0f / mass[a];
+    }
+    const int base = (threadIdx.x & 31) - L.i;
     float3 xn[3];
     float im[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        xn[i] = kick_drift(at[i], P.dt, P.c, P.langevin, P.seed, st, mass, sigv, Ftot, x, v);
-        im[i] = 1.0f / mass[at[i]];
+    for (int k = 0; k < 3; ++k) {
+        xn[k] = water_lanes3(mine, base, k);
+        im[k] = __shfl_sync(0xffffffffu, im_mine, base + k);
     }
     float3 dsp[3];
-    if (!water_shake(at, xn, im, x, B, P, dsp)) atomicOr(status, ST_TIMEOUT);
+    if (L.active && !water_shake(at, xn, im, x, B, P, dsp) && L.i == 0) atomicOr(status, ST_TIMEOUT);
+    __syncwarp();  // the three lanes read the reference positions x before any writes them
+    if (!L.active) return;
+    const float3 d = L.i == 0 ? dsp[0] : (L.i == 1 ? dsp[1] : dsp[2]);
     const float idt = 1.0f / P.dt;
-    // the reference vectors above read x: write the new positions afterwards
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        const int a = at[i];
-        x[3ll * a] = wrap_coord(xn[i].x + dsp[i].x, B.L[0]);
-        x[3ll * a + 1] = wrap_coord(xn[i].y + dsp[i].y, B.L[1]);
-        x[3ll * a + 2] = wrap_coord(xn[i].z + dsp[i].z, B.L[2]);
-        v[3ll * a] = fmaf(dsp[i].x, idt, v[3ll * a]);
-        v[3ll * a + 1] = fmaf(dsp[i].y, idt, v[3ll * a + 1]);
-        v[3ll * a + 2] = fmaf(dsp[i].z, idt, v[3ll * a + 2]);
-    }
+    x[3ll * a] = wrap_coord(mine.x + d.x, B.L[0]);
+    x[3ll * a + 1] = wrap_coord(mine.y + d.y, B.L[1]);
+    x[3ll * a + 2] = wrap_coord(mine.z + d.z, B.L[2]);
+    v[3ll * a] = fmaf(d.x, idt, v[3ll * a]);
+    v[3ll * a + 1] = fmaf(d.y, idt, v[3ll * a + 1]);
+    v[3ll * a + 2] = fmaf(d.z, idt, v[3ll * a + 2]);
 }
 
-// Second half of a step, same threads: B and O with the new forces; a
-// water's velocities then by RATTLE, mu from the 3 x 3 system
+// Second half of a step, same lanes: B and O with the new forces (the
+// short-range and PME forces read from their fixed-point sums); a water's
+// velocities then by RATTLE on its three lanes, mu from the 3 x 3 system
 // sum_l mu_l C_kl (r_k . r_l) = -r_k . (v_a - v_b), v_i += sum_l mu_l s(i,l) r_l / m_i;
-// kinetic energy of the thread's atoms.  The last block to finish writes
-// the energies (short-range + long-range from enb, the fixed-point sums of
-// acc) to energy, when given, and advances the device step counter.
+// kinetic energy (a water's on its first lane).  The last block to finish
+// writes the energies (short-range + long-range from their sums, the
+// fixed-point sums of acc) to energy, when given, and advances the device
+// step counter.
 __global__ void __launch_bounds__(64) k_md_second(int n_free, int nw, MdStep P,
                                                   unsigned long long *__restrict__ step,
                                                   const int *__restrict__ free_atoms, const int4 *__restrict__ waters,
@@ -503,52 +557,71 @@ __global__ void __launch_bounds__(64) k_md_second(int n_free, int nw, MdStep P,
                                                   double pme_self, double *__restrict__ energy)
 {
     pdl_entry();
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned long long st = step[0];
     long long ke[1] = {0};
-    if (t < n_free) {
-        const int a = free_atoms[t];
-        const float3 u = kick(a, P.dt, P.c, P.langevin, P.seed, st, mass, sigv, Nb, bacc, Ftot, v);
-        ke[0] = __float2ll_rn(0.5f * mass[a] * fmaf(u.x, u.x, fmaf(u.y, u.y, u.z * u.z)) / kAccel * 4294967296.0f);
-    } else if (t - n_free < nw) {
-        const int4 W = waters[t - n_free];
-        const int at[3] = {W.x, W.y, W.z};
-        float im[3], vv[3][3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            const float3 u = kick(at[i], P.dt, P.c, P.langevin, P.seed, st, mass, sigv, Nb, bacc, Ftot, v);
-            vv[i][0] = u.x;
-            vv[i][1] = u.y;
-            vv[i][2] = u.z;
-            im[i] = 1.0f / mass[at[i]];
+    const MdLane L = md_lane(n_free, nw);
+    if (!L.water_warp) {
+        if (L.active) {
+            const int a = free_atoms[L.item];
+            const float3 u = kick(a, P.dt, P.c, P.langevin, P.seed, st, mass, sigv, Nb, bacc, Ftot, v);
+            ke[0] = __float2ll_rn(0.5f * mass[a] * fmaf(u.x, u.x, fmaf(u.y, u.y, u.z * u.z)) / kAccel *
+                                  4294967296.0f);
         }
-        float3 r[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) r[k] = disp(x, at[con_b(k)], at[con_a(k)], B);
-        float A[3][3], b[3], mu[3];
+    } else {
+        const int4 W = L.active ? waters[L.item] : make_int4(0, 0, 0, 0);
+        const int at[3] = {W.x, W.y, W.z};
+        const int a = L.i == 0 ? at[0] : (L.i == 1 ? at[1] : at[2]);
+        float3 mine = make_float3(0.0f, 0.0f, 0.0f);
+        float m_mine = 1.0f;
+        if (L.active) {
+            mine = kick(a, P.dt, P.c, P.langevin, P.seed, st, mass, sigv, Nb, bacc, Ftot, v);
+            m_mine = mass[a];
+        }
+        const int base = (threadIdx.x & 31) - L.i;
+        float m[3], im[3], vv[3][3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const int a = con_a(k), bb = con_b(k);
-            const float3 dv = make_float3(vv[a][0] - vv[bb][0], vv[a][1] - vv[bb][1], vv[a][2] - vv[bb][2]);
-            b[k] = -dot3(r[k], dv);
-#pragma unroll
-            for (int l = 0; l < 3; ++l)
-                A[k][l] = (sgn(a, l) * im[a] - sgn(bb, l) * im[bb]) * dot3(r[k], r[l]);
+            const float3 u = water_lanes3(mine, base, k);
+            vv[k][0] = u.x;
+            vv[k][1] = u.y;
+            vv[k][2] = u.z;
+            m[k] = __shfl_sync(0xffffffffu, m_mine, base + k);
+            im[k] = 1.0f / m[k];
         }
-        solve3(A, b, mu);
-        float e = 0.0f;
+        if (L.active) {
+            float3 r[3];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            float3 dv = make_float3(0.0f, 0.0f, 0.0f);
+            for (int k = 0; k < 3; ++k) r[k] = disp(x, at[con_b(k)], at[con_a(k)], B);
+            float A[3][3], b[3], mu[3];
 #pragma unroll
-            for (int l = 0; l < 3; ++l) dv = add3(dv, scale3(mu[l] * sgn(i, l) * im[i], r[l]));
-            const float vx = vv[i][0] + dv.x, vy = vv[i][1] + dv.y, vz = vv[i][2] + dv.z;
-            v[3ll * at[i]] = vx;
-            v[3ll * at[i] + 1] = vy;
-            v[3ll * at[i] + 2] = vz;
-            e = fmaf(0.5f * mass[at[i]], fmaf(vx, vx, fmaf(vy, vy, vz * vz)), e);
+            for (int k = 0; k < 3; ++k) {
+                const int ka = con_a(k), kb = con_b(k);
+                const float3 dv = make_float3(vv[ka][0] - vv[kb][0], vv[ka][1] - vv[kb][1], vv[ka][2] - vv[kb][2]);
+                b[k] = -dot3(r[k], dv);
+#pragma unroll
+                for (int l = 0; l < 3; ++l)
+                    A[k][l] = (sgn(ka, l) * im[ka] - sgn(kb, l) * im[kb]) * dot3(r[k], r[l]);
+            }
+            solve3(A, b, mu);
+            float e = 0.0f, mx = 0.0f, my = 0.0f, mz = 0.0f;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                float3 dv = make_float3(0.0f, 0.0f, 0.0f);
+#pragma unroll
+                for (int l = 0; l < 3; ++l) dv = add3(dv, scale3(mu[l] * sgn(i, l) * im[i], r[l]));
+                const float vx = vv[i][0] + dv.x, vy = vv[i][1] + dv.y, vz = vv[i][2] + dv.z;
+                if (i == L.i) {
+                    mx = vx;
+                    my = vy;
+                    mz = vz;
+                }
+                e = fmaf(0.5f * m[i], fmaf(vx, vx, fmaf(vy, vy, vz * vz)), e);
+            }
+            v[3ll * a] = mx;
+            v[3ll * a + 1] = my;
+            v[3ll * a + 2] = mz;
+            if (L.i == 0) ke[0] = __float2ll_rn(e / kAccel * 4294967296.0f);
         }
-        ke[0] = __float2ll_rn(e / kAccel * 4294967296.0f);
     }
     const int idx[1] = {3};
     md_flush<1>(ke, acc, idx);
@@ -863,9 +936,9 @@ extern "C" nb_status nb_md_step(nb_ctx *ctx, float *d_pos, float *d_vel, const f
     const Box3 B = box_of(ctx);
     const int N = M.n;
     const int ab = (N + 255) / 256;
-    // one thread per unconstrained atom or rigid water, 64-thread blocks
-    // (the integration is latency bound: spread it over the SMs)
-    const int ib = std::max(1, (M.n_free + M.nw + 63) / 64);
+    // one lane per unconstrained atom, three per rigid water, 64-thread
+    // blocks (the integration is latency bound: spread it over the SMs)
+    const int ib = md_lane_blocks(M.n_free, M.nw);
     MdStep P;
     P.dt = M.dt;
     P.c = M.c;
