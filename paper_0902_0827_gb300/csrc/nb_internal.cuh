@@ -274,7 +274,10 @@ cudaError_t launch_adjoint_tile(nb_ctx *ctx, const double *d_dLdE, float *d_dpos
 cudaError_t launch_pme(nb_ctx *ctx, const float *d_pos, const float *d_q);
 // the same chain forked onto the PME side stream, and the join back
 // sums: also the pair-correction energy and virial (the forces always)
-cudaError_t launch_pme_fork(nb_ctx *ctx, const float *d_pos, const float *d_q, bool sums = true);
+// side_first: launched on the side stream before the PME chain (work that
+// is independent of the short-range path, e.g. the MD step's bonded terms).
+cudaError_t launch_pme_fork(nb_ctx *ctx, const float *d_pos, const float *d_q, bool sums = true,
+                            cudaError_t (*side_first)(nb_ctx *, cudaStream_t, const float *) = nullptr);
 cudaError_t launch_pme_join(nb_ctx *ctx);
 void pme_free(nb_ctx *ctx);
 const long long *pme_forces_acc(const nb_ctx *ctx);

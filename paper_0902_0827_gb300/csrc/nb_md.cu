@@ -760,38 +760,38 @@ void md_free(nb_ctx *ctx)
     ctx->md = nullptr;
 }
 
-static cudaError_t launch_bonded(nb_ctx *ctx, const float *d_pos)
+static cudaError_t launch_bonded(nb_ctx *ctx, cudaStream_t st, const float *d_pos)
 {
     MdState &M = *ctx->md;
     const int terms = M.nb + M.na + M.nd;
     if (terms == 0) return cudaSuccess;
     const int blocks = std::max(1, std::min((terms + 255) / 256, 4 * ctx->num_sms));
-    return launch_pdl(k_md_bonded, dim3(blocks), dim3(256), 0, ctx->stream, M.nb, M.na, M.nd,
+    return launch_pdl(k_md_bonded, dim3(blocks), dim3(256), 0, st, M.nb, M.na, M.nd,
                       (const int2 *)M.bonds, (const float2 *)M.bond_p, (const int4 *)M.angles,
                       (const float2 *)M.angle_p, (const int4 *)M.dihedrals, (const float4 *)M.dihedral_p, d_pos,
                       box_of(ctx), M.bacc, M.acc);
 }
 
-// Cell list, short-range forces (+ PME) and bonded forces at d_pos.
 // Forces at d_pos: cell list, short-range forces, PME (when enabled) and
 // bonded terms.  The PME chain needs the sorted atoms but not the pair
 // lists, so it is forked onto its side stream right after the column sort
 // and the charge pack: it overlaps the list kernel and the short-range
-// kernel.  sums: the energies of this evaluation are reported (the PME
-// pair-correction energies are summed only then).
+// kernel; the bonded terms (positions only) run first on that stream, off
+// the short-range path.  sums: the energies of this evaluation are
+// reported (the PME pair-correction energies are summed only then).
 static cudaError_t md_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type, bool sums,
                              bool unpack = true)
 {
     MdState &M = *ctx->md;
     cudaError_t e = launch_build_cells(ctx, d_pos, d_q, d_type);  // q and types packed on the way
     const bool pme = ctx->pme != nullptr;
-    if (e == cudaSuccess && pme) e = launch_pme_fork(ctx, d_pos, d_q, sums);
+    if (e == cudaSuccess && pme) e = launch_pme_fork(ctx, d_pos, d_q, sums, launch_bonded);
     if (e == cudaSuccess) e = launch_build_lists(ctx);
     if (e != cudaSuccess) return e;
     ctx->built = true;
     e = launch_forces_packed(ctx, unpack ? M.Fnb : nullptr, unpack ? M.enb : nullptr, nullptr, false, pme, pme);
-    if (e != cudaSuccess) return e;
-    return launch_bonded(ctx, d_pos);
+    if (e != cudaSuccess || pme) return e;  // with PME the join above waited for the bonded terms too
+    return launch_bonded(ctx, ctx->stream, d_pos);
 }
 
 }  // namespace acenb
@@ -918,7 +918,7 @@ extern "C" nb_status nb_bonded_forces(nb_ctx *ctx, const float *d_pos, float *d_
     MdState &M = *ctx->md;
     cudaError_t e = cudaMemsetAsync(M.bacc, 0, sizeof(long long) * 3 * M.n, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(M.acc, 0, sizeof(long long) * kMdAcc, ctx->stream);
-    if (e == cudaSuccess) e = launch_bonded(ctx, d_pos);
+    if (e == cudaSuccess) e = launch_bonded(ctx, ctx->stream, d_pos);
     if (e == cudaSuccess)
         e = launch_pdl(k_md_bonded_out, dim3((3 * M.n + 255) / 256), dim3(256), 0, ctx->stream, M.n,
                        (const long long *)M.bacc, (const long long *)M.acc, d_F, d_energy);

@@ -723,11 +723,13 @@ cudaError_t launch_pme(nb_ctx *ctx, const float *d_pos, const float *d_q)
     return launch_pme_on(ctx, ctx->stream, d_pos, d_q, true);
 }
 
-cudaError_t launch_pme_fork(nb_ctx *ctx, const float *d_pos, const float *d_q, bool sums)
+cudaError_t launch_pme_fork(nb_ctx *ctx, const float *d_pos, const float *d_q, bool sums,
+                            cudaError_t (*side_first)(nb_ctx *, cudaStream_t, const float *))
 {
     PmeState &P = *ctx->pme;
     cudaError_t e = cudaEventRecord(P.fork, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(P.side, P.fork, 0);
+    if (e == cudaSuccess && side_first) e = side_first(ctx, P.side, d_pos);
     if (e == cudaSuccess) e = launch_pme_on(ctx, P.side, d_pos, d_q, sums);
     if (e == cudaSuccess) e = cudaEventRecord(P.join, P.side);
     return e;
