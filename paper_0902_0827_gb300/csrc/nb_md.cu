@@ -624,7 +624,8 @@ __global__ void __launch_bounds__(64) k_md_second(int n_free, int nw, MdStep P,
         }
     }
     const int idx[1] = {3};
-    md_flush<1>(ke, acc, idx);
+    if (energy) md_flush<1>(ke, acc, idx);  // the kinetic energy only when reported
+    else __syncthreads();                   // (its barrier: every thread has read step before the ticket)
     if (threadIdx.x == 0) {  // the thread that added this block's sum
         __threadfence();
         const unsigned long long done =
