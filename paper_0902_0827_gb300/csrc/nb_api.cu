@@ -313,7 +313,7 @@ nb_status nb_step(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32
     if (e == cudaSuccess) e = launch_build_lists(ctx);
     if (e != cudaSuccess) return NB_ERR_CUDA;
     ctx->built = true;
-    e = launch_forces_packed(ctx, d_F, d_energy, d_virial, false, pme, pme);
+    e = launch_forces_packed(ctx, d_F, d_energy, d_virial, false, pme, pme, pme);
     return e == cudaSuccess ? NB_OK : NB_ERR_CUDA;
 }
 

@@ -358,6 +358,16 @@ __device__ __forceinline__ long long tile_fixed(float f, bool &ovf)
     return __float2ll_rn((ok ? f : 0.0f) * 4294967296.0f);
 }
 
+// Claim of the next work unit (lane 0).  min_left > 0 (a helper launch):
+// claim only while at least min_left units are unclaimed, else return
+// n_units (the launch's own warps finish the rest sooner than a late
+// helper unit would).
+__device__ __forceinline__ int claim_unit(const ForceArgs &A, int n_units, int min_left)
+{
+    if (min_left > 0 && n_units - *(volatile const int *)A.work < min_left) return n_units;
+    return atomicAdd(A.work, 1);
+}
+
 // Work unit u of the tile kernels: group, segment of its list, part of the
 // segment, and the entry range [e_begin, e_end) of that part.
 struct Unit {
@@ -546,7 +556,7 @@ __host__ __device__ inline size_t tile_warp_bytes(int G)
 }
 
 template <int G, int RAD, bool VIRIAL, bool DEBUG>
-__global__ void __launch_bounds__(kTileWarps * 32, ACENB_TILE_MIN_BLOCKS) k_force(ForceArgs A, int parts)
+__global__ void __launch_bounds__(kTileWarps * 32, ACENB_TILE_MIN_BLOCKS) k_force(ForceArgs A, int parts, int min_left)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long s_val[kTileWarps][kTaskVals];
@@ -576,11 +586,11 @@ __global__ void __launch_bounds__(kTileWarps * 32, ACENB_TILE_MIN_BLOCKS) k_forc
     long long wv = 0;  // lane k < 6: fixed-point image virial component k of the current system
     bool ovf = false;  // a force sum out of the fixed-point range
     int u = 0;
-    if (lane == 0) u = atomicAdd(A.work, 1);
+    if (lane == 0) u = claim_unit(A, n_units, min_left);
     u = __shfl_sync(kFull, u, 0);
     while (u < n_units) {
         int u_next = 0;
-        if (lane == 0) u_next = atomicAdd(A.work, 1);  // claimed now, used after this unit
+        if (lane == 0) u_next = claim_unit(A, n_units, min_left);  // claimed now, used after this unit
         const Unit U = unit_of(A, u, parts);
         if (U.e_begin < U.e_end) {
             const int2 gr = __ldg(A.grp + U.g);
@@ -852,7 +862,7 @@ __device__ __forceinline__ void tile1_entry(const ForceArgs &A, const float4 *__
 __host__ __device__ inline size_t tile1_warp_bytes() { return (size_t)kBatch1 * kCluster * (16 + 4); }
 
 template <int RAD, bool VIRIAL, bool DEBUG>
-__global__ void __launch_bounds__(kTileWarps * 32, ACENB_TILE_MIN_BLOCKS) k_force1(ForceArgs A, int parts)
+__global__ void __launch_bounds__(kTileWarps * 32, ACENB_TILE_MIN_BLOCKS) k_force1(ForceArgs A, int parts, int min_left)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long s_val[kTileWarps][kTaskVals];
@@ -877,11 +887,11 @@ __global__ void __launch_bounds__(kTileWarps * 32, ACENB_TILE_MIN_BLOCKS) k_forc
     long long wv = 0;
     bool ovf = false;
     int u = 0;
-    if (lane == 0) u = atomicAdd(A.work, 1);
+    if (lane == 0) u = claim_unit(A, n_units, min_left);
     u = __shfl_sync(kFull, u, 0);
     while (u < n_units) {
         int u_next = 0;
-        if (lane == 0) u_next = atomicAdd(A.work, 1);
+        if (lane == 0) u_next = claim_unit(A, n_units, min_left);
         const Unit U = unit_of(A, u, parts);
         // what needs only the unit's group and segment is loaded before the
         // segment's length is known: one-cluster groups are numbered like
@@ -1648,9 +1658,13 @@ size_t tile_smem_bytes(int T, int G) { return lj_table_bytes(T) + (size_t)kTileW
 
 // beside_pme: the PME chain, forked before the list kernel, runs on its side
 // stream during this kernel; the persistent grid then leaves one block slot
-// per SM free, so that the PME kernels run alongside instead of after it.
+// per SM free, so that the PME kernels run alongside instead of after it,
+// and a second launch of the same kernel, one block per SM on the side
+// stream behind the PME chain (and the lists), takes units from the same
+// counter once the chain is done (helper).  Which block takes which unit
+// does not change any result.
 template <int G, int RAD, bool VIRIAL, bool DEBUG>
-static void launch_force_g(nb_ctx *ctx, const ForceArgs &A, bool beside_pme)
+static void launch_force_g(nb_ctx *ctx, const ForceArgs &A, bool beside_pme, bool helper)
 {
     const size_t smem = tile_smem_bytes(A.P.n_types, G);
     static std::atomic<unsigned long long> optin{0};
@@ -1658,32 +1672,42 @@ static void launch_force_g(nb_ctx *ctx, const ForceArgs &A, bool beside_pme)
     // persistent grid: never more blocks than can be resident at once
     int resident = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_force<G, RAD, VIRIAL, DEBUG>, kTileWarps * 32, smem);
-    const int per_sm = std::max(1, std::min(ctx->tune.blocks_per_sm, resident) - (beside_pme ? 1 : 0));
+    const int per_sm = helper ? 1 : std::max(1, std::min(ctx->tune.blocks_per_sm, resident) - (beside_pme ? 1 : 0));
     const int parts = ctx->tune.list_split > 0 ? ctx->tune.list_split : kDefaultListSplit;
+    // a helper claims units while more are left than the main launch's warps hold
+    const int min_left = helper ? ctx->num_sms * std::max(1, std::min(ctx->tune.blocks_per_sm, resident) - 1) * kTileWarps : 0;
     launch_pdl(k_force<G, RAD, VIRIAL, DEBUG>, dim3(ctx->num_sms * per_sm), dim3(kTileWarps * 32), smem,
-               ctx->stream, A, parts);
+               helper ? pme_side_stream(ctx) : ctx->stream, A, parts, min_left);
 }
 
 template <int RAD, bool VIRIAL, bool DEBUG>
-static void launch_force_1(nb_ctx *ctx, const ForceArgs &A, bool beside_pme)
+static void launch_force_1(nb_ctx *ctx, const ForceArgs &A, bool beside_pme, bool helper)
 {
     const size_t smem = lj_table_bytes(A.P.n_types) + (size_t)kTileWarps * tile1_warp_bytes();
     static std::atomic<unsigned long long> optin{0};
     smem_optin_once(k_force1<RAD, VIRIAL, DEBUG>, ctx->device, 200 * 1024, optin);
     int resident = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_force1<RAD, VIRIAL, DEBUG>, kTileWarps * 32, smem);
-    const int per_sm = std::max(1, std::min(ctx->tune.blocks_per_sm, resident) - (beside_pme ? 1 : 0));
+    const int per_sm = helper ? 1 : std::max(1, std::min(ctx->tune.blocks_per_sm, resident) - (beside_pme ? 1 : 0));
     const int parts = ctx->tune.list_split > 0 ? ctx->tune.list_split : kDefaultListSplit;
-    launch_pdl(k_force1<RAD, VIRIAL, DEBUG>, dim3(ctx->num_sms * per_sm), dim3(kTileWarps * 32), smem, ctx->stream,
-               A, parts);
+    const int min_left = helper ? ctx->num_sms * std::max(1, std::min(ctx->tune.blocks_per_sm, resident) - 1) * kTileWarps : 0;
+    launch_pdl(k_force1<RAD, VIRIAL, DEBUG>, dim3(ctx->num_sms * per_sm), dim3(kTileWarps * 32), smem,
+               helper ? pme_side_stream(ctx) : ctx->stream, A, parts, min_left);
 }
 
 template <int RAD, bool VIRIAL, bool DEBUG>
-static void launch_force_t(nb_ctx *ctx, const ForceArgs &A, bool beside_pme)
+static void launch_force_t(nb_ctx *ctx, const ForceArgs &A, bool beside_pme, bool helper)
 {
-    if (ctx->built_group == 1) launch_force_1<RAD, VIRIAL, DEBUG>(ctx, A, beside_pme);
-    else if (ctx->built_group == 4) launch_force_g<4, RAD, VIRIAL, DEBUG>(ctx, A, beside_pme);
-    else launch_force_g<8, RAD, VIRIAL, DEBUG>(ctx, A, beside_pme);
+    helper = helper && beside_pme;
+    // the lists are the last work on the context's stream here: the side
+    // stream waits for them before the helper
+    if (helper && pme_side_after_lists(ctx) != cudaSuccess) return;
+    for (int h = 0; h < (helper ? 2 : 1); ++h) {  // h = 1: the helper behind the PME chain
+        if (ctx->built_group == 1) launch_force_1<RAD, VIRIAL, DEBUG>(ctx, A, beside_pme, h == 1);
+        else if (ctx->built_group == 4) launch_force_g<4, RAD, VIRIAL, DEBUG>(ctx, A, beside_pme, h == 1);
+        else launch_force_g<8, RAD, VIRIAL, DEBUG>(ctx, A, beside_pme, h == 1);
+        if (h == 1) pme_side_rejoin(ctx);
+    }
 }
 
 static ForceArgs make_args(nb_ctx *ctx)
@@ -1749,7 +1773,7 @@ cudaError_t launch_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, con
 }
 
 cudaError_t launch_forces_packed(nb_ctx *ctx, float *d_F, double *d_energy, double *d_virial, bool debug_pairs,
-                                 bool pme, bool beside_pme)
+                                 bool pme, bool beside_pme, bool helper)
 {
     auto &d = ctx->d;
     ForceArgs A = make_args(ctx);
@@ -1759,17 +1783,17 @@ cudaError_t launch_forces_packed(nb_ctx *ctx, float *d_F, double *d_energy, doub
     const bool prof = ctx->profiling && ctx->prof_n < (int)ctx->prof_ev.size() / 2;
     if (prof) cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n], ctx->stream);
     if (debug_pairs) {  // the pair set does not depend on the radial functions
-        if (ewald) launch_force_t<1, false, true>(ctx, A, beside_pme);
-        else launch_force_t<0, false, true>(ctx, A, beside_pme);
+        if (ewald) launch_force_t<1, false, true>(ctx, A, beside_pme, helper);
+        else launch_force_t<0, false, true>(ctx, A, beside_pme, helper);
     } else if (ctx->tab_n > 0) {
-        if (virial) launch_force_t<2, true, false>(ctx, A, beside_pme);
-        else launch_force_t<2, false, false>(ctx, A, beside_pme);
+        if (virial) launch_force_t<2, true, false>(ctx, A, beside_pme, helper);
+        else launch_force_t<2, false, false>(ctx, A, beside_pme, helper);
     } else if (ewald) {
-        if (virial) launch_force_t<1, true, false>(ctx, A, beside_pme);
-        else launch_force_t<1, false, false>(ctx, A, beside_pme);
+        if (virial) launch_force_t<1, true, false>(ctx, A, beside_pme, helper);
+        else launch_force_t<1, false, false>(ctx, A, beside_pme, helper);
     } else {
-        if (virial) launch_force_t<0, true, false>(ctx, A, beside_pme);
-        else launch_force_t<0, false, false>(ctx, A, beside_pme);
+        if (virial) launch_force_t<0, true, false>(ctx, A, beside_pme, helper);
+        else launch_force_t<0, false, false>(ctx, A, beside_pme, helper);
     }
     if (prof) {
         cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n + 1], ctx->stream);

@@ -262,9 +262,12 @@ cudaError_t launch_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, con
                           float *d_F, double *d_energy, double *d_virial, bool debug_pairs);
 // launch_forces after its pack (and, when pme_forked, the PME fork): the
 // short-range kernel, the PME join and the unpack; beside_pme: the PME chain
-// was forked early enough to share the SMs with the short-range kernel
+// was forked early enough to share the SMs with the short-range kernel;
+// helper: a second launch of the short-range kernel behind the PME chain
+// takes units from the same counter (worth it when the PME chain ends well
+// before the short-range kernel)
 cudaError_t launch_forces_packed(nb_ctx *ctx, float *d_F, double *d_energy, double *d_virial, bool debug_pairs,
-                                 bool pme_forked, bool beside_pme);
+                                 bool pme_forked, bool beside_pme, bool helper = false);
 size_t force_smem_for(int T, int scap, int K);
 cudaError_t launch_pack(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type, bool zero_sums);
 cudaError_t launch_type_grad(nb_ctx *ctx, const double *gsig_tab, const double *geps_tab, double *gsig, double *geps);
@@ -276,6 +279,11 @@ cudaError_t launch_pme(nb_ctx *ctx, const float *d_pos, const float *d_q);
 // sums: also the pair-correction energy and virial (the forces always)
 // side_first: launched on the side stream before the PME chain (work that
 // is independent of the short-range path, e.g. the MD step's bonded terms).
+// The PME side stream; after_lists makes it wait for the pair lists (an event
+// on the context's stream), rejoin moves the join event to its current end.
+cudaStream_t pme_side_stream(const nb_ctx *ctx);
+cudaError_t pme_side_after_lists(nb_ctx *ctx);
+cudaError_t pme_side_rejoin(nb_ctx *ctx);
 cudaError_t launch_pme_fork(nb_ctx *ctx, const float *d_pos, const float *d_q, bool sums = true,
                             cudaError_t (*side_first)(nb_ctx *, cudaStream_t, const float *) = nullptr);
 cudaError_t launch_pme_join(nb_ctx *ctx);

@@ -123,6 +123,7 @@ struct PmeState {
     // context's stream, so it overlaps the short-range kernel
     cudaStream_t side = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
+    cudaEvent_t lists = nullptr;  // the pair lists are built (the short-range helper may start)
     PmeGeom g{};
     PmeCorr c{};
 };
@@ -667,6 +668,7 @@ void pme_free(nb_ctx *ctx)
     }
     if (p->fork) cudaEventDestroy(p->fork);
     if (p->join) cudaEventDestroy(p->join);
+    if (p->lists) cudaEventDestroy(p->lists);
     void *ptrs[] = {p->grid, p->fq, p->gfac, p->pacc, p->acc};
     for (void *q : ptrs)
         if (q) cudaFree(q);
@@ -734,6 +736,17 @@ cudaError_t launch_pme_fork(nb_ctx *ctx, const float *d_pos, const float *d_q, b
     if (e == cudaSuccess) e = cudaEventRecord(P.join, P.side);
     return e;
 }
+
+cudaStream_t pme_side_stream(const nb_ctx *ctx) { return ctx->pme->side; }
+
+cudaError_t pme_side_after_lists(nb_ctx *ctx)
+{
+    PmeState &P = *ctx->pme;
+    cudaError_t e = cudaEventRecord(P.lists, ctx->stream);
+    return e == cudaSuccess ? cudaStreamWaitEvent(P.side, P.lists, 0) : e;
+}
+
+cudaError_t pme_side_rejoin(nb_ctx *ctx) { return cudaEventRecord(ctx->pme->join, ctx->pme->side); }
 
 cudaError_t launch_pme_join(nb_ctx *ctx)
 {
@@ -821,6 +834,7 @@ extern "C" nb_status nb_set_pme(nb_ctx *ctx, const nb_pme_params *p)
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->lists, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         pme_free(ctx);
         return e == cudaErrorMemoryAllocation ? NB_ERR_OOM : NB_ERR_CUDA;
