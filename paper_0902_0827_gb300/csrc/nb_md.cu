@@ -62,6 +62,8 @@ struct MdState {
     long long *acc = nullptr;              // [kMdAcc]
     unsigned long long *step = nullptr;    // [1] device step counter
     unsigned *amax = nullptr;              // [2] minimisation: largest |F_i| / m_i (float bits), two slots
+    cudaStream_t bside = nullptr;          // the bonded terms' stream beside the short-range path (with PME)
+    cudaEvent_t bfork = nullptr, bjoin = nullptr;
 };
 
 // ------------------------------------------------------------------ Philox
@@ -757,6 +759,12 @@ void md_free(nb_ctx *ctx)
                  m->dihedral_p, m->waters, m->Fnb, m->Ftot, m->bacc, m->enb, m->acc, m->step, m->amax};
     for (void *q : p)
         if (q) cudaFree(q);
+    if (m->bside) {
+        cudaStreamSynchronize(m->bside);
+        cudaStreamDestroy(m->bside);
+    }
+    if (m->bfork) cudaEventDestroy(m->bfork);
+    if (m->bjoin) cudaEventDestroy(m->bjoin);
     delete m;
     ctx->md = nullptr;
 }
@@ -777,8 +785,9 @@ static cudaError_t launch_bonded(nb_ctx *ctx, cudaStream_t st, const float *d_po
 // bonded terms.  The PME chain needs the sorted atoms but not the pair
 // lists, so it is forked onto its side stream right after the column sort
 // and the charge pack: it overlaps the list kernel and the short-range
-// kernel; the bonded terms (positions only) run first on that stream, off
-// the short-range path.  sums: the energies of this evaluation are
+// kernel, and behind it a helper launch of the short-range kernel takes
+// units from the same counter; the bonded terms (positions only) run on a
+// stream of their own, off both.  sums: the energies of this evaluation are
 // reported (the PME pair-correction energies are summed only then).
 static cudaError_t md_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, const int32_t *d_type, bool sums,
                              bool unpack = true)
@@ -786,12 +795,20 @@ static cudaError_t md_forces(nb_ctx *ctx, const float *d_pos, const float *d_q, 
     MdState &M = *ctx->md;
     cudaError_t e = launch_build_cells(ctx, d_pos, d_q, d_type);  // q and types packed on the way
     const bool pme = ctx->pme != nullptr;
-    if (e == cudaSuccess && pme) e = launch_pme_fork(ctx, d_pos, d_q, sums, launch_bonded);
+    const bool bside = pme && M.nb + M.na + M.nd > 0;
+    if (e == cudaSuccess && bside) {
+        e = cudaEventRecord(M.bfork, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(M.bside, M.bfork, 0);
+        if (e == cudaSuccess) e = launch_bonded(ctx, M.bside, d_pos);
+        if (e == cudaSuccess) e = cudaEventRecord(M.bjoin, M.bside);
+    }
+    if (e == cudaSuccess && pme) e = launch_pme_fork(ctx, d_pos, d_q, sums);
     if (e == cudaSuccess) e = launch_build_lists(ctx);
     if (e != cudaSuccess) return e;
     ctx->built = true;
-    e = launch_forces_packed(ctx, unpack ? M.Fnb : nullptr, unpack ? M.enb : nullptr, nullptr, false, pme, pme);
-    if (e != cudaSuccess || pme) return e;  // with PME the join above waited for the bonded terms too
+    e = launch_forces_packed(ctx, unpack ? M.Fnb : nullptr, unpack ? M.enb : nullptr, nullptr, false, pme, pme, pme);
+    if (e != cudaSuccess) return e;
+    if (pme) return bside ? cudaStreamWaitEvent(ctx->stream, M.bjoin, 0) : cudaSuccess;
     return launch_bonded(ctx, ctx->stream, d_pos);
 }
 
@@ -843,6 +860,12 @@ extern "C" nb_status nb_md_init(nb_ctx *ctx, const nb_md_params *p)
     md_free(ctx);
     MdState *M = new MdState();
     ctx->md = M;
+    if (cudaStreamCreateWithFlags(&M->bside, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&M->bfork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&M->bjoin, cudaEventDisableTiming) != cudaSuccess) {
+        md_free(ctx);
+        return NB_ERR_CUDA;
+    }
     M->n = N;
     M->nb = p->n_bonds;
     M->na = p->n_angles;
