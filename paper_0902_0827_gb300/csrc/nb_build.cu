@@ -640,7 +640,7 @@ struct GListArgs {
     int K;
     float rcm;
     int cap;                 // entries per group (all segments)
-    int group;               // clusters per group of this build (records hold `group` mask pairs)
+    int group;               // clusters per group of the lists being built (records hold `group` mask pairs)
 };
 
 constexpr int kGListWarps = 4;  // groups (warps) per block of the list kernel
