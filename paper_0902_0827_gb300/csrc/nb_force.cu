@@ -1382,9 +1382,16 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_adjoint1(ForceArgs A, int pa
         int u_next = 0;
         if (lane == 0) u_next = atomicAdd(A.work, 1);
         const Unit U = unit_of(A, u, parts);
+        // as in k_force1: what needs only the unit's group and segment is
+        // loaded before the segment's length is known
+        const int I = U.g;  // one-cluster groups are numbered like their clusters
+        const int sys_id = __ldg(A.clus_sys + I);
+        const long long s0 = (long long)I * kCluster;
+        const TileIA ia = load_tile_ia(A, s0 + ih, T);
+        const TileIA ib = load_tile_ia(A, s0 + ih + 4, T);
+        const uint2 *row = A.glist + U.base;
+        const uint2 first = lane < A.cap / kListSegs ? __ldg(row + lane) : make_uint2(0u, 0u);
         if (U.e_begin < U.e_end) {
-            const int I = U.g;  // one-cluster groups are numbered like their clusters
-            const int sys_id = __ldg(A.clus_sys + I);
             if (sys_id != cur_sys) {
                 cur_sys = sys_id;
                 Lx = A.sys[sys_id].L[0];
@@ -1393,14 +1400,10 @@ __global__ void __launch_bounds__(kAdjWarps * 32) k_adjoint1(ForceArgs A, int pa
                 gE_lj = A.dLdE ? (float)A.dLdE[2 * sys_id] : 0.0f;
                 gE_c = A.dLdE ? (float)A.dLdE[2 * sys_id + 1] : 0.0f;
             }
-            const long long s0 = (long long)I * kCluster;
-            const TileIA ia = load_tile_ia(A, s0 + ih, T);
-            const TileIA ib = load_tile_ia(A, s0 + ih + 4, T);
             AccAdj acA = {0.0f, 0.0f, 0.0f, 0.0f}, acB = {0.0f, 0.0f, 0.0f, 0.0f};
-            const uint2 *row = A.glist + U.base;
             for (int e0 = U.e_begin; e0 < U.e_end; e0 += kBatchA) {
                 const int ne = min(kBatchA, U.e_end - e0);
-                const uint2 my = lane < ne ? __ldg(row + e0 + lane) : make_uint2(0u, 0u);
+                const uint2 my = lane < ne ? (e0 == 0 ? first : __ldg(row + e0 + lane)) : make_uint2(0u, 0u);
                 if (lane < ne) {
                     const long long jbase = (long long)(my.x & kJMask) * kCluster;
 #pragma unroll
