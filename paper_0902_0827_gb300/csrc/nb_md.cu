@@ -288,22 +288,25 @@ __device__ __forceinline__ float3 kick_drift(int a, float dt, float c, bool lang
                                              const float *__restrict__ sigv, const float *__restrict__ Ftot,
                                              const float *__restrict__ x, float *__restrict__ v)
 {
+    // every load is issued first and the noise computed while they are in flight
     float vx = v[3ll * a], vy = v[3ll * a + 1], vz = v[3ll * a + 2];
+    const float sa = langevin ? sigv[a] : 0.0f, ma = mass[a];
+    const float f0 = Ftot[3ll * a], f1 = Ftot[3ll * a + 1], f2 = Ftot[3ll * a + 2];
+    const float x0 = x[3ll * a], x1 = x[3ll * a + 1], x2 = x[3ll * a + 2];
     if (langevin) {
         const float3 xi = md_normals((unsigned)a, step, 0u, seed);
-        const float s = sigv[a];
-        vx = fmaf(c, vx, s * xi.x);
-        vy = fmaf(c, vy, s * xi.y);
-        vz = fmaf(c, vz, s * xi.z);
+        vx = fmaf(c, vx, sa * xi.x);
+        vy = fmaf(c, vy, sa * xi.y);
+        vz = fmaf(c, vz, sa * xi.z);
     }
-    const float h = 0.5f * dt * kAccel / mass[a];
-    vx = fmaf(h, Ftot[3ll * a], vx);
-    vy = fmaf(h, Ftot[3ll * a + 1], vy);
-    vz = fmaf(h, Ftot[3ll * a + 2], vz);
+    const float h = 0.5f * dt * kAccel / ma;
+    vx = fmaf(h, f0, vx);
+    vy = fmaf(h, f1, vy);
+    vz = fmaf(h, f2, vz);
     v[3ll * a] = vx;
     v[3ll * a + 1] = vy;
     v[3ll * a + 2] = vz;
-    return make_float3(fmaf(dt, vx, x[3ll * a]), fmaf(dt, vy, x[3ll * a + 1]), fmaf(dt, vz, x[3ll * a + 2]));
+    return make_float3(fmaf(dt, vx, x0), fmaf(dt, vy, x1), fmaf(dt, vz, x2));
 }
 
 // B and O (stream 1) of atom a with the new forces (v updated in place).
@@ -313,24 +316,28 @@ __device__ __forceinline__ float3 kick(int a, float dt, float c, bool langevin, 
                                        long long *__restrict__ bacc, float *__restrict__ Ftot, float *__restrict__ v)
 {
     const float sc = 2.3283064365386963e-10f;  // 2^-32
+    // every load is issued first and the noise (integer and special-function
+    // work that needs none of them) computed while they are in flight
     const float3 fn = nb_force_of(Nb, a);
-    const float fx = fn.x + __ll2float_rn(bacc[3ll * a]) * sc;
-    const float fy = fn.y + __ll2float_rn(bacc[3ll * a + 1]) * sc;
-    const float fz = fn.z + __ll2float_rn(bacc[3ll * a + 2]) * sc;
+    const long long b0 = bacc[3ll * a], b1 = bacc[3ll * a + 1], b2 = bacc[3ll * a + 2];
+    const float ma = mass[a], sa = langevin ? sigv[a] : 0.0f;
+    const float v0 = v[3ll * a], v1 = v[3ll * a + 1], v2 = v[3ll * a + 2];
+    const float3 xi = langevin ? md_normals((unsigned)a, step, 1u, seed) : make_float3(0.0f, 0.0f, 0.0f);
+    const float fx = fn.x + __ll2float_rn(b0) * sc;
+    const float fy = fn.y + __ll2float_rn(b1) * sc;
+    const float fz = fn.z + __ll2float_rn(b2) * sc;
     bacc[3ll * a] = 0;
     bacc[3ll * a + 1] = 0;
     bacc[3ll * a + 2] = 0;
     Ftot[3ll * a] = fx;
     Ftot[3ll * a + 1] = fy;
     Ftot[3ll * a + 2] = fz;
-    const float h = 0.5f * dt * kAccel / mass[a];
-    float vx = fmaf(h, fx, v[3ll * a]), vy = fmaf(h, fy, v[3ll * a + 1]), vz = fmaf(h, fz, v[3ll * a + 2]);
+    const float h = 0.5f * dt * kAccel / ma;
+    float vx = fmaf(h, fx, v0), vy = fmaf(h, fy, v1), vz = fmaf(h, fz, v2);
     if (langevin) {
-        const float3 xi = md_normals((unsigned)a, step, 1u, seed);
-        const float s = sigv[a];
-        vx = fmaf(c, vx, s * xi.x);
-        vy = fmaf(c, vy, s * xi.y);
-        vz = fmaf(c, vz, s * xi.z);
+        vx = fmaf(c, vx, sa * xi.x);
+        vy = fmaf(c, vy, sa * xi.y);
+        vz = fmaf(c, vz, sa * xi.z);
     }
     v[3ll * a] = vx;
     v[3ll * a + 1] = vy;
