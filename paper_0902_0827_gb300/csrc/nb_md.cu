@@ -386,14 +386,20 @@ struct MdStep {
 // positions x to the unconstrained new positions xn: the displacements dsp
 // that restore |r_k''|^2 = d_k^2; false when max_iter iterations did not
 // reach the tolerance.
-__device__ __forceinline__ bool water_shake(const int (&at)[3], const float3 (&xn)[3], const float (&im)[3],
-                                            const float *__restrict__ x, const Box3 &B, const MdStep &P,
-                                            float3 (&dsp)[3])
+// The reference bond vectors r_k = x_a - x_b of a water (minimum image).
+__device__ __forceinline__ void water_bonds(const int (&at)[3], const float *__restrict__ x, const Box3 &B,
+                                            float3 (&r)[3])
 {
-    float3 r[3], u[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) r[k] = disp(x, at[con_b(k)], at[con_a(k)], B);
+}
+
+__device__ __forceinline__ bool water_shake(const float3 (&r)[3], const float3 (&xn)[3], const float (&im)[3],
+                                            const Box3 &B, const MdStep &P, float3 (&dsp)[3])
+{
+    float3 u[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        r[k] = disp(x, at[con_b(k)], at[con_a(k)], B);  // x_a - x_b
         const float3 pa = xn[con_a(k)], pb = xn[con_b(k)];
         u[k] = make_float3(min_img(pa.x - pb.x, B.L[0], B.h[0]), min_img(pa.y - pb.y, B.L[1], B.h[1]),
                            min_img(pa.z - pb.z, B.L[2], B.h[2]));
@@ -519,6 +525,8 @@ __global__ void __launch_bounds__(64) k_md_first(int n_free, int nw, MdStep P,
     const int4 W = L.active ? waters[L.item] : make_int4(0, 0, 0, 0);
     const int at[3] = {W.x, W.y, W.z};
     const int a = L.i == 0 ? at[0] : (L.i == 1 ? at[1] : at[2]);
+    float3 r[3];  // the reference bonds (loads issued before the kick)
+    if (L.active) water_bonds(at, x, B, r);
     float3 mine = make_float3(0.0f, 0.0f, 0.0f);
     float im_mine = 1.0f;
     if (L.active) {
@@ -534,7 +542,7 @@ __global__ void __launch_bounds__(64) k_md_first(int n_free, int nw, MdStep P,
         im[k] = __shfl_sync(0xffffffffu, im_mine, base + k);
     }
     float3 dsp[3];
-    if (L.active && !water_shake(at, xn, im, x, B, P, dsp) && L.i == 0) atomicOr(status, ST_TIMEOUT);
+    if (L.active && !water_shake(r, xn, im, B, P, dsp) && L.i == 0) atomicOr(status, ST_TIMEOUT);
     __syncwarp();  // the three lanes read the reference positions x before any writes them
     if (!L.active) return;
     const float3 d = L.i == 0 ? dsp[0] : (L.i == 1 ? dsp[1] : dsp[2]);
@@ -580,6 +588,8 @@ __global__ void __launch_bounds__(64) k_md_second(int n_free, int nw, MdStep P,
         const int4 W = L.active ? waters[L.item] : make_int4(0, 0, 0, 0);
         const int at[3] = {W.x, W.y, W.z};
         const int a = L.i == 0 ? at[0] : (L.i == 1 ? at[1] : at[2]);
+        float3 r[3];  // the bonds (loads issued before the kick)
+        if (L.active) water_bonds(at, x, B, r);
         float3 mine = make_float3(0.0f, 0.0f, 0.0f);
         float m_mine = 1.0f;
         if (L.active) {
@@ -598,9 +608,6 @@ __global__ void __launch_bounds__(64) k_md_second(int n_free, int nw, MdStep P,
             im[k] = 1.0f / m[k];
         }
         if (L.active) {
-            float3 r[3];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) r[k] = disp(x, at[con_b(k)], at[con_a(k)], B);
             float A[3][3], b[3], mu[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
@@ -723,7 +730,9 @@ __global__ void __launch_bounds__(64) k_min_move(int n_free, int nw, MdStep P, c
                             fmaf(s, Ftot[3ll * a + 2], x[3ll * a + 2]));
     }
     float3 dsp[3];
-    if (!water_shake(at, xn, im, x, B, P, dsp)) atomicOr(status, ST_TIMEOUT);
+    float3 r[3];
+    water_bonds(at, x, B, r);
+    if (!water_shake(r, xn, im, B, P, dsp)) atomicOr(status, ST_TIMEOUT);
     // the reference vectors above read x: write the new positions afterwards
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
